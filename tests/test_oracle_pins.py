@@ -1,0 +1,260 @@
+"""Pins of the float64 oracle against what the paper and the physics fix (CPU only).
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, values printed in the paper, closed forms, exact
+diagonalisation, a library routine that reduces to the same cell, invariants
+(autoregressive normalisation, constant local energy on an eigenstate) and
+finite differences.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import exact, growth, hamiltonian, model as M, philox, vmc
+from paper_2507_18700_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lp_fn(mod, flat):
+    return lambda s: M.logpsi(mod, flat, s)
+
+
+# ---------------------------------------------------------------- Philox ----
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        out = philox.philox4x32_10([np.array([c]) for c in v[:4]], (v[4], v[5]))
+        assert [int(o[0]) for o in out] == v[6:]
+
+
+def test_philox_uniforms_are_uniform():
+    u = philox.sampling_uniforms(seed=7, step=3, B=2000, N=50).ravel()
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 3e-3
+    assert scipy.stats.kstest(u, "uniform").pvalue > 1e-3
+    z = philox.growth_normals(2, 5, 300, 300).ravel()
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    assert scipy.stats.kstest(z, "norm").pvalue > 1e-3
+
+
+# ------------------------------------------------------------------ cells ----
+def test_gru1d_cell_is_the_reset_after_gru_of_torch():
+    """The App. A cell equals torch.nn.GRUCell with z = 1 - u (weights mapped)."""
+    torch = pytest.importorskip("torch")
+    d = 5
+    mod = M.Model(M.GRU1D, 4, d_h=d)
+    p = mod.unpack(inputs.xavier_params(1, d, seed=3, noise_std=0.3))
+    cell = torch.nn.GRUCell(2, d).double()
+    with torch.no_grad():
+        cell.weight_ih.copy_(torch.from_numpy(np.concatenate(
+            [p["W_r"][:, d:], -p["W_g"][:, d:], p["W_in"]])))
+        cell.weight_hh.copy_(torch.from_numpy(np.concatenate(
+            [p["W_r"][:, :d], -p["W_g"][:, :d], p["W_h"]])))
+        cell.bias_ih.copy_(torch.from_numpy(np.concatenate([p["b_r"], -p["b_g"], p["b_in"]])))
+        cell.bias_hh.copy_(torch.from_numpy(np.concatenate([np.zeros(d), np.zeros(d), p["b_h"]])))
+    rng = np.random.default_rng(0)
+    h = rng.normal(size=(7, d))
+    x = M.onehot(rng.integers(0, 2, size=7))
+    ref = cell(torch.from_numpy(x), torch.from_numpy(h)).detach().numpy()
+    np.testing.assert_allclose(M.gru1d_cell(p, h, x), ref, rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------- normalisation (Eq. 1) ----
+@pytest.mark.parametrize("cell,Lx,Ly,d,sz0", [
+    (M.GRU1D, 10, 1, 6, False),
+    (M.GRU1D, 8, 1, 4, True),
+    (M.GRU2D, 3, 3, 4, False),
+    (M.GRU2D, 2, 4, 3, True),
+    (M.GRU2D, 4, 2, 3, False),
+])
+def test_autoregressive_normalisation(cell, Lx, Ly, d, sz0):
+    """sum_sigma P(sigma) = 1; a conditional that read a later spin would break it."""
+    mod = M.Model(cell, Lx, Ly, d_h=d, sz0=sz0)
+    flat = inputs.xavier_params(cell, d, seed=11, noise_std=0.5)
+    configs = exact.all_configs(mod.N)
+    P = np.exp(2.0 * M.logpsi(mod, flat, configs))
+    assert abs(P.sum() - 1.0) < 1e-12
+    if sz0:
+        outside = configs.sum(axis=1) != mod.N // 2
+        assert np.all(P[outside] == 0.0)
+
+
+# -------------------------------------------------------------- sampling ----
+@pytest.mark.parametrize("cell,Lx,Ly,d,sz0", [(M.GRU1D, 6, 1, 4, False),
+                                             (M.GRU2D, 2, 3, 3, True)])
+def test_sampling_frequencies_match_probabilities(cell, Lx, Ly, d, sz0):
+    mod = M.Model(cell, Lx, Ly, d_h=d, sz0=sz0)
+    flat = inputs.xavier_params(cell, d, seed=5, noise_std=0.7)
+    n = 200_000
+    u = philox.sampling_uniforms(seed=1, step=0, B=n, N=mod.N)
+    out = M.sample(mod, flat, u)
+    configs = exact.all_configs(mod.N)
+    P = np.exp(2.0 * M.logpsi(mod, flat, configs))
+    counts = np.bincount(exact.basis_index(out["sigma"]), minlength=configs.shape[0])
+    keep = P > 0
+    assert counts[~keep].sum() == 0
+    chi2 = ((counts[keep] - n * P[keep]) ** 2 / (n * P[keep])).sum()
+    dof = keep.sum() - 1
+    assert scipy.stats.chi2.sf(chi2, dof) > 1e-4
+    np.testing.assert_allclose(out["logpsi"], M.logpsi(mod, flat, out["sigma"]), atol=1e-12)
+
+
+# ------------------------------------------------ ground energies (pins) ----
+def test_free_fermion_matches_closed_form_and_ed():
+    for N in (2, 5, 10):
+        assert abs(exact.tfim_free_fermion(N, 1.0, 1.0) - exact.tfim_closed_form_critical(N)) < 1e-12
+    for G in (0.5, 1.0, 1.5, 2.0):
+        e_ed, _ = exact.ground_state(exact.tfim_hamiltonian(10, 1.0, G))
+        assert abs(e_ed - exact.tfim_free_fermion(10, 1.0, G)) < 1e-10
+
+
+def test_closed_form_matches_table1():
+    """Table I prints E_RNN and (E_RNN - E_DMRG)/|E_DMRG|; the closed form is E_DMRG."""
+    for line in open(os.path.join(GOLDEN, "table1_tfim_energies.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        N, _, E, _, rel, drel = line.split()
+        e0 = exact.tfim_closed_form_critical(int(N))
+        got = (float(E) - e0) / abs(e0) * 1e7
+        assert float(E) >= e0                       # variational bound
+        assert abs(got - float(rel)) <= float(drel) + 1.0
+
+
+def test_heisenberg_textbook_ground_energies():
+    # two spins: singlet -3/4; 2x2 open square = four-site ring: -2
+    assert abs(exact.ground_state(exact.heisenberg_hamiltonian(2, 1))[0] + 0.75) < 1e-12
+    assert abs(exact.ground_state(exact.heisenberg_hamiltonian(2, 2))[0] + 2.0) < 1e-12
+    # four-site open chain: -(3/4 + sqrt(3)/2)
+    assert abs(exact.ground_state(exact.heisenberg_hamiltonian(4, 1))[0]
+               + 0.75 + np.sqrt(3) / 2) < 1e-12
+    # the Marshall rotation is a unitary: same spectrum
+    for Lx, Ly in ((2, 3), (3, 2), (2, 4)):
+        a = np.linalg.eigvalsh(exact.heisenberg_hamiltonian(Lx, Ly).toarray())
+        b = np.linalg.eigvalsh(exact.heisenberg_hamiltonian(Lx, Ly, marshall=True).toarray())
+        np.testing.assert_allclose(a, b, atol=1e-11)
+
+
+# ----------------------------------- local energy on an exact eigenstate ----
+@pytest.mark.parametrize("Gamma", [0.5, 1.0, 2.0])
+def test_tfim_local_energy_is_constant_on_ground_state(Gamma):
+    N = 10
+    e0, v = exact.ground_state(exact.tfim_hamiltonian(N, 1.0, Gamma))
+    psi = np.abs(v)                       # Perron-Frobenius: one sign
+    table = np.log(psi)
+    lp = lambda s: table[exact.basis_index(s)]
+    configs = exact.all_configs(N)
+    el = hamiltonian.tfim_local_energy(N, 1.0, Gamma, configs, lp)
+    np.testing.assert_allclose(el, e0, atol=1e-9)
+    assert abs(e0 - exact.tfim_free_fermion(N, 1.0, Gamma)) < 1e-10
+
+
+@pytest.mark.parametrize("Lx,Ly", [(2, 2), (2, 4), (4, 3)])
+def test_heisenberg_local_energy_is_constant_on_ground_state(Lx, Ly):
+    N = Lx * Ly
+    configs = exact.sz0_configs(N)
+    sector = exact.basis_index(configs)
+    Hm = exact.heisenberg_hamiltonian(Lx, Ly, marshall=True)
+    e0, v = exact.ground_state(Hm, restrict=sector)
+    psi = np.abs(v)
+    assert np.all(psi > 1e-12)            # positive after the Marshall rotation
+    full = np.full(2 ** N, -np.inf)
+    full[sector] = np.log(psi)
+    lp = lambda s: full[exact.basis_index(s)]
+    el = hamiltonian.heisenberg_local_energy(Lx, Ly, 1.0, True, configs, lp)
+    np.testing.assert_allclose(el, e0, atol=1e-8)
+    e_plain, _ = exact.ground_state(exact.heisenberg_hamiltonian(Lx, Ly), restrict=sector)
+    assert abs(e0 - e_plain) < 1e-10
+
+
+# ---------------------------------------- exact energy by two routes ----
+def test_rnn_energy_two_routes_tfim():
+    N, d = 8, 5
+    mod = M.Model(M.GRU1D, N, d_h=d)
+    flat = inputs.xavier_params(1, d, seed=2, noise_std=0.3)
+    configs = exact.all_configs(N)
+    lpsi = M.logpsi(mod, flat, configs)
+    P = np.exp(2 * lpsi)
+    el = hamiltonian.tfim_local_energy(N, 1.0, 1.0, configs, _lp_fn(mod, flat))
+    e_sum = exact.exact_energy(P, el)
+    psi = np.exp(lpsi)
+    Hm = exact.tfim_hamiltonian(N, 1.0, 1.0)
+    assert abs(e_sum - psi @ (Hm @ psi)) < 1e-11
+    assert e_sum >= exact.tfim_free_fermion(N, 1.0, 1.0)
+
+
+def test_rnn_energy_two_routes_heisenberg():
+    Lx, Ly, d = 2, 4, 4
+    mod = M.Model(M.GRU2D, Lx, Ly, d_h=d, sz0=True)
+    flat = inputs.xavier_params(2, d, seed=4, noise_std=0.3)
+    configs = exact.sz0_configs(mod.N)
+    lpsi = M.logpsi(mod, flat, configs)
+    P = np.exp(2 * lpsi)
+    el = hamiltonian.heisenberg_local_energy(Lx, Ly, 1.0, True, configs, _lp_fn(mod, flat))
+    e_sum = exact.exact_energy(P, el)
+    psi = np.zeros(2 ** mod.N)
+    psi[exact.basis_index(configs)] = np.exp(lpsi)
+    Hm = exact.heisenberg_hamiltonian(Lx, Ly, marshall=True)
+    assert abs(e_sum - psi @ (Hm @ psi)) < 1e-11
+    e0, _ = exact.ground_state(Hm, restrict=exact.basis_index(configs))
+    assert e_sum >= e0
+
+
+def test_energy_stats():
+    st = vmc.energy_stats([1.0, 2.0, 3.0, 6.0])
+    np.testing.assert_allclose(st, [3.0, 3.5, 4.0])
+
+
+# ------------------------------------------------------------- gradients ----
+@pytest.mark.parametrize("cell,Lx,Ly,d,sz0", [(M.GRU1D, 5, 1, 3, False),
+                                             (M.GRU2D, 2, 3, 3, False),
+                                             (M.GRU2D, 3, 2, 2, True)])
+def test_logpsi_gradient_matches_finite_differences(cell, Lx, Ly, d, sz0):
+    mod = M.Model(cell, Lx, Ly, d_h=d, sz0=sz0)
+    flat = inputs.xavier_params(cell, d, seed=8, noise_std=0.4)
+    sig = inputs.random_configs(6, mod.N, seed=9, sz0=sz0).astype(np.int64)
+    w = inputs.random_weights(6, seed=10)
+    g = vmc.logpsi_grad(mod, flat, sig, w)
+    fd = exact.central_fd(lambda x: float(w @ M.logpsi(mod, x, sig)), flat, h=1e-5)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_exact_gradient_matches_fd_of_exact_energy():
+    """d/dtheta <psi|H|psi> (dense H, enumeration) = sum P (E_loc - E) d log P."""
+    N, d = 6, 3
+    mod = M.Model(M.GRU1D, N, d_h=d)
+    flat = inputs.xavier_params(1, d, seed=12, noise_std=0.4)
+    configs = exact.all_configs(N)
+    Hm = exact.tfim_hamiltonian(N, 1.0, 0.7)
+
+    def energy(x):
+        psi = np.exp(M.logpsi(mod, x, configs))
+        return psi @ (Hm @ psi)
+
+    P = np.exp(2 * M.logpsi(mod, flat, configs))
+    el = hamiltonian.tfim_local_energy(N, 1.0, 0.7, configs, _lp_fn(mod, flat))
+    g = exact.exact_gradient(mod, flat, configs, P, el)
+    fd = exact.central_fd(energy, flat, h=1e-5)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+# ---------------------------------------------------------------- growth ----
+@pytest.mark.parametrize("cell,Lx,Ly,sz0", [(M.GRU1D, 8, 1, False), (M.GRU2D, 2, 4, True)])
+def test_growth_with_zero_noise_keeps_the_wave_function(cell, Lx, Ly, sz0):
+    small = M.Model(cell, Lx, Ly, d_h=3, sz0=sz0)
+    big = M.Model(cell, Lx, Ly, d_h=6, sz0=sz0)
+    ps = inputs.xavier_params(cell, 3, seed=13, noise_std=0.3)
+    pb = growth.grow(small, ps, big, seed=2, eps=0.0)
+    configs = exact.sz0_configs(small.N) if sz0 else exact.all_configs(small.N)
+    np.testing.assert_allclose(M.logpsi(big, pb, configs), M.logpsi(small, ps, configs),
+                               atol=1e-13)
+    pe = growth.grow(small, ps, big, seed=2, eps=1e-3)
+    diff = np.abs(M.logpsi(big, pe, configs) - M.logpsi(small, ps, configs))
+    assert 0 < diff.max() < 1e-3 * small.N
+    new = np.abs(pe - pb)
+    assert np.count_nonzero(new) == big.param_count() - small.param_count()
+    assert abs(new[new > 0].mean() - 1e-3 * np.sqrt(2 / np.pi)) < 2e-4
