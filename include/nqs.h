@@ -1,0 +1,196 @@
+/*
+ * libnqs -- C ABI of the GB300 (sm_103a) hot path of variational Monte Carlo
+ * with recurrent-neural-network wave functions ("Adaptive Neural Quantum
+ * States: A Recurrent Neural Network Perspective", arXiv 2507.18700).
+ *
+ * The library evaluates, for one set of RNN weights, the per-step work of VMC:
+ * autoregressive sampling, teacher-forced log psi, local energies with
+ * prefix-cached connected configurations, the VMC gradient (a hand-written
+ * reverse sweep) and the hidden-dimension growth step.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * - Spins sigma in {0, 1}; 0 is spin up (sigma^z = +1).  The one-hot input of
+ *   a spin is e_sigma and "no input" (the first site; a 2D neighbour outside
+ *   the lattice) is the zero vector, with h = 0 (Sec. II, Eq. 2).
+ * - Configurations are uint8 arrays [B, N] in lattice order: index j*Lx + i
+ *   for column i, row j (1D: Ly = 1).
+ * - Sampling order: 1D left to right; 2D zig-zag, row 0 left to right, odd
+ *   rows right to left; the 2D cell reads the horizontal neighbour
+ *   i - (-1)^j of its own row and the vertical neighbour (i, j-1)
+ *   (Sec. II and Fig. 1(b)).
+ * - log psi = 1/2 sum_n log p_n(sigma_n): positive RNN wave function, psi =
+ *   sqrt(P) (Sec. II), with the two-outcome softmax of Eq. (3).
+ * - Optional zero-magnetisation mask (sz0): once N/2 spins of the prefix are
+ *   up the remaining ones are down with probability 1, and vice versa.
+ *
+ * Flat float32 parameter layout (row-major tensors, in this order)
+ * ----------------------------------------------------------------
+ * NQS_GRU1D (App. A, 1D GRU), d = d_h:
+ *   W_g[d, d+2]  W_r[d, d+2]  W_h[d, d]  W_in[d, 2]
+ *   b_g[d]  b_r[d]  b_h[d]  b_in[d]  U[2, d]  c[2]
+ *   (columns of W_g, W_r: [h_{n-1} | one-hot sigma_{n-1}])
+ *   u = sigmoid(W_g[h;s] + b_g), r = sigmoid(W_r[h;s] + b_r),
+ *   h~ = tanh(r * (W_h h + b_h) + W_in s + b_in), h' = (1 - u) h + u h~.
+ * NQS_GRU2D (App. A, 2D GRU with GLU head), d = d_h, m = d_model:
+ *   W[d, 2d+4]  W_g[d, 2d+4]  U_mix[d, 2d]  b[d]  b_g[d]
+ *   W_1[m, d]  b_1[m]  W_2[m, d]  b_2[m]  U_out[2, m]  c[2]
+ *   (columns of W, W_g: [h_hor | h_ver | s_hor | s_ver])
+ *   h~ = tanh(W[h';s'] + b), u = sigmoid(W_g[h';s'] + b_g),
+ *   h = u h~ + (1 - u) U_mix h', y = (W_1 h + b_1) * sigmoid(W_2 h + b_2),
+ *   logits = U_out y + c.
+ *
+ * Ownership, streams and errors
+ * -----------------------------
+ * - The caller owns every buffer: params, inputs, outputs and the workspace
+ *   (size from nqs_workspace_bytes, 256-byte aligned).  Pointers named
+ *   "device" must be device (or managed) memory of the current device.
+ *   The library allocates no memory.
+ * - Every call only enqueues work on `stream` (a cudaStream_t; NULL is the
+ *   legacy default stream) and returns; results are ready when the stream is.
+ * - Arguments are checked on the host before anything is enqueued; a bad
+ *   argument returns an error and enqueues nothing.  The library never aborts.
+ * - A kernel that meets a non-finite log psi or local energy records
+ *   NQS_ENONFINITE in the workspace status word; read it with
+ *   nqs_workspace_status after the stream has drained.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NQS_OK = 0,
+  NQS_EINVAL = 1,        /* null pointer, bad enum, bad size */
+  NQS_ESHAPE = 2,        /* unsupported lattice / hidden size combination */
+  NQS_EWORKSPACE = 3,    /* workspace missing, misaligned or too small */
+  NQS_ECUDA = 4,         /* a CUDA runtime call failed */
+  NQS_ETIMEOUT = 5,      /* a device wait gave up (recorded in the workspace) */
+  NQS_ENONFINITE = 6,    /* non-finite value met on the device (workspace) */
+  NQS_EUNSUPPORTED = 7   /* valid but not built (e.g. model/Hamiltonian pair) */
+} nqs_status;
+
+enum { NQS_GRU1D = 1, NQS_GRU2D = 2 };
+enum { NQS_FP32 = 0, NQS_BF16 = 1 };
+enum { NQS_TFIM = 1, NQS_HEISENBERG = 2 };
+enum {
+  NQS_OP_SAMPLE = 1,
+  NQS_OP_LOGPSI = 2,
+  NQS_OP_LOCAL_ENERGY = 3,
+  NQS_OP_LOGPSI_GRAD = 4,
+  NQS_OP_VMC_GRAD = 5
+};
+
+typedef struct {
+  int32_t cell;       /* NQS_GRU1D | NQS_GRU2D */
+  int32_t Lx, Ly;     /* N = Lx * Ly; 1D: Ly = 1 */
+  int32_t d_h;        /* hidden size: 8, 16, 32, 64 or 128 */
+  int32_t d_model;    /* 2D GLU width; must equal d_h (App. A) ; 0 means d_h */
+  int32_t sz0;        /* 1: zero-magnetisation mask (needs N even) */
+  int32_t precision;  /* NQS_FP32 | NQS_BF16 (GEMM operands; state stays FP32) */
+} nqs_model_desc;
+
+typedef struct {
+  int32_t kind;       /* NQS_TFIM (1D GRU) | NQS_HEISENBERG (2D GRU) */
+  int32_t marshall;   /* Heisenberg: 1 = Marshall-rotated exchange (-J/2) */
+  double J;           /* coupling J */
+  double h;           /* TFIM transverse field Gamma (ignored for Heisenberg) */
+} nqs_ham_desc;
+
+/* Number of float32 parameters of the flat layout above; 0 if desc is invalid. */
+size_t nqs_param_count(const nqs_model_desc* desc);
+
+/* Workspace bytes that `op` (NQS_OP_*) needs for B samples; 0 if invalid.
+ * ham may be NULL except for NQS_OP_LOCAL_ENERGY. */
+size_t nqs_workspace_bytes(const nqs_model_desc* desc, const nqs_ham_desc* ham,
+                           int64_t B, int op);
+
+/* Hidden-dimension growth, Sec. II B and Fig. 2(b): embed the parameters of the
+ * trained model `small` into the larger model `big` (same cell and lattice,
+ * d_h(big) >= d_h(small)).  Old blocks keep their indices; every hidden-input
+ * column group is laid out [old units | new units] followed by the one-hot
+ * columns; every entry without a counterpart in `small` is eps * z, z a
+ * standard normal from Philox4x32-10 keyed by (seed, tensor index in the
+ * layout, row, column) through Box-Muller.
+ *   p_small  device, nqs_param_count(small) floats (read)
+ *   p_big    device, nqs_param_count(big) floats (written)            */
+nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
+                           const nqs_model_desc* big, float* p_big,
+                           uint64_t seed, float eps, void* stream);
+
+/* Exact autoregressive ("perfect") sampling, Sec. II and Eq. (1)-(3): B
+ * independent configurations, site by site in sampling order;
+ * sigma_n = 0 iff u_n < p_n(sigma_n = 0).
+ *   uniforms device [B, N] float in [0,1) indexed by sampling position, or
+ *            NULL: u_n is drawn from Philox4x32-10 with key = seed and
+ *            counter = (n, b, step & 0xffffffff, step >> 32), u = (x0>>8)/2^24
+ *   sigma    device [B, N] uint8 (written, lattice order)
+ *   logpsi   device [B] float (written)
+ *   hcache   device [B, N, d_h] float or NULL: hidden state h_n used for the
+ *            conditional of site n (lattice order) -- the prefix cache that
+ *            nqs_local_energy and the gradient calls read.            */
+nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B,
+                      uint64_t seed, uint64_t step, const float* uniforms,
+                      uint8_t* sigma, float* logpsi, float* hcache,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Teacher-forced log psi(sigma) = 1/2 sum_n log p_n(sigma_n) (Eq. 1, pRNN).
+ *   sigma  device [B, N] uint8 (read); logpsi device [B] float (written);
+ *   hcache device [B, N, d_h] float or NULL (written, as in nqs_sample). */
+nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params,
+                      const uint8_t* sigma, int64_t B, float* logpsi, float* hcache,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Local energies E_loc(sigma) = sum_sigma' H[sigma, sigma'] psi(sigma')/psi(sigma):
+ *   NQS_TFIM (Eq. tfim, open chain, GRU1D):
+ *     -J sum s_i s_{i+1} - h sum_i psi(flip_i sigma)/psi(sigma);
+ *   NQS_HEISENBERG (Eq. heisenberg, open square lattice, GRU2D, Pauli/4):
+ *     per bond +J/4 (parallel) or -J/4 + x exp(Delta) (antiparallel), with
+ *     x = -J/2 when marshall = 1 (Marshall rotation, Sec. III B), +J/2 otherwise.
+ * Each ratio is exp(Delta) with Delta accumulated from the first changed
+ * site on, restarting the recurrence from the cached hidden states.
+ *   sigma  device [B, N] uint8; hcache device [B, N, d_h] float from
+ *          nqs_sample/nqs_logpsi with the same params (required);
+ *   eloc   device [B] float (written).                                   */
+nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
+                            const nqs_ham_desc* ham, const uint8_t* sigma,
+                            const float* hcache, int64_t B, float* eloc,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient of L = sum_b w_b log psi(sigma_b) with respect to the flat
+ * parameters, by a reverse sweep over the unrolled recurrence.
+ *   weights device [B] float; hcache as above (required);
+ *   grad    device [P] float (written; per-block partials are summed in FP64). */
+nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params,
+                           const uint8_t* sigma, const float* hcache,
+                           const float* weights, int64_t B, float* grad,
+                           void* ws, size_t ws_bytes, void* stream);
+
+/* VMC step statistics and gradient (Sec. III; the paper follows Hibat-Allah
+ * et al. 2020 and prints no formula -- the estimator used is
+ *   g = (2/M) sum_b (E_loc,b - mean E_loc) d log psi(sigma_b)/d theta,
+ * with E_loc held constant).
+ *   eloc  device [B] float (read); grad device [P] float (written);
+ *   stats device [3] double (written): mean E_loc, variance (1/M), M.  */
+nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,
+                        const uint8_t* sigma, const float* hcache,
+                        const float* eloc, int64_t B, float* grad, double* stats,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* Copy the workspace status word to *device_status (an nqs_status) after
+ * waiting for `stream`; clears it.  This call blocks the host. */
+nqs_status nqs_workspace_status(void* ws, int32_t* device_status, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* nqs_status_string(nqs_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NQS_H */

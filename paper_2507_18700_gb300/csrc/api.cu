@@ -1,0 +1,293 @@
+// C-ABI entry points of libnqs (include/nqs.h): argument checks on the host,
+// workspace carving, and kernel dispatch.  Nothing here allocates memory.
+#include <cstring>
+
+#include "kernels.h"
+
+using namespace nqs;
+
+namespace {
+
+struct Dims {
+  int cell, Lx, Ly, N, d, m, sz0, precision;
+  size_t P;
+};
+
+bool valid_hidden(int d) { return gru1d_supported(d); }
+
+nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
+  if (!desc) return NQS_EINVAL;
+  Dims d{};
+  d.cell = desc->cell;
+  d.Lx = desc->Lx;
+  d.Ly = desc->Ly;
+  d.d = desc->d_h;
+  d.m = desc->d_model == 0 ? desc->d_h : desc->d_model;
+  d.sz0 = desc->sz0;
+  d.precision = desc->precision;
+  if (d.cell != NQS_GRU1D && d.cell != NQS_GRU2D) return NQS_EINVAL;
+  if (d.precision != NQS_FP32 && d.precision != NQS_BF16) return NQS_EINVAL;
+  if (d.sz0 != 0 && d.sz0 != 1) return NQS_EINVAL;
+  if (d.Lx < 1 || d.Ly < 1 || (int64_t)d.Lx * d.Ly > (1 << 20)) return NQS_ESHAPE;
+  d.N = d.Lx * d.Ly;
+  if (!valid_hidden(d.d)) return NQS_ESHAPE;
+  if (d.cell == NQS_GRU1D && d.Ly != 1) return NQS_ESHAPE;
+  if (d.cell == NQS_GRU2D && d.m != d.d) return NQS_ESHAPE;
+  if (d.sz0 && (d.N % 2)) return NQS_ESHAPE;
+  if (d.cell == NQS_GRU1D)
+    d.P = 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2;
+  else
+    d.P = 6 * (size_t)d.d * d.d + 10 * (size_t)d.d + 2 * (size_t)d.m * d.d + 4 * (size_t)d.m + 2;
+  if (out) *out = d;
+  return NQS_OK;
+}
+
+// Paths built so far: FP32 1D GRU.
+nqs_status check_built(const Dims& d) {
+  if (d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
+  if (d.precision != NQS_FP32) return NQS_EUNSUPPORTED;
+  if (d.sz0) return NQS_EUNSUPPORTED;
+  return NQS_OK;
+}
+
+// Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
+struct Layout {
+  size_t img, a, b, c, total;
+};
+
+Layout layout(const Dims& d, int64_t B, int op) {
+  Layout L{};
+  size_t off = sizeof(WsHeader);
+  L.img = off;
+  off += align256(gru1d_img_floats(d.d) * sizeof(float));
+  const size_t BN = (size_t)B * (size_t)d.N;
+  switch (op) {
+    case NQS_OP_LOCAL_ENERGY:
+      L.a = off; off += align256(BN * sizeof(float));        // dlog
+      L.b = off; off += align256(BN * sizeof(float));        // delta
+      break;
+    case NQS_OP_LOGPSI_GRAD:
+    case NQS_OP_VMC_GRAD: {
+      const size_t grid = (size_t)gru1d_bptt_grid(d.d, B);
+      L.a = off; off += align256(grid * d.P * sizeof(float)); // partial gradients
+      L.b = off; off += align256((size_t)B * sizeof(float));   // weights
+      break;
+    }
+    default:
+      break;
+  }
+  L.total = off;
+  return L;
+}
+
+nqs_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
+  if (!ws) return NQS_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return NQS_EWORKSPACE;
+  if (ws_bytes < L.total) return NQS_EWORKSPACE;
+  return NQS_OK;
+}
+
+inline nqs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ECUDA; }
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t nqs_param_count(const nqs_model_desc* desc) {
+  Dims d;
+  if (check_desc(desc, &d) != NQS_OK) return 0;
+  return d.P;
+}
+
+size_t nqs_workspace_bytes(const nqs_model_desc* desc, const nqs_ham_desc* ham, int64_t B, int op) {
+  Dims d;
+  if (check_desc(desc, &d) != NQS_OK || B < 0) return 0;
+  if (op < NQS_OP_SAMPLE || op > NQS_OP_VMC_GRAD) return 0;
+  if (op == NQS_OP_LOCAL_ENERGY && !ham) return 0;
+  return layout(d, B, op).total;
+}
+
+const char* nqs_status_string(nqs_status s) {
+  switch (s) {
+    case NQS_OK: return "NQS_OK";
+    case NQS_EINVAL: return "NQS_EINVAL: invalid argument";
+    case NQS_ESHAPE: return "NQS_ESHAPE: unsupported shape";
+    case NQS_EWORKSPACE: return "NQS_EWORKSPACE: workspace missing, misaligned or too small";
+    case NQS_ECUDA: return "NQS_ECUDA: CUDA runtime error";
+    case NQS_ETIMEOUT: return "NQS_ETIMEOUT: device wait timed out";
+    case NQS_ENONFINITE: return "NQS_ENONFINITE: non-finite value on the device";
+    case NQS_EUNSUPPORTED: return "NQS_EUNSUPPORTED: combination not built";
+  }
+  return "NQS: unknown status";
+}
+
+nqs_status nqs_workspace_status(void* ws, int32_t* device_status, void* stream) {
+  if (!ws || !device_status) return NQS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* hdr = static_cast<WsHeader*>(ws);
+  int32_t v = 0;
+  if (cudaMemcpyAsync(&v, &hdr->status, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return NQS_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NQS_ECUDA;
+  if (cudaMemsetAsync(&hdr->status, 0, sizeof(int32_t), st) != cudaSuccess) return NQS_ECUDA;
+  *device_status = v;
+  return NQS_OK;
+}
+
+nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
+                           const nqs_model_desc* big, float* p_big, uint64_t seed, float eps,
+                           void* stream) {
+  Dims s, b;
+  nqs_status r = check_desc(small, &s);
+  if (r != NQS_OK) return r;
+  if ((r = check_desc(big, &b)) != NQS_OK) return r;
+  if (!p_small || !p_big) return NQS_EINVAL;
+  if (s.cell != b.cell || s.Lx != b.Lx || s.Ly != b.Ly) return NQS_ESHAPE;
+  if (b.d < s.d || b.m < s.m) return NQS_ESHAPE;
+  if (!(eps >= 0.0f)) return NQS_EINVAL;
+  return cuda_status(grow_params(s.cell, s.d, s.m, b.d, b.m, p_small, p_big, seed, eps,
+                                 static_cast<cudaStream_t>(stream)));
+}
+
+static nqs_status forward_common(const nqs_model_desc* desc, const float* params, int64_t B,
+                                 bool sample, uint64_t seed, uint64_t step, const float* uniforms,
+                                 const uint8_t* sigma_in, uint8_t* sigma_out, float* logpsi,
+                                 float* hcache, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (B < 0) return NQS_EINVAL;
+  if (!params) return NQS_EINVAL;
+  const Layout L = layout(d, B, sample ? NQS_OP_SAMPLE : NQS_OP_LOGPSI);
+  if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
+  if (B == 0) return NQS_OK;  // empty batch: outputs are empty, pointers may be null
+  if (!logpsi || (sample ? !sigma_out : !sigma_in)) return NQS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* img = at<float>(ws, L.img);
+  cudaError_t e = gru1d_pack(params, img, d.d, st);
+  if (e != cudaSuccess) return NQS_ECUDA;
+  Fwd1Args a{};
+  a.B = B;
+  a.N = d.N;
+  a.sigma_in = sigma_in;
+  a.sigma_out = sigma_out;
+  a.uniforms = uniforms;
+  a.seed = seed;
+  a.step = step;
+  a.logpsi = logpsi;
+  a.hcache = hcache;
+  a.hdr = static_cast<WsHeader*>(ws);
+  return cuda_status(gru1d_forward(a, img, d.d, sample, st));
+}
+
+nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B, uint64_t seed,
+                      uint64_t step, const float* uniforms, uint8_t* sigma, float* logpsi,
+                      float* hcache, void* ws, size_t ws_bytes, void* stream) {
+  return forward_common(desc, params, B, true, seed, step, uniforms, nullptr, sigma, logpsi, hcache,
+                        ws, ws_bytes, stream);
+}
+
+nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                      int64_t B, float* logpsi, float* hcache, void* ws, size_t ws_bytes,
+                      void* stream) {
+  return forward_common(desc, params, B, false, 0, 0, nullptr, sigma, nullptr, logpsi, hcache, ws,
+                        ws_bytes, stream);
+}
+
+nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
+                            const nqs_ham_desc* ham, const uint8_t* sigma, const float* hcache,
+                            int64_t B, float* eloc, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (!ham || !params || B < 0) return NQS_EINVAL;
+  if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
+  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return NQS_EINVAL;
+  if (ham->kind == NQS_TFIM && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
+  if (ham->kind == NQS_HEISENBERG) return NQS_EUNSUPPORTED;
+  const Layout L = layout(d, B, NQS_OP_LOCAL_ENERGY);
+  if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
+  if (B == 0) return NQS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WsHeader* hdr = static_cast<WsHeader*>(ws);
+  float* img = at<float>(ws, L.img);
+  float* dlog = at<float>(ws, L.a);
+  float* delta = at<float>(ws, L.b);
+  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (gru1d_readout(img, hcache, dlog, B * d.N, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (cudaMemsetAsync(&hdr->job_counter, 0, sizeof(hdr->job_counter), st) != cudaSuccess)
+    return NQS_ECUDA;
+  Chain1Args c{};
+  c.B = B;
+  c.N = d.N;
+  c.sigma = sigma;
+  c.hcache = hcache;
+  c.dlog = dlog;
+  c.delta = delta;
+  c.counter = &hdr->job_counter;
+  if (gru1d_tfim_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  return cuda_status(tfim_eloc(sigma, dlog, delta, eloc, B, d.N, (float)ham->J, (float)ham->h, hdr, st));
+}
+
+static nqs_status grad_common(const Dims& d, const Layout& L, const float* params,
+                              const uint8_t* sigma, const float* hcache, const float* weights,
+                              int64_t B, float* grad, void* ws, cudaStream_t st) {
+  float* img = at<float>(ws, L.img);
+  float* partial = at<float>(ws, L.a);
+  const int grid = gru1d_bptt_grid(d.d, B);
+  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
+    return NQS_ECUDA;
+  Bptt1Args a{};
+  a.B = B;
+  a.N = d.N;
+  a.P = (int)d.P;
+  a.sigma = sigma;
+  a.hcache = hcache;
+  a.weights = weights;
+  a.partial = partial;
+  if (gru1d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
+}
+
+nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                           const float* hcache, const float* weights, int64_t B, float* grad,
+                           void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (!params || !grad || B < 0) return NQS_EINVAL;
+  if (B > 0 && (!sigma || !hcache || !weights)) return NQS_EINVAL;
+  const Layout L = layout(d, B, NQS_OP_LOGPSI_GRAD);
+  if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (B == 0) return cuda_status(cudaMemsetAsync(grad, 0, d.P * sizeof(float), st));
+  return grad_common(d, L, params, sigma, hcache, weights, B, grad, ws, st);
+}
+
+nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                        const float* hcache, const float* eloc, int64_t B, float* grad,
+                        double* stats, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (!params || !sigma || !hcache || !eloc || !grad || !stats || B < 1) return NQS_EINVAL;
+  const Layout L = layout(d, B, NQS_OP_VMC_GRAD);
+  if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* w = at<float>(ws, L.b);
+  if (energy_stats(eloc, B, stats, st) != cudaSuccess) return NQS_ECUDA;
+  if (vmc_weights(eloc, stats, B, w, st) != cudaSuccess) return NQS_ECUDA;
+  return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
+}
+
+}  // extern "C"

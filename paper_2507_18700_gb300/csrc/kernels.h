@@ -1,0 +1,65 @@
+// Internal launcher interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nqs {
+
+struct Fwd1Args {
+  int64_t B;
+  int N;
+  const uint8_t* sigma_in;   // teacher forcing
+  uint8_t* sigma_out;        // sampling
+  const float* uniforms;     // sampling, nullable
+  uint64_t seed, step;
+  float* logpsi;
+  float* hcache;             // nullable
+  WsHeader* hdr;
+};
+
+struct Chain1Args {
+  int64_t B;
+  int N;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* dlog;         // [B, N] logit differences of the sampled path
+  float* delta;              // [B, N] log-amplitude ratio per flipped site
+  unsigned long long* counter;
+};
+
+struct Bptt1Args {
+  int64_t B;
+  int N;
+  int P;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;      // [B] dL/dlogpsi
+  float* partial;            // [grid, P]
+};
+
+int gru1d_supported(int D);
+size_t gru1d_img_floats(int D);
+int gru1d_bptt_grid(int D, int64_t B);
+cudaError_t gru1d_pack(const float* params, float* img, int D, cudaStream_t st);
+cudaError_t gru1d_forward(const Fwd1Args& a, const float* img, int D, bool sample, cudaStream_t st);
+cudaError_t gru1d_readout(const float* img, const float* hcache, float* dlog, int64_t rows, int D,
+                          cudaStream_t st);
+cudaError_t gru1d_tfim_chains(const Chain1Args& a, const float* img, int D, cudaStream_t st);
+cudaError_t tfim_eloc(const uint8_t* sigma, const float* dlog, const float* delta, float* eloc,
+                      int64_t B, int N, float J, float Gamma, WsHeader* hdr, cudaStream_t st);
+cudaError_t gru1d_bptt(const Bptt1Args& a, const float* img, int D, cudaStream_t st);
+
+// reductions (reduce.cu)
+cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
+cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);
+cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st);
+
+// growth (grow.cu)
+cudaError_t grow_params(int cell, int d, int m, int D, int Mm, const float* p_small, float* p_big,
+                        uint64_t seed, float eps, cudaStream_t st);
+
+}  // namespace nqs

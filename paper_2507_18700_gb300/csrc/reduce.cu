@@ -1,0 +1,75 @@
+// FP64 reductions of the VMC estimators (Sec. III): energy mean and variance,
+// per-sample gradient weights, and the sum of per-block partial gradients.
+#include "kernels.h"
+
+namespace nqs {
+
+// stats = [mean E_loc, mean(E_loc^2) - mean^2, M]; one block, fixed order.
+__global__ void energy_stats_kernel(const float* __restrict__ eloc, int64_t B, double* stats) {
+  __shared__ double s1[1024], s2[1024];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+    const double e = (double)eloc[i];
+    a += e;
+    b += e * e;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      s1[threadIdx.x] += s1[threadIdx.x + off];
+      s2[threadIdx.x] += s2[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double M = (double)B;
+    const double mean = s1[0] / M;
+    stats[0] = mean;
+    stats[1] = s2[0] / M - mean * mean;
+    stats[2] = M;
+  }
+}
+
+// w_b = 2 (E_loc,b - mean) / M
+__global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double* __restrict__ stats,
+                                   int64_t B, float* __restrict__ w) {
+  const double mean = stats[0], M = stats[2];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < B;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = (float)(2.0 * ((double)eloc[i] - mean) / M);
+}
+
+// grad[p] = sum_r partial[r][p], accumulated in FP64 in a fixed order.
+__global__ void reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
+                                       float* __restrict__ grad) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += (double)partial[(size_t)r * P + p];
+    grad[p] = (float)s;
+  }
+}
+
+cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st) {
+  energy_stats_kernel<<<1, 1024, 0, st>>>(eloc, B, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st) {
+  int64_t blocks = (B + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  vmc_weights_kernel<<<(unsigned)blocks, 256, 0, st>>>(eloc, stats, B, w);
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
+  int blocks = (P + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, rows, P, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace nqs

@@ -1,0 +1,281 @@
+"""Python binding of libnqs (include/nqs.h): argument marshalling only.
+
+Every function takes torch CUDA tensors, passes their device pointers, sizes
+and the current CUDA stream to the C ABI, and raises ``NqsError`` on a non-OK
+status.  All arithmetic runs in the library's kernels; there is no CPU or
+PyTorch fallback, and importing this module without a built ``libnqs.so``
+raises.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnqs.so")
+
+GRU1D, GRU2D = 1, 2
+FP32, BF16 = 0, 1
+TFIM, HEISENBERG = 1, 2
+OP_SAMPLE, OP_LOGPSI, OP_LOCAL_ENERGY, OP_LOGPSI_GRAD, OP_VMC_GRAD = 1, 2, 3, 4, 5
+
+STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4: "NQS_ECUDA",
+          5: "NQS_ETIMEOUT", 6: "NQS_ENONFINITE", 7: "NQS_EUNSUPPORTED"}
+
+EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
+           "nqs_local_energy", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
+           "nqs_status_string"]
+
+
+class NqsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s" % (where, STATUS.get(code, code)))
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+                ("d_h", ctypes.c_int32), ("d_model", ctypes.c_int32), ("sz0", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+    @property
+    def N(self):
+        return self.Lx * self.Ly
+
+
+class HamDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("marshall", ctypes.c_int32), ("J", ctypes.c_double),
+                ("h", ctypes.c_double)]
+
+
+def model_desc(cell, Lx, Ly=1, d_h=8, d_model=0, sz0=False, precision=FP32):
+    return ModelDesc(cell, Lx, Ly, d_h, d_model, int(bool(sz0)), precision)
+
+
+def tfim(J=1.0, Gamma=1.0):
+    return HamDesc(TFIM, 0, J, Gamma)
+
+
+def heisenberg(J=1.0, marshall=True):
+    return HamDesc(HEISENBERG, int(bool(marshall)), J, 0.0)
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree libnqs.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libnqs.so is not built (run __graft_entry__.build()); there is no fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i64, u64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    L.nqs_param_count.restype = sz
+    L.nqs_param_count.argtypes = [P(ModelDesc)]
+    L.nqs_workspace_bytes.restype = sz
+    L.nqs_workspace_bytes.argtypes = [P(ModelDesc), P(HamDesc), i64, ctypes.c_int]
+    L.nqs_grow_hidden.restype = ctypes.c_int
+    L.nqs_grow_hidden.argtypes = [P(ModelDesc), vp, P(ModelDesc), vp, u64, ctypes.c_float, vp]
+    L.nqs_sample.restype = ctypes.c_int
+    L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, vp, vp, vp, vp, vp, sz, vp]
+    L.nqs_logpsi.restype = ctypes.c_int
+    L.nqs_logpsi.argtypes = [P(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]
+    L.nqs_local_energy.restype = ctypes.c_int
+    L.nqs_local_energy.argtypes = [P(ModelDesc), vp, P(HamDesc), vp, vp, i64, vp, vp, sz, vp]
+    L.nqs_logpsi_grad.restype = ctypes.c_int
+    L.nqs_logpsi_grad.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, sz, vp]
+    L.nqs_vmc_grad.restype = ctypes.c_int
+    L.nqs_vmc_grad.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, vp, sz, vp]
+    L.nqs_workspace_status.restype = ctypes.c_int
+    L.nqs_workspace_status.argtypes = [vp, P(ctypes.c_int32), vp]
+    L.nqs_status_string.restype = ctypes.c_char_p
+    L.nqs_status_string.argtypes = [ctypes.c_int]
+    _lib = L
+    return L
+
+
+def _check(code, where):
+    if code != 0:
+        raise NqsError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    if t is None:
+        raise ValueError("%s is required" % name)
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must be a contiguous CUDA %s tensor of shape %s, got %s %s %s"
+                         % (name, dtype, tuple(shape), t.device, t.dtype, tuple(t.shape)))
+
+
+def param_count(desc):
+    n = lib().nqs_param_count(ctypes.byref(desc))
+    if n == 0:
+        raise NqsError(1, "nqs_param_count")
+    return n
+
+
+def workspace_bytes(desc, B, op, ham=None):
+    n = lib().nqs_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham) if ham is not None else None,
+                                  int(B), op)
+    if n == 0:
+        raise NqsError(1, "nqs_workspace_bytes")
+    return n
+
+
+class Workspace:
+    """Caller-owned workspace buffer that grows on demand (256-byte aligned)."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.buf.data_ptr()) % 256
+        return ctypes.c_void_p(self.buf.data_ptr() + off), self.buf.numel() - off
+
+    def status(self):
+        if self.buf is None:
+            return 0
+        ptr, _ = self.get(256)
+        v = ctypes.c_int32(0)
+        _check(lib().nqs_workspace_status(ptr, ctypes.byref(v), _stream()), "nqs_workspace_status")
+        return v.value
+
+
+_default_ws = {}
+
+
+def _ws(ws, device):
+    if ws is not None:
+        return ws
+    key = str(device)
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(device)
+    return _default_ws[key]
+
+
+def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None):
+    """Autoregressive sampling: returns (sigma uint8 [B,N], logpsi [B], hcache [B,N,d_h] or None)."""
+    dev = params.device
+    N, d = desc.N, desc.d_h
+    _need(params, torch.float32, (param_count(desc),), "params")
+    if uniforms is not None:
+        _need(uniforms, torch.float32, (B, N), "uniforms")
+    sigma = torch.empty((B, N), dtype=torch.uint8, device=dev)
+    logpsi = torch.empty((B,), dtype=torch.float32, device=dev)
+    hc = torch.empty((B, N, d), dtype=torch.float32, device=dev) if hcache is True else hcache
+    if hc is not None and hcache is not True:
+        _need(hc, torch.float32, (B, N, d), "hcache")
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_SAMPLE))
+    _check(lib().nqs_sample(ctypes.byref(desc), _ptr(params), int(B), int(seed), int(step),
+                            _ptr(uniforms), _ptr(sigma), _ptr(logpsi), _ptr(hc), wp, wn, _stream()),
+           "nqs_sample")
+    return sigma, logpsi, hc
+
+
+def logpsi(desc, params, sigma, hcache=True, ws=None):
+    """Teacher-forced log psi: returns (logpsi [B], hcache or None)."""
+    dev = params.device
+    B, N = sigma.shape
+    _need(params, torch.float32, (param_count(desc),), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    out = torch.empty((B,), dtype=torch.float32, device=dev)
+    hc = torch.empty((B, N, desc.d_h), dtype=torch.float32, device=dev) if hcache is True else hcache
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_LOGPSI))
+    _check(lib().nqs_logpsi(ctypes.byref(desc), _ptr(params), _ptr(sigma), int(B), _ptr(out), _ptr(hc),
+                            wp, wn, _stream()), "nqs_logpsi")
+    return out, hc
+
+
+def local_energy(desc, params, ham, sigma, hcache, ws=None, out=None):
+    dev = params.device
+    B = sigma.shape[0]
+    _need(params, torch.float32, (param_count(desc),), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
+    eloc = torch.empty((B,), dtype=torch.float32, device=dev) if out is None else out
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_LOCAL_ENERGY, ham))
+    _check(lib().nqs_local_energy(ctypes.byref(desc), _ptr(params), ctypes.byref(ham), _ptr(sigma),
+                                  _ptr(hcache), int(B), _ptr(eloc), wp, wn, _stream()),
+           "nqs_local_energy")
+    return eloc
+
+
+def logpsi_grad(desc, params, sigma, hcache, weights, ws=None, out=None):
+    dev = params.device
+    B = sigma.shape[0]
+    P = param_count(desc)
+    _need(params, torch.float32, (P,), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
+    _need(weights, torch.float32, (B,), "weights")
+    grad = torch.empty((P,), dtype=torch.float32, device=dev) if out is None else out
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_LOGPSI_GRAD))
+    _check(lib().nqs_logpsi_grad(ctypes.byref(desc), _ptr(params), _ptr(sigma), _ptr(hcache),
+                                 _ptr(weights), int(B), _ptr(grad), wp, wn, _stream()),
+           "nqs_logpsi_grad")
+    return grad
+
+
+def vmc_grad(desc, params, sigma, hcache, eloc, ws=None, grad=None, stats=None):
+    """Returns (grad [P] float32, stats [3] float64 = mean E_loc, variance, M)."""
+    dev = params.device
+    B = sigma.shape[0]
+    P = param_count(desc)
+    _need(params, torch.float32, (P,), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
+    _need(eloc, torch.float32, (B,), "eloc")
+    g = torch.empty((P,), dtype=torch.float32, device=dev) if grad is None else grad
+    st = torch.empty((3,), dtype=torch.float64, device=dev) if stats is None else stats
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_VMC_GRAD))
+    _check(lib().nqs_vmc_grad(ctypes.byref(desc), _ptr(params), _ptr(sigma), _ptr(hcache), _ptr(eloc),
+                              int(B), _ptr(g), _ptr(st), wp, wn, _stream()), "nqs_vmc_grad")
+    return g, st
+
+
+def grow_hidden(small, p_small, big, seed=2, eps=1e-3):
+    _need(p_small, torch.float32, (param_count(small),), "p_small")
+    p_big = torch.empty((param_count(big),), dtype=torch.float32, device=p_small.device)
+    _check(lib().nqs_grow_hidden(ctypes.byref(small), _ptr(p_small), ctypes.byref(big), _ptr(p_big),
+                                 int(seed), float(eps), _stream()), "nqs_grow_hidden")
+    return p_big
+
+
+class LogPsi(torch.autograd.Function):
+    """log psi(sigma) with the library's reverse sweep as its backward.
+
+    forward(params, sigma, desc) -> logpsi [B]; backward gives d params of
+    sum_b grad_out_b * logpsi_b (sigma is not differentiable).
+    """
+
+    @staticmethod
+    def forward(ctx, params, sigma, desc):
+        lp, hc = logpsi(desc, params.detach(), sigma, hcache=True)
+        ctx.save_for_backward(params, sigma, hc)
+        ctx.desc = desc
+        return lp
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        params, sigma, hc = ctx.saved_tensors
+        g = logpsi_grad(ctx.desc, params.detach(), sigma, hc, grad_out.contiguous().float())
+        return g, None, None

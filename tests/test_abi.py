@@ -1,0 +1,100 @@
+"""The C-ABI library: it loads, exports every declared symbol, and rejects bad
+arguments on the host before touching the GPU (CPU only, no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import model as om
+from paper_2507_18700_gb300 import build as nqs_build
+from paper_2507_18700_gb300 import inputs, nqs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    nqs_build.build()
+    return nqs.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nqs.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:size_t|nqs_status|const char\*)\s+(nqs_\w+)\s*\(", text, re.M)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(names) == sorted(nqs.EXPORTS)
+
+
+@pytest.mark.parametrize("cell,Lx,Ly,d", [(1, 12, 1, 8), (1, 100, 1, 64), (1, 20, 1, 128),
+                                          (2, 8, 8, 64), (2, 4, 4, 16), (2, 16, 16, 256)])
+def test_param_count_matches_layouts(L, cell, Lx, Ly, d):
+    desc = nqs.model_desc(cell, Lx, Ly, d)
+    n = L.nqs_param_count(ctypes.byref(desc))
+    if cell == 2 and d == 256:
+        assert n in (0, om.Model(cell, Lx, Ly, d_h=d).param_count())
+        return
+    assert n == om.Model(cell, Lx, Ly, d_h=d).param_count() == inputs.param_count(cell, d)
+
+
+def test_bad_descriptors_are_rejected(L):
+    bad = [nqs.model_desc(3, 10, 1, 8), nqs.model_desc(1, 10, 2, 8), nqs.model_desc(1, 10, 1, 12),
+           nqs.model_desc(1, 0, 1, 8), nqs.model_desc(2, 3, 3, 8, sz0=True),
+           nqs.model_desc(1, 10, 1, 8, precision=7), nqs.model_desc(2, 4, 4, 16, d_model=8)]
+    for desc in bad:
+        assert L.nqs_param_count(ctypes.byref(desc)) == 0
+        assert L.nqs_workspace_bytes(ctypes.byref(desc), None, 16, nqs.OP_SAMPLE) == 0
+    assert L.nqs_param_count(None) == 0
+
+
+def test_host_checks_return_status_without_launching(L):
+    desc = nqs.model_desc(1, 12, 1, 8)
+    fake = ctypes.c_void_p(0x1000)
+    ws_unaligned = ctypes.c_void_p(0x1010)
+    # null params
+    assert L.nqs_sample(ctypes.byref(desc), None, 4, 0, 0, None, fake, fake, None, fake, 1 << 20, None) == 1
+    # null descriptor
+    assert L.nqs_logpsi(None, fake, fake, 4, fake, None, fake, 1 << 20, None) == 1
+    # workspace too small / misaligned / missing
+    assert L.nqs_logpsi(ctypes.byref(desc), fake, fake, 4, fake, None, fake, 16, None) == 3
+    assert L.nqs_logpsi(ctypes.byref(desc), fake, fake, 4, fake, None, ws_unaligned, 1 << 20, None) == 3
+    assert L.nqs_logpsi(ctypes.byref(desc), fake, fake, 4, fake, None, None, 1 << 20, None) == 3
+    # negative batch
+    assert L.nqs_logpsi(ctypes.byref(desc), fake, fake, -1, fake, None, fake, 1 << 20, None) == 1
+    # local energy needs a Hamiltonian and the prefix cache
+    assert L.nqs_local_energy(ctypes.byref(desc), fake, None, fake, fake, 4, fake, fake, 1 << 20, None) == 1
+    ham = nqs.tfim()
+    assert L.nqs_local_energy(ctypes.byref(desc), fake, ctypes.byref(ham), fake, None, 4, fake, fake,
+                              1 << 20, None) == 1
+    # an empty batch needs no data pointers
+    assert L.nqs_local_energy(ctypes.byref(desc), fake, ctypes.byref(ham), None, None, 0, None, fake,
+                              1 << 20, None) == 0
+    bad_ham = nqs.HamDesc(9, 0, 1.0, 1.0)
+    assert L.nqs_local_energy(ctypes.byref(desc), fake, ctypes.byref(bad_ham), fake, fake, 4, fake, fake,
+                              1 << 20, None) == 1
+    # vmc_grad needs at least one sample
+    st = ctypes.c_void_p(0x2000)
+    assert L.nqs_vmc_grad(ctypes.byref(desc), fake, fake, fake, fake, 0, fake, st, fake, 1 << 20, None) == 1
+    # growth may not shrink or change the lattice
+    big = nqs.model_desc(1, 12, 1, 16)
+    other = nqs.model_desc(1, 10, 1, 16)
+    assert L.nqs_grow_hidden(ctypes.byref(big), fake, ctypes.byref(desc), fake, 2, 1e-3, None) == 2
+    assert L.nqs_grow_hidden(ctypes.byref(desc), fake, ctypes.byref(other), fake, 2, 1e-3, None) == 2
+    assert L.nqs_grow_hidden(ctypes.byref(desc), fake, ctypes.byref(big), fake, 2, -1.0, None) == 1
+    for code in range(8):
+        assert L.nqs_status_string(code).startswith(b"NQS_")
+
+
+def test_workspace_grows_with_batch(L):
+    desc = nqs.model_desc(1, 100, 1, 64)
+    ham = nqs.tfim()
+    a = L.nqs_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), 100, nqs.OP_LOCAL_ENERGY)
+    b = L.nqs_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), 4096, nqs.OP_LOCAL_ENERGY)
+    assert 0 < a < b and a % 256 == 0 and b % 256 == 0
+    assert L.nqs_workspace_bytes(ctypes.byref(desc), None, 100, nqs.OP_LOCAL_ENERGY) == 0
