@@ -182,6 +182,34 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,
                         const float* eloc, int64_t B, float* grad, double* stats,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* Local energies for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a library convenience.  Some callers
+ * cannot call cudaMalloc -- a plugin whose host application owns every device
+ * allocation, code running where an allocation would stall a latency-critical
+ * loop, or a thin foreign-language binding with no device allocator.  This
+ * call computes exactly what nqs_local_energy computes for the 1D TFIM with
+ * the FP32 GRU, but takes no workspace: its scratch is one fixed device array
+ * of NQS_STATIC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library keeps until the process exits.  The call itself allocates
+ * nothing.
+ *   - Capacity: the array holds a 256-byte header, the packed weights and two
+ *     float arrays of B*N entries; larger B*N returns NQS_EWORKSPACE (about
+ *     2 million B*N entries at d_h = 64) and enqueues nothing.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares the one array and it keeps the previous
+ *     call's contents (the call resets what must start at zero).  Calls whose
+ *     work overlaps on the GPU (other streams, other host threads) race on it:
+ *     serialise them, e.g. on one stream.
+ * Arguments as nqs_local_energy; cell must be NQS_GRU1D with NQS_FP32 and ham
+ * NQS_TFIM, otherwise NQS_EUNSUPPORTED. */
+#define NQS_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const float* params,
+                                   const nqs_ham_desc* ham, const uint8_t* sigma,
+                                   const float* hcache, int64_t B, float* eloc, void* stream);
+
 /* Copy the workspace status word to *device_status (an nqs_status) after
  * waiting for `stream`; clears it.  This call blocks the host. */
 nqs_status nqs_workspace_status(void* ws, int32_t* device_status, void* stream);

@@ -23,7 +23,7 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
           5: "NQS_ETIMEOUT", 6: "NQS_ENONFINITE", 7: "NQS_EUNSUPPORTED"}
 
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
-           "nqs_local_energy", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
+           "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string"]
 
 
