@@ -42,35 +42,51 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   return NQS_OK;
 }
 
-// Paths built so far: FP32 1D GRU.
+// Paths built so far: FP32 1D GRU (no mask) and FP32 2D GRU.
 nqs_status check_built(const Dims& d) {
-  if (d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
   if (d.precision != NQS_FP32) return NQS_EUNSUPPORTED;
-  if (d.sz0) return NQS_EUNSUPPORTED;
+  if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
   return NQS_OK;
 }
 
+int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
+
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, a, b, c, total;
+  size_t img, a, b, c, e, f, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
   Layout L{};
   size_t off = sizeof(WsHeader);
+  const bool two = d.cell == NQS_GRU2D;
   L.img = off;
-  off += align256(gru1d_img_floats(d.d) * sizeof(float));
+  off += align256((two ? gru2d_img_floats(d.d) : gru1d_img_floats(d.d)) * sizeof(float));
   const size_t BN = (size_t)B * (size_t)d.N;
+  auto take = [&](size_t bytes) { const size_t at = off; off += align256(bytes); return at; };
   switch (op) {
+    case NQS_OP_SAMPLE:
+    case NQS_OP_LOGPSI:
+      if (two) L.a = take((size_t)gru2d_engine_slots(d.d, B, 1) * d.Lx * d.d * sizeof(float));  // colbuf
+      break;
     case NQS_OP_LOCAL_ENERGY:
-      L.a = off; off += align256(BN * sizeof(float));        // dlog
-      L.b = off; off += align256(BN * sizeof(float));        // delta
+      if (!two) {
+        L.a = take(BN * sizeof(float));        // dlog
+        L.b = take(BN * sizeof(float));        // delta
+      } else {
+        L.a = take((size_t)gru2d_engine_slots(d.d, B, 2) * d.Lx * d.d * sizeof(float));  // colbuf
+        L.b = take((size_t)n_bonds(d) * 16);                  // bond table
+        L.c = take(BN * 2 * sizeof(float));                   // lp_tab
+        L.e = take(BN * sizeof(int));                         // nup_tab
+        L.f = take((size_t)B * n_bonds(d) * sizeof(float));   // delta
+      }
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
-      const size_t grid = (size_t)gru1d_bptt_grid(d.d, B);
-      L.a = off; off += align256(grid * d.P * sizeof(float)); // partial gradients
-      L.b = off; off += align256((size_t)B * sizeof(float));   // weights
+      const size_t grid = (size_t)(two ? gru2d_bptt_grid(d.d, B) : gru1d_bptt_grid(d.d, B));
+      L.a = take(grid * d.P * sizeof(float));               // partial gradients
+      L.b = take((size_t)B * sizeof(float));                 // weights
+      if (two) L.c = take((size_t)B * d.Lx * d.d * sizeof(float));  // vertical carries
       break;
     }
     default:
@@ -170,6 +186,24 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   if (!logpsi || (sample ? !sigma_out : !sigma_in)) return NQS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float* img = at<float>(ws, L.img);
+  if (d.cell == NQS_GRU2D) {
+    if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Eng2Args a{};
+    a.B = B;
+    a.Lx = d.Lx;
+    a.N = d.N;
+    a.sz0 = d.sz0;
+    a.sigma_in = sigma_in;
+    a.sigma_out = sigma_out;
+    a.uniforms = uniforms;
+    a.seed = seed;
+    a.step = step;
+    a.logpsi = logpsi;
+    a.hcache = hcache;
+    a.colbuf = at<float>(ws, L.a);
+    a.hdr = static_cast<WsHeader*>(ws);
+    return cuda_status(gru2d_forward(a, img, d.d, sample, st));
+  }
   cudaError_t e = gru1d_pack(params, img, d.d, st);
   if (e != cudaSuccess) return NQS_ECUDA;
   Fwd1Args a{};
@@ -211,13 +245,45 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
   if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return NQS_EINVAL;
   if (ham->kind == NQS_TFIM && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
-  if (ham->kind == NQS_HEISENBERG) return NQS_EUNSUPPORTED;
+  if (ham->kind == NQS_HEISENBERG && d.cell != NQS_GRU2D) return NQS_EUNSUPPORTED;
+  if (ham->kind == NQS_HEISENBERG && (d.Lx < 2 && d.Ly < 2)) return NQS_ESHAPE;
   const Layout L = layout(d, B, NQS_OP_LOCAL_ENERGY);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   if (B == 0) return NQS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   WsHeader* hdr = static_cast<WsHeader*>(ws);
   float* img = at<float>(ws, L.img);
+  if (ham->kind == NQS_HEISENBERG) {
+    const int nb = n_bonds(d);
+    int4* bonds = at<int4>(ws, L.b);
+    float* lp_tab = at<float>(ws, L.c);
+    int* nup_tab = at<int>(ws, L.e);
+    float* delta = at<float>(ws, L.f);
+    if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (gru2d_bonds(d.Lx, d.Ly, bonds, st) != cudaSuccess) return NQS_ECUDA;
+    if (gru2d_prep(img, hcache, sigma, lp_tab, nup_tab, B, d.Lx, d.N, d.d, d.sz0, st) != cudaSuccess)
+      return NQS_ECUDA;
+    if (cudaMemsetAsync(&hdr->job_counter, 0, sizeof(hdr->job_counter), st) != cudaSuccess)
+      return NQS_ECUDA;
+    Eng2Args c{};
+    c.B = B;
+    c.Lx = d.Lx;
+    c.N = d.N;
+    c.nbonds = nb;
+    c.sz0 = d.sz0;
+    c.sigma_in = sigma;
+    c.hcache = const_cast<float*>(hcache);
+    c.colbuf = at<float>(ws, L.a);
+    c.lp_tab = lp_tab;
+    c.nup_tab = nup_tab;
+    c.bonds = bonds;
+    c.delta = delta;
+    c.counter = &hdr->job_counter;
+    c.hdr = hdr;
+    if (gru2d_heis_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    const float x = ham->marshall ? -0.5f * (float)ham->J : 0.5f * (float)ham->J;
+    return cuda_status(heis_eloc(sigma, bonds, delta, eloc, B, d.N, nb, (float)ham->J, x, hdr, st));
+  }
   float* dlog = at<float>(ws, L.a);
   float* delta = at<float>(ws, L.b);
   if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
@@ -241,6 +307,25 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
                               int64_t B, float* grad, void* ws, cudaStream_t st) {
   float* img = at<float>(ws, L.img);
   float* partial = at<float>(ws, L.a);
+  if (d.cell == NQS_GRU2D) {
+    const int grid = gru2d_bptt_grid(d.d, B);
+    if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
+      return NQS_ECUDA;
+    Bptt2Args a{};
+    a.B = B;
+    a.Lx = d.Lx;
+    a.N = d.N;
+    a.P = (int)d.P;
+    a.sz0 = d.sz0;
+    a.sigma = sigma;
+    a.hcache = hcache;
+    a.weights = weights;
+    a.ccarry = at<float>(ws, L.c);
+    a.partial = partial;
+    if (gru2d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
+  }
   const int grid = gru1d_bptt_grid(d.d, B);
   if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
   if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)

@@ -576,9 +576,13 @@ __global__ void __launch_bounds__(NT) gru1d_bptt_kernel(const float* __restrict_
 // ----------------------------------------------------------------------------
 namespace {
 
+// Raise the dynamic shared-memory limit; a refusal is returned and cleared so
+// that it does not surface in a later, unrelated launch check.
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 int num_sms() {
@@ -636,7 +640,7 @@ cudaError_t launch_chains(const Chain1Args& a, const float* img, cudaStream_t st
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, T::C_NT, smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
   if (per_sm < 1) per_sm = 1;
   const int64_t jobs = a.B * (int64_t)(a.N - 1);
   int64_t grid = (int64_t)num_sms() * per_sm;

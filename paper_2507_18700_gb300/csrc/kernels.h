@@ -53,6 +53,47 @@ cudaError_t tfim_eloc(const uint8_t* sigma, const float* dlog, const float* delt
                       int64_t B, int N, float J, float Gamma, WsHeader* hdr, cudaStream_t st);
 cudaError_t gru1d_bptt(const Bptt1Args& a, const float* img, int D, cudaStream_t st);
 
+struct Eng2Args {
+  int64_t B;
+  int Lx, N, nbonds, sz0;
+  const uint8_t* sigma_in;   // teacher forcing / chains
+  uint8_t* sigma_out;        // sampling
+  const float* uniforms;     // sampling, nullable
+  uint64_t seed, step;
+  float* logpsi;             // sampling / teacher forcing
+  float* hcache;             // written by sampling / teacher forcing, read by chains
+  float* colbuf;             // [slots, Lx, d] column buffers
+  const float* lp_tab;       // chains: [B, N, 2] masked log p of both outcomes on the cached path
+  const int* nup_tab;        // chains: [B, N] up spins before each position
+  const int4* bonds;         // chains: sorted bond table
+  float* delta;              // chains: [B, nbonds]
+  unsigned long long* counter;
+  WsHeader* hdr;
+};
+
+struct Bptt2Args {
+  int64_t B;
+  int Lx, N, P, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;
+  float* ccarry;             // [B, Lx, d] vertical carries
+  float* partial;            // [grid, P]
+};
+
+size_t gru2d_img_floats(int D);
+int64_t gru2d_engine_slots(int D, int64_t B, int mode);
+int gru2d_bptt_grid(int D, int64_t B);
+cudaError_t gru2d_pack(const float* params, float* img, int D, cudaStream_t st);
+cudaError_t gru2d_forward(const Eng2Args& a, const float* img, int D, bool sample, cudaStream_t st);
+cudaError_t gru2d_bonds(int Lx, int Ly, int4* bonds, cudaStream_t st);
+cudaError_t gru2d_prep(const float* img, const float* hcache, const uint8_t* sigma, float* lp_tab,
+                       int* nup_tab, int64_t B, int Lx, int N, int D, int sz0, cudaStream_t st);
+cudaError_t gru2d_heis_chains(const Eng2Args& a, const float* img, int D, cudaStream_t st);
+cudaError_t heis_eloc(const uint8_t* sigma, const int4* bonds, const float* delta, float* eloc, int64_t B,
+                      int N, int nb, float J, float x, WsHeader* hdr, cudaStream_t st);
+cudaError_t gru2d_bptt(const Bptt2Args& a, const float* img, int D, cudaStream_t st);
+
 // reductions (reduce.cu)
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
 cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);

@@ -20,8 +20,11 @@ struct Geo {
 };
 
 // Load / store UPT consecutive floats (16-byte aligned when UPT % 4 == 0).
+// The pointer is deliberately not __restrict__: these helpers also read
+// buffers that the same kernel rewrites (column buffers, carries), which
+// must not go through the non-coherent read-only cache path.
 template <int UPT>
-__device__ __forceinline__ void ld_units(const float* __restrict__ p, float (&v)[UPT]) {
+__device__ __forceinline__ void ld_units(const float* p, float (&v)[UPT]) {
   if constexpr (UPT % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < UPT / 4; ++q) {
@@ -38,7 +41,7 @@ __device__ __forceinline__ void ld_units(const float* __restrict__ p, float (&v)
 }
 
 template <int UPT>
-__device__ __forceinline__ void st_units(float* __restrict__ p, const float (&v)[UPT]) {
+__device__ __forceinline__ void st_units(float* p, const float (&v)[UPT]) {
   if constexpr (UPT % 4 == 0) {
 #pragma unroll
     for (int q = 0; q < UPT / 4; ++q)
