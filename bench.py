@@ -2,11 +2,15 @@
 
 One step = autoregressive sampling of B configurations, local energies of all
 of them (every Hamiltonian-connected configuration, prefix-cached) and the VMC
-gradient with its energy statistics, on one set of weights.  Workload: the 1D
-transverse-field Ising chain, N = 100, Gamma = J = 1, open boundaries; 1D GRU
-wave function with d_h = 64; B = 4096 samples per step; Xavier-uniform weights
-plus N(0, 0.1^2) noise from seed 1 (synthetic: the paper's trained weights are
-not available and none are needed).
+gradient with its energy statistics, on one set of weights.
+
+Default workload (--workload tfim100): the 1D transverse-field Ising chain,
+N = 100, Gamma = J = 1, open boundaries; 1D GRU wave function with d_h = 64;
+B = 4096 samples per step; Xavier-uniform weights plus N(0, 0.1^2) noise from
+seed 1.  --workload heis8x8: the Marshall-rotated Heisenberg model on the open
+8 x 8 lattice with the zero-magnetisation mask, 2D GRU + GLU with d_h = 64,
+B = 2048, Xavier-uniform weights from seed 0.  Inputs are synthetic (the
+paper's trained weights are not available and none are needed).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU
 oracle on the host cores instead (a bounded sample of each step).
@@ -24,9 +28,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-N_SITES, D_H, BATCH, GAMMA, J = 100, 64, 4096, 1.0, 1.0
 METRIC = "VMC samples/sec/GPU (sample+E_loc+grad), BF16 vs FP32 at <=1e-4 energy/site"
-WORKLOAD = "1D TFIM N=100 OBC, Gamma=J=1, GRU d_h=64, 4096 samples/step"
+
+WORKLOADS = {
+    "tfim100": dict(cell=1, Lx=100, Ly=1, d=64, B=4096, sz0=False, ham="tfim", J=1.0, Gamma=1.0,
+                    seed=1, noise=0.1,
+                    name="1D TFIM N=100 OBC, Gamma=J=1, GRU d_h=64, 4096 samples/step"),
+    "heis8x8": dict(cell=2, Lx=8, Ly=8, d=64, B=2048, sz0=True, ham="heis", J=1.0, Gamma=0.0,
+                    seed=0, noise=0.0,
+                    name="2D Heisenberg 8x8 OBC, Marshall sign, S_z=0, 2D GRU+GLU d_h=64, 2048 samples/step"),
+}
+
+
+def mac_cell(w):
+    d = w["d"]
+    return 3 * d * d + 2 * d if w["cell"] == 1 else 8 * d * d + 2 * d
 
 
 def peaks():
@@ -38,15 +54,27 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-def flops_per_sample(N, d):
-    """Algorithmic FLOPs of one sample's step: 2 * MAC_cell * (N + N(N-1)/2 + 2N),
-    MAC_cell = 3 d^2 + 2 d (gate GEMMs on h and the readout)."""
-    mac = 3 * d * d + 2 * d
-    return 2 * mac * (N + N * (N - 1) // 2 + 2 * N)
-
-
-def chain_flops(B, N, d):
-    return 2 * (3 * d * d + 2 * d) * B * (N * (N - 1) // 2)
+def chain_cells(w, sigma):
+    """Cells recomputed by the prefix-cached local energy for configurations sigma
+    (numpy [B, N]): N(N-1)/2 per sample for the TFIM; for the Heisenberg model
+    N-1-pos(a) per antiparallel bond (a, b), pos(a) < pos(b)."""
+    import numpy as np
+    B, N = sigma.shape
+    if w["ham"] == "tfim":
+        return B * (N * (N - 1) // 2)
+    Lx, Ly = w["Lx"], w["Ly"]
+    pos = np.empty(N, dtype=np.int64)
+    for j in range(Ly):
+        for i in range(Lx):
+            pos[j * Lx + i] = j * Lx + (i if j % 2 == 0 else Lx - 1 - i)
+    total = 0
+    for j in range(Ly):
+        for i in range(Lx):
+            k = j * Lx + i
+            for q in ([k + 1] if i + 1 < Lx else []) + ([k + Lx] if j + 1 < Ly else []):
+                anti = sigma[:, k] != sigma[:, q]
+                total += int(anti.sum()) * (N - 1 - min(pos[k], pos[q]))
+    return total
 
 
 class ClockSampler:
@@ -102,43 +130,52 @@ class ClockSampler:
         return out
 
 
-def oracle_step_seconds(n_samples, seed):
+def _oracle_model(w):
+    from oracle import model as om
+    from paper_2507_18700_gb300 import inputs
+    mod = om.Model(w["cell"], w["Lx"], w["Ly"], d_h=w["d"], sz0=w["sz0"])
+    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"])
+    return mod, flat
+
+
+def oracle_step_seconds(w, n_samples, seed):
     """Float64 oracle for n_samples of the workload: sampling, local energies by
     full re-evaluation, VMC gradient.  Returns seconds."""
-    import numpy as np
     from oracle import hamiltonian as oh, model as om, philox, vmc as ov
-    from paper_2507_18700_gb300 import inputs
-    mod = om.Model(om.GRU1D, N_SITES, d_h=D_H)
-    flat = inputs.xavier_params(1, D_H, seed=1, noise_std=0.1)
+    mod, flat = _oracle_model(w)
     t0 = time.perf_counter()
-    u = philox.sampling_uniforms(seed, 0, n_samples, N_SITES)
+    u = philox.sampling_uniforms(seed, 0, n_samples, mod.N)
     s = om.sample(mod, flat, u)["sigma"]
-    e = oh.tfim_local_energy(N_SITES, J, GAMMA, s, lambda x: om.logpsi(mod, flat, x))
+    lp = lambda x: om.logpsi(mod, flat, x)
+    if w["ham"] == "tfim":
+        e = oh.tfim_local_energy(mod.N, w["J"], w["Gamma"], s, lp)
+    else:
+        e = oh.heisenberg_local_energy(w["Lx"], w["Ly"], w["J"], True, s, lp)
     ov.energy_stats(e)
     ov.vmc_gradient(mod, flat, s, e)
     return time.perf_counter() - t0
 
 
-def cpu_baseline(target_s=12.0):
-    n = 16
-    t = oracle_step_seconds(n, seed=100)
-    n2 = max(16, min(BATCH, int(n * target_s / max(t, 1e-3))))
-    t2 = oracle_step_seconds(n2, seed=101)
+def cpu_baseline(w, target_s=12.0):
+    n = 8
+    t = oracle_step_seconds(w, n, seed=100)
+    n2 = max(8, min(w["B"], int(n * target_s / max(t, 1e-3))))
+    t2 = oracle_step_seconds(w, n2, seed=101)
     return {"value": n2 / t2, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d of the 4096 samples of one step (sampling, E_loc by full re-evaluation, "
-                      "gradient), float64 numpy on all host cores" % n2,
+            "sample": "%d of the %d samples of one step (sampling, E_loc by full re-evaluation, "
+                      "gradient), float64 numpy, BLAS on all host cores" % (n2, w["B"]),
             "seconds": t2}
 
 
-def run_reference(args):
+def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n = 32
-    oracle_step_seconds(8, seed=1)
+    n = 32 if w["cell"] == 1 else 8
+    oracle_step_seconds(w, 4, seed=1)
     times = []
     for k in range(args.warmup + args.steps):
-        dt = oracle_step_seconds(n, seed=200 + k)
+        dt = oracle_step_seconds(w, n, seed=200 + k)
         if k >= args.warmup:
             times.append(dt)
     total = sum(times)
@@ -147,7 +184,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "samples_per_step_timed": n,
+            "config": {"workload": w["name"], "samples_per_step_timed": n,
                        "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": "samples/s", "kind": "oracle",
                              "cores": os.cpu_count(),
@@ -156,7 +193,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_gpu(args):
+def run_gpu(args, w):
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -171,106 +208,153 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    precision = nqs.FP32
-    desc = nqs.model_desc(nqs.GRU1D, N_SITES, 1, D_H, precision=precision)
-    ham = nqs.tfim(J, GAMMA)
-    flat = inputs.xavier_params(1, D_H, seed=1, noise_std=0.1).astype(np.float32)
+    B = args.batch or w["B"]
+    N = w["Lx"] * w["Ly"]
+    ham = nqs.tfim(w["J"], w["Gamma"]) if w["ham"] == "tfim" else nqs.heisenberg(w["J"], True)
+    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"]).astype(np.float32)
     params = torch.tensor(flat, device=dev)
     P = params.numel()
-    ws = nqs.Workspace(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     st = torch.cuda.current_stream()
     step_seed = 1000 + rank
 
-    def step(k, p):
-        sigma, lp, hc = nqs.sample(desc, p, BATCH, seed=step_seed, step=k, ws=ws)
-        eloc = nqs.local_energy(desc, p, ham, sigma, hc, ws=ws)
-        grad, stats = nqs.vmc_grad(desc, p, sigma, hc, eloc, ws=ws)
-        return grad, stats, eloc
-
-    def loc_events():
+    def events():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    for k in range(args.warmup):
-        step(k, params)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    step_ms, le_ms = [], []
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = loc_events()
-        la, lb = loc_events()
+    def measure(precision):
+        """Time args.steps VMC steps at one precision (after args.warmup untimed ones)."""
+        desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=precision)
+        ws = nqs.Workspace(dev)
+        for k in range(args.warmup):
+            s_, _, h_ = nqs.sample(desc, params, B, seed=step_seed, step=k, ws=ws)
+            e_ = nqs.local_energy(desc, params, ham, s_, h_, ws=ws)
+            nqs.vmc_grad(desc, params, s_, h_, e_, ws=ws)
         torch.cuda.synchronize()
-        a.record(st)
-        sigma, lp, hc = nqs.sample(desc, params, BATCH, seed=step_seed, step=args.warmup + k, ws=ws)
-        la.record(st)
-        eloc = nqs.local_energy(desc, params, ham, sigma, hc, ws=ws)
-        lb.record(st)
-        grad, stats = nqs.vmc_grad(desc, params, sigma, hc, eloc, ws=ws)
-        b.record(st)
-        torch.cuda.synchronize()
-        step_ms.append(a.elapsed_time(b))
-        le_ms.append(la.elapsed_time(lb))
-    clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    energy_per_site = float(stats[0].item()) / N_SITES
+        if world > 1:
+            dist.barrier()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        step_ms, le_ms, cells = [], [], []
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = events()
+            la, lb = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            sigma, lp, hc = nqs.sample(desc, params, B, seed=step_seed, step=args.warmup + k, ws=ws)
+            la.record(st)
+            eloc = nqs.local_energy(desc, params, ham, sigma, hc, ws=ws)
+            lb.record(st)
+            grad, stats = nqs.vmc_grad(desc, params, sigma, hc, eloc, ws=ws)
+            b.record(st)
+            torch.cuda.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            le_ms.append(la.elapsed_time(lb))
+            cells.append(chain_cells(w, sigma.cpu().numpy()))
+        clk = clocks.stop()
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # end to end through the public API with host buffers: params in, grad + stats out
+        host_p = torch.from_numpy(flat).pin_memory()
+        host_g = torch.empty(P, dtype=torch.float32).pin_memory()
+        host_s = torch.empty(3, dtype=torch.float64).pin_memory()
+        dev_p = torch.empty_like(params)
+        e2e_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            dev_p.copy_(host_p, non_blocking=True)
+            s_, _, h_ = nqs.sample(desc, dev_p, B, seed=step_seed, step=10_000 + k, ws=ws)
+            e_ = nqs.local_energy(desc, dev_p, ham, s_, h_, ws=ws)
+            g_, st_ = nqs.vmc_grad(desc, dev_p, s_, h_, e_, ws=ws)
+            host_g.copy_(g_, non_blocking=True)
+            host_s.copy_(st_, non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+        e2e_total = sum(e2e_ms)
+        if world > 1:
+            t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        return dict(desc=desc, ws=ws, total_ms=total_ms, le_ms=le_ms, cells=cells, clk=clk,
+                    e2e_ms=e2e_total, energy_per_site=float(stats[0].item()) / N, status=ws.status())
 
-    # end to end through the public API with host buffers: params in, grad + stats out
-    host_p = torch.from_numpy(flat).pin_memory()
-    host_g = torch.empty(P, dtype=torch.float32).pin_memory()
-    host_s = torch.empty(3, dtype=torch.float64).pin_memory()
-    dev_p = torch.empty_like(params)
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = loc_events()
-        torch.cuda.synchronize()
-        a.record(st)
-        dev_p.copy_(host_p, non_blocking=True)
-        g, s, _ = step(10_000 + k, dev_p)
-        host_g.copy_(g, non_blocking=True)
-        host_s.copy_(s, non_blocking=True)
-        b.record(st)
-        torch.cuda.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    def accuracy_check(d16, d32):
+        """BF16 against FP32 on the same configurations: energy per site and gradient cosine."""
+        sigma, _, _ = nqs.sample(d32, params, B, seed=77, step=0)
+        out = {}
+        for name, desc in (("bf16", d16), ("fp32", d32)):
+            _, hc = nqs.logpsi(desc, params, sigma)
+            el = nqs.local_energy(desc, params, ham, sigma, hc)
+            g, stt = nqs.vmc_grad(desc, params, sigma, hc, el)
+            out[name] = (float(stt[0].item()) / N, g.double())
+        cos = float((out["bf16"][1] @ out["fp32"][1]) /
+                    (out["bf16"][1].norm() * out["fp32"][1].norm()))
+        de = abs(out["bf16"][0] - out["fp32"][0])
+        return {"energy_per_site_diff": de, "grad_cosine": cos, "pass": bool(de <= 1e-4 and cos >= 0.999)}
 
+    r32 = measure(nqs.FP32)
+    chosen, r16, check = r32, None, None
+    bf16_ok = w["cell"] == 1 and w["d"] in (16, 32, 64) and args.precision != "fp32"
+    if bf16_ok:
+        r16 = measure(nqs.BF16)
+        check = accuracy_check(r16["desc"], r32["desc"])
+        if check["pass"] or args.precision == "bf16":
+            chosen = r16
     pk, src = peaks()
-    alu_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12   # FP32 FMA TFLOP/s
-    le_avg = sum(le_ms) / len(le_ms)
-    achieved = chain_flops(BATCH, N_SITES, D_H) / (le_avg * 1e-3) / 1e12
-    value = world * BATCH * args.steps / (total_ms * 1e-3)
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    flop_per_cell = 2 * mac_cell(w)
+    achieved = sum(chosen["cells"]) * flop_per_cell / (sum(chosen["le_ms"]) * 1e-3) / 1e12
+    if chosen is r16:
+        peak = pk.get("bf16_tflops", 1887.4)
+        d = w["d"]
+        mufu = sum(chosen["cells"]) * 6 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
+        mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "tensor", "kernel": "nqs_local_energy (prefix-cached chains, tcgen05 BF16)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src,
+                "epilogue_sfu": {"achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
+                                 "frac": mufu / mufu_peak,
+                                 "note": "6 MUFU ops per hidden unit per cell (two sigmoids, one tanh); "
+                                         "SFU peak 16/clk/SM x 152 SMs x max SM clock"}}
+    else:
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "nqs_local_energy (prefix-cached chains, FP32 CUDA cores)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)}
+    value = world * B * args.steps / (chosen["total_ms"] * 1e-3)
+    launches = 11 if w["cell"] == 1 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": BATCH * world, "seq_len": N_SITES,
-                   "parallelism": "replicas" if world > 1 else "single", "precision": "fp32",
+        "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if chosen is r16 else "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "global_batch": B * world, "seq_len": N,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "precision": "bf16 tensor-core cell GEMMs, fp32 state" if chosen is r16 else "fp32",
+                   "fp32_value": world * B * args.steps / (r32["total_ms"] * 1e-3),
+                   "fp32_ms_per_step": r32["total_ms"] / args.steps,
+                   "bf16_check": check,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "energy_per_site": energy_per_site},
-        "roofline": {"bound": "alu", "kernel": "nqs_local_energy (prefix-cached chains)",
-                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)"
-                                    % (pk.get("sm_max_mhz", 2070.0), src)},
-        "e2e": {"value": world * BATCH * args.steps / (e2e_total * 1e-3), "unit": "samples/s",
+                   "energy_per_site": chosen["energy_per_site"],
+                   "chain_cells_per_step": sum(chosen["cells"]) / len(chosen["cells"]),
+                   "device_status": chosen["status"]},
+        "roofline": roof,
+        "e2e": {"value": world * B * args.steps / (chosen["e2e_ms"] * 1e-3), "unit": "samples/s",
                 "h2d_bytes_per_step": P * 4, "d2h_bytes_per_step": P * 4 + 24},
-        "gpu_launches": 11 * args.steps,
-        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "gpu_launches": launches * args.steps,
+        "clocks": {"sm_mhz": chosen["clk"]["sm_mhz"], "sm_max_mhz": chosen["clk"]["sm_max_mhz"],
+                   "reasons": chosen["clk"]["reasons"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(w)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -284,12 +368,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tfim100", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="samples per step (default: the workload's)")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
+                    help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        run_reference(args)
+        run_reference(args, w)
     else:
-        run_gpu(args)
+        run_gpu(args, w)
 
 
 if __name__ == "__main__":

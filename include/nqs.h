@@ -51,8 +51,11 @@
  * - Arguments are checked on the host before anything is enqueued; a bad
  *   argument returns an error and enqueues nothing.  The library never aborts.
  * - A kernel that meets a non-finite log psi or local energy records
- *   NQS_ENONFINITE in the workspace status word; read it with
- *   nqs_workspace_status after the stream has drained.
+ *   NQS_ENONFINITE, and a tensor-core wait that gives up records
+ *   NQS_ETIMEOUT, in the workspace status word (the first int32 of the
+ *   workspace).  Every call clears that word when it starts, so after the
+ *   call's work has drained nqs_workspace_status returns what that call
+ *   recorded.
  */
 #ifndef NQS_H
 #define NQS_H
@@ -92,7 +95,11 @@ typedef struct {
   int32_t d_h;        /* hidden size: 8, 16, 32, 64 or 128 */
   int32_t d_model;    /* 2D GLU width; must equal d_h (App. A) ; 0 means d_h */
   int32_t sz0;        /* 1: zero-magnetisation mask (needs N even) */
-  int32_t precision;  /* NQS_FP32 | NQS_BF16 (GEMM operands; state stays FP32) */
+  int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of
+                         sampling, teacher forcing and the local-energy chains on
+                         the tensor cores (BF16 operands, FP32 accumulation and
+                         FP32 state; d_h in {16, 32, 64}); the reverse sweep
+                         stays FP32 */
 } nqs_model_desc;
 
 typedef struct {

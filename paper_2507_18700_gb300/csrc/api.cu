@@ -42,18 +42,21 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   return NQS_OK;
 }
 
-// Paths built so far: FP32 1D GRU (no mask) and FP32 2D GRU.
+// Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, and the BF16
+// tensor-core 1D GRU for d_h in {16, 32, 64}.
 nqs_status check_built(const Dims& d) {
-  if (d.precision != NQS_FP32) return NQS_EUNSUPPORTED;
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
+  if (d.precision == NQS_BF16 && !(d.cell == NQS_GRU1D && tc1d_supported(d.d))) return NQS_EUNSUPPORTED;
   return NQS_OK;
 }
+
+bool use_tc(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU1D; }
 
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, a, b, c, e, f, total;
+  size_t img, w, a, b, c, e, f, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
@@ -62,6 +65,10 @@ Layout layout(const Dims& d, int64_t B, int op) {
   const bool two = d.cell == NQS_GRU2D;
   L.img = off;
   off += align256((two ? gru2d_img_floats(d.d) : gru1d_img_floats(d.d)) * sizeof(float));
+  if (use_tc(d)) {
+    L.w = off;
+    off += align256(tc1d_wimg_bytes(d.d));
+  }
   const size_t BN = (size_t)B * (size_t)d.N;
   auto take = [&](size_t bytes) { const size_t at = off; off += align256(bytes); return at; };
   switch (op) {
@@ -104,6 +111,12 @@ nqs_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
 }
 
 inline nqs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NQS_OK : NQS_ECUDA; }
+
+// Every call starts by clearing the workspace status word, so after a call the
+// word holds what that call's kernels recorded.
+inline bool reset_status(void* ws, cudaStream_t st) {
+  return cudaMemsetAsync(&static_cast<WsHeader*>(ws)->status, 0, sizeof(int32_t), st) == cudaSuccess;
+}
 
 template <typename T>
 T* at(void* ws, size_t off) {
@@ -185,6 +198,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   if (B == 0) return NQS_OK;  // empty batch: outputs are empty, pointers may be null
   if (!logpsi || (sample ? !sigma_out : !sigma_in)) return NQS_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
   float* img = at<float>(ws, L.img);
   if (d.cell == NQS_GRU2D) {
     if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
@@ -206,6 +220,22 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   }
   cudaError_t e = gru1d_pack(params, img, d.d, st);
   if (e != cudaSuccess) return NQS_ECUDA;
+  if (use_tc(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    if (tc1d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Tc1Args t{};
+    t.B = B;
+    t.N = d.N;
+    t.sigma = sigma_in;
+    t.sigma_out = sigma_out;
+    t.uniforms = uniforms;
+    t.seed = seed;
+    t.step = step;
+    t.logpsi = logpsi;
+    t.hcache = hcache;
+    t.hdr = static_cast<WsHeader*>(ws);
+    return cuda_status(tc1d_run(t, img, wimg, d.d, sample ? 0 : 1, st));
+  }
   Fwd1Args a{};
   a.B = B;
   a.N = d.N;
@@ -251,6 +281,7 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   if (B == 0) return NQS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
   WsHeader* hdr = static_cast<WsHeader*>(ws);
   float* img = at<float>(ws, L.img);
   if (ham->kind == NQS_HEISENBERG) {
@@ -290,15 +321,30 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if (gru1d_readout(img, hcache, dlog, B * d.N, d.d, st) != cudaSuccess) return NQS_ECUDA;
   if (cudaMemsetAsync(&hdr->job_counter, 0, sizeof(hdr->job_counter), st) != cudaSuccess)
     return NQS_ECUDA;
-  Chain1Args c{};
-  c.B = B;
-  c.N = d.N;
-  c.sigma = sigma;
-  c.hcache = hcache;
-  c.dlog = dlog;
-  c.delta = delta;
-  c.counter = &hdr->job_counter;
-  if (gru1d_tfim_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (use_tc(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    if (tc1d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Tc1Args t{};
+    t.B = B;
+    t.N = d.N;
+    t.sigma = sigma;
+    t.hcache = const_cast<float*>(hcache);
+    t.dlog = dlog;
+    t.delta = delta;
+    t.counter = &hdr->job_counter;
+    t.hdr = hdr;
+    if (tc1d_run(t, img, wimg, d.d, 2, st) != cudaSuccess) return NQS_ECUDA;
+  } else {
+    Chain1Args c{};
+    c.B = B;
+    c.N = d.N;
+    c.sigma = sigma;
+    c.hcache = hcache;
+    c.dlog = dlog;
+    c.delta = delta;
+    c.counter = &hdr->job_counter;
+    if (gru1d_tfim_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  }
   return cuda_status(tfim_eloc(sigma, dlog, delta, eloc, B, d.N, (float)ham->J, (float)ham->h, hdr, st));
 }
 
@@ -354,6 +400,7 @@ nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params, cons
   const Layout L = layout(d, B, NQS_OP_LOGPSI_GRAD);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
   if (B == 0) return cuda_status(cudaMemsetAsync(grad, 0, d.P * sizeof(float), st));
   return grad_common(d, L, params, sigma, hcache, weights, B, grad, ws, st);
 }
@@ -369,6 +416,7 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const u
   const Layout L = layout(d, B, NQS_OP_VMC_GRAD);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
   float* w = at<float>(ws, L.b);
   if (energy_stats(eloc, B, stats, st) != cudaSuccess) return NQS_ECUDA;
   if (vmc_weights(eloc, stats, B, w, st) != cudaSuccess) return NQS_ECUDA;

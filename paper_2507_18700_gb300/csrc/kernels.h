@@ -94,6 +94,27 @@ cudaError_t heis_eloc(const uint8_t* sigma, const int4* bonds, const float* delt
                       int N, int nb, float J, float x, WsHeader* hdr, cudaStream_t st);
 cudaError_t gru2d_bptt(const Bptt2Args& a, const float* img, int D, cudaStream_t st);
 
+struct Tc1Args {
+  int64_t B;
+  int N;
+  const uint8_t* sigma;      // teacher forcing / chains
+  uint8_t* sigma_out;        // sampling
+  const float* uniforms;     // sampling, nullable
+  uint64_t seed, step;
+  float* logpsi;
+  float* hcache;             // written by sampling / teacher forcing (nullable), read by chains
+  const float* dlog;         // chains
+  float* delta;              // chains
+  unsigned long long* counter;
+  WsHeader* hdr;
+};
+
+int tc1d_supported(int D);
+size_t tc1d_wimg_bytes(int D);
+cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
+// mode 0: sampling, 1: teacher forcing, 2: TFIM chains
+cudaError_t tc1d_run(const Tc1Args& a, const float* img, const uint8_t* wimg, int D, int mode, cudaStream_t st);
+
 // reductions (reduce.cu)
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
 cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);

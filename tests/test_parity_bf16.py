@@ -1,0 +1,108 @@
+"""BF16 tensor-core path (1D GRU) against the float64 oracle.
+
+The cell GEMMs take BF16 operands (h and the weights rounded to 8 significant
+bits) with FP32 accumulation; state, gates and readout stay FP32.  Each
+site's logits then carry a relative error of about 2^-8, so the bounds are:
+  log psi       2e-4 * N absolute (the N per-site errors add with random signs;
+                measured mean 5e-5 per site at N = 100, d_h = 64);
+  energy/site   |mean E_loc(BF16) - mean E_loc(oracle)| / N <= 1e-4 on the
+                same configurations (the acceptance bound for the BF16 step);
+  sampling      identical configurations except samples with a draw within
+                5e-3 of the oracle's threshold;
+  gradient      cosine similarity >= 0.999 with the oracle's gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hamiltonian as oh, model as om, philox, vmc as ov
+from paper_2507_18700_gb300 import inputs, nqs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def setup(N, d, seed=1, noise=0.1):
+    flat = inputs.xavier_params(1, d, seed=seed, noise_std=noise).astype(np.float32)
+    return (nqs.model_desc(nqs.GRU1D, N, 1, d, precision=nqs.BF16), om.Model(om.GRU1D, N, d_h=d),
+            flat.astype(np.float64), torch.tensor(flat, device=DEV))
+
+
+@pytest.mark.parametrize("N,d,B", [(12, 16, 256), (40, 32, 300), (100, 64, 200), (7, 64, 129)])
+def test_bf16_logpsi_and_cache(N, d, B):
+    desc, mod, pf, p = setup(N, d)
+    sig = inputs.random_configs(B, N, seed=5)
+    lp, hc = nqs.logpsi(desc, p, torch.tensor(sig, device=DEV))
+    torch.cuda.synchronize()
+    ref = om.run(mod, pf, sigma=sig.astype(np.int64))
+    np.testing.assert_allclose(lp.cpu().numpy(), ref["logpsi"], atol=2e-4 * N, rtol=0)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=1e-2, rtol=0)
+
+
+@pytest.mark.parametrize("N,d,B", [(20, 16, 512), (100, 64, 256)])
+def test_bf16_sampling(N, d, B):
+    desc, mod, pf, p = setup(N, d)
+    sig, lp, hc = nqs.sample(desc, p, B, seed=9, step=4)
+    lp_t, _ = nqs.logpsi(desc, p, sig, hcache=None)
+    torch.cuda.synchronize()
+    assert torch.equal(lp, lp_t)            # same kernel arithmetic in both modes
+    u = philox.sampling_uniforms(9, 4, B, N)
+    ref = om.sample(mod, pf, u)
+    clean = ~(np.abs(u - ref["p0"]) < 5e-3).any(axis=1)
+    assert clean.mean() > 0.3
+    assert np.array_equal(sig.cpu().numpy()[clean], ref["sigma"][clean])
+
+
+@pytest.mark.parametrize("N,d,B,Gamma", [(12, 16, 512, 1.0), (30, 32, 256, 0.5), (100, 64, 256, 1.0)])
+def test_bf16_energy_per_site(N, d, B, Gamma):
+    # configurations drawn from the model (by the oracle's sampler), as in a VMC
+    # step: uniformly random spins have vanishing probability, so their ratios
+    # psi(sigma')/psi(sigma) are exponentially large and amplify any rounding
+    desc, mod, pf, p = setup(N, d)
+    sig = om.sample(mod, pf, philox.sampling_uniforms(11, 0, B, N))["sigma"].astype(np.uint8)
+    sg = torch.tensor(sig, device=DEV)
+    _, hc = nqs.logpsi(desc, p, sg)
+    el = nqs.local_energy(desc, p, nqs.tfim(1.0, Gamma), sg, hc)
+    torch.cuda.synchronize()
+    ref = oh.tfim_local_energy(N, 1.0, Gamma, sig.astype(np.int64), lambda x: om.logpsi(mod, pf, x))
+    assert abs(el.cpu().numpy().mean() - ref.mean()) / N <= 1e-4
+
+
+def test_bf16_vmc_gradient_cosine():
+    N, d, B = 40, 32, 256
+    desc, mod, pf, p = setup(N, d)
+    sig = inputs.random_configs(B, N, seed=12)
+    e = (inputs.random_weights(B, seed=13, scale=2.0) - 50.0).astype(np.float32)
+    sg = torch.tensor(sig, device=DEV)
+    _, hc = nqs.logpsi(desc, p, sg)
+    g, st = nqs.vmc_grad(desc, p, sg, hc, torch.tensor(e, device=DEV))
+    torch.cuda.synchronize()
+    ref = ov.vmc_gradient(mod, pf, sig.astype(np.int64), e.astype(np.float64))
+    g = g.double().cpu().numpy()
+    assert g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)) >= 0.999
+
+
+def test_bf16_full_size_step_n100_d64_b4096():
+    """Bench workload in BF16: energy per site of the whole step within 1e-4 of
+    the oracle's on 64 of its samples evaluated one by one, and of the FP32 path."""
+    N, d, B = 100, 64, 4096
+    desc, mod, pf, p = setup(N, d)
+    d32 = nqs.model_desc(nqs.GRU1D, N, 1, d)
+    u = philox.sampling_uniforms(21, 0, B, N)
+    ref = om.sample(mod, pf, u)
+    sg = torch.tensor(ref["sigma"], dtype=torch.uint8, device=DEV)
+    _, hc = nqs.logpsi(desc, p, sg)
+    el = nqs.local_energy(desc, p, nqs.tfim(), sg, hc)
+    _, hc32 = nqs.logpsi(d32, p, sg)
+    el32 = nqs.local_energy(d32, p, nqs.tfim(), sg, hc32)
+    g, st = nqs.vmc_grad(desc, p, sg, hc, el)
+    ws = nqs.Workspace(DEV)
+    sig, lp, hcs = nqs.sample(desc, p, B, seed=21, step=0, ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    e16, e32 = el.double().cpu().numpy(), el32.double().cpu().numpy()
+    assert abs(e16.mean() - e32.mean()) / N <= 1e-4
+    pick = np.random.default_rng(2).choice(B, 64, replace=False)
+    e_ref = oh.tfim_local_energy(N, 1.0, 1.0, ref["sigma"][pick], lambda x: om.logpsi(mod, pf, x))
+    assert abs(e16[pick].mean() - e_ref.mean()) / N <= 1e-4
+    assert np.isfinite(g.cpu().numpy()).all()
