@@ -314,14 +314,14 @@ def run_gpu(args, w):
     if chosen is r16:
         peak = pk.get("bf16_tflops", 1887.4)
         d = w["d"]
-        mufu = sum(chosen["cells"]) * 6 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
+        mufu = sum(chosen["cells"]) * 3 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
         mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
         roof = {"bound": "tensor", "kernel": "nqs_local_energy (prefix-cached chains, tcgen05 BF16)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src,
                 "epilogue_sfu": {"achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
                                  "frac": mufu / mufu_peak,
-                                 "note": "6 MUFU ops per hidden unit per cell (two sigmoids, one tanh); "
+                                 "note": "3 MUFU ops (hardware tanh) per hidden unit per cell (two sigmoids, one tanh); "
                                          "SFU peak 16/clk/SM x 152 SMs x max SM clock"}}
     else:
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12

@@ -32,8 +32,16 @@ __global__ void pack1d_tc_kernel(const float* __restrict__ p, uint8_t* __restric
   }
 }
 
-__device__ __forceinline__ float fast_sigmoid(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
-__device__ __forceinline__ float fast_tanh(float x) { return fmaf(2.0f, fast_sigmoid(2.0f * x), -1.0f); }
+// Gate nonlinearities of the BF16 path: one hardware tanh (MUFU.TANH,
+// relative error ~2^-11, below the 2^-9 rounding of the BF16 GEMM operands)
+// per gate; sigmoid(x) = (1 + tanh(x/2)) / 2.
+__device__ __forceinline__ float hw_tanh(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float fast_sigmoid(float x) { return fmaf(0.5f, hw_tanh(0.5f * x), 0.5f); }
+__device__ __forceinline__ float fast_tanh(float x) { return hw_tanh(x); }
 
 // Shared-memory carve-up (bytes from a 1024-aligned base).
 template <int D, int GROUPS>
