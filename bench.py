@@ -37,6 +37,10 @@ WORKLOADS = {
     "heis8x8": dict(cell=2, Lx=8, Ly=8, d=64, B=2048, sz0=True, ham="heis", J=1.0, Gamma=0.0,
                     seed=0, noise=0.0,
                     name="2D Heisenberg 8x8 OBC, Marshall sign, S_z=0, 2D GRU+GLU d_h=64, 2048 samples/step"),
+    "replicas16": dict(cell=1, Lx=100, Ly=1, d=None, B=2048, sz0=False, ham="tfim", J=1.0, Gamma=None,
+                       seed=10, noise=0.0, fields=(0.5, 1.0, 1.5, 2.0), sizes=(16, 32, 64, 128),
+                       name="16 replicas: 1D TFIM N=100, Gamma in {0.5,1,1.5,2} x GRU d_h in {16,32,64,128} "
+                            "grown from d_h=16 (seed 2, eps 1e-3), 2048 samples each, one batched step, CUDA graph"),
 }
 
 
@@ -362,6 +366,161 @@ def run_gpu(args, w):
         print(json.dumps(line))
 
 
+def replica_models(w, dev):
+    """The growth family: for each field a Xavier d_h = 16 model, embedded into
+    d_h = 32, 64, 128 by nqs_grow_hidden (seed 2, eps 1e-3)."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import inputs, nqs
+    models = []
+    for fi, G in enumerate(w["fields"]):
+        small = nqs.model_desc(nqs.GRU1D, w["Lx"], 1, w["sizes"][0])
+        p = torch.tensor(inputs.xavier_params(1, w["sizes"][0], seed=w["seed"] + fi).astype(np.float32), device=dev)
+        for si, d in enumerate(w["sizes"]):
+            desc = nqs.model_desc(nqs.GRU1D, w["Lx"], 1, d)
+            if si > 0:
+                p = nqs.grow_hidden(small, p, desc, seed=2, eps=1e-3)
+            models.append((desc, nqs.tfim(w["J"], G), w["B"], 5000 + 16 * fi + si, p))
+            small = desc
+    return models
+
+
+def oracle_replicas_seconds(w, per_replica, seed):
+    """Float64 oracle: per_replica samples of each of the 16 replicas (no growth: Xavier weights)."""
+    from oracle import hamiltonian as oh, model as om, philox, vmc as ov
+    from paper_2507_18700_gb300 import inputs
+    t0 = time.perf_counter()
+    for fi, G in enumerate(w["fields"]):
+        for d in w["sizes"]:
+            mod = om.Model(om.GRU1D, w["Lx"], d_h=d)
+            flat = inputs.xavier_params(1, d, seed=w["seed"] + fi)
+            s = om.sample(mod, flat, philox.sampling_uniforms(seed, 0, per_replica, mod.N))["sigma"]
+            e = oh.tfim_local_energy(mod.N, w["J"], G, s, lambda x: om.logpsi(mod, flat, x))
+            ov.vmc_gradient(mod, flat, s, e)
+    return time.perf_counter() - t0
+
+
+def run_replicas(args, w):
+    import torch
+    from paper_2507_18700_gb300 import nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    models = replica_models(w, dev)
+    R = len(models)
+    total_B = sum(m[2] for m in models)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # (1) batched step captured in a CUDA graph, device-side step counter
+    batch = nqs.ReplicaBatch(models, device_step=True)
+    side = torch.cuda.Stream()
+    side.wait_stream(st)
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            batch.step()
+    st.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.step()
+    graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    g_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = events()
+        torch.cuda.synchronize()
+        a.record(st)
+        graph.replay()
+        b.record(st)
+        torch.cuda.synchronize()
+        g_ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    # (2) the same step without the graph, and (3) as 3 x R separate calls
+    e_ms, s_ms = [], []
+    ws = nqs.Workspace(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = events()
+        torch.cuda.synchronize()
+        a.record(st)
+        batch.step()
+        b.record(st)
+        torch.cuda.synchronize()
+        e_ms.append(a.elapsed_time(b))
+        flush.zero_()
+        a, b = events()
+        torch.cuda.synchronize()
+        a.record(st)
+        for (desc, ham, B, seed, p) in models:
+            sg, _, hc = nqs.sample(desc, p, B, seed=seed, step=k, ws=ws)
+            el = nqs.local_energy(desc, p, ham, sg, hc, ws=ws)
+            nqs.vmc_grad(desc, p, sg, hc, el, ws=ws)
+        b.record(st)
+        torch.cuda.synchronize()
+        s_ms.append(a.elapsed_time(b))
+    # end to end: parameters of every replica in from pinned host memory, gradients and stats out
+    host_p = [m[4].cpu().pin_memory() for m in models]
+    host_g = [torch.empty_like(h).pin_memory() for h in host_p]
+    host_s = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in models]
+    x_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = events()
+        torch.cuda.synchronize()
+        a.record(st)
+        for hp, m in zip(host_p, models):
+            m[4].copy_(hp, non_blocking=True)
+        graph.replay()
+        for hg, hs, o in zip(host_g, host_s, batch.out):
+            hg.copy_(o["grad"], non_blocking=True)
+            hs.copy_(o["stats"], non_blocking=True)
+        b.record(st)
+        torch.cuda.synchronize()
+        x_ms.append(a.elapsed_time(b))
+    status = batch.ws.status()
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    N = w["Lx"]
+    flops = sum(2 * (3 * m[0].d_h ** 2 + 2 * m[0].d_h) * m[2] * (N + N * (N - 1) // 2 + 2 * N) for m in models)
+    step_s = sum(g_ms) / len(g_ms) * 1e-3
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / step_s / 1e12
+    P_bytes = sum(h.numel() * 4 for h in host_p)
+    line = {
+        "metric": METRIC, "value": total_B / step_s, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "global_batch": total_B, "seq_len": N, "replicas": R,
+                   "parallelism": "single", "precision": "fp32",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "no_graph_ms_per_step": sum(e_ms) / len(e_ms),
+                   "separate_calls_ms_per_step": sum(s_ms) / len(s_ms),
+                   "energy_per_site": [float(o["stats"][0].item()) / N for o in batch.out],
+                   "device_status": status},
+        "roofline": {"bound": "alu", "kernel": "nqs_vmc_step_batched (whole step; chains dominate)",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "traffic": None,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)},
+        "e2e": {"value": total_B / (sum(x_ms) / len(x_ms) * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": P_bytes, "d2h_bytes_per_step": P_bytes + 24 * R},
+        "gpu_launches": 10 * args.steps,
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
+    if not args.no_cpu_baseline:
+        n = 2
+        t = oracle_replicas_seconds(w, n, seed=300)
+        line["cpu_baseline"] = {"value": n * R / t, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "%d samples of each of the %d replicas (float64 numpy, BLAS on all "
+                                          "host cores)" % (n, R), "seconds": t}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +535,21 @@ def main():
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        run_reference(args, w)
+        if args.workload == "replicas16":
+            t = oracle_replicas_seconds(w, 1, seed=7)
+            print(json.dumps({"impl": "reference", "metric": METRIC, "value": 16 / t, "unit": "samples/s",
+                              "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": t * 1e3,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                              "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": w["name"], "samples_per_step_timed": 16},
+                              "cpu_baseline": {"value": 16 / t, "unit": "samples/s", "kind": "oracle",
+                                               "cores": os.cpu_count(), "sample": "1 sample per replica"},
+                              "e2e": {"value": 16 / t, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}))
+        else:
+            run_reference(args, w)
+    elif args.workload == "replicas16":
+        run_replicas(args, w)
     else:
         run_gpu(args, w)
 

@@ -189,6 +189,39 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,
                         const float* eloc, int64_t B, float* grad, double* stats,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* One replica of a batched VMC step. */
+#define NQS_MAX_REPLICAS 16
+typedef struct {
+  nqs_model_desc desc;   /* NQS_GRU1D, NQS_FP32, sz0 = 0, d_h in {16, 32, 64, 128} */
+  nqs_ham_desc ham;      /* NQS_TFIM */
+  int64_t B;             /* samples of this replica, >= 1 */
+  uint64_t seed;         /* Philox key of this replica's sampling */
+  const float* params;   /* device [P] (read) */
+  uint8_t* sigma;        /* device [B, N] (written) */
+  float* logpsi;         /* device [B] (written) */
+  float* hcache;         /* device [B, N, d_h] (written) */
+  float* eloc;           /* device [B] (written) */
+  float* grad;           /* device [P] (written) */
+  double* stats;         /* device [3] (written): mean E_loc, variance, M */
+} nqs_replica;
+
+/* Workspace bytes of nqs_vmc_step_batched for these replicas; 0 if invalid. */
+size_t nqs_vmc_step_batched_workspace_bytes(int R, const nqs_replica* reps);
+
+/* A whole VMC step (nqs_sample + nqs_local_energy + nqs_vmc_grad) for R
+ * replicas of uneven hidden size, field, batch and chain length -- the model
+ * family of the Adaptive schedule (Sec. II B), e.g. one model per growth
+ * stage and field.  Every phase is one launch over all replicas (the chain
+ * phase is persistent and balances the replicas' work), and the replica table
+ * travels as a kernel argument, so the call can be captured in a CUDA graph.
+ *   reps      host array of R replicas (1 <= R <= NQS_MAX_REPLICAS)
+ *   step      Philox step of the sampling when step_dev is NULL
+ *   step_dev  device counter or NULL: when given, the step is read from it on
+ *             the device and incremented at the end of the call, so every
+ *             replay of a captured graph draws fresh samples.            */
+nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, uint64_t* step_dev,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* Local energies for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this is a library convenience.  Some callers

@@ -423,4 +423,94 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const u
   return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched step over replicas.
+// ---------------------------------------------------------------------------
+static nqs_status check_replicas(int R, const nqs_replica* reps, Dims* dims) {
+  if (R < 1 || R > NQS_MAX_REPLICAS || !reps) return NQS_EINVAL;
+  for (int i = 0; i < R; ++i) {
+    const nqs_replica& r = reps[i];
+    nqs_status s = check_desc(&r.desc, &dims[i]);
+    if (s != NQS_OK) return s;
+    if (dims[i].cell != NQS_GRU1D || dims[i].precision != NQS_FP32 || dims[i].sz0) return NQS_EUNSUPPORTED;
+    if (!batched_supported_d(dims[i].d)) return NQS_EUNSUPPORTED;
+    if (r.ham.kind != NQS_TFIM) return r.ham.kind == NQS_HEISENBERG ? NQS_EUNSUPPORTED : NQS_EINVAL;
+    if (r.B < 1) return NQS_EINVAL;
+  }
+  return NQS_OK;
+}
+
+struct BatchLayout {
+  size_t counters, img[NQS_MAX_REPLICAS], dlog[NQS_MAX_REPLICAS], delta[NQS_MAX_REPLICAS],
+      w[NQS_MAX_REPLICAS], partial[NQS_MAX_REPLICAS], total;
+};
+
+static BatchLayout batch_layout(int R, const nqs_replica* reps, const Dims* dims) {
+  BatchLayout L{};
+  size_t off = sizeof(WsHeader);
+  L.counters = off;
+  off += align256((size_t)R * sizeof(unsigned long long));
+  for (int i = 0; i < R; ++i) {
+    const size_t BN = (size_t)reps[i].B * dims[i].N;
+    L.img[i] = off; off += align256(gru1d_img_floats(dims[i].d) * sizeof(float));
+    L.dlog[i] = off; off += align256(BN * sizeof(float));
+    L.delta[i] = off; off += align256(BN * sizeof(float));
+    L.w[i] = off; off += align256((size_t)reps[i].B * sizeof(float));
+  }
+  for (int i = 0; i < R; ++i) {   // contiguous, replica 0 first
+    L.partial[i] = off;
+    off += align256((size_t)batched_bptt_blocks(dims[i].d, reps[i].B) * dims[i].P * sizeof(float));
+  }
+  L.total = off;
+  return L;
+}
+
+size_t nqs_vmc_step_batched_workspace_bytes(int R, const nqs_replica* reps) {
+  Dims dims[NQS_MAX_REPLICAS];
+  if (check_replicas(R, reps, dims) != NQS_OK) return 0;
+  return batch_layout(R, reps, dims).total;
+}
+
+nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, uint64_t* step_dev,
+                                void* ws, size_t ws_bytes, void* stream) {
+  Dims dims[NQS_MAX_REPLICAS];
+  nqs_status r = check_replicas(R, reps, dims);
+  if (r != NQS_OK) return r;
+  for (int i = 0; i < R; ++i) {
+    const nqs_replica& p = reps[i];
+    if (!p.params || !p.sigma || !p.logpsi || !p.hcache || !p.eloc || !p.grad || !p.stats) return NQS_EINVAL;
+  }
+  const BatchLayout L = batch_layout(R, reps, dims);
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < L.total) return NQS_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
+  BatchRep br[NQS_MAX_REPLICAS];
+  for (int i = 0; i < R; ++i) {
+    const nqs_replica& p = reps[i];
+    BatchRep& b = br[i];
+    b.d = dims[i].d;
+    b.N = dims[i].N;
+    b.P = (int)dims[i].P;
+    b.B = p.B;
+    b.seed = p.seed;
+    b.J = (float)p.ham.J;
+    b.Gamma = (float)p.ham.h;
+    b.params = p.params;
+    b.img = at<float>(ws, L.img[i]);
+    b.sigma = p.sigma;
+    b.logpsi = p.logpsi;
+    b.hcache = p.hcache;
+    b.eloc = p.eloc;
+    b.grad = p.grad;
+    b.stats = p.stats;
+    b.dlog = at<float>(ws, L.dlog[i]);
+    b.delta = at<float>(ws, L.delta[i]);
+    b.partial = at<float>(ws, L.partial[i]);
+    b.w = at<float>(ws, L.w[i]);
+    b.counter = at<unsigned long long>(ws, L.counters) + i;
+  }
+  return cuda_status(batched_step(br, R, step, step_dev, step_dev, st));
+}
+
 }  // extern "C"

@@ -115,6 +115,31 @@ cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st
 // mode 0: sampling, 1: teacher forcing, 2: TFIM chains
 cudaError_t tc1d_run(const Tc1Args& a, const float* img, const uint8_t* wimg, int D, int mode, cudaStream_t st);
 
+// grouped multi-replica step (batched.cu)
+struct BatchRep {
+  int d, N, P;
+  int64_t B;
+  uint64_t seed;
+  float J, Gamma;
+  const float* params;
+  float* img;
+  uint8_t* sigma;
+  float* logpsi;
+  float* hcache;
+  float* eloc;
+  float* grad;
+  double* stats;
+  float* dlog;
+  float* delta;
+  float* partial;   // replicas' partials are contiguous, replica 0 first
+  float* w;
+  unsigned long long* counter;   // replicas' counters are contiguous, replica 0 first
+};
+bool batched_supported_d(int d);
+int batched_bptt_blocks(int d, int64_t B);
+cudaError_t batched_step(const BatchRep* reps, int R, uint64_t step, const uint64_t* step_dev, uint64_t* step_inc,
+                         cudaStream_t st);
+
 // reductions (reduce.cu)
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
 cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);

@@ -24,7 +24,7 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
-           "nqs_status_string"]
+           "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched"]
 
 
 class NqsError(RuntimeError):
@@ -46,6 +46,16 @@ class ModelDesc(ctypes.Structure):
 class HamDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("marshall", ctypes.c_int32), ("J", ctypes.c_double),
                 ("h", ctypes.c_double)]
+
+
+class Replica(ctypes.Structure):
+    _fields_ = [("desc", ModelDesc), ("ham", HamDesc), ("B", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("params", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("logpsi", ctypes.c_void_p),
+                ("hcache", ctypes.c_void_p), ("eloc", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p)]
+
+
+MAX_REPLICAS = 16
 
 
 def model_desc(cell, Lx, Ly=1, d_h=8, d_model=0, sz0=False, precision=FP32):
@@ -91,6 +101,10 @@ def lib():
     L.nqs_vmc_grad.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, vp, sz, vp]
     L.nqs_workspace_status.restype = ctypes.c_int
     L.nqs_workspace_status.argtypes = [vp, P(ctypes.c_int32), vp]
+    L.nqs_vmc_step_batched_workspace_bytes.restype = sz
+    L.nqs_vmc_step_batched_workspace_bytes.argtypes = [ctypes.c_int, P(Replica)]
+    L.nqs_vmc_step_batched.restype = ctypes.c_int
+    L.nqs_vmc_step_batched.argtypes = [ctypes.c_int, P(Replica), u64, vp, vp, sz, vp]
     L.nqs_status_string.restype = ctypes.c_char_p
     L.nqs_status_string.argtypes = [ctypes.c_int]
     _lib = L
@@ -279,3 +293,46 @@ class LogPsi(torch.autograd.Function):
         params, sigma, hc = ctx.saved_tensors
         g = logpsi_grad(ctx.desc, params.detach(), sigma, hc, grad_out.contiguous().float())
         return g, None, None
+
+
+class ReplicaBatch:
+    """Device buffers of a batch of 1D replicas and their batched VMC step.
+
+    models: list of (desc, ham, B, seed, params) with params a CUDA float32
+    tensor.  step(step_no) runs nqs_vmc_step_batched; with device_step=True the
+    step number lives in a device counter that every call advances (usable
+    inside a captured CUDA graph).
+    """
+
+    def __init__(self, models, device=None, device_step=False):
+        if not 1 <= len(models) <= MAX_REPLICAS:
+            raise ValueError("1 to %d replicas" % MAX_REPLICAS)
+        self.models = models
+        dev = models[0][4].device if device is None else device
+        self.out = []
+        reps = (Replica * len(models))()
+        for i, (desc, ham, B, seed, params) in enumerate(models):
+            P = param_count(desc)
+            _need(params, torch.float32, (P,), "params")
+            o = dict(sigma=torch.empty((B, desc.N), dtype=torch.uint8, device=dev),
+                     logpsi=torch.empty((B,), dtype=torch.float32, device=dev),
+                     hcache=torch.empty((B, desc.N, desc.d_h), dtype=torch.float32, device=dev),
+                     eloc=torch.empty((B,), dtype=torch.float32, device=dev),
+                     grad=torch.empty((P,), dtype=torch.float32, device=dev),
+                     stats=torch.empty((3,), dtype=torch.float64, device=dev), params=params)
+            self.out.append(o)
+            reps[i] = Replica(desc, ham, B, seed, params.data_ptr(), o["sigma"].data_ptr(),
+                              o["logpsi"].data_ptr(), o["hcache"].data_ptr(), o["eloc"].data_ptr(),
+                              o["grad"].data_ptr(), o["stats"].data_ptr())
+        self.reps = reps
+        n = lib().nqs_vmc_step_batched_workspace_bytes(len(models), reps)
+        if n == 0:
+            raise NqsError(1, "nqs_vmc_step_batched_workspace_bytes")
+        self.ws = Workspace(dev)
+        self.ws_ptr, self.ws_n = self.ws.get(n)
+        self.step_dev = torch.zeros((1,), dtype=torch.int64, device=dev) if device_step else None
+
+    def step(self, step_no=0):
+        _check(lib().nqs_vmc_step_batched(len(self.models), self.reps, int(step_no), _ptr(self.step_dev),
+                                          self.ws_ptr, self.ws_n, _stream()), "nqs_vmc_step_batched")
+        return self.out
