@@ -37,6 +37,9 @@ WORKLOADS = {
     "heis8x8": dict(cell=2, Lx=8, Ly=8, d=64, B=2048, sz0=True, ham="heis", J=1.0, Gamma=0.0,
                     seed=0, noise=0.0,
                     name="2D Heisenberg 8x8 OBC, Marshall sign, S_z=0, 2D GRU+GLU d_h=64, 2048 samples/step"),
+    "heis16x16": dict(cell=2, Lx=16, Ly=16, d=256, B=8192, sz0=True, ham="heis", J=1.0, Gamma=0.0,
+                      seed=3, noise=0.0,
+                      name="2D Heisenberg 16x16 OBC, Marshall sign, S_z=0, 2D GRU+GLU d_h=256, 8192 samples/step"),
     "replicas16": dict(cell=1, Lx=100, Ly=1, d=None, B=2048, sz0=False, ham="tfim", J=1.0, Gamma=None,
                        seed=10, noise=0.0, fields=(0.5, 1.0, 1.5, 2.0), sizes=(16, 32, 64, 128),
                        name="16 replicas: 1D TFIM N=100, Gamma in {0.5,1,1.5,2} x GRU d_h in {16,32,64,128} "

@@ -92,7 +92,7 @@ enum {
 typedef struct {
   int32_t cell;       /* NQS_GRU1D | NQS_GRU2D */
   int32_t Lx, Ly;     /* N = Lx * Ly; 1D: Ly = 1 */
-  int32_t d_h;        /* hidden size: 8, 16, 32, 64 or 128 */
+  int32_t d_h;        /* hidden size: 8, 16, 32, 64, 128 (and 256 for NQS_GRU2D) */
   int32_t d_model;    /* 2D GLU width; must equal d_h (App. A) ; 0 means d_h */
   int32_t sz0;        /* 1: zero-magnetisation mask (needs N even) */
   int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of

@@ -13,7 +13,7 @@ struct Dims {
   size_t P;
 };
 
-bool valid_hidden(int d) { return gru1d_supported(d); }
+bool valid_hidden(int cell, int d) { return cell == NQS_GRU2D ? gru2d_supported(d) : gru1d_supported(d); }
 
 nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   if (!desc) return NQS_EINVAL;
@@ -30,7 +30,7 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   if (d.sz0 != 0 && d.sz0 != 1) return NQS_EINVAL;
   if (d.Lx < 1 || d.Ly < 1 || (int64_t)d.Lx * d.Ly > (1 << 20)) return NQS_ESHAPE;
   d.N = d.Lx * d.Ly;
-  if (!valid_hidden(d.d)) return NQS_ESHAPE;
+  if (!valid_hidden(d.cell, d.d)) return NQS_ESHAPE;
   if (d.cell == NQS_GRU1D && d.Ly != 1) return NQS_ESHAPE;
   if (d.cell == NQS_GRU2D && d.m != d.d) return NQS_ESHAPE;
   if (d.sz0 && (d.N % 2)) return NQS_ESHAPE;
@@ -94,6 +94,7 @@ Layout layout(const Dims& d, int64_t B, int op) {
       L.a = take(grid * d.P * sizeof(float));               // partial gradients
       L.b = take((size_t)B * sizeof(float));                 // weights
       if (two) L.c = take((size_t)B * d.Lx * d.d * sizeof(float));  // vertical carries
+      if (two) L.e = take(gru2d_bptt_scratch_floats(d.d, B) * sizeof(float));  // small-gradient scratch
       break;
     }
     default:
@@ -369,6 +370,9 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     a.weights = weights;
     a.ccarry = at<float>(ws, L.c);
     a.partial = partial;
+    a.sacc = at<float>(ws, L.e);
+    const size_t scratch = gru2d_bptt_scratch_floats(d.d, B);
+    if (scratch && cudaMemsetAsync(a.sacc, 0, scratch * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
     if (gru2d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
   }

@@ -479,7 +479,8 @@ __device__ __forceinline__ void accum_outer(float* part, int base, int ld, const
   constexpr int TU = Geo<D>::TU, UPT = Geo<D>::UPT;
   constexpr int KG = NT / TU, KPT = K / KG;
   static_assert(KPT * KG == K, "bad outer tiling");
-  constexpr int KC = KPT < 8 ? KPT : 8;
+  constexpr int KCMAX = UPT >= 16 ? 4 : 8;
+  constexpr int KC = KPT < KCMAX ? KPT : KCMAX;
   const int ug = threadIdx.x % TU, kg = threadIdx.x / TU;
   const int u0 = ug * UPT;
 #pragma unroll 1
@@ -506,7 +507,7 @@ __device__ __forceinline__ void accum_outer(float* part, int base, int ld, const
   }
 }
 
-template <int D, int RPT, int NT>
+template <int D, int RPT, int NT, bool GSACC>
 __global__ void __launch_bounds__(NT) gru2d_bptt_kernel(const float* __restrict__ img, Bptt2Args a) {
   using G = Geo<D>;
   constexpr int TU = G::TU, UPT = G::UPT;
@@ -518,14 +519,18 @@ __global__ void __launch_bounds__(NT) gru2d_bptt_kernel(const float* __restrict_
   float* Htile = Atile + R * AP;            // [R][HP]  h
   float* DY = Htile + R * HP;               // [R][YP]  [dy1 | dy2]
   float* GG = DY + R * YP;                  // [R][GP]  [da | dg | dmix]
-  float* sacc = GG + R * GP;                // [NRG][kSmall2][D]
-  float* cacc = sacc + NRG * kSmall2 * D;   // [NRG][2]
+  // per-row-group small-gradient accumulators [NRG][kSmall2][D]: shared
+  // memory, or (large d_h) this CTA's slice of a global scratch area
+  float* cacc = GG + R * GP;                // [NRG][2]
+  float* sacc = GSACC ? a.sacc + (size_t)blockIdx.x * NRG * kSmall2 * D : cacc + 2 * NRG;
   const float* Wt1 = img + img2_small(D);
   const float* Wt2 = Wt1 + 6 * D * D;
   const float* Wn1 = Wt2 + 2 * D * D;
   const float* Wn2 = Wn1 + 6 * D * D;
   cta_copy4(sm, img, img2_small(D));
-  for (int q = threadIdx.x; q < NRG * (kSmall2 * D + 2); q += NT) sacc[q] = 0.0f;
+  for (int q = threadIdx.x; q < 2 * NRG; q += NT) cacc[q] = 0.0f;
+  if (!GSACC)
+    for (int q = threadIdx.x; q < NRG * kSmall2 * D; q += NT) sacc[q] = 0.0f;
   __syncthreads();   // the copied constants are read below by every warp
 
   const int lane = threadIdx.x & 31, ug = lane % TU;
@@ -624,11 +629,8 @@ __global__ void __launch_bounds__(NT) gru2d_bptt_kernel(const float* __restrict_
     }
     __syncthreads();
     // ---- (3) recompute the GLU and readout; back through them ----
-    float sg[kSmall2][UPT];
-#pragma unroll
-    for (int q = 0; q < kSmall2; ++q)
-#pragma unroll
-      for (int j = 0; j < UPT; ++j) sg[q][j] = 0.0f;
+    // small gradients go straight to this thread's own accumulator slots
+    auto sacc_add = [&](int q, int u, float v) { sacc[(rg * kSmall2 + q) * D + u] += v; };
     float dcs = 0.0f;
     {
       float acc[RPT][2][UPT];
@@ -669,10 +671,10 @@ __global__ void __launch_bounds__(NT) gru2d_bptt_kernel(const float* __restrict_
           const float dgl = dz0 * (Uo[v] - Uo[D + v]);
           dy[0][j] = dgl * s2[j];
           dy[1][j] = dgl * y1[j] * s2[j] * (1.0f - s2[j]);
-          sg[10][j] += dy[0][j];
-          sg[11][j] += dy[1][j];
-          sg[12][j] = fmaf(dz0, gl[j], sg[12][j]);
-          sg[13][j] = fmaf(-dz0, gl[j], sg[13][j]);
+          sacc_add(10, v, dy[0][j]);
+          sacc_add(11, v, dy[1][j]);
+          sacc_add(12, v, dz0 * gl[j]);
+          sacc_add(13, v, -dz0 * gl[j]);
         }
         st_units<UPT>(DY + (r0 + i) * YP + u0, dy[0]);
         st_units<UPT>(DY + (r0 + i) * YP + D + u0, dy[1]);
@@ -713,25 +715,15 @@ __global__ void __launch_bounds__(NT) gru2d_bptt_kernel(const float* __restrict_
         gg[2][j] = dh[j] * (1.0f - uu[i][j]);                  // d mix
         gg[0][j] = dc * (1.0f - cc[i][j] * cc[i][j]);           // d a
         gg[1][j] = du * uu[i][j] * (1.0f - uu[i][j]);           // d g
-        sg[0][j] += gg[0][j];
-        sg[1][j] += gg[1][j];
-        // one-hot columns (static indices keep the accumulators in registers)
-        sg[2][j] += s_h[i] == 0 ? gg[0][j] : 0.0f;
-        sg[3][j] += s_h[i] == 1 ? gg[0][j] : 0.0f;
-        sg[4][j] += s_v[i] == 0 ? gg[0][j] : 0.0f;
-        sg[5][j] += s_v[i] == 1 ? gg[0][j] : 0.0f;
-        sg[6][j] += s_h[i] == 0 ? gg[1][j] : 0.0f;
-        sg[7][j] += s_h[i] == 1 ? gg[1][j] : 0.0f;
-        sg[8][j] += s_v[i] == 0 ? gg[1][j] : 0.0f;
-        sg[9][j] += s_v[i] == 1 ? gg[1][j] : 0.0f;
+        const int u = u0 + j;
+        sacc_add(0, u, gg[0][j]);
+        sacc_add(1, u, gg[1][j]);
+        if (s_h[i] >= 0) { sacc_add(2 + s_h[i], u, gg[0][j]); sacc_add(6 + s_h[i], u, gg[1][j]); }
+        if (s_v[i] >= 0) { sacc_add(4 + s_v[i], u, gg[0][j]); sacc_add(8 + s_v[i], u, gg[1][j]); }
       }
 #pragma unroll
       for (int g = 0; g < 3; ++g) st_units<UPT>(GG + row * GP + g * D + u0, gg[g]);
     }
-#pragma unroll
-    for (int q = 0; q < kSmall2; ++q)
-#pragma unroll
-      for (int j = 0; j < UPT; ++j) sacc[(rg * kSmall2 + q) * D + u0 + j] += sg[q][j];
     if (ug == 0) { cacc[rg * 2] += dcs; cacc[rg * 2 + 1] -= dcs; }
     accum_outer<D, D, NT, R>(part, o.W1, D, DY, YP, 0, Htile, HP);
     accum_outer<D, D, NT, R>(part, o.W2, D, DY, YP, D, Htile, HP);
@@ -875,6 +867,7 @@ cudaError_t engine_dispatch(const Eng2Args& a, const float* img, int D, cudaStre
     case 32: return launch_engine<32, MODE>(a, img, st, slots);
     case 64: return launch_engine<64, MODE>(a, img, st, slots);
     case 128: return launch_engine<128, MODE>(a, img, st, slots);
+    case 256: return launch_engine<256, MODE>(a, img, st, slots);
   }
   return cudaErrorInvalidValue;
 }
@@ -882,6 +875,7 @@ cudaError_t engine_dispatch(const Eng2Args& a, const float* img, int D, cudaStre
 }  // namespace
 
 size_t gru2d_img_floats(int D) { return (size_t)img2_floats(D); }
+int gru2d_supported(int D) { return D == 8 || D == 16 || D == 32 || D == 64 || D == 128 || D == 256; }
 
 int64_t gru2d_engine_slots(int D, int64_t B, int mode) {
   Eng2Args a{};
@@ -933,8 +927,9 @@ cudaError_t heis_eloc(const uint8_t* sigma, const int4* bonds, const float* delt
 // shared-memory tiles of one CTA stay below 227 KB.
 template <int D> struct TuneB2 {
   static constexpr int NT = D >= 128 ? 128 : (D >= 16 ? 256 : 64);
-  static constexpr int RPT = 2;
+  static constexpr int RPT = D >= 256 ? 1 : 2;
   static constexpr int R = (NT / Geo<D>::TU) * RPT;
+  static constexpr bool GSACC = D >= 256;   // small-gradient accumulators in global scratch
 };
 
 int gru2d_bptt_grid(int D, int64_t B) {
@@ -945,17 +940,25 @@ int gru2d_bptt_grid(int D, int64_t B) {
     case 32: R = TuneB2<32>::R; break;
     case 64: R = TuneB2<64>::R; break;
     case 128: R = TuneB2<128>::R; break;
+    case 256: R = TuneB2<256>::R; break;
   }
   return (int)((B + R - 1) / R);
+}
+
+size_t gru2d_bptt_scratch_floats(int D, int64_t B) {
+  if (D < 256) return 0;
+  constexpr int NRG = TuneB2<256>::NT / Geo<256>::TU;
+  return (size_t)gru2d_bptt_grid(D, B) * NRG * kSmall2 * D;
 }
 
 template <int D>
 cudaError_t launch_bptt2(const Bptt2Args& a, const float* img, cudaStream_t st) {
   constexpr int NT = TuneB2<D>::NT, RPT = TuneB2<D>::RPT;
   constexpr int NRG = NT / Geo<D>::TU, R = NRG * RPT;
+  constexpr bool GS = TuneB2<D>::GSACC;
   const size_t smem = sizeof(float) * (img2_small(D) + R * (2 * D + 4) + R * (D + 4) + R * (2 * D + 4) +
-                                       R * (3 * D + 4) + NRG * (kSmall2 * D + 2));
-  auto k = gru2d_bptt_kernel<D, RPT, NT>;
+                                       R * (3 * D + 4) + 2 * NRG + (GS ? 0 : NRG * kSmall2 * D));
+  auto k = gru2d_bptt_kernel<D, RPT, NT, GS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const unsigned grid = (unsigned)((a.B + R - 1) / R);
@@ -970,6 +973,7 @@ cudaError_t gru2d_bptt(const Bptt2Args& a, const float* img, int D, cudaStream_t
     case 32: return launch_bptt2<32>(a, img, st);
     case 64: return launch_bptt2<64>(a, img, st);
     case 128: return launch_bptt2<128>(a, img, st);
+    case 256: return launch_bptt2<256>(a, img, st);
   }
   return cudaErrorInvalidValue;
 }

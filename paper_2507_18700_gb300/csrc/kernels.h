@@ -79,9 +79,12 @@ struct Bptt2Args {
   const float* weights;
   float* ccarry;             // [B, Lx, d] vertical carries
   float* partial;            // [grid, P]
+  float* sacc;               // large d_h: [grid, row groups, 14, d] small-gradient scratch (zeroed)
 };
 
 size_t gru2d_img_floats(int D);
+int gru2d_supported(int D);
+size_t gru2d_bptt_scratch_floats(int D, int64_t B);
 int64_t gru2d_engine_slots(int D, int64_t B, int mode);
 int gru2d_bptt_grid(int D, int64_t B);
 cudaError_t gru2d_pack(const float* params, float* img, int D, cudaStream_t st);

@@ -27,6 +27,9 @@ def dev(x, dtype=torch.float32):
 
 
 def setup(Lx, Ly, d, sz0, seed=0, noise=0.1):
+    # the noise is kept relative to the Xavier scale: the spectral norm of a
+    # d x 2d Gaussian perturbation grows like sqrt(d)
+    noise = noise * min(1.0, np.sqrt(64.0 / d))
     flat = inputs.xavier_params(2, d, seed=seed, noise_std=noise).astype(np.float32)
     return (nqs.model_desc(nqs.GRU2D, Lx, Ly, d, sz0=sz0), om.Model(om.GRU2D, Lx, Ly, d_h=d, sz0=sz0),
             flat.astype(np.float64), dev(flat))
@@ -49,7 +52,7 @@ def compare_samples(mod, pf, sig_gpu, seed, step):
 
 
 @pytest.mark.parametrize("Lx,Ly,d,B,sz0", [(4, 4, 16, 512, True), (3, 3, 8, 300, False), (8, 8, 64, 256, True),
-                                           (5, 6, 32, 77, False), (3, 4, 128, 40, True)])
+                                           (5, 6, 32, 77, False), (3, 4, 128, 40, True), (4, 4, 256, 24, True)])
 def test_sampling_and_logpsi_2d(Lx, Ly, d, B, sz0):
     desc, mod, pf, p = setup(Lx, Ly, d, sz0)
     sig, lp, hc = nqs.sample(desc, p, B, seed=3, step=1)
@@ -84,7 +87,7 @@ def heis_case(Lx, Ly, d, B, sz0, marshall=True, J=1.0, seed=2):
 @pytest.mark.parametrize("Lx,Ly,d,B,sz0,marshall", [(4, 4, 16, 64, True, True), (2, 2, 8, 16, True, True),
                                                     (3, 4, 32, 50, True, False), (4, 3, 16, 40, False, True),
                                                     (8, 8, 64, 24, True, True), (2, 6, 128, 12, True, True),
-                                                    (5, 2, 8, 33, False, False)])
+                                                    (5, 2, 8, 33, False, False), (4, 4, 256, 10, True, True)])
 def test_heisenberg_local_energy(Lx, Ly, d, B, sz0, marshall):
     heis_case(Lx, Ly, d, B, sz0, marshall)
 
@@ -97,7 +100,7 @@ def grad_check(g, ref):
 
 
 @pytest.mark.parametrize("Lx,Ly,d,B,sz0", [(4, 4, 16, 100, True), (3, 3, 8, 40, False), (8, 8, 64, 64, True),
-                                           (2, 4, 128, 20, True), (5, 3, 32, 37, False)])
+                                           (2, 4, 128, 20, True), (5, 3, 32, 37, False), (3, 4, 256, 12, True)])
 def test_logpsi_grad_2d(Lx, Ly, d, B, sz0):
     # noise 0.05: the mixing path U_mix h' is not squashed, so much larger
     # weights make the hidden state grow geometrically over the lattice and the
@@ -145,3 +148,29 @@ def test_full_size_heisenberg_8x8_d64_b2048():
     g = nqs.logpsi_grad(desc, p, sg, hc2, dev(w))
     torch.cuda.synchronize()
     grad_check(g, ov.logpsi_grad(mod, pf, ref["sigma"], w.astype(np.float64)))
+
+
+def test_largest_model_16x16_d256():
+    """The largest configuration's model: 16 x 16 open lattice, d_h = 256, Marshall
+    sign, zero magnetisation, Xavier weights (seed 3), at a batch the oracle can
+    follow: sampling on every sample, local energies on 2 samples evaluated one by
+    one, gradient on 4 samples."""
+    Lx = Ly = 16
+    d, B = 256, 32
+    desc, mod, pf, p = setup(Lx, Ly, d, True, seed=3, noise=0.0)
+    sig, lp, hc = nqs.sample(desc, p, B, seed=31, step=0)
+    torch.cuda.synchronize()
+    ref = compare_samples(mod, pf, sig.cpu().numpy().astype(np.int64), 31, 0)
+    sg = dev(ref["sigma"], torch.uint8)
+    lp2, hc2 = nqs.logpsi(desc, p, sg)
+    el = nqs.local_energy(desc, p, nqs.heisenberg(1.0, True), sg, hc2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(lp2.cpu().numpy(), ref["logpsi"], atol=1e-4, rtol=0)
+    e_ref = oh.heisenberg_local_energy(Lx, Ly, 1.0, True, ref["sigma"][:2], lambda x: om.logpsi(mod, pf, x))
+    np.testing.assert_allclose(el.cpu().numpy()[:2], e_ref, atol=2e-5 * 480, rtol=0)
+    w = inputs.random_weights(4, seed=32).astype(np.float32)
+    sg4 = sg[:4].contiguous()
+    _, hc4 = nqs.logpsi(desc, p, sg4)
+    g = nqs.logpsi_grad(desc, p, sg4, hc4, dev(w))
+    torch.cuda.synchronize()
+    grad_check(g, ov.logpsi_grad(mod, pf, ref["sigma"][:4], w.astype(np.float64)))
