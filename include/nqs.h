@@ -96,10 +96,9 @@ typedef struct {
   int32_t d_model;    /* 2D GLU width; must equal d_h (App. A) ; 0 means d_h */
   int32_t sz0;        /* 1: zero-magnetisation mask (needs N even) */
   int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of
-                         sampling, teacher forcing and the local-energy chains on
-                         the tensor cores (BF16 operands, FP32 accumulation and
-                         FP32 state; d_h in {16, 32, 64}); the reverse sweep
-                         stays FP32 */
+                         sampling, teacher forcing, the local-energy chains and
+                         the reverse sweep on the tensor cores (BF16 operands,
+                         FP32 accumulation and FP32 state; d_h in {16, 32, 64}) */
 } nqs_model_desc;
 
 typedef struct {

@@ -56,7 +56,7 @@ int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, w, a, b, c, e, f, total;
+  size_t img, w, w2, a, b, c, e, f, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
@@ -67,6 +67,8 @@ Layout layout(const Dims& d, int64_t B, int op) {
   off += align256((two ? gru2d_img_floats(d.d) : gru1d_img_floats(d.d)) * sizeof(float));
   if (use_tc(d)) {
     L.w = off;
+    off += align256(tc1d_wimg_bytes(d.d));
+    L.w2 = off;                                   // transposed image for the reverse sweep
     off += align256(tc1d_wimg_bytes(d.d));
   }
   const size_t BN = (size_t)B * (size_t)d.N;
@@ -90,6 +92,12 @@ Layout layout(const Dims& d, int64_t B, int op) {
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
+      if (use_tc(d)) {
+        L.a = take((size_t)tc1d_bptt_partial_rows(B) * d.P * sizeof(float));  // partial gradients
+        L.b = take((size_t)B * sizeof(float));                                 // weights
+        L.c = take(BN * sizeof(float));                                         // readout gradients dz
+        break;
+      }
       const size_t grid = (size_t)(two ? gru2d_bptt_grid(d.d, B) : gru1d_bptt_grid(d.d, B));
       L.a = take(grid * d.P * sizeof(float));               // partial gradients
       L.b = take((size_t)B * sizeof(float));                 // weights
@@ -354,6 +362,27 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
                               int64_t B, float* grad, void* ws, cudaStream_t st) {
   float* img = at<float>(ws, L.img);
   float* partial = at<float>(ws, L.a);
+  if (use_tc(d)) {
+    uint8_t* w3 = at<uint8_t>(ws, L.w);
+    uint8_t* wt = at<uint8_t>(ws, L.w2);
+    const int rows = tc1d_bptt_partial_rows(B);
+    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
+    TcBpttArgs t{};
+    t.B = B;
+    t.N = d.N;
+    t.P = (int)d.P;
+    t.sigma = sigma;
+    t.hcache = hcache;
+    t.weights = weights;
+    t.dz = at<float>(ws, L.c);
+    t.partial = partial;
+    t.hdr = static_cast<WsHeader*>(ws);
+    if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
+  }
   if (d.cell == NQS_GRU2D) {
     const int grid = gru2d_bptt_grid(d.d, B);
     if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;

@@ -112,7 +112,22 @@ struct Tc1Args {
   WsHeader* hdr;
 };
 
+struct TcBpttArgs {
+  int64_t B;
+  int N, P;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;
+  float* dz;                 // [B, N] readout gradient per (sample, site)
+  float* partial;            // [tc1d_bptt_partial_rows(B), P], zeroed
+  WsHeader* hdr;
+};
+
 int tc1d_supported(int D);
+int tc1d_bptt_partial_rows(int64_t B);
+cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st);
+cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, int D,
+                      cudaStream_t st);
 size_t tc1d_wimg_bytes(int D);
 cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
 // mode 0: sampling, 1: teacher forcing, 2: TFIM chains

@@ -3,11 +3,16 @@
 // completion tracking with bounded waits, and the K-major no-swizzle operand
 // layout.
 //
-// Operand layout (K-major, no swizzle): an operand of R rows x K columns of
-// bf16 is stored as 8 x 8 "core matrices" (8 rows x 16 bytes, rows
-// contiguous).  Core matrix (row group g, k chunk c) sits at
-//   g * kSBO + c * kLBO, kLBO = 128 bytes, kSBO = (K / 8) * 128 bytes,
-// so element (r, k) is at (r/8)*kSBO + (k/8)*128 + (r%8)*16 + (k%8)*2.
+// Operand layout (no swizzle): an operand is stored as "core matrices" of
+// 8 x 16 bytes (8 strided 16-byte rows).  A buffer of R rows x C columns of
+// bf16 written row by row puts element (r, c) at
+//   (r/8) * (C/8) * 128 + (c/8) * 128 + (r%8) * 16 + (c%8) * 2.
+// Read as a K-major operand (rows = M or N, columns = K) its descriptor has
+// LBO = 128 (next 8 columns along K) and SBO = (C/8) * 128 (next 8 rows).
+// Read as an MN-major operand (rows = K, columns = M or N; instruction
+// descriptor transpose bit set) it has LBO = (C/8) * 128 (next 8 rows along
+// K) and SBO = 128 (next 8 columns along M / N): in both cases LBO is the
+// core-matrix stride along K and SBO the stride along M / N.
 #pragma once
 
 #include <cstdint>

@@ -260,6 +260,350 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, GROUPS == 2 ? 512 : 256);
 }
 
+// ----------------------------------------------------------------------------
+// Reverse sweep on the tensor cores.  One CTA = one tile of 128 samples, one
+// thread per sample; sites n = N-1 .. 0.  Per site:
+//   X  = [h_{n-1} | 1 | onehot(s_{n-1}) | 0]  (BF16, 80 columns, row per sample)
+//   MMA_f: acc_f = X[:, :D] W3^T            recompute the gate pre-activations
+//   epilogue: gates, h_n, readout, dz = c_b (onehot - softmax), dh, and
+//             G = [du_a | dr_a | dq | dc_a]  (BF16, 4D columns)
+//   MMA_b: acc_b = G[:, :3D] W3               (dh_{n-1} through the gates)
+//   MMA_w: acc_w += G^T X                     (weight, bias and one-hot-column
+//                                              gradients; G and X read as
+//                                              MN-major operands)
+//   carry = dh direct + acc_b.
+// acc_w stays in TMEM for the whole sweep; readout gradients (U, c) come from
+// dz written per (sample, site) and are reduced by a separate kernel.
+// ----------------------------------------------------------------------------
+constexpr int kXCols = 80;
+
+template <int D>
+struct BSmem {
+  static constexpr int GW = 4 * D >= 128 ? 4 * D : 128;  // G row width (>= one M = 128 operand)
+  static constexpr int kW3 = 0;                         // [3D x D] bf16, K-major
+  static constexpr int kWt = kW3 + 3 * D * D * 2;       // [D x 3D] bf16, K-major
+  static constexpr int kX = kWt + 3 * D * D * 2;        // [128 x 80] bf16
+  static constexpr int kG = kX + 128 * kXCols * 2;      // [128 x GW] bf16
+  static constexpr int kSmall = kG + 128 * GW * 2;      // 12D + 4 floats
+  static constexpr int kBar = (kSmall + (12 * D + 4) * 4 + 15) / 16 * 16;
+  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  // TMEM columns
+  static constexpr int cF = 0, cB = 3 * D, cW0 = 3 * D + D, cW1 = cW0 + kXCols;
+  static_assert(cW1 + kXCols <= 512, "TMEM budget");
+};
+
+__device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+  uint4 q;
+  q.x = *reinterpret_cast<uint32_t*>(&p0);
+  q.y = *reinterpret_cast<uint32_t*>(&p1);
+  q.z = *reinterpret_cast<uint32_t*>(&p2);
+  q.w = *reinterpret_cast<uint32_t*>(&p3);
+  *reinterpret_cast<uint4*>(dst) = q;
+}
+
+template <int D>
+__global__ void __launch_bounds__(128, 1)
+tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3img, const uint8_t* __restrict__ wtimg,
+                 TcBpttArgs a) {
+  using S = BSmem<D>;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sW3 = sm + S::kW3;
+  uint8_t* sWt = sm + S::kWt;
+  uint8_t* sX = sm + S::kX;
+  uint8_t* sG = sm + S::kG;
+  float* small = reinterpret_cast<float*>(sm + S::kSmall);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += 128) {
+    reinterpret_cast<uint4*>(sW3)[i] = reinterpret_cast<const uint4*>(w3img)[i];
+    reinterpret_cast<uint4*>(sWt)[i] = reinterpret_cast<const uint4*>(wtimg)[i];
+  }
+  for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += 128)
+    reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
+  for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += 128) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int m = threadIdx.x;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const float* Ws = small;
+  const float* Bs = small + 6 * D;
+  const float* Us = small + 10 * D;
+  const float c0 = small[12 * D], c1 = small[12 * D + 1];
+  const int N = a.N;
+  const int64_t b = (int64_t)blockIdx.x * 128 + m;
+  const bool valid = b < a.B;
+  const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+  float carry[D];
+#pragma unroll
+  for (int u = 0; u < D; ++u) carry[u] = 0.0f;
+  uint32_t ph_f = 0, ph_b = 0;
+  bool timed_out = false;
+  constexpr uint32_t idesc_f = tc::make_idesc_bf16(128, 3 * D);
+  constexpr uint32_t idesc_b = tc::make_idesc_bf16(128, D);
+  constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, kXCols) | (1u << 15) | (1u << 16);
+  // 16 values of h_{n-1} of this sample (zero at the first site / past the batch)
+  auto load_hp16 = [&](int n, int c, float (&v)[16]) {
+    if (valid && n > 0) {
+      const float4* src = reinterpret_cast<const float4*>(a.hcache + (b * N + n - 1) * D + 16 * c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = src[q];
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+    }
+  };
+
+  for (int n = N - 1; n >= 0; --n) {
+    // ---- X row: [h_{n-1} | 1 | onehot(s_{n-1}) | 0] ----
+    int s_in = -1, s_n = 0;
+    if (valid) {
+      s_n = a.sigma[b * N + n] ? 1 : 0;
+      if (n > 0) s_in = a.sigma[b * N + n - 1] ? 1 : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float hp[16];
+      load_hp16(n, c, hp);
+      st_bf16x8(sX + tc::kmajor_offset(m, 16 * c, kXCols), hp);
+      st_bf16x8(sX + tc::kmajor_offset(m, 16 * c + 8, kXCols), hp + 8);
+    }
+    {
+      float ext[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) ext[q] = 0.0f;
+      ext[0] = 1.0f;
+      if (s_in >= 0) ext[1 + s_in] = 1.0f;
+      st_bf16x8(sX + tc::kmajor_offset(m, D, kXCols), ext);
+      st_bf16x8(sX + tc::kmajor_offset(m, D + 8, kXCols), ext + 8);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (m == 0) {
+#pragma unroll
+      for (int k = 0; k < D / 16; ++k) {
+        const uint64_t da = tc::make_desc(tc::smem_addr(sX) + k * 256, 128, (kXCols / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sW3) + k * 256, 128, (D / 8) * 128);
+        tc::mma_bf16(tbase + S::cF, da, db, idesc_f, k > 0);
+      }
+      tc::mma_commit(&mbar[0]);
+    }
+    if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    ph_f ^= 1;
+    tc::fence_after_sync();
+    const float* Wsel = Ws + (s_in > 0 ? 3 * D : 0);
+    const float on = s_in >= 0 ? 1.0f : 0.0f;
+    // ---- pass 1: recompute h_n for the readout ----
+    float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float au[16], ar[16], ah[16], hp[16];
+      tc::tmem_ld16(trow + S::cF + c * 16, au);
+      tc::tmem_ld16(trow + S::cF + D + c * 16, ar);
+      tc::tmem_ld16(trow + S::cF + 2 * D + c * 16, ah);
+      load_hp16(n, c, hp);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int u = c * 16 + q;
+        const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
+        const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
+        const float cg = fast_tanh(fmaf(rg, ah[q] + Bs[2 * D + u], Bs[3 * D + u] + on * Wsel[2 * D + u]));
+        const float hn = fmaf(ug, cg - hp[q], hp[q]);
+        z0 = fmaf(Us[u], hn, z0);
+        z1 = fmaf(Us[D + u], hn, z1);
+      }
+    }
+    const float d = (z0 + c0) - (z1 + c1);
+    const float dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
+    if (valid) a.dz[b * N + n] = dz0;
+    // ---- pass 2: gates again, backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float au[16], ar[16], ah[16], hp[16];
+      tc::tmem_ld16(trow + S::cF + c * 16, au);
+      tc::tmem_ld16(trow + S::cF + D + c * 16, ar);
+      tc::tmem_ld16(trow + S::cF + 2 * D + c * 16, ah);
+      load_hp16(n, c, hp);
+      tc::tmem_wait_ld();
+      float gbuf[4][16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int u = c * 16 + q;
+        const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
+        const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
+        const float qv = ah[q] + Bs[2 * D + u];
+        const float cg = fast_tanh(fmaf(rg, qv, Bs[3 * D + u] + on * Wsel[2 * D + u]));
+        const float dh = dz0 * (Us[u] - Us[D + u]) + carry[u];
+        const float dc = dh * ug;
+        const float du = dh * (cg - hp[q]);
+        carry[u] = dh * (1.0f - ug);                     // direct path; acc_b adds the rest
+        const float dac = dc * (1.0f - cg * cg);
+        gbuf[0][q] = du * ug * (1.0f - ug);
+        gbuf[1][q] = dac * qv * rg * (1.0f - rg);
+        gbuf[2][q] = dac * rg;
+        gbuf[3][q] = dac;
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        st_bf16x8(sG + tc::kmajor_offset(m, g * D + 16 * c, S::GW), gbuf[g]);
+        st_bf16x8(sG + tc::kmajor_offset(m, g * D + 16 * c + 8, S::GW), gbuf[g] + 8);
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (m == 0) {
+      // dh_{n-1} += G[:, :3D] W3   (K-major: LBO = 128 B along K, SBO = row-group stride)
+#pragma unroll
+      for (int k = 0; k < 3 * D / 16; ++k) {
+        const uint64_t da = tc::make_desc(tc::smem_addr(sG) + k * 256, 128, (S::GW / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sWt) + k * 256, 128, (3 * D / 8) * 128);
+        tc::mma_bf16(tbase + S::cB, da, db, idesc_b, k > 0);
+      }
+      // acc_w += G^T X over the 128 samples of this site, halves of 128 gate rows.
+      // Both operands MN-major: LBO = stride of 8-sample groups along K (the
+      // buffer's row-group stride), SBO = 128 B between 8-column groups along
+      // M / N.  One K = 16 step covers two sample groups.
+#pragma unroll
+      for (int half = 0; half < S::GW / 128; ++half) {
+#pragma unroll
+        for (int k = 0; k < 128 / 16; ++k) {
+          const uint64_t da = tc::make_desc(tc::smem_addr(sG) + half * 16 * 128 + k * 2 * (S::GW / 8) * 128,
+                                            (S::GW / 8) * 128, 128);
+          const uint64_t db = tc::make_desc(tc::smem_addr(sX) + k * 2 * (kXCols / 8) * 128, (kXCols / 8) * 128, 128);
+          tc::mma_bf16(tbase + (half ? S::cW1 : S::cW0), da, db, idesc_w, (n < N - 1) || k > 0);
+        }
+      }
+      tc::mma_commit(&mbar[1]);
+    }
+    if (!tc::mbar_wait(&mbar[1], ph_b, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    ph_b ^= 1;
+    tc::fence_after_sync();
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + S::cB + c * 16, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) carry[c * 16 + q] += v[q];
+    }
+    if (timed_out) break;
+  }
+  // ---- this CTA's weight, bias and one-hot-column gradients from acc_w ----
+  const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2), Win = Wh + D * D;
+  const int bg = Win + 2 * D, br = bg + D, bh = br + D, bin = bh + D;
+  float* part = a.partial + (size_t)blockIdx.x * a.P;
+#pragma unroll 1
+  for (int half = 0; half < S::GW / 128; ++half) {
+    const int gu = half * 128 + m;
+    if (gu < 4 * D) {
+      const int g = gu / D, u = gu % D;
+#pragma unroll 1
+      for (int c = 0; c < kXCols; c += 16) {
+        float v[16];
+        tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int k = c + q;
+          if (k < D) {
+            if (g == 0) part[Wg + u * (D + 2) + k] = v[q];
+            else if (g == 1) part[Wr + u * (D + 2) + k] = v[q];
+            else if (g == 2) part[Wh + u * D + k] = v[q];
+          } else if (k == D) {
+            part[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[q];
+          } else if (k <= D + 2) {
+            const int s = k - D - 1;
+            if (g == 0) part[Wg + u * (D + 2) + D + s] = v[q];
+            else if (g == 1) part[Wr + u * (D + 2) + D + s] = v[q];
+            else if (g == 3) part[Win + u * 2 + s] = v[q];
+          }
+        }
+      }
+    } else {
+      // keep the warp's collective TMEM loads aligned
+#pragma unroll 1
+      for (int c = 0; c < kXCols; c += 16) {
+        float v[16];
+        tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
+        tc::tmem_wait_ld();
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// Readout gradients: dU[0][u] = sum_{b,n} dz h_n[u], dU[1] = -dU[0], dc0 = sum dz,
+// dc1 = -dc0; one partial row per block.
+template <int D>
+__global__ void tc1d_readout_grad_kernel(const float* __restrict__ hcache, const float* __restrict__ dz,
+                                         int64_t rows, float* __restrict__ partial, int P, int part_row0) {
+  __shared__ float red[256];
+  const int Uoff = 3 * D * D + 10 * D, coff = Uoff + 2 * D;   // U and c of the flat 1D layout
+  float* part = partial + (size_t)(part_row0 + blockIdx.x) * P;
+  // thread t accumulates unit t % D over rows t / D, t / D + 256 / D, ...
+  constexpr int RPB = 256 / D;
+  const int u = threadIdx.x % D, r0 = threadIdx.x / D;
+  float acc = 0.0f, accc = 0.0f;
+  for (int64_t r = (int64_t)blockIdx.x * RPB + r0; r < rows; r += (int64_t)gridDim.x * RPB) {
+    const float z = dz[r];
+    acc = fmaf(z, hcache[r * D + u], acc);
+    if (u == 0) accc += z;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < D) {
+    float s = 0.0f;
+    for (int q = 0; q < RPB; ++q) s += red[q * D + threadIdx.x];
+    part[Uoff + threadIdx.x] = s;
+    part[Uoff + D + threadIdx.x] = -s;
+  }
+  __syncthreads();
+  red[threadIdx.x] = accc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int q = 0; q < RPB; ++q) s += red[q * D];
+    part[coff] = s;
+    part[coff + 1] = -s;
+  }
+}
+
+// Gate weights as the B operand of MMA_b: [D rows (k) x 3D (gate, unit)].
+__global__ void pack1d_tc_t_kernel(const float* __restrict__ p, uint8_t* __restrict__ wt, int D) {
+  const int total = 3 * D * D;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int k = t / (3 * D), gu = t % (3 * D), g = gu / D, u = gu % D;
+    const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2);
+    const float v = g == 0 ? p[Wg + u * (D + 2) + k] : g == 1 ? p[Wr + u * (D + 2) + k] : p[Wh + u * D + k];
+    *reinterpret_cast<__nv_bfloat16*>(wt + tc::kmajor_offset(k, gu, 3 * D)) = __float2bfloat16_rn(v);
+  }
+}
+
 int sm_count_tc() {
   static int sms = 0;
   if (!sms) {
@@ -306,6 +650,39 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
 }  // namespace
 
 int tc1d_supported(int D) { return D == 16 || D == 32 || D == 64; }
+
+constexpr int kReadoutGradBlocks = 64;
+int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 127) / 128) + kReadoutGradBlocks; }
+
+template <int D>
+cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, cudaStream_t st) {
+  using S = BSmem<D>;
+  auto k = tc1d_bptt_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int grid = (int)((a.B + 127) / 128);
+  k<<<grid, 128, S::kBytes, st>>>(img, w3, wt, a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
+                                                                   grid);
+  return cudaGetLastError();
+}
+
+cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st) {
+  const int total = 3 * D * D;
+  pack1d_tc_t_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, wt, D);
+  return cudaGetLastError();
+}
+
+cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, int D,
+                      cudaStream_t st) {
+  switch (D) {
+    case 16: return launch_tc_bptt<16>(a, img, w3, wt, st);
+    case 32: return launch_tc_bptt<32>(a, img, w3, wt, st);
+    case 64: return launch_tc_bptt<64>(a, img, w3, wt, st);
+  }
+  return cudaErrorInvalidValue;
+}
 size_t tc1d_wimg_bytes(int D) { return (size_t)3 * D * D * 2; }
 
 cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st) {

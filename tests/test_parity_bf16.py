@@ -106,3 +106,24 @@ def test_bf16_full_size_step_n100_d64_b4096():
     e_ref = oh.tfim_local_energy(N, 1.0, 1.0, ref["sigma"][pick], lambda x: om.logpsi(mod, pf, x))
     assert abs(e16[pick].mean() - e_ref.mean()) / N <= 1e-4
     assert np.isfinite(g.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("N,d,B", [(12, 16, 300), (40, 32, 200), (100, 64, 256), (30, 64, 1)])
+def test_bf16_reverse_sweep(N, d, B):
+    """The BF16 reverse sweep (tensor-core recompute, dh and weight-gradient
+    GEMMs; G and X read as transposed operands) against the oracle's gradient of
+    sum_b w_b log psi_b: cosine >= 0.999 and relative L2 error <= 2e-2 (BF16
+    operands, about 2^-8 per product, summed over B N terms)."""
+    desc, mod, pf, p = setup(N, d)
+    sig = inputs.random_configs(B, N, seed=14)
+    w = inputs.random_weights(B, seed=15).astype(np.float32)
+    sg = torch.tensor(sig, device=DEV)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    g = nqs.logpsi_grad(desc, p, sg, hc, torch.tensor(w, device=DEV), ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    g = g.double().cpu().numpy()
+    assert g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)) >= 0.999
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 2e-2
