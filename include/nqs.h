@@ -249,6 +249,14 @@ nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const float* para
                                    const nqs_ham_desc* ham, const uint8_t* sigma,
                                    const float* hcache, int64_t B, float* eloc, void* stream);
 
+/* Autotuning of the tensor-core kernels' tile shapes (threads per row), on by
+ * default: the first call for a new (kernel, d_h, N, B) that is not inside a
+ * stream capture times every variant on its own inputs (synchronising the
+ * stream once) and caches the fastest for the process; make that first call
+ * before capturing a graph.  on = 0 turns tuning off and clears the cache
+ * (the first variant is then used). */
+void nqs_set_autotune(int on);
+
 /* Copy the workspace status word to *device_status (an nqs_status) after
  * waiting for `stream`; clears it.  This call blocks the host. */
 nqs_status nqs_workspace_status(void* ws, int32_t* device_status, void* stream);

@@ -136,6 +136,8 @@ T* at(void* ws, size_t off) {
 
 extern "C" {
 
+void nqs_set_autotune(int on) { tc1d_set_autotune(on); }
+
 size_t nqs_param_count(const nqs_model_desc* desc) {
   Dims d;
   if (check_desc(desc, &d) != NQS_OK) return 0;
@@ -367,7 +369,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     uint8_t* wt = at<uint8_t>(ws, L.w2);
     const int rows = tc1d_bptt_partial_rows(B);
     if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack_w3(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
     TcBpttArgs t{};

@@ -12,6 +12,10 @@
 // TMEM, applies the gates, updates h in FP32 and the readout, and runs the
 // row logic (draw / teacher forcing / chain bookkeeping).  Two tiles per CTA
 // let one tile's MMA overlap the other tile's epilogue.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -21,8 +25,48 @@ namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before giving up (seconds)
 
-// Row-major [3D][D] gate weights as a K-major BF16 operand (see tc.cuh).
+// Gate weights with the biases and one-hot input columns folded in, as a
+// K-major BF16 operand of 4D rows x (D + 16) columns (see tc.cuh).  Biases and
+// input weights enter as a BF16 pair hi + lo (hi = bf16(v), lo = bf16(v - hi)),
+// so they keep about 16 significant bits.  Against an A row
+// [h | 1 | 1 | onehot(s) | onehot(s) | 0] the four row blocks give
+//   a_u = W_g [h; s] + b_g,  a_r = W_r [h; s] + b_r,  q = W_h h + b_h,
+//   x_in = W_in s + b_in,
+// so the epilogue needs no bias or input terms.
+__device__ __forceinline__ float bf16_hi(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
 __global__ void pack1d_tc_kernel(const float* __restrict__ p, uint8_t* __restrict__ wimg, int D) {
+  const int KA = D + 16, total = 4 * D * KA;
+  const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2), Win = Wh + D * D;
+  const int bg = Win + 2 * D, br = bg + D, bh = br + D, bin = bh + D;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int n = t / KA, k = t % KA, g = n / D, u = n % D;
+    float v = 0.0f;
+    if (k < D) {
+      v = g == 0 ? p[Wg + u * (D + 2) + k] : g == 1 ? p[Wr + u * (D + 2) + k] : g == 2 ? p[Wh + u * D + k] : 0.0f;
+    } else if (k < D + 6) {
+      // extra columns: [b hi | b lo | w0 hi | w1 hi | w0 lo | w1 lo]
+      const int e = k - D;
+      const float bias = p[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u];
+      float w0 = 0.0f, w1 = 0.0f;
+      if (g == 0 || g == 1) {
+        const int W = g == 0 ? Wg : Wr;
+        w0 = p[W + u * (D + 2) + D];
+        w1 = p[W + u * (D + 2) + D + 1];
+      } else if (g == 3) {
+        w0 = p[Win + u * 2];
+        w1 = p[Win + u * 2 + 1];
+      }
+      const float x = e < 2 ? bias : (e == 2 || e == 4) ? w0 : w1;
+      v = e < 2 ? (e == 0 ? bf16_hi(x) : x - bf16_hi(x)) : (e < 4 ? bf16_hi(x) : x - bf16_hi(x));
+    }
+    *reinterpret_cast<__nv_bfloat16*>(wimg + tc::kmajor_offset(n, k, KA)) = __float2bfloat16_rn(v);
+  }
+}
+
+// Gate weights without biases, [3D rows (gate, unit) x D] K-major: the A-side
+// operand of the reverse sweep's recompute GEMM.
+__global__ void pack1d_tc_w3_kernel(const float* __restrict__ p, uint8_t* __restrict__ wimg, int D) {
   const int total = 3 * D * D;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int n = t / D, k = t % D, g = n / D, u = n % D;
@@ -31,6 +75,13 @@ __global__ void pack1d_tc_kernel(const float* __restrict__ p, uint8_t* __restric
     *reinterpret_cast<__nv_bfloat16*>(wimg + tc::kmajor_offset(n, k, D)) = __float2bfloat16_rn(v);
   }
 }
+
+// 16-byte asynchronous global -> shared copies (the chain's next cached state).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Gate nonlinearities of the BF16 path: one hardware tanh (MUFU.TANH,
 // relative error ~2^-11, below the 2^-9 rounding of the BF16 GEMM operands)
@@ -44,33 +95,46 @@ __device__ __forceinline__ float fast_sigmoid(float x) { return fmaf(0.5f, hw_ta
 __device__ __forceinline__ float fast_tanh(float x) { return hw_tanh(x); }
 
 // Shared-memory carve-up (bytes from a 1024-aligned base).
-template <int D, int GROUPS>
+template <int D, int GROUPS, int SPLIT>
 struct Smem {
-  static constexpr int kB = 0;                                   // weights, 3D x D bf16
-  static constexpr int kA = kB + 3 * D * D * 2;                  // GROUPS x 128 x D bf16
-  static constexpr int kSmall = kA + GROUPS * 128 * D * 2;       // 12D+4 floats
-  static constexpr int kBar = (kSmall + (12 * D + 4) * 4 + 15) / 16 * 16;
+  static constexpr int KA = D + 16;                              // A columns: [h | 1 1 | onehot x2 | 0]
+  static constexpr int kB = 0;                                   // weights, 4D x KA bf16
+  static constexpr int kA = kB + 4 * D * KA * 2;                 // GROUPS x 128 x KA bf16
+  static constexpr int kSmall = kA + GROUPS * 128 * KA * 2;      // 12D+4 floats
+  static constexpr int kZ = kSmall + (12 * D + 4) * 4;           // GROUPS x SPLIT x 128 x 2 floats
+  static constexpr int kJob = kZ + GROUPS * SPLIT * 128 * 2 * 4; // GROUPS x 128 long long
+  static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x D floats (next chain state)
+  static constexpr int kBar = (kStage + GROUPS * 128 * D * 4 + 15) / 16 * 16;
   static constexpr int kSlot = kBar + 8 * GROUPS;
   static constexpr int kUsed = kSlot + 16;
   // one CTA per SM for the persistent chain launch (TMEM holds two tiles)
   static constexpr int kBytes = 1024 + (GROUPS == 2 ? (kUsed > 120 * 1024 ? kUsed : 120 * 1024) : kUsed);
 };
 
-template <int D, int MODE, int GROUPS>
-__global__ void __launch_bounds__(128 * GROUPS, 1)
+// Tile threads: SPLIT threads per row, in different warps (a warp reads only
+// its own 32-lane quarter of TMEM): warp w of a tile serves rows 32 (w % 4) ..
+// + 31 and hidden units [(w / 4) D / SPLIT, (w / 4 + 1) D / SPLIT).
+template <int D, int MODE, int GROUPS, int SPLIT>
+__global__ void __launch_bounds__(128 * GROUPS * SPLIT, 1)
 tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wimg, Tc1Args a) {
-  using S = Smem<D, GROUPS>;
-  constexpr int NT = 128 * GROUPS;
-  constexpr int N3 = 3 * D;
+  using S = Smem<D, GROUPS, SPLIT>;
+  constexpr int TT = 128 * SPLIT;          // threads per tile
+  constexpr int NT = TT * GROUPS;
+  constexpr int N4 = 4 * D, KA = S::KA;
+  constexpr int DU = D / SPLIT;            // hidden units per thread
+  static_assert(DU % 16 == 0, "at least 16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sB = sm + S::kB;
   float* small = reinterpret_cast<float*>(sm + S::kSmall);
+  float* zbuf = reinterpret_cast<float*>(sm + S::kZ);
+  long long* jobbuf = reinterpret_cast<long long*>(sm + S::kJob);
+  float* stage = reinterpret_cast<float*>(sm + S::kStage);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
 
   // ---- prologue: operands and constants into shared memory, TMEM, barriers ----
-  for (int i = threadIdx.x; i < N3 * D * 2 / 16; i += NT)
+  for (int i = threadIdx.x; i < N4 * KA * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(wimg)[i];
   for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += NT)
     reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
@@ -85,45 +149,55 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
 
-  const int g = threadIdx.x / 128, m = threadIdx.x % 128, lane = threadIdx.x & 31;
+  const int g = threadIdx.x / TT, tt = threadIdx.x % TT, lane = threadIdx.x & 31;
+  const int wt = tt / 32, part = wt / 4, m = (wt % 4) * 32 + lane;
+  const int u0 = part * DU;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16) + (uint32_t)(g * 256);
-  uint8_t* sA = sm + S::kA + g * 128 * D * 2;
-  const float* Ws = small;
-  const float* Bs = small + 6 * D;
+  const uint32_t bar_main = 1 + g, bar_x = 1 + GROUPS + g;
+  uint8_t* sA = sm + S::kA + g * 128 * KA * 2;
+  float* zb = zbuf + g * SPLIT * 128 * 2;
+  long long* jb = jobbuf + g * 128;
+  float* stg = stage + (g * 128 + m) * D + u0;     // this thread's units of the row's staged state
   const float* Us = small + 10 * D;
   const float c0 = small[12 * D], c1 = small[12 * D + 1];
   const int N = a.N;
   const int64_t B = a.B;
 
-  float h[D];
+  float h[DU];
 #pragma unroll
-  for (int u = 0; u < D; ++u) h[u] = 0.0f;
+  for (int u = 0; u < DU; ++u) h[u] = 0.0f;
   int64_t b = 0;
   int t = 0, s_in = -1, f = 0;
   float acc = 0.0f;            // log psi sum, or Delta of the chain
   bool active = false;
+  long long nxt = -1;          // chains: prefetched next job (-1: none)
+  bool pending = false;        // chains: prefetch requested for the current job
 
   const uint64_t total = MODE == 2 ? (uint64_t)B * (uint64_t)(N - 1) : 0;
-  // Warp-aggregated work-queue pull: one atomic per warp; returns job or -1.
-  auto pull = [&](bool need) -> long long {
-    const unsigned mask = __ballot_sync(0xffffffffu, need);
-    if (!mask) return -1;
-    const int leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (!need) return -1;
-    const unsigned long long j = base + __popc(mask & ((1u << lane) - 1u));
-    return j < total ? (long long)j : -1;
-  };
-  auto load_h = [&](const float* src) {
-#pragma unroll
-    for (int q = 0; q < D / 4; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(src)[q];
-      h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+  // Job hand-out (chains): the part-0 warps pull, one atomic per warp, and
+  // publish the job of each row in shared memory for the other parts.
+  auto pull_publish = [&](bool need) {
+    if (part == 0) {
+      const unsigned mask = __ballot_sync(0xffffffffu, need);
+      long long j = -1;
+      if (mask) {
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const unsigned long long jj = base + __popc(mask & ((1u << lane) - 1u));
+        if (need && jj < total) j = (long long)jj;
+      }
+      if (need) jb[m] = j;
     }
   };
-  auto start_job = [&](long long j) {
+  auto job_src = [&](long long j) -> const float* {
+    const int64_t bj = (int64_t)((unsigned long long)j % (unsigned long long)B);
+    const int fj = (int)((unsigned long long)j / (unsigned long long)B);
+    return a.hcache + (bj * N + fj) * D + u0;
+  };
+  // start job j; its cached state comes from `src` (global or the staging slot)
+  auto start_job = [&](long long j, const float* src) {
     if (j < 0) { active = false; return; }
     b = (int64_t)((unsigned long long)j % (unsigned long long)B);
     f = (int)((unsigned long long)j / (unsigned long long)B);
@@ -133,11 +207,19 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     s_in = 1 - sf;
     acc = 0.5f * (sf == 0 ? -df : df);
     active = true;
-    load_h(a.hcache + (b * N + f) * D);
+    pending = false;
+#pragma unroll
+    for (int q = 0; q < DU / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(src)[q];
+      h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
   };
 
   if constexpr (MODE == 2) {
-    start_job(pull(true));
+    pull_publish(true);
+    tc::group_barrier(bar_x, TT);
+    const long long j = jb[m];
+    if (j >= 0) start_job(j, job_src(j));
   } else {
     b = ((int64_t)blockIdx.x * GROUPS + g) * 128 + m;
     active = b < B;
@@ -146,9 +228,9 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   uint32_t phase = 0;
   bool timed_out = false;
   for (;;) {
-    // ---- (a) this row's h as BF16 into the A operand ----
+    // ---- (a) A row: this thread's units of h as BF16 (+ the constant and input columns by part 0) ----
 #pragma unroll
-    for (int kc = 0; kc < D / 8; ++kc) {
+    for (int kc = 0; kc < DU / 8; ++kc) {
       __nv_bfloat162 p0 = __floats2bfloat162_rn(h[8 * kc + 0], h[8 * kc + 1]);
       __nv_bfloat162 p1 = __floats2bfloat162_rn(h[8 * kc + 2], h[8 * kc + 3]);
       __nv_bfloat162 p2 = __floats2bfloat162_rn(h[8 * kc + 4], h[8 * kc + 5]);
@@ -158,20 +240,32 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       v.y = *reinterpret_cast<uint32_t*>(&p1);
       v.z = *reinterpret_cast<uint32_t*>(&p2);
       v.w = *reinterpret_cast<uint32_t*>(&p3);
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 8 * kc, D)) = v;
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, u0 + 8 * kc, KA)) = v;
+    }
+    if (part == 0) {
+      // bf16 1.0 = 0x3F80: [1 | 1 | s_in == 0 | s_in == 1 | s_in == 0 | s_in == 1 | 0 0]
+      const uint32_t one = 0x3F80u;
+      const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
+      uint4 v;
+      v.x = one | (one << 16);
+      v.y = oh;
+      v.z = oh;
+      v.w = 0u;
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA)) = v;
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
-    const bool any = tc::group_barrier_or(active && !timed_out, 1 + g, 128);
+    const bool any = tc::group_barrier_or(active && !timed_out, bar_main, TT);
     if (!any) break;
     tc::fence_after_sync();
     // ---- (b) one thread issues the tile's MMAs ----
-    if (m == 0) {
-      constexpr uint32_t idesc = tc::make_idesc_bf16(128, N3);
+    if (tt == 0) {
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, N4);
 #pragma unroll
-      for (int k = 0; k < D / 16; ++k) {
-        const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (D / 8) * 128);
-        const uint64_t db = tc::make_desc(tc::smem_addr(sB) + k * 256, 128, (D / 8) * 128);
+      for (int k = 0; k < KA / 16; ++k) {
+        const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (KA / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sB) + k * 256, 128, (KA / 8) * 128);
         tc::mma_bf16(tbase + (uint32_t)(g * 256), da, db, idesc, k > 0);
       }
       tc::mma_commit(&mbar[g]);
@@ -194,65 +288,133 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     }
     phase ^= 1;
     tc::fence_after_sync();
-    // ---- (e) gates and FP32 state update ----
-    const float* Wsel = Ws + (s_in > 0 ? 3 * D : 0);
-    const float on = s_in >= 0 ? 1.0f : 0.0f;
-    float z0 = 0.0f, z1 = 0.0f;
+    // ---- (e) gates and FP32 state update of this thread's units ----
+    // readout: sequential sums over 16-unit chunks, chunks combined by a fixed
+    // pairwise tree, so every SPLIT gives bitwise the same logits
+    float zc0[DU / 16], zc1[DU / 16];
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
-      float au[16], ar[16], ah[16];
-      tc::tmem_ld16(trow + c * 16, au);
-      tc::tmem_ld16(trow + D + c * 16, ar);
-      tc::tmem_ld16(trow + 2 * D + c * 16, ah);
+    for (int c = 0; c < DU / 16; ++c) {
+      float au[16], ar[16], aq[16], ai[16];
+      const int cu = u0 + c * 16;
+      tc::tmem_ld16(trow + cu, au);
+      tc::tmem_ld16(trow + D + cu, ar);
+      tc::tmem_ld16(trow + 2 * D + cu, aq);
+      tc::tmem_ld16(trow + 3 * D + cu, ai);
       tc::tmem_wait_ld();
+      float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int u = c * 16 + q;
-        const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
-        const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
-        const float cc = fast_tanh(fmaf(rg, ah[q] + Bs[2 * D + u], Bs[3 * D + u] + on * Wsel[2 * D + u]));
-        h[u] = fmaf(ug, cc - h[u], h[u]);
-        z0 = fmaf(Us[u], h[u], z0);
-        z1 = fmaf(Us[D + u], h[u], z1);
+        const int u = cu + q, j = c * 16 + q;
+        const float ug = fast_sigmoid(au[q]);
+        const float rg = fast_sigmoid(ar[q]);
+        const float cc = fast_tanh(fmaf(rg, aq[q], ai[q]));
+        h[j] = fmaf(ug, cc - h[j], h[j]);
+        s0 = fmaf(Us[u], h[j], s0);
+        s1 = fmaf(Us[D + u], h[j], s1);
       }
+      zc0[c] = s0;
+      zc1[c] = s1;
     }
-    // ---- (f) row logic ----
-    bool need = false;
+#pragma unroll
+    for (int w = 1; w < DU / 16; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < DU / 16; c += 2 * w) {
+        zc0[c] += zc0[c + w];
+        zc1[c] += zc1[c + w];
+      }
+    float z0 = zc0[0], z1 = zc1[0];
+    if constexpr (SPLIT > 1) {
+      zb[(part * 128 + m) * 2] = z0;
+      zb[(part * 128 + m) * 2 + 1] = z1;
+      tc::group_barrier(bar_x, TT);
+      float p0[SPLIT], p1[SPLIT];
+#pragma unroll
+      for (int p = 0; p < SPLIT; ++p) {
+        p0[p] = zb[(p * 128 + m) * 2];
+        p1[p] = zb[(p * 128 + m) * 2 + 1];
+      }
+#pragma unroll
+      for (int w = 1; w < SPLIT; w *= 2)
+#pragma unroll
+        for (int p = 0; p + w < SPLIT; p += 2 * w) {
+          p0[p] += p0[p + w];
+          p1[p] += p1[p + w];
+        }
+      z0 = p0[0];
+      z1 = p1[0];
+    }
+    // ---- (f) row logic (identical in every part; side effects by part 0) ----
+    bool fin = false;
     if (active && !timed_out) {
       const float d = (z0 + c0) - (z1 + c1);
       if constexpr (MODE == 2) {
         acc += 0.5f * (log_prob(s_t, d) - log_prob(s_t, dl));
         s_in = s_t;
         if (++t == N) {
-          a.delta[b * N + f] = acc;
-          need = true;
+          if (part == 0) a.delta[b * N + f] = acc;
+          fin = true;
         }
       } else {
         int s = s_t;
         if constexpr (MODE == 0) {
           s = uni < sigmoid_acc(d) ? 0 : 1;
-          a.sigma_out[b * N + t] = (uint8_t)s;
+          if (part == 0) a.sigma_out[b * N + t] = (uint8_t)s;
         }
         acc += log_prob(s, d);
         if (a.hcache) {
-          float4* dst = reinterpret_cast<float4*>(a.hcache + (b * N + t) * D);
+          float4* dst = reinterpret_cast<float4*>(a.hcache + (b * N + t) * D + u0);
 #pragma unroll
-          for (int q = 0; q < D / 4; ++q) dst[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+          for (int q = 0; q < DU / 4; ++q) dst[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
         }
         s_in = s;
         if (++t == N) {
           const float lp = 0.5f * acc;
-          a.logpsi[b] = lp;
-          if (!isfinite(lp)) flag_status(a.hdr, NQS_ENONFINITE);
+          if (part == 0) {
+            a.logpsi[b] = lp;
+            if (!isfinite(lp)) flag_status(a.hdr, NQS_ENONFINITE);
+          }
           active = false;
         }
       }
     }
     if constexpr (MODE == 2) {
-      const long long j = pull(need);
-      if (need) start_job(j);
+      // A finished chain takes its prefetched successor (a prefetch that found
+      // the queue empty retires the row); a chain that finished without a
+      // prefetch pulls its successor now.  A chain with one step left pulls
+      // the next job and starts copying its cached state to shared memory.
+      bool need = false;
+      if (fin) {
+        if (!pending) {
+          need = true;
+        } else if (nxt >= 0) {
+          cp_async_wait_all();
+          start_job(nxt, stg);
+        } else {
+          active = false;
+        }
+        nxt = -1;
+      }
+      const bool want = active && !timed_out && !pending && t == N - 1;
+      pull_publish(need || want);
+      tc::group_barrier(bar_x, TT);
+      if (need) {
+        const long long j = jb[m];
+        start_job(j, j >= 0 ? job_src(j) : nullptr);
+      } else if (want) {
+        pending = true;
+        nxt = jb[m];
+        if (nxt >= 0) {
+          const float* src = job_src(nxt);
+#pragma unroll
+          for (int q = 0; q < DU / 4; ++q) cp_async16(stg + 4 * q, src + 4 * q);
+          cp_async_commit();
+        }
+      }
+    } else if constexpr (SPLIT > 1) {
+      tc::group_barrier(bar_x, TT);   // zbuf is rewritten next step
     }
   }
+  cp_async_wait_all();
   // ---- epilogue: free TMEM once both tiles are done ----
   tc::fence_before_sync();
   __syncthreads();
@@ -285,7 +447,8 @@ struct BSmem {
   static constexpr int kX = kWt + 3 * D * D * 2;        // [128 x 80] bf16
   static constexpr int kG = kX + 128 * kXCols * 2;      // [128 x GW] bf16
   static constexpr int kSmall = kG + 128 * GW * 2;      // 12D + 4 floats
-  static constexpr int kBar = (kSmall + (12 * D + 4) * 4 + 15) / 16 * 16;
+  static constexpr int kZ = kSmall + (12 * D + 4) * 4;  // 4 x 128 x 2 floats (readout exchange)
+  static constexpr int kBar = (kZ + 4 * 128 * 2 * 4 + 15) / 16 * 16;
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
   // TMEM columns
@@ -306,11 +469,14 @@ __device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
   *reinterpret_cast<uint4*>(dst) = q;
 }
 
-template <int D>
-__global__ void __launch_bounds__(128, 1)
+template <int D, int SPLIT>
+__global__ void __launch_bounds__(128 * SPLIT, 1)
 tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3img, const uint8_t* __restrict__ wtimg,
                  TcBpttArgs a) {
   using S = BSmem<D>;
+  constexpr int NT = 128 * SPLIT;
+  constexpr int DU = D / SPLIT;            // hidden units per thread
+  static_assert(DU % 16 == 0, "at least 16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sW3 = sm + S::kW3;
@@ -318,15 +484,16 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
   uint8_t* sX = sm + S::kX;
   uint8_t* sG = sm + S::kG;
   float* small = reinterpret_cast<float*>(sm + S::kSmall);
+  float* zb = reinterpret_cast<float*>(sm + S::kZ);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
-  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += 128) {
+  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += NT) {
     reinterpret_cast<uint4*>(sW3)[i] = reinterpret_cast<const uint4*>(w3img)[i];
     reinterpret_cast<uint4*>(sWt)[i] = reinterpret_cast<const uint4*>(wtimg)[i];
   }
-  for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += 128)
+  for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += NT)
     reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
-  for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += 128) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += NT) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -338,7 +505,10 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const int m = threadIdx.x;
+  // thread -> (row, unit range): warp w serves rows 32 (w % 4) + lane and
+  // units [(w / 4) DU, (w / 4 + 1) DU)
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
+  const int u0 = part * DU;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
   const float* Ws = small;
   const float* Bs = small + 6 * D;
@@ -348,18 +518,18 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
   const int64_t b = (int64_t)blockIdx.x * 128 + m;
   const bool valid = b < a.B;
   const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
-  float carry[D];
+  float carry[DU];
 #pragma unroll
-  for (int u = 0; u < D; ++u) carry[u] = 0.0f;
+  for (int u = 0; u < DU; ++u) carry[u] = 0.0f;
   uint32_t ph_f = 0, ph_b = 0;
   bool timed_out = false;
   constexpr uint32_t idesc_f = tc::make_idesc_bf16(128, 3 * D);
   constexpr uint32_t idesc_b = tc::make_idesc_bf16(128, D);
   constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, kXCols) | (1u << 15) | (1u << 16);
-  // 16 values of h_{n-1} of this sample (zero at the first site / past the batch)
-  auto load_hp16 = [&](int n, int c, float (&v)[16]) {
+  // 16 values of h_{n-1} of this sample starting at unit u (zero at the first site / past the batch)
+  auto load_hp16 = [&](int n, int u, float (&v)[16]) {
     if (valid && n > 0) {
-      const float4* src = reinterpret_cast<const float4*>(a.hcache + (b * N + n - 1) * D + 16 * c);
+      const float4* src = reinterpret_cast<const float4*>(a.hcache + (b * N + n - 1) * D + u);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float4 t = src[q];
@@ -379,13 +549,13 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
       if (n > 0) s_in = a.sigma[b * N + n - 1] ? 1 : 0;
     }
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       float hp[16];
-      load_hp16(n, c, hp);
-      st_bf16x8(sX + tc::kmajor_offset(m, 16 * c, kXCols), hp);
-      st_bf16x8(sX + tc::kmajor_offset(m, 16 * c + 8, kXCols), hp + 8);
+      load_hp16(n, u0 + 16 * c, hp);
+      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 16 * c, kXCols), hp);
+      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 16 * c + 8, kXCols), hp + 8);
     }
-    {
+    if (part == 0) {
       float ext[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) ext[q] = 0.0f;
@@ -398,7 +568,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (m == 0) {
+    if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < D / 16; ++k) {
         const uint64_t da = tc::make_desc(tc::smem_addr(sX) + k * 256, 128, (kXCols / 8) * 128);
@@ -412,51 +582,84 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
     tc::fence_after_sync();
     const float* Wsel = Ws + (s_in > 0 ? 3 * D : 0);
     const float on = s_in >= 0 ? 1.0f : 0.0f;
-    // ---- pass 1: recompute h_n for the readout ----
-    float z0 = 0.0f, z1 = 0.0f;
+    // ---- pass 1: recompute h_n for the readout (chunk sums in a fixed tree) ----
+    float zc0[DU / 16], zc1[DU / 16];
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       float au[16], ar[16], ah[16], hp[16];
-      tc::tmem_ld16(trow + S::cF + c * 16, au);
-      tc::tmem_ld16(trow + S::cF + D + c * 16, ar);
-      tc::tmem_ld16(trow + S::cF + 2 * D + c * 16, ah);
-      load_hp16(n, c, hp);
+      const int cu = u0 + 16 * c;
+      tc::tmem_ld16(trow + S::cF + cu, au);
+      tc::tmem_ld16(trow + S::cF + D + cu, ar);
+      tc::tmem_ld16(trow + S::cF + 2 * D + cu, ah);
+      load_hp16(n, cu, hp);
       tc::tmem_wait_ld();
+      float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int u = c * 16 + q;
+        const int u = cu + q;
         const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
         const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
         const float cg = fast_tanh(fmaf(rg, ah[q] + Bs[2 * D + u], Bs[3 * D + u] + on * Wsel[2 * D + u]));
         const float hn = fmaf(ug, cg - hp[q], hp[q]);
-        z0 = fmaf(Us[u], hn, z0);
-        z1 = fmaf(Us[D + u], hn, z1);
+        s0 = fmaf(Us[u], hn, s0);
+        s1 = fmaf(Us[D + u], hn, s1);
       }
+      zc0[c] = s0;
+      zc1[c] = s1;
+    }
+#pragma unroll
+    for (int w = 1; w < DU / 16; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < DU / 16; c += 2 * w) {
+        zc0[c] += zc0[c + w];
+        zc1[c] += zc1[c + w];
+      }
+    float z0 = zc0[0], z1 = zc1[0];
+    if constexpr (SPLIT > 1) {
+      zb[(part * 128 + m) * 2] = z0;
+      zb[(part * 128 + m) * 2 + 1] = z1;
+      __syncthreads();
+      float p0[SPLIT], p1[SPLIT];
+#pragma unroll
+      for (int p = 0; p < SPLIT; ++p) {
+        p0[p] = zb[(p * 128 + m) * 2];
+        p1[p] = zb[(p * 128 + m) * 2 + 1];
+      }
+#pragma unroll
+      for (int w = 1; w < SPLIT; w *= 2)
+#pragma unroll
+        for (int p = 0; p + w < SPLIT; p += 2 * w) {
+          p0[p] += p0[p + w];
+          p1[p] += p1[p + w];
+        }
+      z0 = p0[0];
+      z1 = p1[0];
     }
     const float d = (z0 + c0) - (z1 + c1);
     const float dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
-    if (valid) a.dz[b * N + n] = dz0;
+    if (valid && part == 0) a.dz[b * N + n] = dz0;
     // ---- pass 2: gates again, backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       float au[16], ar[16], ah[16], hp[16];
-      tc::tmem_ld16(trow + S::cF + c * 16, au);
-      tc::tmem_ld16(trow + S::cF + D + c * 16, ar);
-      tc::tmem_ld16(trow + S::cF + 2 * D + c * 16, ah);
-      load_hp16(n, c, hp);
+      const int cu = u0 + 16 * c;
+      tc::tmem_ld16(trow + S::cF + cu, au);
+      tc::tmem_ld16(trow + S::cF + D + cu, ar);
+      tc::tmem_ld16(trow + S::cF + 2 * D + cu, ah);
+      load_hp16(n, cu, hp);
       tc::tmem_wait_ld();
       float gbuf[4][16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int u = c * 16 + q;
+        const int u = cu + q, j = 16 * c + q;
         const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
         const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
         const float qv = ah[q] + Bs[2 * D + u];
         const float cg = fast_tanh(fmaf(rg, qv, Bs[3 * D + u] + on * Wsel[2 * D + u]));
-        const float dh = dz0 * (Us[u] - Us[D + u]) + carry[u];
+        const float dh = dz0 * (Us[u] - Us[D + u]) + carry[j];
         const float dc = dh * ug;
         const float du = dh * (cg - hp[q]);
-        carry[u] = dh * (1.0f - ug);                     // direct path; acc_b adds the rest
+        carry[j] = dh * (1.0f - ug);                     // direct path; acc_b adds the rest
         const float dac = dc * (1.0f - cg * cg);
         gbuf[0][q] = du * ug * (1.0f - ug);
         gbuf[1][q] = dac * qv * rg * (1.0f - rg);
@@ -465,15 +668,15 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
       }
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        st_bf16x8(sG + tc::kmajor_offset(m, g * D + 16 * c, S::GW), gbuf[g]);
-        st_bf16x8(sG + tc::kmajor_offset(m, g * D + 16 * c + 8, S::GW), gbuf[g] + 8);
+        st_bf16x8(sG + tc::kmajor_offset(m, g * D + cu, S::GW), gbuf[g]);
+        st_bf16x8(sG + tc::kmajor_offset(m, g * D + cu + 8, S::GW), gbuf[g] + 8);
       }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (m == 0) {
+    if (threadIdx.x == 0) {
       // dh_{n-1} += G[:, :3D] W3   (K-major: LBO = 128 B along K, SBO = row-group stride)
 #pragma unroll
       for (int k = 0; k < 3 * D / 16; ++k) {
@@ -501,53 +704,46 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
     ph_b ^= 1;
     tc::fence_after_sync();
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       float v[16];
-      tc::tmem_ld16(trow + S::cB + c * 16, v);
+      tc::tmem_ld16(trow + S::cB + u0 + 16 * c, v);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 16; ++q) carry[c * 16 + q] += v[q];
+      for (int q = 0; q < 16; ++q) carry[16 * c + q] += v[q];
     }
     if (timed_out) break;
   }
-  // ---- this CTA's weight, bias and one-hot-column gradients from acc_w ----
+  // ---- this CTA's weight, bias and one-hot-column gradients from acc_w (part-0 warps) ----
   const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2), Win = Wh + D * D;
   const int bg = Win + 2 * D, br = bg + D, bh = br + D, bin = bh + D;
-  float* part = a.partial + (size_t)blockIdx.x * a.P;
+  float* part_g = a.partial + (size_t)blockIdx.x * a.P;
+  if (part == 0) {
 #pragma unroll 1
-  for (int half = 0; half < S::GW / 128; ++half) {
-    const int gu = half * 128 + m;
-    if (gu < 4 * D) {
+    for (int half = 0; half < S::GW / 128; ++half) {
+      const int gu = half * 128 + m;
       const int g = gu / D, u = gu % D;
 #pragma unroll 1
       for (int c = 0; c < kXCols; c += 16) {
         float v[16];
         tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
         tc::tmem_wait_ld();
+        if (gu >= 4 * D) continue;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int k = c + q;
           if (k < D) {
-            if (g == 0) part[Wg + u * (D + 2) + k] = v[q];
-            else if (g == 1) part[Wr + u * (D + 2) + k] = v[q];
-            else if (g == 2) part[Wh + u * D + k] = v[q];
+            if (g == 0) part_g[Wg + u * (D + 2) + k] = v[q];
+            else if (g == 1) part_g[Wr + u * (D + 2) + k] = v[q];
+            else if (g == 2) part_g[Wh + u * D + k] = v[q];
           } else if (k == D) {
-            part[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[q];
+            part_g[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[q];
           } else if (k <= D + 2) {
             const int s = k - D - 1;
-            if (g == 0) part[Wg + u * (D + 2) + D + s] = v[q];
-            else if (g == 1) part[Wr + u * (D + 2) + D + s] = v[q];
-            else if (g == 3) part[Win + u * 2 + s] = v[q];
+            if (g == 0) part_g[Wg + u * (D + 2) + D + s] = v[q];
+            else if (g == 1) part_g[Wr + u * (D + 2) + D + s] = v[q];
+            else if (g == 3) part_g[Win + u * 2 + s] = v[q];
           }
         }
-      }
-    } else {
-      // keep the warp's collective TMEM loads aligned
-#pragma unroll 1
-      for (int c = 0; c < kXCols; c += 16) {
-        float v[16];
-        tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
-        tc::tmem_wait_ld();
       }
     }
   }
@@ -558,38 +754,54 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
 }
 
 // Readout gradients: dU[0][u] = sum_{b,n} dz h_n[u], dU[1] = -dU[0], dc0 = sum dz,
-// dc1 = -dc0; one partial row per block.
+// dc1 = -dc0; one partial row per block.  A warp reads D/4 float4 of a cached
+// state per row (coalesced 256-byte rows) and strides over rows.
 template <int D>
-__global__ void tc1d_readout_grad_kernel(const float* __restrict__ hcache, const float* __restrict__ dz,
-                                         int64_t rows, float* __restrict__ partial, int P, int part_row0) {
-  __shared__ float red[256];
+__global__ void __launch_bounds__(256) tc1d_readout_grad_kernel(const float* __restrict__ hcache,
+                                                               const float* __restrict__ dz, int64_t rows,
+                                                               float* __restrict__ partial, int P, int part_row0) {
+  constexpr int L4 = D / 4;               // float4 per state
+  constexpr int RPW = 32 / L4 > 0 ? 32 / L4 : 1;   // rows per warp pass
+  __shared__ float red[8][D + 1];
   const int Uoff = 3 * D * D + 10 * D, coff = Uoff + 2 * D;   // U and c of the flat 1D layout
   float* part = partial + (size_t)(part_row0 + blockIdx.x) * P;
-  // thread t accumulates unit t % D over rows t / D, t / D + 256 / D, ...
-  constexpr int RPB = 256 / D;
-  const int u = threadIdx.x % D, r0 = threadIdx.x / D;
-  float acc = 0.0f, accc = 0.0f;
-  for (int64_t r = (int64_t)blockIdx.x * RPB + r0; r < rows; r += (int64_t)gridDim.x * RPB) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = lane % L4, sub = lane / L4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  float accc = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * 8 * RPW;
+  for (int64_t r = ((int64_t)blockIdx.x * 8 + warp) * RPW + sub; r < rows; r += stride) {
+    if (sub >= RPW) break;
     const float z = dz[r];
-    acc = fmaf(z, hcache[r * D + u], acc);
-    if (u == 0) accc += z;
+    const float4 h = reinterpret_cast<const float4*>(hcache + r * D)[q];
+    acc.x = fmaf(z, h.x, acc.x); acc.y = fmaf(z, h.y, acc.y);
+    acc.z = fmaf(z, h.z, acc.z); acc.w = fmaf(z, h.w, acc.w);
+    if (q == 0) accc += z;
   }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x < D) {
-    float s = 0.0f;
-    for (int q = 0; q < RPB; ++q) s += red[q * D + threadIdx.x];
-    part[Uoff + threadIdx.x] = s;
-    part[Uoff + D + threadIdx.x] = -s;
+  // sum the RPW sub-rows of the warp, then the 8 warps
+  for (int off = L4; off < 32; off <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
+  }
+  for (int off = 16; off > 0; off >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, off);   // only q == 0 lanes hold sums
+  if (sub == 0) {
+    red[warp][4 * q] = acc.x; red[warp][4 * q + 1] = acc.y;
+    red[warp][4 * q + 2] = acc.z; red[warp][4 * q + 3] = acc.w;
+    if (q == 0) red[warp][D] = accc;
   }
   __syncthreads();
-  red[threadIdx.x] = accc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  for (int u = threadIdx.x; u <= D; u += 256) {
     float s = 0.0f;
-    for (int q = 0; q < RPB; ++q) s += red[q * D];
-    part[coff] = s;
-    part[coff + 1] = -s;
+    for (int w = 0; w < 8; ++w) s += red[w][u];
+    if (u < D) {
+      part[Uoff + u] = s;
+      part[Uoff + D + u] = -s;
+    } else {
+      part[coff] = s;
+      part[coff + 1] = -s;
+    }
   }
 }
 
@@ -617,10 +829,10 @@ int sm_count_tc() {
   return sms;
 }
 
-template <int D, int MODE, int GROUPS>
+template <int D, int MODE, int GROUPS, int SPLIT>
 cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, cudaStream_t st) {
-  using S = Smem<D, GROUPS>;
-  auto k = tc1d_engine_kernel<D, MODE, GROUPS>;
+  using S = Smem<D, GROUPS, SPLIT>;
+  auto k = tc1d_engine_kernel<D, MODE, GROUPS, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   int64_t grid;
@@ -633,38 +845,136 @@ cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, c
     grid = (a.B + 128 * GROUPS - 1) / (128 * GROUPS);
   }
   if (grid < 1) grid = 1;
-  k<<<(unsigned)grid, 128 * GROUPS, S::kBytes, st>>>(img, wimg, a);
+  k<<<(unsigned)grid, 128 * GROUPS * SPLIT, S::kBytes, st>>>(img, wimg, a);
   return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Autotuner: each kernel has a few tile variants (threads per row).  The first
+// call for a (kernel, d_h, N, B) key that is not inside a stream capture runs
+// every variant twice on the call's own inputs, times the second run with
+// CUDA events (this synchronises the stream once) and caches the fastest; the
+// outputs of the final launch are those of the chosen variant (every variant
+// computes the same values).  Inside a capture, or with tuning off, the cached
+// choice or the first variant is used.
+// ----------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, long long>, int> g_tune;
+bool g_tune_on = true;
+
+template <typename Launch, typename Prep>
+cudaError_t tuned_launch(int kind, int D, int N, int64_t B, int nvar, Launch launch, Prep prep, cudaStream_t st) {
+  const auto key = std::make_tuple(kind, D, N, (long long)B);
+  int choice = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) choice = it->second;
+  }
+  cudaError_t e;
+  if (choice < 0) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) { cudaGetLastError(); cap = cudaStreamCaptureStatusActive; }
+    if (!g_tune_on || nvar == 1 || cap != cudaStreamCaptureStatusNone) {
+      choice = 0;
+    } else {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      for (int v = 0; v < nvar; ++v) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          if ((e = prep()) != cudaSuccess) return e;
+          cudaEventRecord(e0, st);
+          if ((e = launch(v)) != cudaSuccess) return e;
+          cudaEventRecord(e1, st);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best) { best = ms; choice = v; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = choice;
+    }
+  }
+  if ((e = prep()) != cudaSuccess) return e;
+  return launch(choice);
 }
 
 template <int D>
 cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wimg, int mode, cudaStream_t st) {
-  switch (mode) {
-    case 0: return launch_tc<D, 0, 1>(a, img, wimg, st);
-    case 1: return launch_tc<D, 1, 1>(a, img, wimg, st);
-    case 2: return launch_tc<D, 2, 2>(a, img, wimg, st);
+  auto none = []() { return cudaSuccess; };
+  if (mode == 2) {
+    // chains: 1 or 2 threads per row (the work counter is reset before every run)
+    auto reset = [&]() { return cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st); };
+    auto run = [&](int v) {
+      if (v == 1 && D >= 32) return launch_tc<D, 2, 2, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
+      return launch_tc<D, 2, 2, 1>(a, img, wimg, st);
+    };
+    return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
   }
-  return cudaErrorInvalidValue;
+  // sampling / teacher forcing: 1, 2 or 4 threads per row
+  auto run = [&](int v) {
+    if (mode == 0) {
+      if (v == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(a, img, wimg, st);
+      if (v == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
+      return launch_tc<D, 0, 1, 1>(a, img, wimg, st);
+    }
+    if (v == 2 && D >= 64) return launch_tc<D, 1, 1, (D >= 64 ? 4 : 1)>(a, img, wimg, st);
+    if (v == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
+    return launch_tc<D, 1, 1, 1>(a, img, wimg, st);
+  };
+  return tuned_launch(mode, D, a.N, a.B, D >= 64 ? 3 : (D >= 32 ? 2 : 1), run, none, st);
 }
 
 }  // namespace
 
 int tc1d_supported(int D) { return D == 16 || D == 32 || D == 64; }
 
-constexpr int kReadoutGradBlocks = 64;
+void tc1d_set_autotune(int on) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_on = on != 0;
+  if (!on) g_tune.clear();
+}
+
+constexpr int kReadoutGradBlocks = 304;
 int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 127) / 128) + kReadoutGradBlocks; }
 
-template <int D>
-cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, cudaStream_t st) {
+template <int D, int SPLIT>
+cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt,
+                             cudaStream_t st) {
   using S = BSmem<D>;
-  auto k = tc1d_bptt_kernel<D>;
+  auto k = tc1d_bptt_kernel<D, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int grid = (int)((a.B + 127) / 128);
-  k<<<grid, 128, S::kBytes, st>>>(img, w3, wt, a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k<<<grid, 128 * SPLIT, S::kBytes, st>>>(img, w3, wt, a);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, cudaStream_t st) {
+  // reverse sweep: 1, 2 or 4 threads per row, picked by the autotuner
+  auto run = [&](int v) {
+    if (v == 2 && D >= 64) return launch_tc_bptt_v<D, (D >= 64 ? 4 : 1)>(a, img, w3, wt, st);
+    if (v == 1 && D >= 32) return launch_tc_bptt_v<D, (D >= 32 ? 2 : 1)>(a, img, w3, wt, st);
+    return launch_tc_bptt_v<D, 1>(a, img, w3, wt, st);
+  };
+  auto none = []() { return cudaSuccess; };
+  cudaError_t e = tuned_launch(3, D, a.N, a.B, D >= 64 ? 3 : (D >= 32 ? 2 : 1), run, none, st);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)((a.B + 127) / 128);
   tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
                                                                    grid);
+  return cudaGetLastError();
+}
+
+cudaError_t tc1d_pack_w3(const float* params, uint8_t* w3, int D, cudaStream_t st) {
+  const int total = 3 * D * D;
+  pack1d_tc_w3_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, w3, D);
   return cudaGetLastError();
 }
 
@@ -683,10 +993,10 @@ cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, 
   }
   return cudaErrorInvalidValue;
 }
-size_t tc1d_wimg_bytes(int D) { return (size_t)3 * D * D * 2; }
+size_t tc1d_wimg_bytes(int D) { return (size_t)4 * D * (D + 16) * 2; }
 
 cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st) {
-  const int total = 3 * D * D;
+  const int total = 4 * D * (D + 16);
   pack1d_tc_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, wimg, D);
   return cudaGetLastError();
 }

@@ -24,7 +24,8 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
-           "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched"]
+           "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
+           "nqs_set_autotune"]
 
 
 class NqsError(RuntimeError):
@@ -105,6 +106,8 @@ def lib():
     L.nqs_vmc_step_batched_workspace_bytes.argtypes = [ctypes.c_int, P(Replica)]
     L.nqs_vmc_step_batched.restype = ctypes.c_int
     L.nqs_vmc_step_batched.argtypes = [ctypes.c_int, P(Replica), u64, vp, vp, sz, vp]
+    L.nqs_set_autotune.restype = None
+    L.nqs_set_autotune.argtypes = [ctypes.c_int]
     L.nqs_status_string.restype = ctypes.c_char_p
     L.nqs_status_string.argtypes = [ctypes.c_int]
     _lib = L
@@ -130,6 +133,11 @@ def _need(t, dtype, shape, name):
     if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
         raise ValueError("%s must be a contiguous CUDA %s tensor of shape %s, got %s %s %s"
                          % (name, dtype, tuple(shape), t.device, t.dtype, tuple(t.shape)))
+
+
+def set_autotune(on):
+    """Turn the tile-shape autotuner of the tensor-core kernels on or off."""
+    lib().nqs_set_autotune(1 if on else 0)
 
 
 def param_count(desc):

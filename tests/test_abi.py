@@ -21,7 +21,7 @@ def L():
 
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "nqs.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:size_t|nqs_status|const char\*)\s+(nqs_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:size_t|nqs_status|const char\*|void)\s+(nqs_\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported(L):

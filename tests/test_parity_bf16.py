@@ -127,3 +127,22 @@ def test_bf16_reverse_sweep(N, d, B):
     g = g.double().cpu().numpy()
     assert g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)) >= 0.999
     assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 2e-2
+
+
+def test_autotuned_variants_agree_bitwise():
+    """Every tile variant the autotuner may pick computes bitwise the same samples,
+    cache, local energies and gradient (tuning off = first variant)."""
+    N, d, B = 60, 64, 700
+    desc, mod, pf, p = setup(N, d)
+    outs = []
+    for on in (False, True, True):
+        nqs.set_autotune(on)
+        s, lp, hc = nqs.sample(desc, p, B, seed=3, step=2)
+        el = nqs.local_energy(desc, p, nqs.tfim(), s, hc)
+        g, st = nqs.vmc_grad(desc, p, s, hc, el)
+        torch.cuda.synchronize()
+        outs.append((s.clone(), lp.clone(), hc.clone(), el.clone(), g.clone(), st.clone()))
+    nqs.set_autotune(True)
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert torch.equal(x, y)
