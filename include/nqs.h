@@ -45,7 +45,8 @@
  * - The caller owns every buffer: params, inputs, outputs and the workspace
  *   (size from nqs_workspace_bytes, 256-byte aligned).  Pointers named
  *   "device" must be device (or managed) memory of the current device.
- *   The library allocates no memory.
+ *   params and hcache are accessed in 16-byte pieces and must be 16-byte
+ *   aligned (NQS_EINVAL otherwise).  The library allocates no memory.
  * - Every call only enqueues work on `stream` (a cudaStream_t; NULL is the
  *   legacy default stream) and returns; results are ready when the stream is.
  * - Arguments are checked on the host before anything is enqueued; a bad
@@ -256,6 +257,13 @@ nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const float* para
  * before capturing a graph.  on = 0 turns tuning off and clears the cache
  * (the first variant is then used). */
 void nqs_set_autotune(int on);
+
+/* Pin the tile variant of every tensor-core kernel: variant >= 0 selects
+ * that variant (a kernel with fewer variants takes its last one), bypassing
+ * the autotuner and its cache; variant < 0 returns to normal selection.
+ * Variants differ only in threads per row (1, 2, 4) and compute bitwise the
+ * same results; this is for timing and testing them one by one. */
+void nqs_set_tile_variant(int variant);
 
 /* Copy the workspace status word to *device_status (an nqs_status) after
  * waiting for `stream`; clears it.  This call blocks the host. */

@@ -112,6 +112,9 @@ Layout layout(const Dims& d, int64_t B, int op) {
   return L;
 }
 
+// params and hcache are read (and hcache written) in 16-byte pieces
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
 nqs_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
   if (!ws) return NQS_EWORKSPACE;
   if (reinterpret_cast<uintptr_t>(ws) % 256) return NQS_EWORKSPACE;
@@ -137,6 +140,7 @@ T* at(void* ws, size_t off) {
 extern "C" {
 
 void nqs_set_autotune(int on) { tc1d_set_autotune(on); }
+void nqs_set_tile_variant(int variant) { tc1d_set_variant(variant); }
 
 size_t nqs_param_count(const nqs_model_desc* desc) {
   Dims d;
@@ -203,7 +207,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   if (r != NQS_OK) return r;
   if ((r = check_built(d)) != NQS_OK) return r;
   if (B < 0) return NQS_EINVAL;
-  if (!params) return NQS_EINVAL;
+  if (!params || misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
   const Layout L = layout(d, B, sample ? NQS_OP_SAMPLE : NQS_OP_LOGPSI);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   if (B == 0) return NQS_OK;  // empty batch: outputs are empty, pointers may be null
@@ -284,6 +288,7 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if ((r = check_built(d)) != NQS_OK) return r;
   if (!ham || !params || B < 0) return NQS_EINVAL;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
+  if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
   if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return NQS_EINVAL;
   if (ham->kind == NQS_TFIM && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
   if (ham->kind == NQS_HEISENBERG && d.cell != NQS_GRU2D) return NQS_EUNSUPPORTED;
@@ -369,7 +374,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     uint8_t* wt = at<uint8_t>(ws, L.w2);
     const int rows = tc1d_bptt_partial_rows(B);
     if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (tc1d_pack_w3(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
     TcBpttArgs t{};
@@ -432,6 +437,7 @@ nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params, cons
   if ((r = check_built(d)) != NQS_OK) return r;
   if (!params || !grad || B < 0) return NQS_EINVAL;
   if (B > 0 && (!sigma || !hcache || !weights)) return NQS_EINVAL;
+  if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
   const Layout L = layout(d, B, NQS_OP_LOGPSI_GRAD);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -448,6 +454,7 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const u
   if (r != NQS_OK) return r;
   if ((r = check_built(d)) != NQS_OK) return r;
   if (!params || !sigma || !hcache || !eloc || !grad || !stats || B < 1) return NQS_EINVAL;
+  if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
   const Layout L = layout(d, B, NQS_OP_VMC_GRAD);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -515,6 +522,7 @@ nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, u
   for (int i = 0; i < R; ++i) {
     const nqs_replica& p = reps[i];
     if (!p.params || !p.sigma || !p.logpsi || !p.hcache || !p.eloc || !p.grad || !p.stats) return NQS_EINVAL;
+    if (misaligned(p.params) || misaligned(p.hcache)) return NQS_EINVAL;
   }
   const BatchLayout L = batch_layout(R, reps, dims);
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < L.total) return NQS_EWORKSPACE;

@@ -128,18 +128,8 @@ __global__ void __launch_bounds__(kFwdNT) grouped_sample_kernel(RepTable t) {
 // Logit differences of every cached state (one warp per (sample, site)).
 __global__ void grouped_readout_kernel(RepTable t) {
   const Rep& r = t.r[blockIdx.y];
-  const int D = r.d;
-  const float* Us = r.img + 10 * D;
-  const float dc = r.img[12 * D] - r.img[12 * D + 1];
-  const int lane = threadIdx.x & 31;
-  const int64_t rows = r.B * r.N;
-  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < rows;
-       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    float z = 0.0f;
-    for (int u = lane; u < D; u += 32) z = fmaf(Us[u] - Us[D + u], r.hcache[q * D + u], z);
-    z = group_sum<32>(z);
-    if (lane == 0) r.dlog[q] = z + dc;
-  }
+  dlog_rows(r.img, r.hcache, r.dlog, r.B * r.N, r.d, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+            ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 __global__ void __launch_bounds__(kChainNT) grouped_chains_kernel(RepTable t) {

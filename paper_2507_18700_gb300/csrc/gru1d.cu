@@ -42,16 +42,8 @@ __global__ void pack1d_kernel(const float* __restrict__ p, float* __restrict__ i
 // ----------------------------------------------------------------------------
 __global__ void readout1d_kernel(const float* __restrict__ img, const float* __restrict__ hcache,
                                  float* __restrict__ dlog, int64_t rows, int D) {
-  const float* Us = img + 10 * D;
-  const float dc = img[12 * D] - img[12 * D + 1];
-  const int lane = threadIdx.x & 31;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
-       r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    float z = 0.0f;
-    for (int u = lane; u < D; u += 32) z = fmaf(Us[u] - Us[D + u], hcache[r * D + u], z);
-    z = group_sum<32>(z);
-    if (lane == 0) dlog[r] = z + dc;
-  }
+  dlog_rows(img, hcache, dlog, rows, D, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+            ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // E_loc = -J sum s_i s_{i+1} - Gamma sum_i exp(Delta_i); one warp per sample.
@@ -235,9 +227,9 @@ cudaError_t gru1d_forward(const Fwd1Args& a, const float* img, int D, bool sampl
 
 cudaError_t gru1d_readout(const float* img, const float* hcache, float* dlog, int64_t rows, int D,
                           cudaStream_t st) {
-  const int64_t warps = rows;
-  int64_t blocks = (warps * 32 + 255) / 256;
-  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  // a grid of a few waves over the SMs; warps stride over row groups
+  int64_t blocks = (rows * (D / 4) + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   readout1d_kernel<<<(unsigned)blocks, 256, 0, st>>>(img, hcache, dlog, rows, D);
   return cudaGetLastError();

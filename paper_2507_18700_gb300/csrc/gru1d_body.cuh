@@ -496,4 +496,30 @@ __device__ __forceinline__ void gru1d_bptt_body(const float* __restrict__ img, c
 }
 
 
+// Readout logit difference of cached states, dlog[r] = (U_0 - U_1) h_r + c_0 - c_1,
+// for rows r = w * RPW + sub, w = warp0, warp0 + nwarps, ...: G = D / 4 lanes
+// per row (one float4 each, D <= 128), RPW = 32 / G rows per warp pass, the
+// G products summed by a fixed xor tree.
+__device__ __forceinline__ void dlog_rows(const float* __restrict__ img, const float* __restrict__ hcache,
+                                          float* __restrict__ dlog, int64_t rows, int D, int64_t warp0,
+                                          int64_t nwarps) {
+  const int lane = threadIdx.x & 31;
+  const int G = D / 4, RPW = 32 / G, sub = lane / G, q = lane % G;
+  const float4 u0 = reinterpret_cast<const float4*>(img + 10 * D)[q];
+  const float4 u1 = reinterpret_cast<const float4*>(img + 11 * D)[q];
+  const float4 du = make_float4(u0.x - u1.x, u0.y - u1.y, u0.z - u1.z, u0.w - u1.w);
+  const float dc = img[12 * D] - img[12 * D + 1];
+#pragma unroll 4
+  for (int64_t base = warp0 * RPW; base < rows; base += nwarps * RPW) {
+    const int64_t r = base + sub;
+    float z = 0.0f;
+    if (r < rows) {
+      const float4 h = reinterpret_cast<const float4*>(hcache + r * D)[q];
+      z = fmaf(du.x, h.x, fmaf(du.y, h.y, fmaf(du.z, h.z, du.w * h.w)));
+    }
+    for (int off = G / 2; off > 0; off >>= 1) z += __shfl_xor_sync(0xffffffffu, z, off);
+    if (r < rows && q == 0) dlog[r] = z + dc;
+  }
+}
+
 }  // namespace nqs

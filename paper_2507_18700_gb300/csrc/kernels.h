@@ -125,9 +125,9 @@ struct TcBpttArgs {
 
 int tc1d_supported(int D);
 void tc1d_set_autotune(int on);
+void tc1d_set_variant(int v);
 int tc1d_bptt_partial_rows(int64_t B);
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st);
-cudaError_t tc1d_pack_w3(const float* params, uint8_t* w3, int D, cudaStream_t st);  // 3D x D, <= tc1d_wimg_bytes
 cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, int D,
                       cudaStream_t st);
 size_t tc1d_wimg_bytes(int D);

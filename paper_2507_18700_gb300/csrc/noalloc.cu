@@ -52,6 +52,7 @@ extern "C" nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const 
   const int D = desc->d_h, N = desc->Lx;
   if (N < 1 || !gru1d_supported(D)) return NQS_ESHAPE;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(hcache)) & 15) return NQS_EINVAL;
   // scratch layout: [header | packed weights | dlog B*N | delta B*N]
   const size_t img_off = sizeof(WsHeader);
   const size_t dlog_off = img_off + align256(gru1d_img_floats(D) * sizeof(float));

@@ -42,11 +42,29 @@ __global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double*
 }
 
 // grad[p] = sum_r partial[r][p], accumulated in FP64 in a fixed order.
-__global__ void reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
-                                       float* __restrict__ grad) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += (double)partial[(size_t)r * P + p];
+// A block sums 32 columns: 8 row groups (r = g mod 8) per column, each with
+// 4 independent FP64 accumulators, then the 8 group sums in a fixed tree.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
+                                                              float* __restrict__ grad) {
+  __shared__ double red[8][33];
+  const int col = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + col;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (p < P) {
+    int r = g;
+    for (; r + 24 < rows; r += 32) {
+      a0 += (double)partial[(size_t)r * P + p];
+      a1 += (double)partial[(size_t)(r + 8) * P + p];
+      a2 += (double)partial[(size_t)(r + 16) * P + p];
+      a3 += (double)partial[(size_t)(r + 24) * P + p];
+    }
+    for (; r < rows; r += 8) a0 += (double)partial[(size_t)r * P + p];
+  }
+  red[g][col] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (g == 0 && p < P) {
+    const double s = ((red[0][col] + red[1][col]) + (red[2][col] + red[3][col])) +
+                     ((red[4][col] + red[5][col]) + (red[6][col] + red[7][col]));
     grad[p] = (float)s;
   }
 }
@@ -65,9 +83,8 @@ cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float
 }
 
 cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
-  int blocks = (P + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
+  const int blocks = (P + 31) / 32;
+  if (blocks < 1) return cudaSuccess;
   reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, rows, P, grad);
   return cudaGetLastError();
 }

@@ -139,6 +139,10 @@ __device__ __forceinline__ bool group_barrier_or(bool v, uint32_t id, uint32_t c
 __device__ __forceinline__ void group_barrier(uint32_t id, uint32_t count) {
   asm volatile("barrier.cta.sync %0, %1;\n" : : "r"(id), "r"(count) : "memory");
 }
+// Arrive on barrier `id` without waiting (the producer side of a hand-off).
+__device__ __forceinline__ void group_arrive(uint32_t id, uint32_t count) {
+  asm volatile("barrier.cta.arrive %0, %1;\n" : : "r"(id), "r"(count) : "memory");
+}
 
 }  // namespace tc
 }  // namespace nqs

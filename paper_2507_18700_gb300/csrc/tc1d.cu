@@ -32,7 +32,8 @@ constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before giving up (
 // [h | 1 | 1 | onehot(s) | onehot(s) | 0] the four row blocks give
 //   a_u = W_g [h; s] + b_g,  a_r = W_r [h; s] + b_r,  q = W_h h + b_h,
 //   x_in = W_in s + b_in,
-// so the epilogue needs no bias or input terms.
+// so the epilogue needs no bias or input terms.  The u and r rows are scaled
+// by 1/2 (exact in BF16), so each sigmoid gate is one tanh and one FMA.
 __device__ __forceinline__ float bf16_hi(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 __global__ void pack1d_tc_kernel(const float* __restrict__ p, uint8_t* __restrict__ wimg, int D) {
@@ -60,19 +61,8 @@ __global__ void pack1d_tc_kernel(const float* __restrict__ p, uint8_t* __restric
       const float x = e < 2 ? bias : (e == 2 || e == 4) ? w0 : w1;
       v = e < 2 ? (e == 0 ? bf16_hi(x) : x - bf16_hi(x)) : (e < 4 ? bf16_hi(x) : x - bf16_hi(x));
     }
+    if (g < 2) v *= 0.5f;   // u, r rows hold half the pre-activation: sigmoid(x) = (1 + tanh(x / 2)) / 2
     *reinterpret_cast<__nv_bfloat16*>(wimg + tc::kmajor_offset(n, k, KA)) = __float2bfloat16_rn(v);
-  }
-}
-
-// Gate weights without biases, [3D rows (gate, unit) x D] K-major: the A-side
-// operand of the reverse sweep's recompute GEMM.
-__global__ void pack1d_tc_w3_kernel(const float* __restrict__ p, uint8_t* __restrict__ wimg, int D) {
-  const int total = 3 * D * D;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-    const int n = t / D, k = t % D, g = n / D, u = n % D;
-    const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2);
-    const float v = g == 0 ? p[Wg + u * (D + 2) + k] : g == 1 ? p[Wr + u * (D + 2) + k] : p[Wh + u * D + k];
-    *reinterpret_cast<__nv_bfloat16*>(wimg + tc::kmajor_offset(n, k, D)) = __float2bfloat16_rn(v);
   }
 }
 
@@ -83,6 +73,48 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk (TMA engine) global -> shared copy of `bytes` (multiple of 16, both
+// addresses 16-byte aligned) that completes on an mbarrier, after this
+// thread's arrival announcing the bytes; and a plain arrival.
+__device__ __forceinline__ void bulk_load_arrive(void* smem, const void* gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" : : "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               :
+               : "r"(tc::smem_addr(smem)), "l"(gmem), "r"(bytes), "r"(tc::smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
+}
+
+// 8 consecutive TMEM columns of this thread's lane, and the wait that makes
+// them usable: the empty asm statements after the wait tie every loaded
+// register to it, so no use of the values can be scheduled above the wait.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+// Shared-memory vector load kept inside the loop (a loop-invariant load of
+// the readout weights would otherwise be hoisted into registers and spill).
+__device__ __forceinline__ float4 lds4(const float* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(tc::smem_addr(p)));
+  return v;
+}
+__device__ __forceinline__ void tmem_wait_regs(float (&v)[4][8]) {
+  tc::tmem_wait_ld();
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) asm volatile("" : "+f"(v[b][q]));
+}
+
 // Gate nonlinearities of the BF16 path: one hardware tanh (MUFU.TANH,
 // relative error ~2^-11, below the 2^-9 rounding of the BF16 GEMM operands)
 // per gate; sigmoid(x) = (1 + tanh(x/2)) / 2.
@@ -91,8 +123,6 @@ __device__ __forceinline__ float hw_tanh(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float fast_sigmoid(float x) { return fmaf(0.5f, hw_tanh(0.5f * x), 0.5f); }
-__device__ __forceinline__ float fast_tanh(float x) { return hw_tanh(x); }
 
 // Shared-memory carve-up (bytes from a 1024-aligned base).
 template <int D, int GROUPS, int SPLIT>
@@ -106,7 +136,8 @@ struct Smem {
   static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x D floats (next chain state)
   static constexpr int kBar = (kStage + GROUPS * 128 * D * 4 + 15) / 16 * 16;
   static constexpr int kSlot = kBar + 8 * GROUPS;
-  static constexpr int kUsed = kSlot + 16;
+  static constexpr int kFlags = kSlot + 16;                      // ping-pong idle flags, one int per tile
+  static constexpr int kUsed = kFlags + 16;
   // one CTA per SM for the persistent chain launch (TMEM holds two tiles)
   static constexpr int kBytes = 1024 + (GROUPS == 2 ? (kUsed > 120 * 1024 ? kUsed : 120 * 1024) : kUsed);
 };
@@ -132,6 +163,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   float* stage = reinterpret_cast<float*>(sm + S::kStage);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  volatile int* idle_flag = reinterpret_cast<volatile int*>(sm + S::kFlags);
 
   // ---- prologue: operands and constants into shared memory, TMEM, barriers ----
   for (int i = threadIdx.x; i < N4 * KA * 2 / 16; i += NT)
@@ -143,6 +175,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     for (int g = 0; g < GROUPS; ++g) tc::mbar_init(&mbar[g], 1);
     tc::mbar_fence_init();
   }
+  if (threadIdx.x < 2) idle_flag[threadIdx.x] = 0;
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, GROUPS == 2 ? 512 : 256);
   tc::fence_before_sync();
   __syncthreads();
@@ -186,7 +219,9 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
         if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(mask));
         base = __shfl_sync(0xffffffffu, base, leader);
         const unsigned long long jj = base + __popc(mask & ((1u << lane) - 1u));
-        if (need && jj < total) j = (long long)jj;
+        if constexpr (MODE == 2) {
+          if (need && jj < total) j = (long long)jj;
+        }
       }
       if (need) jb[m] = j;
     }
@@ -225,6 +260,18 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     active = b < B;
   }
 
+  // Ping-pong (two tiles): the tiles take turns in the MUFU-bound epilogue,
+  // so one tile's MMA and row logic run under the other's epilogue.  Tile g
+  // waits for the other tile's token (named barrier) before its epilogue and
+  // passes its own token after it: E0(0), E1(0), E0(1), E1(1), ...  Each token
+  // carries the sender's idle flag (no active rows, permanent); a tile that
+  // is idle keeps taking turns without work until both are idle, and the
+  // exit rule below leaves no token unconsumed.
+  constexpr bool PP = GROUPS == 2;
+  const uint32_t pp_wait = g == 0 ? 6 : 5, pp_sig = g == 0 ? 5 : 6;
+  bool prev_idle = false;      // the idle flag this tile sent with its last token
+  int pstep = 0;
+
   uint32_t phase = 0;
   bool timed_out = false;
   for (;;) {
@@ -257,10 +304,10 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     tc::fence_async_smem();
     tc::fence_before_sync();
     const bool any = tc::group_barrier_or(active && !timed_out, bar_main, TT);
-    if (!any) break;
+    if (!PP && !any) break;
     tc::fence_after_sync();
     // ---- (b) one thread issues the tile's MMAs ----
-    if (tt == 0) {
+    if (any && tt == 0) {
       constexpr uint32_t idesc = tc::make_idesc_bf16(128, N4);
 #pragma unroll
       for (int k = 0; k < KA / 16; ++k) {
@@ -282,38 +329,102 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       }
     }
     // ---- (d) wait for the accumulator ----
-    if (!tc::mbar_wait(&mbar[g], phase, kWaitLimit)) {
-      timed_out = true;
-      flag_status(a.hdr, NQS_ETIMEOUT);
+    if (any) {
+      if (!tc::mbar_wait(&mbar[g], phase, kWaitLimit)) {
+        timed_out = true;
+        flag_status(a.hdr, NQS_ETIMEOUT);
+      }
+      phase ^= 1;
+      tc::fence_after_sync();
     }
-    phase ^= 1;
-    tc::fence_after_sync();
+    // the first accumulator columns are loaded before the hand-off wait
+    float bufA[4][8], bufB[4][8];
+    auto issue = [&](int sc, float (&bf)[4][8]) {
+      const int cu = u0 + sc * 8;
+      tmem_ld8(trow + cu, bf[0]);
+      tmem_ld8(trow + D + cu, bf[1]);
+      tmem_ld8(trow + 2 * D + cu, bf[2]);
+      tmem_ld8(trow + 3 * D + cu, bf[3]);
+    };
+    if (any) issue(0, bufA);
+    if constexpr (PP) {
+      bool oth = false;        // the other tile's idle flag from its last token
+      if (g == 1 || pstep > 0) {
+        tc::group_barrier(pp_wait, 2 * TT);
+        oth = idle_flag[1 - g] != 0;
+      }
+      // both idle and the other tile saw this tile idle: it has left, no token
+      if (oth && prev_idle) break;
+      // both idle: the other tile waits for one more token, then leaves
+      if (!any && oth) {
+        if (tt == 0) idle_flag[g] = 1;
+        tc::group_arrive(pp_sig, 2 * TT);
+        break;
+      }
+    }
     // ---- (e) gates and FP32 state update of this thread's units ----
-    // readout: sequential sums over 16-unit chunks, chunks combined by a fixed
-    // pairwise tree, so every SPLIT gives bitwise the same logits
+    // Accumulator columns come in 8-unit sub-chunks, double-buffered, and the
+    // gate math is software-pipelined: the u / r gates of sub-chunk c + 1
+    // (stage A) are computed together with the candidate and state update of
+    // sub-chunk c (stage B), so the MUFU always has independent work.
+    // Readout: sequential sums over 16-unit chunks, chunks combined by a fixed
+    // pairwise tree, so every SPLIT gives bitwise the same logits.
     float zc0[DU / 16], zc1[DU / 16];
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      float au[16], ar[16], aq[16], ai[16];
-      const int cu = u0 + c * 16;
-      tc::tmem_ld16(trow + cu, au);
-      tc::tmem_ld16(trow + D + cu, ar);
-      tc::tmem_ld16(trow + 2 * D + cu, aq);
-      tc::tmem_ld16(trow + 3 * D + cu, ai);
-      tc::tmem_wait_ld();
+    for (int c = 0; c < DU / 16; ++c) zc0[c] = zc1[c] = 0.0f;
+    if (any) {
+      constexpr int NS = DU / 8;
+      // stage A: tu = tanh(a_u / 2 pre-scaled), ag = r * q + x_in
+      auto stage_a = [&](float (&bf)[4][8], float (&tu)[8], float (&ag)[8]) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          tu[q] = hw_tanh(bf[0][q]);
+          const float rg = fmaf(0.5f, hw_tanh(bf[1][q]), 0.5f);
+          ag[q] = fmaf(rg, bf[2][q], bf[3][q]);
+        }
+      };
+      float tuA[8], agA[8], tuB[8], agB[8];
+      tmem_wait_regs(bufA);
+      if (NS > 1) issue(1, bufB);
+      stage_a(bufA, tuA, agA);
       float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int u = cu + q, j = c * 16 + q;
-        const float ug = fast_sigmoid(au[q]);
-        const float rg = fast_sigmoid(ar[q]);
-        const float cc = fast_tanh(fmaf(rg, aq[q], ai[q]));
-        h[j] = fmaf(ug, cc - h[j], h[j]);
-        s0 = fmaf(Us[u], h[j], s0);
-        s1 = fmaf(Us[D + u], h[j], s1);
+      for (int sc = 0; sc < NS; ++sc) {
+        float (&tu)[8] = (sc & 1) ? tuB : tuA;
+        float (&ag)[8] = (sc & 1) ? agB : agA;
+        if (sc + 1 < NS) {
+          float (&nb)[4][8] = ((sc + 1) & 1) ? bufB : bufA;
+          float (&fb)[4][8] = ((sc + 1) & 1) ? bufA : bufB;   // consumed by stage A of sc
+          tmem_wait_regs(nb);
+          if (sc + 2 < NS) issue(sc + 2, fb);
+          stage_a(nb, (sc & 1) ? tuA : tuB, (sc & 1) ? agA : agB);
+        }
+        float U0[8], U1[8];
+        {
+          const float* up = Us + u0 + sc * 8;
+          const float4 a0 = lds4(up), a1 = lds4(up + 4), b0 = lds4(up + D), b1 = lds4(up + D + 4);
+          U0[0] = a0.x; U0[1] = a0.y; U0[2] = a0.z; U0[3] = a0.w;
+          U0[4] = a1.x; U0[5] = a1.y; U0[6] = a1.z; U0[7] = a1.w;
+          U1[0] = b0.x; U1[1] = b0.y; U1[2] = b0.z; U1[3] = b0.w;
+          U1[4] = b1.x; U1[5] = b1.y; U1[6] = b1.z; U1[7] = b1.w;
+        }
+        // stage B
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = sc * 8 + q;
+          const float cc = hw_tanh(ag[q]);
+          const float ug = fmaf(0.5f, tu[q], 0.5f);
+          h[j] = fmaf(ug, cc - h[j], h[j]);
+          s0 = fmaf(U0[q], h[j], s0);
+          s1 = fmaf(U1[q], h[j], s1);
+        }
+        if (sc & 1) {
+          zc0[sc / 2] = s0;
+          zc1[sc / 2] = s1;
+          s0 = 0.0f;
+          s1 = 0.0f;
+        }
       }
-      zc0[c] = s0;
-      zc1[c] = s1;
     }
 #pragma unroll
     for (int w = 1; w < DU / 16; w *= 2)
@@ -323,6 +434,11 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
         zc1[c] += zc1[c + w];
       }
     float z0 = zc0[0], z1 = zc1[0];
+    if constexpr (PP) {
+      if (tt == 0) idle_flag[g] = any ? 0 : 1;
+      tc::group_arrive(pp_sig, 2 * TT);
+      prev_idle = !any;
+    }
     if constexpr (SPLIT > 1) {
       zb[(part * 128 + m) * 2] = z0;
       zb[(part * 128 + m) * 2 + 1] = z1;
@@ -413,6 +529,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     } else if constexpr (SPLIT > 1) {
       tc::group_barrier(bar_x, TT);   // zbuf is rewritten next step
     }
+    ++pstep;
   }
   cp_async_wait_all();
   // ---- epilogue: free TMEM once both tiles are done ----
@@ -424,36 +541,46 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
 
 // ----------------------------------------------------------------------------
 // Reverse sweep on the tensor cores.  One CTA = one tile of 128 samples, one
-// thread per sample; sites n = N-1 .. 0.  Per site:
-//   X  = [h_{n-1} | 1 | onehot(s_{n-1}) | 0]  (BF16, 80 columns, row per sample)
-//   MMA_f: acc_f = X[:, :D] W3^T            recompute the gate pre-activations
-//   epilogue: gates, h_n, readout, dz = c_b (onehot - softmax), dh, and
-//             G = [du_a | dr_a | dq | dc_a]  (BF16, 4D columns)
-//   MMA_b: acc_b = G[:, :3D] W3               (dh_{n-1} through the gates)
-//   MMA_w: acc_w += G^T X                     (weight, bias and one-hot-column
-//                                              gradients; G and X read as
-//                                              MN-major operands)
-//   carry = dh direct + acc_b.
-// acc_w stays in TMEM for the whole sweep; readout gradients (U, c) come from
-// dz written per (sample, site) and are reduced by a separate kernel.
+// row per sample (SPLIT threads per row, each on D / SPLIT units); sites
+// n = N-1 .. 0.  Per site:
+//   readout: logits of h_n taken from the forward cache (the exact FP32 state
+//            the forward pass read out, summed in the same order), giving
+//            dz_n = c_b (onehot(s_n) - softmax);
+//   X     = [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0]  (BF16, D + 16 columns)
+//   MMA_f: acc_f = X Wf^T with the engine's folded weights (4D columns: the
+//          u / r / q / x_in pre-activations, bitwise those of the forward);
+//   epilogue: gates, backward through the cell, G = [du_a | dr_a | dq | dc_a];
+//   MMA_b: acc_b = G[:, :3D] W3            (dh_{n-1} through the gates)
+//   MMA_w: acc_w += G^T X                  (weight, bias and one-hot-column
+//                                           gradients; G and X MN-major)
+//   carry = dh_n (1 - u) + acc_b.
+// The cached states h_{n-1} (MMA operand, cell backward) and h_n (readout)
+// sit in two shared-memory row buffers; the state two sites back is copied
+// in with cp.async while the current site runs.  acc_w stays in TMEM for the
+// whole sweep; readout gradients (U, c) come from dz and are reduced by a
+// separate kernel.
 // ----------------------------------------------------------------------------
-constexpr int kXCols = 80;
-
-template <int D>
+template <int D, int SPLIT>
 struct BSmem {
+  static constexpr int KA = D + 16;                       // X columns
   static constexpr int GW = 4 * D >= 128 ? 4 * D : 128;  // G row width (>= one M = 128 operand)
-  static constexpr int kW3 = 0;                         // [3D x D] bf16, K-major
-  static constexpr int kWt = kW3 + 3 * D * D * 2;       // [D x 3D] bf16, K-major
-  static constexpr int kX = kWt + 3 * D * D * 2;        // [128 x 80] bf16
-  static constexpr int kG = kX + 128 * kXCols * 2;      // [128 x GW] bf16
-  static constexpr int kSmall = kG + 128 * GW * 2;      // 12D + 4 floats
-  static constexpr int kZ = kSmall + (12 * D + 4) * 4;  // 4 x 128 x 2 floats (readout exchange)
-  static constexpr int kBar = (kZ + 4 * 128 * 2 * 4 + 15) / 16 * 16;
-  static constexpr int kSlot = kBar + 16;
+  static constexpr int kWf = 0;                           // [4D x KA] bf16, K-major (folded)
+  static constexpr int kWt = kWf + 4 * D * KA * 2;        // [D x 3D] bf16, K-major
+  static constexpr int kX = kWt + 3 * D * D * 2;          // [128 x KA] bf16
+  static constexpr int kG = kX + 128 * KA * 2;            // [128 x GW] bf16
+  static constexpr int HS = D + 4;                        // state row stride (floats): 16-byte
+                                                          // loads of 8 consecutive rows hit distinct banks
+  static constexpr int kH = kG + 128 * GW * 2;            // 2 x [128 x HS] f32 state rows
+  static constexpr int kSmall = kH + 2 * 128 * HS * 4;    // 12D + 4 floats
+  static constexpr int kDU = kSmall + (12 * D + 4) * 4;   // D floats: U[0] - U[1]
+  static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 x 2 floats (readout exchange)
+  static constexpr int kBar = (kZ + SPLIT * 128 * 2 * 4 + 15) / 16 * 16;   // 4 mbarriers
+  static constexpr int kSlot = kBar + 32;
   static constexpr int kBytes = 1024 + kSlot + 16;
   // TMEM columns
-  static constexpr int cF = 0, cB = 3 * D, cW0 = 3 * D + D, cW1 = cW0 + kXCols;
-  static_assert(cW1 + kXCols <= 512, "TMEM budget");
+  static constexpr int cF = 0, cB = 4 * D, cW0 = 5 * D, cW1 = cW0 + KA;
+  static_assert(cW1 + KA <= 512, "TMEM budget");
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
 };
 
 __device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
@@ -469,35 +596,48 @@ __device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
   *reinterpret_cast<uint4*>(dst) = q;
 }
 
+// Spin byte load kept in place (issued one site ahead of its use).
+__device__ __forceinline__ uint32_t ldg_u8(const uint8_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.u8 %0, [%1];\n" : "=r"(v) : "l"(p));
+  return v;
+}
+
 template <int D, int SPLIT>
 __global__ void __launch_bounds__(128 * SPLIT, 1)
-tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3img, const uint8_t* __restrict__ wtimg,
+tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfimg, const uint8_t* __restrict__ wtimg,
                  TcBpttArgs a) {
-  using S = BSmem<D>;
+  using S = BSmem<D, SPLIT>;
   constexpr int NT = 128 * SPLIT;
+  constexpr int KA = S::KA;
   constexpr int DU = D / SPLIT;            // hidden units per thread
   static_assert(DU % 16 == 0, "at least 16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
-  uint8_t* sW3 = sm + S::kW3;
+  uint8_t* sWf = sm + S::kWf;
   uint8_t* sWt = sm + S::kWt;
   uint8_t* sX = sm + S::kX;
   uint8_t* sG = sm + S::kG;
+  float* sH = reinterpret_cast<float*>(sm + S::kH);
   float* small = reinterpret_cast<float*>(sm + S::kSmall);
+  float* dU = reinterpret_cast<float*>(sm + S::kDU);
   float* zb = reinterpret_cast<float*>(sm + S::kZ);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
-  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += NT) {
-    reinterpret_cast<uint4*>(sW3)[i] = reinterpret_cast<const uint4*>(w3img)[i];
+  for (int i = threadIdx.x; i < 4 * D * KA * 2 / 16; i += NT)
+    reinterpret_cast<uint4*>(sWf)[i] = reinterpret_cast<const uint4*>(wfimg)[i];
+  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sWt)[i] = reinterpret_cast<const uint4*>(wtimg)[i];
-  }
   for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += NT)
     reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
+  for (int i = threadIdx.x; i < D; i += NT) dU[i] = img[10 * D + i] - img[11 * D + i];
   for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += NT) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&mbar[2], NT);     // state row buffer 0 filled (every thread arrives)
+    tc::mbar_init(&mbar[3], NT);     // state row buffer 1 filled
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -510,99 +650,84 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
   const int u0 = part * DU;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
-  const float* Ws = small;
-  const float* Bs = small + 6 * D;
   const float* Us = small + 10 * D;
   const float c0 = small[12 * D], c1 = small[12 * D + 1];
   const int N = a.N;
   const int64_t b = (int64_t)blockIdx.x * 128 + m;
   const bool valid = b < a.B;
   const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+  // this thread's units of the two state rows
+  float* hrow[2] = {sH + (0 * 128 + m) * S::HS + u0, sH + (1 * 128 + m) * S::HS + u0};
+  bool timed_out = false;
+  // copy h_n of this sample (zero for n < 0 or past the batch) into row buffer
+  // k: one bulk copy per thread (its units of the row), completing on mbar[2 + k]
+  bool inflight[2] = {false, false};   // a fill of the buffer not yet waited for
+  auto fetch = [&](int n, int k) {
+    inflight[k] = true;
+    if (valid && n >= 0) {
+      tc::fence_async_smem();        // this thread's reads of the buffer come first
+      bulk_load_arrive(hrow[k], a.hcache + (b * N + n) * D + u0, DU * 4, &mbar[2 + k]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < DU / 4; ++q) reinterpret_cast<float4*>(hrow[k])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      mbar_arrive(&mbar[2 + k]);
+    }
+  };
+  uint32_t ph_h[2] = {0, 0};
+  auto wait_rows = [&](int k) {
+    if (!tc::mbar_wait(&mbar[2 + k], ph_h[k], kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    ph_h[k] ^= 1;
+    inflight[k] = false;
+  };
   float carry[DU];
 #pragma unroll
   for (int u = 0; u < DU; ++u) carry[u] = 0.0f;
   uint32_t ph_f = 0, ph_b = 0;
-  bool timed_out = false;
-  constexpr uint32_t idesc_f = tc::make_idesc_bf16(128, 3 * D);
+
+  constexpr uint32_t idesc_f = tc::make_idesc_bf16(128, 4 * D);
   constexpr uint32_t idesc_b = tc::make_idesc_bf16(128, D);
-  constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, kXCols) | (1u << 15) | (1u << 16);
-  // 16 values of h_{n-1} of this sample starting at unit u (zero at the first site / past the batch)
-  auto load_hp16 = [&](int n, int u, float (&v)[16]) {
-    if (valid && n > 0) {
-      const float4* src = reinterpret_cast<const float4*>(a.hcache + (b * N + n - 1) * D + u);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 t = src[q];
-        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.0f;
-    }
-  };
+  constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, KA) | (1u << 15) | (1u << 16);
+  // row buffers: cur = h_n, nxt = h_{n-1}
+  int cur = 0;
+  fetch(N - 1, 0);
+  fetch(N - 2, 1);
+  wait_rows(0);
+  uint32_t s_n = valid ? ldg_u8(a.sigma + b * N + N - 1) : 0u;
+  uint32_t s_p = (valid && N > 1) ? ldg_u8(a.sigma + b * N + N - 2) : 0u;
 
   for (int n = N - 1; n >= 0; --n) {
-    // ---- X row: [h_{n-1} | 1 | onehot(s_{n-1}) | 0] ----
-    int s_in = -1, s_n = 0;
-    if (valid) {
-      s_n = a.sigma[b * N + n] ? 1 : 0;
-      if (n > 0) s_in = a.sigma[b * N + n - 1] ? 1 : 0;
-    }
+    const int nxt = cur ^ 1;
+    wait_rows(nxt);
+    const float* hn = hrow[cur];
+    const float* hp = hrow[nxt];
+    // spin two sites back, for the next site's input
+    const uint32_t s_pp = (valid && n >= 2) ? ldg_u8(a.sigma + b * N + n - 2) : 0u;
+    const int s_in = n > 0 ? (s_p ? 1 : 0) : -1;
+    // ---- X row: [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0] ----
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      float hp[16];
-      load_hp16(n, u0 + 16 * c, hp);
-      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 16 * c, kXCols), hp);
-      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 16 * c + 8, kXCols), hp + 8);
+    for (int c = 0; c < DU / 8; ++c) {
+      float v[8];
+      const float4 x0 = reinterpret_cast<const float4*>(hp)[2 * c];
+      const float4 x1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w; v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 8 * c, KA), v);
     }
     if (part == 0) {
-      float ext[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) ext[q] = 0.0f;
-      ext[0] = 1.0f;
-      if (s_in >= 0) ext[1 + s_in] = 1.0f;
-      st_bf16x8(sX + tc::kmajor_offset(m, D, kXCols), ext);
-      st_bf16x8(sX + tc::kmajor_offset(m, D + 8, kXCols), ext + 8);
+      const uint32_t one = 0x3F80u;
+      const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
+      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
+      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
     }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < D / 16; ++k) {
-        const uint64_t da = tc::make_desc(tc::smem_addr(sX) + k * 256, 128, (kXCols / 8) * 128);
-        const uint64_t db = tc::make_desc(tc::smem_addr(sW3) + k * 256, 128, (D / 8) * 128);
-        tc::mma_bf16(tbase + S::cF, da, db, idesc_f, k > 0);
-      }
-      tc::mma_commit(&mbar[0]);
-    }
-    if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
-    ph_f ^= 1;
-    tc::fence_after_sync();
-    const float* Wsel = Ws + (s_in > 0 ? 3 * D : 0);
-    const float on = s_in >= 0 ? 1.0f : 0.0f;
-    // ---- pass 1: recompute h_n for the readout (chunk sums in a fixed tree) ----
+    // ---- readout of h_n: 16-unit chunk sums in order, chunks by a fixed tree ----
     float zc0[DU / 16], zc1[DU / 16];
 #pragma unroll
     for (int c = 0; c < DU / 16; ++c) {
-      float au[16], ar[16], ah[16], hp[16];
-      const int cu = u0 + 16 * c;
-      tc::tmem_ld16(trow + S::cF + cu, au);
-      tc::tmem_ld16(trow + S::cF + D + cu, ar);
-      tc::tmem_ld16(trow + S::cF + 2 * D + cu, ah);
-      load_hp16(n, cu, hp);
-      tc::tmem_wait_ld();
       float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int u = cu + q;
-        const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
-        const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
-        const float cg = fast_tanh(fmaf(rg, ah[q] + Bs[2 * D + u], Bs[3 * D + u] + on * Wsel[2 * D + u]));
-        const float hn = fmaf(ug, cg - hp[q], hp[q]);
-        s0 = fmaf(Us[u], hn, s0);
-        s1 = fmaf(Us[D + u], hn, s1);
+        const int j = 16 * c + q;
+        s0 = fmaf(Us[u0 + j], hn[j], s0);
+        s1 = fmaf(Us[D + u0 + j], hn[j], s1);
       }
       zc0[c] = s0;
       zc1[c] = s1;
@@ -614,11 +739,25 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
         zc0[c] += zc0[c + w];
         zc1[c] += zc1[c + w];
       }
+    if constexpr (SPLIT > 1) {
+      zb[(part * 128 + m) * 2] = zc0[0];
+      zb[(part * 128 + m) * 2 + 1] = zc1[0];
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < KA / 16; ++k) {
+        const uint64_t da = tc::make_desc(tc::smem_addr(sX) + k * 256, 128, (KA / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sWf) + k * 256, 128, (KA / 8) * 128);
+        tc::mma_bf16(tbase + S::cF, da, db, idesc_f, k > 0);
+      }
+      tc::mma_commit(&mbar[0]);
+    }
     float z0 = zc0[0], z1 = zc1[0];
     if constexpr (SPLIT > 1) {
-      zb[(part * 128 + m) * 2] = z0;
-      zb[(part * 128 + m) * 2 + 1] = z1;
-      __syncthreads();
       float p0[SPLIT], p1[SPLIT];
 #pragma unroll
       for (int p = 0; p < SPLIT; ++p) {
@@ -637,39 +776,54 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
     }
     const float d = (z0 + c0) - (z1 + c1);
     const float dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
+    // h_n is no longer needed: its buffer takes h_{n-2}.  (The copy's proxy
+    // fence comes before this site's global store, so it does not wait on it.)
+    if (n >= 1) fetch(n - 2, cur);
     if (valid && part == 0) a.dz[b * N + n] = dz0;
-    // ---- pass 2: gates again, backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
+    if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    ph_f ^= 1;
+    tc::fence_after_sync();
+    // ---- gates and backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
+    // accumulator columns in 8-unit sub-chunks, double-buffered (the loads of
+    // sub-chunk c + 1 are in flight while sub-chunk c is computed)
+    {
+      float bufA[4][8], bufB[4][8];
+      auto issue = [&](int c, float (&bf)[4][8]) {
+        const int cu = u0 + 8 * c;
+        tmem_ld8(trow + S::cF + cu, bf[0]);
+        tmem_ld8(trow + S::cF + D + cu, bf[1]);
+        tmem_ld8(trow + S::cF + 2 * D + cu, bf[2]);
+        tmem_ld8(trow + S::cF + 3 * D + cu, bf[3]);
+      };
+      issue(0, bufA);
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      float au[16], ar[16], ah[16], hp[16];
-      const int cu = u0 + 16 * c;
-      tc::tmem_ld16(trow + S::cF + cu, au);
-      tc::tmem_ld16(trow + S::cF + D + cu, ar);
-      tc::tmem_ld16(trow + S::cF + 2 * D + cu, ah);
-      load_hp16(n, cu, hp);
-      tc::tmem_wait_ld();
-      float gbuf[4][16];
+      for (int c = 0; c < DU / 8; ++c) {
+        float (&acc)[4][8] = (c & 1) ? bufB : bufA;
+        tmem_wait_regs(acc);
+        if (c + 1 < DU / 8) issue(c + 1, (c & 1) ? bufA : bufB);
+        const int cu = u0 + 8 * c;
+        float g0[8], g1[8], g2[8], g3[8];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int u = cu + q, j = 16 * c + q;
-        const float ug = fast_sigmoid(au[q] + Bs[u] + on * Wsel[u]);
-        const float rg = fast_sigmoid(ar[q] + Bs[D + u] + on * Wsel[D + u]);
-        const float qv = ah[q] + Bs[2 * D + u];
-        const float cg = fast_tanh(fmaf(rg, qv, Bs[3 * D + u] + on * Wsel[2 * D + u]));
-        const float dh = dz0 * (Us[u] - Us[D + u]) + carry[j];
-        const float dc = dh * ug;
-        const float du = dh * (cg - hp[q]);
-        carry[j] = dh * (1.0f - ug);                     // direct path; acc_b adds the rest
-        const float dac = dc * (1.0f - cg * cg);
-        gbuf[0][q] = du * ug * (1.0f - ug);
-        gbuf[1][q] = dac * qv * rg * (1.0f - rg);
-        gbuf[2][q] = dac * rg;
-        gbuf[3][q] = dac;
-      }
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        st_bf16x8(sG + tc::kmajor_offset(m, g * D + cu, S::GW), gbuf[g]);
-        st_bf16x8(sG + tc::kmajor_offset(m, g * D + cu + 8, S::GW), gbuf[g] + 8);
+        for (int q = 0; q < 8; ++q) {
+          const int j = 8 * c + q;
+          const float tu = hw_tanh(acc[0][q]), tr = hw_tanh(acc[1][q]);
+          const float ug = fmaf(0.5f, tu, 0.5f), rg = fmaf(0.5f, tr, 0.5f);
+          const float cg = hw_tanh(fmaf(rg, acc[2][q], acc[3][q]));
+          const float dh = fmaf(dz0, dU[cu + q], carry[j]);
+          const float dc = dh * ug;
+          const float du = dh * (cg - hp[j]);
+          carry[j] = dh - dc;                              // direct path; acc_b adds the rest
+          const float dac = dc * fmaf(-cg, cg, 1.0f);
+          g0[q] = du * (0.25f * fmaf(-tu, tu, 1.0f));      // u (1 - u) = (1 - tanh^2) / 4
+          const float dq = dac * rg;
+          g1[q] = dq * acc[2][q] * (0.5f - 0.5f * tr);     // dac q r (1 - r)
+          g2[q] = dq;
+          g3[q] = dac;
+        }
+        st_bf16x8(sG + tc::kmajor_offset(m, cu, S::GW), g0);
+        st_bf16x8(sG + tc::kmajor_offset(m, D + cu, S::GW), g1);
+        st_bf16x8(sG + tc::kmajor_offset(m, 2 * D + cu, S::GW), g2);
+        st_bf16x8(sG + tc::kmajor_offset(m, 3 * D + cu, S::GW), g3);
       }
     }
     tc::fence_async_smem();
@@ -694,7 +848,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
         for (int k = 0; k < 128 / 16; ++k) {
           const uint64_t da = tc::make_desc(tc::smem_addr(sG) + half * 16 * 128 + k * 2 * (S::GW / 8) * 128,
                                             (S::GW / 8) * 128, 128);
-          const uint64_t db = tc::make_desc(tc::smem_addr(sX) + k * 2 * (kXCols / 8) * 128, (kXCols / 8) * 128, 128);
+          const uint64_t db = tc::make_desc(tc::smem_addr(sX) + k * 2 * (KA / 8) * 128, (KA / 8) * 128, 128);
           tc::mma_bf16(tbase + (half ? S::cW1 : S::cW0), da, db, idesc_w, (n < N - 1) || k > 0);
         }
       }
@@ -703,17 +857,32 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
     if (!tc::mbar_wait(&mbar[1], ph_b, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
     ph_b ^= 1;
     tc::fence_after_sync();
+    {
+      // all of this thread's acc_b columns in one round trip
+      float v[DU / 8][8];
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      float v[16];
-      tc::tmem_ld16(trow + S::cB + u0 + 16 * c, v);
+      for (int c = 0; c < DU / 8; ++c) tmem_ld8(trow + S::cB + u0 + 8 * c, v[c]);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 16; ++q) carry[16 * c + q] += v[q];
+      for (int c = 0; c < DU / 8; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          asm volatile("" : "+f"(v[c][q]));
+          carry[8 * c + q] += v[c][q];
+        }
     }
+    s_n = s_p;
+    s_p = s_pp;
+    cur = nxt;
     if (timed_out) break;
   }
+  // after a timeout, let copies still in flight land before the CTA leaves
+  if (timed_out) {
+    for (int k = 0; k < 2; ++k)
+      if (inflight[k]) tc::mbar_wait(&mbar[2 + k], ph_h[k], kWaitLimit);
+  }
   // ---- this CTA's weight, bias and one-hot-column gradients from acc_w (part-0 warps) ----
+  // X columns: k < D: h; D: bias; D + 2, D + 3: one-hot weights (D + 1, D + 4 .. are duplicates / zero)
   const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2), Win = Wh + D * D;
   const int bg = Win + 2 * D, br = bg + D, bh = br + D, bin = bh + D;
   float* part_g = a.partial + (size_t)blockIdx.x * a.P;
@@ -723,7 +892,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
       const int gu = half * 128 + m;
       const int g = gu / D, u = gu % D;
 #pragma unroll 1
-      for (int c = 0; c < kXCols; c += 16) {
+      for (int c = 0; c < KA; c += 16) {
         float v[16];
         tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
         tc::tmem_wait_ld();
@@ -737,8 +906,8 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ w3im
             else if (g == 2) part_g[Wh + u * D + k] = v[q];
           } else if (k == D) {
             part_g[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[q];
-          } else if (k <= D + 2) {
-            const int s = k - D - 1;
+          } else if (k == D + 2 || k == D + 3) {
+            const int s = k - D - 2;
             if (g == 0) part_g[Wg + u * (D + 2) + D + s] = v[q];
             else if (g == 1) part_g[Wr + u * (D + 2) + D + s] = v[q];
             else if (g == 3) part_g[Win + u * 2 + s] = v[q];
@@ -770,6 +939,7 @@ __global__ void __launch_bounds__(256) tc1d_readout_grad_kernel(const float* __r
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   float accc = 0.0f;
   const int64_t stride = (int64_t)gridDim.x * 8 * RPW;
+#pragma unroll 4
   for (int64_t r = ((int64_t)blockIdx.x * 8 + warp) * RPW + sub; r < rows; r += stride) {
     if (sub >= RPW) break;
     const float z = dz[r];
@@ -861,6 +1031,7 @@ cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, c
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, long long>, int> g_tune;
 bool g_tune_on = true;
+int g_force = -1;            // >= 0: every kernel uses this variant (the last one it has if fewer)
 
 template <typename Launch, typename Prep>
 cudaError_t tuned_launch(int kind, int D, int N, int64_t B, int nvar, Launch launch, Prep prep, cudaStream_t st) {
@@ -868,8 +1039,12 @@ cudaError_t tuned_launch(int kind, int D, int N, int64_t B, int nvar, Launch lau
   int choice = -1;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tune.find(key);
-    if (it != g_tune.end()) choice = it->second;
+    if (g_force >= 0) {
+      choice = g_force < nvar ? g_force : nvar - 1;
+    } else {
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) choice = it->second;
+    }
   }
   cudaError_t e;
   if (choice < 0) {
@@ -940,13 +1115,18 @@ void tc1d_set_autotune(int on) {
   if (!on) g_tune.clear();
 }
 
+void tc1d_set_variant(int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_force = v < 0 ? -1 : v;
+}
+
 constexpr int kReadoutGradBlocks = 304;
 int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 127) / 128) + kReadoutGradBlocks; }
 
 template <int D, int SPLIT>
 cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt,
                              cudaStream_t st) {
-  using S = BSmem<D>;
+  using S = BSmem<D, SPLIT>;
   auto k = tc1d_bptt_kernel<D, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
@@ -969,12 +1149,6 @@ cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t*
   const int grid = (int)((a.B + 127) / 128);
   tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
                                                                    grid);
-  return cudaGetLastError();
-}
-
-cudaError_t tc1d_pack_w3(const float* params, uint8_t* w3, int D, cudaStream_t st) {
-  const int total = 3 * D * D;
-  pack1d_tc_w3_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, w3, D);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
-           "nqs_set_autotune"]
+           "nqs_set_autotune", "nqs_set_tile_variant"]
 
 
 class NqsError(RuntimeError):
@@ -108,6 +108,8 @@ def lib():
     L.nqs_vmc_step_batched.argtypes = [ctypes.c_int, P(Replica), u64, vp, vp, sz, vp]
     L.nqs_set_autotune.restype = None
     L.nqs_set_autotune.argtypes = [ctypes.c_int]
+    L.nqs_set_tile_variant.restype = None
+    L.nqs_set_tile_variant.argtypes = [ctypes.c_int]
     L.nqs_status_string.restype = ctypes.c_char_p
     L.nqs_status_string.argtypes = [ctypes.c_int]
     _lib = L
@@ -138,6 +140,11 @@ def _need(t, dtype, shape, name):
 def set_autotune(on):
     """Turn the tile-shape autotuner of the tensor-core kernels on or off."""
     lib().nqs_set_autotune(1 if on else 0)
+
+
+def set_tile_variant(variant):
+    """Pin the tile variant of the tensor-core kernels (None or < 0: normal selection)."""
+    lib().nqs_set_tile_variant(-1 if variant is None else int(variant))
 
 
 def param_count(desc):

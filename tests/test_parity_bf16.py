@@ -130,18 +130,22 @@ def test_bf16_reverse_sweep(N, d, B):
 
 
 def test_autotuned_variants_agree_bitwise():
-    """Every tile variant the autotuner may pick computes bitwise the same samples,
-    cache, local energies and gradient (tuning off = first variant)."""
+    """Every tile variant (1, 2 or 4 threads per row) computes bitwise the same
+    samples, cache, local energies and gradient, and so does the autotuned
+    choice (tuning off = first variant)."""
     N, d, B = 60, 64, 700
     desc, mod, pf, p = setup(N, d)
     outs = []
-    for on in (False, True, True):
-        nqs.set_autotune(on)
+    runs = [(None, False), (None, True), (None, True), (0, True), (1, True), (2, True)]
+    for variant, tune in runs:
+        nqs.set_autotune(tune)
+        nqs.set_tile_variant(variant)
         s, lp, hc = nqs.sample(desc, p, B, seed=3, step=2)
         el = nqs.local_energy(desc, p, nqs.tfim(), s, hc)
         g, st = nqs.vmc_grad(desc, p, s, hc, el)
         torch.cuda.synchronize()
         outs.append((s.clone(), lp.clone(), hc.clone(), el.clone(), g.clone(), st.clone()))
+    nqs.set_tile_variant(None)
     nqs.set_autotune(True)
     for o in outs[1:]:
         for x, y in zip(outs[0], o):
