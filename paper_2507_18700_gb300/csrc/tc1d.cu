@@ -133,8 +133,10 @@ struct Smem {
   static constexpr int kSmall = kA + GROUPS * 128 * KA * 2;      // 12D+4 floats
   static constexpr int kZ = kSmall + (12 * D + 4) * 4;           // GROUPS x SPLIT x 128 x 2 floats
   static constexpr int kJob = kZ + GROUPS * SPLIT * 128 * 2 * 4; // GROUPS x 128 long long
-  static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x D floats (next chain state)
-  static constexpr int kBar = (kStage + GROUPS * 128 * D * 4 + 15) / 16 * 16;
+  static constexpr int HS = D + 4;                               // staging row stride (floats; conflict-free float4)
+  static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x HS floats: next chain state
+                                                                 // (chains) or the new states (cache stores)
+  static constexpr int kBar = (kStage + GROUPS * 128 * HS * 4 + 15) / 16 * 16;
   static constexpr int kSlot = kBar + 8 * GROUPS;
   static constexpr int kFlags = kSlot + 16;                      // ping-pong idle flags, one int per tile
   static constexpr int kUsed = kFlags + 16;
@@ -190,7 +192,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   uint8_t* sA = sm + S::kA + g * 128 * KA * 2;
   float* zb = zbuf + g * SPLIT * 128 * 2;
   long long* jb = jobbuf + g * 128;
-  float* stg = stage + (g * 128 + m) * D + u0;     // this thread's units of the row's staged state
+  float* stg = stage + (g * 128 + m) * S::HS + u0;   // this thread's units of the row's staged state
   const float* Us = small + 10 * D;
   const float c0 = small[12 * D], c1 = small[12 * D + 1];
   const int N = a.N;
@@ -477,11 +479,6 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           if (part == 0) a.sigma_out[b * N + t] = (uint8_t)s;
         }
         acc += log_prob(s, d);
-        if (a.hcache) {
-          float4* dst = reinterpret_cast<float4*>(a.hcache + (b * N + t) * D + u0);
-#pragma unroll
-          for (int q = 0; q < DU / 4; ++q) dst[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-        }
         s_in = s;
         if (++t == N) {
           const float lp = 0.5f * acc;
@@ -491,6 +488,29 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           }
           active = false;
         }
+      }
+    }
+    if constexpr (MODE != 2) {
+      // cache store of this step's states, coalesced: every thread stages its
+      // units of h, then each warp writes its 32 rows as whole row segments
+      // (all rows of a tile are at the same site, pstep)
+      if (a.hcache && any) {
+#pragma unroll
+        for (int q = 0; q < DU / 4; ++q)
+          reinterpret_cast<float4*>(stg)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        __syncwarp();
+        constexpr int L = DU / 4, RPI = 32 / L;   // lanes per row segment, rows per store
+        const int lr = lane / L, lq = lane % L, m0 = (wt % 4) * 32;
+        const int64_t b0 = ((int64_t)blockIdx.x * GROUPS + g) * 128;
+#pragma unroll 4
+        for (int i = 0; i < 32; i += RPI) {
+          const int mr = m0 + i + lr;
+          const int64_t br = b0 + mr;
+          if (br < B)
+            reinterpret_cast<float4*>(a.hcache + (br * N + pstep) * D + u0)[lq] =
+                reinterpret_cast<const float4*>(stage + (g * 128 + mr) * S::HS + u0)[lq];
+        }
+        __syncwarp();
       }
     }
     if constexpr (MODE == 2) {
