@@ -337,7 +337,9 @@ def run_gpu(args, w):
                 "traffic": None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)}
     value = world * B * args.steps / (chosen["total_ms"] * 1e-3)
-    launches = 11 if w["cell"] == 1 else 12
+    # kernels of one step (memsets excluded): 1D FP32 sample 2, E_loc 4, gradient 5;
+    # 1D BF16 sample 3, E_loc 5, gradient 8; 2D FP32 sample 2, E_loc 5, gradient 5
+    launches = (16 if chosen is r16 else 11) if w["cell"] == 1 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,

@@ -23,7 +23,8 @@ namespace nqs {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before giving up (seconds)
+constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr int kPPEarly = 0;   // ping-pong: sub-chunks of the epilogue left when the token is passed (0 = after the last)
 
 // Gate weights with the biases and one-hot input columns folded in, as a
 // K-major BF16 operand of 4D rows x (D + 16) columns (see tc.cuh).  Biases and
@@ -130,9 +131,9 @@ struct Smem {
   static constexpr int KA = D + 16;                              // A columns: [h | 1 1 | onehot x2 | 0]
   static constexpr int kB = 0;                                   // weights, 4D x KA bf16
   static constexpr int kA = kB + 4 * D * KA * 2;                 // GROUPS x 128 x KA bf16
-  static constexpr int kSmall = kA + GROUPS * 128 * KA * 2;      // 12D+4 floats
-  static constexpr int kZ = kSmall + (12 * D + 4) * 4;           // GROUPS x SPLIT x 128 x 2 floats
-  static constexpr int kJob = kZ + GROUPS * SPLIT * 128 * 2 * 4; // GROUPS x 128 long long
+  static constexpr int kDU = kA + GROUPS * 128 * KA * 2;        // D floats: U[0] - U[1]
+  static constexpr int kZ = kDU + D * 4;                         // GROUPS x SPLIT x 128 floats
+  static constexpr int kJob = kZ + GROUPS * SPLIT * 128 * 4;     // GROUPS x 128 long long
   static constexpr int HS = D + 4;                               // staging row stride (floats; conflict-free float4)
   static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x HS floats: next chain state
                                                                  // (chains) or the new states (cache stores)
@@ -159,7 +160,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sB = sm + S::kB;
-  float* small = reinterpret_cast<float*>(sm + S::kSmall);
+  float* dUs = reinterpret_cast<float*>(sm + S::kDU);
   float* zbuf = reinterpret_cast<float*>(sm + S::kZ);
   long long* jobbuf = reinterpret_cast<long long*>(sm + S::kJob);
   float* stage = reinterpret_cast<float*>(sm + S::kStage);
@@ -170,8 +171,8 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   // ---- prologue: operands and constants into shared memory, TMEM, barriers ----
   for (int i = threadIdx.x; i < N4 * KA * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(wimg)[i];
-  for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += NT)
-    reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
+  // readout: only the logit difference d = (U_0 - U_1) h + c_0 - c_1 is used
+  for (int i = threadIdx.x; i < D; i += NT) dUs[i] = img[10 * D + i] - img[11 * D + i];
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     for (int g = 0; g < GROUPS; ++g) tc::mbar_init(&mbar[g], 1);
@@ -190,11 +191,10 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16) + (uint32_t)(g * 256);
   const uint32_t bar_main = 1 + g, bar_x = 1 + GROUPS + g;
   uint8_t* sA = sm + S::kA + g * 128 * KA * 2;
-  float* zb = zbuf + g * SPLIT * 128 * 2;
+  float* zb = zbuf + g * SPLIT * 128;
   long long* jb = jobbuf + g * 128;
   float* stg = stage + (g * 128 + m) * S::HS + u0;   // this thread's units of the row's staged state
-  const float* Us = small + 10 * D;
-  const float c0 = small[12 * D], c1 = small[12 * D + 1];
+  const float dc = img[12 * D] - img[12 * D + 1];
   const int N = a.N;
   const int64_t B = a.B;
 
@@ -371,9 +371,9 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     // sub-chunk c (stage B), so the MUFU always has independent work.
     // Readout: sequential sums over 16-unit chunks, chunks combined by a fixed
     // pairwise tree, so every SPLIT gives bitwise the same logits.
-    float zc0[DU / 16], zc1[DU / 16];
+    float zc[DU / 16];
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) zc0[c] = zc1[c] = 0.0f;
+    for (int c = 0; c < DU / 16; ++c) zc[c] = 0.0f;
     if (any) {
       constexpr int NS = DU / 8;
       // stage A: tu = tanh(a_u / 2 pre-scaled), ag = r * q + x_in
@@ -389,7 +389,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       tmem_wait_regs(bufA);
       if (NS > 1) issue(1, bufB);
       stage_a(bufA, tuA, agA);
-      float s0 = 0.0f, s1 = 0.0f;
+      float s0 = 0.0f;
 #pragma unroll
       for (int sc = 0; sc < NS; ++sc) {
         float (&tu)[8] = (sc & 1) ? tuB : tuA;
@@ -401,14 +401,11 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           if (sc + 2 < NS) issue(sc + 2, fb);
           stage_a(nb, (sc & 1) ? tuA : tuB, (sc & 1) ? agA : agB);
         }
-        float U0[8], U1[8];
+        float Ud[8];
         {
-          const float* up = Us + u0 + sc * 8;
-          const float4 a0 = lds4(up), a1 = lds4(up + 4), b0 = lds4(up + D), b1 = lds4(up + D + 4);
-          U0[0] = a0.x; U0[1] = a0.y; U0[2] = a0.z; U0[3] = a0.w;
-          U0[4] = a1.x; U0[5] = a1.y; U0[6] = a1.z; U0[7] = a1.w;
-          U1[0] = b0.x; U1[1] = b0.y; U1[2] = b0.z; U1[3] = b0.w;
-          U1[4] = b1.x; U1[5] = b1.y; U1[6] = b1.z; U1[7] = b1.w;
+          const float4 a0 = lds4(dUs + u0 + sc * 8), a1 = lds4(dUs + u0 + sc * 8 + 4);
+          Ud[0] = a0.x; Ud[1] = a0.y; Ud[2] = a0.z; Ud[3] = a0.w;
+          Ud[4] = a1.x; Ud[5] = a1.y; Ud[6] = a1.z; Ud[7] = a1.w;
         }
         // stage B
 #pragma unroll
@@ -417,54 +414,51 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           const float cc = hw_tanh(ag[q]);
           const float ug = fmaf(0.5f, tu[q], 0.5f);
           h[j] = fmaf(ug, cc - h[j], h[j]);
-          s0 = fmaf(U0[q], h[j], s0);
-          s1 = fmaf(U1[q], h[j], s1);
+          s0 = fmaf(Ud[q], h[j], s0);
         }
         if (sc & 1) {
-          zc0[sc / 2] = s0;
-          zc1[sc / 2] = s1;
+          zc[sc / 2] = s0;
           s0 = 0.0f;
-          s1 = 0.0f;
+        }
+        if constexpr (PP) {
+          // pass the token kPPEarly sub-chunks before the end: the other
+          // tile's first loads and gates overlap this tile's last ones
+          if (sc == (NS > kPPEarly ? NS - 1 - kPPEarly : NS - 1)) {
+            if (tt == 0) idle_flag[g] = 0;
+            tc::group_arrive(pp_sig, 2 * TT);
+            prev_idle = false;
+          }
         }
       }
     }
 #pragma unroll
     for (int w = 1; w < DU / 16; w *= 2)
 #pragma unroll
-      for (int c = 0; c + w < DU / 16; c += 2 * w) {
-        zc0[c] += zc0[c + w];
-        zc1[c] += zc1[c + w];
-      }
-    float z0 = zc0[0], z1 = zc1[0];
+      for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
+    float z = zc[0];
     if constexpr (PP) {
-      if (tt == 0) idle_flag[g] = any ? 0 : 1;
-      tc::group_arrive(pp_sig, 2 * TT);
-      prev_idle = !any;
+      if (!any) {             // idle: pass the token with the idle flag
+        if (tt == 0) idle_flag[g] = 1;
+        tc::group_arrive(pp_sig, 2 * TT);
+        prev_idle = true;
+      }
     }
     if constexpr (SPLIT > 1) {
-      zb[(part * 128 + m) * 2] = z0;
-      zb[(part * 128 + m) * 2 + 1] = z1;
+      zb[part * 128 + m] = z;
       tc::group_barrier(bar_x, TT);
-      float p0[SPLIT], p1[SPLIT];
+      float pz[SPLIT];
 #pragma unroll
-      for (int p = 0; p < SPLIT; ++p) {
-        p0[p] = zb[(p * 128 + m) * 2];
-        p1[p] = zb[(p * 128 + m) * 2 + 1];
-      }
+      for (int p = 0; p < SPLIT; ++p) pz[p] = zb[p * 128 + m];
 #pragma unroll
       for (int w = 1; w < SPLIT; w *= 2)
 #pragma unroll
-        for (int p = 0; p + w < SPLIT; p += 2 * w) {
-          p0[p] += p0[p + w];
-          p1[p] += p1[p + w];
-        }
-      z0 = p0[0];
-      z1 = p1[0];
+        for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
+      z = pz[0];
     }
     // ---- (f) row logic (identical in every part; side effects by part 0) ----
     bool fin = false;
     if (active && !timed_out) {
-      const float d = (z0 + c0) - (z1 + c1);
+      const float d = z + dc;
       if constexpr (MODE == 2) {
         acc += 0.5f * (log_prob(s_t, d) - log_prob(s_t, dl));
         s_in = s_t;
@@ -593,8 +587,8 @@ struct BSmem {
   static constexpr int kH = kG + 128 * GW * 2;            // 2 x [128 x HS] f32 state rows
   static constexpr int kSmall = kH + 2 * 128 * HS * 4;    // 12D + 4 floats
   static constexpr int kDU = kSmall + (12 * D + 4) * 4;   // D floats: U[0] - U[1]
-  static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 x 2 floats (readout exchange)
-  static constexpr int kBar = (kZ + SPLIT * 128 * 2 * 4 + 15) / 16 * 16;   // 4 mbarriers
+  static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 floats (readout exchange)
+  static constexpr int kBar = (kZ + SPLIT * 128 * 4 + 15) / 16 * 16;   // 4 mbarriers
   static constexpr int kSlot = kBar + 32;
   static constexpr int kBytes = 1024 + kSlot + 16;
   // TMEM columns
@@ -670,8 +664,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
   const int u0 = part * DU;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
-  const float* Us = small + 10 * D;
-  const float c0 = small[12 * D], c1 = small[12 * D + 1];
+  const float dc = small[12 * D] - small[12 * D + 1];
   const int N = a.N;
   const int64_t b = (int64_t)blockIdx.x * 128 + m;
   const bool valid = b < a.B;
@@ -738,31 +731,21 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
       *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
       *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
     }
-    // ---- readout of h_n: 16-unit chunk sums in order, chunks by a fixed tree ----
-    float zc0[DU / 16], zc1[DU / 16];
+    // ---- readout of h_n (logit difference): 16-unit chunk sums in order, chunks
+    // and parts by fixed trees, as in the forward pass ----
+    float zc[DU / 16];
 #pragma unroll
     for (int c = 0; c < DU / 16; ++c) {
-      float s0 = 0.0f, s1 = 0.0f;
+      float s0 = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int j = 16 * c + q;
-        s0 = fmaf(Us[u0 + j], hn[j], s0);
-        s1 = fmaf(Us[D + u0 + j], hn[j], s1);
-      }
-      zc0[c] = s0;
-      zc1[c] = s1;
+      for (int q = 0; q < 16; ++q) s0 = fmaf(dU[u0 + 16 * c + q], hn[16 * c + q], s0);
+      zc[c] = s0;
     }
 #pragma unroll
     for (int w = 1; w < DU / 16; w *= 2)
 #pragma unroll
-      for (int c = 0; c + w < DU / 16; c += 2 * w) {
-        zc0[c] += zc0[c + w];
-        zc1[c] += zc1[c + w];
-      }
-    if constexpr (SPLIT > 1) {
-      zb[(part * 128 + m) * 2] = zc0[0];
-      zb[(part * 128 + m) * 2 + 1] = zc1[0];
-    }
+      for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
+    if constexpr (SPLIT > 1) zb[part * 128 + m] = zc[0];
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -776,25 +759,18 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
       }
       tc::mma_commit(&mbar[0]);
     }
-    float z0 = zc0[0], z1 = zc1[0];
+    float z = zc[0];
     if constexpr (SPLIT > 1) {
-      float p0[SPLIT], p1[SPLIT];
+      float pz[SPLIT];
 #pragma unroll
-      for (int p = 0; p < SPLIT; ++p) {
-        p0[p] = zb[(p * 128 + m) * 2];
-        p1[p] = zb[(p * 128 + m) * 2 + 1];
-      }
+      for (int p = 0; p < SPLIT; ++p) pz[p] = zb[p * 128 + m];
 #pragma unroll
       for (int w = 1; w < SPLIT; w *= 2)
 #pragma unroll
-        for (int p = 0; p + w < SPLIT; p += 2 * w) {
-          p0[p] += p0[p + w];
-          p1[p] += p1[p + w];
-        }
-      z0 = p0[0];
-      z1 = p1[0];
+        for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
+      z = pz[0];
     }
-    const float d = (z0 + c0) - (z1 + c1);
+    const float d = z + dc;
     const float dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
     // h_n is no longer needed: its buffer takes h_{n-2}.  (The copy's proxy
     // fence comes before this site's global store, so it does not wait on it.)
