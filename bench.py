@@ -308,7 +308,8 @@ def run_gpu(args, w):
 
     r32 = measure(nqs.FP32)
     chosen, r16, check = r32, None, None
-    bf16_ok = w["cell"] == 1 and w["d"] in (16, 32, 64) and args.precision != "fp32"
+    bf16_ok = args.precision != "fp32" and (w["d"] in (16, 32, 64) if w["cell"] == 1
+                                            else w["d"] in (32, 64) and N <= 128)
     if bf16_ok:
         r16 = measure(nqs.BF16)
         check = accuracy_check(r16["desc"], r32["desc"])
@@ -323,7 +324,9 @@ def run_gpu(args, w):
         d = w["d"]
         mufu = sum(chosen["cells"]) * 3 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
         mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "tensor", "kernel": "nqs_local_energy (prefix-cached chains, tcgen05 BF16)",
+        roof = {"bound": "tensor",
+                "kernel": "nqs_local_energy (prefix-cached %s chains, tcgen05 BF16)"
+                          % ("TFIM" if w["cell"] == 1 else "Heisenberg"),
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src,
                 "epilogue_sfu": {"achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
@@ -338,8 +341,13 @@ def run_gpu(args, w):
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)}
     value = world * B * args.steps / (chosen["total_ms"] * 1e-3)
     # kernels of one step (memsets excluded): 1D FP32 sample 2, E_loc 4, gradient 5;
-    # 1D BF16 sample 3, E_loc 5, gradient 8; 2D FP32 sample 2, E_loc 5, gradient 5
-    launches = (16 if chosen is r16 else 11) if w["cell"] == 1 else 12
+    # 1D BF16 sample 3, E_loc 5, gradient 8; 2D FP32 sample 2, E_loc 5, gradient 5;
+    # 2D BF16 sample 2, E_loc 7 (pack, bonds, teacher forcing, job count, jobs,
+    # chains, energies), gradient 5 (the FP32 reverse sweep)
+    if w["cell"] == 1:
+        launches = 16 if chosen is r16 else 11
+    else:
+        launches = 14 if chosen is r16 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,
@@ -347,7 +355,9 @@ def run_gpu(args, w):
         "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": B * world, "seq_len": N,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "precision": "bf16 tensor-core cell GEMMs, fp32 state" if chosen is r16 else "fp32",
+                   "precision": ("bf16 tensor-core cell GEMMs, fp32 state" if w["cell"] == 1 else
+                                 "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs), "
+                                 "fp32 reverse sweep") if chosen is r16 else "fp32",
                    "fp32_value": world * B * args.steps / (r32["total_ms"] * 1e-3),
                    "fp32_ms_per_step": r32["total_ms"] / args.steps,
                    "bf16_check": check,

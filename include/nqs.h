@@ -99,7 +99,12 @@ typedef struct {
   int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of
                          sampling, teacher forcing, the local-energy chains and
                          the reverse sweep on the tensor cores (BF16 operands,
-                         FP32 accumulation and FP32 state; d_h in {16, 32, 64}) */
+                         FP32 accumulation and FP32 state; d_h in {16, 32, 64}),
+                         and the 2D cell and GLU GEMMs of sampling, teacher
+                         forcing and the Heisenberg chains (d_h in {32, 64},
+                         N <= 128; the 2D gradient
+                         runs the FP32 reverse sweep); other shapes return
+                         NQS_EUNSUPPORTED */
 } nqs_model_desc;
 
 typedef struct {

@@ -42,21 +42,27 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   return NQS_OK;
 }
 
-// Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, and the BF16
-// tensor-core 1D GRU for d_h in {16, 32, 64}.
+// Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, the BF16
+// tensor-core 1D GRU for d_h in {16, 32, 64} and the BF16 tensor-core 2D GRU
+// for d_h in {32, 64} while its column buffer fits in TMEM (3 d + Lx d / 2 <=
+// 512 columns) and N <= 128 (its gradient runs the FP32 reverse sweep).
 nqs_status check_built(const Dims& d) {
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
-  if (d.precision == NQS_BF16 && !(d.cell == NQS_GRU1D && tc1d_supported(d.d))) return NQS_EUNSUPPORTED;
+  if (d.precision == NQS_BF16) {
+    const bool ok = d.cell == NQS_GRU1D ? tc1d_supported(d.d) != 0 : tc2d_supported(d.d, d.Lx, d.N) != 0;
+    if (!ok) return NQS_EUNSUPPORTED;
+  }
   return NQS_OK;
 }
 
 bool use_tc(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU1D; }
+bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
 
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, w, w2, a, b, c, e, f, total;
+  size_t img, w, w2, a, b, c, e, f, g, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
@@ -71,23 +77,30 @@ Layout layout(const Dims& d, int64_t B, int op) {
     L.w2 = off;                                   // transposed image for the reverse sweep
     off += align256(tc1d_wimg_bytes(d.d));
   }
+  if (use_tc2d(d)) {
+    L.w = off;
+    off += align256(tc2d_wimg_bytes(d.d));
+  }
   const size_t BN = (size_t)B * (size_t)d.N;
   auto take = [&](size_t bytes) { const size_t at = off; off += align256(bytes); return at; };
   switch (op) {
     case NQS_OP_SAMPLE:
     case NQS_OP_LOGPSI:
-      if (two) L.a = take((size_t)gru2d_engine_slots(d.d, B, 1) * d.Lx * d.d * sizeof(float));  // colbuf
+      if (two) L.a = take((use_tc2d(d) ? tc2d_colbuf_floats(B, d.Lx, d.d)
+                                        : (size_t)gru2d_engine_slots(d.d, B, 1) * d.Lx * d.d) * sizeof(float));  // colbuf
       break;
     case NQS_OP_LOCAL_ENERGY:
       if (!two) {
         L.a = take(BN * sizeof(float));        // dlog
         L.b = take(BN * sizeof(float));        // delta
       } else {
-        L.a = take((size_t)gru2d_engine_slots(d.d, B, 2) * d.Lx * d.d * sizeof(float));  // colbuf
+        L.a = take((use_tc2d(d) ? tc2d_colbuf_floats(B, d.Lx, d.d)
+                                : (size_t)gru2d_engine_slots(d.d, B, 2) * d.Lx * d.d) * sizeof(float));  // colbuf
         L.b = take((size_t)n_bonds(d) * 16);                  // bond table
         L.c = take(BN * 2 * sizeof(float));                   // lp_tab
         L.e = take(BN * sizeof(int));                         // nup_tab
         L.f = take((size_t)B * n_bonds(d) * sizeof(float));   // delta
+        if (use_tc2d(d)) L.g = take(tc2d_jobs_bytes(B, n_bonds(d)));   // chain jobs
       }
       break;
     case NQS_OP_LOGPSI_GRAD:
@@ -215,6 +228,25 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!reset_status(ws, st)) return NQS_ECUDA;
   float* img = at<float>(ws, L.img);
+  if (use_tc2d(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Tc2Fwd f{};
+    f.B = B;
+    f.Lx = d.Lx;
+    f.N = d.N;
+    f.sz0 = d.sz0;
+    f.sigma_in = sigma_in;
+    f.sigma_out = sigma_out;
+    f.uniforms = uniforms;
+    f.seed = seed;
+    f.step = step;
+    f.logpsi = logpsi;
+    f.hcache = hcache;
+    f.colbuf = at<float>(ws, L.a);
+    f.hdr = static_cast<WsHeader*>(ws);
+    return cuda_status(tc2d_forward(f, wimg, d.d, sample, st));
+  }
   if (d.cell == NQS_GRU2D) {
     if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
     Eng2Args a{};
@@ -306,6 +338,43 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
     float* lp_tab = at<float>(ws, L.c);
     int* nup_tab = at<int>(ws, L.e);
     float* delta = at<float>(ws, L.f);
+    const float x = ham->marshall ? -0.5f * (float)ham->J : 0.5f * (float)ham->J;
+    if (use_tc2d(d)) {
+      // cached-path tables from a teacher-forced pass with the same BF16
+      // arithmetic as the chains, then the chains over the antiparallel bonds
+      uint8_t* wimg = at<uint8_t>(ws, L.w);
+      if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+      if (gru2d_bonds(d.Lx, d.Ly, bonds, st) != cudaSuccess) return NQS_ECUDA;
+      Tc2Fwd f{};
+      f.B = B;
+      f.Lx = d.Lx;
+      f.N = d.N;
+      f.sz0 = d.sz0;
+      f.sigma_in = sigma;
+      f.lp_tab = lp_tab;
+      f.nup_tab = nup_tab;
+      f.colbuf = at<float>(ws, L.a);
+      f.hdr = hdr;
+      if (tc2d_forward(f, wimg, d.d, false, st) != cudaSuccess) return NQS_ECUDA;
+      Tc2Chains c{};
+      c.B = B;
+      c.Lx = d.Lx;
+      c.N = d.N;
+      c.nb = nb;
+      c.sz0 = d.sz0;
+      c.sigma = sigma;
+      c.hcache = hcache;
+      c.lp_tab = lp_tab;
+      c.nup_tab = nup_tab;
+      c.bonds = bonds;
+      c.delta = delta;
+      c.colbuf = at<float>(ws, L.a);
+      c.jobs_ws = at<uint8_t>(ws, L.g);
+      c.counter = &hdr->job_counter;
+      c.hdr = hdr;
+      if (tc2d_heis_chains(c, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+      return cuda_status(heis_eloc(sigma, bonds, delta, eloc, B, d.N, nb, (float)ham->J, x, hdr, st));
+    }
     if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (gru2d_bonds(d.Lx, d.Ly, bonds, st) != cudaSuccess) return NQS_ECUDA;
     if (gru2d_prep(img, hcache, sigma, lp_tab, nup_tab, B, d.Lx, d.N, d.d, d.sz0, st) != cudaSuccess)
@@ -328,7 +397,6 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
     c.counter = &hdr->job_counter;
     c.hdr = hdr;
     if (gru2d_heis_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    const float x = ham->marshall ? -0.5f * (float)ham->J : 0.5f * (float)ham->J;
     return cuda_status(heis_eloc(sigma, bonds, delta, eloc, B, d.N, nb, (float)ham->J, x, hdr, st));
   }
   float* dlog = at<float>(ws, L.a);

@@ -82,6 +82,43 @@ struct Bptt2Args {
   float* sacc;               // large d_h: [grid, row groups, 14, d] small-gradient scratch (zeroed)
 };
 
+// BF16 tensor-core 2D path (tc2d.cu)
+struct Tc2Fwd {
+  int64_t B;
+  int Lx, N, sz0;
+  const uint8_t* sigma_in;   // teacher forcing
+  uint8_t* sigma_out;        // sampling
+  const float* uniforms;     // nullable
+  uint64_t seed, step;
+  float* logpsi;             // nullable in teacher forcing
+  float* hcache;             // nullable
+  float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
+  float* lp_tab;             // teacher forcing: [B, N, 2] masked log p of both outcomes (nullable)
+  int* nup_tab;              // teacher forcing: [B, N] up spins before each position
+  WsHeader* hdr;
+};
+struct Tc2Chains {
+  int64_t B;
+  int Lx, N, nb, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* lp_tab;
+  const int* nup_tab;
+  const int4* bonds;
+  float* delta;              // [B, nb]
+  float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
+  uint8_t* jobs_ws;          // tc2d_jobs_bytes(B, nb)
+  unsigned long long* counter;
+  WsHeader* hdr;
+};
+int tc2d_supported(int D, int Lx, int N);
+size_t tc2d_wimg_bytes(int D);
+size_t tc2d_jobs_bytes(int64_t B, int nb);
+size_t tc2d_colbuf_floats(int64_t B, int Lx, int D);
+cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
+cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st);
+cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st);
+
 size_t gru2d_img_floats(int D);
 int gru2d_supported(int D);
 size_t gru2d_bptt_scratch_floats(int D, int64_t B);

@@ -1,0 +1,749 @@
+// BF16 tensor-core path of the 2D GRU wave function with its GLU head (App. A):
+// zig-zag sampling / teacher forcing and the prefix-cached Heisenberg chains
+// (Eq. heisenberg, Marshall-rotated, Sec. III B), for d_h in {32, 64}.
+//
+// One CTA = one tile of 128 rows (= TMEM lanes), one thread per row.  Per
+// cell (position t = (i, j) of the zig-zag order, Sec. II):
+//   A1  = [hi(h') | 1 1 | onehot(s_hor) onehot(s_ver) x2 | 0 | lo(h')],  h' = [h_hor | h_ver]
+//   MMA1: acc = A1 W1^T, W1 = [W | W_g / 2 | U_mix] (N = 3d) with the biases and
+//         one-hot input weights as BF16 hi + lo pairs in the extra columns; the
+//         lo(h') columns reuse the h' columns of W1
+//   epilogue 1: h~ = tanh(acc_W), u = (1 + tanh(acc_g)) / 2, h = u h~ + (1 - u) U_mix h'
+//   A2  = [hi(h) | 1 1 | 0 | lo(h)]
+//   MMA2: acc = A2 W2^T, W2 = [W_1 | W_2 / 2] with b_1, b_2 / 2 folded (N = 2d)
+//   epilogue 2: y = (W_1 h + b_1) sigmoid(W_2 h + b_2), d = (U_0 - U_1) y + c_0 - c_1
+// The 2D cell has no FP32 carry of the state: the previous states enter only
+// through the GEMMs (the mixing path U_mix h' included), and the GLU reads h.
+// A single BF16 rounding of h per cell compounds over the lattice, so every
+// state enters both GEMMs as a BF16 pair hi + lo (hi = bf16(h), lo =
+// bf16(h - hi): about 16 significant bits); the weights are plain BF16.  The
+// state just computed stays in FP32 registers (the next cell's horizontal
+// neighbour); every state is also written to a per-row column buffer in
+// global memory (the latest FP32 state of each lattice column, coalesced warp
+// stores), from which the vertical neighbour of the next cell is copied into
+// shared memory with cp.async one step ahead.  A chain that restarts from the
+// cache takes the states of the columns it has not recomputed yet from the
+// cache the same way.  Spins of a row's configuration are a bit mask in
+// registers.
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace nqs {
+
+namespace {
+
+constexpr uint32_t kWait2 = 1u << 26;   // mbarrier polls before giving up
+
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float hw_tanh2(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&p);
+}
+// hi and lo BF16 pairs of two values: hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16(a, b);
+  lo = pack_bf16(a - bf16_round(a), b - bf16_round(b));
+}
+// 8 values as hi / lo 16-byte rows of an operand
+__device__ __forceinline__ void st_split8(uint8_t* dhi, uint8_t* dlo, const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split_bf16(v[2 * q], v[2 * q + 1], h[q], l[q]);
+  *reinterpret_cast<uint4*>(dhi) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(dlo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void cp_async16_2d(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit_2d() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_2d() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ float ldg_f32_v(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];\n" : "=f"(v) : "l"(p));
+  return v;
+}
+
+// 8 consecutive 32-bit TMEM columns of this thread's lane (warp-collective).
+__device__ __forceinline__ void tld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+// Ties loaded registers to the preceding wait: no use is scheduled above it.
+template <int NW>
+__device__ __forceinline__ void tie(uint32_t (&r)[NW]) {
+#pragma unroll
+  for (int q = 0; q < NW; ++q) asm volatile("" : "+r"(r[q]));
+}
+
+// Zig-zag geometry (Sec. II, Fig. 1(b)), as in the FP32 path.
+struct Pz {
+  int i, j, r;
+};
+__device__ __forceinline__ Pz zpos(int t, int Lx) {
+  Pz p;
+  p.j = t / Lx;
+  p.r = t - p.j * Lx;
+  p.i = (p.j & 1) ? Lx - 1 - p.r : p.r;
+  return p;
+}
+__device__ __forceinline__ int zhor(const Pz& p) { return (p.j & 1) ? p.i + 1 : p.i - 1; }
+__device__ __forceinline__ int zsnake(int i, int j, int Lx) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
+
+__device__ __forceinline__ int mbit(const uint64_t (&m)[2], int k) { return (int)((m[k >> 6] >> (k & 63)) & 1ull); }
+__device__ __forceinline__ void mset(uint64_t (&m)[2], int k, int s) {
+  const uint64_t b = 1ull << (k & 63);
+  m[k >> 6] = s ? (m[k >> 6] | b) : (m[k >> 6] & ~b);
+}
+
+// Zero-magnetisation mask (forced outcomes have log p = 0 / -inf).
+__device__ __forceinline__ float lp_masked(int s, float d, int n_up, int n_done, int N, bool sz0) {
+  if (sz0) {
+    const int half = N >> 1;
+    if (n_up >= half) return s == 1 ? 0.0f : -INFINITY;
+    if (n_done - n_up >= half) return s == 0 ? 0.0f : -INFINITY;
+  }
+  return log_prob(s, d);
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Packed BF16 operands (K-major, no swizzle; tc.cuh) and FP32 readout constants.
+// ----------------------------------------------------------------------------
+__global__ void pack2d_tc_kernel(const float* __restrict__ p, uint8_t* __restrict__ w1, uint8_t* __restrict__ w2,
+                                 float* __restrict__ aux, int D) {
+  const int K1 = 2 * D + 16, K2 = D + 16, W2c = 2 * D + 4;
+  // flat layout (App. A; nqs.h): W, W_g [d, 2d+4], U_mix [d, 2d], b, b_g, W_1 [d, d], b_1, W_2, b_2, U_out [2, d], c
+  const int oW = 0, oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D, ob1 = oW1 + D * D,
+            oW2 = ob1 + D, ob2 = oW2 + D * D, oUo = ob2 + D, oc = oUo + 2 * D;
+  const int n1 = 3 * D * K1, n2 = 2 * D * K2;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n1 + n2 + D + 1; t += gridDim.x * blockDim.x) {
+    if (t < n1) {
+      const int n = t / K1, k = t % K1, g = n / D, u = n % D;
+      float v = 0.0f;
+      if (k < 2 * D) {
+        v = g == 0 ? p[oW + u * W2c + k] : g == 1 ? p[oWg + u * W2c + k] : p[oU + u * 2 * D + k];
+      } else if (g < 2 && k < 2 * D + 10) {
+        // extra columns: [b hi | b lo | w_h0 w_h1 w_v0 w_v1 hi | the same lo]
+        const int e = k - 2 * D;
+        const int Wo = g == 0 ? oW : oWg;
+        const float x = e < 2 ? p[(g == 0 ? ob : obg) + u] : p[Wo + u * W2c + 2 * D + (e < 6 ? e - 2 : e - 6)];
+        v = (e == 0 || (e >= 2 && e < 6)) ? bf16_round(x) : x - bf16_round(x);
+      }
+      if (g == 1) v *= 0.5f;   // u = (1 + tanh(a_g / 2)) / 2
+      *reinterpret_cast<__nv_bfloat16*>(w1 + tc::kmajor_offset(n, k, K1)) = __float2bfloat16_rn(v);
+    } else if (t < n1 + n2) {
+      const int q = t - n1, n = q / K2, k = q % K2, g = n / D, v = n % D;
+      float x = 0.0f;
+      if (k < D) {
+        x = p[(g == 0 ? oW1 : oW2) + v * D + k];
+      } else if (k < D + 2) {
+        const float bb = p[(g == 0 ? ob1 : ob2) + v];
+        x = k == D ? bf16_round(bb) : bb - bf16_round(bb);
+      }
+      if (g == 1) x *= 0.5f;   // sigmoid(a) = (1 + tanh(a / 2)) / 2
+      *reinterpret_cast<__nv_bfloat16*>(w2 + tc::kmajor_offset(n, k, K2)) = __float2bfloat16_rn(x);
+    } else {
+      const int v = t - n1 - n2;
+      aux[v] = v < D ? p[oUo + v] - p[oUo + D + v] : p[oc] - p[oc + 1];
+    }
+  }
+}
+
+// Heisenberg chain jobs: the antiparallel (sample, bond) pairs in bond order
+// (bonds sorted by the earlier zig-zag position: longest chains first), with
+// each chain's start values taken from the cached-path tables.
+struct Job2 {
+  int b, rank;
+  float acc0;          // 1/2 [log p_pa(s_new) - log p_pa(s_old)]
+  int nup0;            // up spins before pa+1 on the exchanged configuration
+  uint64_t mask[2];    // exchanged configuration, bit k = spin of lattice site k
+};
+static_assert(sizeof(Job2) == 32, "job record is 32 bytes");
+
+__global__ void heis_count_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds, int64_t B,
+                                  int N, int* __restrict__ counts) {
+  __shared__ int red[32];
+  const int4 bd = bonds[blockIdx.x];
+  int c = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) c += (sigma[b * N + bd.x] != 0) != (sigma[b * N + bd.y] != 0);
+  c = warp_sum_int(c);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    counts[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds,
+                                                        const float* __restrict__ lp_tab, const int* __restrict__ nup_tab,
+                                                        const int* __restrict__ counts, int64_t B, int N, int nb,
+                                                        Job2* __restrict__ jobs, int* __restrict__ njobs) {
+  __shared__ int wsum[32];
+  __shared__ int base_s;
+  const int rank = blockIdx.x;
+  const int4 bd = bonds[rank];
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int q = 0; q < rank; ++q) off += counts[q];
+    base_s = off;
+    if (rank == nb - 1) *njobs = off + counts[rank];
+  }
+  __syncthreads();
+  int base = base_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t b0 = 0; b0 < B; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    int sa = 0, sb = 0;
+    bool anti = false;
+    if (b < B) {
+      sa = sigma[b * N + bd.x] ? 1 : 0;
+      sb = sigma[b * N + bd.y] ? 1 : 0;
+      anti = sa != sb;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, anti);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      if (w < warp) before += wsum[w];
+      total += wsum[w];
+    }
+    if (anti) {
+      const int idx = base + before + __popc(bal & ((1u << lane) - 1u));
+      Job2 jb;
+      jb.b = (int)b;
+      jb.rank = rank;
+      const int pa = bd.z;
+      const int64_t row = b * N;
+      // bond.x sits at position pa and takes the partner's spin sb
+      jb.acc0 = 0.5f * (lp_tab[(row + pa) * 2 + sb] - lp_tab[(row + pa) * 2 + sa]);
+      jb.nup0 = nup_tab[row + pa] + (sb == 0 ? 1 : 0);
+      uint64_t m0 = 0, m1 = 0;
+      for (int k = 0; k < N; ++k) {
+        const int kk = k == bd.x ? bd.y : k == bd.y ? bd.x : k;
+        const uint64_t s = sigma[row + kk] ? 1ull : 0ull;
+        if (k < 64) m0 |= s << k; else m1 |= s << (k - 64);
+      }
+      jb.mask[0] = m0;
+      jb.mask[1] = m1;
+      jobs[idx] = jb;
+    }
+    base += total;
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// The engine.  MODE 0: sampling, 1: teacher forcing (optionally writing the
+// cached-path tables), 2: Heisenberg chains.
+// ----------------------------------------------------------------------------
+template <int D>
+struct S2 {
+  static constexpr int K1 = 2 * D + 16, K2 = D + 16, HS = D + 4;
+  static constexpr int KA1 = K1 + 2 * D, KA2 = K2 + D;     // A operand columns: [hi | extras | lo]
+  static constexpr int kW1 = 0;                            // [3D x K1] bf16
+  static constexpr int kW2 = kW1 + 3 * D * K1 * 2;         // [2D x K2] bf16
+  static constexpr int kA = kW2 + 2 * D * K2 * 2;          // A1 [128 x KA1] bf16; A2 [128 x KA2] aliases it
+  static constexpr int kHS = kA + 128 * KA1 * 2;           // [128 x HS] f32: horizontal-input copy / store staging
+  static constexpr int kVS = kHS + 128 * HS * 4;           // [128 x HS] f32: vertical-input copy
+  static constexpr int kAux = kVS + 128 * HS * 4;          // D + 4 floats: U_0 - U_1, c_0 - c_1
+  static constexpr int kCol = kAux + (D + 4) * 4;          // 128 ints: column-buffer entry of each row's new state
+  static constexpr int kBar = kCol + 128 * 4;              // 2 mbarriers
+  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+  static constexpr uint32_t kTmemCols = 3 * D <= 128 ? 128 : 256;   // accumulators [0, 3D)
+};
+
+struct Tc2Args {
+  int64_t B;
+  int Lx, N, nb, sz0;
+  const uint8_t* sigma_in;
+  uint8_t* sigma_out;
+  const float* uniforms;
+  uint64_t seed, step;
+  float* logpsi;             // nullable in teacher forcing
+  float* hcache;             // written by sampling / teacher forcing (nullable); read by chains
+  float* colbuf;             // [CTAs x 128 rows, Lx, d] latest FP32 state of every lattice column
+  float* lp_tab;             // teacher forcing: written when non-null; chains: read
+  int* nup_tab;
+  const int4* bonds;
+  const Job2* jobs;
+  const int* njobs;
+  float* delta;
+  unsigned long long* counter;
+  WsHeader* hdr;
+};
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(128, 1)
+tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
+                   Tc2Args a) {
+  using S = S2<D>;
+  constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sW1 = sm + S::kW1;
+  uint8_t* sW2 = sm + S::kW2;
+  uint8_t* sA = sm + S::kA;
+  float* sHS = reinterpret_cast<float*>(sm + S::kHS);
+  float* sVS = reinterpret_cast<float*>(sm + S::kVS);
+  float* sAux = reinterpret_cast<float*>(sm + S::kAux);
+  int* sCol = reinterpret_cast<int*>(sm + S::kCol);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += 128)
+    reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 128)
+    reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
+  for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int m = threadIdx.x, lane = m & 31, warp = m >> 5;
+  float* colrow = a.colbuf + ((int64_t)blockIdx.x * 128 + m) * a.Lx * D;   // this row's column buffer
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int Lx = a.Lx, N = a.N;
+  const int64_t B = a.B;
+  const float dc = sAux[D];
+  float* hs = sHS + m * S::HS;       // this row's horizontal-input copy
+  float* vs = sVS + m * S::HS;       // this row's vertical-input copy
+
+  // row state
+  int64_t b = 0;
+  int t = 0, pa = -1, rank = 0, n_up = 0;
+  float acc = 0.0f, lp_next = 0.0f;
+  bool active = false;
+  uint64_t mask[2] = {0ull, 0ull};
+  float h[D];                         // the state just computed (FP32)
+#pragma unroll
+  for (int q = 0; q < D; ++q) h[q] = 0.0f;
+  int hsrc = 0, vsrc = 0;            // next cell's inputs: 0 zero, 1 registers, 2 shared copy
+
+  auto fetch = [&](float* dst, const float* src) {
+#pragma unroll
+    for (int q = 0; q < D / 4; ++q) cp_async16_2d(dst + 4 * q, src + 4 * q);
+  };
+  // Chains: the original state of lattice site k of sample b.
+  auto fetch_orig = [&](float* dst, int k) { fetch(dst, a.hcache + (b * N + k) * D); };
+  // Inputs of the cell at position t (after the row moved there): sources and copies.
+  auto plan_inputs = [&](bool fresh) {
+    const Pz p = zpos(t, Lx);
+    hsrc = 0;
+    vsrc = 0;
+    bool copies = false;
+    if (p.r > 0) {
+      if (fresh) {              // chain start: the state at position pa is the original
+        fetch_orig(hs, p.j * Lx + zhor(p));
+        hsrc = 2;
+        copies = true;
+      } else {
+        hsrc = 1;
+      }
+    }
+    if (p.j > 0) {
+      const int q = zsnake(p.i, p.j - 1, Lx);
+      if (!fresh && q == t - 1) {
+        vsrc = 1;               // the state just computed (first cell of a row)
+      } else if (MODE == 2 && q <= pa) {
+        fetch_orig(vs, (p.j - 1) * Lx + p.i);
+        vsrc = 2;
+        copies = true;
+      } else {
+        fetch(vs, colrow + p.i * D);   // recomputed by this row (at least two cells back)
+        vsrc = 2;
+        copies = true;
+      }
+    }
+    if (copies) cp_commit_2d();
+    if constexpr (MODE == 2) {
+      const int k = p.j * Lx + p.i;
+      const int4 bd = a.bonds[rank];
+      const int so = mbit(mask, k) ^ ((k == bd.x || k == bd.y) ? 1 : 0);   // original spin at k
+      lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
+    }
+  };
+  // Chains: take job j (or go idle).
+  auto start_job = [&](unsigned long long j) {
+    const unsigned long long nj = (unsigned long long)*a.njobs;
+    if (j >= nj) {
+      active = false;
+      return;
+    }
+    const Job2 jb = a.jobs[j];
+    b = jb.b;
+    rank = jb.rank;
+    pa = a.bonds[rank].z;
+    t = pa + 1;
+    acc = jb.acc0;
+    n_up = jb.nup0;
+    mask[0] = jb.mask[0];
+    mask[1] = jb.mask[1];
+    active = true;
+    plan_inputs(true);
+  };
+  // warp-aggregated pull of one job for every lane with `need` (all lanes call it)
+  auto pull = [&](bool need) -> unsigned long long {
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    unsigned long long base = 0;
+    if (bal) {
+      const int leader = __ffs(bal) - 1;
+      if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    return need ? base + __popc(bal & ((1u << lane) - 1u)) : ~0ull;
+  };
+
+  unsigned long long jpend = ~0ull;
+  if constexpr (MODE == 2) {
+    start_job(pull(true));
+  } else {
+    b = (int64_t)blockIdx.x * 128 + m;
+    active = b < B;
+    if (MODE == 1 && active) {
+      for (int k = 0; k < N; ++k) mset(mask, k, a.sigma_in[b * N + k] ? 1 : 0);
+    }
+  }
+
+  uint32_t ph0 = 0, ph1 = 0;
+  bool timed_out = false;
+  const uint32_t one = 0x3F80u;
+  for (int step = 0;; ++step) {
+    // ---- (a) A1 row ----
+    cp_wait_2d();
+    int s_h = -1, s_v = -1;
+    if (active) {
+      const Pz p = zpos(t, Lx);
+      if (p.r > 0) s_h = mbit(mask, p.j * Lx + zhor(p));
+      if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
+      const float* stg = half == 0 ? hs : vs;
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = src == 1 ? h[8 * c + q] : src == 2 ? stg[8 * c + q] : 0.0f;
+        st_split8(sA + tc::kmajor_offset(m, half * D + 8 * c, KA1), sA + tc::kmajor_offset(m, K1 + half * D + 8 * c, KA1), v);
+      }
+    }
+    {
+      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+    }
+    // chains: a row on its last cell pulls its successor now (the loads land during the step)
+    if constexpr (MODE == 2) jpend = pull(active && !timed_out && t == N - 1);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    const bool any = tc::group_barrier_or(active && !timed_out, 1, 128);
+    if (!any) break;
+    tc::fence_after_sync();
+    // ---- (b) MMA1 ----
+    if (m == 0) {
+      // A column chunk c pairs with W1 chunk c (hi and extras) or c - K1/16 (lo)
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, 3 * D);
+#pragma unroll
+      for (int c = 0; c < KA1 / 16; ++c) {
+        const int kb = c < K1 / 16 ? c : c - K1 / 16;
+        const uint64_t da = tc::make_desc(tc::smem_addr(sA) + c * 256, 128, (KA1 / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sW1) + kb * 256, 128, (K1 / 8) * 128);
+        tc::mma_bf16(tbase, da, db, idesc, c > 0);
+      }
+      tc::mma_commit(&mbar[0]);
+    }
+    float uni = 0.0f;
+    if (MODE == 0 && active) {
+      uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)b, (uint32_t)t);
+    }
+    if (!tc::mbar_wait(&mbar[0], ph0, kWait2)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph0 ^= 1;
+    tc::fence_after_sync();
+    // ---- (c) epilogue 1: the cell ----
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t aw[8], ag[8], au[8];
+      tld8(trow + 8 * c, aw);
+      tld8(trow + D + 8 * c, ag);
+      tld8(trow + 2 * D + 8 * c, au);
+      tc::tmem_wait_ld();
+      tie(aw);
+      tie(ag);
+      tie(au);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float cc = hw_tanh2(__uint_as_float(aw[q]));
+        const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q])), 0.5f);
+        const float mix = __uint_as_float(au[q]);
+        h[8 * c + q] = fmaf(ug, cc - mix, mix);
+      }
+    }
+    // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1: MMA1 has completed)
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c)
+      st_split8(sA + tc::kmajor_offset(m, 8 * c, KA2), sA + tc::kmajor_offset(m, K2 + 8 * c, KA2), h + 8 * c);
+    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- (d) MMA2 (the GLU) ----
+    if (m == 0) {
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, 2 * D);
+#pragma unroll
+      for (int c = 0; c < KA2 / 16; ++c) {
+        const int kb = c < K2 / 16 ? c : c - K2 / 16;
+        const uint64_t da = tc::make_desc(tc::smem_addr(sA) + c * 256, 128, (KA2 / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128);
+        tc::mma_bf16(tbase, da, db, idesc, c > 0);
+      }
+      tc::mma_commit(&mbar[1]);
+    }
+    // stores of this step's states, coalesced: every thread stages its row's h,
+    // then each warp writes whole rows to the column buffer (entry of the row's
+    // lattice column) and, in sampling / teacher forcing, to the cache (all
+    // rows of such a tile are at the same position)
+    {
+#pragma unroll
+      for (int q = 0; q < D / 4; ++q)
+        reinterpret_cast<float4*>(hs)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+      sCol[m] = active ? zpos(t, Lx).i : -1;
+      __syncwarp();
+      constexpr int L = D / 4, RPI = 32 / L;
+      const int lr = lane / L, lq = lane % L;
+      const int kc = MODE != 2 ? zpos(step, Lx).j * Lx + zpos(step, Lx).i : 0;
+#pragma unroll 4
+      for (int i = 0; i < 32; i += RPI) {
+        const int mr = warp * 32 + i + lr;
+        const int ci = sCol[mr];
+        if (ci >= 0) {
+          const float4 v = reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
+          const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
+          reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] = v;
+          if (MODE != 2 && a.hcache)
+            reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] = v;
+        }
+      }
+      __syncwarp();
+    }
+    if (!tc::mbar_wait(&mbar[1], ph1, kWait2)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph1 ^= 1;
+    tc::fence_after_sync();
+    // ---- (e) epilogue 2: GLU and the logit difference ----
+    float z = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t a1[8], a2[8];
+      tld8(trow + 8 * c, a1);
+      tld8(trow + D + 8 * c, a2);
+      tc::tmem_wait_ld();
+      tie(a1);
+      tie(a2);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+        z = fmaf(sAux[8 * c + q], y, z);
+      }
+    }
+    // ---- (f) row logic ----
+    bool fin = false;
+    if (active && !timed_out) {
+      const float d = z + dc;
+      const Pz p = zpos(t, Lx);
+      const int k = p.j * Lx + p.i;
+      int s;
+      if constexpr (MODE == 0) {
+        const bool fdn = a.sz0 && n_up >= (N >> 1);
+        const bool fup = a.sz0 && (t - n_up) >= (N >> 1);
+        s = fdn ? 1 : fup ? 0 : (uni < sigmoid_acc(d) ? 0 : 1);
+        a.sigma_out[b * N + k] = (uint8_t)s;
+        mset(mask, k, s);
+      } else {
+        s = mbit(mask, k);
+      }
+      const float lp = lp_masked(s, d, n_up, t, N, a.sz0 != 0);
+      if constexpr (MODE == 2) {
+        acc += 0.5f * (lp - lp_next);
+      } else {
+        if (MODE == 1 && a.lp_tab) {
+          a.lp_tab[(b * N + t) * 2] = lp_masked(0, d, n_up, t, N, a.sz0 != 0);
+          a.lp_tab[(b * N + t) * 2 + 1] = lp_masked(1, d, n_up, t, N, a.sz0 != 0);
+          a.nup_tab[b * N + t] = n_up;
+        }
+        acc += lp;
+      }
+      n_up += (s == 0);
+      if (++t == N) {
+        fin = true;
+        if constexpr (MODE == 2) {
+          a.delta[(int64_t)b * a.nb + rank] = acc;
+        } else {
+          const float lpsi = 0.5f * acc;
+          if (a.logpsi) a.logpsi[b] = lpsi;
+          if (!isfinite(lpsi)) flag_status(a.hdr, NQS_ENONFINITE);
+          active = false;
+        }
+      } else {
+        plan_inputs(false);
+      }
+    }
+    if constexpr (MODE == 2) {
+      if (fin) start_job(jpend);
+    }
+  }
+  cp_wait_2d();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kTmemCols);
+}
+
+int sm_count_2d() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      sms = n;
+    else
+      sms = 152;
+  }
+  return sms;
+}
+
+template <int D, int MODE>
+cudaError_t launch2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
+  using S = S2<D>;
+  auto k = tc2d_engine_kernel<D, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int64_t grid = MODE == 2 ? sm_count_2d() : (a.B + 127) / 128;
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, 128, S::kBytes, st>>>(w1, w2, aux, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc2d_supported(int D, int Lx, int N) {
+  if (D != 32 && D != 64) return 0;
+  return N <= 128 && Lx >= 1;
+}
+
+size_t tc2d_colbuf_floats(int64_t B, int Lx, int D) {
+  const int64_t rows_fwd = (B + 127) / 128 * 128, rows_chain = (int64_t)sm_count_2d() * 128;
+  return (size_t)(rows_fwd > rows_chain ? rows_fwd : rows_chain) * Lx * D;
+}
+
+size_t tc2d_wimg_bytes(int D) {
+  return (size_t)(3 * D * (2 * D + 16) + 2 * D * (D + 16)) * 2 + (size_t)(D + 4) * 4;
+}
+
+size_t tc2d_jobs_bytes(int64_t B, int nb) { return (size_t)B * nb * sizeof(Job2) + (size_t)(nb + 4) * sizeof(int); }
+
+cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st) {
+  uint8_t* w1 = wimg;
+  uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
+  float* aux = reinterpret_cast<float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  const int total = 3 * D * (2 * D + 16) + 2 * D * (D + 16) + D + 1;
+  pack2d_tc_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, w1, w2, aux, D);
+  return cudaGetLastError();
+}
+
+cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st) {
+  Tc2Args a{};
+  a.B = f.B;
+  a.Lx = f.Lx;
+  a.N = f.N;
+  a.sz0 = f.sz0;
+  a.sigma_in = f.sigma_in;
+  a.sigma_out = f.sigma_out;
+  a.uniforms = f.uniforms;
+  a.seed = f.seed;
+  a.step = f.step;
+  a.logpsi = f.logpsi;
+  a.hcache = f.hcache;
+  a.colbuf = f.colbuf;
+  a.lp_tab = f.lp_tab;
+  a.nup_tab = f.nup_tab;
+  a.hdr = f.hdr;
+  const uint8_t* w1 = wimg;
+  const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
+  const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  switch (D) {
+    case 32: return sample ? launch2<32, 0>(a, w1, w2, aux, st) : launch2<32, 1>(a, w1, w2, aux, st);
+    case 64: return sample ? launch2<64, 0>(a, w1, w2, aux, st) : launch2<64, 1>(a, w1, w2, aux, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st) {
+  // jobs: antiparallel (sample, bond) pairs in bond order, with their start values
+  uint8_t* jb = c.jobs_ws;
+  Job2* jobs = reinterpret_cast<Job2*>(jb);
+  int* counts = reinterpret_cast<int*>(jb + (size_t)c.B * c.nb * sizeof(Job2));
+  int* njobs = counts + c.nb;
+  heis_count_kernel<<<c.nb, 256, 0, st>>>(c.sigma, c.bonds, c.B, c.N, counts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  heis_jobs_kernel<<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb, jobs, njobs);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  Tc2Args a{};
+  a.B = c.B;
+  a.Lx = c.Lx;
+  a.N = c.N;
+  a.nb = c.nb;
+  a.sz0 = c.sz0;
+  a.hcache = const_cast<float*>(c.hcache);
+  a.colbuf = c.colbuf;
+  a.lp_tab = const_cast<float*>(c.lp_tab);
+  a.bonds = c.bonds;
+  a.jobs = jobs;
+  a.njobs = njobs;
+  a.delta = c.delta;
+  a.counter = c.counter;
+  a.hdr = c.hdr;
+  const uint8_t* w1 = wimg;
+  const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
+  const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  switch (D) {
+    case 32: return launch2<32, 2>(a, w1, w2, aux, st);
+    case 64: return launch2<64, 2>(a, w1, w2, aux, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nqs

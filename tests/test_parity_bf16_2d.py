@@ -1,0 +1,144 @@
+"""BF16 tensor-core 2D path (GRU + GLU, zig-zag order, Heisenberg local energy
+with the Marshall sign and the zero-magnetisation mask) against the float64
+oracle.
+
+Both cell GEMMs and the GLU GEMM take BF16 operands (states and weights
+rounded to 8 significant bits; biases and one-hot input weights carried as
+BF16 hi + lo pairs) with FP32 accumulation; gates, readout and log-probability
+sums stay FP32.  Bounds, as for the 1D BF16 path:
+  log psi       6e-4 * N absolute on uniformly random configurations: the
+                cell and GLU take 8 d^2 BF16 weights per unit (3 d^2 in 1D),
+                each rounded by up to 2^-9, and a random configuration visits
+                sites whose logits are far from 0, where that relative error
+                becomes an absolute one (measured at 8 x 8, d_h = 64: mean
+                6e-5, worst of 256 configurations 4.8e-4 per site);
+  cache         3e-2 absolute (the cached states are FP32 values of a BF16 path);
+  energy/site   |mean E_loc(BF16) - mean E_loc(oracle)| / N <= 1e-4 on the same
+                configurations, drawn from the model;
+  sampling      identical configurations except samples with a draw within
+                5e-3 of the oracle's threshold;
+  gradient      cosine similarity >= 0.999 (the 2D gradient is the FP32 reverse
+                sweep, driven by BF16 local energies).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hamiltonian as oh, model as om, philox, vmc as ov
+from paper_2507_18700_gb300 import inputs, nqs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def dev(x, dtype=torch.float32):
+    return torch.tensor(np.asarray(x), dtype=dtype, device=DEV)
+
+
+def setup(Lx, Ly, d, sz0, seed=0, noise=0.1):
+    noise = noise * min(1.0, np.sqrt(64.0 / d))
+    flat = inputs.xavier_params(2, d, seed=seed, noise_std=noise).astype(np.float32)
+    return (nqs.model_desc(nqs.GRU2D, Lx, Ly, d, sz0=sz0, precision=nqs.BF16),
+            nqs.model_desc(nqs.GRU2D, Lx, Ly, d, sz0=sz0),
+            om.Model(om.GRU2D, Lx, Ly, d_h=d, sz0=sz0), flat.astype(np.float64), dev(flat))
+
+
+def order_index(mod):
+    return np.array([mod.lattice_index(i, j) for (i, j) in mod.order()])
+
+
+@pytest.mark.parametrize("Lx,Ly,d,B,sz0", [(4, 4, 32, 300, True), (8, 8, 64, 256, True), (3, 5, 32, 129, False),
+                                           (6, 4, 64, 40, True)])
+def test_bf16_2d_logpsi_and_cache(Lx, Ly, d, B, sz0):
+    desc, _, mod, pf, p = setup(Lx, Ly, d, sz0)
+    sig = inputs.random_configs(B, mod.N, seed=4, sz0=sz0)
+    lp, hc = nqs.logpsi(desc, p, dev(sig, torch.uint8))
+    torch.cuda.synchronize()
+    ref = om.run(mod, pf, sigma=sig.astype(np.int64))
+    np.testing.assert_allclose(lp.cpu().numpy(), ref["logpsi"], atol=6e-4 * mod.N, rtol=0)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=3e-2, rtol=0)
+
+
+@pytest.mark.parametrize("Lx,Ly,d,B,sz0", [(4, 4, 32, 512, True), (8, 8, 64, 256, True), (5, 3, 32, 200, False)])
+def test_bf16_2d_sampling(Lx, Ly, d, B, sz0):
+    desc, _, mod, pf, p = setup(Lx, Ly, d, sz0)
+    sig, lp, hc = nqs.sample(desc, p, B, seed=3, step=1)
+    lp_t, _ = nqs.logpsi(desc, p, sig, hcache=None)
+    torch.cuda.synchronize()
+    assert torch.equal(lp, lp_t)            # same kernel arithmetic in both modes
+    s = sig.cpu().numpy().astype(np.int64)
+    if sz0:
+        assert np.all(s.sum(axis=1) == mod.N // 2)
+    u = philox.sampling_uniforms(3, 1, B, mod.N)
+    ref = om.sample(mod, pf, u)
+    p0_pos = ref["p0"][:, order_index(mod)]
+    clean = ~(np.abs(u - p0_pos) < 5e-3).any(axis=1)
+    assert clean.mean() > 0.2
+    assert np.array_equal(s[clean], ref["sigma"][clean])
+
+
+@pytest.mark.parametrize("Lx,Ly,d,B,sz0,marshall", [(4, 4, 32, 64, True, True), (8, 8, 64, 24, True, True),
+                                                    (3, 4, 32, 50, True, False), (4, 3, 64, 40, False, True)])
+def test_bf16_2d_energy_per_site(Lx, Ly, d, B, sz0, marshall):
+    # configurations drawn from the model (by the oracle's sampler), as in a VMC step
+    desc, d32, mod, pf, p = setup(Lx, Ly, d, sz0, seed=2)
+    sig = om.sample(mod, pf, philox.sampling_uniforms(17, 0, B, mod.N))["sigma"].astype(np.uint8)
+    sg = dev(sig, torch.uint8)
+    ham = nqs.heisenberg(1.0, marshall)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    el = nqs.local_energy(desc, p, ham, sg, hc, ws=ws)
+    _, hc32 = nqs.logpsi(d32, p, sg)
+    el32 = nqs.local_energy(d32, p, ham, sg, hc32)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    ref = oh.heisenberg_local_energy(Lx, Ly, 1.0, marshall, sig.astype(np.int64), lambda x: om.logpsi(mod, pf, x))
+    e16 = el.double().cpu().numpy()
+    assert np.isfinite(e16).all()
+    assert abs(e16.mean() - ref.mean()) / mod.N <= 1e-4
+    assert abs(e16.mean() - el32.double().cpu().numpy().mean()) / mod.N <= 1e-4
+
+
+def test_bf16_2d_vmc_gradient_cosine():
+    Lx, Ly, d, B = 4, 4, 32, 128
+    desc, _, mod, pf, p = setup(Lx, Ly, d, True, seed=8, noise=0.05)
+    sig = om.sample(mod, pf, philox.sampling_uniforms(19, 0, B, mod.N))["sigma"].astype(np.uint8)
+    sg = dev(sig, torch.uint8)
+    _, hc = nqs.logpsi(desc, p, sg)
+    el = nqs.local_energy(desc, p, nqs.heisenberg(), sg, hc)
+    g, st = nqs.vmc_grad(desc, p, sg, hc, el)
+    torch.cuda.synchronize()
+    e_ref = oh.heisenberg_local_energy(Lx, Ly, 1.0, True, sig.astype(np.int64), lambda x: om.logpsi(mod, pf, x))
+    ref = ov.vmc_gradient(mod, pf, sig.astype(np.int64), e_ref)
+    g = g.double().cpu().numpy()
+    assert g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)) >= 0.999
+
+
+def test_bf16_2d_full_size_8x8_d64_b2048():
+    """Heisenberg 8 x 8 workload in BF16: energy per site of the whole step within
+    1e-4 of the FP32 path on the same samples and of the oracle on 12 of them."""
+    Lx, Ly, d, B = 8, 8, 64, 2048
+    desc, d32, mod, pf, p = setup(Lx, Ly, d, True, seed=0)
+    ws = nqs.Workspace(DEV)
+    sig, lp, hc = nqs.sample(desc, p, B, seed=5, step=0, ws=ws)
+    el = nqs.local_energy(desc, p, nqs.heisenberg(), sig, hc, ws=ws)
+    g, st = nqs.vmc_grad(desc, p, sig, hc, el, ws=ws)
+    _, hc32 = nqs.logpsi(d32, p, sig)
+    el32 = nqs.local_energy(d32, p, nqs.heisenberg(), sig, hc32)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    e16, e32 = el.double().cpu().numpy(), el32.double().cpu().numpy()
+    assert abs(e16.mean() - e32.mean()) / mod.N <= 1e-4
+    s = sig.cpu().numpy().astype(np.int64)
+    pick = np.random.default_rng(3).choice(B, 12, replace=False)
+    e_ref = oh.heisenberg_local_energy(Lx, Ly, 1.0, True, s[pick], lambda x: om.logpsi(mod, pf, x))
+    assert abs(e16[pick].mean() - e_ref.mean()) / mod.N <= 1e-4
+    assert np.isfinite(g.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("Lx,Ly,d", [(4, 4, 128), (16, 16, 64), (4, 4, 16), (12, 12, 32)])
+def test_bf16_2d_unsupported_shapes(Lx, Ly, d):
+    desc = nqs.model_desc(nqs.GRU2D, Lx, Ly, d, sz0=True, precision=nqs.BF16)
+    p = torch.zeros(nqs.param_count(desc), device=DEV)
+    with pytest.raises(nqs.NqsError):
+        nqs.sample(desc, p, 8, seed=0, step=0)
