@@ -261,7 +261,8 @@ struct S2 {
   static constexpr int kVS = kHS + 128 * HS * 4;           // [128 x HS] f32: vertical-input copy
   static constexpr int kAux = kVS + 128 * HS * 4;          // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kCol = kAux + (D + 4) * 4;          // 128 ints: column-buffer entry of each row's new state
-  static constexpr int kBar = kCol + 128 * 4;              // 2 mbarriers
+  static constexpr int kPos = kCol + 128 * 4;              // 128 ints: (i, j, r) of every zig-zag position
+  static constexpr int kBar = kPos + 128 * 4;              // 2 mbarriers
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -303,6 +304,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   float* sVS = reinterpret_cast<float*>(sm + S::kVS);
   float* sAux = reinterpret_cast<float*>(sm + S::kAux);
   int* sCol = reinterpret_cast<int*>(sm + S::kCol);
+  int* sPos = reinterpret_cast<int*>(sm + S::kPos);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
 
@@ -311,6 +313,10 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 128)
     reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
   for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += 128) {
+    const Pz p = zpos(t, a.Lx);
+    sPos[t] = p.i | (p.j << 8) | (p.r << 16);
+  }
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -328,12 +334,20 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   const int Lx = a.Lx, N = a.N;
   const int64_t B = a.B;
   const float dc = sAux[D];
+  auto P = [&](int t) -> Pz {        // zig-zag position t (table lookup)
+    const int v = sPos[t];
+    Pz p;
+    p.i = v & 255;
+    p.j = (v >> 8) & 255;
+    p.r = v >> 16;
+    return p;
+  };
   float* hs = sHS + m * S::HS;       // this row's horizontal-input copy
   float* vs = sVS + m * S::HS;       // this row's vertical-input copy
 
   // row state
   int64_t b = 0;
-  int t = 0, pa = -1, rank = 0, n_up = 0;
+  int t = 0, pa = -1, rank = 0, n_up = 0, bsa = -1, bsb = -1;   // chains: exchanged lattice sites
   float acc = 0.0f, lp_next = 0.0f;
   bool active = false;
   uint64_t mask[2] = {0ull, 0ull};
@@ -350,7 +364,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   auto fetch_orig = [&](float* dst, int k) { fetch(dst, a.hcache + (b * N + k) * D); };
   // Inputs of the cell at position t (after the row moved there): sources and copies.
   auto plan_inputs = [&](bool fresh) {
-    const Pz p = zpos(t, Lx);
+    const Pz p = P(t);
     hsrc = 0;
     vsrc = 0;
     bool copies = false;
@@ -380,8 +394,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     if (copies) cp_commit_2d();
     if constexpr (MODE == 2) {
       const int k = p.j * Lx + p.i;
-      const int4 bd = a.bonds[rank];
-      const int so = mbit(mask, k) ^ ((k == bd.x || k == bd.y) ? 1 : 0);   // original spin at k
+      const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
       lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
     }
   };
@@ -395,7 +408,10 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     const Job2 jb = a.jobs[j];
     b = jb.b;
     rank = jb.rank;
-    pa = a.bonds[rank].z;
+    const int4 bd = a.bonds[rank];
+    bsa = bd.x;
+    bsb = bd.y;
+    pa = bd.z;
     t = pa + 1;
     acc = jb.acc0;
     n_up = jb.nup0;
@@ -404,21 +420,25 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     active = true;
     plan_inputs(true);
   };
-  // warp-aggregated pull of one job for every lane with `need` (all lanes call it)
-  auto pull = [&](bool need) -> unsigned long long {
-    const unsigned bal = __ballot_sync(0xffffffffu, need);
-    unsigned long long base = 0;
-    if (bal) {
-      const int leader = __ffs(bal) - 1;
-      if (lane == leader) base = atomicAdd(a.counter, (unsigned long long)__popc(bal));
-      base = __shfl_sync(0xffffffffu, base, leader);
-    }
-    return need ? base + __popc(bal & ((1u << lane) - 1u)) : ~0ull;
+  // warp-aggregated pull of one job for every lane with `need`, in two halves
+  // called by all lanes: the atomic is issued first and its result is read
+  // later, so its round trip overlaps the step
+  unsigned pbal = 0;
+  unsigned long long pbase = 0;
+  auto pull_issue = [&](bool need) {
+    pbal = __ballot_sync(0xffffffffu, need);
+    if (pbal && lane == __ffs(pbal) - 1) pbase = atomicAdd(a.counter, (unsigned long long)__popc(pbal));
+  };
+  auto pull_take = [&]() -> unsigned long long {
+    if (!pbal) return ~0ull;
+    const unsigned long long base = __shfl_sync(0xffffffffu, pbase, __ffs(pbal) - 1);
+    return (pbal >> lane) & 1u ? base + __popc(pbal & ((1u << lane) - 1u)) : ~0ull;
   };
 
   unsigned long long jpend = ~0ull;
   if constexpr (MODE == 2) {
-    start_job(pull(true));
+    pull_issue(true);
+    start_job(pull_take());
   } else {
     b = (int64_t)blockIdx.x * 128 + m;
     active = b < B;
@@ -435,7 +455,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     cp_wait_2d();
     int s_h = -1, s_v = -1;
     if (active) {
-      const Pz p = zpos(t, Lx);
+      const Pz p = P(t);
       if (p.r > 0) s_h = mbit(mask, p.j * Lx + zhor(p));
       if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
     }
@@ -458,7 +478,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
     }
     // chains: a row on its last cell pulls its successor now (the loads land during the step)
-    if constexpr (MODE == 2) jpend = pull(active && !timed_out && t == N - 1);
+    if constexpr (MODE == 2) pull_issue(active && !timed_out && t == N - 1);
     tc::fence_async_smem();
     tc::fence_before_sync();
     const bool any = tc::group_barrier_or(active && !timed_out, 1, 128);
@@ -536,11 +556,11 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
       for (int q = 0; q < D / 4; ++q)
         reinterpret_cast<float4*>(hs)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
-      sCol[m] = active ? zpos(t, Lx).i : -1;
+      sCol[m] = active ? P(t).i : -1;
       __syncwarp();
       constexpr int L = D / 4, RPI = 32 / L;
       const int lr = lane / L, lq = lane % L;
-      const int kc = MODE != 2 ? zpos(step, Lx).j * Lx + zpos(step, Lx).i : 0;
+      const int kc = MODE != 2 ? P(step).j * Lx + P(step).i : 0;
 #pragma unroll 4
       for (int i = 0; i < 32; i += RPI) {
         const int mr = warp * 32 + i + lr;
@@ -581,7 +601,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     bool fin = false;
     if (active && !timed_out) {
       const float d = z + dc;
-      const Pz p = zpos(t, Lx);
+      const Pz p = P(t);
       const int k = p.j * Lx + p.i;
       int s;
       if constexpr (MODE == 0) {
@@ -620,6 +640,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
     }
     if constexpr (MODE == 2) {
+      jpend = pull_take();
       if (fin) start_job(jpend);
     }
   }
