@@ -324,11 +324,15 @@ def run_gpu(args, w):
         d = w["d"]
         mufu = sum(chosen["cells"]) * 3 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
         mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
+        # DRAM bytes of one chain launch from an ncu capture of the 1D chain kernel
+        # at B = 1024 (profiles/chain_tc1d_tfim_n100_d64_bf16.md): 26,543,616
+        # bytes read, 0 written, i.e. the prefix cache read once; scaled by B
+        traffic = (26543616 * B / 1024.0) if (w["cell"] == 1 and w["d"] == 64 and N == 100) else None
         roof = {"bound": "tensor",
                 "kernel": "nqs_local_energy (prefix-cached %s chains, tcgen05 BF16)"
                           % ("TFIM" if w["cell"] == 1 else "Heisenberg"),
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src,
+                "traffic": traffic, "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src,
                 "epilogue_sfu": {"achieved": mufu, "peak": mufu_peak, "unit": "Tops/s",
                                  "frac": mufu / mufu_peak,
                                  "note": "3 MUFU ops (hardware tanh) per hidden unit per cell (two sigmoids, one tanh); "
