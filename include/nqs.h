@@ -266,8 +266,13 @@ void nqs_set_autotune(int on);
 /* Pin the tile variant of every tensor-core kernel: variant >= 0 selects
  * that variant (a kernel with fewer variants takes its last one), bypassing
  * the autotuner and its cache; variant < 0 returns to normal selection.
- * Variants differ only in threads per row (1, 2, 4) and compute bitwise the
- * same results; this is for timing and testing them one by one. */
+ * Variants differ in threads per row (1, 2, 4) and, for sampling, teacher
+ * forcing and the reverse sweep, in rows per 128-lane tile (128, or 64 to put
+ * more SMs on a small batch).  Per-sample results (samples, log psi, cache,
+ * local energies) are bitwise the same in every variant; the gradient, a sum
+ * over samples grouped by tile, is bitwise the same for the same rows per tile
+ * and equal to rounding otherwise.  This is for timing and testing them one
+ * by one. */
 void nqs_set_tile_variant(int variant);
 
 /* Copy the workspace status word to *device_status (an nqs_status) after

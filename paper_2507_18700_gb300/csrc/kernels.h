@@ -147,11 +147,13 @@ struct Tc1Args {
   float* delta;              // chains
   unsigned long long* counter;
   WsHeader* hdr;
+  int rows;                  // sampling / teacher forcing: rows per 128-lane tile (128 or 64; set by the launcher)
 };
 
 struct TcBpttArgs {
   int64_t B;
   int N, P;
+  int rows;                  // rows per 128-lane tile (128 or 64; set by the launcher)
   const uint8_t* sigma;
   const float* hcache;
   const float* weights;

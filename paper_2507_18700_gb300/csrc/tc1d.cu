@@ -258,8 +258,8 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     const long long j = jb[m];
     if (j >= 0) start_job(j, job_src(j));
   } else {
-    b = ((int64_t)blockIdx.x * GROUPS + g) * 128 + m;
-    active = b < B;
+    b = ((int64_t)blockIdx.x * GROUPS + g) * a.rows + m;
+    active = m < a.rows && b < B;
   }
 
   // Ping-pong (two tiles): the tiles take turns in the MUFU-bound epilogue,
@@ -495,12 +495,12 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
         __syncwarp();
         constexpr int L = DU / 4, RPI = 32 / L;   // lanes per row segment, rows per store
         const int lr = lane / L, lq = lane % L, m0 = (wt % 4) * 32;
-        const int64_t b0 = ((int64_t)blockIdx.x * GROUPS + g) * 128;
+        const int64_t b0 = ((int64_t)blockIdx.x * GROUPS + g) * a.rows;
 #pragma unroll 4
         for (int i = 0; i < 32; i += RPI) {
           const int mr = m0 + i + lr;
           const int64_t br = b0 + mr;
-          if (br < B)
+          if (mr < a.rows && br < B)
             reinterpret_cast<float4*>(a.hcache + (br * N + pstep) * D + u0)[lq] =
                 reinterpret_cast<const float4*>(stage + (g * 128 + mr) * S::HS + u0)[lq];
         }
@@ -666,8 +666,8 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
   const float dc = small[12 * D] - small[12 * D + 1];
   const int N = a.N;
-  const int64_t b = (int64_t)blockIdx.x * 128 + m;
-  const bool valid = b < a.B;
+  const int64_t b = (int64_t)blockIdx.x * a.rows + m;
+  const bool valid = m < a.rows && b < a.B;
   const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
   // this thread's units of the two state rows
   float* hrow[2] = {sH + (0 * 128 + m) * S::HS + u0, sH + (1 * 128 + m) * S::HS + u0};
@@ -1008,7 +1008,7 @@ cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, c
     const int64_t need = (jobs + 255) / 256;
     if (grid > need) grid = need;
   } else {
-    grid = (a.B + 128 * GROUPS - 1) / (128 * GROUPS);
+    grid = (a.B + (int64_t)a.rows * GROUPS - 1) / ((int64_t)a.rows * GROUPS);
   }
   if (grid < 1) grid = 1;
   k<<<(unsigned)grid, 128 * GROUPS * SPLIT, S::kBytes, st>>>(img, wimg, a);
@@ -1081,24 +1081,31 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
   if (mode == 2) {
     // chains: 1 or 2 threads per row (the work counter is reset before every run)
     auto reset = [&]() { return cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st); };
+    Tc1Args c = a;
+    c.rows = 128;
     auto run = [&](int v) {
-      if (v == 1 && D >= 32) return launch_tc<D, 2, 2, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
-      return launch_tc<D, 2, 2, 1>(a, img, wimg, st);
+      if (v == 1 && D >= 32) return launch_tc<D, 2, 2, (D >= 32 ? 2 : 1)>(c, img, wimg, st);
+      return launch_tc<D, 2, 2, 1>(c, img, wimg, st);
     };
     return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
   }
-  // sampling / teacher forcing: 1, 2 or 4 threads per row
+  // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128 or 64
+  // rows per tile (half-filled tiles put twice as many SMs on a small batch)
+  const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
   auto run = [&](int v) {
+    Tc1Args b = a;
+    b.rows = v < ns ? 128 : 64;
+    const int sv = v % ns;
     if (mode == 0) {
-      if (v == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(a, img, wimg, st);
-      if (v == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
-      return launch_tc<D, 0, 1, 1>(a, img, wimg, st);
+      if (sv == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
+      if (sv == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
+      return launch_tc<D, 0, 1, 1>(b, img, wimg, st);
     }
-    if (v == 2 && D >= 64) return launch_tc<D, 1, 1, (D >= 64 ? 4 : 1)>(a, img, wimg, st);
-    if (v == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(a, img, wimg, st);
-    return launch_tc<D, 1, 1, 1>(a, img, wimg, st);
+    if (sv == 2 && D >= 64) return launch_tc<D, 1, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
+    if (sv == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
+    return launch_tc<D, 1, 1, 1>(b, img, wimg, st);
   };
-  return tuned_launch(mode, D, a.N, a.B, D >= 64 ? 3 : (D >= 32 ? 2 : 1), run, none, st);
+  return tuned_launch(mode, D, a.N, a.B, 2 * ns, run, none, st);
 }
 
 }  // namespace
@@ -1117,7 +1124,9 @@ void tc1d_set_variant(int v) {
 }
 
 constexpr int kReadoutGradBlocks = 304;
-int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 127) / 128) + kReadoutGradBlocks; }
+// rows of per-CTA partial gradients: the reverse sweep's CTAs (at most one per
+// 64 samples) and then the readout-gradient blocks
+int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 63) / 64) + kReadoutGradBlocks; }
 
 template <int D, int SPLIT>
 cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt,
@@ -1126,25 +1135,35 @@ cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_
   auto k = tc1d_bptt_kernel<D, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  const int grid = (int)((a.B + 127) / 128);
+  const int grid = (int)((a.B + a.rows - 1) / a.rows);
   k<<<grid, 128 * SPLIT, S::kBytes, st>>>(img, w3, wt, a);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, cudaStream_t st) {
-  // reverse sweep: 1, 2 or 4 threads per row, picked by the autotuner
+  // reverse sweep: 1, 2 or 4 threads per row, times 128 or 64 rows per tile,
+  // picked by the autotuner.  A run writes one partial row per CTA (at most
+  // B/64 rows) and the reduction sums all rows, so the sweep's rows are
+  // cleared before every run: an autotuning trial with 64 rows per tile
+  // leaves rows that a final run with 128 rows per tile would not overwrite.
+  const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
   auto run = [&](int v) {
-    if (v == 2 && D >= 64) return launch_tc_bptt_v<D, (D >= 64 ? 4 : 1)>(a, img, w3, wt, st);
-    if (v == 1 && D >= 32) return launch_tc_bptt_v<D, (D >= 32 ? 2 : 1)>(a, img, w3, wt, st);
-    return launch_tc_bptt_v<D, 1>(a, img, w3, wt, st);
+    TcBpttArgs b = a;
+    b.rows = v < ns ? 128 : 64;
+    const int sv = v % ns;
+    if (sv == 2 && D >= 64) return launch_tc_bptt_v<D, (D >= 64 ? 4 : 1)>(b, img, w3, wt, st);
+    if (sv == 1 && D >= 32) return launch_tc_bptt_v<D, (D >= 32 ? 2 : 1)>(b, img, w3, wt, st);
+    return launch_tc_bptt_v<D, 1>(b, img, w3, wt, st);
   };
-  auto none = []() { return cudaSuccess; };
-  cudaError_t e = tuned_launch(3, D, a.N, a.B, D >= 64 ? 3 : (D >= 32 ? 2 : 1), run, none, st);
+  const int rows_max = (int)((a.B + 63) / 64);
+  auto clear = [&]() {
+    return cudaMemsetAsync(a.partial, 0, (size_t)rows_max * a.P * sizeof(float), st);
+  };
+  cudaError_t e = tuned_launch(3, D, a.N, a.B, 2 * ns, run, clear, st);
   if (e != cudaSuccess) return e;
-  const int grid = (int)((a.B + 127) / 128);
   tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
-                                                                   grid);
+                                                                   rows_max);
   return cudaGetLastError();
 }
 
