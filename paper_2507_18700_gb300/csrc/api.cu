@@ -62,7 +62,7 @@ int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, w, w2, a, b, c, e, f, g, total;
+  size_t img, w, w2, a, b, c, e, f, g, h, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
@@ -105,6 +105,16 @@ Layout layout(const Dims& d, int64_t B, int op) {
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
+      if (use_tc2d(d)) {
+        L.a = take((size_t)tc2d_grad_partial_rows(B, d.N) * d.P * sizeof(float));  // partial gradients
+        L.b = take((size_t)B * sizeof(float));                                     // weights
+        L.c = take((size_t)B * d.Lx * d.d * sizeof(float));                        // vertical carries
+        L.e = take(tc2d_grad_image_bytes(B, d.N, d.d, 0));                         // G1 images
+        L.f = take(tc2d_grad_image_bytes(B, d.N, d.d, 1));                         // G2 images
+        L.g = take(tc2d_grad_image_bytes(B, d.N, d.d, 2));                         // GLU outputs
+        L.h = take(tc2d_grad_image_bytes(B, d.N, d.d, 3));                         // readout gradients
+        break;
+      }
       if (use_tc(d)) {
         L.a = take((size_t)tc1d_bptt_partial_rows(B) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                 // weights
@@ -456,6 +466,34 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.partial = partial;
     t.hdr = static_cast<WsHeader*>(ws);
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
+  }
+  if (use_tc2d(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    const int rows = tc2d_grad_partial_rows(B, d.N);
+    if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
+    Tc2Grad g{};
+    g.B = B;
+    g.Lx = d.Lx;
+    g.Ly = d.Ly;
+    g.N = d.N;
+    g.P = (int)d.P;
+    g.sz0 = d.sz0;
+    g.sigma = sigma;
+    g.hcache = hcache;
+    g.weights = weights;
+    g.ccarry = at<float>(ws, L.c);
+    g.g1img = at<uint8_t>(ws, L.e);
+    g.g2img = at<uint8_t>(ws, L.f);
+    g.yimg = at<float>(ws, L.g);
+    g.dzimg = at<float>(ws, L.h);
+    g.partial = partial;
+    g.hdr = static_cast<WsHeader*>(ws);
+    // the images' padding columns (gate rows beyond 3 d / 2 d) must read as zero
+    if (cudaMemsetAsync(g.g1img, 0, tc2d_grad_image_bytes(B, d.N, d.d, 0), st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(g.g2img, 0, tc2d_grad_image_bytes(B, d.N, d.d, 1), st) != cudaSuccess) return NQS_ECUDA;
+    if (tc2d_grad(g, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
   }
   if (d.cell == NQS_GRU2D) {

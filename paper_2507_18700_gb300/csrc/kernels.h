@@ -119,6 +119,26 @@ cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st
 cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st);
 cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st);
 
+// BF16 tensor-core 2D reverse sweep (tc2d_grad.cu)
+struct Tc2Grad {
+  int64_t B;
+  int Lx, Ly, N, P, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;
+  float* ccarry;             // [B, Lx, d] vertical carries
+  uint8_t* g1img;            // tc2d_grad_image_bytes(.., 0), zeroed
+  uint8_t* g2img;            // tc2d_grad_image_bytes(.., 1), zeroed
+  float* yimg;               // tc2d_grad_image_bytes(.., 2)
+  float* dzimg;              // tc2d_grad_image_bytes(.., 3)
+  float* partial;            // [tc2d_grad_partial_rows(B, N), P], zeroed
+  WsHeader* hdr;
+};
+int tc2d_wgrad_grid(int64_t B, int N);
+int tc2d_grad_partial_rows(int64_t B, int N);
+size_t tc2d_grad_image_bytes(int64_t B, int N, int D, int which);
+cudaError_t tc2d_grad(const Tc2Grad& g, const uint8_t* wimg, int D, cudaStream_t st);
+
 size_t gru2d_img_floats(int D);
 int gru2d_supported(int D);
 size_t gru2d_bptt_scratch_floats(int D, int64_t B);

@@ -1,0 +1,92 @@
+// Helpers shared by the BF16 tensor-core 2D kernels (tc2d.cu, tc2d_grad.cu):
+// hi / lo BF16 splitting of FP32 states, tcgen05 loads, cp.async, zig-zag
+// geometry (Sec. II, Fig. 1(b)) and the zero-magnetisation mask.
+#pragma once
+
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace nqs {
+namespace tc2dh {
+
+constexpr uint32_t kWait2 = 1u << 26;   // mbarrier polls before giving up
+
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float hw_tanh2(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&p);
+}
+// hi and lo BF16 pairs of two values: hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16(a, b);
+  lo = pack_bf16(a - bf16_round(a), b - bf16_round(b));
+}
+// 8 values as hi / lo 16-byte rows of an operand
+__device__ __forceinline__ void st_split8(uint8_t* dhi, uint8_t* dlo, const float* v) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) split_bf16(v[2 * q], v[2 * q + 1], h[q], l[q]);
+  *reinterpret_cast<uint4*>(dhi) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(dlo) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void cp_async16_2d(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit_2d() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_2d() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ float ldg_f32_v(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];\n" : "=f"(v) : "l"(p));
+  return v;
+}
+
+// 8 consecutive 32-bit TMEM columns of this thread's lane (warp-collective).
+__device__ __forceinline__ void tld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+// Ties loaded registers to the preceding wait: no use is scheduled above it.
+template <int NW>
+__device__ __forceinline__ void tie(uint32_t (&r)[NW]) {
+#pragma unroll
+  for (int q = 0; q < NW; ++q) asm volatile("" : "+r"(r[q]));
+}
+
+// Zig-zag geometry (Sec. II, Fig. 1(b)), as in the FP32 path.
+struct Pz {
+  int i, j, r;
+};
+__device__ __forceinline__ Pz zpos(int t, int Lx) {
+  Pz p;
+  p.j = t / Lx;
+  p.r = t - p.j * Lx;
+  p.i = (p.j & 1) ? Lx - 1 - p.r : p.r;
+  return p;
+}
+__device__ __forceinline__ int zhor(const Pz& p) { return (p.j & 1) ? p.i + 1 : p.i - 1; }
+__device__ __forceinline__ int zsnake(int i, int j, int Lx) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
+
+__device__ __forceinline__ int mbit(const uint64_t (&m)[2], int k) { return (int)((m[k >> 6] >> (k & 63)) & 1ull); }
+__device__ __forceinline__ void mset(uint64_t (&m)[2], int k, int s) {
+  const uint64_t b = 1ull << (k & 63);
+  m[k >> 6] = s ? (m[k >> 6] | b) : (m[k >> 6] & ~b);
+}
+
+// Zero-magnetisation mask (forced outcomes have log p = 0 / -inf).
+__device__ __forceinline__ float lp_masked(int s, float d, int n_up, int n_done, int N, bool sz0) {
+  if (sz0) {
+    const int half = N >> 1;
+    if (n_up >= half) return s == 1 ? 0.0f : -INFINITY;
+    if (n_done - n_up >= half) return s == 0 ? 0.0f : -INFINITY;
+  }
+  return log_prob(s, d);
+}
+
+}  // namespace tc2dh
+}  // namespace nqs

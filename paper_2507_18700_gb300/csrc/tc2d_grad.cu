@@ -1,0 +1,678 @@
+// BF16 tensor-core reverse sweep of the 2D GRU wave function with its GLU head
+// (App. A): d/dtheta sum_b w_b log psi_b over the zig-zag order (Sec. II),
+// with the zero-magnetisation mask, for d_h in {32, 64} and N <= 128.
+//
+// Phase 1, tc2d_sweep_kernel: one CTA = one tile of 128 samples (= TMEM
+// lanes), one thread per sample; every row is at the same position, sites
+// t = N-1 .. 0.  Per cell, from the cached states:
+//   MMA1: [hi(h') | extras | lo(h')] x W1^T   (the forward's gate pre-activations)
+//   MMA2: [hi(h)  | extras | lo(h)]  x W2^T   (the forward's GLU pre-activations)
+//   epilogue: y, the logit difference d, dz = c_b (onehot(s) - p0) (0 at a
+//             forced site of the mask), G2 = [dy W_1-path | dy W_2-path]
+//   MMA_g: dh = G2 W2           (W2 read as an MN-major operand)
+//   epilogue: back through h = u h~ + (1 - u) U_mix h' into G1 = [da_W | da_g | d(U_mix h')]
+//   MMA_b: dh' = G1 W1          (W1 read as an MN-major operand)
+// dh' splits into the horizontal predecessor's carry (registers) and the
+// vertical predecessor's (a per-sample column carry buffer in global memory).
+// The forward images hold W_g and W_2 halved (their sigmoids are one tanh);
+// G1 and G2 carry those blocks doubled, so both products are exact.  G1, G2
+// go to global memory as ready-made 128-row MMA operand images, and dz and y
+// as sample-minor arrays.
+// Phase 2, tc2d_wgrad_kernel: split-K over the (tile, site) images, a CTA
+// accumulates dW1 += G1^T X1 and dW2 += G2^T X2 in TMEM (X1 = [h' | 1 |
+// one-hots], X2 = [h | 1], built from the cache; both operands MN-major), so
+// the ones and one-hot columns give the bias and one-hot-weight gradients.
+// Phase 3, tc2d_readout_grad_kernel: dU_out and dc from dz and y.
+#include "tc2d_common.cuh"
+
+namespace nqs {
+
+namespace {
+
+using namespace tc2dh;
+
+template <int D>
+struct G2S {
+  static constexpr int K1 = 2 * D + 16, K2 = D + 16;       // weight image columns (as in the forward)
+  static constexpr int KA1 = K1 + 2 * D, KA2 = K2 + D;     // A operand columns: [hi | extras | lo]
+  static constexpr int GW1 = 4 * D >= 128 ? 4 * D : 128;  // G1 image width (whole 128-row M halves)
+  static constexpr int GW2 = 2 * D >= 128 ? 2 * D : 128;  // G2 image width
+  static constexpr int kW1 = 0;                            // [3D x K1] bf16
+  static constexpr int kW2 = kW1 + 3 * D * K1 * 2;         // [2D x K2] bf16
+  static constexpr int kA1 = kW2 + 2 * D * K2 * 2;         // [128 x KA1]; G1 [128 x 3D] aliases it
+  static constexpr int kA2 = kA1 + 128 * KA1 * 2;          // [128 x KA2]; G2 [128 x 2D] aliases it
+  static constexpr int kAux = kA2 + 128 * KA2 * 2;         // D + 4 floats: U_0 - U_1, c_0 - c_1
+  static constexpr int kBar = kAux + (D + 4) * 4;          // 3 mbarriers
+  static constexpr int kSlot = kBar + 32;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+  // TMEM columns: MMA1 [0, 3D), MMA2 and later MMA_b [3D, 5D), MMA_g [5D, 6D)
+  static constexpr uint32_t c1 = 0, c2 = 3 * D, cg = 5 * D;
+  static_assert(6 * D <= 512, "TMEM budget");
+};
+
+struct Sweep2Args {
+  int64_t B;
+  int Lx, Ly, N, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;
+  float* ccarry;             // [B, Lx, d] vertical carries (zeroed)
+  uint8_t* g1img;            // [tiles, N] images of 128 x GW1 bf16 (padding columns zeroed)
+  uint8_t* g2img;            // [tiles, N] images of 128 x GW2 bf16 (padding columns zeroed)
+  float* yimg;               // [tiles, N, d, 128]
+  float* dzimg;              // [tiles, N, 128]
+  WsHeader* hdr;
+};
+
+// 16 values of an FP32 row (16-byte aligned) or zeros
+__device__ __forceinline__ void ld16(const float* src, bool ok, float (&v)[16]) {
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 x = reinterpret_cast<const float4*>(src)[q];
+      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = 0.0f;
+  }
+}
+
+__device__ __forceinline__ void st_bf16_8(uint8_t* dst, const float* v) {
+  *reinterpret_cast<uint4*>(dst) = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                              pack_bf16(v[6], v[7]));
+}
+
+template <int D>
+__global__ void __launch_bounds__(128, 1)
+tc2d_sweep_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
+                  Sweep2Args a) {
+  using S = G2S<D>;
+  constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sW1 = sm + S::kW1;
+  uint8_t* sW2 = sm + S::kW2;
+  uint8_t* sA1 = sm + S::kA1;
+  uint8_t* sA2 = sm + S::kA2;
+  float* sAux = reinterpret_cast<float*>(sm + S::kAux);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += 128)
+    reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 128)
+    reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
+  for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 3; ++q) tc::mbar_init(&mbar[q], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int m = threadIdx.x;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int Lx = a.Lx, Ly = a.Ly, N = a.N;
+  const int64_t tile = blockIdx.x;
+  const int64_t b = tile * 128 + m;
+  const bool valid = b < a.B;
+  const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+  const float dc = sAux[D];
+  const uint8_t* sg = a.sigma + (valid ? b : 0) * N;
+  const float* hc = a.hcache + (valid ? b : 0) * (int64_t)N * D;
+  float* cc = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D;
+  int n_up = 0;                      // up spins before the current position
+  if (valid)
+    for (int k = 0; k < N; ++k) n_up += sg[k] ? 0 : 1;
+  float carry[D];                    // dlog psi / dh_t from the horizontal successor
+#pragma unroll
+  for (int u = 0; u < D; ++u) carry[u] = 0.0f;
+  uint32_t ph[3] = {0, 0, 0};
+  bool timed_out = false;
+  const uint32_t one = 0x3F80u;
+  auto wait = [&](int q) {
+    if (!tc::mbar_wait(&mbar[q], ph[q], kWait2)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph[q] ^= 1;
+    tc::fence_after_sync();
+  };
+  auto sync_tc = [&]() {
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+
+  for (int t = N - 1; t >= 0; --t) {
+    const Pz p = zpos(t, Lx);
+    const int k = p.j * Lx + p.i;
+    const int s_k = valid ? (sg[k] ? 1 : 0) : 0;
+    n_up -= (s_k == 0);
+    const int s_h = p.r > 0 ? (valid ? (sg[p.j * Lx + zhor(p)] ? 1 : 0) : 0) : -1;
+    const int s_v = p.j > 0 ? (valid ? (sg[(p.j - 1) * Lx + p.i] ? 1 : 0) : 0) : -1;
+    // ---- A1 = [hi(h_hor) hi(h_ver) | extras | lo(h_hor) lo(h_ver)], A2 = [hi(h) | 1 1 | lo(h)] ----
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
+      const float* src = hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+#pragma unroll
+      for (int c = 0; c < D / 16; ++c) {
+        float v[16];
+        ld16(src + 16 * c, ok, v);
+        st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c, KA1),
+                  sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c, KA1), v);
+        st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c + 8, KA1),
+                  sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c + 8, KA1), v + 8);
+      }
+    }
+    {
+      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+      *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
+      *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float v[16];
+      ld16(hc + (int64_t)k * D + 16 * c, valid, v);
+      st_split8(sA2 + tc::kmajor_offset(m, 16 * c, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c, KA2), v);
+      st_split8(sA2 + tc::kmajor_offset(m, 16 * c + 8, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c + 8, KA2), v + 8);
+    }
+    *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+    // vertical successor's carry into this cell (its column's buffer entry)
+    const bool has_v = valid && p.j < Ly - 1;
+    sync_tc();
+    // ---- MMA1, MMA2: the forward pre-activations ----
+    if (m == 0) {
+      constexpr uint32_t i1 = tc::make_idesc_bf16(128, 3 * D), i2 = tc::make_idesc_bf16(128, 2 * D);
+#pragma unroll
+      for (int c = 0; c < KA1 / 16; ++c) {
+        const int kb = c < K1 / 16 ? c : c - K1 / 16;
+        tc::mma_bf16(tbase + S::c1, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (KA1 / 8) * 128),
+                     tc::make_desc(tc::smem_addr(sW1) + kb * 256, 128, (K1 / 8) * 128), i1, c > 0);
+      }
+#pragma unroll
+      for (int c = 0; c < KA2 / 16; ++c) {
+        const int kb = c < K2 / 16 ? c : c - K2 / 16;
+        tc::mma_bf16(tbase + S::c2, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (KA2 / 8) * 128),
+                     tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128), i2, c > 0);
+      }
+      tc::mma_commit(&mbar[0]);
+    }
+    wait(0);
+    // ---- GLU forward: the logit difference and dz ----
+    float z = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t a1[8], a2[8];
+      tld8(trow + S::c2 + 8 * c, a1);
+      tld8(trow + S::c2 + D + 8 * c, a2);
+      tc::tmem_wait_ld();
+      tie(a1);
+      tie(a2);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        z = fmaf(sAux[8 * c + q], __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f), z);
+    }
+    const bool forced = a.sz0 && (n_up >= (N >> 1) || (t - n_up) >= (N >> 1));
+    const float dz = (forced || !valid) ? 0.0f : coef * ((s_k == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc));
+    const int64_t img = tile * N + t;
+    a.dzimg[img * 128 + m] = dz;
+    // ---- GLU backward: G2 = [da_1 | 2 da_2], y for the readout gradient ----
+    uint8_t* g2g = a.g2img + (size_t)img * 128 * S::GW2 * 2;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t a1[8], a2[8];
+      tld8(trow + S::c2 + 8 * c, a1);
+      tld8(trow + S::c2 + D + 8 * c, a2);
+      tc::tmem_wait_ld();
+      tie(a1);
+      tie(a2);
+      float g1v[8], g2v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int v = 8 * c + q;
+        const float x1 = __uint_as_float(a1[q]);
+        const float th = hw_tanh2(__uint_as_float(a2[q]));
+        const float sg2 = fmaf(0.5f, th, 0.5f);
+        const float dy = dz * sAux[v];
+        g1v[q] = dy * sg2;                                   // d a_1
+        g2v[q] = 2.0f * dy * x1 * (0.25f * fmaf(-th, th, 1.0f));   // 2 d a_2 (W_2 halved in the image)
+        a.yimg[(img * D + v) * 128 + m] = x1 * sg2;
+      }
+      st_bf16_8(sA2 + tc::kmajor_offset(m, 8 * c, 2 * D), g1v);
+      st_bf16_8(sA2 + tc::kmajor_offset(m, D + 8 * c, 2 * D), g2v);
+      st_bf16_8(g2g + tc::kmajor_offset(m, 8 * c, S::GW2), g1v);
+      st_bf16_8(g2g + tc::kmajor_offset(m, D + 8 * c, S::GW2), g2v);
+    }
+    sync_tc();
+    // ---- MMA_g: dh (from the GLU) = G2 W2 ----
+    if (m == 0) {
+      constexpr uint32_t ig = tc::make_idesc_bf16(128, D) | (1u << 16);   // B MN-major
+#pragma unroll
+      for (int c = 0; c < 2 * D / 16; ++c)
+        tc::mma_bf16(tbase + S::cg, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (2 * D / 8) * 128),
+                     tc::make_desc(tc::smem_addr(sW2) + c * 2 * (K2 / 8) * 128, (K2 / 8) * 128, 128), ig, c > 0);
+      tc::mma_commit(&mbar[1]);
+    }
+    float cv[D];
+    if (has_v) {
+#pragma unroll
+      for (int q = 0; q < D / 4; ++q) {
+        const float4 x = reinterpret_cast<const float4*>(cc + p.i * D)[q];
+        cv[4 * q] = x.x; cv[4 * q + 1] = x.y; cv[4 * q + 2] = x.z; cv[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < D; ++q) cv[q] = 0.0f;
+    }
+    wait(1);
+    // ---- cell backward: G1 = [da_W | 2 da_g | d(U_mix h')] ----
+    uint8_t* g1g = a.g1img + (size_t)img * 128 * S::GW1 * 2;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t aw[8], ag[8], au[8], gh[8];
+      tld8(trow + S::c1 + 8 * c, aw);
+      tld8(trow + S::c1 + D + 8 * c, ag);
+      tld8(trow + S::c1 + 2 * D + 8 * c, au);
+      tld8(trow + S::cg + 8 * c, gh);
+      tc::tmem_wait_ld();
+      tie(aw);
+      tie(ag);
+      tie(au);
+      tie(gh);
+      float gw[8], gg[8], gm[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int u = 8 * c + q;
+        const float cc_ = hw_tanh2(__uint_as_float(aw[q]));
+        const float tg = hw_tanh2(__uint_as_float(ag[q]));
+        const float ug = fmaf(0.5f, tg, 0.5f);
+        const float mix = __uint_as_float(au[q]);
+        const float dh = __uint_as_float(gh[q]) + carry[u] + cv[u];
+        const float dcand = dh * ug;
+        gw[q] = dcand * fmaf(-cc_, cc_, 1.0f);                            // d a_W
+        gg[q] = 2.0f * dh * (cc_ - mix) * (0.25f * fmaf(-tg, tg, 1.0f));   // 2 d a_g (W_g halved)
+        gm[q] = dh - dcand;                                               // d (U_mix h') = dh (1 - u)
+      }
+      st_bf16_8(sA1 + tc::kmajor_offset(m, 8 * c, 3 * D), gw);
+      st_bf16_8(sA1 + tc::kmajor_offset(m, D + 8 * c, 3 * D), gg);
+      st_bf16_8(sA1 + tc::kmajor_offset(m, 2 * D + 8 * c, 3 * D), gm);
+      st_bf16_8(g1g + tc::kmajor_offset(m, 8 * c, S::GW1), gw);
+      st_bf16_8(g1g + tc::kmajor_offset(m, D + 8 * c, S::GW1), gg);
+      st_bf16_8(g1g + tc::kmajor_offset(m, 2 * D + 8 * c, S::GW1), gm);
+    }
+    sync_tc();
+    // ---- MMA_b: dh' = G1 W1 (into the MMA2 columns, already read) ----
+    if (m == 0) {
+      constexpr uint32_t ib = tc::make_idesc_bf16(128, 2 * D) | (1u << 16);   // B MN-major
+#pragma unroll
+      for (int c = 0; c < 3 * D / 16; ++c)
+        tc::mma_bf16(tbase + S::c2, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (3 * D / 8) * 128),
+                     tc::make_desc(tc::smem_addr(sW1) + c * 2 * (K1 / 8) * 128, (K1 / 8) * 128, 128), ib, c > 0);
+      tc::mma_commit(&mbar[2]);
+    }
+    wait(2);
+    // ---- carries: horizontal predecessor (t - 1 in the same row), vertical (i, j - 1) ----
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t dhh[8], dhv[8];
+      tld8(trow + S::c2 + 8 * c, dhh);
+      tld8(trow + S::c2 + D + 8 * c, dhv);
+      tc::tmem_wait_ld();
+      tie(dhh);
+      tie(dhv);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) carry[8 * c + q] = p.r > 0 ? __uint_as_float(dhh[q]) : 0.0f;
+      if (valid && p.j > 0) {
+        float4* dst = reinterpret_cast<float4*>(cc + p.i * D + 8 * c);
+        dst[0] = make_float4(__uint_as_float(dhv[0]), __uint_as_float(dhv[1]), __uint_as_float(dhv[2]),
+                             __uint_as_float(dhv[3]));
+        dst[1] = make_float4(__uint_as_float(dhv[4]), __uint_as_float(dhv[5]), __uint_as_float(dhv[6]),
+                             __uint_as_float(dhv[7]));
+      }
+    }
+    if (timed_out) break;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// ----------------------------------------------------------------------------
+// Phase 2: weight gradients from the G images, split over CTAs by image.
+// ----------------------------------------------------------------------------
+template <int D>
+struct W2S {
+  static constexpr int K1 = 2 * D + 16, K2 = D + 16;
+  static constexpr int GW1 = G2S<D>::GW1, GW2 = G2S<D>::GW2;
+  static constexpr int H1 = GW1 / 128;                     // 128-row halves of the gate rows of W1
+  static constexpr int kG1 = 0;                            // [128 x GW1] bf16
+  static constexpr int kG2 = kG1 + 128 * GW1 * 2;          // [128 x GW2] bf16
+  static constexpr int kX1 = kG2 + 128 * GW2 * 2;          // [128 x K1] bf16
+  static constexpr int kX2 = kX1 + 128 * K1 * 2;           // [128 x K2] bf16
+  static constexpr int kBar = kX2 + 128 * K2 * 2;
+  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+  static constexpr uint32_t cW1 = 0, cW2 = H1 * K1;        // TMEM accumulators
+  static_assert(H1 * K1 + K2 <= 512, "TMEM budget");
+};
+
+struct Wgrad2Args {
+  int64_t B;
+  int Lx, N, P, tiles;
+  const uint8_t* sigma;
+  const float* hcache;
+  const uint8_t* g1img;
+  const uint8_t* g2img;
+  float* partial;            // one row per CTA
+  WsHeader* hdr;
+};
+
+template <int D>
+__global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
+  using S = W2S<D>;
+  constexpr int K1 = S::K1, K2 = S::K2, GW1 = S::GW1, GW2 = S::GW2;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sG1 = sm + S::kG1;
+  uint8_t* sG2 = sm + S::kG2;
+  uint8_t* sX1 = sm + S::kX1;
+  uint8_t* sX2 = sm + S::kX2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int m = threadIdx.x;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int Lx = a.Lx, N = a.N;
+  const int64_t nimg = (int64_t)a.tiles * N;
+  const int64_t i0 = nimg * blockIdx.x / gridDim.x, i1 = nimg * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t one = 0x3F80u;
+  uint32_t ph = 0;
+  bool timed_out = false;
+  for (int64_t im = i0; im < i1 && !timed_out; ++im) {
+    const int64_t tile = im / N;
+    const int t = (int)(im % N);
+    const int64_t b = tile * 128 + m;
+    const bool valid = b < a.B;
+    const Pz p = zpos(t, Lx);
+    const uint8_t* sg = a.sigma + (valid ? b : 0) * N;
+    const float* hc = a.hcache + (valid ? b : 0) * (int64_t)N * D;
+    // G images (this thread copies a 1/128 share of each)
+    const uint4* g1 = reinterpret_cast<const uint4*>(a.g1img + (size_t)im * 128 * GW1 * 2);
+    const uint4* g2 = reinterpret_cast<const uint4*>(a.g2img + (size_t)im * 128 * GW2 * 2);
+    for (int q = m; q < 128 * GW1 * 2 / 16; q += 128) reinterpret_cast<uint4*>(sG1)[q] = g1[q];
+    for (int q = m; q < 128 * GW2 * 2 / 16; q += 128) reinterpret_cast<uint4*>(sG2)[q] = g2[q];
+    // X1 = [h_hor | h_ver | 1 1 | onehot(s_hor) onehot(s_ver) x2 | 0], X2 = [h | 1 1 | 0]
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
+      const float* src = hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+#pragma unroll
+      for (int c = 0; c < D / 16; ++c) {
+        float v[16];
+        ld16(src + 16 * c, ok, v);
+        st_bf16_8(sX1 + tc::kmajor_offset(m, half * D + 16 * c, K1), v);
+        st_bf16_8(sX1 + tc::kmajor_offset(m, half * D + 16 * c + 8, K1), v + 8);
+      }
+    }
+    {
+      const int s_h = p.r > 0 ? (valid ? (sg[p.j * Lx + zhor(p)] ? 1 : 0) : 0) : -1;
+      const int s_v = p.j > 0 ? (valid ? (sg[(p.j - 1) * Lx + p.i] ? 1 : 0) : 0) : -1;
+      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+      *reinterpret_cast<uint4*>(sX1 + tc::kmajor_offset(m, 2 * D, K1)) = make_uint4(one | (one << 16), oh, ov, oh);
+      *reinterpret_cast<uint4*>(sX1 + tc::kmajor_offset(m, 2 * D + 8, K1)) = make_uint4(ov, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) {
+      float v[16];
+      ld16(hc + (int64_t)(p.j * Lx + p.i) * D + 16 * c, valid, v);
+      st_bf16_8(sX2 + tc::kmajor_offset(m, 16 * c, K2), v);
+      st_bf16_8(sX2 + tc::kmajor_offset(m, 16 * c + 8, K2), v + 8);
+    }
+    *reinterpret_cast<uint4*>(sX2 + tc::kmajor_offset(m, D, K2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sX2 + tc::kmajor_offset(m, D + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (m == 0) {
+      // both operands MN-major: rows = the tile's 128 samples (K), columns = gate rows (M) / inputs (N)
+      constexpr uint32_t iw1 = tc::make_idesc_bf16(128, K1) | (1u << 15) | (1u << 16);
+      constexpr uint32_t iw2 = tc::make_idesc_bf16(128, K2) | (1u << 15) | (1u << 16);
+      const uint32_t acc0 = im > i0 ? 1u : 0u;
+#pragma unroll
+      for (int h = 0; h < S::H1; ++h)
+#pragma unroll
+        for (int c = 0; c < 128 / 16; ++c)
+          tc::mma_bf16(tbase + S::cW1 + h * K1,
+                       tc::make_desc(tc::smem_addr(sG1) + h * 16 * 128 + c * 2 * (GW1 / 8) * 128, (GW1 / 8) * 128, 128),
+                       tc::make_desc(tc::smem_addr(sX1) + c * 2 * (K1 / 8) * 128, (K1 / 8) * 128, 128), iw1,
+                       acc0 | (c > 0));
+#pragma unroll
+      for (int c = 0; c < 128 / 16; ++c)
+        tc::mma_bf16(tbase + S::cW2, tc::make_desc(tc::smem_addr(sG2) + c * 2 * (GW2 / 8) * 128, (GW2 / 8) * 128, 128),
+                     tc::make_desc(tc::smem_addr(sX2) + c * 2 * (K2 / 8) * 128, (K2 / 8) * 128, 128), iw2,
+                     acc0 | (c > 0));
+      tc::mma_commit(&mbar[0]);
+    }
+    if (!tc::mbar_wait(&mbar[0], ph, kWait2)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph ^= 1;
+    tc::fence_after_sync();
+    __syncthreads();   // the shared images are rewritten for the next image
+  }
+  // ---- this CTA's partial gradient row (flat 2D layout, App. A; nqs.h) ----
+  const int W2c = 2 * D + 4;
+  const int oW = 0, oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D,
+            ob1 = oW1 + D * D, oW2 = ob1 + D, ob2 = oW2 + D * D;
+  float* part = a.partial + (size_t)blockIdx.x * a.P;
+  if (i1 > i0) {
+#pragma unroll 1
+    for (int h = 0; h < S::H1; ++h) {
+      const int gu = h * 128 + m, g = gu / D, u = gu % D;
+#pragma unroll 1
+      for (int c0 = 0; c0 < K1; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(trow + S::cW1 + h * K1 + c0, v);
+        tc::tmem_wait_ld();
+        if (gu >= 3 * D) continue;
+        const float sc = g == 1 ? 0.5f : 1.0f;   // G1 carries 2 d a_g
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int k = c0 + q;
+          const float x = sc * v[q];
+          if (k < 2 * D) {
+            part[(g == 0 ? oW + u * W2c : g == 1 ? oWg + u * W2c : oU + u * 2 * D) + k] = x;
+          } else if (g < 2) {
+            if (k == 2 * D) part[(g == 0 ? ob : obg) + u] = x;
+            else if (k >= 2 * D + 2 && k < 2 * D + 6) part[(g == 0 ? oW : oWg) + u * W2c + 2 * D + (k - 2 * D - 2)] = x;
+          }
+        }
+      }
+    }
+    {
+      const int g = m / D, v = m % D;
+#pragma unroll 1
+      for (int c0 = 0; c0 < K2; c0 += 16) {
+        float w[16];
+        tc::tmem_ld16(trow + S::cW2 + c0, w);
+        tc::tmem_wait_ld();
+        if (m >= 2 * D) continue;
+        const float sc = g == 1 ? 0.5f : 1.0f;   // G2 carries 2 d a_2
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int k = c0 + q;
+          if (k < D) part[(g == 0 ? oW1 : oW2) + v * D + k] = sc * w[q];
+          else if (k == D) part[(g == 0 ? ob1 : ob2) + v] = sc * w[q];
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// Phase 3: dU_out[0][v] = sum dz y_v, dU_out[1] = -dU_out[0], dc_0 = sum dz,
+// dc_1 = -dc_0; one partial row per block, images split over the blocks.
+template <int D>
+__global__ void __launch_bounds__(128) tc2d_readout_grad_kernel(const float* __restrict__ yimg,
+                                                              const float* __restrict__ dzimg, int64_t nimg,
+                                                              float* __restrict__ partial, int P, int row0) {
+  __shared__ float red[4][D + 1];
+  const int m = threadIdx.x, lane = m & 31, warp = m >> 5;
+  const int64_t i0 = nimg * blockIdx.x / gridDim.x, i1 = nimg * (blockIdx.x + 1) / gridDim.x;
+  float acc[D];
+#pragma unroll
+  for (int v = 0; v < D; ++v) acc[v] = 0.0f;
+  float accd = 0.0f;
+  for (int64_t im = i0; im < i1; ++im) {
+    const float z = dzimg[im * 128 + m];
+    accd += z;
+#pragma unroll
+    for (int v = 0; v < D; ++v) acc[v] = fmaf(z, yimg[(im * D + v) * 128 + m], acc[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < D; ++v) {
+    float x = acc[v];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[warp][v] = x;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) accd += __shfl_xor_sync(0xffffffffu, accd, off);
+  if (lane == 0) red[warp][D] = accd;
+  __syncthreads();
+  const int W2c = 2 * D + 4;
+  const int oUo = 2 * D * W2c + 2 * D * D + 2 * D + 2 * D * D + 2 * D, oc = oUo + 2 * D;
+  float* part = partial + (size_t)(row0 + blockIdx.x) * P;
+  for (int v = m; v <= D; v += 128) {
+    const float s = (red[0][v] + red[1][v]) + (red[2][v] + red[3][v]);
+    if (v < D) {
+      part[oUo + v] = s;
+      part[oUo + D + v] = -s;
+    } else {
+      part[oc] = s;
+      part[oc + 1] = -s;
+    }
+  }
+}
+
+int sm_count_g() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      sms = n;
+    else
+      sms = 152;
+  }
+  return sms;
+}
+
+constexpr int kReadout2Blocks = 152;
+
+template <int D>
+cudaError_t run_grad(const Tc2Grad& g, const uint8_t* wimg, cudaStream_t st) {
+  const int tiles = (int)((g.B + 127) / 128);
+  const int64_t nimg = (int64_t)tiles * g.N;
+  const uint8_t* w1 = wimg;
+  const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
+  const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  Sweep2Args s{};
+  s.B = g.B;
+  s.Lx = g.Lx;
+  s.Ly = g.Ly;
+  s.N = g.N;
+  s.sz0 = g.sz0;
+  s.sigma = g.sigma;
+  s.hcache = g.hcache;
+  s.weights = g.weights;
+  s.ccarry = g.ccarry;
+  s.g1img = g.g1img;
+  s.g2img = g.g2img;
+  s.yimg = g.yimg;
+  s.dzimg = g.dzimg;
+  s.hdr = g.hdr;
+  auto ks = tc2d_sweep_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, G2S<D>::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  ks<<<tiles, 128, G2S<D>::kBytes, st>>>(w1, w2, aux, s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  Wgrad2Args w{};
+  w.B = g.B;
+  w.Lx = g.Lx;
+  w.N = g.N;
+  w.P = g.P;
+  w.tiles = tiles;
+  w.sigma = g.sigma;
+  w.hcache = g.hcache;
+  w.g1img = g.g1img;
+  w.g2img = g.g2img;
+  w.partial = g.partial;
+  w.hdr = g.hdr;
+  auto kw = tc2d_wgrad_kernel<D>;
+  if ((e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, W2S<D>::kBytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  const int gw = tc2d_wgrad_grid(g.B, g.N);
+  kw<<<gw, 128, W2S<D>::kBytes, st>>>(w);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  tc2d_readout_grad_kernel<D><<<kReadout2Blocks, 128, 0, st>>>(g.yimg, g.dzimg, nimg, g.partial, g.P, gw);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc2d_wgrad_grid(int64_t B, int N) {
+  const int64_t nimg = (B + 127) / 128 * N;
+  const int64_t g = sm_count_g();
+  return (int)(nimg < g ? nimg : g);
+}
+
+int tc2d_grad_partial_rows(int64_t B, int N) { return tc2d_wgrad_grid(B, N) + kReadout2Blocks; }
+
+size_t tc2d_grad_image_bytes(int64_t B, int N, int D, int which) {
+  const int64_t nimg = (B + 127) / 128 * N;
+  const int gw1 = 4 * D >= 128 ? 4 * D : 128, gw2 = 2 * D >= 128 ? 2 * D : 128;
+  switch (which) {
+    case 0: return (size_t)nimg * 128 * gw1 * 2;          // G1 images
+    case 1: return (size_t)nimg * 128 * gw2 * 2;          // G2 images
+    case 2: return (size_t)nimg * D * 128 * 4;             // y
+    default: return (size_t)nimg * 128 * 4;                // dz
+  }
+}
+
+cudaError_t tc2d_grad(const Tc2Grad& g, const uint8_t* wimg, int D, cudaStream_t st) {
+  switch (D) {
+    case 32: return run_grad<32>(g, wimg, st);
+    case 64: return run_grad<64>(g, wimg, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nqs

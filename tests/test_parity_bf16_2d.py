@@ -17,8 +17,9 @@ sums stay FP32.  Bounds, as for the 1D BF16 path:
                 configurations, drawn from the model;
   sampling      identical configurations except samples with a draw within
                 5e-3 of the oracle's threshold;
-  gradient      cosine similarity >= 0.999 (the 2D gradient is the FP32 reverse
-                sweep, driven by BF16 local energies).
+  gradient      cosine similarity >= 0.999 and relative L2 error <= 2e-2 for the
+                BF16 tensor-core reverse sweep (gate gradients rounded to BF16
+                in the backward and weight-gradient GEMMs).
 """
 import numpy as np
 import pytest
@@ -112,6 +113,25 @@ def test_bf16_2d_vmc_gradient_cosine():
     ref = ov.vmc_gradient(mod, pf, sig.astype(np.int64), e_ref)
     g = g.double().cpu().numpy()
     assert g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)) >= 0.999
+
+
+@pytest.mark.parametrize("Lx,Ly,d,B,sz0", [(4, 4, 32, 100, True), (8, 8, 64, 64, True), (3, 5, 32, 77, False),
+                                           (4, 6, 64, 130, True)])
+def test_bf16_2d_logpsi_grad(Lx, Ly, d, B, sz0):
+    desc, d32, mod, pf, p = setup(Lx, Ly, d, sz0, seed=5, noise=0.05)
+    sig = inputs.random_configs(B, mod.N, seed=6, sz0=sz0)
+    w = inputs.random_weights(B, seed=7).astype(np.float32)
+    sg = dev(sig, torch.uint8)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    g = nqs.logpsi_grad(desc, p, sg, hc, dev(w), ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    g = g.double().cpu().numpy()
+    cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
 def test_bf16_2d_full_size_8x8_d64_b2048():
