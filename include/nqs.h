@@ -101,10 +101,9 @@ typedef struct {
                          the reverse sweep on the tensor cores (BF16 operands,
                          FP32 accumulation and FP32 state; d_h in {16, 32, 64}),
                          and the 2D cell and GLU GEMMs of sampling, teacher
-                         forcing and the Heisenberg chains (d_h in {32, 64},
-                         N <= 128; the 2D gradient
-                         runs the FP32 reverse sweep); other shapes return
-                         NQS_EUNSUPPORTED */
+                         forcing, the Heisenberg chains and the reverse
+                         sweep (d_h in {32, 64}, N <= 128); other shapes
+                         return NQS_EUNSUPPORTED */
 } nqs_model_desc;
 
 typedef struct {

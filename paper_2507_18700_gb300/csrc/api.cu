@@ -44,8 +44,7 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
 
 // Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, the BF16
 // tensor-core 1D GRU for d_h in {16, 32, 64} and the BF16 tensor-core 2D GRU
-// for d_h in {32, 64} while its column buffer fits in TMEM (3 d + Lx d / 2 <=
-// 512 columns) and N <= 128 (its gradient runs the FP32 reverse sweep).
+// for d_h in {32, 64} and N <= 128 (configurations as 128-bit masks).
 nqs_status check_built(const Dims& d) {
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
   if (d.precision == NQS_BF16) {
