@@ -18,10 +18,11 @@
 // state enters both GEMMs as a BF16 pair hi + lo (hi = bf16(h), lo =
 // bf16(h - hi): about 16 significant bits); the weights are plain BF16.  The
 // state just computed stays in FP32 registers (the next cell's horizontal
-// neighbour); every state is also written to a per-row column buffer in
-// global memory (the latest FP32 state of each lattice column, coalesced warp
-// stores), from which the vertical neighbour of the next cell is copied into
-// shared memory with cp.async one step ahead.  A chain that restarts from the
+// neighbour) as its packed hi / lo words; every state is also written in that
+// packed form to a per-row column buffer in global memory (the latest state of
+// each lattice column, coalesced warp stores), from which the vertical
+// neighbour of the next cell is copied straight into the A operand with
+// cp.async one step ahead.  A chain that restarts from the
 // cache takes the states of the columns it has not recomputed yet from the
 // cache the same way.  Spins of a row's configuration are a bit mask in
 // registers.
@@ -273,10 +274,12 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   float acc = 0.0f, lp_next = 0.0f;
   bool active = false;
   uint64_t mask[2] = {0ull, 0ull};
-  float h[D];                         // the state just computed (FP32)
+  constexpr int HW = D / 2;           // 32-bit words of a packed BF16 state
+  uint32_t hhi[HW], hlo[HW];         // the state just computed, as BF16 hi / lo pairs
 #pragma unroll
-  for (int q = 0; q < D; ++q) h[q] = 0.0f;
-  int hsrc = 0, vsrc = 0;            // next cell's inputs: 0 zero, 1 registers, 2 shared copy
+  for (int q = 0; q < HW; ++q) hhi[q] = hlo[q] = 0u;
+  // next cell's inputs: 0 zero, 1 registers, 2 FP32 shared copy, 3 copied into the A operand
+  int hsrc = 0, vsrc = 0;
 
   auto fetch = [&](float* dst, const float* src) {
 #pragma unroll
@@ -308,8 +311,15 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         vsrc = 2;
         copies = true;
       } else {
-        fetch(vs, colrow + p.i * D);   // recomputed by this row (at least two cells back)
-        vsrc = 2;
+        // recomputed by this row (at least two cells back): its packed hi / lo
+        // words go straight into the A operand's vertical-input columns
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(colrow + p.i * D);
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) {
+          cp_async16_2d(sA + tc::kmajor_offset(m, D + 8 * c, KA1), src + 16 * c);
+          cp_async16_2d(sA + tc::kmajor_offset(m, K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
+        }
+        vsrc = 3;
         copies = true;
       }
     }
@@ -385,12 +395,20 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     for (int half = 0; half < 2; ++half) {
       const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
       const float* stg = half == 0 ? hs : vs;
+      uint8_t* dhi = sA + tc::kmajor_offset(m, half * D, KA1);
+      uint8_t* dlo = sA + tc::kmajor_offset(m, K1 + half * D, KA1);
+      if (src == 2) {
 #pragma unroll
-      for (int c = 0; c < D / 8; ++c) {
-        float v[8];
+        for (int c = 0; c < D / 8; ++c) st_split8(dhi + 128 * c, dlo + 128 * c, stg + 8 * c);
+      } else if (src != 3) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = src == 1 ? h[8 * c + q] : src == 2 ? stg[8 * c + q] : 0.0f;
-        st_split8(sA + tc::kmajor_offset(m, half * D + 8 * c, KA1), sA + tc::kmajor_offset(m, K1 + half * D + 8 * c, KA1), v);
+        for (int c = 0; c < D / 8; ++c) {
+          const bool r = src == 1;
+          *reinterpret_cast<uint4*>(dhi + 128 * c) =
+              r ? make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(dlo + 128 * c) =
+              r ? make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+        }
       }
     }
     {
@@ -430,6 +448,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     ph0 ^= 1;
     tc::fence_after_sync();
     // ---- (c) epilogue 1: the cell ----
+    float h[D];
 #pragma unroll
     for (int c = 0; c < D / 8; ++c) {
       uint32_t aw[8], ag[8], au[8];
@@ -448,10 +467,16 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         h[8 * c + q] = fmaf(ug, cc - mix, mix);
       }
     }
+#pragma unroll
+    for (int q = 0; q < HW; ++q) split_bf16(h[2 * q], h[2 * q + 1], hhi[q], hlo[q]);
     // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1: MMA1 has completed)
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c)
-      st_split8(sA + tc::kmajor_offset(m, 8 * c, KA2), sA + tc::kmajor_offset(m, K2 + 8 * c, KA2), h + 8 * c);
+    for (int c = 0; c < D / 8; ++c) {
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 8 * c, KA2)) =
+          make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
+      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, K2 + 8 * c, KA2)) =
+          make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
+    }
     *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
     tc::fence_async_smem();
@@ -470,29 +495,41 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
       tc::mma_commit(&mbar[1]);
     }
-    // stores of this step's states, coalesced: every thread stages its row's h,
-    // then each warp writes whole rows to the column buffer (entry of the row's
-    // lattice column) and, in sampling / teacher forcing, to the cache (all
-    // rows of such a tile are at the same position)
+    // stores of this step's states, coalesced: every thread stages its row's
+    // packed hi / lo state (and, in sampling / teacher forcing, its FP32
+    // state), then each warp writes whole rows to the column buffer (entry of
+    // the row's lattice column) and to the cache (all rows of such a tile are
+    // at the same position).  Chains stage in hs, whose chain-start copy is
+    // issued after these stores; the forward modes never copy into vs.
     {
+      float* pst = MODE == 2 ? hs : vs;
 #pragma unroll
-      for (int q = 0; q < D / 4; ++q)
-        reinterpret_cast<float4*>(hs)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+      for (int q = 0; q < HW / 4; ++q) {
+        reinterpret_cast<uint4*>(pst)[q] = make_uint4(hhi[4 * q], hhi[4 * q + 1], hhi[4 * q + 2], hhi[4 * q + 3]);
+        reinterpret_cast<uint4*>(pst)[HW / 4 + q] = make_uint4(hlo[4 * q], hlo[4 * q + 1], hlo[4 * q + 2], hlo[4 * q + 3]);
+      }
+      if constexpr (MODE != 2) {
+#pragma unroll
+        for (int q = 0; q < D / 4; ++q)
+          reinterpret_cast<float4*>(hs)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+      }
       sCol[m] = active ? P(t).i : -1;
       __syncwarp();
       constexpr int L = D / 4, RPI = 32 / L;
       const int lr = lane / L, lq = lane % L;
       const int kc = MODE != 2 ? P(step).j * Lx + P(step).i : 0;
+      const float* pbase = MODE == 2 ? sHS : sVS;
 #pragma unroll 4
       for (int i = 0; i < 32; i += RPI) {
         const int mr = warp * 32 + i + lr;
         const int ci = sCol[mr];
         if (ci >= 0) {
-          const float4 v = reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
           const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
-          reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] = v;
+          reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] =
+              reinterpret_cast<const float4*>(pbase + mr * S::HS)[lq];
           if (MODE != 2 && a.hcache)
-            reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] = v;
+            reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] =
+                reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
         }
       }
       __syncwarp();
