@@ -205,7 +205,7 @@ def run_gpu(args, w):
     import torch
     import torch.distributed as dist
 
-    from paper_2507_18700_gb300 import inputs, nqs
+    from paper_2507_18700_gb300 import dist as vdist, inputs, nqs
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -228,6 +228,17 @@ def run_gpu(args, w):
     def events():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    def vmc_grad(desc, sigma, hc, eloc, ws, p=None):
+        """The step's gradient: one rank, nqs_vmc_grad; several ranks, the
+        global energy statistics, globally centred weights and the summed
+        gradient (two all-reduces of small tensors, inside the timed step)."""
+        p = params if p is None else p
+        if world == 1:
+            return nqs.vmc_grad(desc, p, sigma, hc, eloc, ws=ws)
+        stats = vdist.global_energy_stats(eloc)
+        g = nqs.logpsi_grad(desc, p, sigma, hc, vdist.vmc_weights(eloc, stats), ws=ws)
+        return vdist.allreduce_grad(g), stats
+
     def measure(precision):
         """Time args.steps VMC steps at one precision (after args.warmup untimed ones)."""
         desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=precision)
@@ -235,7 +246,7 @@ def run_gpu(args, w):
         for k in range(args.warmup):
             s_, _, h_ = nqs.sample(desc, params, B, seed=step_seed, step=k, ws=ws)
             e_ = nqs.local_energy(desc, params, ham, s_, h_, ws=ws)
-            nqs.vmc_grad(desc, params, s_, h_, e_, ws=ws)
+            vmc_grad(desc, s_, h_, e_, ws)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -252,7 +263,7 @@ def run_gpu(args, w):
             la.record(st)
             eloc = nqs.local_energy(desc, params, ham, sigma, hc, ws=ws)
             lb.record(st)
-            grad, stats = nqs.vmc_grad(desc, params, sigma, hc, eloc, ws=ws)
+            grad, stats = vmc_grad(desc, sigma, hc, eloc, ws)
             b.record(st)
             torch.cuda.synchronize()
             step_ms.append(a.elapsed_time(b))
@@ -278,7 +289,7 @@ def run_gpu(args, w):
             dev_p.copy_(host_p, non_blocking=True)
             s_, _, h_ = nqs.sample(desc, dev_p, B, seed=step_seed, step=10_000 + k, ws=ws)
             e_ = nqs.local_energy(desc, dev_p, ham, s_, h_, ws=ws)
-            g_, st_ = nqs.vmc_grad(desc, dev_p, s_, h_, e_, ws=ws)
+            g_, st_ = vmc_grad(desc, s_, h_, e_, ws, dev_p)
             host_g.copy_(g_, non_blocking=True)
             host_s.copy_(st_, non_blocking=True)
             b.record(st)
@@ -359,7 +370,8 @@ def run_gpu(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if chosen is r16 else "f32",
         "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": B * world, "seq_len": N,
-                   "parallelism": "replicas" if world > 1 else "single",
+                   "parallelism": "dp%d (samples split over ranks; all-reduce of energy statistics and gradient)"
+                                  % world if world > 1 else "single",
                    "precision": ("bf16 tensor-core cell GEMMs, fp32 state" if w["cell"] == 1 else
                                  "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs) "
                                  "and reverse sweep, fp32 state") if chosen is r16 else "fp32",
