@@ -349,8 +349,8 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
     float* delta = at<float>(ws, L.f);
     const float x = ham->marshall ? -0.5f * (float)ham->J : 0.5f * (float)ham->J;
     if (use_tc2d(d)) {
-      // cached-path tables from a teacher-forced pass with the same BF16
-      // arithmetic as the chains, then the chains over the antiparallel bonds
+      // cached-path tables from the cache with the chains' own BF16 readout,
+      // then the chains over the antiparallel bonds
       uint8_t* wimg = at<uint8_t>(ws, L.w);
       if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
       if (gru2d_bonds(d.Lx, d.Ly, bonds, st) != cudaSuccess) return NQS_ECUDA;
@@ -360,11 +360,11 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
       f.N = d.N;
       f.sz0 = d.sz0;
       f.sigma_in = sigma;
+      f.hcache = const_cast<float*>(hcache);
       f.lp_tab = lp_tab;
       f.nup_tab = nup_tab;
-      f.colbuf = at<float>(ws, L.a);
       f.hdr = hdr;
-      if (tc2d_forward(f, wimg, d.d, false, st) != cudaSuccess) return NQS_ECUDA;
+      if (tc2d_tables(f, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
       Tc2Chains c{};
       c.B = B;
       c.Lx = d.Lx;

@@ -93,8 +93,8 @@ struct Tc2Fwd {
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // nullable
   float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
-  float* lp_tab;             // teacher forcing: [B, N, 2] masked log p of both outcomes (nullable)
-  int* nup_tab;              // teacher forcing: [B, N] up spins before each position
+  float* lp_tab;             // tables: [B, N, 2] masked log p of both outcomes
+  int* nup_tab;              // tables: [B, N] up spins before each position
   WsHeader* hdr;
 };
 struct Tc2Chains {
@@ -117,6 +117,8 @@ size_t tc2d_jobs_bytes(int64_t B, int nb);
 size_t tc2d_colbuf_floats(int64_t B, int Lx, int D);
 cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
 cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st);
+// cached-path tables (lp_tab, nup_tab) from sigma_in and hcache of f, all cells in parallel
+cudaError_t tc2d_tables(const Tc2Fwd& f, const uint8_t* wimg, int D, cudaStream_t st);
 cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st);
 
 // BF16 tensor-core 2D reverse sweep (tc2d_grad.cu)

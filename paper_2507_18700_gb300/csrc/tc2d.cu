@@ -170,8 +170,7 @@ __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restri
 }
 
 // ----------------------------------------------------------------------------
-// The engine.  MODE 0: sampling, 1: teacher forcing (optionally writing the
-// cached-path tables), 2: Heisenberg chains.
+// The engine.  MODE 0: sampling, 1: teacher forcing, 2: Heisenberg chains.
 // ----------------------------------------------------------------------------
 template <int D>
 struct S2 {
@@ -202,7 +201,7 @@ struct Tc2Args {
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // written by sampling / teacher forcing (nullable); read by chains
   float* colbuf;             // [CTAs x 128 rows, Lx, d] latest FP32 state of every lattice column
-  float* lp_tab;             // teacher forcing: written when non-null; chains: read
+  float* lp_tab;             // chains: cached-path tables
   int* nup_tab;
   const int4* bonds;
   const Job2* jobs;
@@ -576,11 +575,6 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       if constexpr (MODE == 2) {
         acc += 0.5f * (lp - lp_next);
       } else {
-        if (MODE == 1 && a.lp_tab) {
-          a.lp_tab[(b * N + t) * 2] = lp_masked(0, d, n_up, t, N, a.sz0 != 0);
-          a.lp_tab[(b * N + t) * 2 + 1] = lp_masked(1, d, n_up, t, N, a.sz0 != 0);
-          a.nup_tab[b * N + t] = n_up;
-        }
         acc += lp;
       }
       n_up += (s == 0);
@@ -608,6 +602,142 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kTmemCols);
+}
+
+// ----------------------------------------------------------------------------
+// Cached-path tables for the chains: for every cell (sample b, position t) the
+// masked log p of both outcomes and the up-spin count before t.  The logits
+// come from the GLU readout of the cached state h_t with the engine's own hi /
+// lo GLU GEMM and readout order, so they equal the engine's bit for bit; every
+// cell is independent, so tiles of 128 cells run in parallel.
+// ----------------------------------------------------------------------------
+template <int D>
+struct T2S {
+  static constexpr int K2 = D + 16, KA2 = K2 + D;
+  static constexpr int kW2 = 0;                            // [2D x K2] bf16
+  static constexpr int kA = kW2 + 2 * D * K2 * 2;          // [128 x KA2] bf16
+  static constexpr int kAux = kA + 128 * KA2 * 2;          // D + 4 floats
+  static constexpr int kPos = kAux + (D + 4) * 4;          // 128 ints: lattice site of every position
+  static constexpr int kBar = kPos + 128 * 4;
+  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+};
+
+struct Tab2Args {
+  int64_t B;
+  int Lx, N, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  float* lp_tab;
+  int* nup_tab;
+  WsHeader* hdr;
+};
+
+template <int D>
+__global__ void __launch_bounds__(128, 1)
+tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ aux, Tab2Args a) {
+  using S = T2S<D>;
+  constexpr int K2 = S::K2, KA2 = S::KA2;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sW2 = sm + S::kW2;
+  uint8_t* sA = sm + S::kA;
+  float* sAux = reinterpret_cast<float*>(sm + S::kAux);
+  int* sSite = reinterpret_cast<int*>(sm + S::kPos);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 128)
+    reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
+  for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += 128) {
+    const Pz p = zpos(t, a.Lx);
+    sSite[t] = p.j * a.Lx + p.i;
+  }
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 128);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int m = threadIdx.x;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int N = a.N;
+  const float dc = sAux[D];
+  const uint32_t one = 0x3F80u;
+  const int64_t ncell = a.B * N, ntile = (ncell + 127) / 128;
+  uint32_t ph = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t cell = tile * 128 + m;
+    const bool valid = cell < ncell;
+    const int64_t b = valid ? cell / N : 0;
+    const int t = valid ? (int)(cell % N) : 0;
+    const float* hc = a.hcache + (b * N + sSite[t]) * D;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = valid ? hc[8 * c + q] : 0.0f;
+      st_split8(sA + tc::kmajor_offset(m, 8 * c, KA2), sA + tc::kmajor_offset(m, K2 + 8 * c, KA2), v);
+    }
+    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (m == 0) {
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, 2 * D);
+#pragma unroll
+      for (int c = 0; c < KA2 / 16; ++c) {
+        const int kb = c < K2 / 16 ? c : c - K2 / 16;
+        tc::mma_bf16(tbase, tc::make_desc(tc::smem_addr(sA) + c * 256, 128, (KA2 / 8) * 128),
+                     tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128), idesc, c > 0);
+      }
+      tc::mma_commit(&mbar[0]);
+    }
+    // up spins before position t, while the MMA runs
+    int n_up = 0;
+    if (valid)
+      for (int q = 0; q < t; ++q) n_up += a.sigma[b * N + sSite[q]] ? 0 : 1;
+    const bool ok = tc::mbar_wait(&mbar[0], ph, kWait2);
+    if (!ok) flag_status(a.hdr, NQS_ETIMEOUT);
+    ph ^= 1;
+    tc::fence_after_sync();
+    float z = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t a1[8], a2[8];
+      tld8(trow + 8 * c, a1);
+      tld8(trow + D + 8 * c, a2);
+      tc::tmem_wait_ld();
+      tie(a1);
+      tie(a2);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+        z = fmaf(sAux[8 * c + q], y, z);
+      }
+    }
+    if (valid) {
+      const float d = z + dc;
+      a.lp_tab[(b * N + t) * 2] = lp_masked(0, d, n_up, t, N, a.sz0 != 0);
+      a.lp_tab[(b * N + t) * 2 + 1] = lp_masked(1, d, n_up, t, N, a.sz0 != 0);
+      a.nup_tab[b * N + t] = n_up;
+    }
+    tc::fence_before_sync();
+    // every lane has read the accumulator before the next tile's MMA; a timeout ends all lanes together
+    const bool stop = __syncthreads_or(!ok);
+    tc::fence_after_sync();
+    if (stop) break;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 128);
 }
 
 int sm_count_2d() {
@@ -685,6 +815,38 @@ cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sampl
   switch (D) {
     case 32: return sample ? launch2<32, 0>(a, w1, w2, aux, st) : launch2<32, 1>(a, w1, w2, aux, st);
     case 64: return sample ? launch2<64, 0>(a, w1, w2, aux, st) : launch2<64, 1>(a, w1, w2, aux, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int D>
+cudaError_t launch_tables(const Tab2Args& a, const uint8_t* w2, const float* aux, cudaStream_t st) {
+  auto k = tc2d_tables_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, T2S<D>::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int64_t ntile = (a.B * a.N + 127) / 128;
+  const int64_t grid = ntile < sm_count_2d() ? ntile : sm_count_2d();
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, 128, T2S<D>::kBytes, st>>>(w2, aux, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc2d_tables(const Tc2Fwd& f, const uint8_t* wimg, int D, cudaStream_t st) {
+  Tab2Args a{};
+  a.B = f.B;
+  a.Lx = f.Lx;
+  a.N = f.N;
+  a.sz0 = f.sz0;
+  a.sigma = f.sigma_in;
+  a.hcache = f.hcache;
+  a.lp_tab = f.lp_tab;
+  a.nup_tab = f.nup_tab;
+  a.hdr = f.hdr;
+  const uint8_t* w2 = wimg + (size_t)3 * D * (2 * D + 16) * 2;
+  const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  switch (D) {
+    case 32: return launch_tables<32>(a, w2, aux, st);
+    case 64: return launch_tables<64>(a, w2, aux, st);
   }
   return cudaErrorInvalidValue;
 }
