@@ -175,7 +175,7 @@ struct Tc1Args {
 struct TcBpttArgs {
   int64_t B;
   int N, P;
-  int rows;                  // rows per 128-lane tile (128 or 64; set by the launcher)
+  int rows;                  // rows per 128-lane tile (128, 64 or 32; set by the launcher)
   const uint8_t* sigma;
   const float* hcache;
   const float* weights;

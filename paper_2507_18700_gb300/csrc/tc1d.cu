@@ -74,15 +74,15 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Bulk (TMA engine) global -> shared copy of `bytes` (multiple of 16, both
-// addresses 16-byte aligned) that completes on an mbarrier, after this
-// thread's arrival announcing the bytes; and a plain arrival.
-__device__ __forceinline__ void bulk_load_arrive(void* smem, const void* gmem, uint32_t bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" : : "r"(tc::smem_addr(bar)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-               :
-               : "r"(tc::smem_addr(smem)), "l"(gmem), "r"(bytes), "r"(tc::smem_addr(bar))
-               : "memory");
+// 16-byte global -> shared copy that skips L1 (data read once), and the
+// arrival on an mbarrier that takes place when all of this thread's earlier
+// cp.async copies have landed (counted against the barrier's expected
+// arrivals: no increment); and a plain arrival.
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
@@ -668,18 +668,27 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   const int N = a.N;
   const int64_t b = (int64_t)blockIdx.x * a.rows + m;
   const bool valid = m < a.rows && b < a.B;
+  // warps whose 32 rows lie past the tile's rows (64- and 32-row tiles) skip
+  // the per-site work; they still fill their row buffers with zeros, arrive on
+  // the row barriers and take part in every CTA barrier
+  const bool wact = (m & ~31) < a.rows;
+  const int kw = a.rows / 16;              // K = 16 steps of the weight-gradient MMA
   const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
   // this thread's units of the two state rows
   float* hrow[2] = {sH + (0 * 128 + m) * S::HS + u0, sH + (1 * 128 + m) * S::HS + u0};
   bool timed_out = false;
   // copy h_n of this sample (zero for n < 0 or past the batch) into row buffer
-  // k: one bulk copy per thread (its units of the row), completing on mbar[2 + k]
+  // k: this thread's units of the row by 16-byte cp.async copies (LSU path:
+  // one bulk copy per thread queued 512 small requests per site on the copy
+  // engine), completing on mbar[2 + k].  A thread reads only its own units.
   bool inflight[2] = {false, false};   // a fill of the buffer not yet waited for
   auto fetch = [&](int n, int k) {
     inflight[k] = true;
     if (valid && n >= 0) {
-      tc::fence_async_smem();        // this thread's reads of the buffer come first
-      bulk_load_arrive(hrow[k], a.hcache + (b * N + n) * D + u0, DU * 4, &mbar[2 + k]);
+      const float* src = a.hcache + (b * N + n) * D + u0;
+#pragma unroll
+      for (int q = 0; q < DU / 4; ++q) cp_async16_cg(hrow[k] + 4 * q, src + 4 * q);
+      cp_async_arrive_noinc(&mbar[2 + k]);
     } else {
 #pragma unroll
       for (int q = 0; q < DU / 4; ++q) reinterpret_cast<float4*>(hrow[k])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -716,39 +725,52 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
     // spin two sites back, for the next site's input
     const uint32_t s_pp = (valid && n >= 2) ? ldg_u8(a.sigma + b * N + n - 2) : 0u;
     const int s_in = n > 0 ? (s_p ? 1 : 0) : -1;
-    // ---- X row: [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0] ----
+    float z = 0.0f;
+    if (wact) {
+      // ---- X row: [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0] ----
 #pragma unroll
-    for (int c = 0; c < DU / 8; ++c) {
-      float v[8];
-      const float4 x0 = reinterpret_cast<const float4*>(hp)[2 * c];
-      const float4 x1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
-      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w; v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
-      st_bf16x8(sX + tc::kmajor_offset(m, u0 + 8 * c, KA), v);
+      for (int c = 0; c < DU / 8; ++c) {
+        float v[8];
+        const float4 x0 = reinterpret_cast<const float4*>(hp)[2 * c];
+        const float4 x1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
+        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w; v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+        st_bf16x8(sX + tc::kmajor_offset(m, u0 + 8 * c, KA), v);
+      }
+      if (part == 0) {
+        const uint32_t one = 0x3F80u;
+        const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
+        *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
+        *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      // ---- readout of h_n (logit difference): 16-unit chunk sums in order, chunks
+      // and parts by fixed trees, as in the forward pass.  The row is read as
+      // float4 (scalar reads of rows HS floats apart are 4-way bank conflicts) ----
+      float zc[DU / 16];
+#pragma unroll
+      for (int c = 0; c < DU / 16; ++c) {
+        float s0 = 0.0f;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 h4 = reinterpret_cast<const float4*>(hn)[4 * c + q4];
+          const float4 w4 = reinterpret_cast<const float4*>(dU + u0)[4 * c + q4];
+          s0 = fmaf(w4.x, h4.x, s0);
+          s0 = fmaf(w4.y, h4.y, s0);
+          s0 = fmaf(w4.z, h4.z, s0);
+          s0 = fmaf(w4.w, h4.w, s0);
+        }
+        zc[c] = s0;
+      }
+#pragma unroll
+      for (int w = 1; w < DU / 16; w *= 2)
+#pragma unroll
+        for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
+      z = zc[0];
+      if constexpr (SPLIT > 1) zb[part * 128 + m] = zc[0];
     }
-    if (part == 0) {
-      const uint32_t one = 0x3F80u;
-      const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
-      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
-      *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    // ---- readout of h_n (logit difference): 16-unit chunk sums in order, chunks
-    // and parts by fixed trees, as in the forward pass ----
-    float zc[DU / 16];
-#pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      float s0 = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) s0 = fmaf(dU[u0 + 16 * c + q], hn[16 * c + q], s0);
-      zc[c] = s0;
-    }
-#pragma unroll
-    for (int w = 1; w < DU / 16; w *= 2)
-#pragma unroll
-      for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
-    if constexpr (SPLIT > 1) zb[part * 128 + m] = zc[0];
     tc::fence_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    // a wait that ran out anywhere in the CTA ends the sweep for every thread here
+    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
     tc::fence_after_sync();
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -759,30 +781,30 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
       }
       tc::mma_commit(&mbar[0]);
     }
-    float z = zc[0];
-    if constexpr (SPLIT > 1) {
-      float pz[SPLIT];
+    float dz0 = 0.0f;
+    if (wact) {
+      if constexpr (SPLIT > 1) {
+        float pz[SPLIT];
 #pragma unroll
-      for (int p = 0; p < SPLIT; ++p) pz[p] = zb[p * 128 + m];
+        for (int p = 0; p < SPLIT; ++p) pz[p] = zb[p * 128 + m];
 #pragma unroll
-      for (int w = 1; w < SPLIT; w *= 2)
+        for (int w = 1; w < SPLIT; w *= 2)
 #pragma unroll
-        for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
-      z = pz[0];
+          for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
+        z = pz[0];
+      }
+      const float d = z + dc;
+      dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
     }
-    const float d = z + dc;
-    const float dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
-    // h_n is no longer needed: its buffer takes h_{n-2}.  (The copy's proxy
-    // fence comes before this site's global store, so it does not wait on it.)
+    // h_n is no longer needed: its buffer takes h_{n-2}
     if (n >= 1) fetch(n - 2, cur);
     if (valid && part == 0) a.dz[b * N + n] = dz0;
-    if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
-    ph_f ^= 1;
-    tc::fence_after_sync();
-    // ---- gates and backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
-    // accumulator columns in 8-unit sub-chunks, double-buffered (the loads of
-    // sub-chunk c + 1 are in flight while sub-chunk c is computed)
-    {
+    if (wact) {
+      if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+      tc::fence_after_sync();
+      // ---- gates and backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
+      // accumulator columns in 8-unit sub-chunks, double-buffered (the loads of
+      // sub-chunk c + 1 are in flight while sub-chunk c is computed)
       float bufA[4][8], bufB[4][8];
       auto issue = [&](int c, float (&bf)[4][8]) {
         const int cu = u0 + 8 * c;
@@ -798,6 +820,15 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
         tmem_wait_regs(acc);
         if (c + 1 < DU / 8) issue(c + 1, (c & 1) ? bufA : bufB);
         const int cu = u0 + 8 * c;
+        float hv[8], wv[8];
+        {
+          const float4 p0 = reinterpret_cast<const float4*>(hp)[2 * c];
+          const float4 p1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
+          const float4 w0 = reinterpret_cast<const float4*>(dU + cu)[0];
+          const float4 w1 = reinterpret_cast<const float4*>(dU + cu)[1];
+          hv[0] = p0.x; hv[1] = p0.y; hv[2] = p0.z; hv[3] = p0.w; hv[4] = p1.x; hv[5] = p1.y; hv[6] = p1.z; hv[7] = p1.w;
+          wv[0] = w0.x; wv[1] = w0.y; wv[2] = w0.z; wv[3] = w0.w; wv[4] = w1.x; wv[5] = w1.y; wv[6] = w1.z; wv[7] = w1.w;
+        }
         float g0[8], g1[8], g2[8], g3[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -805,9 +836,9 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
           const float tu = hw_tanh(acc[0][q]), tr = hw_tanh(acc[1][q]);
           const float ug = fmaf(0.5f, tu, 0.5f), rg = fmaf(0.5f, tr, 0.5f);
           const float cg = hw_tanh(fmaf(rg, acc[2][q], acc[3][q]));
-          const float dh = fmaf(dz0, dU[cu + q], carry[j]);
+          const float dh = fmaf(dz0, wv[q], carry[j]);
           const float dc = dh * ug;
-          const float du = dh * (cg - hp[j]);
+          const float du = dh * (cg - hv[q]);
           carry[j] = dh - dc;                              // direct path; acc_b adds the rest
           const float dac = dc * fmaf(-cg, cg, 1.0f);
           g0[q] = du * (0.25f * fmaf(-tu, tu, 1.0f));      // u (1 - u) = (1 - tanh^2) / 4
@@ -822,6 +853,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
         st_bf16x8(sG + tc::kmajor_offset(m, 3 * D + cu, S::GW), g3);
       }
     }
+    ph_f ^= 1;
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -834,14 +866,16 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
         const uint64_t db = tc::make_desc(tc::smem_addr(sWt) + k * 256, 128, (3 * D / 8) * 128);
         tc::mma_bf16(tbase + S::cB, da, db, idesc_b, k > 0);
       }
-      // acc_w += G^T X over the 128 samples of this site, halves of 128 gate rows.
-      // Both operands MN-major: LBO = stride of 8-sample groups along K (the
-      // buffer's row-group stride), SBO = 128 B between 8-column groups along
-      // M / N.  One K = 16 step covers two sample groups.
+      // acc_w += G^T X over this tile's samples (a.rows of them: rows past it
+      // would add exact zeros), halves of 128 gate rows.  Both operands
+      // MN-major: LBO = stride of 8-sample groups along K (the buffer's
+      // row-group stride), SBO = 128 B between 8-column groups along M / N.
+      // One K = 16 step covers two sample groups.
 #pragma unroll
       for (int half = 0; half < S::GW / 128; ++half) {
 #pragma unroll
         for (int k = 0; k < 128 / 16; ++k) {
+          if (k >= kw) break;
           const uint64_t da = tc::make_desc(tc::smem_addr(sG) + half * 16 * 128 + k * 2 * (S::GW / 8) * 128,
                                             (S::GW / 8) * 128, 128);
           const uint64_t db = tc::make_desc(tc::smem_addr(sX) + k * 2 * (KA / 8) * 128, (KA / 8) * 128, 128);
@@ -850,10 +884,9 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
       }
       tc::mma_commit(&mbar[1]);
     }
-    if (!tc::mbar_wait(&mbar[1], ph_b, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
-    ph_b ^= 1;
-    tc::fence_after_sync();
-    {
+    if (wact) {
+      if (!tc::mbar_wait(&mbar[1], ph_b, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+      tc::fence_after_sync();
       // all of this thread's acc_b columns in one round trip
       float v[DU / 8][8];
 #pragma unroll
@@ -867,10 +900,10 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
           carry[8 * c + q] += v[c][q];
         }
     }
+    ph_b ^= 1;
     s_n = s_p;
     s_p = s_pp;
     cur = nxt;
-    if (timed_out) break;
   }
   // after a timeout, let copies still in flight land before the CTA leaves
   if (timed_out) {
@@ -1126,7 +1159,7 @@ void tc1d_set_variant(int v) {
 constexpr int kReadoutGradBlocks = 304;
 // rows of per-CTA partial gradients: the reverse sweep's CTAs (at most one per
 // 64 samples) and then the readout-gradient blocks
-int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 63) / 64) + kReadoutGradBlocks; }
+int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 31) / 32) + kReadoutGradBlocks; }
 
 template <int D, int SPLIT>
 cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt,
@@ -1142,25 +1175,26 @@ cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_
 
 template <int D>
 cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, cudaStream_t st) {
-  // reverse sweep: 1, 2 or 4 threads per row, times 128 or 64 rows per tile,
-  // picked by the autotuner.  A run writes one partial row per CTA (at most
-  // B/64 rows) and the reduction sums all rows, so the sweep's rows are
-  // cleared before every run: an autotuning trial with 64 rows per tile
-  // leaves rows that a final run with 128 rows per tile would not overwrite.
+  // reverse sweep: 1, 2 or 4 threads per row, times 128, 64 or 32 rows per
+  // tile, picked by the autotuner (fewer rows put more SMs on the sequential
+  // sweep of a small batch).  A run writes one partial row per CTA (at most
+  // B/32 rows) and the reduction sums all rows, so the sweep's rows are
+  // cleared before every run: an autotuning trial with fewer rows per tile
+  // leaves rows that a final run with more rows per tile would not overwrite.
   const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
   auto run = [&](int v) {
     TcBpttArgs b = a;
-    b.rows = v < ns ? 128 : 64;
+    b.rows = 128 >> (v / ns);
     const int sv = v % ns;
     if (sv == 2 && D >= 64) return launch_tc_bptt_v<D, (D >= 64 ? 4 : 1)>(b, img, w3, wt, st);
     if (sv == 1 && D >= 32) return launch_tc_bptt_v<D, (D >= 32 ? 2 : 1)>(b, img, w3, wt, st);
     return launch_tc_bptt_v<D, 1>(b, img, w3, wt, st);
   };
-  const int rows_max = (int)((a.B + 63) / 64);
+  const int rows_max = (int)((a.B + 31) / 32);
   auto clear = [&]() {
     return cudaMemsetAsync(a.partial, 0, (size_t)rows_max * a.P * sizeof(float), st);
   };
-  cudaError_t e = tuned_launch(3, D, a.N, a.B, 2 * ns, run, clear, st);
+  cudaError_t e = tuned_launch(3, D, a.N, a.B, 3 * ns, run, clear, st);
   if (e != cudaSuccess) return e;
   tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
                                                                    rows_max);

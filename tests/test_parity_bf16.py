@@ -130,7 +130,8 @@ def test_bf16_reverse_sweep(N, d, B):
 
 
 def test_autotuned_variants_agree_bitwise():
-    """Every tile variant (1, 2 or 4 threads per row; 128 or 64 rows per tile)
+    """Every tile variant (1, 2 or 4 threads per row; 128, 64 or, in the reverse
+    sweep, 32 rows per tile)
     computes bitwise the same samples, cache, local energies and energy
     statistics, and so does the autotuned choice (tuning off = first variant).
     The gradient is a sum over samples whose per-CTA grouping depends on the
@@ -139,7 +140,7 @@ def test_autotuned_variants_agree_bitwise():
     N, d, B = 60, 64, 700
     desc, mod, pf, p = setup(N, d)
     outs = []
-    runs = [(None, False), (None, True), (None, True)] + [(v, True) for v in range(6)]
+    runs = [(None, False), (None, True), (None, True)] + [(v, True) for v in range(9)]
     for variant, tune in runs:
         nqs.set_autotune(tune)
         nqs.set_tile_variant(variant)
@@ -156,7 +157,8 @@ def test_autotuned_variants_agree_bitwise():
             assert torch.equal(x, y)
         rel = float((o[6].double() - ref[6].double()).norm() / ref[6].double().norm())
         assert rel <= 1e-5, rel
-    # pinned variants 0-2 (128 rows) and 3-5 (64 rows): bitwise within each class
-    for lo, hi in ((3, 6), (6, 9)):
+    # pinned reverse-sweep variants 0-2 (128 rows), 3-5 (64 rows) and 6-8 (32
+    # rows; the forward kernels take their last variant): bitwise within each class
+    for lo, hi in ((3, 6), (6, 9), (9, 12)):
         for o in outs[lo + 1:hi]:
             assert torch.equal(o[6], outs[lo][6])
