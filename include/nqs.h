@@ -266,8 +266,8 @@ void nqs_set_autotune(int on);
  * that variant (a kernel with fewer variants takes its last one), bypassing
  * the autotuner and its cache; variant < 0 returns to normal selection.
  * Variants differ in threads per row (1, 2, 4) and, for sampling, teacher
- * forcing and the reverse sweep, in rows per 128-lane tile (128, or 64 to put
- * more SMs on a small batch; the reverse sweep also has 32).  Per-sample results (samples, log psi, cache,
+ * forcing and the reverse sweep, in rows per 128-lane tile (128, or 64 or 32
+ * to put more SMs on a small batch).  Per-sample results (samples, log psi, cache,
  * local energies) are bitwise the same in every variant; the gradient, a sum
  * over samples grouped by tile, is bitwise the same for the same rows per tile
  * and equal to rounding otherwise.  This is for timing and testing them one

@@ -169,7 +169,7 @@ struct Tc1Args {
   float* delta;              // chains
   unsigned long long* counter;
   WsHeader* hdr;
-  int rows;                  // sampling / teacher forcing: rows per 128-lane tile (128 or 64; set by the launcher)
+  int rows;                  // sampling / teacher forcing: rows per 128-lane tile (128, 64 or 32; set by the launcher)
 };
 
 struct TcBpttArgs {

@@ -188,6 +188,10 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   const int g = threadIdx.x / TT, tt = threadIdx.x % TT, lane = threadIdx.x & 31;
   const int wt = tt / 32, part = wt / 4, m = (wt % 4) * 32 + lane;
   const int u0 = part * DU;
+  // sampling / teacher forcing with 64- or 32-row tiles: warps whose 32 rows
+  // lie past the tile's rows skip the A rows, the epilogue and the cache
+  // stores (they still take part in every barrier)
+  const bool wact = MODE == 2 || GROUPS == 2 || (m & ~31) < a.rows;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16) + (uint32_t)(g * 256);
   const uint32_t bar_main = 1 + g, bar_x = 1 + GROUPS + g;
   uint8_t* sA = sm + S::kA + g * 128 * KA * 2;
@@ -289,9 +293,9 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       v.y = *reinterpret_cast<uint32_t*>(&p1);
       v.z = *reinterpret_cast<uint32_t*>(&p2);
       v.w = *reinterpret_cast<uint32_t*>(&p3);
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, u0 + 8 * kc, KA)) = v;
+      if (wact) *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, u0 + 8 * kc, KA)) = v;
     }
-    if (part == 0) {
+    if (part == 0 && wact) {
       // bf16 1.0 = 0x3F80: [1 | 1 | s_in == 0 | s_in == 1 | s_in == 0 | s_in == 1 | 0 0]
       const uint32_t one = 0x3F80u;
       const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
@@ -348,7 +352,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       tmem_ld8(trow + 2 * D + cu, bf[2]);
       tmem_ld8(trow + 3 * D + cu, bf[3]);
     };
-    if (any) issue(0, bufA);
+    if (any && wact) issue(0, bufA);
     if constexpr (PP) {
       bool oth = false;        // the other tile's idle flag from its last token
       if (g == 1 || pstep > 0) {
@@ -374,7 +378,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     float zc[DU / 16];
 #pragma unroll
     for (int c = 0; c < DU / 16; ++c) zc[c] = 0.0f;
-    if (any) {
+    if (any && wact) {
       constexpr int NS = DU / 8;
       // stage A: tu = tanh(a_u / 2 pre-scaled), ag = r * q + x_in
       auto stage_a = [&](float (&bf)[4][8], float (&tu)[8], float (&ag)[8]) {
@@ -488,7 +492,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       // cache store of this step's states, coalesced: every thread stages its
       // units of h, then each warp writes its 32 rows as whole row segments
       // (all rows of a tile are at the same site, pstep)
-      if (a.hcache && any) {
+      if (a.hcache && any && wact) {
 #pragma unroll
         for (int q = 0; q < DU / 4; ++q)
           reinterpret_cast<float4*>(stg)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
@@ -1122,12 +1126,12 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
     };
     return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
   }
-  // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128 or 64
-  // rows per tile (half-filled tiles put twice as many SMs on a small batch)
+  // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128, 64 or
+  // 32 rows per tile (partly filled tiles put more SMs on a small batch)
   const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
   auto run = [&](int v) {
     Tc1Args b = a;
-    b.rows = v < ns ? 128 : 64;
+    b.rows = 128 >> (v / ns);
     const int sv = v % ns;
     if (mode == 0) {
       if (sv == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
@@ -1138,7 +1142,7 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
     if (sv == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
     return launch_tc<D, 1, 1, 1>(b, img, wimg, st);
   };
-  return tuned_launch(mode, D, a.N, a.B, 2 * ns, run, none, st);
+  return tuned_launch(mode, D, a.N, a.B, 3 * ns, run, none, st);
 }
 
 }  // namespace

@@ -130,9 +130,8 @@ def test_bf16_reverse_sweep(N, d, B):
 
 
 def test_autotuned_variants_agree_bitwise():
-    """Every tile variant (1, 2 or 4 threads per row; 128, 64 or, in the reverse
-    sweep, 32 rows per tile)
-    computes bitwise the same samples, cache, local energies and energy
+    """Every tile variant (1, 2 or 4 threads per row; 128, 64 or 32 rows per
+    tile) computes bitwise the same samples, cache, local energies and energy
     statistics, and so does the autotuned choice (tuning off = first variant).
     The gradient is a sum over samples whose per-CTA grouping depends on the
     rows per tile: bitwise equal among variants with the same rows per tile,
@@ -157,8 +156,8 @@ def test_autotuned_variants_agree_bitwise():
             assert torch.equal(x, y)
         rel = float((o[6].double() - ref[6].double()).norm() / ref[6].double().norm())
         assert rel <= 1e-5, rel
-    # pinned reverse-sweep variants 0-2 (128 rows), 3-5 (64 rows) and 6-8 (32
-    # rows; the forward kernels take their last variant): bitwise within each class
+    # pinned variants 0-2 (128 rows), 3-5 (64 rows) and 6-8 (32 rows): bitwise
+    # within each class
     for lo, hi in ((3, 6), (6, 9), (9, 12)):
         for o in outs[lo + 1:hi]:
             assert torch.equal(o[6], outs[lo][6])
