@@ -174,7 +174,11 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
                             void* ws, size_t ws_bytes, void* stream);
 
 /* Gradient of L = sum_b w_b log psi(sigma_b) with respect to the flat
- * parameters, by a reverse sweep over the unrolled recurrence.
+ * parameters, by a reverse sweep over the unrolled recurrence.  In the 1D
+ * BF16 path a parallel pass first stores, per (sample, site), the factors
+ * with which the cell backward is linear in the incoming gradient (FP16,
+ * with the direct path's 1 - u kept to FP16 relative precision); the
+ * sequential sweep then only multiplies and runs the BF16 MMAs.
  *   weights device [B] float; hcache as above (required);
  *   grad    device [P] float (written; per-block partials are summed in FP64). */
 nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params,

@@ -118,6 +118,9 @@ Layout layout(const Dims& d, int64_t B, int op) {
         L.a = take((size_t)tc1d_bptt_partial_rows(B) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                 // weights
         L.c = take(BN * sizeof(float));                                         // readout gradients dz
+        L.e = take(tc1d_tape_bytes(B, d.N, d.d, 0));                            // tape: e
+        L.f = take(tc1d_tape_bytes(B, d.N, d.d, 1));                            // tape: BF16 states
+        L.g = take(tc1d_tape_bytes(B, d.N, d.d, 2));                            // tape: backward factors
         break;
       }
       const size_t grid = (size_t)(two ? gru2d_bptt_grid(d.d, B) : gru1d_bptt_grid(d.d, B));
@@ -463,6 +466,9 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.weights = weights;
     t.dz = at<float>(ws, L.c);
     t.partial = partial;
+    t.tape_e = at<float>(ws, L.e);
+    t.tape_x = at<uint8_t>(ws, L.f);
+    t.tape_k = at<uint8_t>(ws, L.g);
     t.hdr = static_cast<WsHeader*>(ws);
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));

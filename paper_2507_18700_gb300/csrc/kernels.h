@@ -175,12 +175,14 @@ struct Tc1Args {
 struct TcBpttArgs {
   int64_t B;
   int N, P;
-  int rows;                  // rows per 128-lane tile (128, 64 or 32; set by the launcher)
   const uint8_t* sigma;
   const float* hcache;
   const float* weights;
   float* dz;                 // [B, N] readout gradient per (sample, site)
   float* partial;            // [tc1d_bptt_partial_rows(B), P], zeroed
+  float* tape_e;             // [B, N] onehot_0(s_n) - p_0(h_n)
+  uint8_t* tape_x;           // [B, N, d] bf16 h_{n-1}
+  uint8_t* tape_k;           // [B, N, 5, d] fp16 cell-backward factors
   WsHeader* hdr;
 };
 
@@ -188,6 +190,7 @@ int tc1d_supported(int D);
 void tc1d_set_autotune(int on);
 void tc1d_set_variant(int v);
 int tc1d_bptt_partial_rows(int64_t B);
+size_t tc1d_tape_bytes(int64_t B, int N, int D, int which);   // which: 0 e, 1 x, 2 k
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st);
 cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, int D,
                       cudaStream_t st);

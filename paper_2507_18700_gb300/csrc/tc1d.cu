@@ -16,6 +16,8 @@
 #include <mutex>
 #include <tuple>
 
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -74,18 +76,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// 16-byte global -> shared copy that skips L1 (data read once), and the
-// arrival on an mbarrier that takes place when all of this thread's earlier
-// cp.async copies have landed (counted against the barrier's expected
-// arrivals: no increment); and a plain arrival.
-__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
-}
+// The arrival on an mbarrier that takes place when all of this thread's
+// earlier cp.async copies have landed (counted against the barrier's
+// expected arrivals: no increment).
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
 }
 
 // 8 consecutive TMEM columns of this thread's lane, and the wait that makes
@@ -558,60 +553,83 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
 }
 
 // ----------------------------------------------------------------------------
-// Reverse sweep on the tensor cores.  One CTA = one tile of 128 samples, one
-// row per sample (SPLIT threads per row, each on D / SPLIT units); sites
-// n = N-1 .. 0.  Per site:
-//   readout: logits of h_n taken from the forward cache (the exact FP32 state
-//            the forward pass read out, summed in the same order), giving
-//            dz_n = c_b (onehot(s_n) - softmax);
-//   X     = [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0]  (BF16, D + 16 columns)
-//   MMA_f: acc_f = X Wf^T with the engine's folded weights (4D columns: the
-//          u / r / q / x_in pre-activations, bitwise those of the forward);
-//   epilogue: gates, backward through the cell, G = [du_a | dr_a | dq | dc_a];
-//   MMA_b: acc_b = G[:, :3D] W3            (dh_{n-1} through the gates)
-//   MMA_w: acc_w += G^T X                  (weight, bias and one-hot-column
+// Reverse sweep on the tensor cores, in two launches.
+//
+// (1) tc1d_tape_kernel, parallel over (tile of 128 samples, site n): every
+// part of the cell backward that does not depend on the incoming gradient.
+// From the cached states it builds X_n = [h_{n-1} | 1 1 | onehot(s_{n-1}) x2
+// | 0] (BF16), recomputes acc_f = X_n Wf^T with the engine's folded weights
+// (the u / r / q / x_in pre-activations, bitwise those of the forward) and
+// writes per (sample, site):
+//   e_n = onehot_0(s_n) - p_0, p_0 the softmax of the readout of h_n (FP32;
+//         the readout gradient is dz_n = c_b e_n);
+//   x_n = BF16 h_{n-1}, the state part of X_n;
+//   k_n = five factors (FP16, 5 x D) with which the cell backward is linear
+//         in dh = dlog psi / dh_n:  G = [du_a | dr_a | dq | dc_a] = dh [k0 |
+//         k1 | k2 | k3] and the direct path dh k4, where (u, r gates, c the
+//         candidate, q its recurrent pre-activation)
+//           k0 = (c - h_{n-1}) u (1 - u),  k3 = u (1 - c^2),  k2 = k3 r,
+//           k1 = k2 q (1 - r),             k4 = 1 - u.
+// The tape is sample-minor in 8-unit groups ([n][vector][unit / 8][b][8]),
+// so that warps of consecutive samples read and write it in whole lines.
+// One CTA per SM walks a run of consecutive sites of one sample tile; the
+// cached state rows come in by coalesced cp.async into three shared-memory
+// buffers (h_{n-1}, h_n, and h_{n+1} in flight).
+//
+// (2) tc1d_bptt_kernel, one CTA per tile of ROWS samples, sites N-1 .. 0:
+//   dh = dz_n (U_0 - U_1) + carry,  G = dh k_n (BF16),  carry = dh k4
+//   MMA_b: acc_b = G[:, :3D] W3             (dh_{n-1} through the gates)
+//   MMA_w: acc_w += G^T X_n                 (weight, bias and one-hot-column
 //                                           gradients; G and X MN-major)
-//   carry = dh_n (1 - u) + acc_b.
-// The cached states h_{n-1} (MMA operand, cell backward) and h_n (readout)
-// sit in two shared-memory row buffers; the state two sites back is copied
-// in with cp.async while the current site runs.  acc_w stays in TMEM for the
-// whole sweep; readout gradients (U, c) come from dz and are reduced by a
-// separate kernel.
+//   carry += acc_b.
+// Only this chain is sequential.  All four TMEM lane quarters' warps work on
+// every tile: with ROWS < 128 the quarters split the hidden units, and the
+// quarters that hold the samples' TMEM lanes pass acc_b on through shared
+// memory.  The tape of later sites and the next X operand are copied in with
+// cp.async while a site runs, and MMA_w runs under the next site's
+// elementwise work.  acc_w stays in TMEM for the whole sweep; the readout
+// gradients (U, c) come from dz and the cache and are reduced by a separate
+// kernel.
 // ----------------------------------------------------------------------------
-template <int D, int SPLIT>
-struct BSmem {
-  static constexpr int KA = D + 16;                       // X columns
-  static constexpr int GW = 4 * D >= 128 ? 4 * D : 128;  // G row width (>= one M = 128 operand)
-  static constexpr int kWf = 0;                           // [4D x KA] bf16, K-major (folded)
-  static constexpr int kWt = kWf + 4 * D * KA * 2;        // [D x 3D] bf16, K-major
-  static constexpr int kX = kWt + 3 * D * D * 2;          // [128 x KA] bf16
-  static constexpr int kG = kX + 128 * KA * 2;            // [128 x GW] bf16
-  static constexpr int HS = D + 4;                        // state row stride (floats): 16-byte
-                                                          // loads of 8 consecutive rows hit distinct banks
-  static constexpr int kH = kG + 128 * GW * 2;            // 2 x [128 x HS] f32 state rows
-  static constexpr int kSmall = kH + 2 * 128 * HS * 4;    // 12D + 4 floats
-  static constexpr int kDU = kSmall + (12 * D + 4) * 4;   // D floats: U[0] - U[1]
-  static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 floats (readout exchange)
-  static constexpr int kBar = (kZ + SPLIT * 128 * 4 + 15) / 16 * 16;   // 4 mbarriers
-  static constexpr int kSlot = kBar + 32;
-  static constexpr int kBytes = 1024 + kSlot + 16;
-  // TMEM columns
-  static constexpr int cF = 0, cB = 4 * D, cW0 = 5 * D, cW1 = cW0 + KA;
-  static_assert(cW1 + KA <= 512, "TMEM budget");
-  static_assert(kBytes <= 227 * 1024, "shared memory budget");
-};
-
-__device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
+__device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
   __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
   __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
   __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
   __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
-  uint4 q;
-  q.x = *reinterpret_cast<uint32_t*>(&p0);
-  q.y = *reinterpret_cast<uint32_t*>(&p1);
-  q.z = *reinterpret_cast<uint32_t*>(&p2);
-  q.w = *reinterpret_cast<uint32_t*>(&p3);
-  *reinterpret_cast<uint4*>(dst) = q;
+  return make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
+                    *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+}
+
+__device__ __forceinline__ uint4 pack_f16x8(const float* v) {
+  __half2 p0 = __floats2half2_rn(v[0], v[1]);
+  __half2 p1 = __floats2half2_rn(v[2], v[3]);
+  __half2 p2 = __floats2half2_rn(v[4], v[5]);
+  __half2 p3 = __floats2half2_rn(v[6], v[7]);
+  return make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
+                    *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+}
+
+__device__ __forceinline__ void unpack_f16x8(uint4 q, float* v) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
+    const float2 f = __half22float2(h);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+__device__ __forceinline__ void st_bf16x8(uint8_t* dst, const float* v) {
+  *reinterpret_cast<uint4*>(dst) = pack_bf16x8(v);
+}
+
+// 16-byte cp.async that copies `bytes` (16 or 0) and zero-fills the rest.
+__device__ __forceinline__ void cp_async16_zf(void* smem, const void* gmem, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
+               :
+               : "r"(tc::smem_addr(smem)), "l"(gmem), "r"(bytes)
+               : "memory");
 }
 
 // Spin byte load kept in place (issued one site ahead of its use).
@@ -621,172 +639,153 @@ __device__ __forceinline__ uint32_t ldg_u8(const uint8_t* p) {
   return v;
 }
 
-template <int D, int SPLIT>
-__global__ void __launch_bounds__(128 * SPLIT, 1)
-tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfimg, const uint8_t* __restrict__ wtimg,
-                 TcBpttArgs a) {
-  using S = BSmem<D, SPLIT>;
-  constexpr int NT = 128 * SPLIT;
-  constexpr int KA = S::KA;
-  constexpr int DU = D / SPLIT;            // hidden units per thread
-  static_assert(DU % 16 == 0, "at least 16 units per thread");
+// Tape element offsets (in 16-byte groups of 8 units) of sample b, site n.
+__device__ __forceinline__ int64_t tape_k_group(int64_t B, int n, int c, int g, int64_t b, int D) {
+  return (((int64_t)n * 5 + c) * (D / 8) + g) * B + b;
+}
+__device__ __forceinline__ int64_t tape_x_group(int64_t B, int n, int g, int64_t b, int D) {
+  return ((int64_t)n * (D / 8) + g) * B + b;
+}
+
+template <int D>
+struct TpS {
+  static constexpr int SPLIT = D / 16;                    // threads per row (16 units each)
+  static constexpr int NT = 128 * SPLIT;
+  static constexpr int KA = D + 16;                       // X columns
+  static constexpr int HS = D + 4;                        // state row stride (floats): 16-byte
+                                                          // accesses of 8 consecutive rows hit distinct banks
+  static constexpr int kWf = 0;                           // [4D x KA] bf16, K-major (folded)
+  static constexpr int kA = kWf + 4 * D * KA * 2;         // [128 x KA] bf16
+  static constexpr int kH = kA + 128 * KA * 2;            // 3 x [128 x HS] f32 state rows
+  static constexpr int kDU = kH + 3 * 128 * HS * 4;       // D floats: U[0] - U[1]
+  static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 floats (readout exchange)
+  static constexpr int kBar = kZ + SPLIT * 128 * 4;       // 4 mbarriers: MMA, 3 state buffers
+  static constexpr int kSlot = kBar + 32;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static constexpr int kCols = 4 * D;                     // 64, 128 or 256 columns
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+};
+
+template <int D>
+__global__ void __launch_bounds__(TpS<D>::NT, 1)
+tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfimg, TcBpttArgs a, int sites_per_run,
+                 int runs_per_tile) {
+  using S = TpS<D>;
+  constexpr int SPLIT = S::SPLIT, NT = S::NT, KA = S::KA, HS = S::HS, DU = D / SPLIT;
+  static_assert(DU == 16, "16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sWf = sm + S::kWf;
-  uint8_t* sWt = sm + S::kWt;
-  uint8_t* sX = sm + S::kX;
-  uint8_t* sG = sm + S::kG;
+  uint8_t* sA = sm + S::kA;
   float* sH = reinterpret_cast<float*>(sm + S::kH);
-  float* small = reinterpret_cast<float*>(sm + S::kSmall);
   float* dU = reinterpret_cast<float*>(sm + S::kDU);
   float* zb = reinterpret_cast<float*>(sm + S::kZ);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
   for (int i = threadIdx.x; i < 4 * D * KA * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sWf)[i] = reinterpret_cast<const uint4*>(wfimg)[i];
-  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += NT)
-    reinterpret_cast<uint4*>(sWt)[i] = reinterpret_cast<const uint4*>(wtimg)[i];
-  for (int i = threadIdx.x; i < (12 * D + 4) / 4; i += NT)
-    reinterpret_cast<float4*>(small)[i] = reinterpret_cast<const float4*>(img)[i];
   for (int i = threadIdx.x; i < D; i += NT) dU[i] = img[10 * D + i] - img[11 * D + i];
-  for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += NT) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
-    tc::mbar_init(&mbar[2], NT);     // state row buffer 0 filled (every thread arrives)
-    tc::mbar_init(&mbar[3], NT);     // state row buffer 1 filled
+    tc::mbar_init(&mbar[0], 1);                           // MMA done
+    for (int k = 1; k < 4; ++k) tc::mbar_init(&mbar[k], NT);   // state buffer k - 1 filled
     tc::mbar_fence_init();
   }
-  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  // thread -> (row, unit range): warp w serves rows 32 (w % 4) + lane and
-  // units [(w / 4) DU, (w / 4 + 1) DU)
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
   const int u0 = part * DU;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
-  const float dc = small[12 * D] - small[12 * D + 1];
+  const float dc = img[12 * D] - img[12 * D + 1];
   const int N = a.N;
-  const int64_t b = (int64_t)blockIdx.x * a.rows + m;
-  const bool valid = m < a.rows && b < a.B;
-  // warps whose 32 rows lie past the tile's rows (64- and 32-row tiles) skip
-  // the per-site work; they still fill their row buffers with zeros, arrive on
-  // the row barriers and take part in every CTA barrier
-  const bool wact = (m & ~31) < a.rows;
-  const int kw = a.rows / 16;              // K = 16 steps of the weight-gradient MMA
-  const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
-  // this thread's units of the two state rows
-  float* hrow[2] = {sH + (0 * 128 + m) * S::HS + u0, sH + (1 * 128 + m) * S::HS + u0};
+  const int64_t B = a.B;
+  const int64_t runs = (B + 127) / 128 * runs_per_tile;
+  constexpr uint32_t idesc = tc::make_idesc_bf16(128, 4 * D);
+  uint32_t phases = 0;                     // bit k: the phase of mbar[k] waited for next
   bool timed_out = false;
-  // copy h_n of this sample (zero for n < 0 or past the batch) into row buffer
-  // k: this thread's units of the row by 16-byte cp.async copies (LSU path:
-  // one bulk copy per thread queued 512 small requests per site on the copy
-  // engine), completing on mbar[2 + k].  A thread reads only its own units.
-  bool inflight[2] = {false, false};   // a fill of the buffer not yet waited for
-  auto fetch = [&](int n, int k) {
-    inflight[k] = true;
-    if (valid && n >= 0) {
-      const float* src = a.hcache + (b * N + n) * D + u0;
-#pragma unroll
-      for (int q = 0; q < DU / 4; ++q) cp_async16_cg(hrow[k] + 4 * q, src + 4 * q);
-      cp_async_arrive_noinc(&mbar[2 + k]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < DU / 4; ++q) reinterpret_cast<float4*>(hrow[k])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      mbar_arrive(&mbar[2 + k]);
+  auto wait = [&](int k) {
+    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    phases ^= 1u << k;
+  };
+  // state rows h_n of the tile's 128 samples into buffer k, 16 bytes per copy,
+  // consecutive threads on consecutive pieces of a row (zeros for n outside
+  // [0, N) or samples past the batch)
+  auto load_rows = [&](int64_t bt, int n, int k) {
+    float* dst = sH + k * 128 * HS;
+    constexpr int PR = D / 4;              // pieces per row
+    for (int q = threadIdx.x; q < 128 * PR; q += NT) {
+      const int row = q / PR, pc = q % PR;
+      const int64_t b = bt * 128 + row;
+      const bool ok = b < B && n >= 0 && n < N;
+      const float* src = ok ? a.hcache + (b * N + n) * D + 4 * pc : a.hcache;
+      cp_async16_zf(dst + row * HS + 4 * pc, src, ok ? 16u : 0u);
     }
+    cp_async_arrive_noinc(&mbar[1 + k]);
   };
-  uint32_t ph_h[2] = {0, 0};
-  auto wait_rows = [&](int k) {
-    if (!tc::mbar_wait(&mbar[2 + k], ph_h[k], kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
-    ph_h[k] ^= 1;
-    inflight[k] = false;
-  };
-  float carry[DU];
-#pragma unroll
-  for (int u = 0; u < DU; ++u) carry[u] = 0.0f;
-  uint32_t ph_f = 0, ph_b = 0;
-
-  constexpr uint32_t idesc_f = tc::make_idesc_bf16(128, 4 * D);
-  constexpr uint32_t idesc_b = tc::make_idesc_bf16(128, D);
-  constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, KA) | (1u << 15) | (1u << 16);
-  // row buffers: cur = h_n, nxt = h_{n-1}
-  int cur = 0;
-  fetch(N - 1, 0);
-  fetch(N - 2, 1);
-  wait_rows(0);
-  uint32_t s_n = valid ? ldg_u8(a.sigma + b * N + N - 1) : 0u;
-  uint32_t s_p = (valid && N > 1) ? ldg_u8(a.sigma + b * N + N - 2) : 0u;
-
-  for (int n = N - 1; n >= 0; --n) {
-    const int nxt = cur ^ 1;
-    wait_rows(nxt);
-    const float* hn = hrow[cur];
-    const float* hp = hrow[nxt];
-    // spin two sites back, for the next site's input
-    const uint32_t s_pp = (valid && n >= 2) ? ldg_u8(a.sigma + b * N + n - 2) : 0u;
-    const int s_in = n > 0 ? (s_p ? 1 : 0) : -1;
-    float z = 0.0f;
-    if (wact) {
-      // ---- X row: [h_{n-1} | 1 1 | onehot(s_{n-1}) x2 | 0] ----
+  for (int64_t run = blockIdx.x; run < runs; run += gridDim.x) {
+    const int64_t bt = run / runs_per_tile;
+    const int n0 = (int)(run % runs_per_tile) * sites_per_run;
+    const int n1 = n0 + sites_per_run < N ? n0 + sites_per_run : N;
+    if (n0 >= n1) continue;                 // uniform
+    // h_{n} sits in buffer (n - n0 + 1) % 3
+    load_rows(bt, n0 - 1, 0);
+    load_rows(bt, n0, 1);
+    wait(1);
+    const int64_t b = bt * 128 + m;
+    const bool valid = b < B;
+    for (int n = n0; n < n1; ++n) {
+      const int kp = (n - n0) % 3, kn = (n - n0 + 1) % 3;
+      if (n + 1 < n1) load_rows(bt, n + 1, (n - n0 + 2) % 3);
+      wait(1 + kn);
+      const float* hp = sH + (kp * 128 + m) * HS + u0;
+      const float* hn = sH + (kn * 128 + m) * HS + u0;
+      // ---- X_n row (also the tape's x_n) ----
 #pragma unroll
       for (int c = 0; c < DU / 8; ++c) {
         float v[8];
         const float4 x0 = reinterpret_cast<const float4*>(hp)[2 * c];
         const float4 x1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
         v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w; v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
-        st_bf16x8(sX + tc::kmajor_offset(m, u0 + 8 * c, KA), v);
+        const uint4 q = pack_bf16x8(v);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, u0 + 8 * c, KA)) = q;
+        if (valid) reinterpret_cast<uint4*>(a.tape_x)[tape_x_group(B, n, (u0 >> 3) + c, b, D)] = q;
       }
       if (part == 0) {
+        const int s_in = (valid && n > 0) ? (a.sigma[b * N + n - 1] ? 1 : 0) : -1;
         const uint32_t one = 0x3F80u;
         const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
-        *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
-        *reinterpret_cast<uint4*>(sX + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
       }
-      // ---- readout of h_n (logit difference): 16-unit chunk sums in order, chunks
-      // and parts by fixed trees, as in the forward pass.  The row is read as
-      // float4 (scalar reads of rows HS floats apart are 4-way bank conflicts) ----
-      float zc[DU / 16];
+      // ---- readout of h_n: 16-unit chunk sums in order, parts by a fixed
+      // pairwise tree, as in the forward pass ----
+      float z = 0.0f;
 #pragma unroll
-      for (int c = 0; c < DU / 16; ++c) {
-        float s0 = 0.0f;
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 h4 = reinterpret_cast<const float4*>(hn)[q4];
+        const float4 w4 = reinterpret_cast<const float4*>(dU + u0)[q4];
+        z = fmaf(w4.x, h4.x, z);
+        z = fmaf(w4.y, h4.y, z);
+        z = fmaf(w4.z, h4.z, z);
+        z = fmaf(w4.w, h4.w, z);
+      }
+      if constexpr (SPLIT > 1) zb[part * 128 + m] = z;
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (threadIdx.x == 0) {
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 h4 = reinterpret_cast<const float4*>(hn)[4 * c + q4];
-          const float4 w4 = reinterpret_cast<const float4*>(dU + u0)[4 * c + q4];
-          s0 = fmaf(w4.x, h4.x, s0);
-          s0 = fmaf(w4.y, h4.y, s0);
-          s0 = fmaf(w4.z, h4.z, s0);
-          s0 = fmaf(w4.w, h4.w, s0);
+        for (int k = 0; k < KA / 16; ++k) {
+          const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (KA / 8) * 128);
+          const uint64_t db = tc::make_desc(tc::smem_addr(sWf) + k * 256, 128, (KA / 8) * 128);
+          tc::mma_bf16(tbase, da, db, idesc, k > 0);
         }
-        zc[c] = s0;
+        tc::mma_commit(&mbar[0]);
       }
-#pragma unroll
-      for (int w = 1; w < DU / 16; w *= 2)
-#pragma unroll
-        for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
-      z = zc[0];
-      if constexpr (SPLIT > 1) zb[part * 128 + m] = zc[0];
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    // a wait that ran out anywhere in the CTA ends the sweep for every thread here
-    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
-    tc::fence_after_sync();
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < KA / 16; ++k) {
-        const uint64_t da = tc::make_desc(tc::smem_addr(sX) + k * 256, 128, (KA / 8) * 128);
-        const uint64_t db = tc::make_desc(tc::smem_addr(sWf) + k * 256, 128, (KA / 8) * 128);
-        tc::mma_bf16(tbase + S::cF, da, db, idesc_f, k > 0);
-      }
-      tc::mma_commit(&mbar[0]);
-    }
-    float dz0 = 0.0f;
-    if (wact) {
       if constexpr (SPLIT > 1) {
         float pz[SPLIT];
 #pragma unroll
@@ -797,129 +796,348 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
           for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
         z = pz[0];
       }
-      const float d = z + dc;
-      dz0 = coef * ((s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(d));
-    }
-    // h_n is no longer needed: its buffer takes h_{n-2}
-    if (n >= 1) fetch(n - 2, cur);
-    if (valid && part == 0) a.dz[b * N + n] = dz0;
-    if (wact) {
-      if (!tc::mbar_wait(&mbar[0], ph_f, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+      if (valid && part == 0) {
+        const int s_n = a.sigma[b * N + n] ? 1 : 0;
+        a.tape_e[(int64_t)n * B + b] = (s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc);
+      }
+      wait(0);
       tc::fence_after_sync();
-      // ---- gates and backward through the cell, G = [du_a | dr_a | dq | dc_a] ----
-      // accumulator columns in 8-unit sub-chunks, double-buffered (the loads of
-      // sub-chunk c + 1 are in flight while sub-chunk c is computed)
-      float bufA[4][8], bufB[4][8];
-      auto issue = [&](int c, float (&bf)[4][8]) {
-        const int cu = u0 + 8 * c;
-        tmem_ld8(trow + S::cF + cu, bf[0]);
-        tmem_ld8(trow + S::cF + D + cu, bf[1]);
-        tmem_ld8(trow + S::cF + 2 * D + cu, bf[2]);
-        tmem_ld8(trow + S::cF + 3 * D + cu, bf[3]);
-      };
-      issue(0, bufA);
+      // ---- the five factors, 8 units at a time ----
 #pragma unroll
-      for (int c = 0; c < DU / 8; ++c) {
-        float (&acc)[4][8] = (c & 1) ? bufB : bufA;
+      for (int sc = 0; sc < DU / 8; ++sc) {
+        const int cu = u0 + 8 * sc;
+        float acc[4][8];
+        tmem_ld8(trow + cu, acc[0]);
+        tmem_ld8(trow + D + cu, acc[1]);
+        tmem_ld8(trow + 2 * D + cu, acc[2]);
+        tmem_ld8(trow + 3 * D + cu, acc[3]);
         tmem_wait_regs(acc);
-        if (c + 1 < DU / 8) issue(c + 1, (c & 1) ? bufA : bufB);
-        const int cu = u0 + 8 * c;
-        float hv[8], wv[8];
+        float hv[8];
         {
-          const float4 p0 = reinterpret_cast<const float4*>(hp)[2 * c];
-          const float4 p1 = reinterpret_cast<const float4*>(hp)[2 * c + 1];
-          const float4 w0 = reinterpret_cast<const float4*>(dU + cu)[0];
-          const float4 w1 = reinterpret_cast<const float4*>(dU + cu)[1];
-          hv[0] = p0.x; hv[1] = p0.y; hv[2] = p0.z; hv[3] = p0.w; hv[4] = p1.x; hv[5] = p1.y; hv[6] = p1.z; hv[7] = p1.w;
-          wv[0] = w0.x; wv[1] = w0.y; wv[2] = w0.z; wv[3] = w0.w; wv[4] = w1.x; wv[5] = w1.y; wv[6] = w1.z; wv[7] = w1.w;
+          const float4 x0 = reinterpret_cast<const float4*>(hp)[2 * sc];
+          const float4 x1 = reinterpret_cast<const float4*>(hp)[2 * sc + 1];
+          hv[0] = x0.x; hv[1] = x0.y; hv[2] = x0.z; hv[3] = x0.w; hv[4] = x1.x; hv[5] = x1.y; hv[6] = x1.z; hv[7] = x1.w;
         }
-        float g0[8], g1[8], g2[8], g3[8];
+        float k0[8], k1[8], k2[8], k3[8], k4[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int j = 8 * c + q;
           const float tu = hw_tanh(acc[0][q]), tr = hw_tanh(acc[1][q]);
           const float ug = fmaf(0.5f, tu, 0.5f), rg = fmaf(0.5f, tr, 0.5f);
           const float cg = hw_tanh(fmaf(rg, acc[2][q], acc[3][q]));
-          const float dh = fmaf(dz0, wv[q], carry[j]);
-          const float dc = dh * ug;
-          const float du = dh * (cg - hv[q]);
-          carry[j] = dh - dc;                              // direct path; acc_b adds the rest
-          const float dac = dc * fmaf(-cg, cg, 1.0f);
-          g0[q] = du * (0.25f * fmaf(-tu, tu, 1.0f));      // u (1 - u) = (1 - tanh^2) / 4
-          const float dq = dac * rg;
-          g1[q] = dq * acc[2][q] * (0.5f - 0.5f * tr);     // dac q r (1 - r)
-          g2[q] = dq;
-          g3[q] = dac;
+          k3[q] = ug * fmaf(-cg, cg, 1.0f);                      // u (1 - c^2)
+          k2[q] = k3[q] * rg;
+          k1[q] = k2[q] * acc[2][q] * (0.5f - 0.5f * tr);        // q (1 - r)
+          k0[q] = (cg - hv[q]) * (0.25f * fmaf(-tu, tu, 1.0f));  // u (1 - u) = (1 - tanh^2) / 4
+          k4[q] = 0.5f - 0.5f * tu;                              // 1 - u
         }
-        st_bf16x8(sG + tc::kmajor_offset(m, cu, S::GW), g0);
-        st_bf16x8(sG + tc::kmajor_offset(m, D + cu, S::GW), g1);
-        st_bf16x8(sG + tc::kmajor_offset(m, 2 * D + cu, S::GW), g2);
-        st_bf16x8(sG + tc::kmajor_offset(m, 3 * D + cu, S::GW), g3);
+        if (valid) {
+          uint4* kt = reinterpret_cast<uint4*>(a.tape_k);
+          const int g = cu >> 3;
+          kt[tape_k_group(B, n, 0, g, b, D)] = pack_f16x8(k0);
+          kt[tape_k_group(B, n, 1, g, b, D)] = pack_f16x8(k1);
+          kt[tape_k_group(B, n, 2, g, b, D)] = pack_f16x8(k2);
+          kt[tape_k_group(B, n, 3, g, b, D)] = pack_f16x8(k3);
+          kt[tape_k_group(B, n, 4, g, b, D)] = pack_f16x8(k4);
+        }
       }
+      // TMEM, the A tile, the readout exchange and buffer kp are free again
+      tc::fence_before_sync();
+      if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+      tc::fence_after_sync();
     }
-    ph_f ^= 1;
+    if (timed_out) break;                   // uniform
+    // the run's last prefetch was not issued (n + 1 == n1): every buffer's
+    // fills have been waited for, so the next run starts from a clean state
+  }
+  cp_async_wait_all();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kCols);
+}
+
+template <int D, int SPLIT, int ROWS>
+struct BSmem {
+  static constexpr int KA = D + 16;                       // X columns
+  static constexpr int GW = 4 * D >= 128 ? 4 * D : 128;  // G row width (>= one M = 128 operand)
+  static constexpr int RQ = ROWS / 32;                    // lane quarters holding distinct samples
+  static constexpr int NS = (4 / RQ) * SPLIT;             // unit slices per sample
+  static constexpr int DU = D / NS;                       // units per thread
+  static constexpr int NB = ROWS <= 64 ? 2 : 1;           // tape buffers
+  static constexpr int KB = 5 * D * ROWS * 2;             // tape buffer: [5][D/8][ROWS][8] fp16
+  static constexpr int CS = D + 4;                        // acc_b exchange row stride (floats)
+  static constexpr int kWt = 0;                           // [D x 3D] bf16, K-major
+  static constexpr int kX = kWt + 3 * D * D * 2;          // 2 x [128 x KA] bf16
+  static constexpr int kG = kX + 2 * 128 * KA * 2;        // [128 x GW] bf16
+  static constexpr int kK = kG + 128 * GW * 2;            // NB tape buffers
+  static constexpr int kC = kK + NB * KB;                 // [ROWS x CS] f32 (ROWS < 128)
+  static constexpr int kDU = kC + (ROWS < 128 ? ROWS * CS * 4 : 0);   // D floats: U[0] - U[1]
+  static constexpr int kBar = kDU + D * 4;                // 6 mbarriers
+  static constexpr int kSlot = kBar + 48;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  // TMEM columns: acc_b in three accumulators (one per gate block of G, so
+  // that the K steps form three independent chains), acc_w in two halves
+  static constexpr int cB = 0, cW0 = 3 * D, cW1 = 3 * D + KA;
+  static constexpr int kCols = cW1 + KA <= 128 ? 128 : cW1 + KA <= 256 ? 256 : 512;
+  static_assert(cW1 + KA <= kCols, "TMEM budget");
+  static_assert(DU >= 8 && DU % 8 == 0 && ROWS % 32 == 0 && ROWS <= 128, "tile shape");
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+};
+
+template <int D, int SPLIT, int ROWS>
+__global__ void __launch_bounds__(128 * SPLIT, 1)
+tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtimg, TcBpttArgs a) {
+  using S = BSmem<D, SPLIT, ROWS>;
+  constexpr int NT = 128 * SPLIT;
+  constexpr int KA = S::KA, NB = S::NB, RQ = S::RQ, DU = S::DU, CS = S::CS;
+  constexpr int DG = D / 8;                // 8-unit groups per state
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sWt = sm + S::kWt;
+  uint8_t* sX = sm + S::kX;
+  uint8_t* sG = sm + S::kG;
+  uint8_t* sK = sm + S::kK;
+  float* sC = reinterpret_cast<float*>(sm + S::kC);
+  float* dU = reinterpret_cast<float*>(sm + S::kDU);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 3 * D * D * 2 / 16; i += NT)
+    reinterpret_cast<uint4*>(sWt)[i] = reinterpret_cast<const uint4*>(wtimg)[i];
+  for (int i = threadIdx.x; i < D; i += NT) dU[i] = img[10 * D + i] - img[11 * D + i];
+  for (int i = threadIdx.x; i < 128 * S::GW * 2 / 16; i += NT) reinterpret_cast<uint4*>(sG)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);              // MMA_b done
+    tc::mbar_init(&mbar[1], 1);              // MMA_w done
+    for (int k = 2; k < 6; ++k) tc::mbar_init(&mbar[k], NT);   // tape buffers 0, 1 and X buffers 0, 1 filled
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  // thread -> (sample, unit slice): warp w is in TMEM lane quarter q = w % 4;
+  // quarters q % RQ hold distinct samples s = 32 (q % RQ) + lane, and the
+  // 4 / RQ quarters over a sample with the SPLIT warps of a quarter split
+  // its units into NS slices of DU
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, q = wt % 4, p = wt / 4;
+  const int s = 32 * (q % RQ) + lane;
+  const int sl = (q / RQ) * SPLIT + p;
+  const int u0 = sl * DU;
+  const uint32_t tq = tbase + ((uint32_t)(32 * q) << 16);   // this warp's TMEM lanes
+  const int N = a.N;
+  const int64_t B = a.B;
+  const int64_t b = (int64_t)blockIdx.x * ROWS + s;
+  const bool valid = b < B;
+  const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+  bool timed_out = false;
+  uint32_t phases = 0;                     // bit k: the phase of mbar[k] this thread waits for next
+  auto wait = [&](int k) {
+    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    phases ^= 1u << k;
+  };
+  // tape factors k_n of this thread's units into tape buffer kb (zeros past
+  // the batch: G = 0 there).  Global groups of sample b: site n, vector c,
+  // 8-unit group g at kt_b + n (5 DG B) + c (DG B) + g B.
+  const uint4* kt_b = reinterpret_cast<const uint4*>(a.tape_k) + (valid ? b + (int64_t)(u0 >> 3) * B : 0);
+  const uint4* xt_b = reinterpret_cast<const uint4*>(a.tape_x) + (valid ? b + (int64_t)(u0 >> 3) * B : 0);
+  const int64_t vstride = (int64_t)DG * B;
+  const uint32_t cpb = valid ? 16u : 0u;
+  auto fetch_k = [&](int n, int kb) {
+    uint8_t* dst = sK + kb * S::KB + ((u0 >> 3) * ROWS + s) * 16;
+    const uint4* src = kt_b + (valid ? (int64_t)n * 5 * vstride : 0);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+#pragma unroll
+      for (int g = 0; g < DU / 8; ++g) cp_async16_zf(dst + (c * DG + g) * ROWS * 16, src + (valid ? g * B : 0), cpb);
+      if (valid) src += vstride;
+    }
+    cp_async_arrive_noinc(&mbar[2 + kb]);
+  };
+  // X_n = [x_n | 1 1 | onehot(s_{n-1}) x2 | 0] into X buffer xb; s_in is
+  // s_{n-1} (-1: none), loaded one site ahead
+  auto fetch_x = [&](int n, int xb, int s_in) {
+    uint8_t* xs = sX + xb * (128 * KA * 2);
+    const uint4* src = xt_b + (valid ? (int64_t)n * vstride : 0);
+#pragma unroll
+    for (int g = 0; g < DU / 8; ++g)
+      cp_async16_zf(xs + tc::kmajor_offset(s, u0 + 8 * g, KA), src + (valid ? g * B : 0), cpb);
+    if (sl == 0) {
+      const uint32_t one = 0x3F80u;
+      const uint32_t oh = (s_in == 0 ? one : 0u) | ((s_in == 1 ? one : 0u) << 16);
+      *reinterpret_cast<uint4*>(xs + tc::kmajor_offset(s, D, KA)) = make_uint4(one | (one << 16), oh, oh, 0u);
+      *reinterpret_cast<uint4*>(xs + tc::kmajor_offset(s, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_arrive_noinc(&mbar[4 + xb]);
+  };
+  float carry[DU];
+#pragma unroll
+  for (int u = 0; u < DU; ++u) carry[u] = 0.0f;
+
+  constexpr uint32_t idesc_b = tc::make_idesc_bf16(128, D);
+  constexpr uint32_t idesc_w = tc::make_idesc_bf16(128, KA) | (1u << 15) | (1u << 16);
+  fetch_k(N - 1, (N - 1) % NB);
+  if (NB == 2 && N > 1) fetch_k(N - 2, (N - 2) % NB);
+  fetch_x(N - 1, (N - 1) & 1, (valid && N > 1) ? (ldg_u8(a.sigma + b * N + N - 2) ? 1 : 0) : -1);
+  float e_cur = valid ? a.tape_e[(int64_t)(N - 1) * B + b] : 0.0f;
+  uint32_t s_pre = (valid && N > 2) ? ldg_u8(a.sigma + b * N + N - 3) : 0u;   // s_{n-2} at site n
+
+  for (int n = N - 1; n >= 0; --n) {
+    const int xb = n & 1, kb = n % NB;
+    // MMA_w of site n + 1 has read G and X buffer xb ^ 1
+    if (n < N - 1) {
+      wait(1);
+      tc::fence_after_sync();
+    }
+    if (n > 0) fetch_x(n - 1, xb ^ 1, (valid && n > 1) ? (s_pre ? 1 : 0) : -1);
+    s_pre = (valid && n > 2) ? ldg_u8(a.sigma + b * N + n - 3) : 0u;
+    const float e_next = (valid && n > 0) ? a.tape_e[(int64_t)(n - 1) * B + b] : 0.0f;
+    wait(2 + kb);
+    const float dz0 = coef * e_cur;
+    if (valid && sl == 0) a.dz[b * N + n] = dz0;
+    // ---- G = dh k_n, carry = dh k4, 8 units at a time ----
+    const uint8_t* kr = sK + kb * S::KB + s * 16;
+#pragma unroll
+    for (int sc = 0; sc < DU / 8; ++sc) {
+      const int cu = u0 + 8 * sc, gg = cu >> 3;
+      float k0[8], k1[8], k2[8], k3[8], k4[8], w[8];
+      unpack_f16x8(*reinterpret_cast<const uint4*>(kr + (0 * DG + gg) * ROWS * 16), k0);
+      unpack_f16x8(*reinterpret_cast<const uint4*>(kr + (1 * DG + gg) * ROWS * 16), k1);
+      unpack_f16x8(*reinterpret_cast<const uint4*>(kr + (2 * DG + gg) * ROWS * 16), k2);
+      unpack_f16x8(*reinterpret_cast<const uint4*>(kr + (3 * DG + gg) * ROWS * 16), k3);
+      unpack_f16x8(*reinterpret_cast<const uint4*>(kr + (4 * DG + gg) * ROWS * 16), k4);
+      {
+        const float4 w0 = reinterpret_cast<const float4*>(dU + cu)[0];
+        const float4 w1 = reinterpret_cast<const float4*>(dU + cu)[1];
+        w[0] = w0.x; w[1] = w0.y; w[2] = w0.z; w[3] = w0.w; w[4] = w1.x; w[5] = w1.y; w[6] = w1.z; w[7] = w1.w;
+      }
+      float g0[8], g1[8], g2[8], g3[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int j = 8 * sc + i;
+        const float dh = fmaf(dz0, w[i], carry[j]);
+        g0[i] = dh * k0[i];
+        g1[i] = dh * k1[i];
+        g2[i] = dh * k2[i];
+        g3[i] = dh * k3[i];
+        carry[j] = dh * k4[i];                           // direct path; acc_b adds the rest
+      }
+      st_bf16x8(sG + tc::kmajor_offset(s, cu, S::GW), g0);
+      st_bf16x8(sG + tc::kmajor_offset(s, D + cu, S::GW), g1);
+      st_bf16x8(sG + tc::kmajor_offset(s, 2 * D + cu, S::GW), g2);
+      st_bf16x8(sG + tc::kmajor_offset(s, 3 * D + cu, S::GW), g3);
+    }
+    // this thread has read its part of tape buffer kb: it takes site n - NB
+    if (n - NB >= 0) fetch_k(n - NB, kb);
+    wait(4 + xb);                          // X_n is in place
+    e_cur = e_next;
     tc::fence_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    // a wait that ran out anywhere in the CTA ends the sweep for every thread here
+    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
     tc::fence_after_sync();
     if (threadIdx.x == 0) {
-      // dh_{n-1} += G[:, :3D] W3   (K-major: LBO = 128 B along K, SBO = row-group stride)
+      // dh_{n-1} = G[:, :3D] W3 as three K chains, one per gate block j
+      // (acc_b^j = G_j W3_j; K-major: LBO = 128 B along K, SBO = row-group
+      // stride), issued interleaved so that the chains overlap
 #pragma unroll
-      for (int k = 0; k < 3 * D / 16; ++k) {
-        const uint64_t da = tc::make_desc(tc::smem_addr(sG) + k * 256, 128, (S::GW / 8) * 128);
-        const uint64_t db = tc::make_desc(tc::smem_addr(sWt) + k * 256, 128, (3 * D / 8) * 128);
-        tc::mma_bf16(tbase + S::cB, da, db, idesc_b, k > 0);
-      }
-      // acc_w += G^T X over this tile's samples (a.rows of them: rows past it
-      // would add exact zeros), halves of 128 gate rows.  Both operands
+      for (int kk = 0; kk < D / 16; ++kk)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int k = j * (D / 16) + kk;
+          const uint64_t da = tc::make_desc(tc::smem_addr(sG) + k * 256, 128, (S::GW / 8) * 128);
+          const uint64_t db = tc::make_desc(tc::smem_addr(sWt) + k * 256, 128, (3 * D / 8) * 128);
+          tc::mma_bf16(tbase + S::cB + j * D, da, db, idesc_b, kk > 0);
+        }
+      tc::mma_commit(&mbar[0]);
+    } else if (threadIdx.x == 32) {
+      // acc_w += G^T X_n over the tile's ROWS samples, halves of 128 gate
+      // rows, issued by a second warp alongside MMA_b.  Both operands
       // MN-major: LBO = stride of 8-sample groups along K (the buffer's
       // row-group stride), SBO = 128 B between 8-column groups along M / N.
       // One K = 16 step covers two sample groups.
+      const uint32_t xs = tc::smem_addr(sX) + xb * (128 * KA * 2);
 #pragma unroll
       for (int half = 0; half < S::GW / 128; ++half) {
 #pragma unroll
-        for (int k = 0; k < 128 / 16; ++k) {
-          if (k >= kw) break;
+        for (int k = 0; k < ROWS / 16; ++k) {
           const uint64_t da = tc::make_desc(tc::smem_addr(sG) + half * 16 * 128 + k * 2 * (S::GW / 8) * 128,
                                             (S::GW / 8) * 128, 128);
-          const uint64_t db = tc::make_desc(tc::smem_addr(sX) + k * 2 * (KA / 8) * 128, (KA / 8) * 128, 128);
+          const uint64_t db = tc::make_desc(xs + k * 2 * (KA / 8) * 128, (KA / 8) * 128, 128);
           tc::mma_bf16(tbase + (half ? S::cW1 : S::cW0), da, db, idesc_w, (n < N - 1) || k > 0);
         }
       }
       tc::mma_commit(&mbar[1]);
     }
-    if (wact) {
-      if (!tc::mbar_wait(&mbar[1], ph_b, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    // ---- carry += acc_b ----
+    if constexpr (ROWS == 128) {
+      wait(0);
       tc::fence_after_sync();
-      // all of this thread's acc_b columns in one round trip
-      float v[DU / 8][8];
 #pragma unroll
-      for (int c = 0; c < DU / 8; ++c) tmem_ld8(trow + S::cB + u0 + 8 * c, v[c]);
-      tc::tmem_wait_ld();
+      for (int c = 0; c < DU / 8; ++c) {
+        float v0[8], v1[8], v2[8];
+        tmem_ld8(tq + S::cB + u0 + 8 * c, v0);
+        tmem_ld8(tq + S::cB + D + u0 + 8 * c, v1);
+        tmem_ld8(tq + S::cB + 2 * D + u0 + 8 * c, v2);
+        tc::tmem_wait_ld();
 #pragma unroll
-      for (int c = 0; c < DU / 8; ++c)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          asm volatile("" : "+f"(v[c][q]));
-          carry[8 * c + q] += v[c][q];
+        for (int i = 0; i < 8; ++i) {
+          asm volatile("" : "+f"(v0[i]), "+f"(v1[i]), "+f"(v2[i]));
+          carry[8 * c + i] += (v0[i] + v1[i]) + v2[i];
         }
+      }
+    } else {
+      // the quarters holding the samples' lanes pass acc_b on through shared memory
+      if (q < RQ) {
+        wait(0);
+        tc::fence_after_sync();
+        constexpr int CW = D / SPLIT;      // columns per warp of the quarter
+#pragma unroll
+        for (int c = 0; c < CW / 8; ++c) {
+          float v0[8], v1[8], v2[8];
+          tmem_ld8(tq + S::cB + p * CW + 8 * c, v0);
+          tmem_ld8(tq + S::cB + D + p * CW + 8 * c, v1);
+          tmem_ld8(tq + S::cB + 2 * D + p * CW + 8 * c, v2);
+          tc::tmem_wait_ld();
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            asm volatile("" : "+f"(v0[i]), "+f"(v1[i]), "+f"(v2[i]));
+            v[i] = (v0[i] + v1[i]) + v2[i];
+          }
+          float4* dst = reinterpret_cast<float4*>(sC + s * CS + p * CW + 8 * c);
+          dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+          dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+#pragma unroll
+      for (int c = 0; c < DU / 4; ++c) {
+        const float4 x = reinterpret_cast<const float4*>(sC + s * CS + u0)[c];
+        carry[4 * c] += x.x;
+        carry[4 * c + 1] += x.y;
+        carry[4 * c + 2] += x.z;
+        carry[4 * c + 3] += x.w;
+      }
     }
-    ph_b ^= 1;
-    s_n = s_p;
-    s_p = s_pp;
-    cur = nxt;
   }
-  // after a timeout, let copies still in flight land before the CTA leaves
-  if (timed_out) {
-    for (int k = 0; k < 2; ++k)
-      if (inflight[k]) tc::mbar_wait(&mbar[2 + k], ph_h[k], kWaitLimit);
-  }
-  // ---- this CTA's weight, bias and one-hot-column gradients from acc_w (part-0 warps) ----
+  // the last MMA_w, before acc_w is read; copies still in flight (after a
+  // timeout) land before the CTA leaves
+  if (threadIdx.x == 0 && !timed_out) wait(1);
+  cp_async_wait_all();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  // ---- this CTA's weight, bias and one-hot-column gradients from acc_w (warps 0-3) ----
   // X columns: k < D: h; D: bias; D + 2, D + 3: one-hot weights (D + 1, D + 4 .. are duplicates / zero)
   const int Wg = 0, Wr = D * (D + 2), Wh = 2 * D * (D + 2), Win = Wh + D * D;
   const int bg = Win + 2 * D, br = bg + D, bh = br + D, bin = bh + D;
   float* part_g = a.partial + (size_t)blockIdx.x * a.P;
-  if (part == 0) {
+  if (p == 0) {
+    const int m = 32 * q + lane;           // gate row (TMEM lane) of this thread
 #pragma unroll 1
     for (int half = 0; half < S::GW / 128; ++half) {
       const int gu = half * 128 + m;
@@ -927,23 +1145,23 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
 #pragma unroll 1
       for (int c = 0; c < KA; c += 16) {
         float v[16];
-        tc::tmem_ld16(trow + (half ? S::cW1 : S::cW0) + c, v);
+        tc::tmem_ld16(tq + (half ? S::cW1 : S::cW0) + c, v);
         tc::tmem_wait_ld();
         if (gu >= 4 * D) continue;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int k = c + q;
+        for (int i = 0; i < 16; ++i) {
+          const int k = c + i;
           if (k < D) {
-            if (g == 0) part_g[Wg + u * (D + 2) + k] = v[q];
-            else if (g == 1) part_g[Wr + u * (D + 2) + k] = v[q];
-            else if (g == 2) part_g[Wh + u * D + k] = v[q];
+            if (g == 0) part_g[Wg + u * (D + 2) + k] = v[i];
+            else if (g == 1) part_g[Wr + u * (D + 2) + k] = v[i];
+            else if (g == 2) part_g[Wh + u * D + k] = v[i];
           } else if (k == D) {
-            part_g[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[q];
+            part_g[(g == 0 ? bg : g == 1 ? br : g == 2 ? bh : bin) + u] = v[i];
           } else if (k == D + 2 || k == D + 3) {
-            const int s = k - D - 2;
-            if (g == 0) part_g[Wg + u * (D + 2) + D + s] = v[q];
-            else if (g == 1) part_g[Wr + u * (D + 2) + D + s] = v[q];
-            else if (g == 3) part_g[Win + u * 2 + s] = v[q];
+            const int si = k - D - 2;
+            if (g == 0) part_g[Wg + u * (D + 2) + D + si] = v[i];
+            else if (g == 1) part_g[Wr + u * (D + 2) + D + si] = v[i];
+            else if (g == 3) part_g[Win + u * 2 + si] = v[i];
           }
         }
       }
@@ -952,7 +1170,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kCols);
 }
 
 // Readout gradients: dU[0][u] = sum_{b,n} dz h_n[u], dU[1] = -dU[0], dc0 = sum dz,
@@ -1162,18 +1380,75 @@ void tc1d_set_variant(int v) {
 
 constexpr int kReadoutGradBlocks = 304;
 // rows of per-CTA partial gradients: the reverse sweep's CTAs (at most one per
-// 64 samples) and then the readout-gradient blocks
+// 32 samples) and then the readout-gradient blocks
 int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 31) / 32) + kReadoutGradBlocks; }
+size_t tc1d_tape_bytes(int64_t B, int N, int D, int which) {
+  const size_t BN = (size_t)B * (size_t)N;
+  return which == 0 ? BN * sizeof(float) : which == 1 ? BN * D * 2 : BN * 5 * D * 2;
+}
 
-template <int D, int SPLIT>
-cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt,
-                             cudaStream_t st) {
-  using S = BSmem<D, SPLIT>;
-  auto k = tc1d_bptt_kernel<D, SPLIT>;
+template <int D, int SPLIT, int ROWS>
+cudaError_t launch_tc_bptt_v(const TcBpttArgs& a, const float* img, const uint8_t* wt, cudaStream_t st) {
+  using S = BSmem<D, SPLIT, ROWS>;
+  auto k = tc1d_bptt_kernel<D, SPLIT, ROWS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  const int grid = (int)((a.B + a.rows - 1) / a.rows);
-  k<<<grid, 128 * SPLIT, S::kBytes, st>>>(img, w3, wt, a);
+  const int grid = (int)((a.B + ROWS - 1) / ROWS);
+  k<<<grid, 128 * SPLIT, S::kBytes, st>>>(img, wt, a);
+  return cudaGetLastError();
+}
+
+// Reverse-sweep variants (rows per tile, threads per row) with at least 8
+// units per thread; the autotuner picks one.
+template <int D>
+constexpr int bptt_variants() { return D == 64 ? 8 : D == 32 ? 5 : 3; }
+
+template <int D>
+cudaError_t launch_tc_bptt_n(const TcBpttArgs& a, const float* img, const uint8_t* wt, int v, cudaStream_t st) {
+  if constexpr (D == 64) {
+    switch (v) {
+      case 0: return launch_tc_bptt_v<64, 1, 128>(a, img, wt, st);
+      case 1: return launch_tc_bptt_v<64, 2, 128>(a, img, wt, st);
+      case 2: return launch_tc_bptt_v<64, 4, 128>(a, img, wt, st);
+      case 3: return launch_tc_bptt_v<64, 1, 64>(a, img, wt, st);
+      case 4: return launch_tc_bptt_v<64, 2, 64>(a, img, wt, st);
+      case 5: return launch_tc_bptt_v<64, 4, 64>(a, img, wt, st);
+      case 6: return launch_tc_bptt_v<64, 1, 32>(a, img, wt, st);
+      default: return launch_tc_bptt_v<64, 2, 32>(a, img, wt, st);
+    }
+  } else if constexpr (D == 32) {
+    switch (v) {
+      case 0: return launch_tc_bptt_v<32, 1, 128>(a, img, wt, st);
+      case 1: return launch_tc_bptt_v<32, 2, 128>(a, img, wt, st);
+      case 2: return launch_tc_bptt_v<32, 1, 64>(a, img, wt, st);
+      case 3: return launch_tc_bptt_v<32, 2, 64>(a, img, wt, st);
+      default: return launch_tc_bptt_v<32, 1, 32>(a, img, wt, st);
+    }
+  } else {
+    switch (v) {
+      case 0: return launch_tc_bptt_v<D, 1, 128>(a, img, wt, st);
+      case 1: return launch_tc_bptt_v<D, 2, 128>(a, img, wt, st);
+      default: return launch_tc_bptt_v<D, 1, 64>(a, img, wt, st);
+    }
+  }
+}
+
+// The tape: one CTA per SM, each on runs of consecutive sites of one sample
+// tile (a run reads each cached state row once, plus one row before it).
+template <int D>
+cudaError_t launch_tape(const TcBpttArgs& a, const float* img, const uint8_t* w3, cudaStream_t st) {
+  using S = TpS<D>;
+  auto k = tc1d_tape_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  const int64_t tiles = (a.B + 127) / 128;
+  const int sms = sm_count_tc();
+  const int runs_per_tile = tiles >= sms ? 1 : (int)(sms / tiles);
+  const int sites_per_run = (a.N + runs_per_tile - 1) / runs_per_tile;
+  int64_t grid = tiles * runs_per_tile;
+  if (grid > sms) grid = sms;
+  if (grid < 1) grid = 1;
+  k<<<(unsigned)grid, S::NT, S::kBytes, st>>>(img, w3, a, sites_per_run, runs_per_tile);
   return cudaGetLastError();
 }
 
@@ -1185,20 +1460,15 @@ cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t*
   // B/32 rows) and the reduction sums all rows, so the sweep's rows are
   // cleared before every run: an autotuning trial with fewer rows per tile
   // leaves rows that a final run with more rows per tile would not overwrite.
-  const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
-  auto run = [&](int v) {
-    TcBpttArgs b = a;
-    b.rows = 128 >> (v / ns);
-    const int sv = v % ns;
-    if (sv == 2 && D >= 64) return launch_tc_bptt_v<D, (D >= 64 ? 4 : 1)>(b, img, w3, wt, st);
-    if (sv == 1 && D >= 32) return launch_tc_bptt_v<D, (D >= 32 ? 2 : 1)>(b, img, w3, wt, st);
-    return launch_tc_bptt_v<D, 1>(b, img, w3, wt, st);
-  };
+  // The tape launch comes first; the sweep only reads it.
+  cudaError_t e = launch_tape<D>(a, img, w3, st);
+  if (e != cudaSuccess) return e;
+  auto run = [&](int v) { return launch_tc_bptt_n<D>(a, img, wt, v, st); };
   const int rows_max = (int)((a.B + 31) / 32);
   auto clear = [&]() {
     return cudaMemsetAsync(a.partial, 0, (size_t)rows_max * a.P * sizeof(float), st);
   };
-  cudaError_t e = tuned_launch(3, D, a.N, a.B, 3 * ns, run, clear, st);
+  e = tuned_launch(3, D, a.N, a.B, bptt_variants<D>(), run, clear, st);
   if (e != cudaSuccess) return e;
   tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
                                                                    rows_max);
