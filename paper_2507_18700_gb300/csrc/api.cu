@@ -117,7 +117,6 @@ Layout layout(const Dims& d, int64_t B, int op) {
       if (use_tc(d)) {
         L.a = take((size_t)tc1d_bptt_partial_rows(B) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                 // weights
-        L.c = take(BN * sizeof(float));                                         // readout gradients dz
         L.e = take(tc1d_tape_bytes(B, d.N, d.d, 0));                            // tape: e
         L.f = take(tc1d_tape_bytes(B, d.N, d.d, 1));                            // tape: BF16 states
         L.g = take(tc1d_tape_bytes(B, d.N, d.d, 2));                            // tape: backward factors
@@ -464,7 +463,6 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.sigma = sigma;
     t.hcache = hcache;
     t.weights = weights;
-    t.dz = at<float>(ws, L.c);
     t.partial = partial;
     t.tape_e = at<float>(ws, L.e);
     t.tape_x = at<uint8_t>(ws, L.f);

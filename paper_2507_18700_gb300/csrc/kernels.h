@@ -178,7 +178,6 @@ struct TcBpttArgs {
   const uint8_t* sigma;
   const float* hcache;
   const float* weights;
-  float* dz;                 // [B, N] readout gradient per (sample, site)
   float* partial;            // [tc1d_bptt_partial_rows(B), P], zeroed
   float* tape_e;             // [B, N] onehot_0(s_n) - p_0(h_n)
   uint8_t* tape_x;           // [B, N, d] bf16 h_{n-1}

@@ -669,7 +669,7 @@ struct TpS {
 template <int D>
 __global__ void __launch_bounds__(TpS<D>::NT, 1)
 tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfimg, TcBpttArgs a, int sites_per_run,
-                 int runs_per_tile) {
+                 int runs_per_tile, int part_row0) {
   using S = TpS<D>;
   constexpr int SPLIT = S::SPLIT, NT = S::NT, KA = S::KA, HS = S::HS, DU = D / SPLIT;
   static_assert(DU == 16, "16 units per thread");
@@ -710,6 +710,11 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
     if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
     phases ^= 1u << k;
   };
+  // readout gradients of this thread's rows: dU_0[u] += dz_n h_n[u], dc_0 += dz_n
+  float gU[DU];
+#pragma unroll
+  for (int u = 0; u < DU; ++u) gU[u] = 0.0f;
+  float gc = 0.0f;
   // state rows h_n of the tile's 128 samples into buffer k, 16 bytes per copy,
   // consecutive threads on consecutive pieces of a row (zeros for n outside
   // [0, N) or samples past the batch)
@@ -736,6 +741,7 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
     wait(1);
     const int64_t b = bt * 128 + m;
     const bool valid = b < B;
+    const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
     for (int n = n0; n < n1; ++n) {
       const int kp = (n - n0) % 3, kn = (n - n0 + 1) % 3;
       if (n + 1 < n1) load_rows(bt, n + 1, (n - n0 + 2) % 3);
@@ -796,9 +802,20 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
           for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
         z = pz[0];
       }
-      if (valid && part == 0) {
-        const int s_n = a.sigma[b * N + n] ? 1 : 0;
-        a.tape_e[(int64_t)n * B + b] = (s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc);
+      {
+        const int s_n = valid ? (a.sigma[b * N + n] ? 1 : 0) : 0;
+        const float e = (s_n == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc);
+        if (valid && part == 0) a.tape_e[(int64_t)n * B + b] = e;
+        const float dz = coef * e;
+#pragma unroll
+        for (int q4 = 0; q4 < DU / 4; ++q4) {
+          const float4 h4 = reinterpret_cast<const float4*>(hn)[q4];
+          gU[4 * q4] = fmaf(dz, h4.x, gU[4 * q4]);
+          gU[4 * q4 + 1] = fmaf(dz, h4.y, gU[4 * q4 + 1]);
+          gU[4 * q4 + 2] = fmaf(dz, h4.z, gU[4 * q4 + 2]);
+          gU[4 * q4 + 3] = fmaf(dz, h4.w, gU[4 * q4 + 3]);
+        }
+        gc += dz;
       }
       wait(0);
       tc::fence_after_sync();
@@ -854,6 +871,27 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kCols);
+  // ---- this CTA's readout gradients: rows summed in a fixed order into one
+  // partial row (U_1 and c_1 get the negatives: the softmax of two logits) ----
+  float* red = sH;                         // [128 x HS] (the state buffers are free)
+#pragma unroll
+  for (int q4 = 0; q4 < DU / 4; ++q4)
+    reinterpret_cast<float4*>(red + m * HS + u0)[q4] = make_float4(gU[4 * q4], gU[4 * q4 + 1], gU[4 * q4 + 2], gU[4 * q4 + 3]);
+  if (part == 0) red[m * HS + D] = gc;
+  __syncthreads();
+  float* part_g = a.partial + (size_t)(part_row0 + blockIdx.x) * a.P;
+  const int Uoff = 3 * D * D + 10 * D, coff = Uoff + 2 * D;   // U and c of the flat 1D layout
+  for (int u = threadIdx.x; u <= D; u += NT) {
+    float acc = 0.0f;
+    for (int r = 0; r < 128; ++r) acc += red[r * HS + u];
+    if (u < D) {
+      part_g[Uoff + u] = acc;
+      part_g[Uoff + D + u] = -acc;
+    } else {
+      part_g[coff] = acc;
+      part_g[coff + 1] = -acc;
+    }
+  }
 }
 
 template <int D, int SPLIT, int ROWS>
@@ -995,7 +1033,6 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
     const float e_next = (valid && n > 0) ? a.tape_e[(int64_t)(n - 1) * B + b] : 0.0f;
     wait(2 + kb);
     const float dz0 = coef * e_cur;
-    if (valid && sl == 0) a.dz[b * N + n] = dz0;
     // ---- G = dh k_n, carry = dh k4, 8 units at a time ----
     const uint8_t* kr = sK + kb * S::KB + s * 16;
 #pragma unroll
@@ -1173,59 +1210,6 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kCols);
 }
 
-// Readout gradients: dU[0][u] = sum_{b,n} dz h_n[u], dU[1] = -dU[0], dc0 = sum dz,
-// dc1 = -dc0; one partial row per block.  A warp reads D/4 float4 of a cached
-// state per row (coalesced 256-byte rows) and strides over rows.
-template <int D>
-__global__ void __launch_bounds__(256) tc1d_readout_grad_kernel(const float* __restrict__ hcache,
-                                                               const float* __restrict__ dz, int64_t rows,
-                                                               float* __restrict__ partial, int P, int part_row0) {
-  constexpr int L4 = D / 4;               // float4 per state
-  constexpr int RPW = 32 / L4 > 0 ? 32 / L4 : 1;   // rows per warp pass
-  __shared__ float red[8][D + 1];
-  const int Uoff = 3 * D * D + 10 * D, coff = Uoff + 2 * D;   // U and c of the flat 1D layout
-  float* part = partial + (size_t)(part_row0 + blockIdx.x) * P;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int q = lane % L4, sub = lane / L4;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  float accc = 0.0f;
-  const int64_t stride = (int64_t)gridDim.x * 8 * RPW;
-#pragma unroll 4
-  for (int64_t r = ((int64_t)blockIdx.x * 8 + warp) * RPW + sub; r < rows; r += stride) {
-    if (sub >= RPW) break;
-    const float z = dz[r];
-    const float4 h = reinterpret_cast<const float4*>(hcache + r * D)[q];
-    acc.x = fmaf(z, h.x, acc.x); acc.y = fmaf(z, h.y, acc.y);
-    acc.z = fmaf(z, h.z, acc.z); acc.w = fmaf(z, h.w, acc.w);
-    if (q == 0) accc += z;
-  }
-  // sum the RPW sub-rows of the warp, then the 8 warps
-  for (int off = L4; off < 32; off <<= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
-    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, off);
-  }
-  for (int off = 16; off > 0; off >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, off);   // only q == 0 lanes hold sums
-  if (sub == 0) {
-    red[warp][4 * q] = acc.x; red[warp][4 * q + 1] = acc.y;
-    red[warp][4 * q + 2] = acc.z; red[warp][4 * q + 3] = acc.w;
-    if (q == 0) red[warp][D] = accc;
-  }
-  __syncthreads();
-  for (int u = threadIdx.x; u <= D; u += 256) {
-    float s = 0.0f;
-    for (int w = 0; w < 8; ++w) s += red[w][u];
-    if (u < D) {
-      part[Uoff + u] = s;
-      part[Uoff + D + u] = -s;
-    } else {
-      part[coff] = s;
-      part[coff + 1] = -s;
-    }
-  }
-}
-
 // Gate weights as the B operand of MMA_b: [D rows (k) x 3D (gate, unit)].
 __global__ void pack1d_tc_t_kernel(const float* __restrict__ p, uint8_t* __restrict__ wt, int D) {
   const int total = 3 * D * D;
@@ -1378,10 +1362,11 @@ void tc1d_set_variant(int v) {
   g_force = v < 0 ? -1 : v;
 }
 
-constexpr int kReadoutGradBlocks = 304;
 // rows of per-CTA partial gradients: the reverse sweep's CTAs (at most one per
-// 32 samples) and then the readout-gradient blocks
-int tc1d_bptt_partial_rows(int64_t B) { return (int)((B + 31) / 32) + kReadoutGradBlocks; }
+// 32 samples) and then the tape kernel's CTAs (readout gradients)
+constexpr int kTapeRows = 304;
+int bptt_sweep_rows(int64_t B) { return (int)((B + 31) / 32); }
+int tc1d_bptt_partial_rows(int64_t B) { return bptt_sweep_rows(B) + kTapeRows; }
 size_t tc1d_tape_bytes(int64_t B, int N, int D, int which) {
   const size_t BN = (size_t)B * (size_t)N;
   return which == 0 ? BN * sizeof(float) : which == 1 ? BN * D * 2 : BN * 5 * D * 2;
@@ -1447,8 +1432,9 @@ cudaError_t launch_tape(const TcBpttArgs& a, const float* img, const uint8_t* w3
   const int sites_per_run = (a.N + runs_per_tile - 1) / runs_per_tile;
   int64_t grid = tiles * runs_per_tile;
   if (grid > sms) grid = sms;
+  if (grid > kTapeRows) grid = kTapeRows;
   if (grid < 1) grid = 1;
-  k<<<(unsigned)grid, S::NT, S::kBytes, st>>>(img, w3, a, sites_per_run, runs_per_tile);
+  k<<<(unsigned)grid, S::NT, S::kBytes, st>>>(img, w3, a, sites_per_run, runs_per_tile, bptt_sweep_rows(a.B));
   return cudaGetLastError();
 }
 
@@ -1464,15 +1450,11 @@ cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t*
   cudaError_t e = launch_tape<D>(a, img, w3, st);
   if (e != cudaSuccess) return e;
   auto run = [&](int v) { return launch_tc_bptt_n<D>(a, img, wt, v, st); };
-  const int rows_max = (int)((a.B + 31) / 32);
+  const int rows_max = bptt_sweep_rows(a.B);
   auto clear = [&]() {
     return cudaMemsetAsync(a.partial, 0, (size_t)rows_max * a.P * sizeof(float), st);
   };
-  e = tuned_launch(3, D, a.N, a.B, bptt_variants<D>(), run, clear, st);
-  if (e != cudaSuccess) return e;
-  tc1d_readout_grad_kernel<D><<<kReadoutGradBlocks, 256, 0, st>>>(a.hcache, a.dz, a.B * (int64_t)a.N, a.partial, a.P,
-                                                                   rows_max);
-  return cudaGetLastError();
+  return tuned_launch(3, D, a.N, a.B, bptt_variants<D>(), run, clear, st);
 }
 
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st) {
