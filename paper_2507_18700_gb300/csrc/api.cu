@@ -451,11 +451,9 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
   if (use_tc(d)) {
     uint8_t* w3 = at<uint8_t>(ws, L.w);
     uint8_t* wt = at<uint8_t>(ws, L.w2);
-    const int rows = tc1d_bptt_partial_rows(B);
     if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
     if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
     TcBpttArgs t{};
     t.B = B;
     t.N = d.N;
@@ -469,7 +467,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.tape_k = at<uint8_t>(ws, L.g);
     t.hdr = static_cast<WsHeader*>(ws);
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
+    return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
   }
   if (use_tc2d(d)) {
     uint8_t* wimg = at<uint8_t>(ws, L.w);

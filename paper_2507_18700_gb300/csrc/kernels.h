@@ -193,6 +193,8 @@ size_t tc1d_tape_bytes(int64_t B, int N, int D, int which);   // which: 0 e, 1 x
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st);
 cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, const uint8_t* wt, int D,
                       cudaStream_t st);
+// grad = the FP64 sum of the partial rows tc1d_bptt wrote
+cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, float* grad, cudaStream_t st);
 size_t tc1d_wimg_bytes(int D);
 cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
 // mode 0: sampling, 1: teacher forcing, 2: TFIM chains
@@ -227,6 +229,9 @@ cudaError_t batched_step(const BatchRep* reps, int R, uint64_t step, const uint6
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
 cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);
 cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st);
+// grad[0 .. ncols) = FP64 sum over `rows` rows (stride ld floats) of partial
+cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, float* grad,
+                                 cudaStream_t st);
 
 // growth (grow.cu)
 cudaError_t grow_params(int cell, int d, int m, int D, int Mm, const float* p_small, float* p_big,

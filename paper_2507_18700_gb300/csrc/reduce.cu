@@ -45,7 +45,7 @@ __global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double*
 // A block sums 32 columns: 8 row groups (r = g mod 8) per column, each with
 // 4 independent FP64 accumulators, then the 8 group sums in a fixed tree.
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
-                                                              float* __restrict__ grad) {
+                                                              int64_t ld, float* __restrict__ grad) {
   __shared__ double red[8][33];
   const int col = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + col;
@@ -53,12 +53,12 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __res
   if (p < P) {
     int r = g;
     for (; r + 24 < rows; r += 32) {
-      a0 += (double)partial[(size_t)r * P + p];
-      a1 += (double)partial[(size_t)(r + 8) * P + p];
-      a2 += (double)partial[(size_t)(r + 16) * P + p];
-      a3 += (double)partial[(size_t)(r + 24) * P + p];
+      a0 += (double)partial[(size_t)r * ld + p];
+      a1 += (double)partial[(size_t)(r + 8) * ld + p];
+      a2 += (double)partial[(size_t)(r + 16) * ld + p];
+      a3 += (double)partial[(size_t)(r + 24) * ld + p];
     }
-    for (; r < rows; r += 8) a0 += (double)partial[(size_t)r * P + p];
+    for (; r < rows; r += 8) a0 += (double)partial[(size_t)r * ld + p];
   }
   red[g][col] = (a0 + a1) + (a2 + a3);
   __syncthreads();
@@ -82,11 +82,16 @@ cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float
   return cudaGetLastError();
 }
 
-cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
-  const int blocks = (P + 31) / 32;
+cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, float* grad,
+                                 cudaStream_t st) {
+  const int blocks = (ncols + 31) / 32;
   if (blocks < 1) return cudaSuccess;
-  reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, rows, P, grad);
+  reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, rows, ncols, ld, grad);
   return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
+  return reduce_partials_cols(partial, rows, P, P, grad, st);
 }
 
 }  // namespace nqs

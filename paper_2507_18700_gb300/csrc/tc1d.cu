@@ -1420,21 +1420,30 @@ cudaError_t launch_tc_bptt_n(const TcBpttArgs& a, const float* img, const uint8_
 
 // The tape: one CTA per SM, each on runs of consecutive sites of one sample
 // tile (a run reads each cached state row once, plus one row before it).
+struct TapeGrid {
+  int grid, sites_per_run, runs_per_tile;
+};
+TapeGrid tape_grid(int64_t B, int N) {
+  const int64_t tiles = (B + 127) / 128;
+  const int sms = sm_count_tc();
+  TapeGrid t;
+  t.runs_per_tile = tiles >= sms ? 1 : (int)(sms / tiles);
+  t.sites_per_run = (N + t.runs_per_tile - 1) / t.runs_per_tile;
+  int64_t grid = tiles * t.runs_per_tile;
+  if (grid > sms) grid = sms;
+  if (grid > kTapeRows) grid = kTapeRows;
+  t.grid = grid < 1 ? 1 : (int)grid;
+  return t;
+}
+
 template <int D>
 cudaError_t launch_tape(const TcBpttArgs& a, const float* img, const uint8_t* w3, cudaStream_t st) {
   using S = TpS<D>;
   auto k = tc1d_tape_kernel<D>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  const int64_t tiles = (a.B + 127) / 128;
-  const int sms = sm_count_tc();
-  const int runs_per_tile = tiles >= sms ? 1 : (int)(sms / tiles);
-  const int sites_per_run = (a.N + runs_per_tile - 1) / runs_per_tile;
-  int64_t grid = tiles * runs_per_tile;
-  if (grid > sms) grid = sms;
-  if (grid > kTapeRows) grid = kTapeRows;
-  if (grid < 1) grid = 1;
-  k<<<(unsigned)grid, S::NT, S::kBytes, st>>>(img, w3, a, sites_per_run, runs_per_tile, bptt_sweep_rows(a.B));
+  const TapeGrid t = tape_grid(a.B, a.N);
+  k<<<(unsigned)t.grid, S::NT, S::kBytes, st>>>(img, w3, a, t.sites_per_run, t.runs_per_tile, bptt_sweep_rows(a.B));
   return cudaGetLastError();
 }
 
@@ -1455,6 +1464,19 @@ cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t*
     return cudaMemsetAsync(a.partial, 0, (size_t)rows_max * a.P * sizeof(float), st);
   };
   return tuned_launch(3, D, a.N, a.B, bptt_variants<D>(), run, clear, st);
+}
+
+// Partial rows: the sweep's rows (cleared before the sweep, so rows past the
+// chosen variant's CTAs are zero) carry the weight, bias and one-hot-column
+// gradients, columns [0, U); the tape CTAs' rows carry the readout gradients,
+// columns [U, P).  Each block of columns is summed over its own rows.
+cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, float* grad, cudaStream_t st) {
+  const int rows = bptt_sweep_rows(a.B);
+  const int Uoff = 3 * D * D + 10 * D;
+  cudaError_t e = reduce_partials_cols(a.partial, rows, Uoff, a.P, grad, st);
+  if (e != cudaSuccess) return e;
+  return reduce_partials_cols(a.partial + (size_t)rows * a.P + Uoff, tape_grid(a.B, a.N).grid, a.P - Uoff, a.P,
+                              grad + Uoff, st);
 }
 
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st) {
