@@ -61,7 +61,7 @@ int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
 struct Layout {
-  size_t img, w, w2, a, b, c, e, f, g, h, total;
+  size_t img, w, w2, a, b, c, e, f, g, h, i, j, total;
 };
 
 Layout layout(const Dims& d, int64_t B, int op) {
@@ -112,6 +112,8 @@ Layout layout(const Dims& d, int64_t B, int op) {
         L.f = take(tc2d_grad_image_bytes(B, d.N, d.d, 1));                         // G2 images
         L.g = take(tc2d_grad_image_bytes(B, d.N, d.d, 2));                         // GLU outputs
         L.h = take(tc2d_grad_image_bytes(B, d.N, d.d, 3));                         // readout gradients
+        L.i = take(tc2d_grad_image_bytes(B, d.N, d.d, 4));                         // tape: dh_glu
+        L.j = take(tc2d_grad_image_bytes(B, d.N, d.d, 5));                         // tape: factors
         break;
       }
       if (use_tc(d)) {
@@ -489,11 +491,10 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     g.g2img = at<uint8_t>(ws, L.f);
     g.yimg = at<float>(ws, L.g);
     g.dzimg = at<float>(ws, L.h);
+    g.tape_h = at<float>(ws, L.i);
+    g.tape_k = at<uint8_t>(ws, L.j);
     g.partial = partial;
     g.hdr = static_cast<WsHeader*>(ws);
-    // the images' padding columns (gate rows beyond 3 d / 2 d) must read as zero
-    if (cudaMemsetAsync(g.g1img, 0, tc2d_grad_image_bytes(B, d.N, d.d, 0), st) != cudaSuccess) return NQS_ECUDA;
-    if (cudaMemsetAsync(g.g2img, 0, tc2d_grad_image_bytes(B, d.N, d.d, 1), st) != cudaSuccess) return NQS_ECUDA;
     if (tc2d_grad(g, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
   }

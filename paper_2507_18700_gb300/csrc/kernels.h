@@ -129,10 +129,12 @@ struct Tc2Grad {
   const float* hcache;
   const float* weights;
   float* ccarry;             // [B, Lx, d] vertical carries
-  uint8_t* g1img;            // tc2d_grad_image_bytes(.., 0), zeroed
-  uint8_t* g2img;            // tc2d_grad_image_bytes(.., 1), zeroed
+  uint8_t* g1img;            // tc2d_grad_image_bytes(.., 0)
+  uint8_t* g2img;            // tc2d_grad_image_bytes(.., 1)
   float* yimg;               // tc2d_grad_image_bytes(.., 2)
   float* dzimg;              // tc2d_grad_image_bytes(.., 3)
+  float* tape_h;             // tc2d_grad_image_bytes(.., 4)
+  uint8_t* tape_k;           // tc2d_grad_image_bytes(.., 5)
   float* partial;            // [tc2d_grad_partial_rows(B, N), P], zeroed
   WsHeader* hdr;
 };

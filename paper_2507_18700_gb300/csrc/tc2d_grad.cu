@@ -2,27 +2,33 @@
 // (App. A): d/dtheta sum_b w_b log psi_b over the zig-zag order (Sec. II),
 // with the zero-magnetisation mask, for d_h in {32, 64} and N <= 128.
 //
-// Phase 1, tc2d_sweep_kernel: one CTA = one tile of 128 samples (= TMEM
-// lanes), one thread per sample; every row is at the same position, sites
-// t = N-1 .. 0.  Per cell, from the cached states:
+// Phase 1a, tc2d_tape_kernel, parallel over (tile of 128 samples, position
+// t): from the cached states, everything that does not depend on the
+// incoming gradient --
 //   MMA1: [hi(h') | extras | lo(h')] x W1^T   (the forward's gate pre-activations)
 //   MMA2: [hi(h)  | extras | lo(h)]  x W2^T   (the forward's GLU pre-activations)
-//   epilogue: y, the logit difference d, dz = c_b (onehot(s) - p0) (0 at a
-//             forced site of the mask), G2 = [dy W_1-path | dy W_2-path]
-//   MMA_g: dh = G2 W2           (W2 read as an MN-major operand)
-//   epilogue: back through h = u h~ + (1 - u) U_mix h' into G1 = [da_W | da_g | d(U_mix h')]
+//   GLU:  y, the logit difference d, dz = c_b (onehot(s) - p0) (0 at a
+//         forced site of the mask), G2 = [dy W_1-path | dy W_2-path]
+//   MMA_g: dh_glu = G2 W2                     (W2 read as an MN-major operand)
+// and the three factors with which the cell backward through
+// h = u h~ + (1 - u) U_mix h' is linear in dh: G1 = dh [kW | kg | km].
+// dh_glu (FP32) and the factors (FP16) go to a sample-minor tape; G2, dz and
+// y go to the images of phases 2 and 3.
+// Phase 1b, tc2d_bsweep_kernel, sequential over t = N-1 .. 0 for a tile of
+// 128 samples: dh = dh_glu + the carries of the horizontal and vertical
+// successors, G1 = dh [kW | kg | km] (BF16, also written as an image),
 //   MMA_b: dh' = G1 W1          (W1 read as an MN-major operand)
 // dh' splits into the horizontal predecessor's carry (registers) and the
 // vertical predecessor's (a per-sample column carry buffer in global memory).
 // The forward images hold W_g and W_2 halved (their sigmoids are one tanh);
-// G1 and G2 carry those blocks doubled, so both products are exact.  G1, G2
-// go to global memory as ready-made 128-row MMA operand images, and dz and y
-// as sample-minor arrays.
+// G1 and G2 carry those blocks doubled, so both products are exact.
 // Phase 2, tc2d_wgrad_kernel: split-K over the (tile, site) images, a CTA
 // accumulates dW1 += G1^T X1 and dW2 += G2^T X2 in TMEM (X1 = [h' | 1 |
 // one-hots], X2 = [h | 1], built from the cache; both operands MN-major), so
 // the ones and one-hot columns give the bias and one-hot-weight gradients.
 // Phase 3, tc2d_readout_grad_kernel: dU_out and dc from dz and y.
+#include <cuda_fp16.h>
+
 #include "tc2d_common.cuh"
 
 namespace nqs {
@@ -57,11 +63,13 @@ struct Sweep2Args {
   const uint8_t* sigma;
   const float* hcache;
   const float* weights;
-  float* ccarry;             // [B, Lx, d] vertical carries (zeroed)
-  uint8_t* g1img;            // [tiles, N] images of 128 x GW1 bf16 (padding columns zeroed)
-  uint8_t* g2img;            // [tiles, N] images of 128 x GW2 bf16 (padding columns zeroed)
+  float* ccarry;             // [B, Lx, d] vertical carries
+  uint8_t* g1img;            // [tiles, N] images of 128 x GW1 bf16 (padding columns written as zero)
+  uint8_t* g2img;            // [tiles, N] images of 128 x GW2 bf16 (padding columns written as zero)
   float* yimg;               // [tiles, N, d, 128]
   float* dzimg;              // [tiles, N, 128]
+  float* tape_h;             // [N][d / 4][B][4] f32: dlog psi / dh through the GLU
+  uint8_t* tape_k;           // [N][3][d / 8][B][8] f16: cell-backward factors
   WsHeader* hdr;
 };
 
@@ -84,10 +92,59 @@ __device__ __forceinline__ void st_bf16_8(uint8_t* dst, const float* v) {
                                               pack_bf16(v[6], v[7]));
 }
 
+__device__ __forceinline__ uint4 pack_h8(const float* v) {
+  __half2 p0 = __floats2half2_rn(v[0], v[1]);
+  __half2 p1 = __floats2half2_rn(v[2], v[3]);
+  __half2 p2 = __floats2half2_rn(v[4], v[5]);
+  __half2 p3 = __floats2half2_rn(v[6], v[7]);
+  return make_uint4(*reinterpret_cast<uint32_t*>(&p0), *reinterpret_cast<uint32_t*>(&p1),
+                    *reinterpret_cast<uint32_t*>(&p2), *reinterpret_cast<uint32_t*>(&p3));
+}
+
+__device__ __forceinline__ void unpack_h8(uint4 q, float* v) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+// 16-byte cp.async of `bytes` (16 or 0, the rest zero-filled)
+__device__ __forceinline__ void cp_async16_z2(void* smem, const void* gmem, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n"
+               :
+               : "r"(tc::smem_addr(smem)), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_arrive_noinc2(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" : : "r"(tc::smem_addr(bar)) : "memory");
+}
+
+// Tape groups (16 bytes) of sample b at position t: 4 floats of dh_glu, or 8
+// halves of factor vector c.
+__device__ __forceinline__ int64_t t2h_group(int64_t B, int t, int g4, int64_t b, int D) {
+  return ((int64_t)t * (D / 4) + g4) * B + b;
+}
+__device__ __forceinline__ int64_t t2k_group(int64_t B, int t, int c, int g8, int64_t b, int D) {
+  return (((int64_t)t * 3 + c) * (D / 8) + g8) * B + b;
+}
+
+// ----------------------------------------------------------------------------
+// Phase 1a, the tape: parallel over (tile of 128 samples, position t).  One
+// CTA per SM walks runs of consecutive positions of one tile; per cell it
+// recomputes the forward pre-activations (MMA1, MMA2 with the hi / lo
+// operands, as in the forward), the GLU forward and backward (dz, y, G2; the
+// images for the weight gradients), dh_glu = G2 W2 (MMA_g), and the three
+// factors of the cell backward, which is linear in dh:
+//   G1 = [da_W | 2 da_g | d(U_mix h')] = dh [kW | kg | km],
+//   kW = u (1 - c^2),  kg = (c - U_mix h') (1 - tanh^2(a_g)) / 2,  km = 1 - u.
+// ----------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(128, 1)
-tc2d_sweep_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
-                  Sweep2Args a) {
+tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
+                 Sweep2Args a, int sites_per_run, int runs_per_tile) {
   using S = G2S<D>;
   constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
   extern __shared__ uint8_t smraw[];
@@ -106,7 +163,7 @@ tc2d_sweep_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__
   for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
-    for (int q = 0; q < 3; ++q) tc::mbar_init(&mbar[q], 1);
+    for (int q = 0; q < 2; ++q) tc::mbar_init(&mbar[q], 1);
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -116,30 +173,19 @@ tc2d_sweep_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__
   const uint32_t tbase = *tslot;
   const int m = threadIdx.x;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
-  const int Lx = a.Lx, Ly = a.Ly, N = a.N;
-  const int64_t tile = blockIdx.x;
-  const int64_t b = tile * 128 + m;
-  const bool valid = b < a.B;
-  const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+  const int Lx = a.Lx, N = a.N;
+  const int64_t B = a.B;
   const float dc = sAux[D];
-  const uint8_t* sg = a.sigma + (valid ? b : 0) * N;
-  const float* hc = a.hcache + (valid ? b : 0) * (int64_t)N * D;
-  float* cc = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D;
-  int n_up = 0;                      // up spins before the current position
-  if (valid)
-    for (int k = 0; k < N; ++k) n_up += sg[k] ? 0 : 1;
-  float carry[D];                    // dlog psi / dh_t from the horizontal successor
-#pragma unroll
-  for (int u = 0; u < D; ++u) carry[u] = 0.0f;
-  uint32_t ph[3] = {0, 0, 0};
+  const int64_t runs = (B + 127) / 128 * runs_per_tile;
+  uint32_t phases = 0;
   bool timed_out = false;
   const uint32_t one = 0x3F80u;
   auto wait = [&](int q) {
-    if (!tc::mbar_wait(&mbar[q], ph[q], kWait2)) {
+    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, kWait2)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
-    ph[q] ^= 1;
+    phases ^= 1u << q;
     tc::fence_after_sync();
   };
   auto sync_tc = [&]() {
@@ -148,199 +194,406 @@ tc2d_sweep_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__
     __syncthreads();
     tc::fence_after_sync();
   };
-
-  for (int t = N - 1; t >= 0; --t) {
-    const Pz p = zpos(t, Lx);
-    const int k = p.j * Lx + p.i;
-    const int s_k = valid ? (sg[k] ? 1 : 0) : 0;
-    n_up -= (s_k == 0);
-    const int s_h = p.r > 0 ? (valid ? (sg[p.j * Lx + zhor(p)] ? 1 : 0) : 0) : -1;
-    const int s_v = p.j > 0 ? (valid ? (sg[(p.j - 1) * Lx + p.i] ? 1 : 0) : 0) : -1;
-    // ---- A1 = [hi(h_hor) hi(h_ver) | extras | lo(h_hor) lo(h_ver)], A2 = [hi(h) | 1 1 | lo(h)] ----
+  uint4* th = reinterpret_cast<uint4*>(a.tape_h);
+  uint4* tk = reinterpret_cast<uint4*>(a.tape_k);
+  for (int64_t run = blockIdx.x; run < runs; run += gridDim.x) {
+    const int64_t tile = run / runs_per_tile;
+    const int t0 = (int)(run % runs_per_tile) * sites_per_run;
+    const int t1 = t0 + sites_per_run < N ? t0 + sites_per_run : N;
+    if (t0 >= t1) continue;                  // uniform
+    const int64_t b = tile * 128 + m;
+    const bool valid = b < B;
+    const float coef = valid ? 0.5f * a.weights[b] : 0.0f;
+    const uint8_t* sg = a.sigma + (valid ? b : 0) * N;
+    const float* hc = a.hcache + (valid ? b : 0) * (int64_t)N * D;
+    int n_up = 0;                            // up spins before position t
+    if (valid)
+      for (int t = 0; t < t0; ++t) {
+        const Pz q = zpos(t, Lx);
+        n_up += sg[q.j * Lx + q.i] ? 0 : 1;
+      }
+    for (int t = t0; t < t1; ++t) {
+      const Pz p = zpos(t, Lx);
+      const int k = p.j * Lx + p.i;
+      const int s_k = valid ? (sg[k] ? 1 : 0) : 0;
+      const int s_h = p.r > 0 ? (valid ? (sg[p.j * Lx + zhor(p)] ? 1 : 0) : 0) : -1;
+      const int s_v = p.j > 0 ? (valid ? (sg[(p.j - 1) * Lx + p.i] ? 1 : 0) : 0) : -1;
+      // ---- A1 = [hi(h_hor) hi(h_ver) | extras | lo(h_hor) lo(h_ver)], A2 = [hi(h) | 1 1 | lo(h)] ----
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
-      const float* src = hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+      for (int half = 0; half < 2; ++half) {
+        const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
+        const float* src =
+            hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+#pragma unroll
+        for (int c = 0; c < D / 16; ++c) {
+          float v[16];
+          ld16(src + 16 * c, ok, v);
+          st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c, KA1),
+                    sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c, KA1), v);
+          st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c + 8, KA1),
+                    sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c + 8, KA1), v + 8);
+        }
+      }
+      {
+        const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+        const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+        *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
+        *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+      }
 #pragma unroll
       for (int c = 0; c < D / 16; ++c) {
         float v[16];
-        ld16(src + 16 * c, ok, v);
-        st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c, KA1),
-                  sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c, KA1), v);
-        st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c + 8, KA1),
-                  sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c + 8, KA1), v + 8);
+        ld16(hc + (int64_t)k * D + 16 * c, valid, v);
+        st_split8(sA2 + tc::kmajor_offset(m, 16 * c, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c, KA2), v);
+        st_split8(sA2 + tc::kmajor_offset(m, 16 * c + 8, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c + 8, KA2), v + 8);
       }
-    }
-    {
-      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
-      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
-      *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
-      *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
-    }
+      *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+      sync_tc();
+      // ---- MMA1, MMA2: the forward pre-activations ----
+      if (m == 0) {
+        constexpr uint32_t i1 = tc::make_idesc_bf16(128, 3 * D), i2 = tc::make_idesc_bf16(128, 2 * D);
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
-      float v[16];
-      ld16(hc + (int64_t)k * D + 16 * c, valid, v);
-      st_split8(sA2 + tc::kmajor_offset(m, 16 * c, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c, KA2), v);
-      st_split8(sA2 + tc::kmajor_offset(m, 16 * c + 8, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c + 8, KA2), v + 8);
-    }
-    *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
-    // vertical successor's carry into this cell (its column's buffer entry)
-    const bool has_v = valid && p.j < Ly - 1;
-    sync_tc();
-    // ---- MMA1, MMA2: the forward pre-activations ----
-    if (m == 0) {
-      constexpr uint32_t i1 = tc::make_idesc_bf16(128, 3 * D), i2 = tc::make_idesc_bf16(128, 2 * D);
+        for (int c = 0; c < KA1 / 16; ++c) {
+          const int kb = c < K1 / 16 ? c : c - K1 / 16;
+          tc::mma_bf16(tbase + S::c1, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (KA1 / 8) * 128),
+                       tc::make_desc(tc::smem_addr(sW1) + kb * 256, 128, (K1 / 8) * 128), i1, c > 0);
+        }
 #pragma unroll
-      for (int c = 0; c < KA1 / 16; ++c) {
-        const int kb = c < K1 / 16 ? c : c - K1 / 16;
-        tc::mma_bf16(tbase + S::c1, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (KA1 / 8) * 128),
-                     tc::make_desc(tc::smem_addr(sW1) + kb * 256, 128, (K1 / 8) * 128), i1, c > 0);
+        for (int c = 0; c < KA2 / 16; ++c) {
+          const int kb = c < K2 / 16 ? c : c - K2 / 16;
+          tc::mma_bf16(tbase + S::c2, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (KA2 / 8) * 128),
+                       tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128), i2, c > 0);
+        }
+        tc::mma_commit(&mbar[0]);
+      }
+      wait(0);
+      // ---- GLU forward: the logit difference and dz ----
+      float z = 0.0f;
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) {
+        uint32_t a1[8], a2[8];
+        tld8(trow + S::c2 + 8 * c, a1);
+        tld8(trow + S::c2 + D + 8 * c, a2);
+        tc::tmem_wait_ld();
+        tie(a1);
+        tie(a2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          z = fmaf(sAux[8 * c + q], __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f), z);
+      }
+      const bool forced = a.sz0 && (n_up >= (N >> 1) || (t - n_up) >= (N >> 1));
+      const float dz = (forced || !valid) ? 0.0f : coef * ((s_k == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc));
+      n_up += (s_k == 0);
+      const int64_t img = tile * N + t;
+      a.dzimg[img * 128 + m] = dz;
+      // ---- GLU backward: G2 = [da_1 | 2 da_2], y for the readout gradient ----
+      uint8_t* g2g = a.g2img + (size_t)img * 128 * S::GW2 * 2;
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) {
+        uint32_t a1[8], a2[8];
+        tld8(trow + S::c2 + 8 * c, a1);
+        tld8(trow + S::c2 + D + 8 * c, a2);
+        tc::tmem_wait_ld();
+        tie(a1);
+        tie(a2);
+        float g1v[8], g2v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int v = 8 * c + q;
+          const float x1 = __uint_as_float(a1[q]);
+          const float th = hw_tanh2(__uint_as_float(a2[q]));
+          const float sg2 = fmaf(0.5f, th, 0.5f);
+          const float dy = dz * sAux[v];
+          g1v[q] = dy * sg2;                                   // d a_1
+          g2v[q] = 2.0f * dy * x1 * (0.25f * fmaf(-th, th, 1.0f));   // 2 d a_2 (W_2 halved in the image)
+          a.yimg[(img * D + v) * 128 + m] = x1 * sg2;
+        }
+        st_bf16_8(sA2 + tc::kmajor_offset(m, 8 * c, 2 * D), g1v);
+        st_bf16_8(sA2 + tc::kmajor_offset(m, D + 8 * c, 2 * D), g2v);
+        st_bf16_8(g2g + tc::kmajor_offset(m, 8 * c, S::GW2), g1v);
+        st_bf16_8(g2g + tc::kmajor_offset(m, D + 8 * c, S::GW2), g2v);
       }
 #pragma unroll
-      for (int c = 0; c < KA2 / 16; ++c) {
-        const int kb = c < K2 / 16 ? c : c - K2 / 16;
-        tc::mma_bf16(tbase + S::c2, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (KA2 / 8) * 128),
-                     tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128), i2, c > 0);
+      for (int c = 2 * D; c < S::GW2; c += 8)
+        *reinterpret_cast<uint4*>(g2g + tc::kmajor_offset(m, c, S::GW2)) = make_uint4(0u, 0u, 0u, 0u);
+      sync_tc();
+      // ---- MMA_g: dh (from the GLU) = G2 W2 ----
+      if (m == 0) {
+        constexpr uint32_t ig = tc::make_idesc_bf16(128, D) | (1u << 16);   // B MN-major
+#pragma unroll
+        for (int c = 0; c < 2 * D / 16; ++c)
+          tc::mma_bf16(tbase + S::cg, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (2 * D / 8) * 128),
+                       tc::make_desc(tc::smem_addr(sW2) + c * 2 * (K2 / 8) * 128, (K2 / 8) * 128, 128), ig, c > 0);
+        tc::mma_commit(&mbar[1]);
       }
-      tc::mma_commit(&mbar[0]);
-    }
-    wait(0);
-    // ---- GLU forward: the logit difference and dz ----
-    float z = 0.0f;
+      // ---- the cell factors, under MMA_g ----
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t a1[8], a2[8];
-      tld8(trow + S::c2 + 8 * c, a1);
-      tld8(trow + S::c2 + D + 8 * c, a2);
-      tc::tmem_wait_ld();
-      tie(a1);
-      tie(a2);
+      for (int c = 0; c < D / 8; ++c) {
+        uint32_t aw[8], ag[8], au[8];
+        tld8(trow + S::c1 + 8 * c, aw);
+        tld8(trow + S::c1 + D + 8 * c, ag);
+        tld8(trow + S::c1 + 2 * D + 8 * c, au);
+        tc::tmem_wait_ld();
+        tie(aw);
+        tie(ag);
+        tie(au);
+        float kw[8], kg[8], km[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        z = fmaf(sAux[8 * c + q], __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f), z);
-    }
-    const bool forced = a.sz0 && (n_up >= (N >> 1) || (t - n_up) >= (N >> 1));
-    const float dz = (forced || !valid) ? 0.0f : coef * ((s_k == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc));
-    const int64_t img = tile * N + t;
-    a.dzimg[img * 128 + m] = dz;
-    // ---- GLU backward: G2 = [da_1 | 2 da_2], y for the readout gradient ----
-    uint8_t* g2g = a.g2img + (size_t)img * 128 * S::GW2 * 2;
-#pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t a1[8], a2[8];
-      tld8(trow + S::c2 + 8 * c, a1);
-      tld8(trow + S::c2 + D + 8 * c, a2);
-      tc::tmem_wait_ld();
-      tie(a1);
-      tie(a2);
-      float g1v[8], g2v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int v = 8 * c + q;
-        const float x1 = __uint_as_float(a1[q]);
-        const float th = hw_tanh2(__uint_as_float(a2[q]));
-        const float sg2 = fmaf(0.5f, th, 0.5f);
-        const float dy = dz * sAux[v];
-        g1v[q] = dy * sg2;                                   // d a_1
-        g2v[q] = 2.0f * dy * x1 * (0.25f * fmaf(-th, th, 1.0f));   // 2 d a_2 (W_2 halved in the image)
-        a.yimg[(img * D + v) * 128 + m] = x1 * sg2;
+        for (int q = 0; q < 8; ++q) {
+          const float cc_ = hw_tanh2(__uint_as_float(aw[q]));
+          const float tg = hw_tanh2(__uint_as_float(ag[q]));
+          const float ug = fmaf(0.5f, tg, 0.5f);
+          kw[q] = ug * fmaf(-cc_, cc_, 1.0f);                               // u (1 - c^2)
+          kg[q] = (cc_ - __uint_as_float(au[q])) * (0.5f * fmaf(-tg, tg, 1.0f));   // 2 (c - mix) u (1 - u)
+          km[q] = 0.5f - 0.5f * tg;                                         // 1 - u
+        }
+        if (valid) {
+          tk[t2k_group(B, t, 0, c, b, D)] = pack_h8(kw);
+          tk[t2k_group(B, t, 1, c, b, D)] = pack_h8(kg);
+          tk[t2k_group(B, t, 2, c, b, D)] = pack_h8(km);
+        }
       }
-      st_bf16_8(sA2 + tc::kmajor_offset(m, 8 * c, 2 * D), g1v);
-      st_bf16_8(sA2 + tc::kmajor_offset(m, D + 8 * c, 2 * D), g2v);
-      st_bf16_8(g2g + tc::kmajor_offset(m, 8 * c, S::GW2), g1v);
-      st_bf16_8(g2g + tc::kmajor_offset(m, D + 8 * c, S::GW2), g2v);
-    }
-    sync_tc();
-    // ---- MMA_g: dh (from the GLU) = G2 W2 ----
-    if (m == 0) {
-      constexpr uint32_t ig = tc::make_idesc_bf16(128, D) | (1u << 16);   // B MN-major
+      wait(1);
 #pragma unroll
-      for (int c = 0; c < 2 * D / 16; ++c)
-        tc::mma_bf16(tbase + S::cg, tc::make_desc(tc::smem_addr(sA2) + c * 256, 128, (2 * D / 8) * 128),
-                     tc::make_desc(tc::smem_addr(sW2) + c * 2 * (K2 / 8) * 128, (K2 / 8) * 128, 128), ig, c > 0);
-      tc::mma_commit(&mbar[1]);
-    }
-    float cv[D];
-    if (has_v) {
-#pragma unroll
-      for (int q = 0; q < D / 4; ++q) {
-        const float4 x = reinterpret_cast<const float4*>(cc + p.i * D)[q];
-        cv[4 * q] = x.x; cv[4 * q + 1] = x.y; cv[4 * q + 2] = x.z; cv[4 * q + 3] = x.w;
+      for (int c = 0; c < D / 8; ++c) {
+        uint32_t gh[8];
+        tld8(trow + S::cg + 8 * c, gh);
+        tc::tmem_wait_ld();
+        tie(gh);
+        if (valid) {
+          th[t2h_group(B, t, 2 * c, b, D)] = make_uint4(gh[0], gh[1], gh[2], gh[3]);
+          th[t2h_group(B, t, 2 * c + 1, b, D)] = make_uint4(gh[4], gh[5], gh[6], gh[7]);
+        }
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < D; ++q) cv[q] = 0.0f;
+      // TMEM and the operand tiles are free for the next cell
+      tc::fence_before_sync();
+      if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+      tc::fence_after_sync();
     }
+    if (timed_out) break;                   // uniform
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// ----------------------------------------------------------------------------
+// Phase 1b, the sequential sweep: one CTA per tile of 128 samples, SPLIT
+// threads per sample on D / SPLIT units each, positions N-1 .. 0.  Per cell
+//   dh = dh_glu + carry (horizontal successor) + cv (vertical successor)
+//   G1 = dh [kW | kg | km] (BF16; also the image for the weight gradients)
+//   MMA_b: dh' = G1 W1 (W1 read as an MN-major operand; three K chains, one
+//          per gate block, summed on read)
+// dh' splits into the horizontal predecessor's carry (registers) and the
+// vertical predecessor's (a per-sample column carry in global memory, which
+// only the thread owning those units reads and writes).  The tape of the
+// next cell arrives by cp.async while a cell runs.
+// ----------------------------------------------------------------------------
+template <int D, int SPLIT>
+struct B2S {
+  static constexpr int K1 = 2 * D + 16;                    // W1 image columns
+  static constexpr int GW1 = 4 * D >= 128 ? 4 * D : 128;  // G1 image width
+  static constexpr int NG = D / 4 + 3 * D / 8;             // 16-byte tape groups per sample
+  static constexpr int kW1 = 0;                            // [3D x K1] bf16
+  static constexpr int kA1 = kW1 + 3 * D * K1 * 2;         // [128 x 3D] bf16 (G1)
+  static constexpr int kT = kA1 + 128 * 3 * D * 2;         // [NG][128] x 16 B tape of one cell
+  static constexpr int kBar = kT + NG * 128 * 16;          // 2 mbarriers
+  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+  static_assert(6 * D <= 512, "TMEM budget");
+};
+
+template <int D, int SPLIT>
+__global__ void __launch_bounds__(128 * SPLIT, 1)
+tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
+  using S = B2S<D, SPLIT>;
+  constexpr int NT = 128 * SPLIT, DU = D / SPLIT, K1 = S::K1;
+  static_assert(DU % 8 == 0, "at least 8 units per thread");
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  uint8_t* sW1 = sm + S::kW1;
+  uint8_t* sA1 = sm + S::kA1;
+  uint8_t* sT = sm + S::kT;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += NT)
+    reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);              // MMA_b done
+    tc::mbar_init(&mbar[1], NT);             // tape of the cell in place
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
+  const int u0 = part * DU;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int Lx = a.Lx, Ly = a.Ly, N = a.N;
+  const int64_t B = a.B;
+  const int64_t tile = blockIdx.x;
+  const int64_t b = tile * 128 + m;
+  const bool valid = b < B;
+  float* cc = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D + u0;
+  const uint4* th = reinterpret_cast<const uint4*>(a.tape_h);
+  const uint4* tk = reinterpret_cast<const uint4*>(a.tape_k);
+  uint32_t phases = 0;
+  bool timed_out = false;
+  auto wait = [&](int q) {
+    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, kWait2)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    phases ^= 1u << q;
+    tc::fence_after_sync();
+  };
+  // this thread's groups of the tape at position t (zeros past the batch)
+  auto fetch = [&](int t) {
+    const uint32_t n = valid ? 16u : 0u;
+#pragma unroll
+    for (int g = 0; g < DU / 4; ++g) {
+      const int gg = u0 / 4 + g;
+      cp_async16_z2(sT + (gg * 128 + m) * 16, th + (valid ? t2h_group(B, t, gg, b, D) : 0), n);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int g = 0; g < DU / 8; ++g) {
+        const int gg = u0 / 8 + g;
+        cp_async16_z2(sT + ((D / 4 + c * (D / 8) + gg) * 128 + m) * 16, tk + (valid ? t2k_group(B, t, c, gg, b, D) : 0),
+                      n);
+      }
+    cp_arrive_noinc2(&mbar[1]);
+  };
+  float carry[DU], cv[DU];
+#pragma unroll
+  for (int u = 0; u < DU; ++u) carry[u] = cv[u] = 0.0f;   // the last cell has no successors
+  fetch(N - 1);
+  for (int t = N - 1; t >= 0; --t) {
+    const Pz p = zpos(t, Lx);
     wait(1);
-    // ---- cell backward: G1 = [da_W | 2 da_g | d(U_mix h')] ----
+    // ---- G1 = dh [kW | kg | km], 8 units at a time ----
+    const int64_t img = tile * N + t;
     uint8_t* g1g = a.g1img + (size_t)img * 128 * S::GW1 * 2;
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t aw[8], ag[8], au[8], gh[8];
-      tld8(trow + S::c1 + 8 * c, aw);
-      tld8(trow + S::c1 + D + 8 * c, ag);
-      tld8(trow + S::c1 + 2 * D + 8 * c, au);
-      tld8(trow + S::cg + 8 * c, gh);
-      tc::tmem_wait_ld();
-      tie(aw);
-      tie(ag);
-      tie(au);
-      tie(gh);
+    for (int sc = 0; sc < DU / 8; ++sc) {
+      const int cu = u0 + 8 * sc;
+      float hg[8], kw[8], kg[8], km[8];
+      {
+        const float4 x0 = *reinterpret_cast<const float4*>(sT + ((cu / 4) * 128 + m) * 16);
+        const float4 x1 = *reinterpret_cast<const float4*>(sT + ((cu / 4 + 1) * 128 + m) * 16);
+        hg[0] = x0.x; hg[1] = x0.y; hg[2] = x0.z; hg[3] = x0.w; hg[4] = x1.x; hg[5] = x1.y; hg[6] = x1.z; hg[7] = x1.w;
+      }
+      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 0 * (D / 8) + cu / 8) * 128 + m) * 16), kw);
+      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 1 * (D / 8) + cu / 8) * 128 + m) * 16), kg);
+      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 2 * (D / 8) + cu / 8) * 128 + m) * 16), km);
       float gw[8], gg[8], gm[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int u = 8 * c + q;
-        const float cc_ = hw_tanh2(__uint_as_float(aw[q]));
-        const float tg = hw_tanh2(__uint_as_float(ag[q]));
-        const float ug = fmaf(0.5f, tg, 0.5f);
-        const float mix = __uint_as_float(au[q]);
-        const float dh = __uint_as_float(gh[q]) + carry[u] + cv[u];
-        const float dcand = dh * ug;
-        gw[q] = dcand * fmaf(-cc_, cc_, 1.0f);                            // d a_W
-        gg[q] = 2.0f * dh * (cc_ - mix) * (0.25f * fmaf(-tg, tg, 1.0f));   // 2 d a_g (W_g halved)
-        gm[q] = dh - dcand;                                               // d (U_mix h') = dh (1 - u)
+        const int j = 8 * sc + q;
+        const float dh = hg[q] + carry[j] + cv[j];
+        gw[q] = dh * kw[q];
+        gg[q] = dh * kg[q];
+        gm[q] = dh * km[q];
       }
-      st_bf16_8(sA1 + tc::kmajor_offset(m, 8 * c, 3 * D), gw);
-      st_bf16_8(sA1 + tc::kmajor_offset(m, D + 8 * c, 3 * D), gg);
-      st_bf16_8(sA1 + tc::kmajor_offset(m, 2 * D + 8 * c, 3 * D), gm);
-      st_bf16_8(g1g + tc::kmajor_offset(m, 8 * c, S::GW1), gw);
-      st_bf16_8(g1g + tc::kmajor_offset(m, D + 8 * c, S::GW1), gg);
-      st_bf16_8(g1g + tc::kmajor_offset(m, 2 * D + 8 * c, S::GW1), gm);
+      st_bf16_8(sA1 + tc::kmajor_offset(m, cu, 3 * D), gw);
+      st_bf16_8(sA1 + tc::kmajor_offset(m, D + cu, 3 * D), gg);
+      st_bf16_8(sA1 + tc::kmajor_offset(m, 2 * D + cu, 3 * D), gm);
+      st_bf16_8(g1g + tc::kmajor_offset(m, cu, S::GW1), gw);
+      st_bf16_8(g1g + tc::kmajor_offset(m, D + cu, S::GW1), gg);
+      st_bf16_8(g1g + tc::kmajor_offset(m, 2 * D + cu, S::GW1), gm);
     }
-    sync_tc();
-    // ---- MMA_b: dh' = G1 W1 (into the MMA2 columns, already read) ----
-    if (m == 0) {
+    // the image's padding columns (3D .. GW1), shared out over the parts
+    for (int c = 3 * D + 8 * part; c < S::GW1; c += 8 * SPLIT)
+      *reinterpret_cast<uint4*>(g1g + tc::kmajor_offset(m, c, S::GW1)) = make_uint4(0u, 0u, 0u, 0u);
+    // the tape buffer is read (each thread reads only its own groups): next cell's tape
+    if (t > 0) fetch(t - 1);
+    // the vertical carry into cell t - 1 from global memory, unless its
+    // vertical successor is this cell (then it is computed below)
+    const Pz pq = zpos(t > 0 ? t - 1 : 0, Lx);
+    const bool has_v1 = valid && t > 0 && pq.j < Ly - 1;
+    const bool succ_here = has_v1 && zsnake(pq.i, pq.j + 1, Lx) == t;
+    float cv1[DU];
+    if (has_v1 && !succ_here) {
+#pragma unroll
+      for (int q = 0; q < DU / 4; ++q) {
+        const float4 x = reinterpret_cast<const float4*>(cc + pq.i * D)[q];
+        cv1[4 * q] = x.x; cv1[4 * q + 1] = x.y; cv1[4 * q + 2] = x.z; cv1[4 * q + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < DU; ++q) cv1[q] = 0.0f;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    if (__syncthreads_or(timed_out)) { timed_out = true; break; }
+    tc::fence_after_sync();
+    // ---- MMA_b: dh' = G1 W1, three K chains into three column blocks ----
+    if (threadIdx.x == 0) {
       constexpr uint32_t ib = tc::make_idesc_bf16(128, 2 * D) | (1u << 16);   // B MN-major
 #pragma unroll
-      for (int c = 0; c < 3 * D / 16; ++c)
-        tc::mma_bf16(tbase + S::c2, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (3 * D / 8) * 128),
-                     tc::make_desc(tc::smem_addr(sW1) + c * 2 * (K1 / 8) * 128, (K1 / 8) * 128, 128), ib, c > 0);
-      tc::mma_commit(&mbar[2]);
+      for (int kk = 0; kk < D / 16; ++kk)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int c = j * (D / 16) + kk;
+          tc::mma_bf16(tbase + j * 2 * D, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (3 * D / 8) * 128),
+                       tc::make_desc(tc::smem_addr(sW1) + c * 2 * (K1 / 8) * 128, (K1 / 8) * 128, 128), ib, kk > 0);
+        }
+      tc::mma_commit(&mbar[0]);
     }
-    wait(2);
+    wait(0);
     // ---- carries: horizontal predecessor (t - 1 in the same row), vertical (i, j - 1) ----
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t dhh[8], dhv[8];
-      tld8(trow + S::c2 + 8 * c, dhh);
-      tld8(trow + S::c2 + D + 8 * c, dhv);
-      tc::tmem_wait_ld();
-      tie(dhh);
-      tie(dhv);
+    for (int c = 0; c < DU / 8; ++c) {
+      float hh[8], hv[8];
+      {
+        uint32_t r0[8], r1[8], r2[8];
+        tld8(trow + u0 + 8 * c, r0);
+        tld8(trow + 2 * D + u0 + 8 * c, r1);
+        tld8(trow + 4 * D + u0 + 8 * c, r2);
+        tc::tmem_wait_ld();
+        tie(r0);
+        tie(r1);
+        tie(r2);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) carry[8 * c + q] = p.r > 0 ? __uint_as_float(dhh[q]) : 0.0f;
+        for (int q = 0; q < 8; ++q)
+          hh[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
+      }
+      {
+        uint32_t r0[8], r1[8], r2[8];
+        tld8(trow + D + u0 + 8 * c, r0);
+        tld8(trow + 3 * D + u0 + 8 * c, r1);
+        tld8(trow + 5 * D + u0 + 8 * c, r2);
+        tc::tmem_wait_ld();
+        tie(r0);
+        tie(r1);
+        tie(r2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          hv[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) carry[8 * c + q] = p.r > 0 ? hh[q] : 0.0f;
       if (valid && p.j > 0) {
         float4* dst = reinterpret_cast<float4*>(cc + p.i * D + 8 * c);
-        dst[0] = make_float4(__uint_as_float(dhv[0]), __uint_as_float(dhv[1]), __uint_as_float(dhv[2]),
-                             __uint_as_float(dhv[3]));
-        dst[1] = make_float4(__uint_as_float(dhv[4]), __uint_as_float(dhv[5]), __uint_as_float(dhv[6]),
-                             __uint_as_float(dhv[7]));
+        dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+      }
+      if (succ_here) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cv1[8 * c + q] = hv[q];
       }
     }
-    if (timed_out) break;
+#pragma unroll
+    for (int u = 0; u < DU; ++u) cv[u] = cv1[u];
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // copies in flight after a timeout
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -616,11 +869,29 @@ cudaError_t run_grad(const Tc2Grad& g, const uint8_t* wimg, cudaStream_t st) {
   s.g2img = g.g2img;
   s.yimg = g.yimg;
   s.dzimg = g.dzimg;
+  s.tape_h = g.tape_h;
+  s.tape_k = g.tape_k;
   s.hdr = g.hdr;
-  auto ks = tc2d_sweep_kernel<D>;
-  cudaError_t e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, G2S<D>::kBytes);
+  // the tape: one CTA per SM, runs of consecutive positions of one tile
+  const int sms = sm_count_g();
+  const int runs_per_tile = tiles >= sms ? 1 : sms / tiles;
+  const int sites_per_run = (g.N + runs_per_tile - 1) / runs_per_tile;
+  int64_t tgrid = (int64_t)tiles * runs_per_tile;
+  if (tgrid > sms) tgrid = sms;
+  auto kt = tc2d_tape_kernel<D>;
+  cudaError_t e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, G2S<D>::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  ks<<<tiles, 128, G2S<D>::kBytes, st>>>(w1, w2, aux, s);
+  kt<<<(unsigned)tgrid, 128, G2S<D>::kBytes, st>>>(w1, w2, aux, s, sites_per_run, runs_per_tile);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the sequential sweep: 16 units per thread
+  constexpr int SPLIT = D / 16;
+  auto ks = tc2d_bsweep_kernel<D, SPLIT>;
+  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, B2S<D, SPLIT>::kBytes)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  ks<<<tiles, 128 * SPLIT, B2S<D, SPLIT>::kBytes, st>>>(w1, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   Wgrad2Args w{};
   w.B = g.B;
@@ -663,7 +934,9 @@ size_t tc2d_grad_image_bytes(int64_t B, int N, int D, int which) {
     case 0: return (size_t)nimg * 128 * gw1 * 2;          // G1 images
     case 1: return (size_t)nimg * 128 * gw2 * 2;          // G2 images
     case 2: return (size_t)nimg * D * 128 * 4;             // y
-    default: return (size_t)nimg * 128 * 4;                // dz
+    case 3: return (size_t)nimg * 128 * 4;                 // dz
+    case 4: return (size_t)B * N * D * 4;                  // tape: dh through the GLU
+    default: return (size_t)B * N * 3 * D * 2;             // tape: cell-backward factors
   }
 }
 
