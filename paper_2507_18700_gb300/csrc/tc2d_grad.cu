@@ -64,8 +64,8 @@ struct Sweep2Args {
   const float* hcache;
   const float* weights;
   float* ccarry;             // [B, Lx, d] vertical carries
-  uint8_t* g1img;            // [tiles, N] images of 128 x GW1 bf16 (padding columns written as zero)
-  uint8_t* g2img;            // [tiles, N] images of 128 x GW2 bf16 (padding columns written as zero)
+  uint8_t* g1img;            // [tiles, N] images of 128 x GW1 bf16 (padding columns never read back)
+  uint8_t* g2img;            // [tiles, N] images of 128 x GW2 bf16 (padding columns never read back)
   float* yimg;               // [tiles, N, d, 128]
   float* dzimg;              // [tiles, N, 128]
   float* tape_h;             // [N][d / 4][B][4] f32: dlog psi / dh through the GLU
@@ -314,9 +314,6 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
         st_bf16_8(g2g + tc::kmajor_offset(m, 8 * c, S::GW2), g1v);
         st_bf16_8(g2g + tc::kmajor_offset(m, D + 8 * c, S::GW2), g2v);
       }
-#pragma unroll
-      for (int c = 2 * D; c < S::GW2; c += 8)
-        *reinterpret_cast<uint4*>(g2g + tc::kmajor_offset(m, c, S::GW2)) = make_uint4(0u, 0u, 0u, 0u);
       sync_tc();
       // ---- MMA_g: dh (from the GLU) = G2 W2 ----
       if (m == 0) {
@@ -423,8 +420,9 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
-    tc::mbar_init(&mbar[0], 1);              // MMA_b done
+    tc::mbar_init(&mbar[0], 1);              // MMA_b, horizontal half, done
     tc::mbar_init(&mbar[1], NT);             // tape of the cell in place
+    tc::mbar_init(&mbar[2], 1);              // MMA_b, vertical half, done
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -441,8 +439,11 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   const int64_t b = tile * 128 + m;
   const bool valid = b < B;
   float* cc = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D + u0;
-  const uint4* th = reinterpret_cast<const uint4*>(a.tape_h);
-  const uint4* tk = reinterpret_cast<const uint4*>(a.tape_k);
+  // this thread's tape groups: dh_glu group g at th_b + t GH + g B, factor
+  // vector c group g at tk_b + (3 t + c) GK + g B
+  const int64_t GH = (int64_t)(D / 4) * B, GK = (int64_t)(D / 8) * B;
+  const uint4* th_b = reinterpret_cast<const uint4*>(a.tape_h) + (valid ? b + (int64_t)(u0 / 4) * B : 0);
+  const uint4* tk_b = reinterpret_cast<const uint4*>(a.tape_k) + (valid ? b + (int64_t)(u0 / 8) * B : 0);
   uint32_t phases = 0;
   bool timed_out = false;
   auto wait = [&](int q) {
@@ -456,28 +457,74 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   // this thread's groups of the tape at position t (zeros past the batch)
   auto fetch = [&](int t) {
     const uint32_t n = valid ? 16u : 0u;
+    const uint4* h = th_b + (valid ? t * GH : 0);
+    const uint4* k = tk_b + (valid ? 3 * t * GK : 0);
 #pragma unroll
-    for (int g = 0; g < DU / 4; ++g) {
-      const int gg = u0 / 4 + g;
-      cp_async16_z2(sT + (gg * 128 + m) * 16, th + (valid ? t2h_group(B, t, gg, b, D) : 0), n);
-    }
+    for (int g = 0; g < DU / 4; ++g)
+      cp_async16_z2(sT + ((u0 / 4 + g) * 128 + m) * 16, h + (valid ? g * B : 0), n);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int g = 0; g < DU / 8; ++g) {
-        const int gg = u0 / 8 + g;
-        cp_async16_z2(sT + ((D / 4 + c * (D / 8) + gg) * 128 + m) * 16, tk + (valid ? t2k_group(B, t, c, gg, b, D) : 0),
-                      n);
-      }
+      for (int g = 0; g < DU / 8; ++g)
+        cp_async16_z2(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * 128 + m) * 16, k + (valid ? c * GK + g * B : 0), n);
     cp_arrive_noinc2(&mbar[1]);
   };
-  float carry[DU], cv[DU];
+  // dh' = G1 W1 in six accumulators: three K chains (one per gate block) for
+  // each of its halves, the horizontal predecessor's [0, D) (needed at once)
+  // and the vertical predecessor's [D, 2D) (needed a row later; its MMAs run
+  // under the next cell)
+  auto tmem_sum3 = [&](int col, float (&v)[8]) {
+    uint32_t r0[8], r1[8], r2[8];
+    tld8(trow + col, r0);
+    tld8(trow + D + col, r1);
+    tld8(trow + 2 * D + col, r2);
+    tc::tmem_wait_ld();
+    tie(r0);
+    tie(r1);
+    tie(r2);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
+  };
+  float carry[DU], cv[DU];                 // dh' of the horizontal and the vertical successor
 #pragma unroll
   for (int u = 0; u < DU; ++u) carry[u] = cv[u] = 0.0f;   // the last cell has no successors
   fetch(N - 1);
   for (int t = N - 1; t >= 0; --t) {
     const Pz p = zpos(t, Lx);
     wait(1);
+    // this thread's tape groups into registers; the buffer then takes the
+    // next cell's tape, whose copy runs under the rest of this cell
+    uint4 th4[DU / 4], tk4[3][DU / 8];
+#pragma unroll
+    for (int g = 0; g < DU / 4; ++g) th4[g] = *reinterpret_cast<const uint4*>(sT + ((u0 / 4 + g) * 128 + m) * 16);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int g = 0; g < DU / 8; ++g)
+        tk4[c][g] = *reinterpret_cast<const uint4*>(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * 128 + m) * 16);
+    if (t > 0) fetch(t - 1);
+    if (t < N - 1) {
+      // the vertical half of cell t + 1: G1 is free again, and its dh' goes
+      // to the column carry of (i, j - 1), or straight into this cell when
+      // this cell is that predecessor
+      wait(2);
+      const Pz p1 = zpos(t + 1, Lx);
+      const bool here = p.j < Ly - 1 && zsnake(p.i, p.j + 1, Lx) == t + 1;
+#pragma unroll
+      for (int c = 0; c < DU / 8; ++c) {
+        float hv[8];
+        tmem_sum3(3 * D + u0 + 8 * c, hv);
+        if (valid && p1.j > 0) {
+          float4* dst = reinterpret_cast<float4*>(cc + p1.i * D + 8 * c);
+          dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        }
+        if (here) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) cv[8 * c + q] = hv[q];
+        }
+      }
+    }
     // ---- G1 = dh [kW | kg | km], 8 units at a time ----
     const int64_t img = tile * N + t;
     uint8_t* g1g = a.g1img + (size_t)img * 128 * S::GW1 * 2;
@@ -486,13 +533,14 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
       const int cu = u0 + 8 * sc;
       float hg[8], kw[8], kg[8], km[8];
       {
-        const float4 x0 = *reinterpret_cast<const float4*>(sT + ((cu / 4) * 128 + m) * 16);
-        const float4 x1 = *reinterpret_cast<const float4*>(sT + ((cu / 4 + 1) * 128 + m) * 16);
-        hg[0] = x0.x; hg[1] = x0.y; hg[2] = x0.z; hg[3] = x0.w; hg[4] = x1.x; hg[5] = x1.y; hg[6] = x1.z; hg[7] = x1.w;
+        const uint4 x0 = th4[2 * sc], x1 = th4[2 * sc + 1];
+        hg[0] = __uint_as_float(x0.x); hg[1] = __uint_as_float(x0.y); hg[2] = __uint_as_float(x0.z);
+        hg[3] = __uint_as_float(x0.w); hg[4] = __uint_as_float(x1.x); hg[5] = __uint_as_float(x1.y);
+        hg[6] = __uint_as_float(x1.z); hg[7] = __uint_as_float(x1.w);
       }
-      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 0 * (D / 8) + cu / 8) * 128 + m) * 16), kw);
-      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 1 * (D / 8) + cu / 8) * 128 + m) * 16), kg);
-      unpack_h8(*reinterpret_cast<const uint4*>(sT + ((D / 4 + 2 * (D / 8) + cu / 8) * 128 + m) * 16), km);
+      unpack_h8(tk4[0][sc], kw);
+      unpack_h8(tk4[1][sc], kg);
+      unpack_h8(tk4[2][sc], km);
       float gw[8], gg[8], gm[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -505,22 +553,19 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
       st_bf16_8(sA1 + tc::kmajor_offset(m, cu, 3 * D), gw);
       st_bf16_8(sA1 + tc::kmajor_offset(m, D + cu, 3 * D), gg);
       st_bf16_8(sA1 + tc::kmajor_offset(m, 2 * D + cu, 3 * D), gm);
+      // the image for the weight gradients (its padding columns 3D .. GW1 are
+      // never written: they only feed accumulator rows that are not read)
       st_bf16_8(g1g + tc::kmajor_offset(m, cu, S::GW1), gw);
       st_bf16_8(g1g + tc::kmajor_offset(m, D + cu, S::GW1), gg);
       st_bf16_8(g1g + tc::kmajor_offset(m, 2 * D + cu, S::GW1), gm);
     }
-    // the image's padding columns (3D .. GW1), shared out over the parts
-    for (int c = 3 * D + 8 * part; c < S::GW1; c += 8 * SPLIT)
-      *reinterpret_cast<uint4*>(g1g + tc::kmajor_offset(m, c, S::GW1)) = make_uint4(0u, 0u, 0u, 0u);
-    // the tape buffer is read (each thread reads only its own groups): next cell's tape
-    if (t > 0) fetch(t - 1);
-    // the vertical carry into cell t - 1 from global memory, unless its
-    // vertical successor is this cell (then it is computed below)
+    // the vertical carry into cell t - 1 from global memory (written when its
+    // vertical successor's MMAs completed, one cell after that successor),
+    // unless that successor is this cell (then it is taken at the next cell)
     const Pz pq = zpos(t > 0 ? t - 1 : 0, Lx);
-    const bool has_v1 = valid && t > 0 && pq.j < Ly - 1;
-    const bool succ_here = has_v1 && zsnake(pq.i, pq.j + 1, Lx) == t;
+    const bool from_mem = valid && t > 0 && pq.j < Ly - 1 && zsnake(pq.i, pq.j + 1, Lx) != t;
     float cv1[DU];
-    if (has_v1 && !succ_here) {
+    if (from_mem) {
 #pragma unroll
       for (int q = 0; q < DU / 4; ++q) {
         const float4 x = reinterpret_cast<const float4*>(cc + pq.i * D)[q];
@@ -534,65 +579,38 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     tc::fence_before_sync();
     if (__syncthreads_or(timed_out)) { timed_out = true; break; }
     tc::fence_after_sync();
-    // ---- MMA_b: dh' = G1 W1, three K chains into three column blocks ----
+    // ---- MMA_b: the horizontal half, then the vertical half ----
     if (threadIdx.x == 0) {
-      constexpr uint32_t ib = tc::make_idesc_bf16(128, 2 * D) | (1u << 16);   // B MN-major
+      constexpr uint32_t ib = tc::make_idesc_bf16(128, D) | (1u << 16);   // B MN-major, N = D
 #pragma unroll
-      for (int kk = 0; kk < D / 16; ++kk)
+      for (int half = 0; half < 2; ++half) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int c = j * (D / 16) + kk;
-          tc::mma_bf16(tbase + j * 2 * D, tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (3 * D / 8) * 128),
-                       tc::make_desc(tc::smem_addr(sW1) + c * 2 * (K1 / 8) * 128, (K1 / 8) * 128, 128), ib, kk > 0);
-        }
-      tc::mma_commit(&mbar[0]);
+        for (int kk = 0; kk < D / 16; ++kk)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const int c = j * (D / 16) + kk;
+            tc::mma_bf16(tbase + half * 3 * D + j * D,
+                         tc::make_desc(tc::smem_addr(sA1) + c * 256, 128, (3 * D / 8) * 128),
+                         tc::make_desc(tc::smem_addr(sW1) + c * 2 * (K1 / 8) * 128 + half * (D / 8) * 128,
+                                       (K1 / 8) * 128, 128),
+                         ib, kk > 0);
+          }
+        tc::mma_commit(&mbar[half ? 2 : 0]);
+      }
     }
     wait(0);
-    // ---- carries: horizontal predecessor (t - 1 in the same row), vertical (i, j - 1) ----
+    // ---- the horizontal predecessor's carry (t - 1 in the same row) ----
 #pragma unroll
     for (int c = 0; c < DU / 8; ++c) {
-      float hh[8], hv[8];
-      {
-        uint32_t r0[8], r1[8], r2[8];
-        tld8(trow + u0 + 8 * c, r0);
-        tld8(trow + 2 * D + u0 + 8 * c, r1);
-        tld8(trow + 4 * D + u0 + 8 * c, r2);
-        tc::tmem_wait_ld();
-        tie(r0);
-        tie(r1);
-        tie(r2);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          hh[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
-      }
-      {
-        uint32_t r0[8], r1[8], r2[8];
-        tld8(trow + D + u0 + 8 * c, r0);
-        tld8(trow + 3 * D + u0 + 8 * c, r1);
-        tld8(trow + 5 * D + u0 + 8 * c, r2);
-        tc::tmem_wait_ld();
-        tie(r0);
-        tie(r1);
-        tie(r2);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          hv[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
-      }
+      float hh[8];
+      tmem_sum3(u0 + 8 * c, hh);
 #pragma unroll
       for (int q = 0; q < 8; ++q) carry[8 * c + q] = p.r > 0 ? hh[q] : 0.0f;
-      if (valid && p.j > 0) {
-        float4* dst = reinterpret_cast<float4*>(cc + p.i * D + 8 * c);
-        dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
-      }
-      if (succ_here) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) cv1[8 * c + q] = hv[q];
-      }
     }
 #pragma unroll
     for (int u = 0; u < DU; ++u) cv[u] = cv1[u];
   }
+  if (!timed_out) wait(2);                 // the last vertical half, before TMEM is freed
   asm volatile("cp.async.wait_all;\n" ::: "memory");   // copies in flight after a timeout
   tc::fence_before_sync();
   __syncthreads();
