@@ -271,7 +271,8 @@ void nqs_set_autotune(int on);
  * the autotuner and its cache; variant < 0 returns to normal selection.
  * Variants differ in threads per row (1, 2, 4) and, for sampling, teacher
  * forcing and the reverse sweep, in rows per 128-lane tile (128, or 64 or 32
- * to put more SMs on a small batch).  Per-sample results (samples, log psi, cache,
+ * to put more SMs on a small batch; the 2D reverse sweep takes 128 rows for
+ * variant 0 and 32 for any other).  Per-sample results (samples, log psi, cache,
  * local energies) are bitwise the same in every variant; the gradient, a sum
  * over samples grouped by tile, is bitwise the same for the same rows per tile
  * and equal to rounding otherwise.  This is for timing and testing them one

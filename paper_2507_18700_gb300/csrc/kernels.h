@@ -190,6 +190,7 @@ struct TcBpttArgs {
 int tc1d_supported(int D);
 void tc1d_set_autotune(int on);
 void tc1d_set_variant(int v);
+int tc1d_pinned_variant();   // the pinned tile variant, -1 if none
 int tc1d_bptt_partial_rows(int64_t B);
 size_t tc1d_tape_bytes(int64_t B, int N, int D, int which);   // which: 0 e, 1 x, 2 k
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st);

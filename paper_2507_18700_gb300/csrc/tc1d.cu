@@ -1362,6 +1362,11 @@ void tc1d_set_variant(int v) {
   g_force = v < 0 ? -1 : v;
 }
 
+int tc1d_pinned_variant() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_force;
+}
+
 // rows of per-CTA partial gradients: the reverse sweep's CTAs (at most one per
 // 32 samples) and then the tape kernel's CTAs (readout gradients)
 constexpr int kTapeRows = 304;

@@ -388,32 +388,44 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
 // only the thread owning those units reads and writes).  The tape of the
 // next cell arrives by cp.async while a cell runs.
 // ----------------------------------------------------------------------------
-template <int D, int SPLIT>
+template <int D, int SPLIT, int ROWS>
 struct B2S {
   static constexpr int K1 = 2 * D + 16;                    // W1 image columns
   static constexpr int GW1 = 4 * D >= 128 ? 4 * D : 128;  // G1 image width
+  static constexpr int RQ = ROWS / 32;                     // TMEM lane quarters holding distinct samples
+  static constexpr int NS = (4 / RQ) * SPLIT;              // unit slices per sample
+  static constexpr int DU = D / NS;                        // units per thread
   static constexpr int NG = D / 4 + 3 * D / 8;             // 16-byte tape groups per sample
+  static constexpr int CS = D + 4;                         // exchange row stride (floats)
   static constexpr int kW1 = 0;                            // [3D x K1] bf16
-  static constexpr int kA1 = kW1 + 3 * D * K1 * 2;         // [128 x 3D] bf16 (G1)
-  static constexpr int kT = kA1 + 128 * 3 * D * 2;         // [NG][128] x 16 B tape of one cell
-  static constexpr int kBar = kT + NG * 128 * 16;          // 2 mbarriers
-  static constexpr int kSlot = kBar + 16;
+  static constexpr int kA1 = kW1 + 3 * D * K1 * 2;         // [128 x 3D] bf16 (G1; rows past ROWS unused)
+  static constexpr int kT = kA1 + 128 * 3 * D * 2;         // [NG][ROWS] x 16 B tape of one cell
+  static constexpr int kC = kT + NG * ROWS * 16;           // 2 x [ROWS x CS] f32 (ROWS < 128)
+  static constexpr int kBar = kC + (ROWS < 128 ? 2 * ROWS * CS * 4 : 0);   // 3 mbarriers
+  static constexpr int kSlot = kBar + 32;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
   static_assert(6 * D <= 512, "TMEM budget");
+  static_assert(DU >= 8 && DU % 8 == 0 && ROWS % 32 == 0 && ROWS <= 128, "tile shape");
 };
 
-template <int D, int SPLIT>
+// Thread -> (sample, unit slice): warp w is in TMEM lane quarter q = w % 4;
+// quarters q % RQ hold distinct samples s = 32 (q % RQ) + lane and split its
+// units with the SPLIT warps of a quarter into NS slices.  With ROWS < 128
+// the quarters that own the samples' lanes pass dh' on through shared memory.
+template <int D, int SPLIT, int ROWS>
 __global__ void __launch_bounds__(128 * SPLIT, 1)
 tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
-  using S = B2S<D, SPLIT>;
-  constexpr int NT = 128 * SPLIT, DU = D / SPLIT, K1 = S::K1;
-  static_assert(DU % 8 == 0, "at least 8 units per thread");
+  using S = B2S<D, SPLIT, ROWS>;
+  constexpr int NT = 128 * SPLIT, DU = S::DU, K1 = S::K1, RQ = S::RQ, CS = S::CS;
+  constexpr bool XCH = ROWS < 128;         // carries exchanged through shared memory
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sW1 = sm + S::kW1;
   uint8_t* sA1 = sm + S::kA1;
   uint8_t* sT = sm + S::kT;
+  float* sCh = reinterpret_cast<float*>(sm + S::kC);
+  float* sCv = sCh + ROWS * CS;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
   for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += NT)
@@ -430,17 +442,22 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, part = wt / 4, m = (wt % 4) * 32 + lane;
-  const int u0 = part * DU;
-  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, q4 = wt % 4, p = wt / 4;
+  const int s = 32 * (q4 % RQ) + lane;     // sample row of the tile (and its TMEM lane)
+  const int u0 = ((q4 / RQ) * SPLIT + p) * DU;
+  const bool owner = q4 < RQ;              // this warp's TMEM lanes are its samples'
+  constexpr int CW = D / SPLIT;            // columns an owner moves in an exchange
+  const uint32_t trow = tbase + ((uint32_t)(32 * q4) << 16);
   const int Lx = a.Lx, Ly = a.Ly, N = a.N;
   const int64_t B = a.B;
-  const int64_t tile = blockIdx.x;
-  const int64_t b = tile * 128 + m;
+  const int64_t b = (int64_t)blockIdx.x * ROWS + s;
   const bool valid = b < B;
-  float* cc = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D + u0;
-  // this thread's tape groups: dh_glu group g at th_b + t GH + g B, factor
-  // vector c group g at tk_b + (3 t + c) GK + g B
+  // the G1 image of the 128-sample tile holding this sample
+  const int64_t itile = ((int64_t)blockIdx.x * ROWS) / 128;
+  const int irow = (int)(((int64_t)blockIdx.x * ROWS) % 128) + s;
+  float* ccb = a.ccarry + (valid ? b : 0) * (int64_t)Lx * D;
+  // tape groups: dh_glu group g at th_b + t GH + g B, factor vector c group g
+  // at tk_b + (3 t + c) GK + g B
   const int64_t GH = (int64_t)(D / 4) * B, GK = (int64_t)(D / 8) * B;
   const uint4* th_b = reinterpret_cast<const uint4*>(a.tape_h) + (valid ? b + (int64_t)(u0 / 4) * B : 0);
   const uint4* tk_b = reinterpret_cast<const uint4*>(a.tape_k) + (valid ? b + (int64_t)(u0 / 8) * B : 0);
@@ -454,6 +471,11 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     phases ^= 1u << q;
     tc::fence_after_sync();
   };
+  auto sync = [&]() {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
   // this thread's groups of the tape at position t (zeros past the batch)
   auto fetch = [&](int t) {
     const uint32_t n = valid ? 16u : 0u;
@@ -461,12 +483,12 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     const uint4* k = tk_b + (valid ? 3 * t * GK : 0);
 #pragma unroll
     for (int g = 0; g < DU / 4; ++g)
-      cp_async16_z2(sT + ((u0 / 4 + g) * 128 + m) * 16, h + (valid ? g * B : 0), n);
+      cp_async16_z2(sT + ((u0 / 4 + g) * ROWS + s) * 16, h + (valid ? g * B : 0), n);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int g = 0; g < DU / 8; ++g)
-        cp_async16_z2(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * 128 + m) * 16, k + (valid ? c * GK + g * B : 0), n);
+        cp_async16_z2(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * ROWS + s) * 16, k + (valid ? c * GK + g * B : 0), n);
     cp_arrive_noinc2(&mbar[1]);
   };
   // dh' = G1 W1 in six accumulators: three K chains (one per gate block) for
@@ -483,51 +505,81 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     tie(r1);
     tie(r2);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (__uint_as_float(r0[q]) + __uint_as_float(r1[q])) + __uint_as_float(r2[q]);
+    for (int i = 0; i < 8; ++i) v[i] = (__uint_as_float(r0[i]) + __uint_as_float(r1[i])) + __uint_as_float(r2[i]);
   };
   float carry[DU], cv[DU];                 // dh' of the horizontal and the vertical successor
 #pragma unroll
   for (int u = 0; u < DU; ++u) carry[u] = cv[u] = 0.0f;   // the last cell has no successors
   fetch(N - 1);
   for (int t = N - 1; t >= 0; --t) {
-    const Pz p = zpos(t, Lx);
+    const Pz pz = zpos(t, Lx);
     wait(1);
     // this thread's tape groups into registers; the buffer then takes the
     // next cell's tape, whose copy runs under the rest of this cell
     uint4 th4[DU / 4], tk4[3][DU / 8];
 #pragma unroll
-    for (int g = 0; g < DU / 4; ++g) th4[g] = *reinterpret_cast<const uint4*>(sT + ((u0 / 4 + g) * 128 + m) * 16);
+    for (int g = 0; g < DU / 4; ++g) th4[g] = *reinterpret_cast<const uint4*>(sT + ((u0 / 4 + g) * ROWS + s) * 16);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int g = 0; g < DU / 8; ++g)
-        tk4[c][g] = *reinterpret_cast<const uint4*>(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * 128 + m) * 16);
+        tk4[c][g] = *reinterpret_cast<const uint4*>(sT + ((D / 4 + c * (D / 8) + u0 / 8 + g) * ROWS + s) * 16);
     if (t > 0) fetch(t - 1);
     if (t < N - 1) {
       // the vertical half of cell t + 1: G1 is free again, and its dh' goes
       // to the column carry of (i, j - 1), or straight into this cell when
       // this cell is that predecessor
-      wait(2);
       const Pz p1 = zpos(t + 1, Lx);
-      const bool here = p.j < Ly - 1 && zsnake(p.i, p.j + 1, Lx) == t + 1;
+      const bool here = pz.j < Ly - 1 && zsnake(pz.i, pz.j + 1, Lx) == t + 1;   // uniform
+      if (!XCH) {
+        wait(2);
 #pragma unroll
-      for (int c = 0; c < DU / 8; ++c) {
-        float hv[8];
-        tmem_sum3(3 * D + u0 + 8 * c, hv);
-        if (valid && p1.j > 0) {
-          float4* dst = reinterpret_cast<float4*>(cc + p1.i * D + 8 * c);
-          dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
-          dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        for (int c = 0; c < DU / 8; ++c) {
+          float hv[8];
+          tmem_sum3(3 * D + u0 + 8 * c, hv);
+          if (valid && p1.j > 0) {
+            float4* dst = reinterpret_cast<float4*>(ccb + p1.i * D + u0 + 8 * c);
+            dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+          }
+          if (here) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cv[8 * c + i] = hv[i];
+          }
         }
+      } else {
+        if (owner) {
+          wait(2);
+#pragma unroll
+          for (int c = 0; c < CW / 8; ++c) {
+            float hv[8];
+            tmem_sum3(3 * D + p * CW + 8 * c, hv);
+            if (valid && p1.j > 0) {
+              float4* dst = reinterpret_cast<float4*>(ccb + p1.i * D + p * CW + 8 * c);
+              dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+              dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+            }
+            if (here) {
+              float4* dst = reinterpret_cast<float4*>(sCv + s * CS + p * CW + 8 * c);
+              dst[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+              dst[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+            }
+          }
+        }
+        // G1 is rewritten below (the MMAs have read it), and the column
+        // carries and the exchange are published
+        sync();
         if (here) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) cv[8 * c + q] = hv[q];
+          for (int c = 0; c < DU / 4; ++c) {
+            const float4 x = reinterpret_cast<const float4*>(sCv + s * CS + u0)[c];
+            cv[4 * c] = x.x; cv[4 * c + 1] = x.y; cv[4 * c + 2] = x.z; cv[4 * c + 3] = x.w;
+          }
         }
       }
     }
     // ---- G1 = dh [kW | kg | km], 8 units at a time ----
-    const int64_t img = tile * N + t;
-    uint8_t* g1g = a.g1img + (size_t)img * 128 * S::GW1 * 2;
+    uint8_t* g1g = a.g1img + (size_t)(itile * N + t) * 128 * S::GW1 * 2;
 #pragma unroll
     for (int sc = 0; sc < DU / 8; ++sc) {
       const int cu = u0 + 8 * sc;
@@ -543,37 +595,21 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
       unpack_h8(tk4[2][sc], km);
       float gw[8], gg[8], gm[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = 8 * sc + q;
-        const float dh = hg[q] + carry[j] + cv[j];
-        gw[q] = dh * kw[q];
-        gg[q] = dh * kg[q];
-        gm[q] = dh * km[q];
+      for (int i = 0; i < 8; ++i) {
+        const int j = 8 * sc + i;
+        const float dh = hg[i] + carry[j] + cv[j];
+        gw[i] = dh * kw[i];
+        gg[i] = dh * kg[i];
+        gm[i] = dh * km[i];
       }
-      st_bf16_8(sA1 + tc::kmajor_offset(m, cu, 3 * D), gw);
-      st_bf16_8(sA1 + tc::kmajor_offset(m, D + cu, 3 * D), gg);
-      st_bf16_8(sA1 + tc::kmajor_offset(m, 2 * D + cu, 3 * D), gm);
+      st_bf16_8(sA1 + tc::kmajor_offset(s, cu, 3 * D), gw);
+      st_bf16_8(sA1 + tc::kmajor_offset(s, D + cu, 3 * D), gg);
+      st_bf16_8(sA1 + tc::kmajor_offset(s, 2 * D + cu, 3 * D), gm);
       // the image for the weight gradients (its padding columns 3D .. GW1 are
       // never written: they only feed accumulator rows that are not read)
-      st_bf16_8(g1g + tc::kmajor_offset(m, cu, S::GW1), gw);
-      st_bf16_8(g1g + tc::kmajor_offset(m, D + cu, S::GW1), gg);
-      st_bf16_8(g1g + tc::kmajor_offset(m, 2 * D + cu, S::GW1), gm);
-    }
-    // the vertical carry into cell t - 1 from global memory (written when its
-    // vertical successor's MMAs completed, one cell after that successor),
-    // unless that successor is this cell (then it is taken at the next cell)
-    const Pz pq = zpos(t > 0 ? t - 1 : 0, Lx);
-    const bool from_mem = valid && t > 0 && pq.j < Ly - 1 && zsnake(pq.i, pq.j + 1, Lx) != t;
-    float cv1[DU];
-    if (from_mem) {
-#pragma unroll
-      for (int q = 0; q < DU / 4; ++q) {
-        const float4 x = reinterpret_cast<const float4*>(cc + pq.i * D)[q];
-        cv1[4 * q] = x.x; cv1[4 * q + 1] = x.y; cv1[4 * q + 2] = x.z; cv1[4 * q + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < DU; ++q) cv1[q] = 0.0f;
+      st_bf16_8(g1g + tc::kmajor_offset(irow, cu, S::GW1), gw);
+      st_bf16_8(g1g + tc::kmajor_offset(irow, D + cu, S::GW1), gg);
+      st_bf16_8(g1g + tc::kmajor_offset(irow, 2 * D + cu, S::GW1), gm);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -598,19 +634,58 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
         tc::mma_commit(&mbar[half ? 2 : 0]);
       }
     }
-    wait(0);
+    // the vertical carry into cell t - 1 from global memory (written when its
+    // vertical successor's MMAs completed, published by the barrier above),
+    // unless that successor is this cell (then it is taken at the next cell)
+    const Pz pq = zpos(t > 0 ? t - 1 : 0, Lx);
+    const bool from_mem = valid && t > 0 && pq.j < Ly - 1 && zsnake(pq.i, pq.j + 1, Lx) != t;
+    float cv1[DU];
+    if (from_mem) {
+#pragma unroll
+      for (int c = 0; c < DU / 4; ++c) {
+        const float4 x = reinterpret_cast<const float4*>(ccb + pq.i * D + u0)[c];
+        cv1[4 * c] = x.x; cv1[4 * c + 1] = x.y; cv1[4 * c + 2] = x.z; cv1[4 * c + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < DU; ++c) cv1[c] = 0.0f;
+    }
     // ---- the horizontal predecessor's carry (t - 1 in the same row) ----
+    if (!XCH) {
+      wait(0);
 #pragma unroll
-    for (int c = 0; c < DU / 8; ++c) {
-      float hh[8];
-      tmem_sum3(u0 + 8 * c, hh);
+      for (int c = 0; c < DU / 8; ++c) {
+        float hh[8];
+        tmem_sum3(u0 + 8 * c, hh);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) carry[8 * c + q] = p.r > 0 ? hh[q] : 0.0f;
+        for (int i = 0; i < 8; ++i) carry[8 * c + i] = pz.r > 0 ? hh[i] : 0.0f;
+      }
+    } else {
+      if (owner) {
+        wait(0);
+#pragma unroll
+        for (int c = 0; c < CW / 8; ++c) {
+          float hh[8];
+          tmem_sum3(p * CW + 8 * c, hh);
+          float4* dst = reinterpret_cast<float4*>(sCh + s * CS + p * CW + 8 * c);
+          dst[0] = make_float4(hh[0], hh[1], hh[2], hh[3]);
+          dst[1] = make_float4(hh[4], hh[5], hh[6], hh[7]);
+        }
+      }
+      sync();
+#pragma unroll
+      for (int c = 0; c < DU / 4; ++c) {
+        const float4 x = reinterpret_cast<const float4*>(sCh + s * CS + u0)[c];
+        carry[4 * c] = pz.r > 0 ? x.x : 0.0f;
+        carry[4 * c + 1] = pz.r > 0 ? x.y : 0.0f;
+        carry[4 * c + 2] = pz.r > 0 ? x.z : 0.0f;
+        carry[4 * c + 3] = pz.r > 0 ? x.w : 0.0f;
+      }
     }
 #pragma unroll
     for (int u = 0; u < DU; ++u) cv[u] = cv1[u];
   }
-  if (!timed_out) wait(2);                 // the last vertical half, before TMEM is freed
+  if (!timed_out && (!XCH || owner)) wait(2);   // the last vertical half, before TMEM is freed
   asm volatile("cp.async.wait_all;\n" ::: "memory");   // copies in flight after a timeout
   tc::fence_before_sync();
   __syncthreads();
@@ -866,6 +941,18 @@ int sm_count_g() {
 
 constexpr int kReadout2Blocks = 152;
 
+template <int D, int SPLIT, int ROWS>
+cudaError_t launch_bsweep(int64_t B, const uint8_t* w1, const Sweep2Args& s, cudaStream_t st) {
+  using S = B2S<D, SPLIT, ROWS>;
+  auto k = tc2d_bsweep_kernel<D, SPLIT, ROWS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  // whole 128-sample tiles, so that every row of the weight-gradient images
+  // is written (zeros past the batch)
+  k<<<(unsigned)((B + 127) / 128 * (128 / ROWS)), 128 * SPLIT, S::kBytes, st>>>(w1, s);
+  return cudaGetLastError();
+}
+
 template <int D>
 cudaError_t run_grad(const Tc2Grad& g, const uint8_t* wimg, cudaStream_t st) {
   const int tiles = (int)((g.B + 127) / 128);
@@ -901,16 +988,13 @@ cudaError_t run_grad(const Tc2Grad& g, const uint8_t* wimg, cudaStream_t st) {
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   kt<<<(unsigned)tgrid, 128, G2S<D>::kBytes, st>>>(w1, w2, aux, s, sites_per_run, runs_per_tile);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // the sequential sweep: 16 units per thread
-  constexpr int SPLIT = D / 16;
-  auto ks = tc2d_bsweep_kernel<D, SPLIT>;
-  if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, B2S<D, SPLIT>::kBytes)) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return e;
-  }
-  ks<<<tiles, 128 * SPLIT, B2S<D, SPLIT>::kBytes, st>>>(w1, s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // the sequential sweep: 32-sample tiles (the four TMEM lane quarters split
+  // the units) while the batch leaves SMs idle, else 128-sample tiles; a
+  // pinned tile variant selects 128 (variant 0) or 32 (any other)
+  const int pin = tc1d_pinned_variant();
+  if (pin >= 0 ? pin > 0 : g.B <= 32LL * sms) e = launch_bsweep<D, (D >= 64 ? 2 : 1), 32>(g.B, w1, s, st);
+  else e = launch_bsweep<D, D / 16, 128>(g.B, w1, s, st);
+  if (e != cudaSuccess) return e;
   Wgrad2Args w{};
   w.B = g.B;
   w.Lx = g.Lx;

@@ -134,6 +134,29 @@ def test_bf16_2d_logpsi_grad(Lx, Ly, d, B, sz0):
     assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
+@pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 300), (6, 4, 64, 200)])
+def test_bf16_2d_grad_tile_rows_agree(Lx, Ly, d, B):
+    """The sequential sweep on 32-sample tiles (the TMEM lane quarters split the
+    units and exchange dh' through shared memory) and on 128-sample tiles gives
+    bitwise the same gradient: the MMA rows are independent and the exchange
+    copies FP32 values.  B is not a multiple of 128 (ragged last tile)."""
+    desc, d32, mod, pf, p = setup(Lx, Ly, d, True, seed=9, noise=0.05)
+    sig = inputs.random_configs(B, mod.N, seed=10, sz0=True)
+    w = inputs.random_weights(B, seed=11).astype(np.float32)
+    sg = dev(sig, torch.uint8)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    out = []
+    for v in (0, 1):
+        nqs.set_tile_variant(v)
+        out.append(nqs.logpsi_grad(desc, p, sg, hc, dev(w), ws=ws).clone())
+    nqs.set_tile_variant(None)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    assert torch.isfinite(out[0]).all()
+    assert torch.equal(out[0], out[1])
+
+
 def test_bf16_2d_full_size_8x8_d64_b2048():
     """Heisenberg 8 x 8 workload in BF16: energy per site of the whole step within
     1e-4 of the FP32 path on the same samples and of the oracle on 12 of them."""
