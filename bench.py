@@ -356,14 +356,15 @@ def run_gpu(args, w):
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)}
     value = world * B * args.steps / (chosen["total_ms"] * 1e-3)
     # kernels of one step (memsets excluded): 1D FP32 sample 2, E_loc 4, gradient 5;
-    # 1D BF16 sample 3, E_loc 5, gradient 8; 2D FP32 sample 2, E_loc 5, gradient 5;
-    # 2D BF16 sample 2, E_loc 7 (pack, bonds, teacher forcing, job count, jobs,
-    # chains, energies), gradient 7 (statistics, weights, pack, sweep, weight
-    # gradients, readout gradient, reduction)
+    # 1D BF16 sample 3, E_loc 5, gradient 9 (statistics, weights, three packs,
+    # tape, sweep, two reductions); 2D FP32 sample 2, E_loc 5, gradient 5;
+    # 2D BF16 sample 2, E_loc 7 (pack, bonds, cached-path tables, job count,
+    # jobs, chains, energies), gradient 8 (statistics, weights, pack, tape,
+    # sweep, weight gradients, readout gradient, reduction)
     if w["cell"] == 1:
-        launches = 16 if chosen is r16 else 11
+        launches = 17 if chosen is r16 else 11
     else:
-        launches = 16 if chosen is r16 else 12
+        launches = 17 if chosen is r16 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,
