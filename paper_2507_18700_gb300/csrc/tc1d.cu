@@ -142,15 +142,22 @@ struct Smem {
 
 // Tile threads: SPLIT threads per row, in different warps (a warp reads only
 // its own 32-lane quarter of TMEM): warp w of a tile serves rows 32 (w % 4) ..
-// + 31 and hidden units [(w / 4) D / SPLIT, (w / 4 + 1) D / SPLIT).
-template <int D, int MODE, int GROUPS, int SPLIT>
+// + 31 and hidden units [(w / 4) D / SPLIT, (w / 4 + 1) D / SPLIT).  With REP
+// = 4 (sampling / teacher forcing on 32-sample tiles) every sample's A row is
+// written into all four lane quarters (the MMA's 128 rows are computed
+// anyway), and the quarters' warps take a quarter of the units each, so the
+// MUFU-bound epilogue of a small tile runs on all four sub-partitions.
+template <int D, int MODE, int GROUPS, int SPLIT, int REP = 1>
 __global__ void __launch_bounds__(128 * GROUPS * SPLIT, 1)
 tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wimg, Tc1Args a) {
   using S = Smem<D, GROUPS, SPLIT>;
+  static_assert(REP == 1 || (REP == 4 && MODE != 2 && GROUPS == 1), "replicated rows: sampling / teacher forcing");
   constexpr int TT = 128 * SPLIT;          // threads per tile
   constexpr int NT = TT * GROUPS;
   constexpr int N4 = 4 * D, KA = S::KA;
-  constexpr int DU = D / SPLIT;            // hidden units per thread
+  constexpr int NSL = REP * SPLIT;         // unit slices per row
+  constexpr int RS = 128 / REP;            // rows per tile with REP
+  constexpr int DU = D / NSL;              // hidden units per thread
   static_assert(DU % 16 == 0, "at least 16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
@@ -181,18 +188,20 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   const uint32_t tbase = *tslot;
 
   const int g = threadIdx.x / TT, tt = threadIdx.x % TT, lane = threadIdx.x & 31;
-  const int wt = tt / 32, part = wt / 4, m = (wt % 4) * 32 + lane;
+  const int wt = tt / 32, m = (wt % 4) * 32 + lane;          // m: this thread's A row and TMEM lane
+  const int r = REP == 4 ? lane : m;                          // r: its sample row in the tile
+  const int part = REP == 4 ? (wt % 4) * SPLIT + wt / 4 : wt / 4;   // its unit slice (0: side effects)
   const int u0 = part * DU;
   // sampling / teacher forcing with 64- or 32-row tiles: warps whose 32 rows
   // lie past the tile's rows skip the A rows, the epilogue and the cache
   // stores (they still take part in every barrier)
-  const bool wact = MODE == 2 || GROUPS == 2 || (m & ~31) < a.rows;
+  const bool wact = MODE == 2 || GROUPS == 2 || REP == 4 || (m & ~31) < a.rows;
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16) + (uint32_t)(g * 256);
   const uint32_t bar_main = 1 + g, bar_x = 1 + GROUPS + g;
   uint8_t* sA = sm + S::kA + g * 128 * KA * 2;
   float* zb = zbuf + g * SPLIT * 128;
   long long* jb = jobbuf + g * 128;
-  float* stg = stage + (g * 128 + m) * S::HS + u0;   // this thread's units of the row's staged state
+  float* stg = stage + (g * 128 + r) * S::HS + u0;   // this thread's units of the row's staged state
   const float dc = img[12 * D] - img[12 * D + 1];
   const int N = a.N;
   const int64_t B = a.B;
@@ -257,8 +266,8 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     const long long j = jb[m];
     if (j >= 0) start_job(j, job_src(j));
   } else {
-    b = ((int64_t)blockIdx.x * GROUPS + g) * a.rows + m;
-    active = m < a.rows && b < B;
+    b = ((int64_t)blockIdx.x * GROUPS + g) * a.rows + r;
+    active = r < a.rows && b < B;
   }
 
   // Ping-pong (two tiles): the tiles take turns in the MUFU-bound epilogue,
@@ -288,7 +297,11 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       v.y = *reinterpret_cast<uint32_t*>(&p1);
       v.z = *reinterpret_cast<uint32_t*>(&p2);
       v.w = *reinterpret_cast<uint32_t*>(&p3);
-      if (wact) *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, u0 + 8 * kc, KA)) = v;
+      if (wact) {
+#pragma unroll
+        for (int c4 = 0; c4 < REP; ++c4)
+          *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(REP == 4 ? r + 32 * c4 : m, u0 + 8 * kc, KA)) = v;
+      }
     }
     if (part == 0 && wact) {
       // bf16 1.0 = 0x3F80: [1 | 1 | s_in == 0 | s_in == 1 | s_in == 0 | s_in == 1 | 0 0]
@@ -299,8 +312,12 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       v.y = oh;
       v.z = oh;
       v.w = 0u;
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA)) = v;
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int c4 = 0; c4 < REP; ++c4) {
+        const int row = REP == 4 ? r + 32 * c4 : m;
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, D, KA)) = v;
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, D + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -442,16 +459,16 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
         prev_idle = true;
       }
     }
-    if constexpr (SPLIT > 1) {
-      zb[part * 128 + m] = z;
+    if constexpr (NSL > 1) {
+      zb[part * RS + r] = z;
       tc::group_barrier(bar_x, TT);
-      float pz[SPLIT];
+      float pz[NSL];
 #pragma unroll
-      for (int p = 0; p < SPLIT; ++p) pz[p] = zb[p * 128 + m];
+      for (int p = 0; p < NSL; ++p) pz[p] = zb[p * RS + r];
 #pragma unroll
-      for (int w = 1; w < SPLIT; w *= 2)
+      for (int w = 1; w < NSL; w *= 2)
 #pragma unroll
-        for (int p = 0; p + w < SPLIT; p += 2 * w) pz[p] += pz[p + w];
+        for (int p = 0; p + w < NSL; p += 2 * w) pz[p] += pz[p + w];
       z = pz[0];
     }
     // ---- (f) row logic (identical in every part; side effects by part 0) ----
@@ -493,7 +510,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           reinterpret_cast<float4*>(stg)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
         __syncwarp();
         constexpr int L = DU / 4, RPI = 32 / L;   // lanes per row segment, rows per store
-        const int lr = lane / L, lq = lane % L, m0 = (wt % 4) * 32;
+        const int lr = lane / L, lq = lane % L, m0 = REP == 4 ? 0 : (wt % 4) * 32;
         const int64_t b0 = ((int64_t)blockIdx.x * GROUPS + g) * a.rows;
 #pragma unroll 4
         for (int i = 0; i < 32; i += RPI) {
@@ -539,7 +556,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
           cp_async_commit();
         }
       }
-    } else if constexpr (SPLIT > 1) {
+    } else if constexpr (NSL > 1) {
       tc::group_barrier(bar_x, TT);   // zbuf is rewritten next step
     }
     ++pstep;
@@ -1234,10 +1251,10 @@ int sm_count_tc() {
   return sms;
 }
 
-template <int D, int MODE, int GROUPS, int SPLIT>
+template <int D, int MODE, int GROUPS, int SPLIT, int REP = 1>
 cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, cudaStream_t st) {
   using S = Smem<D, GROUPS, SPLIT>;
-  auto k = tc1d_engine_kernel<D, MODE, GROUPS, SPLIT>;
+  auto k = tc1d_engine_kernel<D, MODE, GROUPS, SPLIT, REP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   int64_t grid;
@@ -1329,12 +1346,19 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
     return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
   }
   // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128, 64 or
-  // 32 rows per tile (partly filled tiles put more SMs on a small batch)
+  // 32 rows per tile (partly filled tiles put more SMs on a small batch); at
+  // d_h = 64 the 32-row tile has its A rows in all four lane quarters instead
   const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
   auto run = [&](int v) {
     Tc1Args b = a;
     b.rows = 128 >> (v / ns);
     const int sv = v % ns;
+    if constexpr (D == 64) {
+      if (v >= 2 * ns) {
+        b.rows = 32;
+        return mode == 0 ? launch_tc<D, 0, 1, 1, 4>(b, img, wimg, st) : launch_tc<D, 1, 1, 1, 4>(b, img, wimg, st);
+      }
+    }
     if (mode == 0) {
       if (sv == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
       if (sv == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
@@ -1344,7 +1368,7 @@ cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wim
     if (sv == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
     return launch_tc<D, 1, 1, 1>(b, img, wimg, st);
   };
-  return tuned_launch(mode, D, a.N, a.B, 3 * ns, run, none, st);
+  return tuned_launch(mode, D, a.N, a.B, D == 64 ? 2 * ns + 1 : 3 * ns, run, none, st);
 }
 
 }  // namespace
