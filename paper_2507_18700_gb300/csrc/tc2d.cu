@@ -184,7 +184,8 @@ struct S2 {
   static constexpr int kAux = kVS + 128 * HS * 4;          // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kCol = kAux + (D + 4) * 4;          // 128 ints: column-buffer entry of each row's new state
   static constexpr int kPos = kCol + 128 * 4;              // 128 ints: (i, j, r) of every zig-zag position
-  static constexpr int kBar = kPos + 128 * 4;              // 2 mbarriers
+  static constexpr int kZx = kPos + 128 * 4;               // 4 x 32 floats: readout partials (replicated rows)
+  static constexpr int kBar = kZx + 128 * 4;               // 2 mbarriers
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -211,12 +212,22 @@ struct Tc2Args {
   WsHeader* hdr;
 };
 
-template <int D, int MODE>
+// REP = 4 (sampling / teacher forcing of a small batch): a CTA holds 32
+// samples, every sample's A rows are written into all four TMEM lane quarters
+// (the MMAs compute 128 rows either way), and warp q takes units [16 q, 16 q
+// + 16) of every sample, so the epilogues of a small tile run on all four
+// sub-partitions; the readout partials of the four slices meet in shared
+// memory.  The readout sums 16-unit chunks in order and combines the chunks by
+// a fixed pairwise tree in every variant (and in the cached-path tables).
+template <int D, int MODE, int REP = 1>
 __global__ void __launch_bounds__(128, 1)
 tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
                    Tc2Args a) {
   using S = S2<D>;
+  static_assert(REP == 1 || (REP == 4 && MODE != 2 && D == 64), "replicated rows: sampling / teacher forcing, d_h 64");
   constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
+  constexpr int DU = D / REP;              // hidden units per thread
+  constexpr int RT = 128 / REP;            // samples per CTA
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sW1 = sm + S::kW1;
@@ -227,6 +238,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   float* sAux = reinterpret_cast<float*>(sm + S::kAux);
   int* sCol = reinterpret_cast<int*>(sm + S::kCol);
   int* sPos = reinterpret_cast<int*>(sm + S::kPos);
+  float* sZx = reinterpret_cast<float*>(sm + S::kZx);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
 
@@ -251,8 +263,10 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
   const int m = threadIdx.x, lane = m & 31, warp = m >> 5;
-  float* colrow = a.colbuf + ((int64_t)blockIdx.x * 128 + m) * a.Lx * D;   // this row's column buffer
-  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  const int r = REP == 4 ? lane : m;       // this thread's sample row in the CTA
+  const int u0 = REP == 4 ? warp * DU : 0; // its first unit
+  float* colrow = a.colbuf + ((int64_t)blockIdx.x * RT + r) * a.Lx * D;   // this row's column buffer
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);               // its TMEM lane (m)
   const int Lx = a.Lx, N = a.N;
   const int64_t B = a.B;
   const float dc = sAux[D];
@@ -264,8 +278,8 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     p.r = v >> 16;
     return p;
   };
-  float* hs = sHS + m * S::HS;       // this row's horizontal-input copy
-  float* vs = sVS + m * S::HS;       // this row's vertical-input copy
+  float* hs = sHS + r * S::HS;       // this row's horizontal-input copy
+  float* vs = sVS + r * S::HS;       // this row's vertical-input copy
 
   // row state
   int64_t b = 0;
@@ -273,7 +287,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   float acc = 0.0f, lp_next = 0.0f;
   bool active = false;
   uint64_t mask[2] = {0ull, 0ull};
-  constexpr int HW = D / 2;           // 32-bit words of a packed BF16 state
+  constexpr int HW = DU / 2;          // 32-bit words of this thread's packed BF16 units
   uint32_t hhi[HW], hlo[HW];         // the state just computed, as BF16 hi / lo pairs
 #pragma unroll
   for (int q = 0; q < HW; ++q) hhi[q] = hlo[q] = 0u;
@@ -282,7 +296,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 
   auto fetch = [&](float* dst, const float* src) {
 #pragma unroll
-    for (int q = 0; q < D / 4; ++q) cp_async16_2d(dst + 4 * q, src + 4 * q);
+    for (int q = 0; q < DU / 4; ++q) cp_async16_2d(dst + u0 + 4 * q, src + u0 + 4 * q);
   };
   // Chains: the original state of lattice site k of sample b.
   auto fetch_orig = [&](float* dst, int k) { fetch(dst, a.hcache + (b * N + k) * D); };
@@ -314,10 +328,13 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         // words go straight into the A operand's vertical-input columns
         const uint8_t* src = reinterpret_cast<const uint8_t*>(colrow + p.i * D);
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
-          cp_async16_2d(sA + tc::kmajor_offset(m, D + 8 * c, KA1), src + 16 * c);
-          cp_async16_2d(sA + tc::kmajor_offset(m, K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
-        }
+        for (int c = u0 / 8; c < u0 / 8 + DU / 8; ++c)
+#pragma unroll
+          for (int c4 = 0; c4 < REP; ++c4) {
+            const int row = REP == 4 ? r + 32 * c4 : m;
+            cp_async16_2d(sA + tc::kmajor_offset(row, D + 8 * c, KA1), src + 16 * c);
+            cp_async16_2d(sA + tc::kmajor_offset(row, K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
+          }
         vsrc = 3;
         copies = true;
       }
@@ -371,7 +388,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     pull_issue(true);
     start_job(pull_take());
   } else {
-    b = (int64_t)blockIdx.x * 128 + m;
+    b = (int64_t)blockIdx.x * RT + r;
     active = b < B;
     if (MODE == 1 && active) {
       for (int k = 0; k < N; ++k) mset(mask, k, a.sigma_in[b * N + k] ? 1 : 0);
@@ -391,30 +408,34 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
     }
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
-      const float* stg = half == 0 ? hs : vs;
-      uint8_t* dhi = sA + tc::kmajor_offset(m, half * D, KA1);
-      uint8_t* dlo = sA + tc::kmajor_offset(m, K1 + half * D, KA1);
-      if (src == 2) {
+    for (int c4 = 0; c4 < REP; ++c4) {
+      const int row = REP == 4 ? r + 32 * c4 : m;
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) st_split8(dhi + 128 * c, dlo + 128 * c, stg + 8 * c);
-      } else if (src != 3) {
+      for (int half = 0; half < 2; ++half) {
+        const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
+        const float* stg = half == 0 ? hs : vs;
+        uint8_t* dhi = sA + tc::kmajor_offset(row, half * D + u0, KA1);
+        uint8_t* dlo = sA + tc::kmajor_offset(row, K1 + half * D + u0, KA1);
+        if (src == 2) {
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
-          const bool r = src == 1;
-          *reinterpret_cast<uint4*>(dhi + 128 * c) =
-              r ? make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4*>(dlo + 128 * c) =
-              r ? make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+          for (int c = 0; c < DU / 8; ++c) st_split8(dhi + 128 * c, dlo + 128 * c, stg + u0 + 8 * c);
+        } else if (src != 3) {
+#pragma unroll
+          for (int c = 0; c < DU / 8; ++c) {
+            const bool rg = src == 1;
+            *reinterpret_cast<uint4*>(dhi + 128 * c) =
+                rg ? make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(dlo + 128 * c) =
+                rg ? make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+          }
         }
       }
-    }
-    {
-      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
-      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+      if (u0 == 0) {
+        const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+        const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+      }
     }
     // chains: a row on its last cell pulls its successor now (the loads land during the step)
     if constexpr (MODE == 2) pull_issue(active && !timed_out && t == N - 1);
@@ -447,13 +468,13 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     ph0 ^= 1;
     tc::fence_after_sync();
     // ---- (c) epilogue 1: the cell ----
-    float h[D];
+    float h[DU];
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
+    for (int c = 0; c < DU / 8; ++c) {
       uint32_t aw[8], ag[8], au[8];
-      tld8(trow + 8 * c, aw);
-      tld8(trow + D + 8 * c, ag);
-      tld8(trow + 2 * D + 8 * c, au);
+      tld8(trow + u0 + 8 * c, aw);
+      tld8(trow + D + u0 + 8 * c, ag);
+      tld8(trow + 2 * D + u0 + 8 * c, au);
       tc::tmem_wait_ld();
       tie(aw);
       tie(ag);
@@ -470,14 +491,20 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     for (int q = 0; q < HW; ++q) split_bf16(h[2 * q], h[2 * q + 1], hhi[q], hlo[q]);
     // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1: MMA1 has completed)
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, 8 * c, KA2)) =
-          make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
-      *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, K2 + 8 * c, KA2)) =
-          make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
+    for (int c4 = 0; c4 < REP; ++c4) {
+      const int row = REP == 4 ? r + 32 * c4 : m;
+#pragma unroll
+      for (int c = 0; c < DU / 8; ++c) {
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, u0 + 8 * c, KA2)) =
+            make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, K2 + u0 + 8 * c, KA2)) =
+            make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
+      }
+      if (u0 == 0) {
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(row, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
-    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -501,34 +528,60 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // at the same position).  Chains stage in hs, whose chain-start copy is
     // issued after these stores; the forward modes never copy into vs.
     {
+      // packed row: [hi words (D / 2) | lo words (D / 2)]; this thread's units
+      // are words [u0 / 2, (u0 + DU) / 2) of each half
       float* pst = MODE == 2 ? hs : vs;
 #pragma unroll
       for (int q = 0; q < HW / 4; ++q) {
-        reinterpret_cast<uint4*>(pst)[q] = make_uint4(hhi[4 * q], hhi[4 * q + 1], hhi[4 * q + 2], hhi[4 * q + 3]);
-        reinterpret_cast<uint4*>(pst)[HW / 4 + q] = make_uint4(hlo[4 * q], hlo[4 * q + 1], hlo[4 * q + 2], hlo[4 * q + 3]);
+        reinterpret_cast<uint4*>(pst + u0 / 2)[q] = make_uint4(hhi[4 * q], hhi[4 * q + 1], hhi[4 * q + 2], hhi[4 * q + 3]);
+        reinterpret_cast<uint4*>(pst + D / 2 + u0 / 2)[q] =
+            make_uint4(hlo[4 * q], hlo[4 * q + 1], hlo[4 * q + 2], hlo[4 * q + 3]);
       }
       if constexpr (MODE != 2) {
 #pragma unroll
-        for (int q = 0; q < D / 4; ++q)
-          reinterpret_cast<float4*>(hs)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        for (int q = 0; q < DU / 4; ++q)
+          reinterpret_cast<float4*>(hs + u0)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
       }
-      sCol[m] = active ? P(t).i : -1;
+      sCol[r] = active ? P(t).i : -1;     // (REP: every slice writes the same value for its own lanes)
       __syncwarp();
-      constexpr int L = D / 4, RPI = 32 / L;
-      const int lr = lane / L, lq = lane % L;
       const int kc = MODE != 2 ? P(step).j * Lx + P(step).i : 0;
       const float* pbase = MODE == 2 ? sHS : sVS;
+      if constexpr (REP == 1) {
+        constexpr int L = D / 4, RPI = 32 / L;
+        const int lr = lane / L, lq = lane % L;
 #pragma unroll 4
-      for (int i = 0; i < 32; i += RPI) {
-        const int mr = warp * 32 + i + lr;
-        const int ci = sCol[mr];
-        if (ci >= 0) {
-          const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
-          reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] =
-              reinterpret_cast<const float4*>(pbase + mr * S::HS)[lq];
-          if (MODE != 2 && a.hcache)
-            reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] =
-                reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
+        for (int i = 0; i < 32; i += RPI) {
+          const int mr = warp * 32 + i + lr;
+          const int ci = sCol[mr];
+          if (ci >= 0) {
+            const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
+            reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] =
+                reinterpret_cast<const float4*>(pbase + mr * S::HS)[lq];
+            if (MODE != 2 && a.hcache)
+              reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] =
+                  reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
+          }
+        }
+      } else {
+        // this warp's slice of all 32 rows: 2 + 2 packed and 4 FP32 pieces
+        // of 16 bytes per row, four rows per pass
+        const int lr = lane / 8, lq = lane % 8;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) {
+          const int mr = i + lr;
+          const int ci = sCol[mr];
+          if (ci >= 0) {
+            const int64_t slot = (int64_t)blockIdx.x * RT + mr;
+            if (lq < 4) {
+              const int off = (lq < 2 ? u0 / 2 : D / 2 + u0 / 2) + 4 * (lq & 1);
+              *reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D + off) =
+                  *reinterpret_cast<const float4*>(pbase + mr * S::HS + off);
+            } else if (a.hcache) {
+              const int off = u0 + 4 * (lq - 4);
+              *reinterpret_cast<float4*>(a.hcache + (slot * N + kc) * D + off) =
+                  *reinterpret_cast<const float4*>(sHS + mr * S::HS + off);
+            }
+          }
         }
       }
       __syncwarp();
@@ -539,21 +592,34 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     ph1 ^= 1;
     tc::fence_after_sync();
-    // ---- (e) epilogue 2: GLU and the logit difference ----
-    float z = 0.0f;
+    // ---- (e) epilogue 2: GLU and the logit difference (16-unit chunks in
+    // order, chunks by a fixed pairwise tree) ----
+    float zc[DU / 16];
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
+    for (int c = 0; c < DU / 16; ++c) zc[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < DU / 8; ++c) {
       uint32_t a1[8], a2[8];
-      tld8(trow + 8 * c, a1);
-      tld8(trow + D + 8 * c, a2);
+      tld8(trow + u0 + 8 * c, a1);
+      tld8(trow + D + u0 + 8 * c, a2);
       tc::tmem_wait_ld();
       tie(a1);
       tie(a2);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-        z = fmaf(sAux[8 * c + q], y, z);
+        zc[c / 2] = fmaf(sAux[u0 + 8 * c + q], y, zc[c / 2]);
       }
+    }
+#pragma unroll
+    for (int w = 1; w < DU / 16; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
+    float z = zc[0];
+    if constexpr (REP == 4) {
+      sZx[warp * 32 + r] = z;
+      __syncthreads();
+      z = (sZx[r] + sZx[32 + r]) + (sZx[64 + r] + sZx[96 + r]);
     }
     // ---- (f) row logic ----
     bool fin = false;
@@ -566,7 +632,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         const bool fdn = a.sz0 && n_up >= (N >> 1);
         const bool fup = a.sz0 && (t - n_up) >= (N >> 1);
         s = fdn ? 1 : fup ? 0 : (uni < sigmoid_acc(d) ? 0 : 1);
-        a.sigma_out[b * N + k] = (uint8_t)s;
+        if (u0 == 0) a.sigma_out[b * N + k] = (uint8_t)s;
         mset(mask, k, s);
       } else {
         s = mbit(mask, k);
@@ -584,7 +650,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
           a.delta[(int64_t)b * a.nb + rank] = acc;
         } else {
           const float lpsi = 0.5f * acc;
-          if (a.logpsi) a.logpsi[b] = lpsi;
+          if (a.logpsi && u0 == 0) a.logpsi[b] = lpsi;
           if (!isfinite(lpsi)) flag_status(a.hdr, NQS_ENONFINITE);
           active = false;
         }
@@ -707,7 +773,10 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
     if (!ok) flag_status(a.hdr, NQS_ETIMEOUT);
     ph ^= 1;
     tc::fence_after_sync();
-    float z = 0.0f;
+    // the engine's readout order: 16-unit chunks in order, chunks by a fixed pairwise tree
+    float zc[D / 16];
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) zc[c] = 0.0f;
 #pragma unroll
     for (int c = 0; c < D / 8; ++c) {
       uint32_t a1[8], a2[8];
@@ -719,9 +788,14 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-        z = fmaf(sAux[8 * c + q], y, z);
+        zc[c / 2] = fmaf(sAux[8 * c + q], y, zc[c / 2]);
       }
     }
+#pragma unroll
+    for (int w = 1; w < D / 16; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < D / 16; c += 2 * w) zc[c] += zc[c + w];
+    const float z = zc[0];
     if (valid) {
       const float d = z + dc;
       a.lp_tab[(b * N + t) * 2] = lp_masked(0, d, n_up, t, N, a.sz0 != 0);
@@ -753,16 +827,26 @@ int sm_count_2d() {
   return sms;
 }
 
-template <int D, int MODE>
+template <int D, int MODE, int REP = 1>
 cudaError_t launch2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
   using S = S2<D>;
-  auto k = tc2d_engine_kernel<D, MODE>;
+  auto k = tc2d_engine_kernel<D, MODE, REP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  const int64_t grid = MODE == 2 ? sm_count_2d() : (a.B + 127) / 128;
+  const int64_t grid = MODE == 2 ? sm_count_2d() : (a.B + 128 / REP - 1) / (128 / REP);
   if (grid < 1) return cudaSuccess;
   k<<<(unsigned)grid, 128, S::kBytes, st>>>(w1, w2, aux, a);
   return cudaGetLastError();
+}
+
+// Sampling / teacher forcing at d_h = 64: 32-sample CTAs with replicated A
+// rows while 128-sample tiles would leave SMs idle; a pinned tile variant
+// selects 128 (variant 0) or 32 (any other).
+template <int MODE>
+cudaError_t launch2_fwd64(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
+  const int pin = tc1d_pinned_variant();
+  if (pin >= 0 ? pin > 0 : a.B <= 32LL * sm_count_2d()) return launch2<64, MODE, 4>(a, w1, w2, aux, st);
+  return launch2<64, MODE, 1>(a, w1, w2, aux, st);
 }
 
 }  // namespace
@@ -814,7 +898,7 @@ cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sampl
   const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
   switch (D) {
     case 32: return sample ? launch2<32, 0>(a, w1, w2, aux, st) : launch2<32, 1>(a, w1, w2, aux, st);
-    case 64: return sample ? launch2<64, 0>(a, w1, w2, aux, st) : launch2<64, 1>(a, w1, w2, aux, st);
+    case 64: return sample ? launch2_fwd64<0>(a, w1, w2, aux, st) : launch2_fwd64<1>(a, w1, w2, aux, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -268,8 +268,10 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
         tc::mma_commit(&mbar[0]);
       }
       wait(0);
-      // ---- GLU forward: the logit difference and dz ----
-      float z = 0.0f;
+      // ---- GLU forward: the logit difference (the engine's readout order) and dz ----
+      float zc[D / 16];
+#pragma unroll
+      for (int c = 0; c < D / 16; ++c) zc[c] = 0.0f;
 #pragma unroll
       for (int c = 0; c < D / 8; ++c) {
         uint32_t a1[8], a2[8];
@@ -280,8 +282,14 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
         tie(a2);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          z = fmaf(sAux[8 * c + q], __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f), z);
+          zc[c / 2] = fmaf(sAux[8 * c + q],
+                           __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f), zc[c / 2]);
       }
+#pragma unroll
+      for (int w = 1; w < D / 16; w *= 2)
+#pragma unroll
+        for (int c = 0; c + w < D / 16; c += 2 * w) zc[c] += zc[c + w];
+      const float z = zc[0];
       const bool forced = a.sz0 && (n_up >= (N >> 1) || (t - n_up) >= (N >> 1));
       const float dz = (forced || !valid) ? 0.0f : coef * ((s_k == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc));
       n_up += (s_k == 0);

@@ -134,6 +134,27 @@ def test_bf16_2d_logpsi_grad(Lx, Ly, d, B, sz0):
     assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
+@pytest.mark.parametrize("Lx,Ly,B", [(8, 8, 300), (6, 4, 77)])
+def test_bf16_2d_forward_tile_rows_agree(Lx, Ly, B):
+    """Sampling and teacher forcing at d_h = 64 on 32-sample CTAs (every A row
+    in all four TMEM lane quarters, the units split over the quarters' warps)
+    and on 128-sample CTAs give bitwise the same samples, log psi and cache:
+    the readout sums 16-unit chunks in order and the chunks by a fixed tree in
+    both.  B is not a multiple of 32 (ragged last CTA)."""
+    desc, _, mod, pf, p = setup(Lx, Ly, 64, True, seed=12)
+    out = []
+    for v in (0, 1):
+        nqs.set_tile_variant(v)
+        s, lp, hc = nqs.sample(desc, p, B, seed=4, step=3)
+        lp_t, hc_t = nqs.logpsi(desc, p, s)
+        out.append((s.clone(), lp.clone(), hc.clone(), lp_t.clone(), hc_t.clone()))
+    nqs.set_tile_variant(None)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out[0][1]).all()
+    for x, y in zip(out[0], out[1]):
+        assert torch.equal(x, y)
+
+
 @pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 300), (6, 4, 64, 200)])
 def test_bf16_2d_grad_tile_rows_agree(Lx, Ly, d, B):
     """The sequential sweep on 32-sample tiles (the TMEM lane quarters split the
