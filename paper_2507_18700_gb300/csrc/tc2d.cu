@@ -184,8 +184,9 @@ struct S2 {
   static constexpr int kAux = kVS + 128 * HS * 4;          // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kCol = kAux + (D + 4) * 4;          // 128 ints: column-buffer entry of each row's new state
   static constexpr int kPos = kCol + 128 * 4;              // 128 ints: (i, j, r) of every zig-zag position
-  static constexpr int kZx = kPos + 128 * 4;               // 4 x 32 floats: readout partials (replicated rows)
-  static constexpr int kBar = kZx + 128 * 4;               // 2 mbarriers
+  static constexpr int kZx = kPos + 128 * 4;               // 512 floats: readout partials of the unit slices
+  static constexpr int kJob = kZx + 512 * 4;               // 128 long long: chain job of each row (split rows)
+  static constexpr int kBar = kJob + 128 * 8;              // 2 mbarriers
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -216,18 +217,23 @@ struct Tc2Args {
 // samples, every sample's A rows are written into all four TMEM lane quarters
 // (the MMAs compute 128 rows either way), and warp q takes units [16 q, 16 q
 // + 16) of every sample, so the epilogues of a small tile run on all four
-// sub-partitions; the readout partials of the four slices meet in shared
-// memory.  The readout sums 16-unit chunks in order and combines the chunks by
-// a fixed pairwise tree in every variant (and in the cached-path tables).
-template <int D, int MODE, int REP = 1>
-__global__ void __launch_bounds__(128, 1)
+// sub-partitions.  SPLIT > 1 (128 rows): SPLIT warps per lane quarter split a
+// row's units; part 0 pulls the chain jobs and publishes them in shared
+// memory.  The readout partials of the unit slices meet in shared memory; the
+// readout sums 16-unit chunks in order and combines the chunks by a fixed
+// pairwise tree in every variant (and in the cached-path tables).
+template <int D, int MODE, int REP = 1, int SPLIT = 1>
+__global__ void __launch_bounds__(128 * SPLIT, 1)
 tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
                    Tc2Args a) {
   using S = S2<D>;
-  static_assert(REP == 1 || (REP == 4 && MODE != 2 && D == 64), "replicated rows: sampling / teacher forcing, d_h 64");
+  static_assert(REP == 1 || (REP == 4 && MODE != 2 && D == 64 && SPLIT == 1), "replicated rows: sampling / teacher forcing, d_h 64");
   constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
-  constexpr int DU = D / REP;              // hidden units per thread
-  constexpr int RT = 128 / REP;            // samples per CTA
+  constexpr int NT = 128 * SPLIT;          // threads
+  constexpr int NSL = REP * SPLIT;         // unit slices per row
+  constexpr int DU = D / NSL;              // hidden units per thread
+  constexpr int RT = 128 / REP;            // samples (rows) per CTA
+  static_assert(DU >= 16 && DU % 16 == 0, "16-unit readout chunks");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   uint8_t* sW1 = sm + S::kW1;
@@ -242,12 +248,13 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
 
-  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += 128)
+  long long* jbuf = reinterpret_cast<long long*>(sm + S::kJob);
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
-  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 128)
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
-  for (int i = threadIdx.x; i < D + 1; i += 128) sAux[i] = aux[i];
-  for (int t = threadIdx.x; t < a.N; t += 128) {
+  for (int i = threadIdx.x; i < D + 1; i += NT) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += NT) {
     const Pz p = zpos(t, a.Lx);
     sPos[t] = p.i | (p.j << 8) | (p.r << 16);
   }
@@ -262,9 +269,11 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const int m = threadIdx.x, lane = m & 31, warp = m >> 5;
-  const int r = REP == 4 ? lane : m;       // this thread's sample row in the CTA
-  const int u0 = REP == 4 ? warp * DU : 0; // its first unit
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, part = warp / 4;
+  const int m = (warp % 4) * 32 + lane;    // this thread's A row and TMEM lane
+  const int r = REP == 4 ? lane : m;       // its sample row in the CTA
+  const int u0 = (REP == 4 ? warp : part) * DU;   // its first unit
+  constexpr uint32_t kBarPub = 2;          // named barrier: chain jobs published
   float* colrow = a.colbuf + ((int64_t)blockIdx.x * RT + r) * a.Lx * D;   // this row's column buffer
   const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);               // its TMEM lane (m)
   const int Lx = a.Lx, N = a.N;
@@ -385,8 +394,18 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 
   unsigned long long jpend = ~0ull;
   if constexpr (MODE == 2) {
-    pull_issue(true);
-    start_job(pull_take());
+    if constexpr (SPLIT == 1) {
+      pull_issue(true);
+      start_job(pull_take());
+    } else {
+      // part 0 pulls one job per row and publishes it to the row's other parts
+      if (part == 0) {
+        pull_issue(true);
+        jbuf[m] = (long long)pull_take();
+      }
+      tc::group_barrier(kBarPub, NT);
+      start_job((unsigned long long)jbuf[m]);
+    }
   } else {
     b = (int64_t)blockIdx.x * RT + r;
     active = b < B;
@@ -438,14 +457,16 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
     }
     // chains: a row on its last cell pulls its successor now (the loads land during the step)
-    if constexpr (MODE == 2) pull_issue(active && !timed_out && t == N - 1);
+    if constexpr (MODE == 2) {
+      if (SPLIT == 1 || part == 0) pull_issue(active && !timed_out && t == N - 1);
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
-    const bool any = tc::group_barrier_or(active && !timed_out, 1, 128);
+    const bool any = tc::group_barrier_or(active && !timed_out, 1, NT);
     if (!any) break;
     tc::fence_after_sync();
     // ---- (b) MMA1 ----
-    if (m == 0) {
+    if (threadIdx.x == 0) {
       // A column chunk c pairs with W1 chunk c (hi and extras) or c - K1/16 (lo)
       constexpr uint32_t idesc = tc::make_idesc_bf16(128, 3 * D);
 #pragma unroll
@@ -510,7 +531,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     __syncthreads();
     tc::fence_after_sync();
     // ---- (d) MMA2 (the GLU) ----
-    if (m == 0) {
+    if (threadIdx.x == 0) {
       constexpr uint32_t idesc = tc::make_idesc_bf16(128, 2 * D);
 #pragma unroll
       for (int c = 0; c < KA2 / 16; ++c) {
@@ -546,7 +567,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       __syncwarp();
       const int kc = MODE != 2 ? P(step).j * Lx + P(step).i : 0;
       const float* pbase = MODE == 2 ? sHS : sVS;
-      if constexpr (REP == 1) {
+      if constexpr (NSL == 1) {
         constexpr int L = D / 4, RPI = 32 / L;
         const int lr = lane / L, lq = lane % L;
 #pragma unroll 4
@@ -563,21 +584,23 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
           }
         }
       } else {
-        // this warp's slice of all 32 rows: 2 + 2 packed and 4 FP32 pieces
-        // of 16 bytes per row, four rows per pass
-        const int lr = lane / 8, lq = lane % 8;
-#pragma unroll
-        for (int i = 0; i < 32; i += 4) {
-          const int mr = i + lr;
+        // this warp's unit slice of its 32 rows (all 32 samples with REP):
+        // DU / 8 packed hi, DU / 8 packed lo and (forward modes) DU / 4 FP32
+        // pieces of 16 bytes per row
+        constexpr int PH = DU / 8, PF = MODE != 2 ? DU / 4 : 0, PPR = 2 * PH + PF;
+        const int m0 = REP == 4 ? 0 : (warp % 4) * 32;
+#pragma unroll 4
+        for (int idx = lane; idx < 32 * PPR; idx += 32) {
+          const int mr = m0 + idx / PPR, pc = idx % PPR;
           const int ci = sCol[mr];
           if (ci >= 0) {
             const int64_t slot = (int64_t)blockIdx.x * RT + mr;
-            if (lq < 4) {
-              const int off = (lq < 2 ? u0 / 2 : D / 2 + u0 / 2) + 4 * (lq & 1);
+            if (pc < 2 * PH) {
+              const int off = (pc < PH ? u0 / 2 : D / 2 + u0 / 2) + 4 * (pc % PH);
               *reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D + off) =
                   *reinterpret_cast<const float4*>(pbase + mr * S::HS + off);
-            } else if (a.hcache) {
-              const int off = u0 + 4 * (lq - 4);
+            } else if (MODE != 2 && a.hcache) {
+              const int off = u0 + 4 * (pc - 2 * PH);
               *reinterpret_cast<float4*>(a.hcache + (slot * N + kc) * D + off) =
                   *reinterpret_cast<const float4*>(sHS + mr * S::HS + off);
             }
@@ -620,6 +643,17 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       sZx[warp * 32 + r] = z;
       __syncthreads();
       z = (sZx[r] + sZx[32 + r]) + (sZx[64 + r] + sZx[96 + r]);
+    } else if constexpr (SPLIT > 1) {
+      sZx[part * 128 + m] = z;
+      __syncthreads();
+      float pz[SPLIT];
+#pragma unroll
+      for (int q = 0; q < SPLIT; ++q) pz[q] = sZx[q * 128 + m];
+#pragma unroll
+      for (int w = 1; w < SPLIT; w *= 2)
+#pragma unroll
+        for (int q = 0; q + w < SPLIT; q += 2 * w) pz[q] += pz[q + w];
+      z = pz[0];
     }
     // ---- (f) row logic ----
     bool fin = false;
@@ -647,7 +681,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       if (++t == N) {
         fin = true;
         if constexpr (MODE == 2) {
-          a.delta[(int64_t)b * a.nb + rank] = acc;
+          if (u0 == 0) a.delta[(int64_t)b * a.nb + rank] = acc;
         } else {
           const float lpsi = 0.5f * acc;
           if (a.logpsi && u0 == 0) a.logpsi[b] = lpsi;
@@ -659,8 +693,14 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
     }
     if constexpr (MODE == 2) {
-      jpend = pull_take();
-      if (fin) start_job(jpend);
+      if constexpr (SPLIT == 1) {
+        jpend = pull_take();
+        if (fin) start_job(jpend);
+      } else {
+        if (part == 0) jbuf[m] = (long long)pull_take();
+        tc::group_barrier(kBarPub, NT);
+        if (fin) start_job((unsigned long long)jbuf[m]);
+      }
     }
   }
   cp_wait_2d();
@@ -827,15 +867,15 @@ int sm_count_2d() {
   return sms;
 }
 
-template <int D, int MODE, int REP = 1>
+template <int D, int MODE, int REP = 1, int SPLIT = 1>
 cudaError_t launch2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
   using S = S2<D>;
-  auto k = tc2d_engine_kernel<D, MODE, REP>;
+  auto k = tc2d_engine_kernel<D, MODE, REP, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int64_t grid = MODE == 2 ? sm_count_2d() : (a.B + 128 / REP - 1) / (128 / REP);
   if (grid < 1) return cudaSuccess;
-  k<<<(unsigned)grid, 128, S::kBytes, st>>>(w1, w2, aux, a);
+  k<<<(unsigned)grid, 128 * SPLIT, S::kBytes, st>>>(w1, w2, aux, a);
   return cudaGetLastError();
 }
 
@@ -966,8 +1006,15 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
   const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
   switch (D) {
-    case 32: return launch2<32, 2>(a, w1, w2, aux, st);
-    case 64: return launch2<64, 2>(a, w1, w2, aux, st);
+    // one thread per row (measured faster at 8 x 8, d_h = 64: 1.19 ms per
+    // launch against 1.33 ms with four threads per row, whose extra barriers
+    // and job publishing outweigh the shorter epilogues); a pinned tile
+    // variant >= 1 selects 16 units per thread (2 threads per row at d_h =
+    // 32, 4 at 64)
+    case 32:
+      return tc1d_pinned_variant() >= 1 ? launch2<32, 2, 1, 2>(a, w1, w2, aux, st) : launch2<32, 2>(a, w1, w2, aux, st);
+    case 64:
+      return tc1d_pinned_variant() >= 1 ? launch2<64, 2, 1, 4>(a, w1, w2, aux, st) : launch2<64, 2>(a, w1, w2, aux, st);
   }
   return cudaErrorInvalidValue;
 }
