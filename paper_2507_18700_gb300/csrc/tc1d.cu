@@ -1,17 +1,27 @@
 // BF16 tensor-core path of the 1D GRU wave function (App. A) for sm_103a:
-// sampling, teacher-forced log psi and the prefix-cached TFIM chains, with the
-// gate GEMM h x [W_g | W_r | W_h] on tcgen05 (BF16 operands, FP32 accumulate
-// in TMEM) and the FP32 recurrent state in registers.
+// sampling, teacher-forced log psi, the prefix-cached TFIM chains and the
+// reverse sweep, with the gate GEMM [h | 1 | onehot(s)] x W^T on tcgen05 (BF16
+// operands, FP32 accumulate in TMEM; biases and one-hot weights folded into
+// 16 extra K columns as BF16 hi / lo pairs) and the FP32 recurrent state in
+// registers.
 //
-// A CTA runs GROUPS independent tiles of 128 rows; tile g uses warps 4g..4g+3,
-// one thread per row (= TMEM lane), and TMEM columns [256 g, 256 g + 3D).  Per
-// cell step a tile: writes its rows' h (BF16) into its A operand in shared
-// memory; one thread issues D/16 MMAs (M = 128, N = 3D, K = 16) against the
-// weight operand kept in shared memory and commits them to the tile's
-// mbarrier; after the wait every thread reads its row's 3D accumulators from
+// Engine (tc1d_engine_kernel): a CTA runs GROUPS tiles of 128 TMEM lanes;
+// tile g uses warps 4g.. with SPLIT threads per row (a warp reads only its own
+// 32-lane quarter of TMEM).  Per cell step a tile writes its rows' h (BF16)
+// into its A operand in shared memory; one thread issues (D + 16) / 16 MMAs
+// (M = 128, N = 4D = the u / r / q / x_in pre-activations, K = 16) against
+// the weight operand kept in shared memory and commits them to the tile's
+// mbarrier; after the wait every thread reads its row's accumulators from
 // TMEM, applies the gates, updates h in FP32 and the readout, and runs the
-// row logic (draw / teacher forcing / chain bookkeeping).  Two tiles per CTA
-// let one tile's MMA overlap the other tile's epilogue.
+// row logic (draw / teacher forcing / chain bookkeeping).  Chains ping-pong
+// two tiles per CTA, so one tile's MMA and row logic run under the other's
+// MUFU-bound epilogue; sampling and teacher forcing of a small batch use 64-
+// or 32-row tiles, at d_h = 64 with each A row in all four lane quarters.
+//
+// Reverse sweep: a parallel tape kernel (the carry-independent factors of the
+// cell backward) and a sequential kernel (MMA_b, MMA_w and the carries);
+// their comment block below gives the details.  The autotuner at the end
+// picks the tile variant of each kernel per shape.
 #include <map>
 #include <mutex>
 #include <tuple>
