@@ -269,14 +269,19 @@ void nqs_set_autotune(int on);
 /* Pin the tile variant of every tensor-core kernel: variant >= 0 selects
  * that variant (a kernel with fewer variants takes its last one), bypassing
  * the autotuner and its cache; variant < 0 returns to normal selection.
- * Variants differ in threads per row (1, 2, 4) and, for sampling, teacher
- * forcing and the reverse sweep, in rows per 128-lane tile (128, or 64 or 32
- * to put more SMs on a small batch; the 2D reverse sweep takes 128 rows for
- * variant 0 and 32 for any other).  Per-sample results (samples, log psi, cache,
+ * 1D: variants differ in threads per row (1, 2, 4) and, for sampling,
+ * teacher forcing and the reverse sweep, in rows per 128-lane tile (128, or
+ * 64 or 32 to put more SMs on a small batch; at d_h = 64 the 32-row sampling
+ * / teacher-forcing tile writes each A row into all four lane quarters).
+ * 2D (d_h 64 where noted): variant 0 selects 128-sample tiles with one
+ * thread per row everywhere; any other variant selects 32-sample tiles with
+ * replicated A rows for sampling / teacher forcing (d_h 64), 32-sample tiles
+ * for the sequential reverse sweep, and 16 units per thread (2 or 4 threads
+ * per row) for the chains.  Per-sample results (samples, log psi, cache,
  * local energies) are bitwise the same in every variant; the gradient, a sum
  * over samples grouped by tile, is bitwise the same for the same rows per tile
- * and equal to rounding otherwise.  This is for timing and testing them one
- * by one. */
+ * and equal to rounding otherwise (2D: bitwise the same).  This is for timing
+ * and testing them one by one. */
 void nqs_set_tile_variant(int variant);
 
 /* Copy the workspace status word to *device_status (an nqs_status) after
