@@ -258,3 +258,64 @@ def test_growth_with_zero_noise_keeps_the_wave_function(cell, Lx, Ly, sz0):
     new = np.abs(pe - pb)
     assert np.count_nonzero(new) == big.param_count() - small.param_count()
     assert abs(new[new > 0].mean() - 1e-3 * np.sqrt(2 / np.pi)) < 2e-4
+
+
+# ------------------------------------ sample estimator of the gradient ----
+def test_vmc_weights_hand_computed():
+    """Three local energies 1, 2, 6: mean 3, w = 2 (E - 3) / 3 = (-4/3, -2/3, 2)."""
+    np.testing.assert_allclose(vmc.vmc_weights([1.0, 2.0, 6.0]), [-4.0 / 3, -2.0 / 3, 2.0],
+                               rtol=0, atol=1e-15)
+
+
+def _estimator_setup():
+    N, d, Gamma = 6, 3, 0.7
+    mod = M.Model(M.GRU1D, N, d_h=d)
+    flat = inputs.xavier_params(1, d, seed=21, noise_std=0.6)
+    configs = exact.all_configs(N)
+    el_all = hamiltonian.tfim_local_energy(N, 1.0, Gamma, configs, _lp_fn(mod, flat))
+    return mod, flat, configs, el_all, exact.tfim_hamiltonian(N, 1.0, Gamma)
+
+
+def test_vmc_gradient_is_unbiased_for_fd_of_exact_energy():
+    """The sample estimator g = (2/M) sum_s (E_s - mean) d log psi_s, on M = 2e5
+    exact autoregressive samples, equals the central finite difference of the
+    exact energy <psi|H|psi> (dense H) within 4 standard errors per component.
+    A dropped factor 2 or a sign error fails by many standard errors (checked)."""
+    mod, flat, configs, el_all, Hm = _estimator_setup()
+    Msamp = 200_000
+    u = philox.sampling_uniforms(seed=5, step=0, B=Msamp, N=mod.N)
+    sig = M.sample(mod, flat, u)["sigma"]
+    idx = exact.basis_index(sig)
+    eloc = el_all[idx]
+    g = vmc.vmc_gradient(mod, flat, sig, eloc)
+
+    def energy(x):
+        psi = np.exp(M.logpsi(mod, x, configs))
+        return psi @ (Hm @ psi)
+
+    fd = exact.central_fd(energy, flat, h=1e-5)
+    # per-sample contributions 2 (E_s - mean) d log psi(sigma_s) for the standard error
+    jac = np.stack([vmc.logpsi_grad(mod, flat, configs[k:k + 1], np.ones(1))
+                    for k in range(configs.shape[0])])
+    contrib = 2.0 * (eloc - eloc.mean())[:, None] * jac[idx]
+    np.testing.assert_allclose(contrib.mean(axis=0), g, rtol=1e-9, atol=1e-12)
+    se = contrib.std(axis=0) / np.sqrt(Msamp) + 1e-12
+    z = np.abs(g - fd) / se
+    assert z.max() < 4.0, z.max()
+    # the test has power: half the estimator, or its negative, is far outside
+    assert (np.abs(0.5 * g - fd) / se).max() > 20.0
+    assert (np.abs(-g - fd) / se).max() > 20.0
+
+
+def test_vmc_gradient_is_invariant_to_an_energy_shift():
+    """Adding a constant to H adds it to every E_loc and leaves dE/dtheta unchanged;
+    the mean subtraction makes the sample estimator invariant exactly (up to
+    rounding), which an estimator without the centring is not (checked)."""
+    mod, flat, configs, el_all, _ = _estimator_setup()
+    sig = inputs.random_configs(64, mod.N, seed=22).astype(np.int64)
+    eloc = el_all[exact.basis_index(sig)]
+    g0 = vmc.vmc_gradient(mod, flat, sig, eloc)
+    g1 = vmc.vmc_gradient(mod, flat, sig, eloc + 17.25)
+    np.testing.assert_allclose(g1, g0, rtol=1e-10, atol=1e-12)
+    raw = lambda e: vmc.logpsi_grad(mod, flat, sig, 2.0 * np.asarray(e) / len(e))
+    assert np.abs(raw(eloc + 17.25) - raw(eloc)).max() > 1e-2
