@@ -17,6 +17,7 @@ import torch
 
 from oracle import hamiltonian as oh, model as om, philox, vmc as ov
 from paper_2507_18700_gb300 import inputs, nqs
+from _draws import check_draws
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -48,6 +49,9 @@ def compare_samples(mod, pf, sig_gpu, seed, step):
     assert near.mean() <= 1e-4
     clean = ~near.any(axis=1)
     assert np.array_equal(sig_gpu[clean], ref["sigma"][clean])
+    # every draw along the GPU's own path (the oracle teacher-forced on it)
+    frac, _ = check_draws(mod, pf, sig_gpu, u, 1e-6)
+    assert frac <= 1e-4
     return ref
 
 
