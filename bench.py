@@ -223,28 +223,27 @@ def run_gpu(args, w):
     P = params.numel()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     st = torch.cuda.current_stream()
-    step_seed = 1000 + rank
+    step_seed = 1000          # one Philox stream; rank r draws global samples r*B .. r*B + B - 1
+    offset = vdist.sample_offset(B)
 
     def events():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def vmc_grad(desc, sigma, hc, eloc, ws, p=None):
         """The step's gradient: one rank, nqs_vmc_grad; several ranks, the
-        global energy statistics, globally centred weights and the summed
-        gradient (two all-reduces of small tensors, inside the timed step)."""
+        library's energy sums and gradient share with an all-reduce of each
+        (3 and P doubles, inside the timed step)."""
         p = params if p is None else p
         if world == 1:
             return nqs.vmc_grad(desc, p, sigma, hc, eloc, ws=ws)
-        stats = vdist.global_energy_stats(eloc)
-        g = nqs.logpsi_grad(desc, p, sigma, hc, vdist.vmc_weights(eloc, stats), ws=ws)
-        return vdist.allreduce_grad(g), stats
+        return vdist.global_gradient(desc, p, sigma, hc, eloc, ws=ws)
 
     def measure(precision):
         """Time args.steps VMC steps at one precision (after args.warmup untimed ones)."""
         desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=precision)
         ws = nqs.Workspace(dev)
         for k in range(args.warmup):
-            s_, _, h_ = nqs.sample(desc, params, B, seed=step_seed, step=k, ws=ws)
+            s_, _, h_ = nqs.sample(desc, params, B, seed=step_seed, step=k, ws=ws, sample_offset=offset)
             e_ = nqs.local_energy(desc, params, ham, s_, h_, ws=ws)
             vmc_grad(desc, s_, h_, e_, ws)
         torch.cuda.synchronize()
@@ -259,7 +258,8 @@ def run_gpu(args, w):
             la, lb = events()
             torch.cuda.synchronize()
             a.record(st)
-            sigma, lp, hc = nqs.sample(desc, params, B, seed=step_seed, step=args.warmup + k, ws=ws)
+            sigma, lp, hc = nqs.sample(desc, params, B, seed=step_seed, step=args.warmup + k, ws=ws,
+                                         sample_offset=offset)
             la.record(st)
             eloc = nqs.local_energy(desc, params, ham, sigma, hc, ws=ws)
             lb.record(st)
@@ -277,7 +277,8 @@ def run_gpu(args, w):
             total_ms = float(t.item())
         # end to end through the public API with host buffers: params in, grad + stats out
         host_p = torch.from_numpy(flat).pin_memory()
-        host_g = torch.empty(P, dtype=torch.float32).pin_memory()
+        gdt = torch.float32 if world == 1 else torch.float64    # several ranks: the FP64 all-reduced gradient
+        host_g = torch.empty(P, dtype=gdt).pin_memory()
         host_s = torch.empty(3, dtype=torch.float64).pin_memory()
         dev_p = torch.empty_like(params)
         e2e_ms = []
@@ -287,7 +288,7 @@ def run_gpu(args, w):
             torch.cuda.synchronize()
             a.record(st)
             dev_p.copy_(host_p, non_blocking=True)
-            s_, _, h_ = nqs.sample(desc, dev_p, B, seed=step_seed, step=10_000 + k, ws=ws)
+            s_, _, h_ = nqs.sample(desc, dev_p, B, seed=step_seed, step=10_000 + k, ws=ws, sample_offset=offset)
             e_ = nqs.local_energy(desc, dev_p, ham, s_, h_, ws=ws)
             g_, st_ = vmc_grad(desc, s_, h_, e_, ws, dev_p)
             host_g.copy_(g_, non_blocking=True)
@@ -385,7 +386,7 @@ def run_gpu(args, w):
                    "device_status": chosen["status"]},
         "roofline": roof,
         "e2e": {"value": world * B * args.steps / (chosen["e2e_ms"] * 1e-3), "unit": "samples/s",
-                "h2d_bytes_per_step": P * 4, "d2h_bytes_per_step": P * 4 + 24},
+                "h2d_bytes_per_step": P * 4, "d2h_bytes_per_step": P * (4 if world == 1 else 8) + 24},
         "gpu_launches": launches * args.steps,
         "clocks": {"sm_mhz": chosen["clk"]["sm_mhz"], "sm_max_mhz": chosen["clk"]["sm_max_mhz"],
                    "reasons": chosen["clk"]["reasons"]},

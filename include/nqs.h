@@ -138,16 +138,21 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
  * independent configurations, site by site in sampling order;
  * sigma_n = 0 iff u_n < p_n(sigma_n = 0).
  *   uniforms device [B, N] float in [0,1) indexed by sampling position, or
- *            NULL: u_n is drawn from Philox4x32-10 with key = seed and
- *            counter = (n, b, step & 0xffffffff, step >> 32), u = (x0>>8)/2^24
+ *            NULL: u_n of sample b is drawn from Philox4x32-10 with key = seed
+ *            and counter = (n, sample_offset + b, step & 0xffffffff,
+ *            step >> 32), u = (x0>>8)/2^24
+ *   sample_offset  global index of this call's first sample: ranks that each
+ *            draw B samples of one step pass rank * B, so the union of their
+ *            samples is bitwise the one-rank batch (sample_offset + B <= 2^32,
+ *            NQS_EINVAL otherwise)
  *   sigma    device [B, N] uint8 (written, lattice order)
  *   logpsi   device [B] float (written)
  *   hcache   device [B, N, d_h] float or NULL: hidden state h_n used for the
  *            conditional of site n (lattice order) -- the prefix cache that
  *            nqs_local_energy and the gradient calls read.            */
 nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B,
-                      uint64_t seed, uint64_t step, const float* uniforms,
-                      uint8_t* sigma, float* logpsi, float* hcache,
+                      uint64_t seed, uint64_t step, uint64_t sample_offset,
+                      const float* uniforms, uint8_t* sigma, float* logpsi, float* hcache,
                       void* ws, size_t ws_bytes, void* stream);
 
 /* Teacher-forced log psi(sigma) = 1/2 sum_n log p_n(sigma_n) (Eq. 1, pRNN).
@@ -196,6 +201,26 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,
                         const uint8_t* sigma, const float* hcache,
                         const float* eloc, int64_t B, float* grad, double* stats,
                         void* ws, size_t ws_bytes, void* stream);
+
+/* Data-parallel VMC step over ranks (Sec. III; samples are independent, so
+ * each rank draws and evaluates its own share of the batch with replicated
+ * weights).  The step's only exchange is the energy statistics that centre
+ * the gradient weights and the sum of the ranks' gradients:
+ *   1. nqs_energy_sums on each rank: sums = [sum E_loc, sum E_loc^2, B]
+ *      (device [3] double, written);
+ *   2. the caller sums `sums` over ranks (an all-reduce of 3 doubles);
+ *   3. nqs_vmc_grad_global on each rank with the global sums: writes
+ *      stats = [mean, variance (1/M), M] of all ranks and this rank's share
+ *        grad = sum_{b in this rank} 2 (E_loc,b - mean) / M d log psi_b / d theta
+ *      (device [P] double, FP64 sum of the per-block partials);
+ *   4. the caller sums `grad` over ranks (an all-reduce of P doubles).
+ * With one rank, stats equal nqs_vmc_grad's bitwise and grad equals its
+ * gradient before the rounding to float. */
+nqs_status nqs_energy_sums(const float* eloc, int64_t B, double* sums, void* stream);
+nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params,
+                               const uint8_t* sigma, const float* hcache, const float* eloc,
+                               int64_t B, const double* sums, double* grad, double* stats,
+                               void* ws, size_t ws_bytes, void* stream);
 
 /* One replica of a batched VMC step. */
 #define NQS_MAX_REPLICAS 16
@@ -283,6 +308,15 @@ void nqs_set_autotune(int on);
  * and equal to rounding otherwise (2D: bitwise the same).  This is for timing
  * and testing them one by one. */
 void nqs_set_tile_variant(int variant);
+
+/* Bound, in polls, of every tensor-core wait that may give up (default 2^26
+ * polls, about a second); polls < 0 restores the default.  It exists to
+ * exercise the NQS_ETIMEOUT path: with 0 every such wait gives up at once,
+ * the kernels record NQS_ETIMEOUT, finish early with garbage outputs, and
+ * free their tensor memory only after every MMA they issued has drained
+ * (that drain keeps the default bound).  Applies to the current device, for
+ * the whole process; do not change it while kernels of this library run. */
+nqs_status nqs_set_wait_limit(int64_t polls);
 
 /* Copy the workspace status word to *device_status (an nqs_status) after
  * waiting for `stream`; clears it.  This call blocks the host. */

@@ -163,6 +163,100 @@ T* at(void* ws, size_t off) {
 
 }  // namespace
 
+// The gradient reverse sweep behind nqs_logpsi_grad, nqs_vmc_grad and
+// nqs_vmc_grad_global; T is the type of the reduced gradient (float or double).
+template <typename T>
+static nqs_status grad_common(const Dims& d, const Layout& L, const float* params,
+                              const uint8_t* sigma, const float* hcache, const float* weights,
+                              int64_t B, T* grad, void* ws, cudaStream_t st) {
+  float* img = at<float>(ws, L.img);
+  float* partial = at<float>(ws, L.a);
+  if (use_tc(d)) {
+    uint8_t* w3 = at<uint8_t>(ws, L.w);
+    uint8_t* wt = at<uint8_t>(ws, L.w2);
+    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    TcBpttArgs t{};
+    t.B = B;
+    t.N = d.N;
+    t.P = (int)d.P;
+    t.sigma = sigma;
+    t.hcache = hcache;
+    t.weights = weights;
+    t.partial = partial;
+    t.tape_e = at<float>(ws, L.e);
+    t.tape_x = at<uint8_t>(ws, L.f);
+    t.tape_k = at<uint8_t>(ws, L.g);
+    t.hdr = static_cast<WsHeader*>(ws);
+    if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
+  }
+  if (use_tc2d(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    const int rows = tc2d_grad_partial_rows(B, d.N);
+    if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
+    Tc2Grad g{};
+    g.B = B;
+    g.Lx = d.Lx;
+    g.Ly = d.Ly;
+    g.N = d.N;
+    g.P = (int)d.P;
+    g.sz0 = d.sz0;
+    g.sigma = sigma;
+    g.hcache = hcache;
+    g.weights = weights;
+    g.ccarry = at<float>(ws, L.c);
+    g.g1img = at<uint8_t>(ws, L.e);
+    g.g2img = at<uint8_t>(ws, L.f);
+    g.yimg = at<float>(ws, L.g);
+    g.dzimg = at<float>(ws, L.h);
+    g.tape_h = at<float>(ws, L.i);
+    g.tape_k = at<uint8_t>(ws, L.j);
+    g.partial = partial;
+    g.hdr = static_cast<WsHeader*>(ws);
+    if (tc2d_grad(g, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
+  }
+  if (d.cell == NQS_GRU2D) {
+    const int grid = gru2d_bptt_grid(d.d, B);
+    if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
+      return NQS_ECUDA;
+    Bptt2Args a{};
+    a.B = B;
+    a.Lx = d.Lx;
+    a.N = d.N;
+    a.P = (int)d.P;
+    a.sz0 = d.sz0;
+    a.sigma = sigma;
+    a.hcache = hcache;
+    a.weights = weights;
+    a.ccarry = at<float>(ws, L.c);
+    a.partial = partial;
+    a.sacc = at<float>(ws, L.e);
+    const size_t scratch = gru2d_bptt_scratch_floats(d.d, B);
+    if (scratch && cudaMemsetAsync(a.sacc, 0, scratch * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
+    if (gru2d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
+  }
+  const int grid = gru1d_bptt_grid(d.d, B);
+  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
+    return NQS_ECUDA;
+  Bptt1Args a{};
+  a.B = B;
+  a.N = d.N;
+  a.P = (int)d.P;
+  a.sigma = sigma;
+  a.hcache = hcache;
+  a.weights = weights;
+  a.partial = partial;
+  if (gru1d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
+}
+
 extern "C" {
 
 void nqs_set_autotune(int on) { tc1d_set_autotune(on); }
@@ -225,7 +319,8 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
 }
 
 static nqs_status forward_common(const nqs_model_desc* desc, const float* params, int64_t B,
-                                 bool sample, uint64_t seed, uint64_t step, const float* uniforms,
+                                 bool sample, uint64_t seed, uint64_t step, uint64_t b0,
+                                 const float* uniforms,
                                  const uint8_t* sigma_in, uint8_t* sigma_out, float* logpsi,
                                  float* hcache, void* ws, size_t ws_bytes, void* stream) {
   Dims d;
@@ -233,6 +328,8 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   if (r != NQS_OK) return r;
   if ((r = check_built(d)) != NQS_OK) return r;
   if (B < 0) return NQS_EINVAL;
+  // the Philox counter holds the global sample index in 32 bits
+  if (sample && (b0 > ((uint64_t)1 << 32) || (uint64_t)B > ((uint64_t)1 << 32) - b0)) return NQS_EINVAL;
   if (!params || misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
   const Layout L = layout(d, B, sample ? NQS_OP_SAMPLE : NQS_OP_LOGPSI);
   if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
@@ -254,6 +351,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     f.uniforms = uniforms;
     f.seed = seed;
     f.step = step;
+    f.b0 = b0;
     f.logpsi = logpsi;
     f.hcache = hcache;
     f.colbuf = at<float>(ws, L.a);
@@ -272,6 +370,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     a.uniforms = uniforms;
     a.seed = seed;
     a.step = step;
+    a.b0 = b0;
     a.logpsi = logpsi;
     a.hcache = hcache;
     a.colbuf = at<float>(ws, L.a);
@@ -291,6 +390,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     t.uniforms = uniforms;
     t.seed = seed;
     t.step = step;
+    t.b0 = b0;
     t.logpsi = logpsi;
     t.hcache = hcache;
     t.hdr = static_cast<WsHeader*>(ws);
@@ -304,6 +404,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   a.uniforms = uniforms;
   a.seed = seed;
   a.step = step;
+  a.b0 = b0;
   a.logpsi = logpsi;
   a.hcache = hcache;
   a.hdr = static_cast<WsHeader*>(ws);
@@ -311,16 +412,16 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
 }
 
 nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B, uint64_t seed,
-                      uint64_t step, const float* uniforms, uint8_t* sigma, float* logpsi,
-                      float* hcache, void* ws, size_t ws_bytes, void* stream) {
-  return forward_common(desc, params, B, true, seed, step, uniforms, nullptr, sigma, logpsi, hcache,
-                        ws, ws_bytes, stream);
+                      uint64_t step, uint64_t sample_offset, const float* uniforms, uint8_t* sigma,
+                      float* logpsi, float* hcache, void* ws, size_t ws_bytes, void* stream) {
+  return forward_common(desc, params, B, true, seed, step, sample_offset, uniforms, nullptr, sigma, logpsi,
+                        hcache, ws, ws_bytes, stream);
 }
 
 nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
                       int64_t B, float* logpsi, float* hcache, void* ws, size_t ws_bytes,
                       void* stream) {
-  return forward_common(desc, params, B, false, 0, 0, nullptr, sigma, nullptr, logpsi, hcache, ws,
+  return forward_common(desc, params, B, false, 0, 0, 0, nullptr, sigma, nullptr, logpsi, hcache, ws,
                         ws_bytes, stream);
 }
 
@@ -445,96 +546,6 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   return cuda_status(tfim_eloc(sigma, dlog, delta, eloc, B, d.N, (float)ham->J, (float)ham->h, hdr, st));
 }
 
-static nqs_status grad_common(const Dims& d, const Layout& L, const float* params,
-                              const uint8_t* sigma, const float* hcache, const float* weights,
-                              int64_t B, float* grad, void* ws, cudaStream_t st) {
-  float* img = at<float>(ws, L.img);
-  float* partial = at<float>(ws, L.a);
-  if (use_tc(d)) {
-    uint8_t* w3 = at<uint8_t>(ws, L.w);
-    uint8_t* wt = at<uint8_t>(ws, L.w2);
-    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (tc1d_pack(params, w3, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (tc1d_pack_t(params, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    TcBpttArgs t{};
-    t.B = B;
-    t.N = d.N;
-    t.P = (int)d.P;
-    t.sigma = sigma;
-    t.hcache = hcache;
-    t.weights = weights;
-    t.partial = partial;
-    t.tape_e = at<float>(ws, L.e);
-    t.tape_x = at<uint8_t>(ws, L.f);
-    t.tape_k = at<uint8_t>(ws, L.g);
-    t.hdr = static_cast<WsHeader*>(ws);
-    if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
-  }
-  if (use_tc2d(d)) {
-    uint8_t* wimg = at<uint8_t>(ws, L.w);
-    const int rows = tc2d_grad_partial_rows(B, d.N);
-    if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (cudaMemsetAsync(partial, 0, (size_t)rows * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
-    Tc2Grad g{};
-    g.B = B;
-    g.Lx = d.Lx;
-    g.Ly = d.Ly;
-    g.N = d.N;
-    g.P = (int)d.P;
-    g.sz0 = d.sz0;
-    g.sigma = sigma;
-    g.hcache = hcache;
-    g.weights = weights;
-    g.ccarry = at<float>(ws, L.c);
-    g.g1img = at<uint8_t>(ws, L.e);
-    g.g2img = at<uint8_t>(ws, L.f);
-    g.yimg = at<float>(ws, L.g);
-    g.dzimg = at<float>(ws, L.h);
-    g.tape_h = at<float>(ws, L.i);
-    g.tape_k = at<uint8_t>(ws, L.j);
-    g.partial = partial;
-    g.hdr = static_cast<WsHeader*>(ws);
-    if (tc2d_grad(g, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    return cuda_status(reduce_partials(partial, rows, (int)d.P, grad, st));
-  }
-  if (d.cell == NQS_GRU2D) {
-    const int grid = gru2d_bptt_grid(d.d, B);
-    if (gru2d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
-      return NQS_ECUDA;
-    Bptt2Args a{};
-    a.B = B;
-    a.Lx = d.Lx;
-    a.N = d.N;
-    a.P = (int)d.P;
-    a.sz0 = d.sz0;
-    a.sigma = sigma;
-    a.hcache = hcache;
-    a.weights = weights;
-    a.ccarry = at<float>(ws, L.c);
-    a.partial = partial;
-    a.sacc = at<float>(ws, L.e);
-    const size_t scratch = gru2d_bptt_scratch_floats(d.d, B);
-    if (scratch && cudaMemsetAsync(a.sacc, 0, scratch * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
-    if (gru2d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-    return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
-  }
-  const int grid = gru1d_bptt_grid(d.d, B);
-  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-  if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess)
-    return NQS_ECUDA;
-  Bptt1Args a{};
-  a.B = B;
-  a.N = d.N;
-  a.P = (int)d.P;
-  a.sigma = sigma;
-  a.hcache = hcache;
-  a.weights = weights;
-  a.partial = partial;
-  if (gru1d_bptt(a, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
-  return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
-}
 
 nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
                            const float* hcache, const float* weights, int64_t B, float* grad,
@@ -573,6 +584,40 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const u
   return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
 }
 
+
+nqs_status nqs_energy_sums(const float* eloc, int64_t B, double* sums, void* stream) {
+  if (!sums || B < 0 || (B > 0 && !eloc)) return NQS_EINVAL;
+  return cuda_status(energy_sums(eloc, B, sums, static_cast<cudaStream_t>(stream)));
+}
+
+nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                               const float* hcache, const float* eloc, int64_t B, const double* sums,
+                               double* grad, double* stats, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (!params || !sums || !grad || !stats || B < 0) return NQS_EINVAL;
+  if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
+  if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
+  const Layout L = layout(d, B, NQS_OP_VMC_GRAD);
+  if ((r = check_ws(ws, ws_bytes, L)) != NQS_OK) return r;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
+  if (stats_from_sums(sums, stats, st) != cudaSuccess) return NQS_ECUDA;
+  if (B == 0) return cuda_status(cudaMemsetAsync(grad, 0, d.P * sizeof(double), st));
+  float* w = at<float>(ws, L.b);
+  if (vmc_weights(eloc, stats, B, w, st) != cudaSuccess) return NQS_ECUDA;
+  return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
+}
+
+nqs_status nqs_set_wait_limit(int64_t polls) {
+  const uint32_t v = polls < 0 ? tc_default_wait_polls() : (uint32_t)(polls > 0xFFFFFFFFll ? 0xFFFFFFFFll : polls);
+  if (tc1d_set_wait_polls(v) != cudaSuccess || tc2d_set_wait_polls(v) != cudaSuccess ||
+      tc2d_grad_set_wait_polls(v) != cudaSuccess)
+    return NQS_ECUDA;
+  return NQS_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Batched step over replicas.

@@ -16,6 +16,7 @@ struct Fwd1Args {
   uint8_t* sigma_out;        // sampling
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   float* logpsi;
   float* hcache;             // nullable
   WsHeader* hdr;
@@ -60,6 +61,7 @@ struct Eng2Args {
   uint8_t* sigma_out;        // sampling
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   float* logpsi;             // sampling / teacher forcing
   float* hcache;             // written by sampling / teacher forcing, read by chains
   float* colbuf;             // [slots, Lx, d] column buffers
@@ -90,6 +92,7 @@ struct Tc2Fwd {
   uint8_t* sigma_out;        // sampling
   const float* uniforms;     // nullable
   uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // nullable
   float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
@@ -165,6 +168,7 @@ struct Tc1Args {
   uint8_t* sigma_out;        // sampling
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   float* logpsi;
   float* hcache;             // written by sampling / teacher forcing (nullable), read by chains
   const float* dlog;         // chains
@@ -198,6 +202,7 @@ cudaError_t tc1d_bptt(const TcBpttArgs& a, const float* img, const uint8_t* w3, 
                       cudaStream_t st);
 // grad = the FP64 sum of the partial rows tc1d_bptt wrote
 cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, float* grad, cudaStream_t st);
+cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, double* grad, cudaStream_t st);
 size_t tc1d_wimg_bytes(int D);
 cudaError_t tc1d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
 // mode 0: sampling, 1: teacher forcing, 2: TFIM chains
@@ -231,10 +236,22 @@ cudaError_t batched_step(const BatchRep* reps, int R, uint64_t step, const uint6
 // reductions (reduce.cu)
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st);
 cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float* w, cudaStream_t st);
+// sums = [sum E, sum E^2, B] of one rank; stats = [mean, variance, M] from the sums of all ranks
+cudaError_t energy_sums(const float* eloc, int64_t B, double* sums, cudaStream_t st);
+cudaError_t stats_from_sums(const double* sums, double* stats, cudaStream_t st);
 cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st);
+cudaError_t reduce_partials(const float* partial, int rows, int P, double* grad, cudaStream_t st);
 // grad[0 .. ncols) = FP64 sum over `rows` rows (stride ld floats) of partial
 cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, float* grad,
                                  cudaStream_t st);
+cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, double* grad,
+                                 cudaStream_t st);
+
+// bound of the tensor-core waits that may give up, per translation unit
+uint32_t tc_default_wait_polls();
+cudaError_t tc1d_set_wait_polls(uint32_t polls);
+cudaError_t tc2d_set_wait_polls(uint32_t polls);
+cudaError_t tc2d_grad_set_wait_polls(uint32_t polls);
 
 // growth (grow.cu)
 cudaError_t grow_params(int cell, int d, int m, int D, int Mm, const float* p_small, float* p_big,

@@ -32,6 +32,42 @@ __global__ void energy_stats_kernel(const float* __restrict__ eloc, int64_t B, d
   }
 }
 
+// sums = [sum E_loc, sum E_loc^2, B]: one rank's share of the statistics of
+// a data-parallel step, in the fixed order of energy_stats_kernel.
+__global__ void energy_sums_kernel(const float* __restrict__ eloc, int64_t B, double* sums) {
+  __shared__ double s1[1024], s2[1024];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
+    const double e = (double)eloc[i];
+    a += e;
+    b += e * e;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      s1[threadIdx.x] += s1[threadIdx.x + off];
+      s2[threadIdx.x] += s2[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[0] = s1[0];
+    sums[1] = s2[0];
+    sums[2] = (double)B;
+  }
+}
+
+// stats = [mean, mean(E^2) - mean^2, M] from sums = [sum E, sum E^2, M] of all ranks.
+__global__ void stats_from_sums_kernel(const double* __restrict__ sums, double* stats) {
+  const double M = sums[2];
+  const double mean = sums[0] / M;
+  stats[0] = mean;
+  stats[1] = sums[1] / M - mean * mean;
+  stats[2] = M;
+}
+
 // w_b = 2 (E_loc,b - mean) / M
 __global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double* __restrict__ stats,
                                    int64_t B, float* __restrict__ w) {
@@ -41,11 +77,13 @@ __global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double*
     w[i] = (float)(2.0 * ((double)eloc[i] - mean) / M);
 }
 
-// grad[p] = sum_r partial[r][p], accumulated in FP64 in a fixed order.
+// grad[p] = sum_r partial[r][p], accumulated in FP64 in a fixed order and
+// written as T (float, or double for gradients that are summed over ranks).
 // A block sums 32 columns: 8 row groups (r = g mod 8) per column, each with
 // 4 independent FP64 accumulators, then the 8 group sums in a fixed tree.
+template <typename T>
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
-                                                              int64_t ld, float* __restrict__ grad) {
+                                                              int64_t ld, T* __restrict__ grad) {
   __shared__ double red[8][33];
   const int col = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + col;
@@ -65,12 +103,22 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __res
   if (g == 0 && p < P) {
     const double s = ((red[0][col] + red[1][col]) + (red[2][col] + red[3][col])) +
                      ((red[4][col] + red[5][col]) + (red[6][col] + red[7][col]));
-    grad[p] = (float)s;
+    grad[p] = (T)s;
   }
 }
 
 cudaError_t energy_stats(const float* eloc, int64_t B, double* stats, cudaStream_t st) {
   energy_stats_kernel<<<1, 1024, 0, st>>>(eloc, B, stats);
+  return cudaGetLastError();
+}
+
+cudaError_t energy_sums(const float* eloc, int64_t B, double* sums, cudaStream_t st) {
+  energy_sums_kernel<<<1, 1024, 0, st>>>(eloc, B, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t stats_from_sums(const double* sums, double* stats, cudaStream_t st) {
+  stats_from_sums_kernel<<<1, 1, 0, st>>>(sums, stats);
   return cudaGetLastError();
 }
 
@@ -82,15 +130,27 @@ cudaError_t vmc_weights(const float* eloc, const double* stats, int64_t B, float
   return cudaGetLastError();
 }
 
-cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, float* grad,
-                                 cudaStream_t st) {
+template <typename T>
+static cudaError_t reduce_cols(const float* partial, int rows, int ncols, int64_t ld, T* grad, cudaStream_t st) {
   const int blocks = (ncols + 31) / 32;
   if (blocks < 1) return cudaSuccess;
-  reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, rows, ncols, ld, grad);
+  reduce_partials_kernel<T><<<blocks, 256, 0, st>>>(partial, rows, ncols, ld, grad);
   return cudaGetLastError();
 }
 
+cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, float* grad,
+                                 cudaStream_t st) {
+  return reduce_cols(partial, rows, ncols, ld, grad, st);
+}
+cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, double* grad,
+                                 cudaStream_t st) {
+  return reduce_cols(partial, rows, ncols, ld, grad, st);
+}
+
 cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
+  return reduce_partials_cols(partial, rows, P, P, grad, st);
+}
+cudaError_t reduce_partials(const float* partial, int rows, int P, double* grad, cudaStream_t st) {
   return reduce_partials_cols(partial, rows, P, P, grad, st);
 }
 

@@ -123,6 +123,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// Bound, in polls of mbarrier.try_wait, of the waits that may give up (and
+// record NQS_ETIMEOUT).  Every translation unit that includes this header has
+// its own copy; the host sets all of them through nqs_set_wait_limit, which
+// exists to exercise the give-up path.  The drain below always uses the
+// default bound, so TMEM is never freed under a running MMA.
+constexpr uint32_t kDefaultWaitPolls = 1u << 26;
+static __device__ uint32_t g_wait_polls = kDefaultWaitPolls;
+
+// Drain before TMEM is freed.  After a bounded wait gave up, MMAs committed
+// earlier (some never waited for) may still be running and writing TMEM.
+// Every MMA-issuing thread of the CTA calls this once: it commits once more to
+// `drain` (initialised with one arrival per issuing thread), whose phase 0
+// completes when every MMA those threads issued has completed, and waits for
+// it with the same bound.
+__device__ __forceinline__ void drain_mmas(uint64_t* drain, uint32_t max_iters) {
+  mma_commit(drain);
+  mbar_wait(drain, 0, max_iters);
+}
+
 // Barrier over `count` threads with id `id` (1..15), OR-reducing a predicate.
 __device__ __forceinline__ bool group_barrier_or(bool v, uint32_t id, uint32_t count) {
   uint32_t r;

@@ -35,7 +35,7 @@ namespace nqs {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kWaitLimit = tc::kDefaultWaitPolls;   // the drain's bound
 constexpr int kPPEarly = 0;   // ping-pong: sub-chunks of the epilogue left when the token is passed (0 = after the last)
 
 // Gate weights with the biases and one-hot input columns folded in, as a
@@ -142,12 +142,13 @@ struct Smem {
   static constexpr int HS = D + 4;                               // staging row stride (floats; conflict-free float4)
   static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x HS floats: next chain state
                                                                  // (chains) or the new states (cache stores)
-  static constexpr int kBar = (kStage + GROUPS * 128 * HS * 4 + 15) / 16 * 16;
-  static constexpr int kSlot = kBar + 8 * GROUPS;
+  static constexpr int kBar = (kStage + GROUPS * 128 * HS * 4 + 15) / 16 * 16;   // GROUPS MMA + 1 drain
+  static constexpr int kSlot = kBar + 8 * (GROUPS + 1);
   static constexpr int kFlags = kSlot + 16;                      // ping-pong idle flags, one int per tile
   static constexpr int kUsed = kFlags + 16;
   // one CTA per SM for the persistent chain launch (TMEM holds two tiles)
   static constexpr int kBytes = 1024 + (GROUPS == 2 ? (kUsed > 120 * 1024 ? kUsed : 120 * 1024) : kUsed);
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
 };
 
 // Tile threads: SPLIT threads per row, in different warps (a warp reads only
@@ -171,6 +172,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   static_assert(DU % 16 == 0, "at least 16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sB = sm + S::kB;
   float* dUs = reinterpret_cast<float*>(sm + S::kDU);
   float* zbuf = reinterpret_cast<float*>(sm + S::kZ);
@@ -188,6 +190,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     for (int g = 0; g < GROUPS; ++g) tc::mbar_init(&mbar[g], 1);
+    tc::mbar_init(&mbar[GROUPS], GROUPS);    // drain: one arrival per tile's MMA issuer
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 2) idle_flag[threadIdx.x] = 0;
@@ -350,7 +353,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     float dl = 0.0f, uni = 0.0f;
     if (active) {
       if constexpr (MODE == 0) {
-        uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)b, (uint32_t)t);
+        uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
       } else {
         s_t = a.sigma[b * N + t] ? 1 : 0;
         if constexpr (MODE == 2) dl = a.dlog[b * N + t];
@@ -358,7 +361,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     }
     // ---- (d) wait for the accumulator ----
     if (any) {
-      if (!tc::mbar_wait(&mbar[g], phase, kWaitLimit)) {
+      if (!tc::mbar_wait(&mbar[g], phase, wlim)) {
         timed_out = true;
         flag_status(a.hdr, NQS_ETIMEOUT);
       }
@@ -572,8 +575,10 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     ++pstep;
   }
   cp_async_wait_all();
-  // ---- epilogue: free TMEM once both tiles are done ----
+  // ---- epilogue: free TMEM once both tiles are done (and, after a wait that
+  // gave up, once their MMAs have drained) ----
   tc::fence_before_sync();
+  if (__syncthreads_or(timed_out) && tt == 0) tc::drain_mmas(&mbar[GROUPS], kWaitLimit);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, GROUPS == 2 ? 512 : 256);
@@ -686,8 +691,8 @@ struct TpS {
   static constexpr int kH = kA + 128 * KA * 2;            // 3 x [128 x HS] f32 state rows
   static constexpr int kDU = kH + 3 * 128 * HS * 4;       // D floats: U[0] - U[1]
   static constexpr int kZ = kDU + D * 4;                  // SPLIT x 128 floats (readout exchange)
-  static constexpr int kBar = kZ + SPLIT * 128 * 4;       // 4 mbarriers: MMA, 3 state buffers
-  static constexpr int kSlot = kBar + 32;
+  static constexpr int kBar = kZ + SPLIT * 128 * 4;       // 5 mbarriers: MMA, 3 state buffers, drain
+  static constexpr int kSlot = kBar + 40;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static constexpr int kCols = 4 * D;                     // 64, 128 or 256 columns
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -702,6 +707,7 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   static_assert(DU == 16, "16 units per thread");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sWf = sm + S::kWf;
   uint8_t* sA = sm + S::kA;
   float* sH = reinterpret_cast<float*>(sm + S::kH);
@@ -716,6 +722,7 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);                           // MMA done
     for (int k = 1; k < 4; ++k) tc::mbar_init(&mbar[k], NT);   // state buffer k - 1 filled
+    tc::mbar_init(&mbar[4], 1);                           // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kCols);
@@ -734,7 +741,7 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   uint32_t phases = 0;                     // bit k: the phase of mbar[k] waited for next
   bool timed_out = false;
   auto wait = [&](int k) {
-    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, wlim)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
     phases ^= 1u << k;
   };
   // readout gradients of this thread's rows: dU_0[u] += dz_n h_n[u], dc_0 += dz_n
@@ -895,6 +902,8 @@ tc1d_tape_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wfim
   }
   cp_async_wait_all();
   tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMAs have drained
+  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(&mbar[4], kWaitLimit);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kCols);
@@ -937,8 +946,8 @@ struct BSmem {
   static constexpr int kK = kG + 128 * GW * 2;            // NB tape buffers
   static constexpr int kC = kK + NB * KB;                 // [ROWS x CS] f32 (ROWS < 128)
   static constexpr int kDU = kC + (ROWS < 128 ? ROWS * CS * 4 : 0);   // D floats: U[0] - U[1]
-  static constexpr int kBar = kDU + D * 4;                // 6 mbarriers
-  static constexpr int kSlot = kBar + 48;
+  static constexpr int kBar = kDU + D * 4;                // 7 mbarriers (the last: drain)
+  static constexpr int kSlot = kBar + 56;
   static constexpr int kBytes = 1024 + kSlot + 16;
   // TMEM columns: acc_b in three accumulators (one per gate block of G, so
   // that the K steps form three independent chains), acc_w in two halves
@@ -958,6 +967,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
   constexpr int DG = D / 8;                // 8-unit groups per state
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sWt = sm + S::kWt;
   uint8_t* sX = sm + S::kX;
   uint8_t* sG = sm + S::kG;
@@ -975,6 +985,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
     tc::mbar_init(&mbar[0], 1);              // MMA_b done
     tc::mbar_init(&mbar[1], 1);              // MMA_w done
     for (int k = 2; k < 6; ++k) tc::mbar_init(&mbar[k], NT);   // tape buffers 0, 1 and X buffers 0, 1 filled
+    tc::mbar_init(&mbar[6], 2);              // drain: MMA issuers threads 0 and 32
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kCols);
@@ -999,7 +1010,7 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
   bool timed_out = false;
   uint32_t phases = 0;                     // bit k: the phase of mbar[k] this thread waits for next
   auto wait = [&](int k) {
-    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, kWaitLimit)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
+    if (!tc::mbar_wait(&mbar[k], (phases >> k) & 1u, wlim)) { timed_out = true; flag_status(a.hdr, NQS_ETIMEOUT); }
     phases ^= 1u << k;
   };
   // tape factors k_n of this thread's units into tape buffer kb (zeros past
@@ -1193,6 +1204,10 @@ tc1d_bptt_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wtim
   if (threadIdx.x == 0 && !timed_out) wait(1);
   cp_async_wait_all();
   tc::fence_before_sync();
+  // after a wait that gave up, acc_w is read and TMEM freed only once every
+  // MMA_b and MMA_w has drained
+  if (__syncthreads_or(timed_out) && (threadIdx.x == 0 || threadIdx.x == 32))
+    tc::drain_mmas(&mbar[6], kWaitLimit);
   __syncthreads();
   tc::fence_after_sync();
   // ---- this CTA's weight, bias and one-hot-column gradients from acc_w (warps 0-3) ----
@@ -1509,13 +1524,20 @@ cudaError_t launch_tc_bptt(const TcBpttArgs& a, const float* img, const uint8_t*
 // chosen variant's CTAs are zero) carry the weight, bias and one-hot-column
 // gradients, columns [0, U); the tape CTAs' rows carry the readout gradients,
 // columns [U, P).  Each block of columns is summed over its own rows.
-cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, float* grad, cudaStream_t st) {
+template <typename T>
+static cudaError_t bptt_reduce(const TcBpttArgs& a, int D, T* grad, cudaStream_t st) {
   const int rows = bptt_sweep_rows(a.B);
   const int Uoff = 3 * D * D + 10 * D;
   cudaError_t e = reduce_partials_cols(a.partial, rows, Uoff, a.P, grad, st);
   if (e != cudaSuccess) return e;
   return reduce_partials_cols(a.partial + (size_t)rows * a.P + Uoff, tape_grid(a.B, a.N).grid, a.P - Uoff, a.P,
                               grad + Uoff, st);
+}
+cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, float* grad, cudaStream_t st) {
+  return bptt_reduce(a, D, grad, st);
+}
+cudaError_t tc1d_bptt_reduce(const TcBpttArgs& a, int D, double* grad, cudaStream_t st) {
+  return bptt_reduce(a, D, grad, st);
 }
 
 cudaError_t tc1d_pack_t(const float* params, uint8_t* wt, int D, cudaStream_t st) {
@@ -1550,4 +1572,9 @@ cudaError_t tc1d_run(const Tc1Args& a, const float* img, const uint8_t* wimg, in
   return cudaErrorInvalidValue;
 }
 
+}  // namespace nqs
+
+namespace nqs {
+uint32_t tc_default_wait_polls() { return tc::kDefaultWaitPolls; }
+cudaError_t tc1d_set_wait_polls(uint32_t polls) { return cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof(polls)); }
 }  // namespace nqs

@@ -186,8 +186,8 @@ struct S2 {
   static constexpr int kPos = kCol + 128 * 4;              // 128 ints: (i, j, r) of every zig-zag position
   static constexpr int kZx = kPos + 128 * 4;               // 512 floats: readout partials of the unit slices
   static constexpr int kJob = kZx + 512 * 4;               // 128 long long: chain job of each row (split rows)
-  static constexpr int kBar = kJob + 128 * 8;              // 2 mbarriers
-  static constexpr int kSlot = kBar + 16;
+  static constexpr int kBar = kJob + 128 * 8;              // 3 mbarriers: MMA1, MMA2, drain
+  static constexpr int kSlot = kBar + 24;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
   static constexpr uint32_t kTmemCols = 3 * D <= 128 ? 128 : 256;   // accumulators [0, 3D)
@@ -200,6 +200,7 @@ struct Tc2Args {
   uint8_t* sigma_out;
   const float* uniforms;
   uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // written by sampling / teacher forcing (nullable); read by chains
   float* colbuf;             // [CTAs x 128 rows, Lx, d] latest FP32 state of every lattice column
@@ -236,6 +237,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   static_assert(DU >= 16 && DU % 16 == 0, "16-unit readout chunks");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sW1 = sm + S::kW1;
   uint8_t* sW2 = sm + S::kW2;
   uint8_t* sA = sm + S::kA;
@@ -262,6 +264,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&mbar[2], 1);              // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kTmemCols);
@@ -480,9 +483,9 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     float uni = 0.0f;
     if (MODE == 0 && active) {
-      uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)b, (uint32_t)t);
+      uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
     }
-    if (!tc::mbar_wait(&mbar[0], ph0, kWait2)) {
+    if (!tc::mbar_wait(&mbar[0], ph0, wlim)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
@@ -609,7 +612,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
       __syncwarp();
     }
-    if (!tc::mbar_wait(&mbar[1], ph1, kWait2)) {
+    if (!tc::mbar_wait(&mbar[1], ph1, wlim)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
@@ -705,6 +708,8 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   }
   cp_wait_2d();
   tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMAs have drained
+  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(&mbar[2], kWait2);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kTmemCols);
@@ -724,7 +729,7 @@ struct T2S {
   static constexpr int kA = kW2 + 2 * D * K2 * 2;          // [128 x KA2] bf16
   static constexpr int kAux = kA + 128 * KA2 * 2;          // D + 4 floats
   static constexpr int kPos = kAux + (D + 4) * 4;          // 128 ints: lattice site of every position
-  static constexpr int kBar = kPos + 128 * 4;
+  static constexpr int kBar = kPos + 128 * 4;              // 2 mbarriers: MMA, drain
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
 };
@@ -746,6 +751,7 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
   constexpr int K2 = S::K2, KA2 = S::KA2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sW2 = sm + S::kW2;
   uint8_t* sA = sm + S::kA;
   float* sAux = reinterpret_cast<float*>(sm + S::kAux);
@@ -762,6 +768,7 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);              // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 128);
@@ -776,6 +783,7 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
   const uint32_t one = 0x3F80u;
   const int64_t ncell = a.B * N, ntile = (ncell + 127) / 128;
   uint32_t ph = 0;
+  bool timed_out = false;
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t cell = tile * 128 + m;
     const bool valid = cell < ncell;
@@ -809,7 +817,7 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
     int n_up = 0;
     if (valid)
       for (int q = 0; q < t; ++q) n_up += a.sigma[b * N + sSite[q]] ? 0 : 1;
-    const bool ok = tc::mbar_wait(&mbar[0], ph, kWait2);
+    const bool ok = tc::mbar_wait(&mbar[0], ph, wlim);
     if (!ok) flag_status(a.hdr, NQS_ETIMEOUT);
     ph ^= 1;
     tc::fence_after_sync();
@@ -846,9 +854,14 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
     // every lane has read the accumulator before the next tile's MMA; a timeout ends all lanes together
     const bool stop = __syncthreads_or(!ok);
     tc::fence_after_sync();
-    if (stop) break;
+    if (stop) {
+      timed_out = true;
+      break;
+    }
   }
   tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMA has drained
+  if (timed_out && m == 0) tc::drain_mmas(&mbar[1], kWait2);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 128);
@@ -927,6 +940,7 @@ cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sampl
   a.uniforms = f.uniforms;
   a.seed = f.seed;
   a.step = f.step;
+  a.b0 = f.b0;
   a.logpsi = f.logpsi;
   a.hcache = f.hcache;
   a.colbuf = f.colbuf;
@@ -1019,4 +1033,8 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   return cudaErrorInvalidValue;
 }
 
+}  // namespace nqs
+
+namespace nqs {
+cudaError_t tc2d_set_wait_polls(uint32_t polls) { return cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof(polls)); }
 }  // namespace nqs

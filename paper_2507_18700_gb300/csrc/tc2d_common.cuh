@@ -9,7 +9,7 @@
 namespace nqs {
 namespace tc2dh {
 
-constexpr uint32_t kWait2 = 1u << 26;   // mbarrier polls before giving up
+constexpr uint32_t kWait2 = tc::kDefaultWaitPolls;   // the drain's bound (mbarrier polls)
 
 __device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float hw_tanh2(float x) {

@@ -48,7 +48,7 @@ struct G2S {
   static constexpr int kA1 = kW2 + 2 * D * K2 * 2;         // [128 x KA1]; G1 [128 x 3D] aliases it
   static constexpr int kA2 = kA1 + 128 * KA1 * 2;          // [128 x KA2]; G2 [128 x 2D] aliases it
   static constexpr int kAux = kA2 + 128 * KA2 * 2;         // D + 4 floats: U_0 - U_1, c_0 - c_1
-  static constexpr int kBar = kAux + (D + 4) * 4;          // 3 mbarriers
+  static constexpr int kBar = kAux + (D + 4) * 4;          // 4 mbarrier slots: MMA1+2, MMA_g, -, drain
   static constexpr int kSlot = kBar + 32;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -149,6 +149,7 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
   constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sW1 = sm + S::kW1;
   uint8_t* sW2 = sm + S::kW2;
   uint8_t* sA1 = sm + S::kA1;
@@ -164,6 +165,7 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     for (int q = 0; q < 2; ++q) tc::mbar_init(&mbar[q], 1);
+    tc::mbar_init(&mbar[3], 1);              // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -181,7 +183,7 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
   bool timed_out = false;
   const uint32_t one = 0x3F80u;
   auto wait = [&](int q) {
-    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, kWait2)) {
+    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, wlim)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
@@ -379,6 +381,8 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
     if (timed_out) break;                   // uniform
   }
   tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMAs have drained
+  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(&mbar[3], kWait2);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
@@ -409,7 +413,7 @@ struct B2S {
   static constexpr int kA1 = kW1 + 3 * D * K1 * 2;         // [128 x 3D] bf16 (G1; rows past ROWS unused)
   static constexpr int kT = kA1 + 128 * 3 * D * 2;         // [NG][ROWS] x 16 B tape of one cell
   static constexpr int kC = kT + NG * ROWS * 16;           // 2 x [ROWS x CS] f32 (ROWS < 128)
-  static constexpr int kBar = kC + (ROWS < 128 ? 2 * ROWS * CS * 4 : 0);   // 3 mbarriers
+  static constexpr int kBar = kC + (ROWS < 128 ? 2 * ROWS * CS * 4 : 0);   // 4 mbarriers (the last: drain)
   static constexpr int kSlot = kBar + 32;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -429,6 +433,7 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   constexpr bool XCH = ROWS < 128;         // carries exchanged through shared memory
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sW1 = sm + S::kW1;
   uint8_t* sA1 = sm + S::kA1;
   uint8_t* sT = sm + S::kT;
@@ -443,6 +448,7 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
     tc::mbar_init(&mbar[0], 1);              // MMA_b, horizontal half, done
     tc::mbar_init(&mbar[1], NT);             // tape of the cell in place
     tc::mbar_init(&mbar[2], 1);              // MMA_b, vertical half, done
+    tc::mbar_init(&mbar[3], 1);              // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -472,7 +478,7 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   uint32_t phases = 0;
   bool timed_out = false;
   auto wait = [&](int q) {
-    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, kWait2)) {
+    if (!tc::mbar_wait(&mbar[q], (phases >> q) & 1u, wlim)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
@@ -696,6 +702,8 @@ tc2d_bsweep_kernel(const uint8_t* __restrict__ w1img, Sweep2Args a) {
   if (!timed_out && (!XCH || owner)) wait(2);   // the last vertical half, before TMEM is freed
   asm volatile("cp.async.wait_all;\n" ::: "memory");   // copies in flight after a timeout
   tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMAs have drained
+  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(&mbar[3], kWait2);
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
@@ -713,7 +721,7 @@ struct W2S {
   static constexpr int kG2 = kG1 + 128 * GW1 * 2;          // [128 x GW2] bf16
   static constexpr int kX1 = kG2 + 128 * GW2 * 2;          // [128 x K1] bf16
   static constexpr int kX2 = kX1 + 128 * K1 * 2;           // [128 x K2] bf16
-  static constexpr int kBar = kX2 + 128 * K2 * 2;
+  static constexpr int kBar = kX2 + 128 * K2 * 2;          // 2 mbarriers: MMA, drain
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -738,6 +746,7 @@ __global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
   constexpr int K1 = S::K1, K2 = S::K2, GW1 = S::GW1, GW2 = S::GW2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
   uint8_t* sG1 = sm + S::kG1;
   uint8_t* sG2 = sm + S::kG2;
   uint8_t* sX1 = sm + S::kX1;
@@ -746,6 +755,7 @@ __global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
   if (threadIdx.x == 0) {
     tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);              // drain (MMA issuer: thread 0)
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -828,14 +838,20 @@ __global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
                      acc0 | (c > 0));
       tc::mma_commit(&mbar[0]);
     }
-    if (!tc::mbar_wait(&mbar[0], ph, kWait2)) {
+    if (!tc::mbar_wait(&mbar[0], ph, wlim)) {
       timed_out = true;
       flag_status(a.hdr, NQS_ETIMEOUT);
     }
     ph ^= 1;
     tc::fence_after_sync();
-    __syncthreads();   // the shared images are rewritten for the next image
+    // the shared images are rewritten for the next image; a wait that gave up
+    // anywhere ends the loop for every thread (the drain below)
+    if (__syncthreads_or(timed_out)) timed_out = true;
   }
+  tc::fence_before_sync();
+  if (timed_out && threadIdx.x == 0) tc::drain_mmas(&mbar[1], kWait2);
+  __syncthreads();
+  tc::fence_after_sync();
   // ---- this CTA's partial gradient row (flat 2D layout, App. A; nqs.h) ----
   const int W2c = 2 * D + 4;
   const int oW = 0, oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D,
@@ -1058,4 +1074,10 @@ cudaError_t tc2d_grad(const Tc2Grad& g, const uint8_t* wimg, int D, cudaStream_t
   return cudaErrorInvalidValue;
 }
 
+}  // namespace nqs
+
+namespace nqs {
+cudaError_t tc2d_grad_set_wait_polls(uint32_t polls) {
+  return cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof(polls));
+}
 }  // namespace nqs

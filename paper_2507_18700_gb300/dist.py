@@ -1,12 +1,15 @@
 """Data-parallel VMC step over ranks (one process per GPU).
 
-Samples are independent, so each rank draws and evaluates its own batch with
-the replicated weights.  The step has one real exchange (Sec. III): the
-gradient weights w_b = 2 (E_loc,b - E_mean) / M need the mean energy and the
-sample count over all ranks, and the gradient is the sum of the ranks' sums.
-Both are all-reduces of small tensors; the kernels stay per rank.
+Samples are independent (Sec. III), so each rank draws and evaluates its own
+share of the batch with the replicated weights.  Rank r draws the samples
+with global indices r*B .. r*B + B - 1 of one Philox stream (the library's
+sample offset), so the union over ranks is bitwise the batch one rank would
+draw and the result does not depend on the rank count.  The step has one real
+exchange: the gradient weights w_b = 2 (E_loc,b - mean) / M need the energy
+sums of all ranks, and the gradient is the sum of the ranks' shares.  All of
+the arithmetic runs in the library (nqs_energy_sums, nqs_vmc_grad_global);
+this module only moves buffers through all-reduces.
 """
-import torch
 import torch.distributed as dist
 
 from . import nqs
@@ -16,41 +19,37 @@ def _world(group):
     return dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
 
 
-def global_energy_stats(eloc, group=None):
-    """[mean, variance, M] of the local energies of all ranks, in float64: one
-    all-reduce of (sum E, sum E^2, M)."""
-    e = eloc.double()
-    s = torch.stack([e.sum(), (e * e).sum(), torch.tensor(float(e.numel()), dtype=torch.float64, device=e.device)])
+def _rank(group):
+    return dist.get_rank(group) if _world(group) > 1 else 0
+
+
+def allreduce(t, group=None):
+    """Sum a library-filled buffer over ranks, in place (no-op on one rank)."""
     if _world(group) > 1:
-        dist.all_reduce(s, group=group)
-    M = s[2]
-    mean = s[0] / M
-    return torch.stack([mean, s[1] / M - mean * mean, M])
+        dist.all_reduce(t, group=group)
+    return t
 
 
-def vmc_weights(eloc, stats):
-    """w_b = 2 (E_loc,b - mean) / M with the global statistics (float32)."""
-    return (2.0 * (eloc.double() - stats[0]) / stats[2]).float()
+def sample_offset(B, group=None):
+    """Global index of this rank's first sample when every rank draws B."""
+    return _rank(group) * B
 
 
-def allreduce_grad(grad, group=None):
-    """Sum the ranks' partial gradients in place."""
-    if _world(group) > 1:
-        dist.all_reduce(grad, group=group)
-    return grad
+def global_gradient(desc, params, sigma, hcache, eloc, ws=None, group=None, api=nqs):
+    """(grad float64 [P], stats float64 [3]) of all ranks' samples: the energy
+    sums are all-reduced, the library forms the centred weights and this
+    rank's gradient share, and the shares are all-reduced."""
+    sums = allreduce(api.energy_sums(eloc), group)
+    grad, stats = api.vmc_grad_global(desc, params, sigma, hcache, eloc, sums, ws=ws)
+    return allreduce(grad, group), stats
 
 
-def rank_seed(seed, group=None):
-    """Sampling seed of this rank: distinct Philox streams per rank."""
-    r = dist.get_rank(group) if _world(group) > 1 else 0
-    return seed + 1000003 * r
-
-
-def vmc_step(desc, params, ham, B, seed, step, ws=None, group=None):
-    """One VMC step on this rank's B samples with the exchange above.
-    Returns (grad, stats, sigma, eloc); grad and stats are global."""
-    sigma, _, hc = nqs.sample(desc, params, B, seed=rank_seed(seed, group), step=step, ws=ws)
-    eloc = nqs.local_energy(desc, params, ham, sigma, hc, ws=ws)
-    stats = global_energy_stats(eloc, group)
-    grad = nqs.logpsi_grad(desc, params, sigma, hc, vmc_weights(eloc, stats), ws=ws)
-    return allreduce_grad(grad, group), stats, sigma, eloc
+def vmc_step(desc, params, ham, B, seed, step, ws=None, group=None, api=nqs):
+    """One VMC step on this rank's B samples (every rank passes the same B,
+    seed and step).  Returns (grad, stats, sigma, eloc); grad and stats are
+    global."""
+    sigma, _, hc = api.sample(desc, params, B, seed=seed, step=step, ws=ws,
+                              sample_offset=sample_offset(B, group))
+    eloc = api.local_energy(desc, params, ham, sigma, hc, ws=ws)
+    grad, stats = global_gradient(desc, params, sigma, hc, eloc, ws=ws, group=group, api=api)
+    return grad, stats, sigma, eloc

@@ -25,7 +25,7 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
-           "nqs_set_autotune", "nqs_set_tile_variant"]
+           "nqs_set_autotune", "nqs_set_tile_variant", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit"]
 
 
 class NqsError(RuntimeError):
@@ -91,7 +91,7 @@ def lib():
     L.nqs_grow_hidden.restype = ctypes.c_int
     L.nqs_grow_hidden.argtypes = [P(ModelDesc), vp, P(ModelDesc), vp, u64, ctypes.c_float, vp]
     L.nqs_sample.restype = ctypes.c_int
-    L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, vp, vp, vp, vp, vp, sz, vp]
+    L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, u64, vp, vp, vp, vp, vp, sz, vp]
     L.nqs_logpsi.restype = ctypes.c_int
     L.nqs_logpsi.argtypes = [P(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]
     L.nqs_local_energy.restype = ctypes.c_int
@@ -100,6 +100,12 @@ def lib():
     L.nqs_logpsi_grad.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, sz, vp]
     L.nqs_vmc_grad.restype = ctypes.c_int
     L.nqs_vmc_grad.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, vp, sz, vp]
+    L.nqs_energy_sums.restype = ctypes.c_int
+    L.nqs_energy_sums.argtypes = [vp, i64, vp, vp]
+    L.nqs_vmc_grad_global.restype = ctypes.c_int
+    L.nqs_vmc_grad_global.argtypes = [P(ModelDesc), vp, vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    L.nqs_set_wait_limit.restype = ctypes.c_int
+    L.nqs_set_wait_limit.argtypes = [i64]
     L.nqs_workspace_status.restype = ctypes.c_int
     L.nqs_workspace_status.argtypes = [vp, P(ctypes.c_int32), vp]
     L.nqs_vmc_step_batched_workspace_bytes.restype = sz
@@ -140,6 +146,12 @@ def _need(t, dtype, shape, name):
 def set_autotune(on):
     """Turn the tile-shape autotuner of the tensor-core kernels on or off."""
     lib().nqs_set_autotune(1 if on else 0)
+
+
+def set_wait_limit(polls):
+    """Bound of the tensor-core waits that may give up (None: the default);
+    0 makes every such wait give up at once (testing NQS_ETIMEOUT)."""
+    _check(lib().nqs_set_wait_limit(-1 if polls is None else int(polls)), "nqs_set_wait_limit")
 
 
 def set_tile_variant(variant):
@@ -196,8 +208,9 @@ def _ws(ws, device):
     return _default_ws[key]
 
 
-def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None):
-    """Autoregressive sampling: returns (sigma uint8 [B,N], logpsi [B], hcache [B,N,d_h] or None)."""
+def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None, sample_offset=0):
+    """Autoregressive sampling: returns (sigma uint8 [B,N], logpsi [B], hcache [B,N,d_h] or None).
+    sample_offset is the global index of the first sample (the Philox counter)."""
     dev = params.device
     N, d = desc.N, desc.d_h
     _need(params, torch.float32, (param_count(desc),), "params")
@@ -211,7 +224,7 @@ def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None)
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_SAMPLE))
     _check(lib().nqs_sample(ctypes.byref(desc), _ptr(params), int(B), int(seed), int(step),
-                            _ptr(uniforms), _ptr(sigma), _ptr(logpsi), _ptr(hc), wp, wn, _stream()),
+                            int(sample_offset), _ptr(uniforms), _ptr(sigma), _ptr(logpsi), _ptr(hc), wp, wn, _stream()),
            "nqs_sample")
     return sigma, logpsi, hc
 
@@ -278,6 +291,36 @@ def vmc_grad(desc, params, sigma, hcache, eloc, ws=None, grad=None, stats=None):
     wp, wn = w.get(workspace_bytes(desc, B, OP_VMC_GRAD))
     _check(lib().nqs_vmc_grad(ctypes.byref(desc), _ptr(params), _ptr(sigma), _ptr(hcache), _ptr(eloc),
                               int(B), _ptr(g), _ptr(st), wp, wn, _stream()), "nqs_vmc_grad")
+    return g, st
+
+
+def energy_sums(eloc, out=None):
+    """This rank's [sum E_loc, sum E_loc^2, B] (float64 [3]) for the data-parallel step."""
+    _need(eloc, torch.float32, (eloc.shape[0],), "eloc")
+    s = torch.empty((3,), dtype=torch.float64, device=eloc.device) if out is None else out
+    _check(lib().nqs_energy_sums(_ptr(eloc), int(eloc.shape[0]), _ptr(s), _stream()), "nqs_energy_sums")
+    return s
+
+
+def vmc_grad_global(desc, params, sigma, hcache, eloc, sums, ws=None, grad=None, stats=None):
+    """This rank's share of the VMC gradient (float64 [P]) with weights centred
+    by the global sums of all ranks; returns (grad, stats [3] = global mean,
+    variance, M)."""
+    dev = params.device
+    B = sigma.shape[0]
+    P = param_count(desc)
+    _need(params, torch.float32, (P,), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
+    _need(eloc, torch.float32, (B,), "eloc")
+    _need(sums, torch.float64, (3,), "sums")
+    g = torch.empty((P,), dtype=torch.float64, device=dev) if grad is None else grad
+    st = torch.empty((3,), dtype=torch.float64, device=dev) if stats is None else stats
+    w = _ws(ws, dev)
+    wp, wn = w.get(workspace_bytes(desc, B, OP_VMC_GRAD))
+    _check(lib().nqs_vmc_grad_global(ctypes.byref(desc), _ptr(params), _ptr(sigma), _ptr(hcache), _ptr(eloc),
+                                     int(B), _ptr(sums), _ptr(g), _ptr(st), wp, wn, _stream()),
+           "nqs_vmc_grad_global")
     return g, st
 
 

@@ -58,7 +58,15 @@ def test_host_checks_return_status_without_launching(L):
     fake = ctypes.c_void_p(0x1000)
     ws_unaligned = ctypes.c_void_p(0x1010)
     # null params
-    assert L.nqs_sample(ctypes.byref(desc), None, 4, 0, 0, None, fake, fake, None, fake, 1 << 20, None) == 1
+    assert L.nqs_sample(ctypes.byref(desc), None, 4, 0, 0, 0, None, fake, fake, None, fake, 1 << 20, None) == 1
+    # the global sample index must fit the 32-bit Philox counter word
+    assert L.nqs_sample(ctypes.byref(desc), fake, 4, 0, 0, (1 << 32) - 3, None, fake, fake, None, fake,
+                        1 << 20, None) == 1
+    # data-parallel calls: null pointers are rejected before any launch
+    assert L.nqs_energy_sums(None, 4, fake, None) == 1
+    assert L.nqs_energy_sums(fake, 4, None, None) == 1
+    assert L.nqs_vmc_grad_global(ctypes.byref(desc), fake, fake, fake, fake, 4, None, fake, fake, fake,
+                                 1 << 20, None) == 1
     # null descriptor
     assert L.nqs_logpsi(None, fake, fake, 4, fake, None, fake, 1 << 20, None) == 1
     # workspace too small / misaligned / missing
