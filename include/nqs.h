@@ -276,7 +276,13 @@ nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, u
  *     call's contents (the call resets what must start at zero).  Calls whose
  *     work overlaps on the GPU (other streams, other host threads) race on it:
  *     serialise them, e.g. on one stream.
- * Arguments as nqs_local_energy; cell must be NQS_GRU1D with NQS_FP32 and ham
+ *   - The looked-up address is kept per device number for the process: use
+ *     the device's primary context (the runtime's default) and do not call
+ *     cudaDeviceReset between calls.
+ *   - No device-side status is reported (there is no workspace status word to
+ *     read): a non-finite local energy shows only in eloc.
+ * Arguments as nqs_local_energy, with the same status for an invalid
+ * descriptor; a valid one must be NQS_GRU1D with NQS_FP32 and no mask, and ham
  * NQS_TFIM, otherwise NQS_EUNSUPPORTED. */
 #define NQS_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const float* params,

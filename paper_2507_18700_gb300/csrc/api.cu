@@ -163,6 +163,11 @@ T* at(void* ws, size_t off) {
 
 }  // namespace
 
+namespace nqs {
+// The descriptor checks of every workspace call, for the other entry points.
+nqs_status desc_status(const nqs_model_desc* desc) { return check_desc(desc, nullptr); }
+}  // namespace nqs
+
 // The gradient reverse sweep behind nqs_logpsi_grad, nqs_vmc_grad and
 // nqs_vmc_grad_global; T is the type of the reduced gradient (float or double).
 template <typename T>

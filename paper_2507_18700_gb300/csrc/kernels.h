@@ -9,6 +9,10 @@
 
 namespace nqs {
 
+// NQS_OK for a valid model descriptor, else the status every workspace call
+// returns for it (api.cu).
+nqs_status desc_status(const nqs_model_desc* desc);
+
 struct Fwd1Args {
   int64_t B;
   int N;

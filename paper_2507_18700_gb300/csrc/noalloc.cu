@@ -45,12 +45,15 @@ extern "C" nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const 
                                               const nqs_ham_desc* ham, const uint8_t* sigma,
                                               const float* hcache, int64_t B, float* eloc,
                                               void* stream) {
-  if (!desc || !ham || !params || B < 0) return NQS_EINVAL;
-  if (desc->cell != NQS_GRU1D || desc->Ly != 1 || desc->precision != NQS_FP32 || desc->sz0 != 0)
-    return desc->cell == NQS_GRU1D || desc->cell == NQS_GRU2D ? NQS_EUNSUPPORTED : NQS_EINVAL;
-  if (ham->kind != NQS_TFIM) return ham->kind == NQS_HEISENBERG ? NQS_EUNSUPPORTED : NQS_EINVAL;
+  // a bad descriptor gets the status nqs_local_energy gives it; a valid one
+  // outside this call's single path gets NQS_EUNSUPPORTED
+  const nqs_status ds = desc_status(desc);
+  if (ds != NQS_OK) return ds;
+  if (!ham || !params || B < 0) return NQS_EINVAL;
+  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return NQS_EINVAL;
+  if (desc->cell != NQS_GRU1D || desc->precision != NQS_FP32 || desc->sz0 != 0 || ham->kind != NQS_TFIM)
+    return NQS_EUNSUPPORTED;
   const int D = desc->d_h, N = desc->Lx;
-  if (N < 1 || !gru1d_supported(D)) return NQS_ESHAPE;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
   if ((reinterpret_cast<uintptr_t>(params) | reinterpret_cast<uintptr_t>(hcache)) & 15) return NQS_EINVAL;
   // scratch layout: [header | packed weights | dlog B*N | delta B*N]
@@ -83,7 +86,10 @@ extern "C" nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const 
   c.delta = delta;
   c.counter = &hdr->job_counter;
   if (gru1d_tfim_chains(c, img, D, st) != cudaSuccess) return NQS_ECUDA;
-  return tfim_eloc(sigma, dlog, delta, eloc, B, N, (float)ham->J, (float)ham->h, hdr, st) == cudaSuccess
+  // no status word is reported by this call (the caller cannot read the
+  // array), so the energy kernel gets none: a non-finite energy is only seen
+  // in eloc itself
+  return tfim_eloc(sigma, dlog, delta, eloc, B, N, (float)ham->J, (float)ham->h, nullptr, st) == cudaSuccess
              ? NQS_OK
              : NQS_ECUDA;
 }

@@ -106,3 +106,26 @@ def test_workspace_grows_with_batch(L):
     b = L.nqs_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), 4096, nqs.OP_LOCAL_ENERGY)
     assert 0 < a < b and a % 256 == 0 and b % 256 == 0
     assert L.nqs_workspace_bytes(ctypes.byref(desc), None, 100, nqs.OP_LOCAL_ENERGY) == 0
+
+
+def test_static_scratch_call_rejects_bad_descriptors_like_the_workspace_call(L):
+    """nqs_local_energy_static returns the status nqs_local_energy returns for
+    an invalid descriptor (both check on the host before any launch)."""
+    fake = ctypes.c_void_p(0x1000)
+    ham = nqs.tfim()
+    f = L.nqs_local_energy_static
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(nqs.ModelDesc), ctypes.c_void_p, ctypes.POINTER(nqs.HamDesc), ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    bad = [nqs.model_desc(1, 12, 1, 8, precision=5), nqs.ModelDesc(1, 12, 1, 8, 0, 2, 0),
+           nqs.model_desc(1, 12, 2, 8), nqs.model_desc(1, (1 << 20) + 1, 1, 8), nqs.model_desc(7, 12, 1, 8),
+           nqs.model_desc(1, 12, 1, 12), nqs.model_desc(1, 0, 1, 8)]
+    for desc in bad:
+        want = L.nqs_local_energy(ctypes.byref(desc), fake, ctypes.byref(ham), fake, fake, 4, fake, fake,
+                                  1 << 20, None)
+        assert want in (1, 2)
+        assert f(ctypes.byref(desc), fake, ctypes.byref(ham), fake, fake, 4, fake, None) == want, desc.precision
+    # valid descriptors off the call's single path
+    assert f(ctypes.byref(nqs.model_desc(1, 12, 1, 8, precision=nqs.BF16)), fake, ctypes.byref(ham), fake, fake,
+             4, fake, None) == 7
+    assert f(ctypes.byref(nqs.model_desc(2, 4, 4, 8)), fake, ctypes.byref(ham), fake, fake, 4, fake, None) == 7
