@@ -141,6 +141,10 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
  *            NULL: u_n of sample b is drawn from Philox4x32-10 with key = seed
  *            and counter = (n, sample_offset + b, step & 0xffffffff,
  *            step >> 32), u = (x0>>8)/2^24
+ *   step_dev device uint64 or NULL: when given, the Philox step is read from
+ *            it on the device instead of `step` (a captured CUDA graph of a
+ *            training step then draws fresh samples on every replay;
+ *            nqs_adam_step advances the counter)
  *   sample_offset  global index of this call's first sample: ranks that each
  *            draw B samples of one step pass rank * B, so the union of their
  *            samples is bitwise the one-rank batch (sample_offset + B <= 2^32,
@@ -151,9 +155,9 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
  *            conditional of site n (lattice order) -- the prefix cache that
  *            nqs_local_energy and the gradient calls read.            */
 nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B,
-                      uint64_t seed, uint64_t step, uint64_t sample_offset,
-                      const float* uniforms, uint8_t* sigma, float* logpsi, float* hcache,
-                      void* ws, size_t ws_bytes, void* stream);
+                      uint64_t seed, uint64_t step, const uint64_t* step_dev,
+                      uint64_t sample_offset, const float* uniforms, uint8_t* sigma,
+                      float* logpsi, float* hcache, void* ws, size_t ws_bytes, void* stream);
 
 /* Teacher-forced log psi(sigma) = 1/2 sum_n log p_n(sigma_n) (Eq. 1, pRNN).
  *   sigma  device [B, N] uint8 (read); logpsi device [B] float (written);
@@ -221,6 +225,73 @@ nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params,
                                const uint8_t* sigma, const float* hcache, const float* eloc,
                                int64_t B, const double* sums, double* grad, double* stats,
                                void* ws, size_t ws_bytes, void* stream);
+
+/* Training loop (Sec. II B, Sec. III; hyperparameters of Tab. III).
+ *
+ * Learning-rate schedules, with t the 0-based training step:
+ *   NQS_LR_CONSTANT  lr0
+ *   NQS_LR_STEP      lr0 for t < t_switch, lr1 from t_switch on (1D TFIM
+ *                    Adaptive: 5e-3, then 5e-4 from step 25,000)
+ *   NQS_LR_INVERSE   lr0 for t < t_switch, lr0 / (1 + (t - t_switch) / decay)
+ *                    from t_switch on (2D Heisenberg Static: t_switch = 0,
+ *                    decay = 5000; 2D Adaptive: t_switch = 100,000, reading
+ *                    the table's floor term as the switch to the decay in the
+ *                    second half of training) */
+enum { NQS_LR_CONSTANT = 1, NQS_LR_STEP = 2, NQS_LR_INVERSE = 3 };
+typedef struct {
+  int32_t kind;       /* NQS_LR_* */
+  int32_t reserved;
+  double lr0, lr1;
+  int64_t t_switch;
+  double decay;
+} nqs_lr_schedule;
+
+/* Adam hyperparameters (Kingma and Ba 2014): beta1, beta2 in [0, 1), eps > 0. */
+typedef struct {
+  double beta1, beta2, eps;
+} nqs_adam_desc;
+
+/* One Adam update of the flat parameters (Adam is the paper's optimiser,
+ * Sec. III and the hyperparameter appendix):
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,  k = t + 1,
+ *   params -= lr(t) (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps).
+ *   grad     device [P] float, or grad64 device [P] double (exactly one of
+ *            them non-NULL; grad64 takes the rank-summed gradient of
+ *            nqs_vmc_grad_global)
+ *   params, m, v  device [P] float (updated in place); m = v = 0 before the
+ *            first update.  On growth the moments are embedded like the
+ *            parameters: nqs_grow_hidden with eps = 0 (the appendix carries
+ *            parameters and momentum states over to the larger model).
+ *   t_dev    device uint64 step counter or NULL (then t is used): read for
+ *            the update and incremented after it, so the step of a captured
+ *            graph advances on every replay; nqs_sample may read the same
+ *            counter as its Philox step. */
+nqs_status nqs_adam_step(const float* grad, const double* grad64, float* params, float* m, float* v,
+                         int64_t P, const nqs_adam_desc* adam, const nqs_lr_schedule* sched,
+                         uint64_t t, uint64_t* t_dev, void* stream);
+
+/* log[t mod cap] = (t, stats[0], stats[1], stats[2]) with t = *t_dev: a
+ * per-step record of the energy statistics of a captured training step
+ * (log: device [cap, 4] double). */
+nqs_status nqs_record_stats(const double* stats, double* log, int64_t cap, const uint64_t* t_dev,
+                            void* stream);
+
+/* Final evaluation (Sec. III A, Tab. I and Tab. II: energies and variances
+ * from 10^6 samples after training): M samples drawn in chunks of `chunk`
+ * (global sample indices 0 .. M - 1 of the Philox stream (seed, step), so the
+ * result does not depend on the chunk size beyond FP64 rounding), their local
+ * energies, and FP64 statistics:
+ *   stats  device [5] double (written): mean E_loc, variance (1/M), M,
+ *          standard error of the mean sqrt(var / M), and the error of the
+ *          variance var sqrt(2 / (M - 1)) for Gaussian local energies (the
+ *          error bar of Tab. I);
+ *   ws     nqs_evaluate_workspace_bytes(desc, ham, chunk) bytes (it holds one
+ *          chunk's configurations and prefix cache); its status word is the
+ *          first status any chunk recorded.  M <= 2^32. */
+size_t nqs_evaluate_workspace_bytes(const nqs_model_desc* desc, const nqs_ham_desc* ham, int64_t chunk);
+nqs_status nqs_evaluate(const nqs_model_desc* desc, const float* params, const nqs_ham_desc* ham,
+                        int64_t M, int64_t chunk, uint64_t seed, uint64_t step, double* stats,
+                        void* ws, size_t ws_bytes, void* stream);
 
 /* One replica of a batched VMC step. */
 #define NQS_MAX_REPLICAS 16

@@ -324,8 +324,8 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
 }
 
 static nqs_status forward_common(const nqs_model_desc* desc, const float* params, int64_t B,
-                                 bool sample, uint64_t seed, uint64_t step, uint64_t b0,
-                                 const float* uniforms,
+                                 bool sample, uint64_t seed, uint64_t step, const uint64_t* step_dev,
+                                 uint64_t b0, const float* uniforms,
                                  const uint8_t* sigma_in, uint8_t* sigma_out, float* logpsi,
                                  float* hcache, void* ws, size_t ws_bytes, void* stream) {
   Dims d;
@@ -357,6 +357,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     f.seed = seed;
     f.step = step;
     f.b0 = b0;
+    f.step_dev = step_dev;
     f.logpsi = logpsi;
     f.hcache = hcache;
     f.colbuf = at<float>(ws, L.a);
@@ -376,6 +377,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     a.seed = seed;
     a.step = step;
     a.b0 = b0;
+    a.step_dev = step_dev;
     a.logpsi = logpsi;
     a.hcache = hcache;
     a.colbuf = at<float>(ws, L.a);
@@ -396,6 +398,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
     t.seed = seed;
     t.step = step;
     t.b0 = b0;
+    t.step_dev = step_dev;
     t.logpsi = logpsi;
     t.hcache = hcache;
     t.hdr = static_cast<WsHeader*>(ws);
@@ -410,6 +413,7 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   a.seed = seed;
   a.step = step;
   a.b0 = b0;
+  a.step_dev = step_dev;
   a.logpsi = logpsi;
   a.hcache = hcache;
   a.hdr = static_cast<WsHeader*>(ws);
@@ -417,16 +421,16 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
 }
 
 nqs_status nqs_sample(const nqs_model_desc* desc, const float* params, int64_t B, uint64_t seed,
-                      uint64_t step, uint64_t sample_offset, const float* uniforms, uint8_t* sigma,
-                      float* logpsi, float* hcache, void* ws, size_t ws_bytes, void* stream) {
-  return forward_common(desc, params, B, true, seed, step, sample_offset, uniforms, nullptr, sigma, logpsi,
-                        hcache, ws, ws_bytes, stream);
+                      uint64_t step, const uint64_t* step_dev, uint64_t sample_offset, const float* uniforms,
+                      uint8_t* sigma, float* logpsi, float* hcache, void* ws, size_t ws_bytes, void* stream) {
+  return forward_common(desc, params, B, true, seed, step, step_dev, sample_offset, uniforms, nullptr, sigma,
+                        logpsi, hcache, ws, ws_bytes, stream);
 }
 
 nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
                       int64_t B, float* logpsi, float* hcache, void* ws, size_t ws_bytes,
                       void* stream) {
-  return forward_common(desc, params, B, false, 0, 0, 0, nullptr, sigma, nullptr, logpsi, hcache, ws,
+  return forward_common(desc, params, B, false, 0, 0, nullptr, 0, nullptr, sigma, nullptr, logpsi, hcache, ws,
                         ws_bytes, stream);
 }
 
@@ -622,6 +626,110 @@ nqs_status nqs_set_wait_limit(int64_t polls) {
       tc2d_grad_set_wait_polls(v) != cudaSuccess)
     return NQS_ECUDA;
   return NQS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Training loop and final evaluation.
+// ---------------------------------------------------------------------------
+static bool valid_schedule(const nqs_lr_schedule* s) {
+  if (!s || s->kind < NQS_LR_CONSTANT || s->kind > NQS_LR_INVERSE) return false;
+  if (!(s->lr0 >= 0.0) || (s->kind == NQS_LR_STEP && !(s->lr1 >= 0.0))) return false;
+  if (s->kind == NQS_LR_INVERSE && !(s->decay > 0.0)) return false;
+  return s->t_switch >= 0;
+}
+
+nqs_status nqs_adam_step(const float* grad, const double* grad64, float* params, float* m, float* v, int64_t P,
+                         const nqs_adam_desc* adam, const nqs_lr_schedule* sched, uint64_t t, uint64_t* t_dev,
+                         void* stream) {
+  if ((grad == nullptr) == (grad64 == nullptr)) return NQS_EINVAL;
+  if (!params || !m || !v || P < 1 || !adam || !valid_schedule(sched)) return NQS_EINVAL;
+  if (!(adam->beta1 >= 0.0 && adam->beta1 < 1.0 && adam->beta2 >= 0.0 && adam->beta2 < 1.0 && adam->eps > 0.0))
+    return NQS_EINVAL;
+  AdamArgs a{};
+  a.beta1 = adam->beta1;
+  a.beta2 = adam->beta2;
+  a.eps = adam->eps;
+  a.t = (int64_t)t;
+  a.sched.kind = sched->kind - NQS_LR_CONSTANT;
+  a.sched.lr0 = sched->lr0;
+  a.sched.lr1 = sched->lr1;
+  a.sched.t_switch = sched->t_switch;
+  a.sched.decay = sched->decay;
+  return cuda_status(adam_update(grad, grad64, params, m, v, P, a, t_dev, static_cast<cudaStream_t>(stream)));
+}
+
+nqs_status nqs_record_stats(const double* stats, double* log, int64_t cap, const uint64_t* t_dev, void* stream) {
+  if (!stats || !log || cap < 1 || !t_dev) return NQS_EINVAL;
+  return cuda_status(record_stats(stats, log, cap, t_dev, static_cast<cudaStream_t>(stream)));
+}
+
+namespace {
+struct EvalLayout {
+  size_t sums, sigma, logpsi, hcache, eloc, inner, inner_bytes, total;
+};
+EvalLayout eval_layout(const Dims& d, const nqs_ham_desc* ham, int64_t chunk) {
+  EvalLayout L{};
+  size_t off = sizeof(WsHeader);
+  L.sums = off;
+  off += 256;
+  L.sigma = off;
+  off += align256((size_t)chunk * d.N);
+  L.logpsi = off;
+  off += align256((size_t)chunk * sizeof(float));
+  L.hcache = off;
+  off += align256((size_t)chunk * d.N * d.d * sizeof(float));
+  L.eloc = off;
+  off += align256((size_t)chunk * sizeof(float));
+  L.inner = off;
+  const Layout ls = layout(d, chunk, NQS_OP_SAMPLE), le = layout(d, chunk, NQS_OP_LOCAL_ENERGY);
+  L.inner_bytes = ls.total > le.total ? ls.total : le.total;
+  L.total = off + L.inner_bytes;
+  (void)ham;
+  return L;
+}
+}  // namespace
+
+size_t nqs_evaluate_workspace_bytes(const nqs_model_desc* desc, const nqs_ham_desc* ham, int64_t chunk) {
+  Dims d;
+  if (check_desc(desc, &d) != NQS_OK || !ham || chunk < 1) return 0;
+  return eval_layout(d, ham, chunk).total;
+}
+
+nqs_status nqs_evaluate(const nqs_model_desc* desc, const float* params, const nqs_ham_desc* ham, int64_t M,
+                        int64_t chunk, uint64_t seed, uint64_t step, double* stats, void* ws, size_t ws_bytes,
+                        void* stream) {
+  Dims d;
+  nqs_status r = check_desc(desc, &d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(d)) != NQS_OK) return r;
+  if (!params || !ham || !stats || M < 1 || chunk < 1 || (uint64_t)M > ((uint64_t)1 << 32)) return NQS_EINVAL;
+  if (misaligned(params)) return NQS_EINVAL;
+  if (chunk > M) chunk = M;
+  const EvalLayout L = eval_layout(d, ham, chunk);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < L.total) return NQS_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
+  double* sums = at<double>(ws, L.sums);
+  if (cudaMemsetAsync(sums, 0, 3 * sizeof(double), st) != cudaSuccess) return NQS_ECUDA;
+  uint8_t* sigma = at<uint8_t>(ws, L.sigma);
+  float* logpsi = at<float>(ws, L.logpsi);
+  float* hcache = at<float>(ws, L.hcache);
+  float* eloc = at<float>(ws, L.eloc);
+  void* inner = at<void>(ws, L.inner);
+  for (int64_t off = 0; off < M; off += chunk) {
+    const int64_t B = M - off < chunk ? M - off : chunk;
+    if ((r = nqs_sample(desc, params, B, seed, step, nullptr, (uint64_t)off, nullptr, sigma, logpsi, hcache, inner,
+                        L.inner_bytes, stream)) != NQS_OK)
+      return r;
+    if (status_merge(static_cast<const WsHeader*>(inner), static_cast<WsHeader*>(ws), st) != cudaSuccess)
+      return NQS_ECUDA;
+    if ((r = nqs_local_energy(desc, params, ham, sigma, hcache, B, eloc, inner, L.inner_bytes, stream)) != NQS_OK)
+      return r;
+    if (status_merge(static_cast<const WsHeader*>(inner), static_cast<WsHeader*>(ws), st) != cudaSuccess)
+      return NQS_ECUDA;
+    if (energy_sums_acc(eloc, B, sums, st) != cudaSuccess) return NQS_ECUDA;
+  }
+  return cuda_status(eval_stats(sums, stats, st));
 }
 
 // ---------------------------------------------------------------------------

@@ -119,7 +119,7 @@ __device__ __forceinline__ void gru1d_forward_body(const float* __restrict__ img
       if (valid) {
         if constexpr (SAMPLE) {
           const float u = a.uniforms ? a.uniforms[b * N + n]
-                                     : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + b), (uint32_t)n);
+                                     : sampling_uniform(a.seed, a.step_dev ? *a.step_dev : a.step, (uint32_t)(a.b0 + b), (uint32_t)n);
           s = u < sigmoid_acc(d) ? 0 : 1;
           if (ug == 0) a.sigma_out[b * N + n] = (uint8_t)s;
         } else {

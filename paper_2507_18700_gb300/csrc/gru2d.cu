@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(NT) gru2d_engine_kernel(const float* __restric
             const bool forced_dn = a.sz0 && n_up[i] >= (N >> 1);
             const bool forced_up = a.sz0 && (t[i] - n_up[i]) >= (N >> 1);
             const float u = a.uniforms ? a.uniforms[jb[i] * N + t[i]]
-                                       : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + jb[i]), (uint32_t)t[i]);
+                                       : sampling_uniform(a.seed, a.step_dev ? *a.step_dev : a.step, (uint32_t)(a.b0 + jb[i]), (uint32_t)t[i]);
             s = forced_dn ? 1 : forced_up ? 0 : (u < sigmoid_acc(d) ? 0 : 1);
             if (ug == 0) a.sigma_out[jb[i] * N + k] = (uint8_t)s;
           } else {

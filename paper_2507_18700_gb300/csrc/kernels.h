@@ -21,6 +21,7 @@ struct Fwd1Args {
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step (read on the device) or null: step
   float* logpsi;
   float* hcache;             // nullable
   WsHeader* hdr;
@@ -66,6 +67,7 @@ struct Eng2Args {
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step (read on the device) or null: step
   float* logpsi;             // sampling / teacher forcing
   float* hcache;             // written by sampling / teacher forcing, read by chains
   float* colbuf;             // [slots, Lx, d] column buffers
@@ -97,6 +99,7 @@ struct Tc2Fwd {
   const float* uniforms;     // nullable
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step (read on the device) or null: step
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // nullable
   float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
@@ -173,6 +176,7 @@ struct Tc1Args {
   const float* uniforms;     // sampling, nullable
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step (read on the device) or null: step
   float* logpsi;
   float* hcache;             // written by sampling / teacher forcing (nullable), read by chains
   const float* dlog;         // chains
@@ -250,6 +254,27 @@ cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int6
                                  cudaStream_t st);
 cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, double* grad,
                                  cudaStream_t st);
+
+// training loop and final evaluation (train.cu)
+struct LrSchedule {
+  int kind;            // 0 constant, 1 step at t_switch, 2 inverse decay from t_switch
+  double lr0, lr1;
+  int64_t t_switch;
+  double decay;
+};
+struct AdamArgs {
+  double beta1, beta2, eps;
+  int64_t t;           // step when no device counter is given
+  LrSchedule sched;
+};
+// Adam update from grad32 or grad64 (one of them non-null); t_dev (nullable)
+// holds the step and is incremented after the update
+cudaError_t adam_update(const float* grad32, const double* grad64, float* params, float* m, float* v, int64_t P,
+                        const AdamArgs& a, uint64_t* t_dev, cudaStream_t st);
+cudaError_t record_stats(const double* stats, double* log, int64_t cap, const uint64_t* t_dev, cudaStream_t st);
+cudaError_t energy_sums_acc(const float* eloc, int64_t B, double* sums, cudaStream_t st);
+cudaError_t eval_stats(const double* sums, double* stats, cudaStream_t st);
+cudaError_t status_merge(const WsHeader* from, WsHeader* into, cudaStream_t st);
 
 // bound of the tensor-core waits that may give up, per translation unit
 uint32_t tc_default_wait_polls();

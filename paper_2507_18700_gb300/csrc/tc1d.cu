@@ -353,7 +353,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     float dl = 0.0f, uni = 0.0f;
     if (active) {
       if constexpr (MODE == 0) {
-        uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
+        uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step_dev ? *a.step_dev : a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
       } else {
         s_t = a.sigma[b * N + t] ? 1 : 0;
         if constexpr (MODE == 2) dl = a.dlog[b * N + t];

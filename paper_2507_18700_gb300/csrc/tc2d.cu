@@ -201,6 +201,7 @@ struct Tc2Args {
   const float* uniforms;
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step or null
   float* logpsi;             // nullable in teacher forcing
   float* hcache;             // written by sampling / teacher forcing (nullable); read by chains
   float* colbuf;             // [CTAs x 128 rows, Lx, d] latest FP32 state of every lattice column
@@ -483,7 +484,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     float uni = 0.0f;
     if (MODE == 0 && active) {
-      uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
+      uni = a.uniforms ? a.uniforms[b * N + t] : sampling_uniform(a.seed, a.step_dev ? *a.step_dev : a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
     }
     if (!tc::mbar_wait(&mbar[0], ph0, wlim)) {
       timed_out = true;
@@ -941,6 +942,7 @@ cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sampl
   a.seed = f.seed;
   a.step = f.step;
   a.b0 = f.b0;
+  a.step_dev = f.step_dev;
   a.logpsi = f.logpsi;
   a.hcache = f.hcache;
   a.colbuf = f.colbuf;

@@ -25,7 +25,8 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
-           "nqs_set_autotune", "nqs_set_tile_variant", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit"]
+           "nqs_set_autotune", "nqs_set_tile_variant", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit", "nqs_adam_step",
+           "nqs_record_stats", "nqs_evaluate_workspace_bytes", "nqs_evaluate"]
 
 
 class NqsError(RuntimeError):
@@ -47,6 +48,34 @@ class ModelDesc(ctypes.Structure):
 class HamDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("marshall", ctypes.c_int32), ("J", ctypes.c_double),
                 ("h", ctypes.c_double)]
+
+
+class LrSchedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lr0", ctypes.c_double),
+                ("lr1", ctypes.c_double), ("t_switch", ctypes.c_int64), ("decay", ctypes.c_double)]
+
+
+class AdamDesc(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+LR_CONSTANT, LR_STEP, LR_INVERSE = 1, 2, 3
+
+
+def lr_constant(lr):
+    return LrSchedule(LR_CONSTANT, 0, lr, 0.0, 0, 1.0)
+
+
+def lr_step(lr0, lr1, t_switch):
+    return LrSchedule(LR_STEP, 0, lr0, lr1, int(t_switch), 1.0)
+
+
+def lr_inverse(lr0, decay, t_switch=0):
+    return LrSchedule(LR_INVERSE, 0, lr0, 0.0, int(t_switch), float(decay))
+
+
+def adam_desc(beta1=0.9, beta2=0.999, eps=1e-8):
+    return AdamDesc(beta1, beta2, eps)
 
 
 class Replica(ctypes.Structure):
@@ -91,7 +120,15 @@ def lib():
     L.nqs_grow_hidden.restype = ctypes.c_int
     L.nqs_grow_hidden.argtypes = [P(ModelDesc), vp, P(ModelDesc), vp, u64, ctypes.c_float, vp]
     L.nqs_sample.restype = ctypes.c_int
-    L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, u64, vp, vp, vp, vp, vp, sz, vp]
+    L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, vp, u64, vp, vp, vp, vp, vp, sz, vp]
+    L.nqs_adam_step.restype = ctypes.c_int
+    L.nqs_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, P(AdamDesc), P(LrSchedule), u64, vp, vp]
+    L.nqs_record_stats.restype = ctypes.c_int
+    L.nqs_record_stats.argtypes = [vp, vp, i64, vp, vp]
+    L.nqs_evaluate_workspace_bytes.restype = sz
+    L.nqs_evaluate_workspace_bytes.argtypes = [P(ModelDesc), P(HamDesc), i64]
+    L.nqs_evaluate.restype = ctypes.c_int
+    L.nqs_evaluate.argtypes = [P(ModelDesc), vp, P(HamDesc), i64, i64, u64, u64, vp, vp, sz, vp]
     L.nqs_logpsi.restype = ctypes.c_int
     L.nqs_logpsi.argtypes = [P(ModelDesc), vp, vp, i64, vp, vp, vp, sz, vp]
     L.nqs_local_energy.restype = ctypes.c_int
@@ -208,22 +245,30 @@ def _ws(ws, device):
     return _default_ws[key]
 
 
-def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None, sample_offset=0):
+def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None, sample_offset=0,
+           step_dev=None, out=None):
     """Autoregressive sampling: returns (sigma uint8 [B,N], logpsi [B], hcache [B,N,d_h] or None).
-    sample_offset is the global index of the first sample (the Philox counter)."""
+    sample_offset is the global index of the first sample (the Philox counter);
+    step_dev (a CUDA uint64/int64 tensor of one element) replaces `step` by a
+    device counter; out = (sigma, logpsi) reuses output buffers."""
     dev = params.device
     N, d = desc.N, desc.d_h
     _need(params, torch.float32, (param_count(desc),), "params")
     if uniforms is not None:
         _need(uniforms, torch.float32, (B, N), "uniforms")
-    sigma = torch.empty((B, N), dtype=torch.uint8, device=dev)
-    logpsi = torch.empty((B,), dtype=torch.float32, device=dev)
+    if out is None:
+        sigma = torch.empty((B, N), dtype=torch.uint8, device=dev)
+        logpsi = torch.empty((B,), dtype=torch.float32, device=dev)
+    else:
+        sigma, logpsi = out
+        _need(sigma, torch.uint8, (B, N), "sigma")
+        _need(logpsi, torch.float32, (B,), "logpsi")
     hc = torch.empty((B, N, d), dtype=torch.float32, device=dev) if hcache is True else hcache
     if hc is not None and hcache is not True:
         _need(hc, torch.float32, (B, N, d), "hcache")
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_SAMPLE))
-    _check(lib().nqs_sample(ctypes.byref(desc), _ptr(params), int(B), int(seed), int(step),
+    _check(lib().nqs_sample(ctypes.byref(desc), _ptr(params), int(B), int(seed), int(step), _ptr(step_dev),
                             int(sample_offset), _ptr(uniforms), _ptr(sigma), _ptr(logpsi), _ptr(hc), wp, wn, _stream()),
            "nqs_sample")
     return sigma, logpsi, hc
@@ -322,6 +367,39 @@ def vmc_grad_global(desc, params, sigma, hcache, eloc, sums, ws=None, grad=None,
                                      int(B), _ptr(sums), _ptr(g), _ptr(st), wp, wn, _stream()),
            "nqs_vmc_grad_global")
     return g, st
+
+
+def adam_step(params, m, v, grad, adam, sched, t=0, t_dev=None):
+    """One Adam update in place (grad float32 or float64); t_dev advances."""
+    P = params.numel()
+    _need(params, torch.float32, (P,), "params")
+    _need(m, torch.float32, (P,), "m")
+    _need(v, torch.float32, (P,), "v")
+    g32 = grad if grad.dtype == torch.float32 else None
+    g64 = grad if grad.dtype == torch.float64 else None
+    _need(grad, grad.dtype if grad.dtype in (torch.float32, torch.float64) else torch.float32, (P,), "grad")
+    _check(lib().nqs_adam_step(_ptr(g32), _ptr(g64), _ptr(params), _ptr(m), _ptr(v), int(P), ctypes.byref(adam),
+                               ctypes.byref(sched), int(t), _ptr(t_dev), _stream()), "nqs_adam_step")
+
+
+def record_stats(stats, log, t_dev):
+    _check(lib().nqs_record_stats(_ptr(stats), _ptr(log), int(log.shape[0]), _ptr(t_dev), _stream()),
+           "nqs_record_stats")
+
+
+def evaluate(desc, params, ham, M, chunk=65536, seed=0, step=0, ws=None):
+    """Final evaluation: float64 [5] = mean E_loc, variance, M, error of the mean, error of the variance."""
+    dev = params.device
+    _need(params, torch.float32, (param_count(desc),), "params")
+    n = lib().nqs_evaluate_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), int(min(chunk, M)))
+    if n == 0:
+        raise NqsError(1, "nqs_evaluate_workspace_bytes")
+    st = torch.empty((5,), dtype=torch.float64, device=dev)
+    w = _ws(ws, dev)
+    wp, wn = w.get(n)
+    _check(lib().nqs_evaluate(ctypes.byref(desc), _ptr(params), ctypes.byref(ham), int(M), int(chunk), int(seed),
+                              int(step), _ptr(st), wp, wn, _stream()), "nqs_evaluate")
+    return st
 
 
 def grow_hidden(small, p_small, big, seed=2, eps=1e-3):

@@ -58,10 +58,30 @@ def test_host_checks_return_status_without_launching(L):
     fake = ctypes.c_void_p(0x1000)
     ws_unaligned = ctypes.c_void_p(0x1010)
     # null params
-    assert L.nqs_sample(ctypes.byref(desc), None, 4, 0, 0, 0, None, fake, fake, None, fake, 1 << 20, None) == 1
+    assert L.nqs_sample(ctypes.byref(desc), None, 4, 0, 0, None, 0, None, fake, fake, None, fake, 1 << 20, None) == 1
     # the global sample index must fit the 32-bit Philox counter word
-    assert L.nqs_sample(ctypes.byref(desc), fake, 4, 0, 0, (1 << 32) - 3, None, fake, fake, None, fake,
+    assert L.nqs_sample(ctypes.byref(desc), fake, 4, 0, 0, None, (1 << 32) - 3, None, fake, fake, None, fake,
                         1 << 20, None) == 1
+    # training and evaluation calls: bad arguments are rejected on the host
+    adam, sched = nqs.adam_desc(), nqs.lr_constant(1e-3)
+    assert L.nqs_adam_step(fake, fake, fake, fake, fake, 10, ctypes.byref(adam), ctypes.byref(sched), 0, None,
+                           None) == 1                      # both gradient pointers
+    assert L.nqs_adam_step(None, None, fake, fake, fake, 10, ctypes.byref(adam), ctypes.byref(sched), 0, None,
+                           None) == 1                      # no gradient
+    bad_sched = nqs.lr_inverse(1e-3, 0.0)
+    assert L.nqs_adam_step(fake, None, fake, fake, fake, 10, ctypes.byref(adam), ctypes.byref(bad_sched), 0, None,
+                           None) == 1
+    bad_adam = nqs.adam_desc(beta1=1.0)
+    assert L.nqs_adam_step(fake, None, fake, fake, fake, 10, ctypes.byref(bad_adam), ctypes.byref(sched), 0, None,
+                           None) == 1
+    assert L.nqs_record_stats(fake, fake, 0, fake, None) == 1
+    ham = nqs.tfim()
+    assert L.nqs_evaluate_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), 0) == 0
+    assert L.nqs_evaluate_workspace_bytes(ctypes.byref(desc), ctypes.byref(ham), 1000) > 1000 * 12 * 8 * 4
+    assert L.nqs_evaluate(ctypes.byref(desc), fake, ctypes.byref(ham), 0, 10, 0, 0, fake, fake, 1 << 30,
+                          None) == 1                       # no samples
+    assert L.nqs_evaluate(ctypes.byref(desc), fake, ctypes.byref(ham), 100, 10, 0, 0, fake, fake, 16,
+                          None) == 3                       # workspace too small
     # data-parallel calls: null pointers are rejected before any launch
     assert L.nqs_energy_sums(None, 4, fake, None) == 1
     assert L.nqs_energy_sums(fake, 4, None, None) == 1
