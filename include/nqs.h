@@ -81,7 +81,7 @@ typedef enum {
 
 enum { NQS_GRU1D = 1, NQS_GRU2D = 2 };
 enum { NQS_FP32 = 0, NQS_BF16 = 1 };
-enum { NQS_TFIM = 1, NQS_HEISENBERG = 2 };
+enum { NQS_TFIM = 1, NQS_HEISENBERG = 2, NQS_LRTFIM = 3 };
 enum {
   NQS_OP_SAMPLE = 1,
   NQS_OP_LOGPSI = 2,
@@ -107,10 +107,11 @@ typedef struct {
 } nqs_model_desc;
 
 typedef struct {
-  int32_t kind;       /* NQS_TFIM (1D GRU) | NQS_HEISENBERG (2D GRU) */
+  int32_t kind;       /* NQS_TFIM | NQS_LRTFIM (1D GRU) | NQS_HEISENBERG (2D GRU) */
   int32_t marshall;   /* Heisenberg: 1 = Marshall-rotated exchange (-J/2) */
   double J;           /* coupling J */
-  double h;           /* TFIM transverse field Gamma (ignored for Heisenberg) */
+  double h;           /* TFIM / long-range TFIM transverse field Gamma (ignored for Heisenberg) */
+  double alpha;       /* long-range TFIM: coupling J / |i - j|^alpha, alpha >= 0 (may be +inf) */
 } nqs_ham_desc;
 
 /* Number of float32 parameters of the flat layout above; 0 if desc is invalid. */
@@ -169,6 +170,10 @@ nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params,
 /* Local energies E_loc(sigma) = sum_sigma' H[sigma, sigma'] psi(sigma')/psi(sigma):
  *   NQS_TFIM (Eq. tfim, open chain, GRU1D):
  *     -J sum s_i s_{i+1} - h sum_i psi(flip_i sigma)/psi(sigma);
+ *   NQS_LRTFIM (the long-range TFIM of Sec. III C, open chain, GRU1D):
+ *     -J sum_{i<j} s_i s_j / |i - j|^alpha - h sum_i psi(flip_i sigma)/psi(sigma)
+ *     (the O(N^2) diagonal summed in FP64 per sample; the flips run the
+ *     prefix-cached chains of the TFIM);
  *   NQS_HEISENBERG (Eq. heisenberg, open square lattice, GRU2D, Pauli/4):
  *     per bond +J/4 (parallel) or -J/4 + x exp(Delta) (antiparallel), with
  *     x = -J/2 when marshall = 1 (Marshall rotation, Sec. III B), +J/2 otherwise.

@@ -3,6 +3,7 @@
 * ``all_configs``          every configuration of N spins (lattice order)
 * ``tfim_hamiltonian``     sparse Eq. (tfim) in the sigma basis
 * ``heisenberg_hamiltonian`` sparse Eq. (heisenberg), optionally Marshall-rotated
+* ``lr_tfim_hamiltonian``  sparse long-range TFIM (Sec. III C)
 * ``ground_state``         exact diagonalisation (scipy eigsh / dense eigh)
 * ``tfim_free_fermion``    ground energy of the open TFIM from free fermions:
                            E0 = -1/2 sum_k eps_k, with eps_k the singular values
@@ -44,6 +45,27 @@ def tfim_hamiltonian(N, J, Gamma):
     rows = [idx]
     cols = [idx]
     vals = [diag.astype(np.float64)]
+    for k in range(N):
+        rows.append(idx)
+        cols.append(idx ^ (1 << k))
+        vals.append(np.full(dim, -Gamma, dtype=np.float64))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(dim, dim))
+
+
+def lr_tfim_hamiltonian(N, alpha, J, Gamma):
+    """Sparse long-range TFIM (Sec. III C) in the sigma basis."""
+    dim = 2 ** N
+    idx = np.arange(dim, dtype=np.int64)
+    bits = (idx[:, None] >> np.arange(N)[None, :]) & 1
+    z = 1 - 2 * bits
+    diag = np.zeros(dim)
+    for i in range(N):
+        for j in range(i + 1, N):
+            diag -= J * z[:, i] * z[:, j] / float(j - i) ** alpha
+    rows = [idx]
+    cols = [idx]
+    vals = [diag]
     for k in range(N):
         rows.append(idx)
         cols.append(idx ^ (1 << k))

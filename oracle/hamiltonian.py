@@ -10,6 +10,10 @@ TFIM, Eq. (tfim), open chain:
   E_loc = -J sum_i s_i s_{i+1} - Gamma sum_i psi(flip_i sigma) / psi(sigma),
   with s = +1 for sigma = 0 (spin up) and -1 for sigma = 1.
 
+Long-range TFIM, Sec. III C, open chain:
+  H = -J sum_{i<j} Z_i Z_j / |i - j|^alpha - Gamma sum_i X_i
+  (the paper's J = 1; alpha -> infinity is the nearest-neighbour chain).
+
 Heisenberg, Eq. (heisenberg), open Lx x Ly square lattice, Pauli matrices with
 the prefactor 1/4 (so J S_i.S_j per bond):
   diagonal  +J/4 for a parallel bond, -J/4 for an antiparallel bond;
@@ -65,3 +69,22 @@ def heisenberg_local_energy(Lx, Ly, J, marshall, sigma, logpsi_fn):
         ratio = np.where(par, 0.0, np.exp(np.where(par, 0.0, lp_s[:, t] - lp)))
         eloc += np.where(par, 0.25 * J, -0.25 * J + off * ratio)
     return eloc
+
+
+def lr_tfim_local_energy(N, alpha, J, Gamma, sigma, logpsi_fn):
+    """E_loc of the long-range TFIM (Sec. III C), open chain:
+    H = -J sum_{i<j} Z_i Z_j / |i - j|^alpha - Gamma sum_i X_i; the flips as
+    in the TFIM, the diagonal summed over every pair."""
+    sigma = np.asarray(sigma, dtype=np.int64)
+    B = sigma.shape[0]
+    s = 1 - 2 * sigma
+    diag = np.zeros(B)
+    for i in range(N):
+        for j in range(i + 1, N):
+            diag -= J * s[:, i] * s[:, j] / float(j - i) ** alpha
+    lp = logpsi_fn(sigma)
+    flipped = np.repeat(sigma[:, None, :], N, axis=1)
+    idx = np.arange(N)
+    flipped[:, idx, idx] = 1 - flipped[:, idx, idx]
+    lp_f = logpsi_fn(flipped.reshape(B * N, N)).reshape(B, N)
+    return diag - Gamma * np.exp(lp_f - lp[:, None]).sum(axis=1)

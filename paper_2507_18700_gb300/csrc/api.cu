@@ -444,8 +444,9 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if (!ham || !params || B < 0) return NQS_EINVAL;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
   if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
-  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG) return NQS_EINVAL;
-  if (ham->kind == NQS_TFIM && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
+  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG && ham->kind != NQS_LRTFIM) return NQS_EINVAL;
+  if (ham->kind == NQS_LRTFIM && !(ham->alpha >= 0.0)) return NQS_EINVAL;
+  if ((ham->kind == NQS_TFIM || ham->kind == NQS_LRTFIM) && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
   if (ham->kind == NQS_HEISENBERG && d.cell != NQS_GRU2D) return NQS_EUNSUPPORTED;
   if (ham->kind == NQS_HEISENBERG && (d.Lx < 2 && d.Ly < 2)) return NQS_ESHAPE;
   const Layout L = layout(d, B, NQS_OP_LOCAL_ENERGY);
@@ -552,6 +553,8 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
     c.counter = &hdr->job_counter;
     if (gru1d_tfim_chains(c, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
   }
+  if (ham->kind == NQS_LRTFIM)
+    return cuda_status(lrtfim_eloc(sigma, dlog, delta, eloc, B, d.N, ham->J, ham->h, ham->alpha, hdr, st));
   return cuda_status(tfim_eloc(sigma, dlog, delta, eloc, B, d.N, (float)ham->J, (float)ham->h, hdr, st));
 }
 
@@ -743,7 +746,8 @@ static nqs_status check_replicas(int R, const nqs_replica* reps, Dims* dims) {
     if (s != NQS_OK) return s;
     if (dims[i].cell != NQS_GRU1D || dims[i].precision != NQS_FP32 || dims[i].sz0) return NQS_EUNSUPPORTED;
     if (!batched_supported_d(dims[i].d)) return NQS_EUNSUPPORTED;
-    if (r.ham.kind != NQS_TFIM) return r.ham.kind == NQS_HEISENBERG ? NQS_EUNSUPPORTED : NQS_EINVAL;
+    if (r.ham.kind != NQS_TFIM)
+      return r.ham.kind == NQS_HEISENBERG || r.ham.kind == NQS_LRTFIM ? NQS_EUNSUPPORTED : NQS_EINVAL;
     if (r.B < 1) return NQS_EINVAL;
   }
   return NQS_OK;

@@ -76,6 +76,46 @@ __global__ void tfim_eloc_kernel(const uint8_t* __restrict__ sigma, const float*
   }
 }
 
+// Long-range TFIM (Sec. III C): E_loc = -J sum_{i<j} s_i s_j / (j - i)^alpha
+// - Gamma sum_i exp(Delta_i); one warp per sample.  The diagonal is summed by
+// distance r = j - i, c_r = sum_i s_i s_{i+r}, in FP64 (N^2 / 2 products of
+// size up to 1 would lose the small couplings' share in FP32).
+__global__ void lrtfim_eloc_kernel(const uint8_t* __restrict__ sigma, const float* __restrict__ dlog,
+                                   const float* __restrict__ delta, float* __restrict__ eloc,
+                                   int64_t B, int N, double J, double Gamma, double alpha, WsHeader* hdr) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < B;
+       b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const uint8_t* sg = sigma + b * N;
+    double diag = 0.0;
+    for (int r = 1 + lane; r < N; r += 32) {
+      int c = 0;
+      for (int i = 0; i + r < N; ++i) c += ((sg[i] ? 1 : 0) == (sg[i + r] ? 1 : 0)) ? 1 : -1;
+      // r^-alpha (1 at r = 1 for every alpha, also alpha = +inf: the NN chain)
+      diag += (double)c * (r == 1 ? 1.0 : exp2(-alpha * log2((double)r)));
+    }
+    float off = 0.0f;
+    for (int n = lane; n < N; n += 32) {
+      float dl;
+      if (n + 1 < N) {
+        dl = delta[b * N + n];
+      } else {
+        const float d = dlog[b * N + n];
+        dl = 0.5f * ((sg[n] ? 1 : 0) == 0 ? -d : d);
+      }
+      off += expf(dl);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diag += __shfl_xor_sync(0xffffffffu, diag, o);
+    off = group_sum<32>(off);
+    if (lane == 0) {
+      const float e = (float)(-J * diag - Gamma * (double)off);
+      eloc[b] = e;
+      if (!isfinite(e)) flag_status(hdr, NQS_ENONFINITE);
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Kernels: one model per launch.
 // ----------------------------------------------------------------------------
@@ -252,6 +292,15 @@ cudaError_t tfim_eloc(const uint8_t* sigma, const float* dlog, const float* delt
   if (blocks > 65535 * 8) blocks = 65535 * 8;
   if (blocks < 1) blocks = 1;
   tfim_eloc_kernel<<<(unsigned)blocks, 256, 0, st>>>(sigma, dlog, delta, eloc, B, N, J, Gamma, hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t lrtfim_eloc(const uint8_t* sigma, const float* dlog, const float* delta, float* eloc, int64_t B,
+                        int N, double J, double Gamma, double alpha, WsHeader* hdr, cudaStream_t st) {
+  int64_t blocks = (B * 32 + 255) / 256;
+  if (blocks > 65535 * 8) blocks = 65535 * 8;
+  if (blocks < 1) blocks = 1;
+  lrtfim_eloc_kernel<<<(unsigned)blocks, 256, 0, st>>>(sigma, dlog, delta, eloc, B, N, J, Gamma, alpha, hdr);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,9 @@ cudaError_t gru1d_readout(const float* img, const float* hcache, float* dlog, in
 cudaError_t gru1d_tfim_chains(const Chain1Args& a, const float* img, int D, cudaStream_t st);
 cudaError_t tfim_eloc(const uint8_t* sigma, const float* dlog, const float* delta, float* eloc,
                       int64_t B, int N, float J, float Gamma, WsHeader* hdr, cudaStream_t st);
+// long-range TFIM energies (FP64 diagonal) from the same chain outputs
+cudaError_t lrtfim_eloc(const uint8_t* sigma, const float* dlog, const float* delta, float* eloc, int64_t B,
+                        int N, double J, double Gamma, double alpha, WsHeader* hdr, cudaStream_t st);
 cudaError_t gru1d_bptt(const Bptt1Args& a, const float* img, int D, cudaStream_t st);
 
 struct Eng2Args {

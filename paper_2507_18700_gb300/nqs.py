@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libnqs.so")
 
 GRU1D, GRU2D = 1, 2
 FP32, BF16 = 0, 1
-TFIM, HEISENBERG = 1, 2
+TFIM, HEISENBERG, LRTFIM = 1, 2, 3
 OP_SAMPLE, OP_LOGPSI, OP_LOCAL_ENERGY, OP_LOGPSI_GRAD, OP_VMC_GRAD = 1, 2, 3, 4, 5
 
 STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4: "NQS_ECUDA",
@@ -47,7 +47,7 @@ class ModelDesc(ctypes.Structure):
 
 class HamDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("marshall", ctypes.c_int32), ("J", ctypes.c_double),
-                ("h", ctypes.c_double)]
+                ("h", ctypes.c_double), ("alpha", ctypes.c_double)]
 
 
 class LrSchedule(ctypes.Structure):
@@ -93,11 +93,16 @@ def model_desc(cell, Lx, Ly=1, d_h=8, d_model=0, sz0=False, precision=FP32):
 
 
 def tfim(J=1.0, Gamma=1.0):
-    return HamDesc(TFIM, 0, J, Gamma)
+    return HamDesc(TFIM, 0, J, Gamma, 0.0)
+
+
+def lr_tfim(alpha, J=1.0, Gamma=1.0):
+    """Long-range TFIM of Sec. III C: -J sum_{i<j} Z_i Z_j / |i-j|^alpha - Gamma sum X_i."""
+    return HamDesc(LRTFIM, 0, J, Gamma, alpha)
 
 
 def heisenberg(J=1.0, marshall=True):
-    return HamDesc(HEISENBERG, int(bool(marshall)), J, 0.0)
+    return HamDesc(HEISENBERG, int(bool(marshall)), J, 0.0, 0.0)
 
 
 _lib = None

@@ -319,3 +319,73 @@ def test_vmc_gradient_is_invariant_to_an_energy_shift():
     np.testing.assert_allclose(g1, g0, rtol=1e-10, atol=1e-12)
     raw = lambda e: vmc.logpsi_grad(mod, flat, sig, 2.0 * np.asarray(e) / len(e))
     assert np.abs(raw(eloc + 17.25) - raw(eloc)).max() > 1e-2
+
+
+# ---------------------------------------------------- long-range TFIM ----
+def _lmg_ground_energy(N, J, Gamma):
+    """alpha = 0: sum_{i<j} Z_i Z_j = (M^2 - N) / 2 with M = sum Z = 2 S_z, so
+    H = -J (4 S_z^2 - N) / 2 - 2 Gamma S_x (the Lipkin-Meshkov-Glick form); its
+    ground state lies in the symmetric sector S = N/2, an (N + 1)-dimensional
+    matrix in the S_z basis with S_x from the ladder operators."""
+    S = N / 2.0
+    m = np.arange(-S, S + 1.0)
+    Hm = np.diag(-J * (4.0 * m * m - N) / 2.0)
+    for k in range(len(m) - 1):
+        x = 0.5 * np.sqrt(S * (S + 1) - m[k] * (m[k] + 1))      # <m+1|S_x|m>
+        Hm[k, k + 1] = Hm[k + 1, k] = -2.0 * Gamma * x
+    return np.linalg.eigvalsh(Hm)[0]
+
+
+def test_lr_tfim_alpha_zero_matches_the_symmetric_sector():
+    for N, G in ((6, 0.7), (9, 1.3)):
+        e_ed, _ = exact.ground_state(exact.lr_tfim_hamiltonian(N, 0.0, 1.0, G))
+        assert abs(e_ed - _lmg_ground_energy(N, 1.0, G)) < 1e-10
+
+
+def test_lr_tfim_alpha_infinity_is_the_nearest_neighbour_chain():
+    N, d = 9, 4
+    mod = M.Model(M.GRU1D, N, d_h=d)
+    flat = inputs.xavier_params(1, d, seed=23, noise_std=0.3)
+    sig = inputs.random_configs(40, N, seed=24).astype(np.int64)
+    a = hamiltonian.lr_tfim_local_energy(N, np.inf, 1.0, 0.8, sig, _lp_fn(mod, flat))
+    b = hamiltonian.tfim_local_energy(N, 1.0, 0.8, sig, _lp_fn(mod, flat))
+    np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13)
+    e_lr, _ = exact.ground_state(exact.lr_tfim_hamiltonian(8, np.inf, 1.0, 1.0))
+    assert abs(e_lr - exact.tfim_free_fermion(8, 1.0, 1.0)) < 1e-10
+
+
+def test_lr_tfim_classical_and_mean_field_limits():
+    """Gamma = 0: the all-up state has E = -sum_{r>=1} (N - r) r^-alpha (pairs
+    counted by distance); alpha = 0: E_loc = -(M^2 - N) / 2 for every sigma."""
+    N = 11
+    up = np.zeros((1, N), dtype=np.int64)
+    for alpha in (0.1, 1.0, 2.5):
+        e = hamiltonian.lr_tfim_local_energy(N, alpha, 1.0, 0.0, up, lambda s: np.zeros(len(s)))
+        assert abs(e[0] + sum((N - r) * r ** -alpha for r in range(1, N))) < 1e-12
+    sig = inputs.random_configs(30, N, seed=25).astype(np.int64)
+    Mz = (1 - 2 * sig).sum(axis=1)
+    e0 = hamiltonian.lr_tfim_local_energy(N, 0.0, 1.0, 0.0, sig, lambda s: np.zeros(len(s)))
+    np.testing.assert_allclose(e0, -(Mz * Mz - N) / 2.0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("alpha", [0.1, 1.0, 3.0])
+def test_lr_tfim_local_energy_is_constant_on_ground_state(alpha):
+    N = 10
+    e0, v = exact.ground_state(exact.lr_tfim_hamiltonian(N, alpha, 1.0, 1.0))
+    table = np.log(np.abs(v))
+    lp = lambda s: table[exact.basis_index(s)]
+    el = hamiltonian.lr_tfim_local_energy(N, alpha, 1.0, 1.0, exact.all_configs(N), lp)
+    np.testing.assert_allclose(el, e0, atol=1e-8)
+
+
+def test_lr_tfim_energy_two_routes():
+    N, d, alpha = 8, 5, 0.5
+    mod = M.Model(M.GRU1D, N, d_h=d)
+    flat = inputs.xavier_params(1, d, seed=26, noise_std=0.3)
+    configs = exact.all_configs(N)
+    lpsi = M.logpsi(mod, flat, configs)
+    el = hamiltonian.lr_tfim_local_energy(N, alpha, 1.0, 1.0, configs, _lp_fn(mod, flat))
+    psi = np.exp(lpsi)
+    Hm = exact.lr_tfim_hamiltonian(N, alpha, 1.0, 1.0)
+    assert abs(exact.exact_energy(np.exp(2 * lpsi), el) - psi @ (Hm @ psi)) < 1e-10
+    assert exact.exact_energy(np.exp(2 * lpsi), el) >= exact.ground_state(Hm)[0]
