@@ -4,6 +4,7 @@
 * ``tfim_hamiltonian``     sparse Eq. (tfim) in the sigma basis
 * ``heisenberg_hamiltonian`` sparse Eq. (heisenberg), optionally Marshall-rotated
 * ``lr_tfim_hamiltonian``  sparse long-range TFIM (Sec. III C)
+* ``cluster_hamiltonian``  sparse cluster Hamiltonian (Sec. III D)
 * ``ground_state``         exact diagonalisation (scipy eigsh / dense eigh)
 * ``tfim_free_fermion``    ground energy of the open TFIM from free fermions:
                            E0 = -1/2 sum_k eps_k, with eps_k the singular values
@@ -74,6 +75,25 @@ def lr_tfim_hamiltonian(N, alpha, J, Gamma):
                          shape=(dim, dim))
 
 
+def cluster_hamiltonian(N):
+    """Sparse cluster Hamiltonian (Sec. III D, the stabiliser reading of
+    ``hamiltonian.cluster_terms``): <sigma^(k)| -K_k |sigma> = -s_k(sigma)."""
+    dim = 2 ** N
+    idx = np.arange(dim, dtype=np.int64)
+    bits = (idx[:, None] >> np.arange(N)[None, :]) & 1
+    z = 1 - 2 * bits
+    rows, cols, vals = [], [], []
+    for k, flips in H.cluster_terms(N):
+        mask = 0
+        for f in flips:
+            mask |= 1 << f
+        rows.append(idx ^ mask)
+        cols.append(idx)
+        vals.append(-z[:, k].astype(np.float64))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(dim, dim))
+
+
 def heisenberg_hamiltonian(Lx, Ly, J=1.0, marshall=False):
     """Eq. (heisenberg) with Pauli matrices and prefactor J/4 on every open-lattice bond.
 
@@ -137,9 +157,12 @@ def exact_energy(probs, eloc):
 
 
 def exact_gradient(model, flat, configs, probs, eloc):
-    """Exact dE/dtheta = sum_sigma P (E_loc - E) d log P / d theta = 2 sum P (E_loc - E) d log psi."""
+    """Exact dE/dtheta = sum_sigma P (E_loc - E) d log P / d theta = 2 sum P (E_loc - E) d log psi;
+    for a complex E_loc (cRNN), 2 sum P [Re(E_loc - E) d log|psi| + Im(E_loc - E) d phi]."""
     E = np.sum(probs * eloc)
     w = 2.0 * probs * (eloc - E)
+    if np.iscomplexobj(w):
+        return vmc.logpsi_grad(model, flat, configs, w.real, phase_weights=w.imag)
     return vmc.logpsi_grad(model, flat, configs, w)
 
 

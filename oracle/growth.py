@@ -32,9 +32,9 @@ def _index_map(cell, name, small, big):
             return rows_h, np.arange(2)
         if name in ("b_g", "b_r", "b_h", "b_in"):
             return rows_h, None
-        if name == "U":
+        if name in ("U", "U_phi"):
             return np.arange(2), np.arange(d)
-        if name == "c":
+        if name in ("c", "c_phi"):
             return np.arange(2), None
     else:
         hcols = np.concatenate([np.arange(d), D + np.arange(d)])
@@ -57,7 +57,7 @@ def _index_map(cell, name, small, big):
 
 def grow(small, p_small, big, seed, eps):
     """Embed the parameters of ``small`` into the larger model ``big``."""
-    if small.cell != big.cell or small.Lx != big.Lx or small.Ly != big.Ly:
+    if small.cell != big.cell or small.Lx != big.Lx or small.Ly != big.Ly or small.phase != big.phase:
         raise ValueError("growth keeps the cell and the lattice")
     if big.d < small.d or big.m < small.m:
         raise ValueError("growth cannot shrink the model")

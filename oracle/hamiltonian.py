@@ -14,6 +14,14 @@ Long-range TFIM, Sec. III C, open chain:
   H = -J sum_{i<j} Z_i Z_j / |i - j|^alpha - Gamma sum_i X_i
   (the paper's J = 1; alpha -> infinity is the nearest-neighbour chain).
 
+Cluster state, Sec. III D, open chain of N sites: H = -sum_k K_k with the
+stabilisers K_1 = Z_1 X_2, K_k = X_{k-1} Z_k X_{k+1} (1 < k < N) and
+K_N = X_{N-1} Z_N.  The paper's boundary terms are garbled; this reading keeps
+every stabiliser of the (Hadamard-rotated) cluster state, whose ground energy
+is then exactly -N.  E_loc is complex for a cRNN:
+  E_loc = -sum_k s_k psi(sigma^(k)) / psi(sigma),
+with sigma^(k) the configuration with the X sites of K_k flipped.
+
 Heisenberg, Eq. (heisenberg), open Lx x Ly square lattice, Pauli matrices with
 the prefactor 1/4 (so J S_i.S_j per bond):
   diagonal  +J/4 for a parallel bond, -J/4 for an antiparallel bond;
@@ -88,3 +96,27 @@ def lr_tfim_local_energy(N, alpha, J, Gamma, sigma, logpsi_fn):
     flipped[:, idx, idx] = 1 - flipped[:, idx, idx]
     lp_f = logpsi_fn(flipped.reshape(B * N, N)).reshape(B, N)
     return diag - Gamma * np.exp(lp_f - lp[:, None]).sum(axis=1)
+
+
+def cluster_terms(N):
+    """[(k, flipped sites)] of the cluster Hamiltonian, 0-based (see the module docstring)."""
+    if N < 2:
+        raise ValueError("the cluster chain needs N >= 2")
+    out = [(0, (1,))]
+    out += [(k, (k - 1, k + 1)) for k in range(1, N - 1)]
+    out.append((N - 1, (N - 2,)))
+    return out
+
+
+def cluster_local_energy(N, sigma, logamp_fn, phase_fn):
+    """Complex E_loc of the cluster Hamiltonian for psi = exp(logamp + i phase)."""
+    sigma = np.asarray(sigma, dtype=np.int64)
+    s = 1 - 2 * sigma
+    la, ph = logamp_fn(sigma), phase_fn(sigma)
+    e = np.zeros(sigma.shape[0], dtype=np.complex128)
+    for k, flips in cluster_terms(N):
+        sp = sigma.copy()
+        for f in flips:
+            sp[:, f] = 1 - sp[:, f]
+        e -= s[:, k] * np.exp(logamp_fn(sp) - la + 1j * (phase_fn(sp) - ph))
+    return e

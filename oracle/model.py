@@ -19,6 +19,7 @@ Flat parameter layout (row-major, in this order; also the C-ABI layout):
 1D GRU (App. A), d = d_h:
   W_g[d, d+2], W_r[d, d+2], W_h[d, d], W_in[d, 2], b_g[d], b_r[d], b_h[d],
   b_in[d], U[2, d], c[2]                 -- columns of W_g, W_r: [h | sigma]
+  cRNN (phase head, Eq. softsign) appends U_phi[2, d], c_phi[2]
 2D GRU + GLU (App. A), d = d_h, m = d_model:
   W[d, 2d+4], W_g[d, 2d+4], U_mix[d, 2d], b[d], b_g[d], W_1[m, d], b_1[m],
   W_2[m, d], b_2[m], U_out[2, m], c[2]   -- columns: [h_hor | h_ver | s_hor | s_ver]
@@ -32,7 +33,7 @@ GRU2D = 2
 class Model:
     """Shape of one RNN wave function."""
 
-    def __init__(self, cell, Lx, Ly=1, d_h=8, d_model=None, sz0=False):
+    def __init__(self, cell, Lx, Ly=1, d_h=8, d_model=None, sz0=False, phase=False):
         self.cell = cell
         self.Lx = Lx
         self.Ly = Ly
@@ -40,15 +41,20 @@ class Model:
         self.d = d_h
         self.m = d_h if d_model is None else d_model
         self.sz0 = bool(sz0)
+        self.phase = bool(phase)
         if cell == GRU1D and Ly != 1:
             raise ValueError("1D GRU needs Ly == 1")
+        if phase and cell != GRU1D:
+            raise ValueError("the phase head is built for the 1D GRU")
 
     def shapes(self):
         d, m = self.d, self.m
         if self.cell == GRU1D:
-            return [("W_g", (d, d + 2)), ("W_r", (d, d + 2)), ("W_h", (d, d)),
+            base = [("W_g", (d, d + 2)), ("W_r", (d, d + 2)), ("W_h", (d, d)),
                     ("W_in", (d, 2)), ("b_g", (d,)), ("b_r", (d,)), ("b_h", (d,)),
                     ("b_in", (d,)), ("U", (2, d)), ("c", (2,))]
+            # cRNN (Eq. softsign): phase layer U_phi h_n + c_phi after the amplitude head
+            return base + ([("U_phi", (2, d)), ("c_phi", (2,))] if self.phase else [])
         return [("W", (d, 2 * d + 4)), ("W_g", (d, 2 * d + 4)), ("U_mix", (d, 2 * d)),
                 ("b", (d,)), ("b_g", (d,)), ("W_1", (m, d)), ("b_1", (m,)),
                 ("W_2", (m, d)), ("b_2", (m,)), ("U_out", (2, m)), ("c", (2,))]
@@ -131,6 +137,15 @@ def readout_logits(model, p, h):
     return glu(p, h) @ p["U_out"].T + p["c"]
 
 
+def softsign(x):
+    return x / (1.0 + np.abs(x))
+
+
+def phase_logits(p, h):
+    """cRNN phase layer (Eq. softsign): z_phi = U_phi h + c_phi, one entry per spin value."""
+    return h @ p["U_phi"].T + p["c_phi"]
+
+
 def _mask_logp(model, logp, n_up, n_dn):
     """Zero-magnetisation mask: forced spins get log p = 0 and the other -inf."""
     if not model.sz0:
@@ -167,6 +182,8 @@ def run(model, flat, sigma=None, uniforms=None):
     hid = np.zeros((B, N, d))
     logits = np.zeros((B, N, 2))
     logp_site = np.zeros((B, N))
+    phi_site = np.zeros((B, N))
+    phlog = np.zeros((B, N, 2))
     p0 = np.zeros((B, N))
     n_up = np.zeros(B, dtype=np.int64)
     n_dn = np.zeros(B, dtype=np.int64)
@@ -202,15 +219,26 @@ def run(model, flat, sigma=None, uniforms=None):
             sigma[:, k] = s
         s = sigma[:, k]
         logp_site[:, k] = lp[np.arange(B), s]
+        if model.phase:
+            # phi_n = pi Softsign(U_phi h_n + c_phi) . onehot(sigma_n) (Eq. softsign)
+            zp = phase_logits(p, h)
+            phlog[:, k] = zp
+            phi_site[:, k] = np.pi * softsign(zp[np.arange(B), s])
         n_up += (s == 0)
         n_dn += (s == 1)
     return {"sigma": sigma, "logp": logp_site, "p0": p0, "logits": logits,
-            "hidden": hid, "logpsi": 0.5 * logp_site.sum(axis=1)}
+            "hidden": hid, "logpsi": 0.5 * logp_site.sum(axis=1),
+            "phase_logits": phlog, "phase": phi_site.sum(axis=1)}
 
 
 def logpsi(model, flat, sigma):
     """log psi(sigma) = 1/2 sum_n log p_n(sigma_n) (Eq. 1 and the pRNN amplitude)."""
     return run(model, flat, sigma=sigma)["logpsi"]
+
+
+def phase(model, flat, sigma):
+    """phi(sigma) = sum_n phi_n of the cRNN (Sec. II, Eq. softsign); 0 for a pRNN."""
+    return run(model, flat, sigma=sigma)["phase"]
 
 
 def sample(model, flat, uniforms):

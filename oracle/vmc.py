@@ -18,20 +18,33 @@ from . import model as M
 
 
 def energy_stats(eloc):
-    """[mean, variance (1/M), M] of the local energies, in float64."""
+    """[mean, variance (1/M), M] of the local energies, in float64; for complex
+    local energies (cRNN) [Re mean, mean |E - mean|^2, M, Im mean]."""
+    if np.iscomplexobj(eloc):
+        e = np.asarray(eloc, dtype=np.complex128)
+        mean = e.mean()
+        return np.array([mean.real, np.mean(np.abs(e - mean) ** 2), float(e.size), mean.imag])
     e = np.asarray(eloc, dtype=np.float64)
     mean = e.mean()
     return np.array([mean, (e * e).mean() - mean * mean, float(e.size)])
 
 
 def vmc_weights(eloc):
-    """w_s = 2 (E_loc,s - mean) / M, the per-sample factor of the VMC gradient."""
-    e = np.asarray(eloc, dtype=np.float64)
+    """w_s = 2 (E_loc,s - mean) / M, the per-sample factor of the VMC gradient
+    (complex for a complex E_loc)."""
+    e = np.asarray(eloc)
+    e = e.astype(np.complex128) if np.iscomplexobj(e) else e.astype(np.float64)
     return 2.0 * (e - e.mean()) / e.size
 
 
 def vmc_gradient(model, flat, sigma, eloc):
-    return logpsi_grad(model, flat, sigma, vmc_weights(eloc))
+    """g = (2/M) sum_s Re[(E_s - mean)^* d log psi_s]: for a real psi the sum of
+    (E_s - mean) d log psi_s; for a cRNN, log psi = log|psi| + i phi, so
+    g = (2/M) sum_s [Re(E_s - mean) d log|psi_s| + Im(E_s - mean) d phi_s]."""
+    w = vmc_weights(eloc)
+    if np.iscomplexobj(w):
+        return logpsi_grad(model, flat, sigma, w.real, phase_weights=w.imag)
+    return logpsi_grad(model, flat, sigma, w)
 
 
 def _dlogits(model, z, s, n_up, n_dn, coef):
@@ -45,11 +58,13 @@ def _dlogits(model, z, s, n_up, n_dn, coef):
     return dz
 
 
-def logpsi_grad(model, flat, sigma, weights):
-    """d/dtheta of sum_s w_s log psi(sigma_s), as a flat float64 vector."""
+def logpsi_grad(model, flat, sigma, weights, phase_weights=None):
+    """d/dtheta of sum_s [w_s log|psi(sigma_s)| + v_s phi(sigma_s)] (v = phase_weights,
+    cRNN only), as a flat float64 vector."""
     p = model.unpack(flat)
     sigma = np.asarray(sigma, dtype=np.int64)
     w = np.asarray(weights, dtype=np.float64)
+    vph = None if phase_weights is None else np.asarray(phase_weights, dtype=np.float64)
     B, N = sigma.shape
     d = model.d
     g = {name: np.zeros(shape) for name, shape in model.shapes()}
@@ -109,6 +124,15 @@ def logpsi_grad(model, flat, sigma, weights):
         if model.cell == M.GRU1D:
             g["U"] += dz.T @ h
             dh = dz @ p["U"] + carry[:, k]
+            if model.phase and vph is not None:
+                # phi_k = pi softsign(z_phi[s_k]); d softsign / dz = 1 / (1 + |z|)^2
+                zp = M.phase_logits(p, h)
+                sel = M.onehot(sigma[:, k])
+                zs = (zp * sel).sum(axis=1)
+                dzp = sel * (vph * np.pi / (1.0 + np.abs(zs)) ** 2)[:, None]
+                g["U_phi"] += dzp.T @ h
+                g["c_phi"] += dzp.sum(axis=0)
+                dh = dh + dzp @ p["U_phi"]
             u, r, q, c, h_prev = rec["u"], rec["r"], rec["q"], rec["c"], rec["h_prev"]
             dc = dh * u
             du = dh * (c - h_prev)

@@ -12,14 +12,16 @@ GRU1D = 1
 GRU2D = 2
 
 
-def tensor_shapes(cell, d_h, d_model=None):
-    """(name, shape) of every tensor of the flat layout, in order."""
+def tensor_shapes(cell, d_h, d_model=None, phase=False):
+    """(name, shape) of every tensor of the flat layout, in order (phase: the
+    cRNN's phase layer U_phi, c_phi after the amplitude head)."""
     d = d_h
     m = d_h if d_model is None else d_model
     if cell == GRU1D:
         return [("W_g", (d, d + 2)), ("W_r", (d, d + 2)), ("W_h", (d, d)),
                 ("W_in", (d, 2)), ("b_g", (d,)), ("b_r", (d,)), ("b_h", (d,)),
-                ("b_in", (d,)), ("U", (2, d)), ("c", (2,))]
+                ("b_in", (d,)), ("U", (2, d)), ("c", (2,))] + (
+                    [("U_phi", (2, d)), ("c_phi", (2,))] if phase else [])
     if cell == GRU2D:
         return [("W", (d, 2 * d + 4)), ("W_g", (d, 2 * d + 4)), ("U_mix", (d, 2 * d)),
                 ("b", (d,)), ("b_g", (d,)), ("W_1", (m, d)), ("b_1", (m,)),
@@ -27,17 +29,17 @@ def tensor_shapes(cell, d_h, d_model=None):
     raise ValueError("unknown cell")
 
 
-def param_count(cell, d_h, d_model=None):
-    return sum(int(np.prod(s)) for _, s in tensor_shapes(cell, d_h, d_model))
+def param_count(cell, d_h, d_model=None, phase=False):
+    return sum(int(np.prod(s)) for _, s in tensor_shapes(cell, d_h, d_model, phase))
 
 
-def xavier_params(cell, d_h, seed, noise_std=0.0, d_model=None):
+def xavier_params(cell, d_h, seed, noise_std=0.0, d_model=None, phase=False):
     """Xavier-uniform weights U(-a, a), a = sqrt(6 / (fan_in + fan_out)) per matrix,
     zero biases, plus N(0, noise_std^2) on every entry when noise_std > 0.
     Returned as float64; callers cast to float32 for the device."""
     rng = np.random.Generator(np.random.PCG64(seed))
     parts = []
-    for _, shape in tensor_shapes(cell, d_h, d_model):
+    for _, shape in tensor_shapes(cell, d_h, d_model, phase):
         if len(shape) == 2:
             a = np.sqrt(6.0 / (shape[0] + shape[1]))
             parts.append(rng.uniform(-a, a, size=shape).reshape(-1))

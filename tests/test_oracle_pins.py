@@ -389,3 +389,90 @@ def test_lr_tfim_energy_two_routes():
     Hm = exact.lr_tfim_hamiltonian(N, alpha, 1.0, 1.0)
     assert abs(exact.exact_energy(np.exp(2 * lpsi), el) - psi @ (Hm @ psi)) < 1e-10
     assert exact.exact_energy(np.exp(2 * lpsi), el) >= exact.ground_state(Hm)[0]
+
+
+# ------------------------------------------- cRNN and the cluster state ----
+def test_cluster_hamiltonian_ground_energy_is_minus_n():
+    """All N stabilisers commute and are independent, so the ground state is
+    the unique joint +1 eigenstate with energy exactly -N, and the first
+    excited level (one stabiliser at -1) is -N + 2."""
+    for N in (3, 4, 7, 9):
+        w = np.linalg.eigvalsh(exact.cluster_hamiltonian(N).toarray())
+        assert abs(w[0] + N) < 1e-10 and abs(w[1] - (-N + 2)) < 1e-10
+
+
+def test_cluster_local_energy_is_constant_on_ground_state():
+    N = 8
+    e0, v = exact.ground_state(exact.cluster_hamiltonian(N))
+    nz = np.abs(v) > 1e-12
+    la = np.where(nz, np.log(np.where(nz, np.abs(v), 1.0)), -np.inf)
+    ph = np.where(v < 0, np.pi, 0.0)
+    configs = exact.all_configs(N)[nz]
+    el = hamiltonian.cluster_local_energy(N, configs, lambda s: la[exact.basis_index(s)],
+                                          lambda s: ph[exact.basis_index(s)])
+    np.testing.assert_allclose(el, e0, atol=1e-9)
+    assert abs(e0 + N) < 1e-10
+    assert (v < -1e-12).any()                   # the ground state has a sign structure
+
+
+def _crnn(N, d, seed):
+    mod = M.Model(M.GRU1D, N, d_h=d, phase=True)
+    return mod, inputs.xavier_params(1, d, seed=seed, noise_std=0.4, phase=True)
+
+
+def test_crnn_phase_range_and_normalisation():
+    mod, flat = _crnn(7, 4, 30)
+    configs = exact.all_configs(7)
+    out = M.run(mod, flat, sigma=configs)
+    assert abs(np.exp(2 * out["logpsi"]).sum() - 1.0) < 1e-12
+    assert np.all(np.abs(out["phase"]) < 7 * np.pi)
+    # phi_n of the spin that was not chosen does not enter phi
+    zp = out["phase_logits"]
+    phi = np.pi * M.softsign(zp[np.arange(len(configs))[:, None], np.arange(7)[None, :], configs]).sum(axis=1)
+    np.testing.assert_allclose(out["phase"], phi, rtol=0, atol=1e-13)
+
+
+def test_crnn_cluster_energy_two_routes():
+    N, d = 7, 4
+    mod, flat = _crnn(N, d, 31)
+    configs = exact.all_configs(N)
+    la, ph = M.logpsi(mod, flat, configs), M.phase(mod, flat, configs)
+    el = hamiltonian.cluster_local_energy(N, configs, lambda s: M.logpsi(mod, flat, s),
+                                          lambda s: M.phase(mod, flat, s))
+    P = np.exp(2 * la)
+    e_sum = np.sum(P * el)
+    psi = np.exp(la + 1j * ph)
+    e_h = np.vdot(psi, exact.cluster_hamiltonian(N) @ psi)
+    assert abs(e_sum - e_h) < 1e-11 and abs(e_sum.imag) < 1e-11
+    assert e_sum.real >= -N - 1e-12
+
+
+def test_crnn_gradient_matches_fd_of_exact_energy():
+    """d <psi|H|psi> / d theta for the cRNN on the cluster Hamiltonian (dense
+    H, complex psi) = 2 sum P [Re(E_loc - E) d log|psi| + Im(E_loc - E) d phi]."""
+    N, d = 5, 3
+    mod, flat = _crnn(N, d, 32)
+    configs = exact.all_configs(N)
+    Hm = exact.cluster_hamiltonian(N).toarray()
+
+    def energy(x):
+        psi = np.exp(M.logpsi(mod, x, configs) + 1j * M.phase(mod, x, configs))
+        return float(np.vdot(psi, Hm @ psi).real)
+
+    P = np.exp(2 * M.logpsi(mod, flat, configs))
+    el = hamiltonian.cluster_local_energy(N, configs, lambda s: M.logpsi(mod, flat, s),
+                                          lambda s: M.phase(mod, flat, s))
+    g = exact.exact_gradient(mod, flat, configs, P, el)
+    fd = exact.central_fd(energy, flat, h=1e-5)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+def test_crnn_phase_gradient_matches_fd():
+    N, d = 6, 3
+    mod, flat = _crnn(N, d, 33)
+    sig = inputs.random_configs(5, N, seed=34).astype(np.int64)
+    w = inputs.random_weights(5, seed=35)
+    v = inputs.random_weights(5, seed=36)
+    g = vmc.logpsi_grad(mod, flat, sig, w, phase_weights=v)
+    fd = exact.central_fd(lambda x: float(w @ M.logpsi(mod, x, sig) + v @ M.phase(mod, x, sig)), flat)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8)
