@@ -40,6 +40,10 @@ WORKLOADS = {
     "heis16x16": dict(cell=2, Lx=16, Ly=16, d=256, B=8192, sz0=True, ham="heis", J=1.0, Gamma=0.0,
                       seed=3, noise=0.0,
                       name="2D Heisenberg 16x16 OBC, Marshall sign, S_z=0, 2D GRU+GLU d_h=256, 8192 samples/step"),
+    "cluster64": dict(cell=1, Lx=64, Ly=1, d=128, B=4096, sz0=False, ham="cluster", J=1.0, Gamma=0.0,
+                      seed=4, noise=0.0, phase=True,
+                      name="1D cluster state N=64 (Sec. III D), cRNN (GRU d_h=128 + softsign phase layer), "
+                           "4096 samples/step, FP32"),
     "eval1m": dict(cell=1, Lx=100, Ly=1, d=64, B=1_000_000, sz0=False, ham="tfim", J=1.0, Gamma=1.0,
                    seed=1, noise=0.1, chunk=65536,
                    name="final evaluation: 1D TFIM N=100, Gamma=J=1, GRU d_h=64, 10^6 samples in chunks of 65,536 "
@@ -53,7 +57,9 @@ WORKLOADS = {
 
 def mac_cell(w):
     d = w["d"]
-    return 3 * d * d + 2 * d if w["cell"] == 1 else 8 * d * d + 2 * d
+    if w["cell"] == 1:
+        return 3 * d * d + 2 * d + (2 * d if w.get("phase") else 0)   # cRNN: the phase layer
+    return 8 * d * d + 2 * d
 
 
 def peaks():
@@ -73,6 +79,10 @@ def chain_cells(w, sigma):
     B, N = sigma.shape
     if w["ham"] == "tfim":
         return B * (N * (N - 1) // 2)
+    if w["ham"] == "cluster":
+        # term k restarts at its first flipped site f: 1 (k = 0), k - 1, N - 2 (k = N - 1)
+        firsts = [1] + list(range(0, N - 2)) + [N - 2]
+        return B * sum(N - 1 - f for f in firsts)
     Lx, Ly = w["Lx"], w["Ly"]
     pos = np.empty(N, dtype=np.int64)
     for j in range(Ly):
@@ -144,8 +154,8 @@ class ClockSampler:
 def _oracle_model(w):
     from oracle import model as om
     from paper_2507_18700_gb300 import inputs
-    mod = om.Model(w["cell"], w["Lx"], w["Ly"], d_h=w["d"], sz0=w["sz0"])
-    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"])
+    mod = om.Model(w["cell"], w["Lx"], w["Ly"], d_h=w["d"], sz0=w["sz0"], phase=w.get("phase", False))
+    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"], phase=w.get("phase", False))
     return mod, flat
 
 
@@ -160,6 +170,8 @@ def oracle_step_seconds(w, n_samples, seed):
     lp = lambda x: om.logpsi(mod, flat, x)
     if w["ham"] == "tfim":
         e = oh.tfim_local_energy(mod.N, w["J"], w["Gamma"], s, lp)
+    elif w["ham"] == "cluster":
+        e = w["J"] * oh.cluster_local_energy(mod.N, s, lp, lambda x: om.phase(mod, flat, x))
     else:
         e = oh.heisenberg_local_energy(w["Lx"], w["Ly"], w["J"], True, s, lp)
     ov.energy_stats(e)
@@ -221,8 +233,11 @@ def run_gpu(args, w):
     torch.cuda.set_device(dev)
     B = args.batch or w["B"]
     N = w["Lx"] * w["Ly"]
-    ham = nqs.tfim(w["J"], w["Gamma"]) if w["ham"] == "tfim" else nqs.heisenberg(w["J"], True)
-    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"]).astype(np.float32)
+    phase = w.get("phase", False)
+    ham = (nqs.tfim(w["J"], w["Gamma"]) if w["ham"] == "tfim" else
+           nqs.cluster(w["J"]) if w["ham"] == "cluster" else nqs.heisenberg(w["J"], True))
+    flat = inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"],
+                                phase=phase).astype(np.float32)
     params = torch.tensor(flat, device=dev)
     P = params.numel()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -244,7 +259,7 @@ def run_gpu(args, w):
 
     def measure(precision):
         """Time args.steps VMC steps at one precision (after args.warmup untimed ones)."""
-        desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=precision)
+        desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=precision, phase=phase)
         ws = nqs.Workspace(dev)
         for k in range(args.warmup):
             s_, _, h_ = nqs.sample(desc, params, B, seed=step_seed, step=k, ws=ws, sample_offset=offset)
@@ -283,7 +298,7 @@ def run_gpu(args, w):
         host_p = torch.from_numpy(flat).pin_memory()
         gdt = torch.float32 if world == 1 else torch.float64    # several ranks: the FP64 all-reduced gradient
         host_g = torch.empty(P, dtype=gdt).pin_memory()
-        host_s = torch.empty(3, dtype=torch.float64).pin_memory()
+        host_s = torch.empty(4 if phase else 3, dtype=torch.float64).pin_memory()
         dev_p = torch.empty_like(params)
         e2e_ms = []
         for k in range(args.steps):
@@ -324,8 +339,8 @@ def run_gpu(args, w):
 
     r32 = measure(nqs.FP32)
     chosen, r16, check = r32, None, None
-    bf16_ok = args.precision != "fp32" and (w["d"] in (16, 32, 64) if w["cell"] == 1
-                                            else w["d"] in (32, 64) and N <= 128)
+    bf16_ok = args.precision != "fp32" and not phase and (w["d"] in (16, 32, 64) if w["cell"] == 1
+                                                          else w["d"] in (32, 64) and N <= 128)
     if bf16_ok:
         r16 = measure(nqs.BF16)
         check = accuracy_check(r16["desc"], r32["desc"])
@@ -390,7 +405,8 @@ def run_gpu(args, w):
                    "device_status": chosen["status"]},
         "roofline": roof,
         "e2e": {"value": world * B * args.steps / (chosen["e2e_ms"] * 1e-3), "unit": "samples/s",
-                "h2d_bytes_per_step": P * 4, "d2h_bytes_per_step": P * (4 if world == 1 else 8) + 24},
+                "h2d_bytes_per_step": P * 4,
+                "d2h_bytes_per_step": P * (4 if world == 1 else 8) + (32 if phase else 24)},
         "gpu_launches": launches * args.steps,
         "clocks": {"sm_mhz": chosen["clk"]["sm_mhz"], "sm_max_mhz": chosen["clk"]["sm_max_mhz"],
                    "reasons": chosen["clk"]["reasons"]},

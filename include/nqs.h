@@ -29,6 +29,7 @@
  * NQS_GRU1D (App. A, 1D GRU), d = d_h:
  *   W_g[d, d+2]  W_r[d, d+2]  W_h[d, d]  W_in[d, 2]
  *   b_g[d]  b_r[d]  b_h[d]  b_in[d]  U[2, d]  c[2]
+ *   and, for a cRNN (phase = 1), U_phi[2, d]  c_phi[2]
  *   (columns of W_g, W_r: [h_{n-1} | one-hot sigma_{n-1}])
  *   u = sigmoid(W_g[h;s] + b_g), r = sigmoid(W_r[h;s] + b_r),
  *   h~ = tanh(r * (W_h h + b_h) + W_in s + b_in), h' = (1 - u) h + u h~.
@@ -81,7 +82,7 @@ typedef enum {
 
 enum { NQS_GRU1D = 1, NQS_GRU2D = 2 };
 enum { NQS_FP32 = 0, NQS_BF16 = 1 };
-enum { NQS_TFIM = 1, NQS_HEISENBERG = 2, NQS_LRTFIM = 3 };
+enum { NQS_TFIM = 1, NQS_HEISENBERG = 2, NQS_LRTFIM = 3, NQS_CLUSTER = 4 };
 enum {
   NQS_OP_SAMPLE = 1,
   NQS_OP_LOGPSI = 2,
@@ -104,10 +105,18 @@ typedef struct {
                          forcing, the Heisenberg chains and the reverse
                          sweep (d_h in {32, 64}, N <= 128); other shapes
                          return NQS_EUNSUPPORTED */
+  int32_t phase;      /* 1: complex RNN (cRNN, Sec. II and Eq. softsign): a phase
+                         layer z_phi = U_phi h_n + c_phi after the amplitude head,
+                         phi_n = pi Softsign(z_phi) . onehot(sigma_n), log psi =
+                         1/2 sum log p_n + i sum phi_n.  Built for NQS_GRU1D,
+                         NQS_FP32, d_h >= 16, with NQS_CLUSTER.  Every log psi,
+                         local energy and gradient weight of a cRNN is a float
+                         pair (real, imaginary): logpsi [B, 2], eloc [B, 2],
+                         weights [B, 2]; vmc stats [4] */
 } nqs_model_desc;
 
 typedef struct {
-  int32_t kind;       /* NQS_TFIM | NQS_LRTFIM (1D GRU) | NQS_HEISENBERG (2D GRU) */
+  int32_t kind;       /* NQS_TFIM | NQS_LRTFIM | NQS_CLUSTER (1D GRU) | NQS_HEISENBERG (2D GRU) */
   int32_t marshall;   /* Heisenberg: 1 = Marshall-rotated exchange (-J/2) */
   double J;           /* coupling J */
   double h;           /* TFIM / long-range TFIM transverse field Gamma (ignored for Heisenberg) */
@@ -168,6 +177,13 @@ nqs_status nqs_logpsi(const nqs_model_desc* desc, const float* params,
                       void* ws, size_t ws_bytes, void* stream);
 
 /* Local energies E_loc(sigma) = sum_sigma' H[sigma, sigma'] psi(sigma')/psi(sigma):
+ *   NQS_CLUSTER (the cluster state of Sec. III D, open chain, GRU1D, FP32,
+ *     N >= 3, d_h >= 16): H = -J sum_k K_k with the stabilisers K_1 = Z_1 X_2,
+ *     K_k = X_{k-1} Z_k X_{k+1}, K_N = X_{N-1} Z_N (the paper's boundary
+ *     terms read as the cluster state's stabilisers; ground energy -J N):
+ *     E_loc = -J sum_k s_k psi(sigma^(k))/psi(sigma), complex [B, 2] for a
+ *     cRNN, real [B] for a positive RNN; a term flipping two sites restarts
+ *     from the cached state at the first and flips the second on the way;
  *   NQS_TFIM (Eq. tfim, open chain, GRU1D):
  *     -J sum s_i s_{i+1} - h sum_i psi(flip_i sigma)/psi(sigma);
  *   NQS_LRTFIM (the long-range TFIM of Sec. III C, open chain, GRU1D):
@@ -187,7 +203,9 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
                             const float* hcache, int64_t B, float* eloc,
                             void* ws, size_t ws_bytes, void* stream);
 
-/* Gradient of L = sum_b w_b log psi(sigma_b) with respect to the flat
+/* Gradient of L = sum_b w_b log psi(sigma_b) (cRNN: weights [B, 2] = (w, v)
+ * and L = sum_b [w_b log |psi_b| + v_b phi_b] = sum_b Re(conj(w_b + i v_b)
+ * log psi_b)) with respect to the flat
  * parameters, by a reverse sweep over the unrolled recurrence.  In the 1D
  * BF16 path a parallel pass first stores, per (sample, site), the factors
  * with which the cell backward is linear in the incoming gradient (FP16,
@@ -203,7 +221,9 @@ nqs_status nqs_logpsi_grad(const nqs_model_desc* desc, const float* params,
 /* VMC step statistics and gradient (Sec. III; the paper follows Hibat-Allah
  * et al. 2020 and prints no formula -- the estimator used is
  *   g = (2/M) sum_b (E_loc,b - mean E_loc) d log psi(sigma_b)/d theta,
- * with E_loc held constant).
+ * with E_loc held constant; for a cRNN, g = (2/M) sum_b Re[(E_loc,b -
+ * mean)^* d log psi_b], eloc [B, 2] and stats [4] = Re mean, mean |E -
+ * mean|^2, M, Im mean).
  *   eloc  device [B] float (read); grad device [P] float (written);
  *   stats device [3] double (written): mean E_loc, variance (1/M), M.  */
 nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,

@@ -9,7 +9,7 @@ using namespace nqs;
 namespace {
 
 struct Dims {
-  int cell, Lx, Ly, N, d, m, sz0, precision;
+  int cell, Lx, Ly, N, d, m, sz0, precision, phase;
   size_t P;
 };
 
@@ -24,10 +24,12 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   d.d = desc->d_h;
   d.m = desc->d_model == 0 ? desc->d_h : desc->d_model;
   d.sz0 = desc->sz0;
+  d.phase = desc->phase;
   d.precision = desc->precision;
   if (d.cell != NQS_GRU1D && d.cell != NQS_GRU2D) return NQS_EINVAL;
   if (d.precision != NQS_FP32 && d.precision != NQS_BF16) return NQS_EINVAL;
   if (d.sz0 != 0 && d.sz0 != 1) return NQS_EINVAL;
+  if (d.phase != 0 && d.phase != 1) return NQS_EINVAL;
   if (d.Lx < 1 || d.Ly < 1 || (int64_t)d.Lx * d.Ly > (1 << 20)) return NQS_ESHAPE;
   d.N = d.Lx * d.Ly;
   if (!valid_hidden(d.cell, d.d)) return NQS_ESHAPE;
@@ -35,7 +37,7 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
   if (d.cell == NQS_GRU2D && d.m != d.d) return NQS_ESHAPE;
   if (d.sz0 && (d.N % 2)) return NQS_ESHAPE;
   if (d.cell == NQS_GRU1D)
-    d.P = 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2;
+    d.P = 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2 + (d.phase ? 2 * (size_t)d.d + 2 : 0);
   else
     d.P = 6 * (size_t)d.d * d.d + 10 * (size_t)d.d + 2 * (size_t)d.m * d.d + 4 * (size_t)d.m + 2;
   if (out) *out = d;
@@ -47,6 +49,8 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
 // for d_h in {32, 64} and N <= 128 (configurations as 128-bit masks).
 nqs_status check_built(const Dims& d) {
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
+  // the cRNN phase head: FP32 1D GRU, d_h >= 16
+  if (d.phase && (d.cell != NQS_GRU1D || d.precision != NQS_FP32 || d.d < 16)) return NQS_EUNSUPPORTED;
   if (d.precision == NQS_BF16) {
     const bool ok = d.cell == NQS_GRU1D ? tc1d_supported(d.d) != 0 : tc2d_supported(d.d, d.Lx, d.N) != 0;
     if (!ok) return NQS_EUNSUPPORTED;
@@ -55,6 +59,8 @@ nqs_status check_built(const Dims& d) {
 }
 
 bool use_tc(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU1D; }
+// flat offset of the cRNN phase layer [U_phi | c_phi] (after the amplitude parameters)
+size_t phase_offset(const Dims& d) { return 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2; }
 bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
 
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
@@ -91,7 +97,9 @@ Layout layout(const Dims& d, int64_t B, int op) {
     case NQS_OP_LOCAL_ENERGY:
       if (!two) {
         L.a = take(BN * sizeof(float));        // dlog
-        L.b = take(BN * sizeof(float));        // delta
+        L.b = take(BN * sizeof(float));        // delta (cluster: its real part)
+        L.c = take(BN * 2 * sizeof(float));    // cluster: phase logits of the cached path
+        L.e = take(BN * sizeof(float));        // cluster: imaginary part of delta
       } else {
         L.a = take((use_tc2d(d) ? tc2d_colbuf_floats(B, d.Lx, d.d)
                                 : (size_t)gru2d_engine_slots(d.d, B, 2) * d.Lx * d.d) * sizeof(float));  // colbuf
@@ -124,9 +132,10 @@ Layout layout(const Dims& d, int64_t B, int op) {
         L.g = take(tc1d_tape_bytes(B, d.N, d.d, 2));                            // tape: backward factors
         break;
       }
-      const size_t grid = (size_t)(two ? gru2d_bptt_grid(d.d, B) : gru1d_bptt_grid(d.d, B));
+      const size_t grid = (size_t)(two ? gru2d_bptt_grid(d.d, B)
+                                       : d.phase ? crnn_bptt_grid(B, d.d) : gru1d_bptt_grid(d.d, B));
       L.a = take(grid * d.P * sizeof(float));               // partial gradients
-      L.b = take((size_t)B * sizeof(float));                 // weights
+      L.b = take((size_t)B * 2 * sizeof(float));             // weights (complex for the cRNN)
       if (two) L.c = take((size_t)B * d.Lx * d.d * sizeof(float));  // vertical carries
       if (two) L.e = take(gru2d_bptt_scratch_floats(d.d, B) * sizeof(float));  // small-gradient scratch
       break;
@@ -176,6 +185,21 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
                               int64_t B, T* grad, void* ws, cudaStream_t st) {
   float* img = at<float>(ws, L.img);
   float* partial = at<float>(ws, L.a);
+  if (d.phase) {
+    // cRNN: weights are [B, 2] = (w for log |psi|, v for phi)
+    const int grid = crnn_bptt_grid(B, d.d);
+    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Bptt1Args a{};
+    a.B = B;
+    a.N = d.N;
+    a.P = (int)d.P;
+    a.sigma = sigma;
+    a.hcache = hcache;
+    a.weights = weights;
+    a.partial = partial;
+    if (crnn_bptt(a, img, params + phase_offset(d), weights, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
+  }
   if (use_tc(d)) {
     uint8_t* w3 = at<uint8_t>(ws, L.w);
     uint8_t* wt = at<uint8_t>(ws, L.w2);
@@ -319,7 +343,8 @@ nqs_status nqs_grow_hidden(const nqs_model_desc* small, const float* p_small,
   if (s.cell != b.cell || s.Lx != b.Lx || s.Ly != b.Ly) return NQS_ESHAPE;
   if (b.d < s.d || b.m < s.m) return NQS_ESHAPE;
   if (!(eps >= 0.0f)) return NQS_EINVAL;
-  return cuda_status(grow_params(s.cell, s.d, s.m, b.d, b.m, p_small, p_big, seed, eps,
+  if (s.phase != b.phase) return NQS_ESHAPE;
+  return cuda_status(grow_params(s.cell, s.phase, s.d, s.m, b.d, b.m, p_small, p_big, seed, eps,
                                  static_cast<cudaStream_t>(stream)));
 }
 
@@ -343,6 +368,23 @@ static nqs_status forward_common(const nqs_model_desc* desc, const float* params
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!reset_status(ws, st)) return NQS_ECUDA;
   float* img = at<float>(ws, L.img);
+  if (d.phase) {
+    // cRNN: logpsi is [B, 2] = (log |psi|, phi)
+    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Fwd1Args a{};
+    a.B = B;
+    a.N = d.N;
+    a.sigma_in = sigma_in;
+    a.sigma_out = sigma_out;
+    a.uniforms = uniforms;
+    a.seed = seed;
+    a.step = step;
+    a.b0 = b0;
+    a.step_dev = step_dev;
+    a.hcache = hcache;
+    a.hdr = static_cast<WsHeader*>(ws);
+    return cuda_status(crnn_forward(a, img, params + phase_offset(d), logpsi, d.d, sample, st));
+  }
   if (use_tc2d(d)) {
     uint8_t* wimg = at<uint8_t>(ws, L.w);
     if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
@@ -444,9 +486,16 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if (!ham || !params || B < 0) return NQS_EINVAL;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
   if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
-  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG && ham->kind != NQS_LRTFIM) return NQS_EINVAL;
+  if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG && ham->kind != NQS_LRTFIM && ham->kind != NQS_CLUSTER)
+    return NQS_EINVAL;
   if (ham->kind == NQS_LRTFIM && !(ham->alpha >= 0.0)) return NQS_EINVAL;
-  if ((ham->kind == NQS_TFIM || ham->kind == NQS_LRTFIM) && d.cell != NQS_GRU1D) return NQS_EUNSUPPORTED;
+  if ((ham->kind == NQS_TFIM || ham->kind == NQS_LRTFIM || ham->kind == NQS_CLUSTER) && d.cell != NQS_GRU1D)
+    return NQS_EUNSUPPORTED;
+  // the phase head is built with the cluster Hamiltonian, which runs on the FP32 path
+  if (d.phase && ham->kind != NQS_CLUSTER) return NQS_EUNSUPPORTED;
+  if (ham->kind == NQS_CLUSTER && d.precision != NQS_FP32) return NQS_EUNSUPPORTED;
+  if (ham->kind == NQS_CLUSTER && d.N < 3) return NQS_ESHAPE;
+  if (ham->kind == NQS_CLUSTER && d.d < 16) return NQS_EUNSUPPORTED;
   if (ham->kind == NQS_HEISENBERG && d.cell != NQS_GRU2D) return NQS_EUNSUPPORTED;
   if (ham->kind == NQS_HEISENBERG && (d.Lx < 2 && d.Ly < 2)) return NQS_ESHAPE;
   const Layout L = layout(d, B, NQS_OP_LOCAL_ENERGY);
@@ -456,6 +505,24 @@ nqs_status nqs_local_energy(const nqs_model_desc* desc, const float* params,
   if (!reset_status(ws, st)) return NQS_ECUDA;
   WsHeader* hdr = static_cast<WsHeader*>(ws);
   float* img = at<float>(ws, L.img);
+  if (ham->kind == NQS_CLUSTER) {
+    // cRNN: eloc is [B, 2] (complex); pRNN: [B] (real ratios)
+    if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    const float* php = d.phase ? params + phase_offset(d) : nullptr;
+    float* dlog = at<float>(ws, L.a);
+    float* dre = at<float>(ws, L.b);
+    float* zph = at<float>(ws, L.c);
+    float* dim = at<float>(ws, L.e);
+    if (crnn_readout(img, php, hcache, dlog, zph, B * d.N, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Fwd1Args f{};
+    f.B = B;
+    f.N = d.N;
+    f.sigma_in = sigma;
+    f.hcache = const_cast<float*>(hcache);
+    f.hdr = hdr;
+    return cuda_status(cluster_local_energy(f, img, php, d.phase, dlog, zph, dre, dim, eloc, &hdr->job_counter,
+                                            (float)ham->J, d.d, st));
+  }
   if (ham->kind == NQS_HEISENBERG) {
     const int nb = n_bonds(d);
     int4* bonds = at<int4>(ws, L.b);
@@ -591,6 +658,11 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params, const u
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!reset_status(ws, st)) return NQS_ECUDA;
   float* w = at<float>(ws, L.b);
+  if (d.phase) {
+    // complex local energies: stats [Re mean, variance, M, Im mean], w = 2 (E - mean) / M
+    if (complex_stats_weights(eloc, B, stats, w, st) != cudaSuccess) return NQS_ECUDA;
+    return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
+  }
   if (energy_stats(eloc, B, stats, st) != cudaSuccess) return NQS_ECUDA;
   if (vmc_weights(eloc, stats, B, w, st) != cudaSuccess) return NQS_ECUDA;
   return grad_common(d, L, params, sigma, hcache, w, B, grad, ws, st);
@@ -609,6 +681,7 @@ nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params, 
   nqs_status r = check_desc(desc, &d);
   if (r != NQS_OK) return r;
   if ((r = check_built(d)) != NQS_OK) return r;
+  if (d.phase) return NQS_EUNSUPPORTED;
   if (!params || !sums || !grad || !stats || B < 0) return NQS_EINVAL;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;
   if (misaligned(params) || misaligned(hcache)) return NQS_EINVAL;
@@ -705,6 +778,7 @@ nqs_status nqs_evaluate(const nqs_model_desc* desc, const float* params, const n
   nqs_status r = check_desc(desc, &d);
   if (r != NQS_OK) return r;
   if ((r = check_built(d)) != NQS_OK) return r;
+  if (d.phase || ham == nullptr || ham->kind == NQS_CLUSTER) return ham ? NQS_EUNSUPPORTED : NQS_EINVAL;
   if (!params || !ham || !stats || M < 1 || chunk < 1 || (uint64_t)M > ((uint64_t)1 << 32)) return NQS_EINVAL;
   if (misaligned(params)) return NQS_EINVAL;
   if (chunk > M) chunk = M;
@@ -744,7 +818,8 @@ static nqs_status check_replicas(int R, const nqs_replica* reps, Dims* dims) {
     const nqs_replica& r = reps[i];
     nqs_status s = check_desc(&r.desc, &dims[i]);
     if (s != NQS_OK) return s;
-    if (dims[i].cell != NQS_GRU1D || dims[i].precision != NQS_FP32 || dims[i].sz0) return NQS_EUNSUPPORTED;
+    if (dims[i].cell != NQS_GRU1D || dims[i].precision != NQS_FP32 || dims[i].sz0 || dims[i].phase)
+      return NQS_EUNSUPPORTED;
     if (!batched_supported_d(dims[i].d)) return NQS_EUNSUPPORTED;
     if (r.ham.kind != NQS_TFIM)
       return r.ham.kind == NQS_HEISENBERG || r.ham.kind == NQS_LRTFIM ? NQS_EUNSUPPORTED : NQS_EINVAL;

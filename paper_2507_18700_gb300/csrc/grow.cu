@@ -20,8 +20,8 @@ __device__ TensorShape tensor_shape(int cell, int t, int D, int M) {
       case 2: return {D, D};
       case 3: return {D, 2};
       case 4: case 5: case 6: case 7: return {D, 1};
-      case 8: return {2, D};
-      default: return {2, 1};
+      case 8: case 10: return {2, D};     // U; cRNN U_phi
+      default: return {2, 1};            // c; cRNN c_phi
     }
   }
   switch (t) {
@@ -49,7 +49,7 @@ __device__ void old_index(int cell, int t, int r, int c, int d, int m, int D, in
         break;
       case 2: if (r < d) ocol = hcol(c); break;
       case 3: case 4: case 5: case 6: case 7: if (r < d) ocol = c; break;
-      case 8: ocol = hcol(c); break;
+      case 8: case 10: ocol = hcol(c); break;
       default: ocol = c; break;
     }
   } else {
@@ -74,9 +74,9 @@ __device__ void old_index(int cell, int t, int r, int c, int d, int m, int D, in
   if (ocol >= 0) orow = r;
 }
 
-__global__ void grow_kernel(int cell, int d, int m, int D, int M, const float* __restrict__ ps,
+__global__ void grow_kernel(int cell, int phase, int d, int m, int D, int M, const float* __restrict__ ps,
                             float* __restrict__ pb, uint32_t k0, uint32_t k1, float eps) {
-  const int ntens = cell == NQS_GRU1D ? 10 : 11;
+  const int ntens = cell == NQS_GRU1D ? (phase ? 12 : 10) : 11;   // cRNN: U_phi, c_phi after c
   // offsets of every tensor in both layouts
   int offb = 0, offs = 0;
   for (int t = 0; t < ntens; ++t) {
@@ -104,9 +104,9 @@ __global__ void grow_kernel(int cell, int d, int m, int D, int M, const float* _
 }
 }  // namespace
 
-cudaError_t grow_params(int cell, int d, int m, int D, int M, const float* p_small, float* p_big,
+cudaError_t grow_params(int cell, int phase, int d, int m, int D, int M, const float* p_small, float* p_big,
                         uint64_t seed, float eps, cudaStream_t st) {
-  grow_kernel<<<256, 256, 0, st>>>(cell, d, m, D, M, p_small, p_big, (uint32_t)seed,
+  grow_kernel<<<256, 256, 0, st>>>(cell, phase, d, m, D, M, p_small, p_big, (uint32_t)seed,
                                    (uint32_t)(seed >> 32), eps);
   return cudaGetLastError();
 }

@@ -258,6 +258,24 @@ cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int6
 cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int64_t ld, double* grad,
                                  cudaStream_t st);
 
+// cRNN (phase head) and the cluster Hamiltonian on the FP32 1D path (crnn.cu);
+// phase_params points at [U_phi | c_phi] after the amplitude parameters;
+// logpsi2, eloc and weights2 are [B, 2] float pairs (real, imaginary)
+int crnn_bptt_grid(int64_t B, int D);
+cudaError_t crnn_forward(const Fwd1Args& a, const float* img, const float* phase_params, float* logpsi2, int D,
+                         bool sample, cudaStream_t st);
+// dlog [rows] and, when phase_params is non-null, the phase logits zph [rows, 2]
+cudaError_t crnn_readout(const float* img, const float* phase_params, const float* hcache, float* dlog, float* zph,
+                         int64_t rows, int D, cudaStream_t st);
+// chains and energies of the cluster Hamiltonian (f: B, N, sigma_in, hcache, hdr)
+cudaError_t cluster_local_energy(const Fwd1Args& f, const float* img, const float* phase_params, int phase,
+                                 const float* dlog, const float* zph, float* dre, float* dim, float* eloc,
+                                 unsigned long long* counter, float J, int D, cudaStream_t st);
+// stats = [Re mean, mean |E - mean|^2, M, Im mean] and w = 2 (E - mean) / M (nullable)
+cudaError_t complex_stats_weights(const float* eloc, int64_t B, double* stats, float* w, cudaStream_t st);
+cudaError_t crnn_bptt(const Bptt1Args& a, const float* img, const float* phase_params, const float* weights2, int D,
+                      cudaStream_t st);
+
 // training loop and final evaluation (train.cu)
 struct LrSchedule {
   int kind;            // 0 constant, 1 step at t_switch, 2 inverse decay from t_switch
@@ -286,7 +304,7 @@ cudaError_t tc2d_set_wait_polls(uint32_t polls);
 cudaError_t tc2d_grad_set_wait_polls(uint32_t polls);
 
 // growth (grow.cu)
-cudaError_t grow_params(int cell, int d, int m, int D, int Mm, const float* p_small, float* p_big,
+cudaError_t grow_params(int cell, int phase, int d, int m, int D, int Mm, const float* p_small, float* p_big,
                         uint64_t seed, float eps, cudaStream_t st);
 
 }  // namespace nqs

@@ -51,7 +51,8 @@ extern "C" nqs_status nqs_local_energy_static(const nqs_model_desc* desc, const 
   if (ds != NQS_OK) return ds;
   if (!ham || !params || B < 0) return NQS_EINVAL;
   if (ham->kind != NQS_TFIM && ham->kind != NQS_HEISENBERG && ham->kind != NQS_LRTFIM) return NQS_EINVAL;
-  if (desc->cell != NQS_GRU1D || desc->precision != NQS_FP32 || desc->sz0 != 0 || ham->kind != NQS_TFIM)
+  if (desc->cell != NQS_GRU1D || desc->precision != NQS_FP32 || desc->sz0 != 0 || desc->phase != 0 ||
+      ham->kind != NQS_TFIM)
     return NQS_EUNSUPPORTED;
   const int D = desc->d_h, N = desc->Lx;
   if (B > 0 && (!sigma || !hcache || !eloc)) return NQS_EINVAL;

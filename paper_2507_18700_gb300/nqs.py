@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libnqs.so")
 
 GRU1D, GRU2D = 1, 2
 FP32, BF16 = 0, 1
-TFIM, HEISENBERG, LRTFIM = 1, 2, 3
+TFIM, HEISENBERG, LRTFIM, CLUSTER = 1, 2, 3, 4
 OP_SAMPLE, OP_LOGPSI, OP_LOCAL_ENERGY, OP_LOGPSI_GRAD, OP_VMC_GRAD = 1, 2, 3, 4, 5
 
 STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4: "NQS_ECUDA",
@@ -38,7 +38,7 @@ class NqsError(RuntimeError):
 class ModelDesc(ctypes.Structure):
     _fields_ = [("cell", ctypes.c_int32), ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
                 ("d_h", ctypes.c_int32), ("d_model", ctypes.c_int32), ("sz0", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("phase", ctypes.c_int32)]
 
     @property
     def N(self):
@@ -88,8 +88,8 @@ class Replica(ctypes.Structure):
 MAX_REPLICAS = 16
 
 
-def model_desc(cell, Lx, Ly=1, d_h=8, d_model=0, sz0=False, precision=FP32):
-    return ModelDesc(cell, Lx, Ly, d_h, d_model, int(bool(sz0)), precision)
+def model_desc(cell, Lx, Ly=1, d_h=8, d_model=0, sz0=False, precision=FP32, phase=False):
+    return ModelDesc(cell, Lx, Ly, d_h, d_model, int(bool(sz0)), precision, int(bool(phase)))
 
 
 def tfim(J=1.0, Gamma=1.0):
@@ -99,6 +99,11 @@ def tfim(J=1.0, Gamma=1.0):
 def lr_tfim(alpha, J=1.0, Gamma=1.0):
     """Long-range TFIM of Sec. III C: -J sum_{i<j} Z_i Z_j / |i-j|^alpha - Gamma sum X_i."""
     return HamDesc(LRTFIM, 0, J, Gamma, alpha)
+
+
+def cluster(J=1.0):
+    """Cluster-state Hamiltonian of Sec. III D (stabiliser reading; ground energy -J N)."""
+    return HamDesc(CLUSTER, 0, J, 0.0, 0.0)
 
 
 def heisenberg(J=1.0, marshall=True):
@@ -175,6 +180,12 @@ def _ptr(t):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _per_sample(desc, B):
+    """Shape of a per-sample log psi / local energy / weight: [B] or, for a
+    cRNN, [B, 2] (real and imaginary parts)."""
+    return (B, 2) if desc.phase else (B,)
 
 
 def _need(t, dtype, shape, name):
@@ -263,11 +274,11 @@ def sample(desc, params, B, seed=0, step=0, uniforms=None, hcache=True, ws=None,
         _need(uniforms, torch.float32, (B, N), "uniforms")
     if out is None:
         sigma = torch.empty((B, N), dtype=torch.uint8, device=dev)
-        logpsi = torch.empty((B,), dtype=torch.float32, device=dev)
+        logpsi = torch.empty(_per_sample(desc, B), dtype=torch.float32, device=dev)
     else:
         sigma, logpsi = out
         _need(sigma, torch.uint8, (B, N), "sigma")
-        _need(logpsi, torch.float32, (B,), "logpsi")
+        _need(logpsi, torch.float32, _per_sample(desc, B), "logpsi")
     hc = torch.empty((B, N, d), dtype=torch.float32, device=dev) if hcache is True else hcache
     if hc is not None and hcache is not True:
         _need(hc, torch.float32, (B, N, d), "hcache")
@@ -285,7 +296,7 @@ def logpsi(desc, params, sigma, hcache=True, ws=None):
     B, N = sigma.shape
     _need(params, torch.float32, (param_count(desc),), "params")
     _need(sigma, torch.uint8, (B, desc.N), "sigma")
-    out = torch.empty((B,), dtype=torch.float32, device=dev)
+    out = torch.empty(_per_sample(desc, B), dtype=torch.float32, device=dev)
     hc = torch.empty((B, N, desc.d_h), dtype=torch.float32, device=dev) if hcache is True else hcache
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_LOGPSI))
@@ -300,7 +311,8 @@ def local_energy(desc, params, ham, sigma, hcache, ws=None, out=None):
     _need(params, torch.float32, (param_count(desc),), "params")
     _need(sigma, torch.uint8, (B, desc.N), "sigma")
     _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
-    eloc = torch.empty((B,), dtype=torch.float32, device=dev) if out is None else out
+    eloc = torch.empty(_per_sample(desc, B) if ham.kind == CLUSTER else (B,), dtype=torch.float32,
+                       device=dev) if out is None else out
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_LOCAL_ENERGY, ham))
     _check(lib().nqs_local_energy(ctypes.byref(desc), _ptr(params), ctypes.byref(ham), _ptr(sigma),
@@ -316,7 +328,7 @@ def logpsi_grad(desc, params, sigma, hcache, weights, ws=None, out=None):
     _need(params, torch.float32, (P,), "params")
     _need(sigma, torch.uint8, (B, desc.N), "sigma")
     _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
-    _need(weights, torch.float32, (B,), "weights")
+    _need(weights, torch.float32, _per_sample(desc, B), "weights")
     grad = torch.empty((P,), dtype=torch.float32, device=dev) if out is None else out
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_LOGPSI_GRAD))
@@ -334,9 +346,9 @@ def vmc_grad(desc, params, sigma, hcache, eloc, ws=None, grad=None, stats=None):
     _need(params, torch.float32, (P,), "params")
     _need(sigma, torch.uint8, (B, desc.N), "sigma")
     _need(hcache, torch.float32, (B, desc.N, desc.d_h), "hcache")
-    _need(eloc, torch.float32, (B,), "eloc")
+    _need(eloc, torch.float32, _per_sample(desc, B), "eloc")
     g = torch.empty((P,), dtype=torch.float32, device=dev) if grad is None else grad
-    st = torch.empty((3,), dtype=torch.float64, device=dev) if stats is None else stats
+    st = torch.empty((4 if desc.phase else 3,), dtype=torch.float64, device=dev) if stats is None else stats
     w = _ws(ws, dev)
     wp, wn = w.get(workspace_bytes(desc, B, OP_VMC_GRAD))
     _check(lib().nqs_vmc_grad(ctypes.byref(desc), _ptr(params), _ptr(sigma), _ptr(hcache), _ptr(eloc),

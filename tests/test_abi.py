@@ -43,6 +43,21 @@ def test_param_count_matches_layouts(L, cell, Lx, Ly, d):
     assert n == om.Model(cell, Lx, Ly, d_h=d).param_count() == inputs.param_count(cell, d)
 
 
+@pytest.mark.parametrize("d", [16, 64, 128])
+def test_param_count_of_the_crnn(L, d):
+    desc = nqs.model_desc(1, 30, 1, d, phase=True)
+    assert L.nqs_param_count(ctypes.byref(desc)) == om.Model(1, 30, 1, d_h=d, phase=True).param_count() \
+        == inputs.param_count(1, d, phase=True)
+    # built only on the FP32 1D path with d_h >= 16, and only with the cluster Hamiltonian
+    fake = ctypes.c_void_p(0x1000)
+    for bad in (nqs.model_desc(1, 30, 1, 8, phase=True), nqs.model_desc(1, 30, 1, 32, phase=True, precision=1)):
+        assert L.nqs_logpsi(ctypes.byref(bad), fake, fake, 4, fake, None, fake, 1 << 30, None) == 7
+    assert L.nqs_local_energy(ctypes.byref(desc), fake, ctypes.byref(nqs.tfim()), fake, fake, 4, fake, fake,
+                              1 << 30, None) == 7
+    assert nqs.ModelDesc(1, 30, 1, d, 0, 0, 0, 2).phase == 2
+    assert L.nqs_param_count(ctypes.byref(nqs.ModelDesc(1, 30, 1, d, 0, 0, 0, 2))) == 0
+
+
 def test_bad_descriptors_are_rejected(L):
     bad = [nqs.model_desc(3, 10, 1, 8), nqs.model_desc(1, 10, 2, 8), nqs.model_desc(1, 10, 1, 12),
            nqs.model_desc(1, 0, 1, 8), nqs.model_desc(2, 3, 3, 8, sz0=True),
