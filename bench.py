@@ -635,6 +635,43 @@ def run_eval(args, w):
     print(json.dumps(line))
 
 
+def run_chain_variants(args, w):
+    """Diagnostic: the 1D BF16 chain kernel in each tile variant (one and two
+    threads per row), pinned with the autotuner off, on one sampled batch:
+    prints per-variant CUDA-event times of the local-energy call (median of
+    --steps after --warmup) and the MUFU tanh rate they imply.  Under ncu each
+    variant's chain launch is the only launch of its template instance."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import inputs, nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, N, d = args.batch or w["B"], w["Lx"], w["d"]
+    p = torch.tensor(inputs.xavier_params(1, d, seed=w["seed"], noise_std=w["noise"]).astype(np.float32), device=dev)
+    desc = nqs.model_desc(1, N, 1, d, precision=nqs.BF16)
+    nqs.set_autotune(False)
+    s, _, hc = nqs.sample(desc, p, B, seed=1, step=0)
+    ws = nqs.Workspace(dev)
+    out = {}
+    for v in (0, 1):
+        nqs.set_tile_variant(v)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            nqs.local_energy(desc, p, nqs.tfim(w["J"], w["Gamma"]), s, hc, ws=ws)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        out["threads_per_row_%d" % (v + 1)] = {
+            "ms": ms, "tanh_per_clock_per_sm": 3 * d * B * N * (N - 1) / 2 / (ms * 1e-3 * 2.07e9 * 152)}
+    nqs.set_tile_variant(None)
+    nqs.set_autotune(True)
+    print(json.dumps({"probe": "chain-variants", "workload": w["name"], "batch": B, "variants": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -646,8 +683,13 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
                     help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", default=None, choices=["chain-variants"],
+                    help="diagnostic run instead of the bench line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.probe == "chain-variants":
+        run_chain_variants(args, w)
+        return
     if args.impl == "reference":
         if args.workload == "replicas16":
             t = oracle_replicas_seconds(w, 1, seed=7)
