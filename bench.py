@@ -672,6 +672,48 @@ def run_chain_variants(args, w):
     print(json.dumps({"probe": "chain-variants", "workload": w["name"], "batch": B, "variants": out}))
 
 
+def run_ckpt_probe(args, w):
+    """Diagnostic: teacher forcing + gradient of sum_b w_b log psi_b with the
+    full prefix cache against hidden-state checkpoints every k sites (FP32 1D
+    GRU): CUDA-event times (median of --steps after --warmup) and the bytes of
+    saved states per sample."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import inputs, nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, N, d = args.batch or w["B"], w["Lx"], w["d"]
+    p = torch.tensor(inputs.xavier_params(1, d, seed=w["seed"], noise_std=w["noise"]).astype(np.float32), device=dev)
+    desc = nqs.model_desc(1, N, 1, d)
+    sig, _, _ = nqs.sample(desc, p, B, seed=1, step=0, hcache=None)
+    wts = torch.tensor(inputs.random_weights(B, seed=2).astype(np.float32), device=dev)
+    ws = nqs.Workspace(dev)
+
+    def timed(fn):
+        ts = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    def full():
+        _, hc = nqs.logpsi(desc, p, sig, ws=ws)
+        nqs.logpsi_grad(desc, p, sig, hc, wts, ws=ws)
+
+    out = {"full_cache": {"ms": timed(full), "saved_bytes_per_sample": N * d * 4}}
+    for k in sorted({int(round(N ** 0.5)), 4, 25}):
+        def ck(k=k):
+            _, c = nqs.logpsi_ckpt(desc, p, sig, k, ws=ws)
+            nqs.logpsi_grad_ckpt(desc, p, sig, k, c, wts, ws=ws)
+        out["ckpt_every_%d" % k] = {"ms": timed(ck), "saved_bytes_per_sample": ((N + k - 1) // k - 1) * d * 4}
+    print(json.dumps({"probe": "ckpt", "workload": w["name"], "precision": "fp32", "batch": B, "runs": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -683,12 +725,15 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
                     help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["chain-variants"],
+    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt"],
                     help="diagnostic run instead of the bench line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.probe == "chain-variants":
         run_chain_variants(args, w)
+        return
+    if args.probe == "ckpt":
+        run_ckpt_probe(args, w)
         return
     if args.impl == "reference":
         if args.workload == "replicas16":

@@ -231,6 +231,29 @@ nqs_status nqs_vmc_grad(const nqs_model_desc* desc, const float* params,
                         const float* eloc, int64_t B, float* grad, double* stats,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* Hidden-state checkpointing for the gradient (FP32 1D GRU, positive RNN):
+ * the forward keeps only every k-th state and the reverse sweep recomputes
+ * each segment of k sites from its checkpoint (k ~ sqrt(N) keeps
+ * O(sqrt(N)) states per sample instead of the N of the prefix cache, at the
+ * cost of one more forward).  The gradient equals nqs_logpsi_grad's up to the
+ * FP32 rounding of the per-block partial sums (the segments' partial rows are
+ * summed in FP64).
+ *   ckpt      device [B, ceil(N/k) - 1, d_h] float: ckpt[b, j] = h_{(j+1)k - 1},
+ *             the state that produced the conditional of site (j+1)k - 1
+ *             (nqs_ckpt_floats gives the size; may be NULL when k >= N)
+ *   logpsi    device [B] float (written); weights device [B]; grad device [P]
+ *   ws        nqs_ckpt_workspace_bytes(desc, B, k) bytes (one segment's
+ *             states, two carries, per-block partial rows, 2 P doubles)
+ * Other models return NQS_EUNSUPPORTED. */
+size_t nqs_ckpt_floats(const nqs_model_desc* desc, int64_t B, int32_t k);
+size_t nqs_ckpt_workspace_bytes(const nqs_model_desc* desc, int64_t B, int32_t k);
+nqs_status nqs_logpsi_ckpt(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                           int64_t B, int32_t k, float* logpsi, float* ckpt, void* ws, size_t ws_bytes,
+                           void* stream);
+nqs_status nqs_logpsi_grad_ckpt(const nqs_model_desc* desc, const float* params, const uint8_t* sigma,
+                                int64_t B, int32_t k, const float* ckpt, const float* weights, float* grad,
+                                void* ws, size_t ws_bytes, void* stream);
+
 /* Data-parallel VMC step over ranks (Sec. III; samples are independent, so
  * each rank draws and evaluates its own share of the batch with replicated
  * weights).  The step's only exchange is the energy statistics that centre

@@ -705,6 +705,139 @@ nqs_status nqs_set_wait_limit(int64_t polls) {
 }
 
 // ---------------------------------------------------------------------------
+// Checkpointed teacher forcing and gradient (FP32 1D GRU).
+// ---------------------------------------------------------------------------
+namespace {
+nqs_status check_ckpt(const nqs_model_desc* desc, int64_t B, int32_t k, Dims* d) {
+  nqs_status r = check_desc(desc, d);
+  if (r != NQS_OK) return r;
+  if ((r = check_built(*d)) != NQS_OK) return r;
+  if (d->cell != NQS_GRU1D || d->precision != NQS_FP32 || d->phase) return NQS_EUNSUPPORTED;
+  if (B < 0 || k < 1) return NQS_EINVAL;
+  return NQS_OK;
+}
+int n_ckpt(const Dims& d, int32_t k) { return (d.N + k - 1) / k - 1; }
+struct CkptLayout {
+  size_t img, seg, ca, cb, partial, acc, total;
+};
+CkptLayout ckpt_layout(const Dims& d, int64_t B, int32_t k) {
+  CkptLayout L{};
+  size_t off = sizeof(WsHeader);
+  auto take = [&](size_t bytes) { const size_t at = off; off += align256(bytes); return at; };
+  L.img = take(gru1d_img_floats(d.d) * sizeof(float));
+  L.seg = take((size_t)B * k * d.d * sizeof(float));          // one segment's recomputed states
+  L.ca = take((size_t)B * d.d * sizeof(float));               // carries between segments
+  L.cb = take((size_t)B * d.d * sizeof(float));
+  L.partial = take((size_t)gru1d_bptt_grid(d.d, B) * d.P * sizeof(float));
+  L.acc = take(2 * d.P * sizeof(double));
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+size_t nqs_ckpt_floats(const nqs_model_desc* desc, int64_t B, int32_t k) {
+  Dims d;
+  if (check_ckpt(desc, B, k, &d) != NQS_OK) return 0;
+  return (size_t)B * n_ckpt(d, k) * d.d;
+}
+
+size_t nqs_ckpt_workspace_bytes(const nqs_model_desc* desc, int64_t B, int32_t k) {
+  Dims d;
+  if (check_ckpt(desc, B, k, &d) != NQS_OK) return 0;
+  return ckpt_layout(d, B, k).total;
+}
+
+nqs_status nqs_logpsi_ckpt(const nqs_model_desc* desc, const float* params, const uint8_t* sigma, int64_t B,
+                           int32_t k, float* logpsi, float* ckpt, void* ws, size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_ckpt(desc, B, k, &d);
+  if (r != NQS_OK) return r;
+  if (!params || misaligned(params) || misaligned(ckpt)) return NQS_EINVAL;
+  if (B > 0 && (!sigma || !logpsi || (n_ckpt(d, k) > 0 && !ckpt))) return NQS_EINVAL;
+  const CkptLayout L = ckpt_layout(d, B, k);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < L.img + align256(gru1d_img_floats(d.d) * 4))
+    return NQS_EWORKSPACE;
+  if (B == 0) return NQS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
+  float* img = at<float>(ws, L.img);
+  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  Fwd1Args a{};
+  a.B = B;
+  a.N = d.N;
+  a.sigma_in = sigma;
+  a.logpsi = logpsi;
+  a.hdr = static_cast<WsHeader*>(ws);
+  a.ckpt = n_ckpt(d, k) > 0 ? ckpt : nullptr;
+  a.ck = k;
+  return cuda_status(gru1d_forward(a, img, d.d, false, st));
+}
+
+nqs_status nqs_logpsi_grad_ckpt(const nqs_model_desc* desc, const float* params, const uint8_t* sigma, int64_t B,
+                                int32_t k, const float* ckpt, const float* weights, float* grad, void* ws,
+                                size_t ws_bytes, void* stream) {
+  Dims d;
+  nqs_status r = check_ckpt(desc, B, k, &d);
+  if (r != NQS_OK) return r;
+  if (!params || !grad || misaligned(params) || misaligned(ckpt)) return NQS_EINVAL;
+  if (B > 0 && (!sigma || !weights || (n_ckpt(d, k) > 0 && !ckpt))) return NQS_EINVAL;
+  const CkptLayout L = ckpt_layout(d, B, k);
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < L.total) return NQS_EWORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!reset_status(ws, st)) return NQS_ECUDA;
+  if (B == 0) return cuda_status(cudaMemsetAsync(grad, 0, d.P * sizeof(float), st));
+  float* img = at<float>(ws, L.img);
+  float* seg = at<float>(ws, L.seg);
+  float* carry[2] = {at<float>(ws, L.ca), at<float>(ws, L.cb)};
+  float* partial = at<float>(ws, L.partial);
+  double* acc = at<double>(ws, L.acc);
+  if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+  if (cudaMemsetAsync(acc, 0, d.P * sizeof(double), st) != cudaSuccess) return NQS_ECUDA;
+  const int nseg = n_ckpt(d, k) + 1;
+  const int grid = gru1d_bptt_grid(d.d, B);
+  const int64_t ld = (int64_t)n_ckpt(d, k) * d.d;
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int n0 = s * k, n1 = n0 + k < d.N ? n0 + k : d.N;
+    const float* h0 = s > 0 ? ckpt + (size_t)(s - 1) * d.d : nullptr;
+    // (1) recompute the segment's states from its checkpoint
+    Fwd1Args f{};
+    f.B = B;
+    f.N = d.N;
+    f.sigma_in = sigma;
+    f.hcache = seg;
+    f.hdr = static_cast<WsHeader*>(ws);
+    f.n0 = n0;
+    f.n1 = n1;
+    f.h_init = h0;
+    f.hi_ld = ld;
+    f.hc_rows = k;
+    f.hc_base = n0;
+    if (gru1d_forward(f, img, d.d, false, st) != cudaSuccess) return NQS_ECUDA;
+    // (2) the reverse sweep over the segment, carrying dL/dh across segments
+    if (cudaMemsetAsync(partial, 0, (size_t)grid * d.P * sizeof(float), st) != cudaSuccess) return NQS_ECUDA;
+    Bptt1Args b{};
+    b.B = B;
+    b.N = d.N;
+    b.P = (int)d.P;
+    b.sigma = sigma;
+    b.hcache = seg;
+    b.weights = weights;
+    b.partial = partial;
+    b.n0 = n0;
+    b.n1 = n1;
+    b.h_init = h0;
+    b.hi_ld = ld;
+    b.hc_rows = k;
+    b.hc_base = n0;
+    b.carry_in = s == nseg - 1 ? nullptr : carry[(s + 1) & 1];
+    b.carry_out = s > 0 ? carry[s & 1] : nullptr;
+    if (gru1d_bptt(b, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    if (reduce_partials_acc(partial, grid, (int)d.P, acc, st) != cudaSuccess) return NQS_ECUDA;
+  }
+  return cuda_status(f64_to_f32(acc, grad, (int64_t)d.P, st));
+}
+
+// ---------------------------------------------------------------------------
 // Training loop and final evaluation.
 // ---------------------------------------------------------------------------
 static bool valid_schedule(const nqs_lr_schedule* s) {

@@ -85,13 +85,30 @@ __device__ __forceinline__ void gru1d_forward_body(const float* __restrict__ img
   const int lane = threadIdx.x & 31, ug = lane % TU;
   const int rg = threadIdx.x / TU, r0 = rg * RPT, u0 = ug * UPT;
   const int N = a.N;
+  // a segment [n0, n1) of teacher forcing starts from h_{n0-1} and sigma_{n0-1}
+  const int n0 = a.n0, n1 = a.n1 ? a.n1 : N;
+  const int hcr = a.hc_rows ? a.hc_rows : N;
   int s_prev[RPT];
   float lpsum[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) { s_prev[i] = -1; lpsum[i] = 0.0f; }
+  if (n0 > 0) {
+    __syncthreads();   // the zeroing above and the initial states below touch the same rows
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int64_t b = (int64_t)blk * R + r0 + i;
+      if (b < a.B) {
+        float hv[UPT];
+        ld_units<UPT>(a.h_init + b * (a.hi_ld ? a.hi_ld : D) + u0, hv);
+        st_units<UPT>(hbuf + (n0 & 1) * R * DP + (r0 + i) * DP + u0, hv);
+        s_prev[i] = a.sigma_in[b * N + n0 - 1] ? 1 : 0;
+      }
+    }
+  }
+  const int nck = a.ckpt ? (N + a.ck - 1) / a.ck - 1 : 0;
   __syncthreads();
 
-  for (int n = 0; n < N; ++n) {
+  for (int n = n0; n < n1; ++n) {
     const float* hc = hbuf + (n & 1) * R * DP;
     float* hx = hbuf + ((n + 1) & 1) * R * DP;
     float acc[RPT][3][UPT];
@@ -125,7 +142,8 @@ __device__ __forceinline__ void gru1d_forward_body(const float* __restrict__ img
         } else {
           s = a.sigma_in[b * N + n] ? 1 : 0;
         }
-        if (a.hcache) st_units<UPT>(a.hcache + (b * N + n) * D + u0, hn);
+        if (a.hcache) st_units<UPT>(a.hcache + (b * hcr + n - a.hc_base) * D + u0, hn);
+        if (a.ckpt && n % a.ck == a.ck - 1 && n / a.ck < nck) st_units<UPT>(a.ckpt + (b * nck + n / a.ck) * D + u0, hn);
       }
       lpsum[i] += log_prob(s, d);
       s_prev[i] = s;
@@ -135,7 +153,7 @@ __device__ __forceinline__ void gru1d_forward_body(const float* __restrict__ img
 #pragma unroll
   for (int i = 0; i < RPT; ++i) {
     const int64_t b = (int64_t)blk * R + r0 + i;
-    if (b < a.B && ug == 0) {
+    if (b < a.B && ug == 0 && a.logpsi) {
       const float lp = 0.5f * lpsum[i];
       a.logpsi[b] = lp;
       if (!isfinite(lp)) flag_status(a.hdr, NQS_ENONFINITE);
@@ -286,11 +304,20 @@ __device__ __forceinline__ void gru1d_bptt_body(const float* __restrict__ img, c
     bb[i] = (int64_t)blk * R + r0 + i;
     coef[i] = bb[i] < a.B ? 0.5f * a.weights[bb[i]] : 0.0f;
   }
+  // a segment [n0, n1) starts from the carry of the later sites and hands
+  // dL/dh_{n0-1} on; its first state h_{n0-1} comes from h_init
+  const int n0 = a.n0, n1 = a.n1 ? a.n1 : N;
+  const int hcr = a.hc_rows ? a.hc_rows : N;
   float carry[RPT][UPT];
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+  for (int i = 0; i < RPT; ++i) {
+    if (a.carry_in && bb[i] < a.B) {
+      ld_units<UPT>(a.carry_in + bb[i] * D + u0, carry[i]);
+    } else {
 #pragma unroll
-    for (int j = 0; j < UPT; ++j) carry[i][j] = 0.0f;
+      for (int j = 0; j < UPT; ++j) carry[i][j] = 0.0f;
+    }
+  }
   float dw[DW_REGS ? 3 : 1][UPT][KPT];
   if constexpr (DW_REGS) {
 #pragma unroll
@@ -303,13 +330,17 @@ __device__ __forceinline__ void gru1d_bptt_body(const float* __restrict__ img, c
   float* part = a.partial + (size_t)blk * a.P;
   const Off1 o = off1(D);
 
-  for (int n = N - 1; n >= 0; --n) {
+  for (int n = n1 - 1; n >= n0; --n) {
     // stage h_{n-1} of every row of the tile
     for (int q = threadIdx.x; q < R * (D / 4); q += NT) {
       const int row = q / (D / 4), c4 = q % (D / 4);
       const int64_t b = (int64_t)blk * R + row;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (n > 0 && b < a.B) v = reinterpret_cast<const float4*>(a.hcache + (b * N + n - 1) * D)[c4];
+      if (n > 0 && b < a.B) {
+        const float* src = n > n0 ? a.hcache + (b * hcr + n - 1 - a.hc_base) * D
+                                  : a.h_init + b * (a.hi_ld ? a.hi_ld : D);
+        v = reinterpret_cast<const float4*>(src)[c4];
+      }
       reinterpret_cast<float4*>(Hs + row * DP)[c4] = v;
     }
     __syncthreads();
@@ -455,6 +486,11 @@ __device__ __forceinline__ void gru1d_bptt_body(const float* __restrict__ img, c
     __syncthreads();
   }
 
+  if (a.carry_out) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+      if (bb[i] < a.B) st_units<UPT>(a.carry_out + bb[i] * D + u0, carry[i]);
+  }
   // write this CTA's partial gradient
   if constexpr (DW_REGS) {
 #pragma unroll

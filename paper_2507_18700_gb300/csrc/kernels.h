@@ -22,9 +22,16 @@ struct Fwd1Args {
   uint64_t seed, step;
   uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
   const uint64_t* step_dev;  // sampling: device Philox step (read on the device) or null: step
-  float* logpsi;
+  float* logpsi;             // nullable for a segment (n0 > 0 or n1 < N)
   float* hcache;             // nullable
   WsHeader* hdr;
+  // segments (FP32 1D teacher forcing, checkpointed gradient); zero = whole chain
+  int n0, n1;                // sites [n0, n1) of this call (n1 = 0: N)
+  const float* h_init;       // h_{n0-1} of sample b at h_init + b * hi_ld (n0 > 0)
+  int64_t hi_ld;             // floats between samples in h_init (0: d)
+  int hc_rows, hc_base;      // cache row of site n: b * hc_rows + n - hc_base (hc_rows = 0: N)
+  float* ckpt;               // nullable: h_{(j+1) ck - 1} -> ckpt[b, j], j < ceil(N / ck) - 1
+  int ck;
 };
 
 struct Chain1Args {
@@ -45,6 +52,13 @@ struct Bptt1Args {
   const float* hcache;
   const float* weights;      // [B] dL/dlogpsi
   float* partial;            // [grid, P]
+  // segments (checkpointed gradient); zero = whole chain
+  int n0, n1;                // sites [n0, n1) (n1 = 0: N)
+  const float* h_init;       // h_{n0-1} of sample b at h_init + b * hi_ld (n0 > 0)
+  int64_t hi_ld;
+  int hc_rows, hc_base;      // cache row of site n: b * hc_rows + n - hc_base (hc_rows = 0: N)
+  const float* carry_in;     // [B, d] dL/dh_{n1-1} from the later sites, or null
+  float* carry_out;          // [B, d] dL/dh_{n0-1} (n0 > 0), or null
 };
 
 int gru1d_supported(int D);
@@ -61,6 +75,10 @@ cudaError_t tfim_eloc(const uint8_t* sigma, const float* dlog, const float* delt
 cudaError_t lrtfim_eloc(const uint8_t* sigma, const float* dlog, const float* delta, float* eloc, int64_t B,
                         int N, double J, double Gamma, double alpha, WsHeader* hdr, cudaStream_t st);
 cudaError_t gru1d_bptt(const Bptt1Args& a, const float* img, int D, cudaStream_t st);
+// acc[p] += sum of the partial rows (FP64), for gradients accumulated over
+// segments; acc has 2 P doubles (the second half is scratch)
+cudaError_t reduce_partials_acc(const float* partial, int rows, int P, double* acc, cudaStream_t st);
+cudaError_t f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st);
 
 struct Eng2Args {
   int64_t B;

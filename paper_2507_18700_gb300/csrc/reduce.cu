@@ -147,8 +147,37 @@ cudaError_t reduce_partials_cols(const float* partial, int rows, int ncols, int6
   return reduce_cols(partial, rows, ncols, ld, grad, st);
 }
 
+// acc[p] += grad of the partial rows (FP64): the checkpointed gradient sums
+// its segments' partial rows this way.
+__global__ void add_f64_kernel(const double* __restrict__ x, double* __restrict__ acc, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] += x[i];
+}
+__global__ void f64_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 cudaError_t reduce_partials(const float* partial, int rows, int P, float* grad, cudaStream_t st) {
   return reduce_partials_cols(partial, rows, P, P, grad, st);
+}
+
+cudaError_t reduce_partials_acc(const float* partial, int rows, int P, double* acc, cudaStream_t st) {
+  // the segment's sum goes to the P doubles after acc, then is added in
+  double* seg = acc + P;
+  cudaError_t e = reduce_partials_cols(partial, rows, P, P, seg, st);
+  if (e != cudaSuccess) return e;
+  const int blocks = (P + 255) / 256 < 1024 ? (P + 255) / 256 : 1024;
+  add_f64_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(seg, acc, P);
+  return cudaGetLastError();
+}
+
+cudaError_t f64_to_f32(const double* x, float* y, int64_t n, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  f64_to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
 }
 cudaError_t reduce_partials(const float* partial, int rows, int P, double* grad, cudaStream_t st) {
   return reduce_partials_cols(partial, rows, P, P, grad, st);

@@ -26,7 +26,8 @@ EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sam
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
            "nqs_set_autotune", "nqs_set_tile_variant", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit", "nqs_adam_step",
-           "nqs_record_stats", "nqs_evaluate_workspace_bytes", "nqs_evaluate"]
+           "nqs_record_stats", "nqs_evaluate_workspace_bytes", "nqs_evaluate", "nqs_ckpt_floats",
+           "nqs_ckpt_workspace_bytes", "nqs_logpsi_ckpt", "nqs_logpsi_grad_ckpt"]
 
 
 class NqsError(RuntimeError):
@@ -131,6 +132,14 @@ def lib():
     L.nqs_grow_hidden.argtypes = [P(ModelDesc), vp, P(ModelDesc), vp, u64, ctypes.c_float, vp]
     L.nqs_sample.restype = ctypes.c_int
     L.nqs_sample.argtypes = [P(ModelDesc), vp, i64, u64, u64, vp, u64, vp, vp, vp, vp, vp, sz, vp]
+    L.nqs_ckpt_floats.restype = sz
+    L.nqs_ckpt_floats.argtypes = [P(ModelDesc), i64, ctypes.c_int32]
+    L.nqs_ckpt_workspace_bytes.restype = sz
+    L.nqs_ckpt_workspace_bytes.argtypes = [P(ModelDesc), i64, ctypes.c_int32]
+    L.nqs_logpsi_ckpt.restype = ctypes.c_int
+    L.nqs_logpsi_ckpt.argtypes = [P(ModelDesc), vp, vp, i64, ctypes.c_int32, vp, vp, vp, sz, vp]
+    L.nqs_logpsi_grad_ckpt.restype = ctypes.c_int
+    L.nqs_logpsi_grad_ckpt.argtypes = [P(ModelDesc), vp, vp, i64, ctypes.c_int32, vp, vp, vp, vp, sz, vp]
     L.nqs_adam_step.restype = ctypes.c_int
     L.nqs_adam_step.argtypes = [vp, vp, vp, vp, vp, i64, P(AdamDesc), P(LrSchedule), u64, vp, vp]
     L.nqs_record_stats.restype = ctypes.c_int
@@ -427,25 +436,64 @@ def grow_hidden(small, p_small, big, seed=2, eps=1e-3):
     return p_big
 
 
+def logpsi_ckpt(desc, params, sigma, k, ws=None):
+    """Teacher-forced log psi keeping every k-th state: (logpsi [B], ckpt)."""
+    B = sigma.shape[0]
+    _need(params, torch.float32, (param_count(desc),), "params")
+    _need(sigma, torch.uint8, (B, desc.N), "sigma")
+    n = lib().nqs_ckpt_floats(ctypes.byref(desc), int(B), int(k))
+    out = torch.empty((B,), dtype=torch.float32, device=params.device)
+    ck = torch.empty((max(n, 1),), dtype=torch.float32, device=params.device)
+    w = _ws(ws, params.device)
+    wp, wn = w.get(lib().nqs_ckpt_workspace_bytes(ctypes.byref(desc), int(B), int(k)))
+    _check(lib().nqs_logpsi_ckpt(ctypes.byref(desc), _ptr(params), _ptr(sigma), int(B), int(k), _ptr(out),
+                                 _ptr(ck), wp, wn, _stream()), "nqs_logpsi_ckpt")
+    return out, ck[:n]
+
+
+def logpsi_grad_ckpt(desc, params, sigma, k, ckpt, weights, ws=None):
+    """Gradient of sum_b w_b log psi_b from the checkpoints of logpsi_ckpt."""
+    B = sigma.shape[0]
+    P = param_count(desc)
+    _need(params, torch.float32, (P,), "params")
+    _need(weights, torch.float32, (B,), "weights")
+    grad = torch.empty((P,), dtype=torch.float32, device=params.device)
+    w = _ws(ws, params.device)
+    wp, wn = w.get(lib().nqs_ckpt_workspace_bytes(ctypes.byref(desc), int(B), int(k)))
+    _check(lib().nqs_logpsi_grad_ckpt(ctypes.byref(desc), _ptr(params), _ptr(sigma), int(B), int(k),
+                                      _ptr(ckpt) if ckpt.numel() else None, _ptr(weights), _ptr(grad), wp, wn,
+                                      _stream()), "nqs_logpsi_grad_ckpt")
+    return grad
+
+
 class LogPsi(torch.autograd.Function):
     """log psi(sigma) with the library's reverse sweep as its backward.
 
-    forward(params, sigma, desc) -> logpsi [B]; backward gives d params of
-    sum_b grad_out_b * logpsi_b (sigma is not differentiable).
+    forward(params, sigma, desc, checkpoint=None) -> logpsi [B] ([B, 2] for a
+    cRNN); backward gives d params of sum_b grad_out_b * logpsi_b (sigma is not
+    differentiable).  With checkpoint = k the forward keeps every k-th hidden
+    state only (FP32 1D GRU) and the backward recomputes the segments.
     """
 
     @staticmethod
-    def forward(ctx, params, sigma, desc):
+    def forward(ctx, params, sigma, desc, checkpoint=None):
+        ctx.desc, ctx.k = desc, checkpoint
+        if checkpoint:
+            lp, ck = logpsi_ckpt(desc, params.detach(), sigma, int(checkpoint))
+            ctx.save_for_backward(params, sigma, ck)
+            return lp
         lp, hc = logpsi(desc, params.detach(), sigma, hcache=True)
         ctx.save_for_backward(params, sigma, hc)
-        ctx.desc = desc
         return lp
 
     @staticmethod
     def backward(ctx, grad_out):
-        params, sigma, hc = ctx.saved_tensors
-        g = logpsi_grad(ctx.desc, params.detach(), sigma, hc, grad_out.contiguous().float())
-        return g, None, None
+        params, sigma, saved = ctx.saved_tensors
+        if ctx.k:
+            g = logpsi_grad_ckpt(ctx.desc, params.detach(), sigma, int(ctx.k), saved, grad_out.contiguous().float())
+        else:
+            g = logpsi_grad(ctx.desc, params.detach(), sigma, saved, grad_out.contiguous().float())
+        return g, None, None, None
 
 
 class ReplicaBatch:
