@@ -339,7 +339,7 @@ def run_gpu(args, w):
 
     r32 = measure(nqs.FP32)
     chosen, r16, check = r32, None, None
-    bf16_ok = args.precision != "fp32" and not phase and (w["d"] in (16, 32, 64) if w["cell"] == 1
+    bf16_ok = args.precision != "fp32" and not phase and (w["d"] in (16, 32, 64, 128) if w["cell"] == 1
                                                           else w["d"] in (32, 64) and N <= 128)
     if bf16_ok:
         r16 = measure(nqs.BF16)
@@ -420,12 +420,13 @@ def run_gpu(args, w):
         print(json.dumps(line))
 
 
-def replica_models(w, dev):
+def replica_models(w, dev, precision=None):
     """The growth family: for each field a Xavier d_h = 16 model, embedded into
     d_h = 32, 64, 128 by nqs_grow_hidden (seed 2, eps 1e-3)."""
     import numpy as np
     import torch
     from paper_2507_18700_gb300 import inputs, nqs
+    precision = nqs.FP32 if precision is None else precision
     models = []
     for fi, G in enumerate(w["fields"]):
         small = nqs.model_desc(nqs.GRU1D, w["Lx"], 1, w["sizes"][0])
@@ -434,7 +435,8 @@ def replica_models(w, dev):
             desc = nqs.model_desc(nqs.GRU1D, w["Lx"], 1, d)
             if si > 0:
                 p = nqs.grow_hidden(small, p, desc, seed=2, eps=1e-3)
-            models.append((desc, nqs.tfim(w["J"], G), w["B"], 5000 + 16 * fi + si, p))
+            models.append((nqs.model_desc(nqs.GRU1D, w["Lx"], 1, d, precision=precision), nqs.tfim(w["J"], G),
+                           w["B"], 5000 + 16 * fi + si, p))
             small = desc
     return models
 
@@ -459,112 +461,149 @@ def run_replicas(args, w):
     from paper_2507_18700_gb300 import nqs
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    models = replica_models(w, dev)
-    R = len(models)
-    total_B = sum(m[2] for m in models)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
     def events():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    # (1) batched step captured in a CUDA graph, device-side step counter
-    batch = nqs.ReplicaBatch(models, device_step=True)
-    side = torch.cuda.Stream()
-    side.wait_stream(st)
-    with torch.cuda.stream(side):
-        for _ in range(args.warmup):
+    def measure(models):
+        """(1) the batched step captured in a CUDA graph with the device step
+        counter, (2) the same step without the graph, (3) 3 x R separate calls,
+        (4) end to end: parameters in from pinned host memory, gradients and
+        statistics out."""
+        batch = nqs.ReplicaBatch(models, device_step=True)
+        side = torch.cuda.Stream()
+        side.wait_stream(st)
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                batch.step()
+        st.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
             batch.step()
-    st.wait_stream(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        batch.step()
-    graph.replay()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    g_ms = []
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = events()
-        torch.cuda.synchronize()
-        a.record(st)
         graph.replay()
-        b.record(st)
         torch.cuda.synchronize()
-        g_ms.append(a.elapsed_time(b))
-    clk = clocks.stop()
-    # (2) the same step without the graph, and (3) as 3 x R separate calls
-    e_ms, s_ms = [], []
-    ws = nqs.Workspace(dev)
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = events()
-        torch.cuda.synchronize()
-        a.record(st)
-        batch.step()
-        b.record(st)
-        torch.cuda.synchronize()
-        e_ms.append(a.elapsed_time(b))
-        flush.zero_()
-        a, b = events()
-        torch.cuda.synchronize()
-        a.record(st)
-        for (desc, ham, B, seed, p) in models:
-            sg, _, hc = nqs.sample(desc, p, B, seed=seed, step=k, ws=ws)
-            el = nqs.local_energy(desc, p, ham, sg, hc, ws=ws)
-            nqs.vmc_grad(desc, p, sg, hc, el, ws=ws)
-        b.record(st)
-        torch.cuda.synchronize()
-        s_ms.append(a.elapsed_time(b))
-    # end to end: parameters of every replica in from pinned host memory, gradients and stats out
-    host_p = [m[4].cpu().pin_memory() for m in models]
-    host_g = [torch.empty_like(h).pin_memory() for h in host_p]
-    host_s = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in models]
-    x_ms = []
-    for k in range(args.steps):
-        flush.zero_()
-        a, b = events()
-        torch.cuda.synchronize()
-        a.record(st)
-        for hp, m in zip(host_p, models):
-            m[4].copy_(hp, non_blocking=True)
-        graph.replay()
-        for hg, hs, o in zip(host_g, host_s, batch.out):
-            hg.copy_(o["grad"], non_blocking=True)
-            hs.copy_(o["stats"], non_blocking=True)
-        b.record(st)
-        torch.cuda.synchronize()
-        x_ms.append(a.elapsed_time(b))
-    status = batch.ws.status()
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        g_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            graph.replay()
+            b.record(st)
+            torch.cuda.synchronize()
+            g_ms.append(a.elapsed_time(b))
+        clk = clocks.stop()
+        e_ms, s_ms = [], []
+        ws = nqs.Workspace(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            batch.step()
+            b.record(st)
+            torch.cuda.synchronize()
+            e_ms.append(a.elapsed_time(b))
+            flush.zero_()
+            a, b = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            for (desc, ham, B, seed, p) in models:
+                sg, _, hc = nqs.sample(desc, p, B, seed=seed, step=k, ws=ws)
+                el = nqs.local_energy(desc, p, ham, sg, hc, ws=ws)
+                nqs.vmc_grad(desc, p, sg, hc, el, ws=ws)
+            b.record(st)
+            torch.cuda.synchronize()
+            s_ms.append(a.elapsed_time(b))
+        host_p = [m[4].cpu().pin_memory() for m in models]
+        host_g = [torch.empty_like(h).pin_memory() for h in host_p]
+        host_s = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in models]
+        x_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = events()
+            torch.cuda.synchronize()
+            a.record(st)
+            for hp, m in zip(host_p, models):
+                m[4].copy_(hp, non_blocking=True)
+            graph.replay()
+            for hg, hs, o in zip(host_g, host_s, batch.out):
+                hg.copy_(o["grad"], non_blocking=True)
+                hs.copy_(o["stats"], non_blocking=True)
+            b.record(st)
+            torch.cuda.synchronize()
+            x_ms.append(a.elapsed_time(b))
+        return dict(step_ms=sum(g_ms) / len(g_ms), no_graph_ms=sum(e_ms) / len(e_ms),
+                    separate_ms=sum(s_ms) / len(s_ms), e2e_ms=sum(x_ms) / len(x_ms), clk=clk,
+                    status=batch.ws.status(), P_bytes=sum(h.numel() * 4 for h in host_p),
+                    energy_per_site=[float(o["stats"][0].item()) / w["Lx"] for o in batch.out])
+
+    m32 = replica_models(w, dev, nqs.FP32)
+    m16 = [(nqs.model_desc(1, d.Lx, 1, d.d_h, precision=nqs.BF16), h, B, sd, p) for (d, h, B, sd, p) in m32]
+    r32 = measure(m32)
+    r16 = measure(m16) if args.precision != "fp32" else None
+    # BF16 against FP32 on the same configurations, replica by replica
+    check = None
+    if r16 is not None:
+        de, cos_min = 0.0, 1.0
+        for (d32, ham, B, seed, p), (d16, _, _, _, _) in zip(m32, m16):
+            sg, _, _ = nqs.sample(d32, p, B, seed=77, step=0, hcache=None)
+            res = []
+            for desc in (d16, d32):
+                _, hc = nqs.logpsi(desc, p, sg)
+                el = nqs.local_energy(desc, p, ham, sg, hc)
+                g, stt = nqs.vmc_grad(desc, p, sg, hc, el)
+                res.append((float(stt[0].item()) / w["Lx"], g.double()))
+            de = max(de, abs(res[0][0] - res[1][0]))
+            cos_min = min(cos_min, float(res[0][1] @ res[1][1] / (res[0][1].norm() * res[1][1].norm())))
+        check = {"max_energy_per_site_diff": de, "min_grad_cosine": cos_min,
+                 "pass": bool(de <= 1e-4 and cos_min >= 0.999)}
+    chosen = r16 if (r16 is not None and (check["pass"] or args.precision == "bf16")) else r32
+    models = m16 if chosen is r16 else m32
+    R = len(models)
+    total_B = sum(m[2] for m in models)
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     N = w["Lx"]
     flops = sum(2 * (3 * m[0].d_h ** 2 + 2 * m[0].d_h) * m[2] * (N + N * (N - 1) // 2 + 2 * N) for m in models)
-    step_s = sum(g_ms) / len(g_ms) * 1e-3
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    step_s = chosen["step_ms"] * 1e-3
     achieved = flops / step_s / 1e12
-    P_bytes = sum(h.numel() * 4 for h in host_p)
+    if chosen is r16:
+        peak = pk.get("bf16_tflops", 1887.4)
+        roof = {"bound": "tensor", "kernel": "nqs_vmc_step_batched (whole step, BF16 tcgen05 replicas)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "bf16_tflops (burst) of measured peaks (%s)" % src}
+    else:
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "nqs_vmc_step_batched (whole step; chains dominate)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)}
     line = {
         "metric": METRIC, "value": total_B / step_s, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": chosen["step_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if chosen is r16 else "f32", "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": total_B, "seq_len": N, "replicas": R,
-                   "parallelism": "single", "precision": "fp32",
+                   "parallelism": "single",
+                   "precision": ("bf16 tensor-core replicas (d_h 16-128; the d_h 128 gradient on the FP32 sweep)"
+                                 if chosen is r16 else "fp32"),
+                   "fp32_value": total_B / (r32["step_ms"] * 1e-3), "fp32_ms_per_step": r32["step_ms"],
+                   "bf16_check": check,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "no_graph_ms_per_step": sum(e_ms) / len(e_ms),
-                   "separate_calls_ms_per_step": sum(s_ms) / len(s_ms),
-                   "energy_per_site": [float(o["stats"][0].item()) / N for o in batch.out],
-                   "device_status": status},
-        "roofline": {"bound": "alu", "kernel": "nqs_vmc_step_batched (whole step; chains dominate)",
-                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                     "traffic": None,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x %s MHz (%s)" % (sm_mhz, src)},
-        "e2e": {"value": total_B / (sum(x_ms) / len(x_ms) * 1e-3), "unit": "samples/s",
-                "h2d_bytes_per_step": P_bytes, "d2h_bytes_per_step": P_bytes + 24 * R},
-        "gpu_launches": 10 * args.steps,
-        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+                   "no_graph_ms_per_step": chosen["no_graph_ms"],
+                   "separate_calls_ms_per_step": chosen["separate_ms"],
+                   "energy_per_site": chosen["energy_per_site"],
+                   "device_status": chosen["status"]},
+        "roofline": roof,
+        "e2e": {"value": total_B / (chosen["e2e_ms"] * 1e-3), "unit": "samples/s",
+                "h2d_bytes_per_step": chosen["P_bytes"], "d2h_bytes_per_step": chosen["P_bytes"] + 24 * R},
+        "gpu_launches": (10 if chosen is r32 else 17 * R + 3 * R) * args.steps,
+        "clocks": {"sm_mhz": chosen["clk"]["sm_mhz"], "sm_max_mhz": chosen["clk"]["sm_max_mhz"],
+                   "reasons": chosen["clk"]["reasons"]},
     }
     if not args.no_cpu_baseline:
         n = 2

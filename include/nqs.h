@@ -100,7 +100,9 @@ typedef struct {
   int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of
                          sampling, teacher forcing, the local-energy chains and
                          the reverse sweep on the tensor cores (BF16 operands,
-                         FP32 accumulation and FP32 state; d_h in {16, 32, 64}),
+                         FP32 accumulation and FP32 state; d_h in {16, 32, 64};
+                         at d_h = 128 sampling, teacher forcing and the chains,
+                         with the FP32 reverse sweep on the prefix cache),
                          and the 2D cell and GLU GEMMs of sampling, teacher
                          forcing, the Heisenberg chains and the reverse
                          sweep (d_h in {32, 64}, N <= 128); other shapes
@@ -344,7 +346,10 @@ nqs_status nqs_evaluate(const nqs_model_desc* desc, const float* params, const n
 /* One replica of a batched VMC step. */
 #define NQS_MAX_REPLICAS 16
 typedef struct {
-  nqs_model_desc desc;   /* NQS_GRU1D, NQS_FP32, sz0 = 0, d_h in {16, 32, 64, 128} */
+  nqs_model_desc desc;   /* NQS_GRU1D, sz0 = 0, phase = 0, d_h in {16, 32, 64, 128};
+                            NQS_FP32 replicas run as grouped launches over all
+                            of them, NQS_BF16 replicas the tensor-core calls of
+                            one model each (autotuned tiles) */
   nqs_ham_desc ham;      /* NQS_TFIM */
   int64_t B;             /* samples of this replica, >= 1 */
   uint64_t seed;         /* Philox key of this replica's sampling */
@@ -363,9 +368,12 @@ size_t nqs_vmc_step_batched_workspace_bytes(int R, const nqs_replica* reps);
 /* A whole VMC step (nqs_sample + nqs_local_energy + nqs_vmc_grad) for R
  * replicas of uneven hidden size, field, batch and chain length -- the model
  * family of the Adaptive schedule (Sec. II B), e.g. one model per growth
- * stage and field.  Every phase is one launch over all replicas (the chain
- * phase is persistent and balances the replicas' work), and the replica table
- * travels as a kernel argument, so the call can be captured in a CUDA graph.
+ * stage and field.  For the FP32 replicas every phase is one launch over all
+ * of them (the chain phase is persistent and balances the replicas' work),
+ * and the replica table travels as a kernel argument; the BF16 replicas run
+ * first, each through the single-model tensor-core calls on the same stream
+ * and Philox step.  The call can be captured in a CUDA graph (after a first
+ * call outside the capture, which tunes the BF16 tiles).
  *   reps      host array of R replicas (1 <= R <= NQS_MAX_REPLICAS)
  *   step      Philox step of the sampling when step_dev is NULL
  *   step_dev  device counter or NULL: when given, the step is read from it on

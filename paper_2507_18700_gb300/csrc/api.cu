@@ -59,6 +59,9 @@ nqs_status check_built(const Dims& d) {
 }
 
 bool use_tc(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU1D; }
+// the BF16 reverse sweep is built for d_h <= 64; at d_h = 128 the BF16 model's
+// gradient runs the FP32 reverse sweep on the (FP32) prefix cache
+bool use_tc_grad(const Dims& d) { return use_tc(d) && d.d <= 64; }
 // flat offset of the cRNN phase layer [U_phi | c_phi] (after the amplitude parameters)
 size_t phase_offset(const Dims& d) { return 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2; }
 bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
@@ -124,7 +127,7 @@ Layout layout(const Dims& d, int64_t B, int op) {
         L.j = take(tc2d_grad_image_bytes(B, d.N, d.d, 5));                         // tape: factors
         break;
       }
-      if (use_tc(d)) {
+      if (use_tc_grad(d)) {
         L.a = take((size_t)tc1d_bptt_partial_rows(B) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                 // weights
         L.e = take(tc1d_tape_bytes(B, d.N, d.d, 0));                            // tape: e
@@ -200,7 +203,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     if (crnn_bptt(a, img, params + phase_offset(d), weights, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, grid, (int)d.P, grad, st));
   }
-  if (use_tc(d)) {
+  if (use_tc_grad(d)) {
     uint8_t* w3 = at<uint8_t>(ws, L.w);
     uint8_t* wt = at<uint8_t>(ws, L.w2);
     if (gru1d_pack(params, img, d.d, st) != cudaSuccess) return NQS_ECUDA;
@@ -951,9 +954,9 @@ static nqs_status check_replicas(int R, const nqs_replica* reps, Dims* dims) {
     const nqs_replica& r = reps[i];
     nqs_status s = check_desc(&r.desc, &dims[i]);
     if (s != NQS_OK) return s;
-    if (dims[i].cell != NQS_GRU1D || dims[i].precision != NQS_FP32 || dims[i].sz0 || dims[i].phase)
+    if (dims[i].cell != NQS_GRU1D || dims[i].sz0 || dims[i].phase) return NQS_EUNSUPPORTED;
+    if (dims[i].precision == NQS_FP32 ? !batched_supported_d(dims[i].d) : !tc1d_supported(dims[i].d))
       return NQS_EUNSUPPORTED;
-    if (!batched_supported_d(dims[i].d)) return NQS_EUNSUPPORTED;
     if (r.ham.kind != NQS_TFIM)
       return r.ham.kind == NQS_HEISENBERG || r.ham.kind == NQS_LRTFIM ? NQS_EUNSUPPORTED : NQS_EINVAL;
     if (r.B < 1) return NQS_EINVAL;
@@ -961,9 +964,13 @@ static nqs_status check_replicas(int R, const nqs_replica* reps, Dims* dims) {
   return NQS_OK;
 }
 
+// FP32 replicas run as grouped launches over all of them (their counters and
+// partial rows contiguous, in replica order); BF16 replicas run the
+// tensor-core calls of one model each, one after the other, in a shared
+// inner workspace.
 struct BatchLayout {
   size_t counters, img[NQS_MAX_REPLICAS], dlog[NQS_MAX_REPLICAS], delta[NQS_MAX_REPLICAS],
-      w[NQS_MAX_REPLICAS], partial[NQS_MAX_REPLICAS], total;
+      w[NQS_MAX_REPLICAS], partial[NQS_MAX_REPLICAS], inner, inner_bytes, total;
 };
 
 static BatchLayout batch_layout(int R, const nqs_replica* reps, const Dims* dims) {
@@ -972,16 +979,27 @@ static BatchLayout batch_layout(int R, const nqs_replica* reps, const Dims* dims
   L.counters = off;
   off += align256((size_t)R * sizeof(unsigned long long));
   for (int i = 0; i < R; ++i) {
+    if (dims[i].precision != NQS_FP32) continue;
     const size_t BN = (size_t)reps[i].B * dims[i].N;
     L.img[i] = off; off += align256(gru1d_img_floats(dims[i].d) * sizeof(float));
     L.dlog[i] = off; off += align256(BN * sizeof(float));
     L.delta[i] = off; off += align256(BN * sizeof(float));
     L.w[i] = off; off += align256((size_t)reps[i].B * sizeof(float));
   }
-  for (int i = 0; i < R; ++i) {   // contiguous, replica 0 first
+  for (int i = 0; i < R; ++i) {   // contiguous, first FP32 replica first
+    if (dims[i].precision != NQS_FP32) continue;
     L.partial[i] = off;
     off += align256((size_t)batched_bptt_blocks(dims[i].d, reps[i].B) * dims[i].P * sizeof(float));
   }
+  for (int i = 0; i < R; ++i) {
+    if (dims[i].precision == NQS_FP32) continue;
+    for (int op : {NQS_OP_SAMPLE, NQS_OP_LOCAL_ENERGY, NQS_OP_VMC_GRAD}) {
+      const size_t b = layout(dims[i], reps[i].B, op).total;
+      if (b > L.inner_bytes) L.inner_bytes = b;
+    }
+  }
+  L.inner = off;
+  off += align256(L.inner_bytes);
   L.total = off;
   return L;
 }
@@ -1006,10 +1024,36 @@ nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, u
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 || ws_bytes < L.total) return NQS_EWORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!reset_status(ws, st)) return NQS_ECUDA;
-  BatchRep br[NQS_MAX_REPLICAS];
+  // BF16 replicas first (they read the step before the grouped launches advance it)
+  void* inner = at<void>(ws, L.inner);
+  WsHeader* hdr = static_cast<WsHeader*>(ws);
+  int nf = 0;
   for (int i = 0; i < R; ++i) {
     const nqs_replica& p = reps[i];
-    BatchRep& b = br[i];
+    if (dims[i].precision == NQS_FP32) {
+      ++nf;
+      continue;
+    }
+    if ((r = nqs_sample(&p.desc, p.params, p.B, p.seed, step, step_dev, 0, nullptr, p.sigma, p.logpsi, p.hcache,
+                        inner, L.inner_bytes, stream)) != NQS_OK)
+      return r;
+    if (status_merge(static_cast<const WsHeader*>(inner), hdr, st) != cudaSuccess) return NQS_ECUDA;
+    if ((r = nqs_local_energy(&p.desc, p.params, &p.ham, p.sigma, p.hcache, p.B, p.eloc, inner, L.inner_bytes,
+                              stream)) != NQS_OK)
+      return r;
+    if (status_merge(static_cast<const WsHeader*>(inner), hdr, st) != cudaSuccess) return NQS_ECUDA;
+    if ((r = nqs_vmc_grad(&p.desc, p.params, p.sigma, p.hcache, p.eloc, p.B, p.grad, p.stats, inner,
+                          L.inner_bytes, stream)) != NQS_OK)
+      return r;
+    if (status_merge(static_cast<const WsHeader*>(inner), hdr, st) != cudaSuccess) return NQS_ECUDA;
+  }
+  if (nf == 0) return step_dev ? cuda_status(step_increment(step_dev, st)) : NQS_OK;
+  BatchRep br[NQS_MAX_REPLICAS];
+  int nb = 0;
+  for (int i = 0; i < R; ++i) {
+    const nqs_replica& p = reps[i];
+    if (dims[i].precision != NQS_FP32) continue;
+    BatchRep& b = br[nb++];
     b.d = dims[i].d;
     b.N = dims[i].N;
     b.P = (int)dims[i].P;
@@ -1029,9 +1073,9 @@ nqs_status nqs_vmc_step_batched(int R, const nqs_replica* reps, uint64_t step, u
     b.delta = at<float>(ws, L.delta[i]);
     b.partial = at<float>(ws, L.partial[i]);
     b.w = at<float>(ws, L.w[i]);
-    b.counter = at<unsigned long long>(ws, L.counters) + i;
+    b.counter = at<unsigned long long>(ws, L.counters) + (nb - 1);
   }
-  return cuda_status(batched_step(br, R, step, step_dev, step_dev, st));
+  return cuda_status(batched_step(br, nb, step, step_dev, step_dev, st));
 }
 
 }  // extern "C"

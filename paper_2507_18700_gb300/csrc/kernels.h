@@ -311,6 +311,7 @@ struct AdamArgs {
 cudaError_t adam_update(const float* grad32, const double* grad64, float* params, float* m, float* v, int64_t P,
                         const AdamArgs& a, uint64_t* t_dev, cudaStream_t st);
 cudaError_t record_stats(const double* stats, double* log, int64_t cap, const uint64_t* t_dev, cudaStream_t st);
+cudaError_t step_increment(uint64_t* t_dev, cudaStream_t st);
 cudaError_t energy_sums_acc(const float* eloc, int64_t B, double* sums, cudaStream_t st);
 cudaError_t eval_stats(const double* sums, double* stats, cudaStream_t st);
 cudaError_t status_merge(const WsHeader* from, WsHeader* into, cudaStream_t st);

@@ -134,15 +134,23 @@ __device__ __forceinline__ float hw_tanh(float x) {
 template <int D, int GROUPS, int SPLIT>
 struct Smem {
   static constexpr int KA = D + 16;                              // A columns: [h | 1 1 | onehot x2 | 0]
-  static constexpr int kB = 0;                                   // weights, 4D x KA bf16
-  static constexpr int kA = kB + 4 * D * KA * 2;                 // GROUPS x 128 x KA bf16
+  // d_h = 128: the x_in block (W_in s + b_in depends on the input spin only)
+  // comes from a 3 x D FP32 table instead of the MMA, so the weight operand
+  // keeps 3D rows and the accumulators 3D columns (the 4D rows would not fit
+  // shared memory beside the A operand and the staging buffer)
+  static constexpr bool XT = D >= 128;
+  static constexpr int kRowsB = (XT ? 3 : 4) * D;                // weight operand rows
+  static constexpr int kTmemCols = GROUPS * 4 * D <= 256 ? 256 : 512;
+  static constexpr int kB = 0;                                   // weights, kRowsB x KA bf16
+  static constexpr int kA = kB + kRowsB * KA * 2;                // GROUPS x 128 x KA bf16
   static constexpr int kDU = kA + GROUPS * 128 * KA * 2;        // D floats: U[0] - U[1]
   static constexpr int kZ = kDU + D * 4;                         // GROUPS x SPLIT x 128 floats
   static constexpr int kJob = kZ + GROUPS * SPLIT * 128 * 4;     // GROUPS x 128 long long
   static constexpr int HS = D + 4;                               // staging row stride (floats; conflict-free float4)
   static constexpr int kStage = kJob + GROUPS * 128 * 8;         // GROUPS x 128 x HS floats: next chain state
                                                                  // (chains) or the new states (cache stores)
-  static constexpr int kBar = (kStage + GROUPS * 128 * HS * 4 + 15) / 16 * 16;   // GROUPS MMA + 1 drain
+  static constexpr int kXin = kStage + GROUPS * 128 * HS * 4;    // XT: x_in table [no input | s = 0 | s = 1][D]
+  static constexpr int kBar = (kXin + (XT ? 3 * D * 4 : 0) + 15) / 16 * 16;   // GROUPS MMA + 1 drain
   static constexpr int kSlot = kBar + 8 * (GROUPS + 1);
   static constexpr int kFlags = kSlot + 16;                      // ping-pong idle flags, one int per tile
   static constexpr int kUsed = kFlags + 16;
@@ -183,10 +191,18 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   volatile int* idle_flag = reinterpret_cast<volatile int*>(sm + S::kFlags);
 
   // ---- prologue: operands and constants into shared memory, TMEM, barriers ----
-  for (int i = threadIdx.x; i < N4 * KA * 2 / 16; i += NT)
+  for (int i = threadIdx.x; i < S::kRowsB * KA * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(wimg)[i];
   // readout: only the logit difference d = (U_0 - U_1) h + c_0 - c_1 is used
   for (int i = threadIdx.x; i < D; i += NT) dUs[i] = img[10 * D + i] - img[11 * D + i];
+  float* xin = reinterpret_cast<float*>(sm + S::kXin);
+  if constexpr (S::XT) {
+    // x_in = b_in + W_in onehot(s) in FP32 (image: Ws[s][2D + u] = W_in[u][s], Bs[3D + u] = b_in[u])
+    for (int i = threadIdx.x; i < 3 * D; i += NT) {
+      const int sv = i / D - 1, u = i % D;
+      xin[i] = img[6 * D + 3 * D + u] + (sv >= 0 ? img[sv * 3 * D + 2 * D + u] : 0.0f);
+    }
+  }
   tc::fence_async_smem();
   if (threadIdx.x == 0) {
     for (int g = 0; g < GROUPS; ++g) tc::mbar_init(&mbar[g], 1);
@@ -194,7 +210,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 2) idle_flag[threadIdx.x] = 0;
-  if (threadIdx.x < 32) tc::tmem_alloc(tslot, GROUPS == 2 ? 512 : 256);
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -339,12 +355,26 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     tc::fence_after_sync();
     // ---- (b) one thread issues the tile's MMAs ----
     if (any && tt == 0) {
-      constexpr uint32_t idesc = tc::make_idesc_bf16(128, N4);
+      if constexpr (S::XT) {
+        // 3D = 384 gate rows: u and r (N = 256) and q (N = 128) as two MMAs per K step
+        constexpr uint32_t idesc0 = tc::make_idesc_bf16(128, 256), idesc1 = tc::make_idesc_bf16(128, D);
+        constexpr uint32_t row256 = (256 / 8) * (KA / 8) * 128;   // byte offset of weight row 256
 #pragma unroll
-      for (int k = 0; k < KA / 16; ++k) {
-        const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (KA / 8) * 128);
-        const uint64_t db = tc::make_desc(tc::smem_addr(sB) + k * 256, 128, (KA / 8) * 128);
-        tc::mma_bf16(tbase + (uint32_t)(g * 256), da, db, idesc, k > 0);
+        for (int k = 0; k < KA / 16; ++k) {
+          const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (KA / 8) * 128);
+          const uint64_t db0 = tc::make_desc(tc::smem_addr(sB) + k * 256, 128, (KA / 8) * 128);
+          const uint64_t db1 = tc::make_desc(tc::smem_addr(sB) + row256 + k * 256, 128, (KA / 8) * 128);
+          tc::mma_bf16(tbase, da, db0, idesc0, k > 0);
+          tc::mma_bf16(tbase + 256u, da, db1, idesc1, k > 0);
+        }
+      } else {
+        constexpr uint32_t idesc = tc::make_idesc_bf16(128, N4);
+#pragma unroll
+        for (int k = 0; k < KA / 16; ++k) {
+          const uint64_t da = tc::make_desc(tc::smem_addr(sA) + k * 256, 128, (KA / 8) * 128);
+          const uint64_t db = tc::make_desc(tc::smem_addr(sB) + k * 256, 128, (KA / 8) * 128);
+          tc::mma_bf16(tbase + (uint32_t)(g * 256), da, db, idesc, k > 0);
+        }
       }
       tc::mma_commit(&mbar[g]);
     }
@@ -375,7 +405,14 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
       tmem_ld8(trow + cu, bf[0]);
       tmem_ld8(trow + D + cu, bf[1]);
       tmem_ld8(trow + 2 * D + cu, bf[2]);
-      tmem_ld8(trow + 3 * D + cu, bf[3]);
+      if constexpr (S::XT) {
+        const float* xr = xin + (s_in + 1) * D + cu;
+        const float4 x0 = lds4(xr), x1 = lds4(xr + 4);
+        bf[3][0] = x0.x; bf[3][1] = x0.y; bf[3][2] = x0.z; bf[3][3] = x0.w;
+        bf[3][4] = x1.x; bf[3][5] = x1.y; bf[3][6] = x1.z; bf[3][7] = x1.w;
+      } else {
+        tmem_ld8(trow + 3 * D + cu, bf[3]);
+      }
     };
     if (any && wact) issue(0, bufA);
     if constexpr (PP) {
@@ -581,7 +618,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
   if (__syncthreads_or(timed_out) && tt == 0) tc::drain_mmas(&mbar[GROUPS], kWaitLimit);
   __syncthreads();
   tc::fence_after_sync();
-  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, GROUPS == 2 ? 512 : 256);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, S::kTmemCols);
 }
 
 // ----------------------------------------------------------------------------
@@ -1286,7 +1323,7 @@ cudaError_t launch_tc(const Tc1Args& a, const float* img, const uint8_t* wimg, c
   if (MODE == 2) {
     const int64_t jobs = a.B * (int64_t)(a.N - 1);
     grid = sm_count_tc();
-    const int64_t need = (jobs + 255) / 256;
+    const int64_t need = (jobs + 128 * GROUPS - 1) / (128 * GROUPS);
     if (grid > need) grid = need;
   } else {
     grid = (a.B + (int64_t)a.rows * GROUPS - 1) / ((int64_t)a.rows * GROUPS);
@@ -1359,46 +1396,67 @@ cudaError_t tuned_launch(int kind, int D, int N, int64_t B, int nvar, Launch lau
 template <int D>
 cudaError_t dispatch_mode(const Tc1Args& a, const float* img, const uint8_t* wimg, int mode, cudaStream_t st) {
   auto none = []() { return cudaSuccess; };
-  if (mode == 2) {
-    // chains: 1 or 2 threads per row (the work counter is reset before every run)
-    auto reset = [&]() { return cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st); };
-    Tc1Args c = a;
-    c.rows = 128;
+  if constexpr (D == 128) {
+    // one tile per CTA (its 3D accumulator columns take TMEM's 512), 2 or 4
+    // threads per row (64 or 32 units each); chains without ping-pong
+    if (mode == 2) {
+      auto reset = [&]() { return cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st); };
+      Tc1Args c = a;
+      c.rows = 128;
+      auto run = [&](int v) {
+        return v == 1 ? launch_tc<D, 2, 1, 4>(c, img, wimg, st) : launch_tc<D, 2, 1, 2>(c, img, wimg, st);
+      };
+      return tuned_launch(2, D, a.N, a.B, 2, run, reset, st);
+    }
     auto run = [&](int v) {
-      if (v == 1 && D >= 32) return launch_tc<D, 2, 2, (D >= 32 ? 2 : 1)>(c, img, wimg, st);
-      return launch_tc<D, 2, 2, 1>(c, img, wimg, st);
+      Tc1Args b = a;
+      b.rows = 128 >> (v / 2);
+      if (mode == 0) return v % 2 ? launch_tc<D, 0, 1, 4>(b, img, wimg, st) : launch_tc<D, 0, 1, 2>(b, img, wimg, st);
+      return v % 2 ? launch_tc<D, 1, 1, 4>(b, img, wimg, st) : launch_tc<D, 1, 1, 2>(b, img, wimg, st);
     };
-    return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
-  }
-  // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128, 64 or
-  // 32 rows per tile (partly filled tiles put more SMs on a small batch); at
-  // d_h = 64 the 32-row tile has its A rows in all four lane quarters instead
-  const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
-  auto run = [&](int v) {
-    Tc1Args b = a;
-    b.rows = 128 >> (v / ns);
-    const int sv = v % ns;
-    if constexpr (D == 64) {
-      if (v >= 2 * ns) {
-        b.rows = 32;
-        return mode == 0 ? launch_tc<D, 0, 1, 1, 4>(b, img, wimg, st) : launch_tc<D, 1, 1, 1, 4>(b, img, wimg, st);
+    return tuned_launch(mode, D, a.N, a.B, 6, run, none, st);
+  } else {
+    if (mode == 2) {
+      // chains: 1 or 2 threads per row (the work counter is reset before every run)
+      auto reset = [&]() { return cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st); };
+      Tc1Args c = a;
+      c.rows = 128;
+      auto run = [&](int v) {
+        if (v == 1 && D >= 32) return launch_tc<D, 2, 2, (D >= 32 ? 2 : 1)>(c, img, wimg, st);
+        return launch_tc<D, 2, 2, 1>(c, img, wimg, st);
+      };
+      return tuned_launch(2, D, a.N, a.B, D >= 32 ? 2 : 1, run, reset, st);
+    }
+    // sampling / teacher forcing: 1, 2 or 4 threads per row, times 128, 64 or
+    // 32 rows per tile (partly filled tiles put more SMs on a small batch); at
+    // d_h = 64 the 32-row tile has its A rows in all four lane quarters instead
+    const int ns = D >= 64 ? 3 : (D >= 32 ? 2 : 1);
+    auto run = [&](int v) {
+      Tc1Args b = a;
+      b.rows = 128 >> (v / ns);
+      const int sv = v % ns;
+      if constexpr (D == 64) {
+        if (v >= 2 * ns) {
+          b.rows = 32;
+          return mode == 0 ? launch_tc<D, 0, 1, 1, 4>(b, img, wimg, st) : launch_tc<D, 1, 1, 1, 4>(b, img, wimg, st);
+        }
       }
-    }
-    if (mode == 0) {
-      if (sv == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
-      if (sv == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
-      return launch_tc<D, 0, 1, 1>(b, img, wimg, st);
-    }
-    if (sv == 2 && D >= 64) return launch_tc<D, 1, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
-    if (sv == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
-    return launch_tc<D, 1, 1, 1>(b, img, wimg, st);
-  };
-  return tuned_launch(mode, D, a.N, a.B, D == 64 ? 2 * ns + 1 : 3 * ns, run, none, st);
+      if (mode == 0) {
+        if (sv == 2 && D >= 64) return launch_tc<D, 0, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
+        if (sv == 1 && D >= 32) return launch_tc<D, 0, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
+        return launch_tc<D, 0, 1, 1>(b, img, wimg, st);
+      }
+      if (sv == 2 && D >= 64) return launch_tc<D, 1, 1, (D >= 64 ? 4 : 1)>(b, img, wimg, st);
+      if (sv == 1 && D >= 32) return launch_tc<D, 1, 1, (D >= 32 ? 2 : 1)>(b, img, wimg, st);
+      return launch_tc<D, 1, 1, 1>(b, img, wimg, st);
+    };
+    return tuned_launch(mode, D, a.N, a.B, D == 64 ? 2 * ns + 1 : 3 * ns, run, none, st);
+  }
 }
 
 }  // namespace
 
-int tc1d_supported(int D) { return D == 16 || D == 32 || D == 64; }
+int tc1d_supported(int D) { return D == 16 || D == 32 || D == 64 || D == 128; }
 
 void tc1d_set_autotune(int on) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1568,6 +1626,7 @@ cudaError_t tc1d_run(const Tc1Args& a, const float* img, const uint8_t* wimg, in
     case 16: return dispatch_mode<16>(a, img, wimg, mode, st);
     case 32: return dispatch_mode<32>(a, img, wimg, mode, st);
     case 64: return dispatch_mode<64>(a, img, wimg, mode, st);
+    case 128: return dispatch_mode<128>(a, img, wimg, mode, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -128,6 +128,11 @@ cudaError_t adam_update(const float* grad32, const double* grad64, float* params
   return cudaGetLastError();
 }
 
+cudaError_t step_increment(uint64_t* t_dev, cudaStream_t st) {
+  step_incr_kernel<<<1, 1, 0, st>>>(t_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t record_stats(const double* stats, double* log, int64_t cap, const uint64_t* t_dev, cudaStream_t st) {
   record_stats_kernel<<<1, 1, 0, st>>>(stats, log, cap, t_dev);
   return cudaGetLastError();

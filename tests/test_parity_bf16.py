@@ -54,7 +54,7 @@ def setup(N, d, seed=1, noise=0.1):
             flat.astype(np.float64), torch.tensor(flat, device=DEV))
 
 
-@pytest.mark.parametrize("N,d,B", [(12, 16, 256), (40, 32, 300), (100, 64, 200), (7, 64, 129)])
+@pytest.mark.parametrize("N,d,B", [(12, 16, 256), (40, 32, 300), (100, 64, 200), (7, 64, 129), (100, 128, 130)])
 def test_bf16_logpsi_and_cache(N, d, B):
     desc, mod, pf, p = setup(N, d)
     sig = inputs.random_configs(B, N, seed=5)
@@ -62,7 +62,8 @@ def test_bf16_logpsi_and_cache(N, d, B):
     torch.cuda.synchronize()
     ref = om.run(mod, pf, sigma=sig.astype(np.int64))
     np.testing.assert_allclose(lp.cpu().numpy(), ref["logpsi"], atol=2e-4 * N, rtol=0)
-    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=1e-2, rtol=0)
+    # the cache error grows with the number of BF16 products per gate (d_h + 16)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=1e-2 if d <= 64 else 2e-2, rtol=0)
 
 
 @pytest.mark.parametrize("N,d,B", [(20, 16, 512), (100, 64, 256)])
@@ -204,3 +205,59 @@ def test_autotuned_variants_agree_bitwise():
     for lo, hi in ((3, 6), (6, 9), (9, 12)):
         for o in outs[lo + 1:hi]:
             assert torch.equal(o[6], outs[lo][6])
+
+def test_bf16_d128_against_oracle():
+    """d_h = 128 on the tensor cores (one 128-row tile per CTA, the x_in block
+    from an FP32 table, 2 or 4 threads per row): log psi and cache, every
+    sampling draw (window 2e-3: twice the d_h = 64 window, the gate GEMMs sum
+    twice as many BF16 products), per-sample local energies, and the gradient
+    (the FP32 reverse sweep on the cache of the BF16 forward)."""
+    N, d, B = 60, 128, 200
+    desc, mod, pf, p = setup(N, d)
+    sig = inputs.random_configs(B, N, seed=61)
+    lp, hc = nqs.logpsi(desc, p, torch.tensor(sig, device=DEV))
+    torch.cuda.synchronize()
+    ref = om.run(mod, pf, sigma=sig.astype(np.int64))
+    np.testing.assert_allclose(lp.cpu().numpy(), ref["logpsi"], atol=2e-4 * N, rtol=0)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=2e-2, rtol=0)
+    s, lps, hcs = nqs.sample(desc, p, B, seed=9, step=4)
+    torch.cuda.synchronize()
+    frac, _ = check_draws(mod, pf, s.cpu().numpy(), philox.sampling_uniforms(9, 4, B, N), 2e-3)
+    assert frac <= 1e-2, frac
+    sm = om.sample(mod, pf, philox.sampling_uniforms(62, 0, B, N))["sigma"]
+    sg = torch.tensor(sm.astype(np.uint8), device=DEV)
+    ws = nqs.Workspace(DEV)
+    _, hc2 = nqs.logpsi(desc, p, sg, ws=ws)
+    el = nqs.local_energy(desc, p, nqs.tfim(1.0, 1.0), sg, hc2, ws=ws)
+    g, st = nqs.vmc_grad(desc, p, sg, hc2, el, ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    e_ref = oh.tfim_local_energy(N, 1.0, 1.0, sm, lambda x: om.logpsi(mod, pf, x))
+    e16 = el.double().cpu().numpy()
+    assert abs(e16.mean() - e_ref.mean()) / N <= 1e-4
+    assert_eloc_per_sample(e16, e_ref, sm, 1.0, 1.0, N)
+    g_ref = ov.vmc_gradient(mod, pf, sm.astype(np.int64), e_ref)
+    gg = g.double().cpu().numpy()
+    assert gg @ g_ref / (np.linalg.norm(gg) * np.linalg.norm(g_ref)) >= 0.999
+
+
+def test_bf16_d128_variants_agree_bitwise():
+    """Every d_h = 128 tile variant (2 or 4 threads per row; 128, 64 or 32 rows
+    per tile for sampling / teacher forcing) gives bitwise the same samples,
+    log psi, cache and local energies."""
+    N, d, B = 40, 128, 300
+    desc, mod, pf, p = setup(N, d)
+    outs = []
+    for v in range(6):
+        nqs.set_tile_variant(v)
+        s, lp, hc = nqs.sample(desc, p, B, seed=5, step=1)
+        lpt, hct = nqs.logpsi(desc, p, s)
+        el = nqs.local_energy(desc, p, nqs.tfim(), s, hc)
+        torch.cuda.synchronize()
+        outs.append((s.clone(), lp.clone(), hc.clone(), lpt.clone(), hct.clone(), el.clone()))
+    nqs.set_tile_variant(None)
+    assert torch.isfinite(outs[0][5]).all()
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert torch.equal(x, y)
+    assert torch.equal(outs[0][1], outs[0][3]) and torch.equal(outs[0][2], outs[0][4])
