@@ -753,6 +753,30 @@ def run_ckpt_probe(args, w):
     print(json.dumps({"probe": "ckpt", "workload": w["name"], "precision": "fp32", "batch": B, "runs": out}))
 
 
+def run_batched_probe(args, w):
+    """Diagnostic: the replica family's batched step on the BF16 path, eagerly
+    (no graph), for launch lists: prints the median step time."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m32 = replica_models(w, dev, nqs.FP32)
+    models = [(nqs.model_desc(1, d.Lx, 1, d.d_h, precision=nqs.BF16), h, B, sd, p) for (d, h, B, sd, p) in m32]
+    batch = nqs.ReplicaBatch(models)
+    ts = []
+    for k in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.step(step_no=k)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ts.append(a.elapsed_time(b))
+    print(json.dumps({"probe": "batched", "workload": w["name"], "precision": "bf16",
+                      "ms_per_step": float(np.median(ts)), "device_status": batch.ws.status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -764,7 +788,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
                     help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt"],
+    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt", "batched"],
                     help="diagnostic run instead of the bench line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -773,6 +797,9 @@ def main():
         return
     if args.probe == "ckpt":
         run_ckpt_probe(args, w)
+        return
+    if args.probe == "batched":
+        run_batched_probe(args, w)
         return
     if args.impl == "reference":
         if args.workload == "replicas16":
