@@ -165,10 +165,8 @@ template <int D> struct Tune1 {
   static constexpr int F_NT = D >= 16 ? 128 : 64;
   static constexpr int C_RPT = D >= 128 ? 2 : 4;
   static constexpr int C_NT = D >= 16 ? 256 : 128;
-  // reverse sweep: at d_h = 128 one row per lane group and 128 threads, so
-  // that a batch of a few thousand samples still spreads over every SM
-  static constexpr int B_RPT = D >= 128 ? 1 : 2;
-  static constexpr int B_NT = D >= 128 ? 128 : (D >= 16 ? 256 : 64);
+  static constexpr int B_RPT = 2;
+  static constexpr int B_NT = D >= 16 ? 256 : 64;
   static constexpr bool WSMEM_F = D <= 64;
   static constexpr bool WSMEM_B = D <= 64;
 };
