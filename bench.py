@@ -179,15 +179,51 @@ def oracle_step_seconds(w, n_samples, seed):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(w, target_s=12.0):
-    n = 8
-    t = oracle_step_seconds(w, n, seed=100)
-    n2 = max(8, min(w["B"], int(n * target_s / max(t, 1e-3))))
-    t2 = oracle_step_seconds(w, n2, seed=101)
-    return {"value": n2 / t2, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d of the %d samples of one step (sampling, E_loc by full re-evaluation, "
-                      "gradient), float64 numpy, BLAS on all host cores" % (n2, w["B"]),
-            "seconds": t2}
+def _single_thread_blas():
+    """Pool initializer: one BLAS thread per worker (set before numpy loads)."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_share(job):
+    w, n, seed = job
+    return oracle_step_seconds(w, n, seed), n
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def cpu_baseline(w, target_s=8.0):
+    """The float64 oracle on the host: single-threaded, and one single-threaded
+    worker process per core (spawned, so no process is forked after the GPU
+    calls) on disjoint samples; throughput = samples / the slowest worker's
+    time (worker start-up excluded)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    with ctx.Pool(1, initializer=_single_thread_blas) as pool:
+        t, _ = pool.apply(_oracle_share, ((w, 4, 100),))
+        n1 = max(4, min(w["B"], int(4 * target_s / max(t, 1e-3))))
+        t1, _ = pool.apply(_oracle_share, ((w, n1, 101),))
+    single = n1 / t1
+    per = max(2, min(max(1, w["B"] // cores), int(single * target_s)))
+    with ctx.Pool(cores, initializer=_single_thread_blas) as pool:
+        res = pool.map(_oracle_share, [(w, per, 200 + i) for i in range(cores)])
+    slowest = max(r[0] for r in res)
+    return {"value": per * cores / slowest, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "single_thread": single, "cpu_model": cpu_model(),
+            "sample": "one single-threaded worker per core on %d samples each (%d of the %d samples of a step "
+                      "in all; sampling, E_loc by full re-evaluation, gradient; float64 numpy); single thread: "
+                      "%d samples" % (per, per * cores, w["B"], n1),
+            "seconds": slowest}
 
 
 def run_reference(args, w):
@@ -355,9 +391,9 @@ def run_gpu(args, w):
         d = w["d"]
         mufu = sum(chosen["cells"]) * 3 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
         mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
-        # DRAM bytes of one chain launch from an ncu capture of the 1D chain kernel
-        # at B = 1024 (profiles/chain_tc1d_tfim_n100_d64_bf16.md): 26,543,616
-        # bytes read, 0 written, i.e. the prefix cache read once; scaled by B
+        # DRAM bytes of one chain launch, from an ncu capture of the 1D chain
+        # kernel at B = 1024 (dram__bytes_read.sum 26,543,616, write 0: the
+        # prefix cache read once), scaled by B (traffic grows with B)
         traffic = (26543616 * B / 1024.0) if (w["cell"] == 1 and w["d"] == 64 and N == 100) else None
         roof = {"bound": "tensor",
                 "kernel": "nqs_local_energy (prefix-cached %s chains, tcgen05 BF16)"
