@@ -376,7 +376,8 @@ def run_gpu(args, w):
     r32 = measure(nqs.FP32)
     chosen, r16, check = r32, None, None
     bf16_ok = args.precision != "fp32" and not phase and (w["d"] in (16, 32, 64, 128) if w["cell"] == 1
-                                                          else w["d"] in (32, 64) and N <= 128)
+                                                          else (w["d"] in (32, 64) and N <= 128)
+                                                          or (w["d"] == 256 and N <= 256))
     if bf16_ok:
         r16 = measure(nqs.BF16)
         check = accuracy_check(r16["desc"], r32["desc"])
@@ -416,11 +417,14 @@ def run_gpu(args, w):
     # tape, sweep, two reductions); 2D FP32 sample 2, E_loc 5, gradient 5;
     # 2D BF16 sample 2, E_loc 7 (pack, bonds, cached-path tables, job count,
     # jobs, chains, energies), gradient 8 (statistics, weights, pack, tape,
-    # sweep, weight gradients, readout gradient, reduction)
+    # sweep, weight gradients, readout gradient, reduction); 2D BF16 at d_h =
+    # 256: E_loc 8 (the tables' up-spin prefix counts as one more), gradient 5
+    # (the FP32 reverse sweep)
+    wide = w["cell"] == 2 and w["d"] == 256
     if w["cell"] == 1:
         launches = 17 if chosen is r16 else 11
     else:
-        launches = 17 if chosen is r16 else 12
+        launches = (15 if wide else 17) if chosen is r16 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,
@@ -430,6 +434,9 @@ def run_gpu(args, w):
                    "parallelism": "dp%d (samples split over ranks; all-reduce of energy statistics and gradient)"
                                   % world if world > 1 else "single",
                    "precision": ("bf16 tensor-core cell GEMMs, fp32 state" if w["cell"] == 1 else
+                                 "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs, weights "
+                                 "streamed from L2 through a shared-memory ring), fp32 state; gradient on the "
+                                 "fp32 reverse sweep" if wide else
                                  "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs) "
                                  "and reverse sweep, fp32 state") if chosen is r16 else "fp32",
                    "fp32_value": world * B * args.steps / (r32["total_ms"] * 1e-3),

@@ -45,8 +45,9 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
 }
 
 // Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, the BF16
-// tensor-core 1D GRU for d_h in {16, 32, 64} and the BF16 tensor-core 2D GRU
-// for d_h in {32, 64} and N <= 128 (configurations as 128-bit masks).
+// tensor-core 1D GRU for d_h in {16, 32, 64, 128} and the BF16 tensor-core 2D
+// GRU for d_h in {32, 64} with N <= 128 (configurations as 128-bit masks) and
+// for d_h = 256 with N <= 256.
 nqs_status check_built(const Dims& d) {
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
   // the cRNN phase head: FP32 1D GRU, d_h >= 16
@@ -65,6 +66,9 @@ bool use_tc_grad(const Dims& d) { return use_tc(d) && d.d <= 64; }
 // flat offset of the cRNN phase layer [U_phi | c_phi] (after the amplitude parameters)
 size_t phase_offset(const Dims& d) { return 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2; }
 bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
+// the 2D BF16 reverse sweep is built for d_h <= 64; at d_h = 256 the BF16
+// model's gradient runs the FP32 reverse sweep on the (FP32) prefix cache
+bool use_tc2d_grad(const Dims& d) { return use_tc2d(d) && d.d <= 64; }
 
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
@@ -110,12 +114,12 @@ Layout layout(const Dims& d, int64_t B, int op) {
         L.c = take(BN * 2 * sizeof(float));                   // lp_tab
         L.e = take(BN * sizeof(int));                         // nup_tab
         L.f = take((size_t)B * n_bonds(d) * sizeof(float));   // delta
-        if (use_tc2d(d)) L.g = take(tc2d_jobs_bytes(B, n_bonds(d)));   // chain jobs
+        if (use_tc2d(d)) L.g = take(tc2d_jobs_bytes(B, n_bonds(d), d.N, d.d));   // chain jobs
       }
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
-      if (use_tc2d(d)) {
+      if (use_tc2d_grad(d)) {
         L.a = take((size_t)tc2d_grad_partial_rows(B, d.N) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                     // weights
         L.c = take((size_t)B * d.Lx * d.d * sizeof(float));                        // vertical carries
@@ -224,7 +228,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
   }
-  if (use_tc2d(d)) {
+  if (use_tc2d_grad(d)) {
     uint8_t* wimg = at<uint8_t>(ws, L.w);
     const int rows = tc2d_grad_partial_rows(B, d.N);
     if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
@@ -701,7 +705,7 @@ nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params, 
 
 nqs_status nqs_set_wait_limit(int64_t polls) {
   const uint32_t v = polls < 0 ? tc_default_wait_polls() : (uint32_t)(polls > 0xFFFFFFFFll ? 0xFFFFFFFFll : polls);
-  if (tc1d_set_wait_polls(v) != cudaSuccess || tc2d_set_wait_polls(v) != cudaSuccess ||
+  if (tc1d_set_wait_polls(v) != cudaSuccess || tc2d_set_wait_polls(v) != cudaSuccess || tc2dw_set_wait_polls(v) != cudaSuccess ||
       tc2d_grad_set_wait_polls(v) != cudaSuccess)
     return NQS_ECUDA;
   return NQS_OK;

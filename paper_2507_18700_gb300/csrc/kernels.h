@@ -138,19 +138,27 @@ struct Tc2Chains {
   const int4* bonds;
   float* delta;              // [B, nb]
   float* colbuf;             // tc2d_colbuf_floats(B, Lx, d)
-  uint8_t* jobs_ws;          // tc2d_jobs_bytes(B, nb)
+  uint8_t* jobs_ws;          // tc2d_jobs_bytes(B, nb, N, d)
   unsigned long long* counter;
   WsHeader* hdr;
 };
 int tc2d_supported(int D, int Lx, int N);
 size_t tc2d_wimg_bytes(int D);
-size_t tc2d_jobs_bytes(int64_t B, int nb);
+size_t tc2d_jobs_bytes(int64_t B, int nb, int N, int D);
 size_t tc2d_colbuf_floats(int64_t B, int Lx, int D);
 cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st);
 cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st);
 // cached-path tables (lp_tab, nup_tab) from sigma_in and hcache of f, all cells in parallel
 cudaError_t tc2d_tables(const Tc2Fwd& f, const uint8_t* wimg, int D, cudaStream_t st);
 cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st);
+// d_h = 256 (tc2d_wide.cu), reached through the tc2d_* calls above: the
+// weights stream from global memory through a shared-memory ring; the image
+// has the same size as tc2d_wimg_bytes(256) in another layout
+cudaError_t tc2dw_pack(const float* params, uint8_t* wimg, cudaStream_t st);
+cudaError_t tc2dw_forward(const Tc2Fwd& f, const uint8_t* wimg, bool sample, cudaStream_t st);
+cudaError_t tc2dw_tables(const Tc2Fwd& f, const uint8_t* wimg, cudaStream_t st);
+cudaError_t tc2dw_chains(const Tc2Chains& c, const uint8_t* wimg, const uint8_t* jobs, const int* njobs, cudaStream_t st);
+cudaError_t tc2dw_set_wait_polls(uint32_t polls);
 
 // BF16 tensor-core 2D reverse sweep (tc2d_grad.cu)
 struct Tc2Grad {

@@ -86,13 +86,7 @@ __global__ void pack2d_tc_kernel(const float* __restrict__ p, uint8_t* __restric
 // Heisenberg chain jobs: the antiparallel (sample, bond) pairs in bond order
 // (bonds sorted by the earlier zig-zag position: longest chains first), with
 // each chain's start values taken from the cached-path tables.
-struct Job2 {
-  int b, rank;
-  float acc0;          // 1/2 [log p_pa(s_new) - log p_pa(s_old)]
-  int nup0;            // up spins before pa+1 on the exchanged configuration
-  uint64_t mask[2];    // exchanged configuration, bit k = spin of lattice site k
-};
-static_assert(sizeof(Job2) == 32, "job record is 32 bytes");
+using Job2 = JobT<2>;
 
 __global__ void heis_count_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds, int64_t B,
                                   int N, int* __restrict__ counts) {
@@ -110,10 +104,11 @@ __global__ void heis_count_kernel(const uint8_t* __restrict__ sigma, const int4*
   }
 }
 
+template <int NW>
 __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds,
                                                         const float* __restrict__ lp_tab, const int* __restrict__ nup_tab,
                                                         const int* __restrict__ counts, int64_t B, int N, int nb,
-                                                        Job2* __restrict__ jobs, int* __restrict__ njobs) {
+                                                        JobT<NW>* __restrict__ jobs, int* __restrict__ njobs) {
   __shared__ int wsum[32];
   __shared__ int base_s;
   const int rank = blockIdx.x;
@@ -146,7 +141,7 @@ __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restri
     }
     if (anti) {
       const int idx = base + before + __popc(bal & ((1u << lane) - 1u));
-      Job2 jb;
+      JobT<NW> jb;
       jb.b = (int)b;
       jb.rank = rank;
       const int pa = bd.z;
@@ -154,14 +149,12 @@ __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restri
       // bond.x sits at position pa and takes the partner's spin sb
       jb.acc0 = 0.5f * (lp_tab[(row + pa) * 2 + sb] - lp_tab[(row + pa) * 2 + sa]);
       jb.nup0 = nup_tab[row + pa] + (sb == 0 ? 1 : 0);
-      uint64_t m0 = 0, m1 = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) jb.mask[w] = 0ull;
       for (int k = 0; k < N; ++k) {
         const int kk = k == bd.x ? bd.y : k == bd.y ? bd.x : k;
-        const uint64_t s = sigma[row + kk] ? 1ull : 0ull;
-        if (k < 64) m0 |= s << k; else m1 |= s << (k - 64);
+        if (sigma[row + kk]) jb.mask[k >> 6] |= 1ull << (k & 63);
       }
-      jb.mask[0] = m0;
-      jb.mask[1] = m1;
       jobs[idx] = jb;
     }
     base += total;
@@ -906,6 +899,7 @@ cudaError_t launch2_fwd64(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2
 }  // namespace
 
 int tc2d_supported(int D, int Lx, int N) {
+  if (D == 256) return N <= 256 && Lx >= 1;   // tc2d_wide.cu
   if (D != 32 && D != 64) return 0;
   return N <= 128 && Lx >= 1;
 }
@@ -919,9 +913,17 @@ size_t tc2d_wimg_bytes(int D) {
   return (size_t)(3 * D * (2 * D + 16) + 2 * D * (D + 16)) * 2 + (size_t)(D + 4) * 4;
 }
 
-size_t tc2d_jobs_bytes(int64_t B, int nb) { return (size_t)B * nb * sizeof(Job2) + (size_t)(nb + 4) * sizeof(int); }
+// chain job records carry 128-bit configuration masks where N <= 128 and the
+// engine is the d_h <= 64 one, 256-bit masks otherwise
+static bool wide_jobs(int N, int D) { return N > 128 || D == 256; }
+
+size_t tc2d_jobs_bytes(int64_t B, int nb, int N, int D) {
+  const size_t rec = wide_jobs(N, D) ? sizeof(JobT<4>) : sizeof(JobT<2>);
+  return (size_t)B * nb * rec + (size_t)(nb + 4) * sizeof(int);
+}
 
 cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st) {
+  if (D == 256) return tc2dw_pack(params, wimg, st);
   uint8_t* w1 = wimg;
   uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
   float* aux = reinterpret_cast<float*>(w2 + (size_t)2 * D * (D + 16) * 2);
@@ -931,6 +933,7 @@ cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st
 }
 
 cudaError_t tc2d_forward(const Tc2Fwd& f, const uint8_t* wimg, int D, bool sample, cudaStream_t st) {
+  if (D == 256) return tc2dw_forward(f, wimg, sample, st);
   Tc2Args a{};
   a.B = f.B;
   a.Lx = f.Lx;
@@ -972,6 +975,7 @@ cudaError_t launch_tables(const Tab2Args& a, const uint8_t* w2, const float* aux
 }
 
 cudaError_t tc2d_tables(const Tc2Fwd& f, const uint8_t* wimg, int D, cudaStream_t st) {
+  if (D == 256) return tc2dw_tables(f, wimg, st);
   Tab2Args a{};
   a.B = f.B;
   a.Lx = f.Lx;
@@ -994,15 +998,23 @@ cudaError_t tc2d_tables(const Tc2Fwd& f, const uint8_t* wimg, int D, cudaStream_
 cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cudaStream_t st) {
   // jobs: antiparallel (sample, bond) pairs in bond order, with their start values
   uint8_t* jb = c.jobs_ws;
-  Job2* jobs = reinterpret_cast<Job2*>(jb);
-  int* counts = reinterpret_cast<int*>(jb + (size_t)c.B * c.nb * sizeof(Job2));
+  const bool wide = wide_jobs(c.N, D);
+  const size_t rec = wide ? sizeof(JobT<4>) : sizeof(JobT<2>);
+  int* counts = reinterpret_cast<int*>(jb + (size_t)c.B * c.nb * rec);
   int* njobs = counts + c.nb;
   heis_count_kernel<<<c.nb, 256, 0, st>>>(c.sigma, c.bonds, c.B, c.N, counts);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  heis_jobs_kernel<<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb, jobs, njobs);
+  if (!wide)
+    heis_jobs_kernel<2><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb,
+                                                reinterpret_cast<JobT<2>*>(jb), njobs);
+  else
+    heis_jobs_kernel<4><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb,
+                                                reinterpret_cast<JobT<4>*>(jb), njobs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  if (D == 256) return tc2dw_chains(c, wimg, jb, njobs, st);
+  Job2* jobs = reinterpret_cast<Job2*>(jb);
   Tc2Args a{};
   a.B = c.B;
   a.Lx = c.Lx;

@@ -37,6 +37,10 @@ __device__ __forceinline__ void st_split8(uint8_t* dhi, uint8_t* dlo, const floa
 __device__ __forceinline__ void cp_async16_2d(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
 }
+// L2-only variant (the source may have been written by this thread earlier in the kernel)
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" : : "r"(tc::smem_addr(smem)), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_commit_2d() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_2d() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ float ldg_f32_v(const float* p) {
@@ -72,11 +76,25 @@ __device__ __forceinline__ Pz zpos(int t, int Lx) {
 __device__ __forceinline__ int zhor(const Pz& p) { return (p.j & 1) ? p.i + 1 : p.i - 1; }
 __device__ __forceinline__ int zsnake(int i, int j, int Lx) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
 
-__device__ __forceinline__ int mbit(const uint64_t (&m)[2], int k) { return (int)((m[k >> 6] >> (k & 63)) & 1ull); }
-__device__ __forceinline__ void mset(uint64_t (&m)[2], int k, int s) {
+// A configuration of up to 64 NW spins as a bit mask (bit k = spin of lattice site k).
+template <int NW>
+__device__ __forceinline__ int mbit(const uint64_t (&m)[NW], int k) { return (int)((m[k >> 6] >> (k & 63)) & 1ull); }
+template <int NW>
+__device__ __forceinline__ void mset(uint64_t (&m)[NW], int k, int s) {
   const uint64_t b = 1ull << (k & 63);
   m[k >> 6] = s ? (m[k >> 6] | b) : (m[k >> 6] & ~b);
 }
+
+// Heisenberg chain job: one antiparallel (sample, bond) pair with the start
+// values of its chain taken from the cached-path tables.
+template <int NW>
+struct JobT {
+  int b, rank;
+  float acc0;          // 1/2 [log p_pa(s_new) - log p_pa(s_old)]
+  int nup0;            // up spins before pa+1 on the exchanged configuration
+  uint64_t mask[NW];   // exchanged configuration, bit k = spin of lattice site k
+};
+static_assert(sizeof(JobT<2>) == 32 && sizeof(JobT<4>) == 48, "job records of 32 / 48 bytes");
 
 // Zero-magnetisation mask (forced outcomes have log p = 0 / -inf).
 __device__ __forceinline__ float lp_masked(int s, float d, int n_up, int n_done, int N, bool sz0) {

@@ -1,0 +1,821 @@
+// BF16 tensor-core path of the 2D GRU + GLU wave function (App. A) at d_h =
+// 256: zig-zag sampling, teacher forcing, the cached-path tables and the
+// prefix-cached Heisenberg chains (Eq. heisenberg, Marshall-rotated, Sec.
+// III B) on lattices of up to 256 sites (the 16 x 16 lattice of Sec. III B).
+//
+// The cell arithmetic is that of tc2d.cu: states enter the GEMMs as BF16
+// pairs hi + lo, the weights are BF16 with the biases and one-hot input
+// weights folded into 16 extra columns, accumulation is FP32, and the
+// epilogues and the readout order are the same.  What changes is the size:
+// the weights (1.09 MB of BF16) do not fit in shared memory, and the 3 d_h =
+// 768 gate accumulators of a 128-row tile do not fit in TMEM (512 columns).
+//
+//  * Weights stream from global memory (L2-resident: every CTA reads the same
+//    1.09 MB) as a fixed sequence of "slabs": 16 K columns of all B rows of
+//    one MMA phase (12 or 16 KB, already in the K-major core-matrix layout).
+//    One issuing thread copies slabs with bulk asynchronous copies into a
+//    five-slot ring in shared memory and runs ahead of its MMAs across phase
+//    and cell boundaries (the sequence does not depend on the data); slot
+//    reuse waits on the commit of the MMAs that read the slot.
+//  * The gates run in two chunks of 128 units (N = 384: the W, W_g / 2 and
+//    U_mix rows of those units, accumulators in TMEM columns [0, 384)), each
+//    over the horizontal and the vertical input.  The A operand (128 rows x
+//    [hi(h) | extras | lo(h)], 135 KB) holds one input state at a time:
+//        h_hor: chunk 0 | h_ver: chunk 0, chunk 1 | h_hor: chunk 1 | h: GLU
+//    so a cell stages its vertical input once and its horizontal input
+//    twice, and the state it computes (chunk 0 kept in registers until the
+//    A operand is free) is the GLU's input and, in place, the next cell's
+//    horizontal input.  The GLU (N = 512) then fills all of TMEM.
+//  * 16 worker warps, four per TMEM lane quarter, hold a row each in four
+//    slices (32 units of each gate chunk, 64 GLU units); they stage the
+//    inputs, run the epilogues and the row logic.  Warp 16 issues the copies
+//    and the MMAs and meets the workers at named barriers.
+// States leave the cell as packed hi / lo words in a per-row column buffer
+// (the latest state of each lattice column) and, in sampling / teacher
+// forcing, as FP32 in the prefix cache.
+#include "tc2d_common.cuh"
+
+namespace nqs {
+
+namespace {
+
+using namespace tc2dh;
+
+constexpr int WD = 256;                            // d_h
+constexpr int WKA = 2 * WD + 16;                   // A operand columns: [hi(h) | extras | lo(h)]
+constexpr int WEX = WD;                            // first extra column
+constexpr int WLO = WD + 16;                       // first lo column
+constexpr uint32_t kSboA = (WKA / 8) * 128;        // A: bytes between 8-row groups
+constexpr int kGateRows = 384, kGluRows = 512;     // B rows of a gate / GLU slab
+constexpr uint32_t kGateSlab = kGateRows * 32;     // 16 BF16 K columns of every B row
+constexpr uint32_t kGluSlab = kGluRows * 32;
+constexpr int kNHor = 17, kNVer = 16, kNGlu = 17;  // slabs per phase (horizontal and GLU: + the extras slab)
+constexpr int kGateSlabs = 2 * kNHor + 2 * kNVer;  // 66
+constexpr int kCellSlabs = kGateSlabs + kNGlu;     // 83
+constexpr size_t kOffGlu = (size_t)kGateSlabs * kGateSlab;
+constexpr size_t kOffAux = kOffGlu + (size_t)kNGlu * kGluSlab;
+constexpr int kRing = 5;                           // ring slots
+constexpr uint32_t kSlotBytes = 16384;
+constexpr int kWorkers = 512, kThreads = kWorkers + 32;
+constexpr uint32_t kBarAll = 1, kBarGo = 2, kBarW = 3;   // named barriers
+constexpr uint32_t kIdesc256 = tc::make_idesc_bf16(128, 256);
+constexpr uint32_t kIdesc128 = tc::make_idesc_bf16(128, 128);
+static_assert(kGluSlab <= kSlotBytes && kGateSlab <= kSlotBytes, "slab fits a slot");
+
+// ----------------------------------------------------------------------------
+// Weight image: the slabs of one cell in the order the MMAs use them, then the
+// FP32 readout constants.  Slab q (element (n, k) at kmajor_offset(n, k, 16)):
+//   [0, 17)   chunk 0 (units 0-127) on h_hor: W columns [16 q, 16 q + 16), then the extras
+//   [17, 33)  chunk 0 on h_ver
+//   [33, 49)  chunk 1 (units 128-255) on h_ver
+//   [49, 66)  chunk 1 on h_hor, then the extras
+//   [66, 83)  GLU: W_1 / W_2 columns, then the extras
+// Gate slab rows: [W | W_g / 2 | U_mix] rows of the chunk's 128 units; extra
+// columns [b hi | b lo | w_h0 w_h1 w_v0 w_v1 hi | the same lo] (W, W_g rows; U_mix
+// rows have none).  GLU slab rows: [W_1 | W_2 / 2], extras [b hi | b lo].
+// ----------------------------------------------------------------------------
+__global__ void pack_wide_kernel(const float* __restrict__ p, uint8_t* __restrict__ img) {
+  constexpr int D = WD, W2c = 2 * D + 4;
+  // flat layout (App. A; nqs.h): W, W_g [d, 2d+4], U_mix [d, 2d], b, b_g, W_1 [d, d], b_1, W_2, b_2, U_out [2, d], c
+  const int oW = 0, oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D, ob1 = oW1 + D * D,
+            oW2 = ob1 + D, ob2 = oW2 + D * D, oUo = ob2 + D, oc = oUo + 2 * D;
+  const int ng = kGateSlabs * kGateRows * 16, nl = kNGlu * kGluRows * 16;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ng + nl + D + 1; t += gridDim.x * blockDim.x) {
+    if (t < ng) {
+      const int q = t / (kGateRows * 16), e = t % (kGateRows * 16), n = e / 16, k = e % 16;
+      const int chunk = q < 33 ? 0 : 1;
+      const bool ver = q >= 17 && q < 49;
+      const int kk = q < 17 ? q : q < 33 ? q - 17 : q < 49 ? q - 33 : q - 49;
+      const int g = n / 128, u = chunk * 128 + n % 128;
+      float v = 0.0f;
+      if (kk < 16) {
+        const int col = (ver ? D : 0) + 16 * kk + k;
+        v = g == 0 ? p[oW + u * W2c + col] : g == 1 ? p[oWg + u * W2c + col] : p[oU + u * 2 * D + col];
+      } else if (g < 2 && k < 10) {
+        const int Wo = g == 0 ? oW : oWg;
+        const float x = k < 2 ? p[(g == 0 ? ob : obg) + u] : p[Wo + u * W2c + 2 * D + (k < 6 ? k - 2 : k - 6)];
+        v = (k == 0 || (k >= 2 && k < 6)) ? bf16_round(x) : x - bf16_round(x);
+      }
+      if (g == 1) v *= 0.5f;   // u = (1 + tanh(a_g / 2)) / 2
+      *reinterpret_cast<__nv_bfloat16*>(img + (size_t)q * kGateSlab + tc::kmajor_offset(n, k, 16)) = __float2bfloat16_rn(v);
+    } else if (t < ng + nl) {
+      const int r = t - ng, q = r / (kGluRows * 16), e = r % (kGluRows * 16), n = e / 16, k = e % 16;
+      const int g = n / 256, v = n % 256;
+      float x = 0.0f;
+      if (q < 16) {
+        x = p[(g == 0 ? oW1 : oW2) + v * D + 16 * q + k];
+      } else if (k < 2) {
+        const float bb = p[(g == 0 ? ob1 : ob2) + v];
+        x = k == 0 ? bf16_round(bb) : bb - bf16_round(bb);
+      }
+      if (g == 1) x *= 0.5f;   // sigmoid(a) = (1 + tanh(a / 2)) / 2
+      *reinterpret_cast<__nv_bfloat16*>(img + kOffGlu + (size_t)q * kGluSlab + tc::kmajor_offset(n, k, 16)) =
+          __float2bfloat16_rn(x);
+    } else {
+      const int v = t - ng - nl;
+      float* aux = reinterpret_cast<float*>(img + kOffAux);
+      aux[v] = v < D ? p[oUo + v] - p[oUo + D + v] : p[oc] - p[oc + 1];
+    }
+  }
+}
+
+// up spins before every zig-zag position (the tables' n_up), one thread per sample
+__global__ void nup_prefix_kernel(const uint8_t* __restrict__ sigma, int64_t B, int Lx, int N, int* __restrict__ nup) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int n = 0;
+  for (int t = 0; t < N; ++t) {
+    nup[b * N + t] = n;
+    const Pz p = zpos(t, Lx);
+    n += sigma[b * N + p.j * Lx + p.i] ? 0 : 1;
+  }
+}
+
+// Bulk asynchronous copy global -> shared, completing on an mbarrier's
+// transaction count (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" : : "r"(tc::smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               :
+               : "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
+               : "memory");
+}
+
+struct SW {
+  static constexpr uint32_t kA = 0;                                  // [128 x WKA] bf16
+  static constexpr uint32_t kRingOff = kA + 128 * WKA * 2;           // kRing x 16 KB
+  static constexpr uint32_t kAux = kRingOff + kRing * kSlotBytes;    // WD + 4 floats: U_0 - U_1, c_0 - c_1
+  static constexpr uint32_t kPos = kAux + (WD + 4) * 4;              // 256 ints: (i, j, r) of every position
+  static constexpr uint32_t kZx = kPos + 256 * 4;                    // 4 x 128 floats: readout partials
+  static constexpr uint32_t kJob = kZx + 512 * 4;                    // 128 long long: published chain jobs
+  static constexpr uint32_t kBar = kJob + 128 * 8;                   // full[kRing], empty[kRing], done, drain
+  static constexpr uint32_t kMisc = kBar + (2 * kRing + 2) * 8;      // TMEM slot, abort flag
+  static constexpr uint32_t kBytes = 1024 + kMisc + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+};
+
+struct WArgs {
+  int64_t B;
+  int Lx, N, nb, sz0;
+  const uint8_t* sigma_in;
+  uint8_t* sigma_out;
+  const float* uniforms;
+  uint64_t seed, step;
+  uint64_t b0;               // sampling: global index of sample 0 (Philox counter offset)
+  const uint64_t* step_dev;  // sampling: device Philox step or null
+  float* logpsi;             // nullable in teacher forcing
+  float* hcache;             // written by sampling / teacher forcing (nullable); read by tables and chains
+  float* colbuf;             // [CTAs x 128 rows, Lx, d] latest packed hi / lo state of every lattice column
+  float* lp_tab;             // written by the tables, read by the chains
+  const int* nup_tab;
+  const int4* bonds;
+  const JobT<4>* jobs;
+  const int* njobs;
+  float* delta;
+  unsigned long long* counter;
+  WsHeader* hdr;
+};
+
+// MODE 0: sampling, 1: teacher forcing, 2: Heisenberg chains, 3: cached-path tables.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __restrict__ img, WArgs a) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
+  uint8_t* sA = sm + SW::kA;
+  uint8_t* ring = sm + SW::kRingOff;
+  float* sAux = reinterpret_cast<float*>(sm + SW::kAux);
+  int* sPos = reinterpret_cast<int*>(sm + SW::kPos);
+  float* sZx = reinterpret_cast<float*>(sm + SW::kZx);
+  long long* jbuf = reinterpret_cast<long long*>(sm + SW::kJob);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + SW::kBar);
+  uint64_t* empty = full + kRing;
+  uint64_t* done = empty + kRing;
+  uint64_t* drain = done + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SW::kMisc);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SW::kMisc + 4);
+
+  const float* aux = reinterpret_cast<const float*>(img + kOffAux);
+  for (int i = threadIdx.x; i < WD + 1; i += kThreads) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += kThreads) {
+    const Pz p = zpos(t, a.Lx);
+    sPos[t] = p.i | (p.j << 8) | (p.r << 16);
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kRing; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(drain, 1);
+    *s_abort = 0;
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool timed_out = false;
+
+  if (warp == kWorkers / 32) {
+    // ======================== issuer warp ========================
+    const bool leader = lane == 0;
+    const uint32_t a_addr = tc::smem_addr(sA), r_addr = tc::smem_addr(ring);
+    uint32_t s_cons = 0, s_fill = 0;   // slabs consumed by MMAs / copied (leader)
+    bool dead = false;                 // a wait gave up: no more copies or MMAs
+    auto die = [&]() {
+      dead = true;
+      timed_out = true;
+      *s_abort = 1;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    };
+    auto fill = [&]() {                // copy slab s_fill into its slot
+      if (dead) return;
+      const uint32_t s = s_fill, slot = s % kRing;
+      // the slot's previous slab: its MMAs have committed to empty[slot]
+      if (s >= (uint32_t)kRing && !tc::mbar_wait(&empty[slot], ((s / kRing) - 1) & 1, wlim)) {
+        die();
+        return;
+      }
+      const uint8_t* src;
+      uint32_t bytes;
+      if constexpr (MODE == 3) {
+        src = img + kOffGlu + (size_t)(s % kNGlu) * kGluSlab;
+        bytes = kGluSlab;
+      } else {
+        const uint32_t q = s % kCellSlabs;
+        src = q < (uint32_t)kGateSlabs ? img + (size_t)q * kGateSlab : img + kOffGlu + (size_t)(q - kGateSlabs) * kGluSlab;
+        bytes = q < (uint32_t)kGateSlabs ? kGateSlab : kGluSlab;
+      }
+      mbar_expect_tx(&full[slot], bytes);
+      bulk_g2s(ring + slot * kSlotBytes, src, bytes, &full[slot]);
+      ++s_fill;
+    };
+    // one slab: wait for its copy, issue its MMAs, release the slot, refill
+    // the slots of earlier slabs (their MMAs precede the ones just issued)
+    auto consume = [&](auto&& mmas) {
+      if (dead) return;
+      const uint32_t s = s_cons, slot = s % kRing;
+      if (!tc::mbar_wait(&full[slot], (s / kRing) & 1, wlim)) {
+        die();
+        return;
+      }
+      tc::fence_after_sync();
+      mmas(r_addr + slot * kSlotBytes);
+      tc::mma_commit(&empty[slot]);
+      ++s_cons;
+      while (!dead && s_fill < s_cons + kRing - 1) fill();
+    };
+    // end of a phase: completion to the workers, then the last slab's slot
+    auto end_phase = [&]() {
+      tc::mma_commit(done);
+      while (!dead && s_fill < s_cons + kRing) fill();
+    };
+    auto desc_a = [&](int col) { return tc::make_desc(a_addr + (uint32_t)col * 16, 128, kSboA); };
+    // gate slab: rows [0, 256) -> TMEM [0, 256), rows [256, 384) -> [256, 384)
+    auto mma_gate = [&](uint32_t sa, int col, bool lo, uint32_t accf) {
+      const uint64_t b0 = tc::make_desc(sa, 128, 256), b1 = tc::make_desc(sa + 8192, 128, 256);
+      tc::mma_bf16(tbase, desc_a(col), b0, kIdesc256, accf);
+      tc::mma_bf16(tbase + 256, desc_a(col), b1, kIdesc128, accf);
+      if (lo) {
+        tc::mma_bf16(tbase, desc_a(WLO + col), b0, kIdesc256, 1);
+        tc::mma_bf16(tbase + 256, desc_a(WLO + col), b1, kIdesc128, 1);
+      }
+    };
+    // GLU slab: rows [0, 256) -> TMEM [0, 256), rows [256, 512) -> [256, 512)
+    auto mma_glu = [&](uint32_t sa, int col, bool lo, uint32_t accf) {
+      const uint64_t b0 = tc::make_desc(sa, 128, 256), b1 = tc::make_desc(sa + 8192, 128, 256);
+      tc::mma_bf16(tbase, desc_a(col), b0, kIdesc256, accf);
+      tc::mma_bf16(tbase + 256, desc_a(col), b1, kIdesc256, accf);
+      if (lo) {
+        tc::mma_bf16(tbase, desc_a(WLO + col), b0, kIdesc256, 1);
+        tc::mma_bf16(tbase + 256, desc_a(WLO + col), b1, kIdesc256, 1);
+      }
+    };
+    auto phase_hor = [&](bool first) {   // 16 slabs on hi / lo, then the extras
+      for (int i = 0; i < kNHor; ++i)
+        consume([&](uint32_t sa) {
+          if (i < 16) mma_gate(sa, 16 * i, true, (first && i == 0) ? 0u : 1u);
+          else mma_gate(sa, WEX, false, 1u);
+        });
+      end_phase();
+    };
+    auto phase_ver = [&](bool first) {
+      for (int i = 0; i < kNVer; ++i)
+        consume([&](uint32_t sa) { mma_gate(sa, 16 * i, true, (first && i == 0) ? 0u : 1u); });
+      end_phase();
+    };
+    auto phase_glu = [&]() {
+      for (int i = 0; i < kNGlu; ++i)
+        consume([&](uint32_t sa) {
+          if (i < 16) mma_glu(sa, 16 * i, true, i == 0 ? 0u : 1u);
+          else mma_glu(sa, WEX, false, 1u);
+        });
+      end_phase();
+    };
+    auto go = [&]() {                  // the workers' inputs / TMEM reads are done
+      __syncwarp();
+      tc::group_barrier(kBarGo, kThreads);
+      tc::fence_after_sync();
+    };
+    if (leader)
+      for (int q = 0; q < kRing; ++q) fill();
+    __syncwarp();
+    for (;;) {
+      const bool any = tc::group_barrier_or(false, kBarAll, kThreads);
+      if (!any) break;
+      tc::fence_after_sync();
+      if constexpr (MODE == 3) {
+        if (leader) phase_glu();
+      } else {
+        if (leader) phase_hor(true);    // chunk 0, h_hor
+        go();
+        if (leader) phase_ver(false);   // chunk 0, h_ver
+        go();
+        if (leader) phase_ver(true);    // chunk 1, h_ver
+        go();
+        if (leader) phase_hor(false);   // chunk 1, h_hor
+        go();
+        if (leader) phase_glu();
+      }
+      __syncwarp();
+    }
+    // no copy may still be landing when the CTA exits
+    if (leader)
+      for (uint32_t s = s_cons; s < s_fill; ++s) tc::mbar_wait(&full[s % kRing], (s / kRing) & 1, kWait2);
+    __syncwarp();
+  } else {
+    // ======================== worker warps ========================
+    const int part = warp >> 2, quarter = warp & 3;
+    const int m = quarter * 32 + lane;                                  // row = TMEM lane
+    const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16);
+    const int Lx = a.Lx, N = a.N;
+    const int64_t B = a.B;
+    const float dc = sAux[WD];
+    const uint32_t one = 0x3F80u;
+    auto P = [&](int t) -> Pz {        // zig-zag position t (table lookup)
+      const int v = sPos[t];
+      Pz p;
+      p.i = v & 255;
+      p.j = (v >> 8) & 255;
+      p.r = v >> 16;
+      return p;
+    };
+    auto kmo = [&](int k) { return sA + tc::kmajor_offset(m, k, WKA); };
+    // this thread's units: gate chunk c -> 128 c + 32 part + [0, 32); GLU -> 64 part + [0, 64)
+    auto stage_zero = [&]() {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = 128 * c + 32 * part + 8 * q;
+          *reinterpret_cast<uint4*>(kmo(u)) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(kmo(WLO + u)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    auto stage_f32 = [&](const float* src) {   // FP32 state (the prefix cache)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = 128 * c + 32 * part + 8 * q;
+          const float4 x0 = *reinterpret_cast<const float4*>(src + u);
+          const float4 x1 = *reinterpret_cast<const float4*>(src + u + 4);
+          const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          st_split8(kmo(u), kmo(WLO + u), v);
+        }
+    };
+    auto stage_packed = [&](const float* entry) {   // packed [hi words | lo words] column-buffer entry
+      const uint8_t* e = reinterpret_cast<const uint8_t*>(entry);
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = 128 * c + 32 * part + 8 * q;
+          cp_async16_cg(kmo(u), e + 2 * u);
+          cp_async16_cg(kmo(WLO + u), e + 2 * WD + 2 * u);
+        }
+      cp_commit_2d();
+    };
+    auto glu_extras = [&]() {
+      *reinterpret_cast<uint4*>(kmo(WEX)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(kmo(WEX + 8)) = make_uint4(0u, 0u, 0u, 0u);
+    };
+    // GLU epilogue and readout: 16-unit chunks in order, chunks by a fixed
+    // pairwise tree (within the slice, then over the four slices)
+    auto glu_readout = [&]() -> float {
+      float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int c8 = 0; c8 < 8; ++c8) {
+        uint32_t a1[8], a2[8];
+        const int col = 64 * part + 8 * c8;
+        tld8(trow + col, a1);
+        tld8(trow + 256 + col, a2);
+        tc::tmem_wait_ld();
+        tie(a1);
+        tie(a2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+          zc[c8 >> 1] = fmaf(sAux[col + q], y, zc[c8 >> 1]);
+        }
+      }
+      sZx[part * 128 + m] = (zc[0] + zc[1]) + (zc[2] + zc[3]);
+      tc::fence_before_sync();
+      tc::group_barrier(kBarW, kWorkers);
+      return (sZx[m] + sZx[128 + m]) + (sZx[256 + m] + sZx[384 + m]);
+    };
+    uint32_t pd = 0;                   // parity of the next completion on `done`
+    auto wait_done = [&]() {
+      if (!tc::mbar_wait(done, pd, wlim)) {
+        timed_out = true;
+        *s_abort = 1;
+        flag_status(a.hdr, NQS_ETIMEOUT);
+      }
+      pd ^= 1;
+      tc::fence_after_sync();
+    };
+    auto to_issuer = [&]() {           // inputs staged / TMEM read: the next phase may start
+      cp_wait_2d();
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::group_arrive(kBarGo, kThreads);
+    };
+
+    if constexpr (MODE == 3) {
+      // ---- cached-path tables: every (sample, position) cell is a row ----
+      const int64_t ncell = B * N, ntile = (ncell + 127) / 128;
+      for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
+        const int64_t cell = tile * 128 + m;
+        const bool valid = tile < ntile && cell < ncell;
+        int64_t b = 0;
+        int t = 0;
+        if (valid) {
+          b = cell / N;
+          t = (int)(cell % N);
+          const Pz p = P(t);
+          stage_f32(a.hcache + (b * N + p.j * Lx + p.i) * WD);
+          if (part == 0) glu_extras();
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        const bool any = tc::group_barrier_or(valid && !*s_abort, kBarAll, kThreads);
+        if (!any) break;
+        wait_done();
+        const float z = glu_readout();
+        if (valid && part == 0 && !timed_out) {
+          const float d = z + dc;
+          const int nu = a.nup_tab[b * N + t];
+          a.lp_tab[(b * N + t) * 2] = lp_masked(0, d, nu, t, N, a.sz0 != 0);
+          a.lp_tab[(b * N + t) * 2 + 1] = lp_masked(1, d, nu, t, N, a.sz0 != 0);
+        }
+      }
+    } else {
+      // row state
+      int64_t b = 0;
+      int t = 0, pa = -1, rank = 0, n_up = 0, bsa = -1, bsb = -1;
+      float acc = 0.0f, lp_next = 0.0f;
+      bool active = false, fresh = false;
+      uint64_t mask[4] = {0ull, 0ull, 0ull, 0ull};
+      int hsrc = 0, vsrc = 0;          // 0 zero, 1 previous state (A / column buffer), 2 cached FP32 state, 3 column buffer
+      const int64_t slot_row = (int64_t)blockIdx.x * 128 + m;
+      float* colrow = a.colbuf + slot_row * Lx * WD;   // this row's column buffer
+
+      auto plan = [&]() {              // input sources of the cell at position t
+        const Pz p = P(t);
+        hsrc = p.r == 0 ? 0 : (MODE == 2 && fresh) ? 2 : 1;
+        vsrc = p.j == 0 ? 0 : (MODE == 2 && zsnake(p.i, p.j - 1, Lx) <= pa) ? 2 : 3;
+        if constexpr (MODE == 2) {
+          const int k = p.j * Lx + p.i;
+          const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
+          lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
+        }
+      };
+      auto stage_hor = [&](bool restage) {
+        const Pz p = P(t);
+        if (hsrc == 0) stage_zero();
+        else if (hsrc == 2) stage_f32(a.hcache + (b * N + p.j * Lx + zhor(p)) * WD);
+        else if (restage) stage_packed(colrow + zhor(p) * WD);
+        // hsrc == 1 at the start of a cell: the A operand holds the previous state
+      };
+      auto stage_ver = [&]() {
+        const Pz p = P(t);
+        if (vsrc == 0) stage_zero();
+        else if (vsrc == 2) stage_f32(a.hcache + (b * N + (p.j - 1) * Lx + p.i) * WD);
+        else stage_packed(colrow + p.i * WD);
+      };
+      auto gate_extras = [&]() {
+        const Pz p = P(t);
+        const int s_h = p.r > 0 ? mbit(mask, p.j * Lx + zhor(p)) : -1;
+        const int s_v = p.j > 0 ? mbit(mask, (p.j - 1) * Lx + p.i) : -1;
+        const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+        const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+        *reinterpret_cast<uint4*>(kmo(WEX)) = make_uint4(one | (one << 16), oh, ov, oh);
+        *reinterpret_cast<uint4*>(kmo(WEX + 8)) = make_uint4(ov, 0u, 0u, 0u);
+      };
+      // gate epilogue of chunk c: h~ = tanh(a_W), u = (1 + tanh(a_g)) / 2, h = u h~ + (1 - u) U_mix h'
+      auto gate_epilogue = [&](float (&h)[32]) {
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          uint32_t aw[8], ag[8], au[8];
+          const int col = 32 * part + 8 * q4;
+          tld8(trow + col, aw);
+          tld8(trow + 128 + col, ag);
+          tld8(trow + 256 + col, au);
+          tc::tmem_wait_ld();
+          tie(aw);
+          tie(ag);
+          tie(au);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float cc = hw_tanh2(__uint_as_float(aw[q]));
+            const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q])), 0.5f);
+            const float mix = __uint_as_float(au[q]);
+            h[8 * q4 + q] = fmaf(ug, cc - mix, mix);
+          }
+        }
+      };
+      // the state's 32 units of chunk c: packed words to the column buffer
+      // (entry of lattice column i) and, forward modes, FP32 to the cache
+      auto store_state = [&](int c, const float (&h)[32], const uint32_t (&hi)[16], const uint32_t (&lo)[16]) {
+        const Pz p = P(t);
+        const int u = 128 * c + 32 * part;
+        uint8_t* e = reinterpret_cast<uint8_t*>(colrow + p.i * WD);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          *reinterpret_cast<uint4*>(e + 2 * u + 16 * q) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+          *reinterpret_cast<uint4*>(e + 2 * WD + 2 * u + 16 * q) =
+              make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+        }
+        if (MODE != 2 && a.hcache) {
+          float* dst = a.hcache + (b * N + p.j * Lx + p.i) * WD + u;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            reinterpret_cast<float4*>(dst)[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        }
+      };
+      auto write_a = [&](int c, const uint32_t (&hi)[16], const uint32_t (&lo)[16]) {
+        const int u = 128 * c + 32 * part;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          *reinterpret_cast<uint4*>(kmo(u + 8 * q)) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+          *reinterpret_cast<uint4*>(kmo(WLO + u + 8 * q)) =
+              make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+        }
+      };
+
+      // Chains: take job j (or go idle).
+      auto start_job = [&](unsigned long long j) {
+        const unsigned long long nj = (unsigned long long)*a.njobs;
+        if (j >= nj) {
+          active = false;
+          return;
+        }
+        const JobT<4> jb = a.jobs[j];
+        b = jb.b;
+        rank = jb.rank;
+        const int4 bd = a.bonds[rank];
+        bsa = bd.x;
+        bsb = bd.y;
+        pa = bd.z;
+        t = pa + 1;
+        acc = jb.acc0;
+        n_up = jb.nup0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) mask[w] = jb.mask[w];
+        active = true;
+        fresh = true;
+        plan();
+      };
+      // warp-aggregated pull of one job for every lane with `need` (part 0 warps)
+      unsigned pbal = 0;
+      unsigned long long pbase = 0;
+      auto pull_issue = [&](bool need) {
+        pbal = __ballot_sync(0xffffffffu, need);
+        if (pbal && lane == __ffs(pbal) - 1) pbase = atomicAdd(a.counter, (unsigned long long)__popc(pbal));
+      };
+      auto pull_take = [&]() -> unsigned long long {
+        if (!pbal) return ~0ull;
+        const unsigned long long base = __shfl_sync(0xffffffffu, pbase, __ffs(pbal) - 1);
+        return (pbal >> lane) & 1u ? base + __popc(pbal & ((1u << lane) - 1u)) : ~0ull;
+      };
+
+      if constexpr (MODE == 2) {
+        if (part == 0) {
+          pull_issue(true);
+          jbuf[m] = (long long)pull_take();
+        }
+        tc::group_barrier(kBarW, kWorkers);
+        start_job((unsigned long long)jbuf[m]);
+      } else {
+        b = (int64_t)blockIdx.x * 128 + m;
+        active = b < B;
+        if (MODE == 1 && active)
+          for (int k = 0; k < N; ++k) mset(mask, k, a.sigma_in[b * N + k] ? 1 : 0);
+        plan();
+      }
+
+      for (;;) {
+        // ---- (a) horizontal input and extras ----
+        if (active) {
+          stage_hor(false);
+          if (part == 0) gate_extras();
+        }
+        if constexpr (MODE == 2) {
+          if (part == 0) pull_issue(active && !timed_out && t == N - 1);   // a row on its last cell pulls now
+        }
+        cp_wait_2d();
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        const bool any = tc::group_barrier_or(active && !*s_abort, kBarAll, kThreads);
+        if (!any) break;
+        float uni = 0.0f;
+        if (MODE == 0 && active)
+          uni = a.uniforms ? a.uniforms[b * N + t]
+                           : sampling_uniform(a.seed, a.step_dev ? *a.step_dev : a.step, (uint32_t)(a.b0 + b), (uint32_t)t);
+        // ---- (b) chunk 0 on h_hor done: stage h_ver ----
+        wait_done();
+        if (active) stage_ver();
+        to_issuer();
+        // ---- (c) chunk 0 complete: its units of the new state ----
+        wait_done();
+        float h[32];
+        uint32_t h0hi[16], h0lo[16];
+        gate_epilogue(h);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) split_bf16(h[2 * q], h[2 * q + 1], h0hi[q], h0lo[q]);
+        if (active) store_state(0, h, h0hi, h0lo);
+        to_issuer();
+        // ---- (d) chunk 1 on h_ver done: stage h_hor again ----
+        wait_done();
+        if (active) stage_hor(true);
+        to_issuer();
+        // ---- (e) chunk 1 complete: the new state into the A operand ----
+        wait_done();
+        {
+          uint32_t h1hi[16], h1lo[16];
+          gate_epilogue(h);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) split_bf16(h[2 * q], h[2 * q + 1], h1hi[q], h1lo[q]);
+          if (active) store_state(1, h, h1hi, h1lo);
+          write_a(0, h0hi, h0lo);
+          write_a(1, h1hi, h1lo);
+          if (part == 0) glu_extras();
+        }
+        to_issuer();
+        // ---- (f) GLU and the logit difference ----
+        wait_done();
+        const float z = glu_readout();
+        // ---- (g) row logic (every slice of a row runs it; slice 0 writes) ----
+        bool fin = false;
+        if (active && !timed_out) {
+          const float d = z + dc;
+          const Pz p = P(t);
+          const int k = p.j * Lx + p.i;
+          int s;
+          if constexpr (MODE == 0) {
+            const bool fdn = a.sz0 && n_up >= (N >> 1);
+            const bool fup = a.sz0 && (t - n_up) >= (N >> 1);
+            s = fdn ? 1 : fup ? 0 : (uni < sigmoid_acc(d) ? 0 : 1);
+            if (part == 0) a.sigma_out[b * N + k] = (uint8_t)s;
+            mset(mask, k, s);
+          } else {
+            s = mbit(mask, k);
+          }
+          const float lp = lp_masked(s, d, n_up, t, N, a.sz0 != 0);
+          if constexpr (MODE == 2) {
+            acc += 0.5f * (lp - lp_next);
+          } else {
+            acc += lp;
+          }
+          n_up += (s == 0);
+          if (++t == N) {
+            fin = true;
+            if constexpr (MODE == 2) {
+              if (part == 0) a.delta[b * a.nb + rank] = acc;
+            } else {
+              const float lpsi = 0.5f * acc;
+              if (a.logpsi && part == 0) a.logpsi[b] = lpsi;
+              if (!isfinite(lpsi)) flag_status(a.hdr, NQS_ENONFINITE);
+              active = false;
+            }
+          } else {
+            fresh = false;
+            plan();
+          }
+        }
+        if constexpr (MODE == 2) {
+          if (part == 0) jbuf[m] = (long long)pull_take();
+          tc::group_barrier(kBarW, kWorkers);
+          if (fin) start_job((unsigned long long)jbuf[m]);
+        }
+      }
+    }
+    cp_wait_2d();
+  }
+  tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once the MMAs have drained
+  if (__syncthreads_or(timed_out) && threadIdx.x == kWorkers) tc::drain_mmas(drain, kWait2);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+template <int MODE>
+cudaError_t launch_w(const WArgs& a, const uint8_t* img, int64_t grid, cudaStream_t st) {
+  auto k = tc2dw_kernel<MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SW::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  if (grid < 1) return cudaSuccess;
+  k<<<(unsigned)grid, kThreads, SW::kBytes, st>>>(img, a);
+  return cudaGetLastError();
+}
+
+int sm_count_w() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      sms = n;
+    else
+      sms = 152;
+  }
+  return sms;
+}
+
+}  // namespace
+
+cudaError_t tc2dw_pack(const float* params, uint8_t* wimg, cudaStream_t st) {
+  const int total = kGateSlabs * kGateRows * 16 + kNGlu * kGluRows * 16 + WD + 1;
+  pack_wide_kernel<<<(total + 255) / 256, 256, 0, st>>>(params, wimg);
+  return cudaGetLastError();
+}
+
+cudaError_t tc2dw_forward(const Tc2Fwd& f, const uint8_t* wimg, bool sample, cudaStream_t st) {
+  WArgs a{};
+  a.B = f.B;
+  a.Lx = f.Lx;
+  a.N = f.N;
+  a.sz0 = f.sz0;
+  a.sigma_in = f.sigma_in;
+  a.sigma_out = f.sigma_out;
+  a.uniforms = f.uniforms;
+  a.seed = f.seed;
+  a.step = f.step;
+  a.b0 = f.b0;
+  a.step_dev = f.step_dev;
+  a.logpsi = f.logpsi;
+  a.hcache = f.hcache;
+  a.colbuf = f.colbuf;
+  a.hdr = f.hdr;
+  const int64_t grid = (f.B + 127) / 128;
+  return sample ? launch_w<0>(a, wimg, grid, st) : launch_w<1>(a, wimg, grid, st);
+}
+
+cudaError_t tc2dw_tables(const Tc2Fwd& f, const uint8_t* wimg, cudaStream_t st) {
+  if (f.B > 0) {
+    nup_prefix_kernel<<<(unsigned)((f.B + 127) / 128), 128, 0, st>>>(f.sigma_in, f.B, f.Lx, f.N, f.nup_tab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  WArgs a{};
+  a.B = f.B;
+  a.Lx = f.Lx;
+  a.N = f.N;
+  a.sz0 = f.sz0;
+  a.hcache = f.hcache;
+  a.lp_tab = f.lp_tab;
+  a.nup_tab = f.nup_tab;
+  a.hdr = f.hdr;
+  const int64_t ntile = (f.B * f.N + 127) / 128;
+  return launch_w<3>(a, wimg, ntile < sm_count_w() ? ntile : sm_count_w(), st);
+}
+
+cudaError_t tc2dw_chains(const Tc2Chains& c, const uint8_t* wimg, const uint8_t* jobs, const int* njobs, cudaStream_t st) {
+  WArgs a{};
+  a.B = c.B;
+  a.Lx = c.Lx;
+  a.N = c.N;
+  a.nb = c.nb;
+  a.sz0 = c.sz0;
+  a.hcache = const_cast<float*>(c.hcache);
+  a.colbuf = c.colbuf;
+  a.lp_tab = const_cast<float*>(c.lp_tab);
+  a.bonds = c.bonds;
+  a.jobs = reinterpret_cast<const JobT<4>*>(jobs);
+  a.njobs = njobs;
+  a.delta = c.delta;
+  a.counter = c.counter;
+  a.hdr = c.hdr;
+  return launch_w<2>(a, wimg, sm_count_w(), st);
+}
+
+cudaError_t tc2dw_set_wait_polls(uint32_t polls) { return cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof(polls)); }
+
+}  // namespace nqs
