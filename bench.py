@@ -418,13 +418,14 @@ def run_gpu(args, w):
     # 2D BF16 sample 2, E_loc 7 (pack, bonds, cached-path tables, job count,
     # jobs, chains, energies), gradient 8 (statistics, weights, pack, tape,
     # sweep, weight gradients, readout gradient, reduction); 2D BF16 at d_h =
-    # 256: E_loc 8 (the tables' up-spin prefix counts as one more), gradient 5
-    # (the FP32 reverse sweep)
+    # 256: E_loc 8 (the tables' up-spin prefix counts as one more), gradient 11
+    # (statistics, weights, two packs, up-spin prefix, tape, sweep, weight
+    # gradients, readout gradients, final reduction, conversion)
     wide = w["cell"] == 2 and w["d"] == 256
     if w["cell"] == 1:
         launches = 17 if chosen is r16 else 11
     else:
-        launches = (15 if wide else 17) if chosen is r16 else 12
+        launches = (21 if wide else 17) if chosen is r16 else 12
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["total_ms"] / args.steps, "higher_is_better": True,
@@ -435,8 +436,8 @@ def run_gpu(args, w):
                                   % world if world > 1 else "single",
                    "precision": ("bf16 tensor-core cell GEMMs, fp32 state" if w["cell"] == 1 else
                                  "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs, weights "
-                                 "streamed from L2 through a shared-memory ring), fp32 state; gradient on the "
-                                 "fp32 reverse sweep" if wide else
+                                 "streamed from L2 through a shared-memory ring) and reverse sweep, fp32 state"
+                                 if wide else
                                  "bf16 tensor-core cell and GLU GEMMs (states as bf16 hi+lo pairs) "
                                  "and reverse sweep, fp32 state") if chosen is r16 else "fp32",
                    "fp32_value": world * B * args.steps / (r32["total_ms"] * 1e-3),
@@ -820,6 +821,47 @@ def run_batched_probe(args, w):
                       "ms_per_step": float(np.median(ts)), "device_status": batch.ws.status()}))
 
 
+def run_step_probe(args, w):
+    """Diagnostic: the workload's VMC step at one precision (--precision, BF16
+    for auto), without the FP32 comparison: CUDA-event times of sampling,
+    local energy and gradient (median of --steps after --warmup) and the
+    chain FLOP rate of the local-energy call.  A short target for launch
+    lists."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import inputs, nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B = args.batch or w["B"]
+    prec = nqs.FP32 if args.precision == "fp32" else nqs.BF16
+    p = torch.tensor(inputs.xavier_params(w["cell"], w["d"], seed=w["seed"], noise_std=w["noise"]).astype(np.float32),
+                     device=dev)
+    desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], w["d"], sz0=w["sz0"], precision=prec)
+    ham = nqs.tfim(w["J"], w["Gamma"]) if w["ham"] == "tfim" else nqs.heisenberg(w["J"], True)
+    ws = nqs.Workspace(dev)
+    ph = {"sample": [], "local_energy": [], "gradient": []}
+    cells = 0
+    for k in range(args.warmup + args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        s, _, hc = nqs.sample(desc, p, B, seed=1, step=k, ws=ws)
+        ev[1].record()
+        el = nqs.local_energy(desc, p, ham, s, hc, ws=ws)
+        ev[2].record()
+        nqs.vmc_grad(desc, p, s, hc, el, ws=ws)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            for i, name in enumerate(ph):
+                ph[name].append(ev[i].elapsed_time(ev[i + 1]))
+            cells = chain_cells(w, s.cpu().numpy())
+    ms = {k: float(np.median(v)) for k, v in ph.items()}
+    print(json.dumps({"probe": "step", "workload": w["name"], "precision": "fp32" if prec == nqs.FP32 else "bf16",
+                      "batch": B, "ms": ms, "ms_per_step": sum(ms.values()),
+                      "chain_tflops": cells * 2 * mac_cell(w) / (ms["local_energy"] * 1e-3) / 1e12,
+                      "device_status": ws.status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,7 +873,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
                     help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt", "batched"],
+    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt", "batched", "step"],
                     help="diagnostic run instead of the bench line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -843,6 +885,9 @@ def main():
         return
     if args.probe == "batched":
         run_batched_probe(args, w)
+        return
+    if args.probe == "step":
+        run_step_probe(args, w)
         return
     if args.impl == "reference":
         if args.workload == "replicas16":

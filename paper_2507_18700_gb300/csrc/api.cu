@@ -66,9 +66,10 @@ bool use_tc_grad(const Dims& d) { return use_tc(d) && d.d <= 64; }
 // flat offset of the cRNN phase layer [U_phi | c_phi] (after the amplitude parameters)
 size_t phase_offset(const Dims& d) { return 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2; }
 bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
-// the 2D BF16 reverse sweep is built for d_h <= 64; at d_h = 256 the BF16
-// model's gradient runs the FP32 reverse sweep on the (FP32) prefix cache
+// the 2D BF16 reverse sweep: weights in shared memory for d_h <= 64
+// (tc2d_grad.cu), streamed for d_h = 256 (tc2d_wide.cu)
 bool use_tc2d_grad(const Dims& d) { return use_tc2d(d) && d.d <= 64; }
+bool use_tc2dw_grad(const Dims& d) { return use_tc2d(d) && d.d == 256; }
 
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
@@ -119,6 +120,12 @@ Layout layout(const Dims& d, int64_t B, int op) {
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
+      if (use_tc2dw_grad(d)) {
+        L.a = take(d.P * sizeof(float));                       // the flat FP32 gradient
+        L.b = take((size_t)B * sizeof(float));                 // weights
+        L.c = take(tc2dw_grad_bytes(B, d.Lx, d.N));            // tapes of the reverse sweep
+        break;
+      }
       if (use_tc2d_grad(d)) {
         L.a = take((size_t)tc2d_grad_partial_rows(B, d.N) * d.P * sizeof(float));  // partial gradients
         L.b = take((size_t)B * sizeof(float));                                     // weights
@@ -227,6 +234,23 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.hdr = static_cast<WsHeader*>(ws);
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
+  }
+  if (use_tc2dw_grad(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    if (tc2d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Tc2WGrad g{};
+    g.B = B;
+    g.Lx = d.Lx;
+    g.N = d.N;
+    g.sz0 = d.sz0;
+    g.sigma = sigma;
+    g.hcache = hcache;
+    g.weights = weights;
+    g.params = params;
+    g.scratch = at<uint8_t>(ws, L.c);
+    g.hdr = static_cast<WsHeader*>(ws);
+    if (tc2dw_grad(g, wimg, partial, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, 1, (int)d.P, grad, st));
   }
   if (use_tc2d_grad(d)) {
     uint8_t* wimg = at<uint8_t>(ws, L.w);

@@ -159,6 +159,20 @@ cudaError_t tc2dw_forward(const Tc2Fwd& f, const uint8_t* wimg, bool sample, cud
 cudaError_t tc2dw_tables(const Tc2Fwd& f, const uint8_t* wimg, cudaStream_t st);
 cudaError_t tc2dw_chains(const Tc2Chains& c, const uint8_t* wimg, const uint8_t* jobs, const int* njobs, cudaStream_t st);
 cudaError_t tc2dw_set_wait_polls(uint32_t polls);
+// d_h = 256 BF16 reverse sweep (tc2d_wide.cu): tape pass, sequential sweep,
+// weight-gradient GEMMs, readout gradients; writes grad [P] directly
+struct Tc2WGrad {
+  int64_t B;
+  int Lx, N, sz0;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;      // [B] w_b of sum_b w_b log psi_b
+  const float* params;
+  uint8_t* scratch;          // tc2dw_grad_bytes(B, Lx, N), 256-byte aligned
+  WsHeader* hdr;
+};
+size_t tc2dw_grad_bytes(int64_t B, int Lx, int N);
+cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cudaStream_t st);
 
 // BF16 tensor-core 2D reverse sweep (tc2d_grad.cu)
 struct Tc2Grad {

@@ -33,6 +33,8 @@
 // States leave the cell as packed hi / lo words in a per-row column buffer
 // (the latest state of each lattice column) and, in sampling / teacher
 // forcing, as FP32 in the prefix cache.
+#include <cuda_fp16.h>
+
 #include "tc2d_common.cuh"
 
 namespace nqs {
@@ -54,6 +56,14 @@ constexpr int kGateSlabs = 2 * kNHor + 2 * kNVer;  // 66
 constexpr int kCellSlabs = kGateSlabs + kNGlu;     // 83
 constexpr size_t kOffGlu = (size_t)kGateSlabs * kGateSlab;
 constexpr size_t kOffAux = kOffGlu + (size_t)kNGlu * kGluSlab;
+// backward image: the sweep's transposed gate weights (48 slabs of [512 h'
+// columns x 16 gate units]) and the GLU's transposed weights (32 slabs of
+// [256 h units x 16 GLU units]), true (not halved) W_g and W_2
+constexpr uint32_t kW1tSlab = 512 * 32, kGlutSlab = 256 * 32;
+constexpr int kNW1t = 48, kNGlut = 32;
+constexpr size_t kOffGlut = (size_t)kNW1t * kW1tSlab;
+constexpr size_t kBwdImg = kOffGlut + (size_t)kNGlut * kGlutSlab;
+constexpr int kTapeSlabs = kCellSlabs + kNGlut;    // 115 slabs per tape-pass tile
 constexpr int kRing = 5;                           // ring slots
 constexpr uint32_t kSlotBytes = 16384;
 constexpr int kWorkers = 512, kThreads = kWorkers + 32;
@@ -144,6 +154,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Byte offset of element (cell c, column v) in an operand tape of the
+// weight-gradient GEMMs: columns split into tiles of TW, cells into blocks of
+// 16; each (tile, block) is one contiguous MN-major [16 x TW] BF16 operand
+// (rows = cells = K, LBO = (TW / 8) * 128, SBO = 128).  v is a multiple of 8.
+__device__ __forceinline__ size_t tape_off(int64_t c, int v, int TW, int64_t nkb) {
+  const int tile = v / TW, vv = v % TW, r = (int)(c & 15);
+  return ((size_t)tile * nkb + (size_t)(c >> 4)) * (size_t)(16 * TW * 2) + (size_t)((r >> 3) * (TW / 8) * 128) +
+         (size_t)((vv >> 3) * 128) + (size_t)((r & 7) * 16);
+}
+__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
+  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
 struct SW {
   static constexpr uint32_t kA = 0;                                  // [128 x WKA] bf16
   static constexpr uint32_t kRingOff = kA + 128 * WKA * 2;           // kRing x 16 KB
@@ -177,9 +200,25 @@ struct WArgs {
   float* delta;
   unsigned long long* counter;
   WsHeader* hdr;
+  // tape pass of the reverse sweep (MODE 4); cells c = t * Bp + b
+  const uint8_t* img2;       // backward image (its GLU slabs)
+  const float* wts;          // [B] per-sample weights w_b of sum_b w_b log psi_b
+  int64_t Bp;                // B rounded up to a whole tile of 128
+  __half* tape_f;            // [cells, 3, D] FP16 factors u (1 - h~^2), (h~ - U_mix h') u (1 - u), 1 - u
+  float* tape_dh;            // [cells, D] dh_glu
+  uint8_t* x1a;              // operand tapes (tape_off layout): h_hor, h_ver, [1 | one-hots] ...
+  uint8_t* x1b;
+  uint8_t* x1c;
+  uint8_t* g2;               // ... [dy_1 | dy_2] (GLU pre-activation gradients), [h], [1]
+  uint8_t* x2a;
+  uint8_t* x2c;
+  __nv_bfloat16* ytape;      // [cells, D] GLU outputs
+  float* gd;                 // [cells] d(sum w log psi) / d(logit difference)
 };
 
-// MODE 0: sampling, 1: teacher forcing, 2: Heisenberg chains, 3: cached-path tables.
+// MODE 0: sampling, 1: teacher forcing, 2: Heisenberg chains, 3: cached-path
+// tables, 4: tape pass of the reverse sweep (every (sample, position) cell in
+// parallel: gate factors, GLU backward, weight-gradient operands).
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __restrict__ img, WArgs a) {
   extern __shared__ uint8_t smraw[];
@@ -247,8 +286,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       if constexpr (MODE == 3) {
         src = img + kOffGlu + (size_t)(s % kNGlu) * kGluSlab;
         bytes = kGluSlab;
+      } else if (MODE == 4 && s % kTapeSlabs >= (uint32_t)kCellSlabs) {
+        src = a.img2 + kOffGlut + (size_t)(s % kTapeSlabs - kCellSlabs) * kGlutSlab;
+        bytes = kGlutSlab;
       } else {
-        const uint32_t q = s % kCellSlabs;
+        const uint32_t q = s % (MODE == 4 ? kTapeSlabs : kCellSlabs);
         src = q < (uint32_t)kGateSlabs ? img + (size_t)q * kGateSlab : img + kOffGlu + (size_t)(q - kGateSlabs) * kGluSlab;
         bytes = q < (uint32_t)kGateSlabs ? kGateSlab : kGluSlab;
       }
@@ -318,6 +360,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         });
       end_phase();
     };
+    // GLU backward (tape pass): dh_glu = [dy_1 | dy_2] [W_1 ; W_2] over A
+    // columns [0, 512) (single BF16), N = 256 -> TMEM [0, 256)
+    auto phase_glub = [&]() {
+      for (int i = 0; i < kNGlut; ++i)
+        consume([&](uint32_t sa) {
+          tc::mma_bf16(tbase, desc_a(16 * i), tc::make_desc(sa, 128, 256), kIdesc256, i == 0 ? 0u : 1u);
+        });
+      end_phase();
+    };
     auto go = [&]() {                  // the workers' inputs / TMEM reads are done
       __syncwarp();
       tc::group_barrier(kBarGo, kThreads);
@@ -342,6 +393,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         if (leader) phase_hor(false);   // chunk 1, h_hor
         go();
         if (leader) phase_glu();
+        if constexpr (MODE == 4) {
+          go();
+          if (leader) phase_glub();
+        }
       }
       __syncwarp();
     }
@@ -408,7 +463,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
     };
     // GLU epilogue and readout: 16-unit chunks in order, chunks by a fixed
     // pairwise tree (within the slice, then over the four slices)
-    auto glu_readout = [&]() -> float {
+    // (yout: this slice's 64 GLU outputs as BF16, the tape pass)
+    auto glu_readout = [&](__nv_bfloat16* yout) -> float {
       float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int c8 = 0; c8 < 8; ++c8) {
@@ -419,11 +475,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         tc::tmem_wait_ld();
         tie(a1);
         tie(a2);
+        float y[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-          zc[c8 >> 1] = fmaf(sAux[col + q], y, zc[c8 >> 1]);
+          y[q] = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+          zc[c8 >> 1] = fmaf(sAux[col + q], y[q], zc[c8 >> 1]);
         }
+        if (yout) *reinterpret_cast<uint4*>(yout + col) = pack8_bf16(y);
       }
       sZx[part * 128 + m] = (zc[0] + zc[1]) + (zc[2] + zc[3]);
       tc::fence_before_sync();
@@ -447,7 +505,173 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       tc::group_arrive(kBarGo, kThreads);
     };
 
-    if constexpr (MODE == 3) {
+    if constexpr (MODE == 4) {
+      // ---- tape pass of the reverse sweep: tiles of 128 samples at one position ----
+      const int nbt = (int)(a.Bp / 128);
+      const int64_t ntile = (int64_t)N * nbt, nkb = a.Bp * N / 16;
+      // an FP32 state (null: zeros) into the A operand and, if xt, its BF16
+      // rounding into an operand tape of width 256
+      auto stage_x = [&](const float* src, uint8_t* xt, int64_t cell) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int u = 128 * c + 32 * part + 8 * q;
+            float v[8];
+            if (src) {
+              const float4 x0 = *reinterpret_cast<const float4*>(src + u);
+              const float4 x1 = *reinterpret_cast<const float4*>(src + u + 4);
+              v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+              v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+            } else {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+            }
+            st_split8(kmo(u), kmo(WLO + u), v);
+            if (xt) *reinterpret_cast<uint4*>(xt + tape_off(cell, u, 256, nkb)) = pack8_bf16(v);
+          }
+      };
+      // chunk c's factors of the cell backward through h = u h~ + (1 - u) U_mix h':
+      // dh [u (1 - h~^2) | (h~ - U_mix h') u (1 - u) | 1 - u] are the
+      // gradients of the three pre-activation blocks
+      auto factors = [&](int c, int64_t cell) {
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          uint32_t aw[8], ag[8], au[8];
+          const int col = 32 * part + 8 * q4;
+          tld8(trow + col, aw);
+          tld8(trow + 128 + col, ag);
+          tld8(trow + 256 + col, au);
+          tc::tmem_wait_ld();
+          tie(aw);
+          tie(ag);
+          tie(au);
+          __half2 f1[4], f2[4], f3[4];
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) {
+            float g1[2], g2[2], g3[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float cc = hw_tanh2(__uint_as_float(aw[q + e]));
+              const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q + e])), 0.5f);
+              const float mix = __uint_as_float(au[q + e]);
+              g1[e] = ug * (1.0f - cc * cc);
+              g2[e] = (cc - mix) * ug * (1.0f - ug);
+              g3[e] = 1.0f - ug;
+            }
+            f1[q / 2] = __floats2half2_rn(g1[0], g1[1]);
+            f2[q / 2] = __floats2half2_rn(g2[0], g2[1]);
+            f3[q / 2] = __floats2half2_rn(g3[0], g3[1]);
+          }
+          __half* dst = a.tape_f + cell * (3 * WD) + 128 * c + col;
+          *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(f1);
+          *reinterpret_cast<uint4*>(dst + WD) = *reinterpret_cast<const uint4*>(f2);
+          *reinterpret_cast<uint4*>(dst + 2 * WD) = *reinterpret_cast<const uint4*>(f3);
+        }
+      };
+      for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
+        const bool has = tile < ntile;                  // the same for every row of the CTA
+        const int t = has ? (int)(tile / nbt) : 0;
+        const int64_t b = has ? (tile % nbt) * 128 + m : 0;
+        const bool valid = has && b < B;                // rows past B: zeros in, zeros out
+        const int64_t cell = (int64_t)t * a.Bp + b;
+        const Pz p = P(t);
+        const float* src_h = valid && p.r > 0 ? a.hcache + (b * N + p.j * Lx + zhor(p)) * WD : nullptr;
+        const float* src_v = valid && p.j > 0 ? a.hcache + (b * N + (p.j - 1) * Lx + p.i) * WD : nullptr;
+        const float* src_c = valid ? a.hcache + (b * N + p.j * Lx + p.i) * WD : nullptr;
+        if (has) {
+          stage_x(src_h, a.x1a, cell);
+          if (part == 0) {
+            const int s_h = valid && p.r > 0 ? (a.sigma_in[b * N + p.j * Lx + zhor(p)] ? 1 : 0) : -1;
+            const int s_v = valid && p.j > 0 ? (a.sigma_in[b * N + (p.j - 1) * Lx + p.i] ? 1 : 0) : -1;
+            const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+            const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+            *reinterpret_cast<uint4*>(kmo(WEX)) = make_uint4(one | (one << 16), oh, ov, oh);
+            *reinterpret_cast<uint4*>(kmo(WEX + 8)) = make_uint4(ov, 0u, 0u, 0u);
+            // the extra columns of the gate weight gradient: [1 | onehot(s_hor) | onehot(s_ver) | 0]
+            const float xe[8] = {1.0f, s_h == 0 ? 1.0f : 0.0f, s_h == 1 ? 1.0f : 0.0f, s_v == 0 ? 1.0f : 0.0f,
+                                 s_v == 1 ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f};
+            *reinterpret_cast<uint4*>(a.x1c + tape_off(cell, 0, 16, nkb)) = pack8_bf16(xe);
+            *reinterpret_cast<uint4*>(a.x1c + tape_off(cell, 8, 16, nkb)) = make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        if (!tc::group_barrier_or(has && !*s_abort, kBarAll, kThreads)) break;
+        wait_done();                                    // chunk 0 on h_hor
+        stage_x(src_v, a.x1b, cell);
+        to_issuer();
+        wait_done();                                    // chunk 0 complete
+        factors(0, cell);
+        to_issuer();
+        wait_done();                                    // chunk 1 on h_ver
+        stage_x(src_h, nullptr, cell);
+        to_issuer();
+        wait_done();                                    // chunk 1 complete
+        factors(1, cell);
+        stage_x(src_c, a.x2a, cell);                    // the cell's own state: the GLU's input
+        if (part == 0) {
+          glu_extras();
+          const float xe[8] = {1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          *reinterpret_cast<uint4*>(a.x2c + tape_off(cell, 0, 16, nkb)) = pack8_bf16(xe);
+          *reinterpret_cast<uint4*>(a.x2c + tape_off(cell, 8, 16, nkb)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        to_issuer();
+        wait_done();                                    // GLU
+        const float z = glu_readout(a.ytape + cell * WD);
+        // gradient of sum_b w_b log psi_b (log psi = 1/2 sum_t log p) with
+        // respect to the logit difference d; 0 at a site the mask forces
+        float gdv = 0.0f;
+        if (valid && !timed_out) {
+          const int s = a.sigma_in[b * N + p.j * Lx + p.i] ? 1 : 0;
+          const int nu = a.nup_tab[b * N + t];
+          const bool forced = a.sz0 && (nu >= (N >> 1) || t - nu >= (N >> 1));
+          if (!forced) gdv = 0.5f * a.wts[b] * ((s == 0 ? 1.0f : 0.0f) - sigmoid_acc(z + dc));
+        }
+        if (part == 0) a.gd[cell] = gdv;
+        // [dy_1 | dy_2] = dy [sigmoid(a_2) | y_1 sigmoid'(a_2)], dy = (U_0 - U_1) gdv,
+        // into the A operand (single BF16) and the G2 tape
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+          uint32_t a1[8], a2[8];
+          const int col = 64 * part + 8 * c8;
+          tld8(trow + col, a1);
+          tld8(trow + 256 + col, a2);
+          tc::tmem_wait_ld();
+          tie(a1);
+          tie(a2);
+          float d1[8], d2[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float sg = fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+            const float dy = sAux[col + q] * gdv;
+            d1[q] = dy * sg;
+            d2[q] = dy * __uint_as_float(a1[q]) * sg * (1.0f - sg);
+          }
+          const uint4 p1 = pack8_bf16(d1), p2 = pack8_bf16(d2);
+          *reinterpret_cast<uint4*>(kmo(col)) = p1;
+          *reinterpret_cast<uint4*>(kmo(256 + col)) = p2;
+          *reinterpret_cast<uint4*>(a.g2 + tape_off(cell, col, 128, nkb)) = p1;
+          *reinterpret_cast<uint4*>(a.g2 + tape_off(cell, 256 + col, 128, nkb)) = p2;
+        }
+        to_issuer();
+        wait_done();                                    // GLU backward: dh_glu
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+          uint32_t r[8];
+          const int col = 64 * part + 8 * c8;
+          tld8(trow + col, r);
+          tc::tmem_wait_ld();
+          tie(r);
+          float* dst = a.tape_dh + cell * WD + col;
+          reinterpret_cast<float4*>(dst)[0] =
+              make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+          reinterpret_cast<float4*>(dst)[1] =
+              make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+        }
+        tc::fence_before_sync();
+      }
+    } else if constexpr (MODE == 3) {
       // ---- cached-path tables: every (sample, position) cell is a row ----
       const int64_t ncell = B * N, ntile = (ncell + 127) / 128;
       for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
@@ -467,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         const bool any = tc::group_barrier_or(valid && !*s_abort, kBarAll, kThreads);
         if (!any) break;
         wait_done();
-        const float z = glu_readout();
+        const float z = glu_readout(nullptr);
         if (valid && part == 0 && !timed_out) {
           const float d = z + dc;
           const int nu = a.nup_tab[b * N + t];
@@ -670,7 +894,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         to_issuer();
         // ---- (f) GLU and the logit difference ----
         wait_done();
-        const float z = glu_readout();
+        const float z = glu_readout(nullptr);
         // ---- (g) row logic (every slice of a row runs it; slice 0 writes) ----
         bool fin = false;
         if (active && !timed_out) {
@@ -749,6 +973,522 @@ int sm_count_w() {
   return sms;
 }
 
+
+// ----------------------------------------------------------------------------
+// Reverse sweep at d_h = 256: d/dtheta sum_b w_b log psi_b (App. A cell and GLU,
+// zig-zag order of Sec. II), in four passes:
+//  1. tape pass (tc2dw_kernel<4>, every (sample, position) cell in parallel):
+//     from the cached states the forward's gates give the three factors with
+//     which the cell backward is linear in dh; the GLU forward gives y and the
+//     logit difference, hence gd = d(sum w log psi)/dd = w_b (onehot_0(s) -
+//     p0) / 2, dy = (U_0 - U_1) gd and [dy_1 | dy_2]; the GLU backward
+//     [dy_1 | dy_2] [W_1 ; W_2] is dh_glu.  The cell's inputs h_hor, h_ver,
+//     [1 | one-hots], its state h and [dy_1 | dy_2] go to the operand tapes of
+//     the weight-gradient GEMMs.
+//  2. sequential sweep (tc2dw_sweep_kernel, t = N-1 .. 0 for a tile of 128
+//     samples): dh = dh_glu + the horizontal successor's and the vertical
+//     successor's carries, G1 = dh [f1 | f2 | f3] (BF16, to the G1 tape and the
+//     A operand, in six chunks of 128 gate units), dh' = G1 [W ; W_g ; U_mix]
+//     (N = 512: the horizontal and the vertical predecessor's carries);
+//  3. weight-gradient GEMMs (tc2dw_wgrad_kernel): dW1 = G1^T [h_hor | h_ver |
+//     1 | one-hots] and dW2 = G2^T [h | 1] summed over every cell, split over
+//     cell ranges, both operands MN-major blocks of 16 cells streamed by bulk
+//     copies; dU_out and dc from gd and y (tc2dw_readout_kernel);
+//  4. the final reduction into the flat gradient (tc2dw_final_kernel).
+// ----------------------------------------------------------------------------
+
+// Backward image.  W1t slab q (q = 0..47): gate block g = q / 16 (W, W_g, U_mix,
+// true values), gate units 16 (q % 16) + k; element (n, k) = block[unit][n] for
+// the 512 h' columns n.  GLU-t slab q (0..31): element (n, k) = W_1[16 q + k][n]
+// (q < 16) or W_2[16 (q - 16) + k][n], n < 256.
+__global__ void pack_wide_bwd_kernel(const float* __restrict__ p, uint8_t* __restrict__ img2) {
+  constexpr int D = WD, W2c = 2 * D + 4;
+  const int oW = 0, oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D, ob1 = oW1 + D * D,
+            oW2 = ob1 + D;
+  const int n1 = kNW1t * 512 * 16, n2 = kNGlut * 256 * 16;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n1 + n2; t += gridDim.x * blockDim.x) {
+    if (t < n1) {
+      const int q = t / (512 * 16), e = t % (512 * 16), n = e / 16, k = e % 16;
+      const int g = q / 16, u = 16 * (q % 16) + k;
+      const float v = g == 0 ? p[oW + u * W2c + n] : g == 1 ? p[oWg + u * W2c + n] : p[oU + u * 2 * D + n];
+      *reinterpret_cast<__nv_bfloat16*>(img2 + (size_t)q * kW1tSlab + tc::kmajor_offset(n, k, 16)) =
+          __float2bfloat16_rn(v);
+    } else {
+      const int r = t - n1, q = r / (256 * 16), e = r % (256 * 16), n = e / 16, k = e % 16;
+      const float v = q < 16 ? p[oW1 + (16 * q + k) * D + n] : p[oW2 + (16 * (q - 16) + k) * D + n];
+      *reinterpret_cast<__nv_bfloat16*>(img2 + kOffGlut + (size_t)q * kGlutSlab + tc::kmajor_offset(n, k, 16)) =
+          __float2bfloat16_rn(v);
+    }
+  }
+}
+
+struct SwArgs {
+  int64_t B, Bp;
+  int Lx, N;
+  const __half* tape_f;      // [cells, 3, D]
+  const float* tape_dh;      // [cells, D]
+  float* carry_h;            // [Bp, D] the horizontal successor's dh' share
+  float* carry_v;            // [Bp, Lx, D] the vertical successor's dh' share, per lattice column
+  uint8_t* g1;               // G1 tape: [dh_W | dh_g | dh_mix] in six tiles of 128 columns
+  WsHeader* hdr;
+};
+
+struct SS {
+  static constexpr uint32_t kA = 0;                                  // 4 x [128 x 128] bf16 chunk slots
+  static constexpr uint32_t kRingOff = kA + 4 * 128 * 128 * 2;       // kRing x 16 KB
+  static constexpr uint32_t kPos = kRingOff + kRing * kSlotBytes;    // 256 ints
+  static constexpr uint32_t kBar = kPos + 256 * 4;                   // full[kRing], empty[kRing], done, drain
+  static constexpr uint32_t kMisc = kBar + (2 * kRing + 2) * 8;      // TMEM slot, abort flag
+  static constexpr uint32_t kBytes = 1024 + kMisc + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+};
+
+__global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t* __restrict__ w1t, SwArgs a) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
+  uint8_t* sA = sm + SS::kA;
+  uint8_t* ring = sm + SS::kRingOff;
+  int* sPos = reinterpret_cast<int*>(sm + SS::kPos);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + SS::kBar);
+  uint64_t* empty = full + kRing;
+  uint64_t* done = empty + kRing;
+  uint64_t* drain = done + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SS::kMisc);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SS::kMisc + 4);
+  const int N = a.N, Lx = a.Lx, Ly = a.N / a.Lx;
+  for (int t = threadIdx.x; t < N; t += kThreads) {
+    const Pz p = zpos(t, Lx);
+    sPos[t] = p.i | (p.j << 8) | (p.r << 16);
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kRing; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(drain, 1);
+    *s_abort = 0;
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool timed_out = false;
+  auto P = [&](int t) -> Pz {
+    const int v = sPos[t];
+    Pz p;
+    p.i = v & 255;
+    p.j = (v >> 8) & 255;
+    p.r = v >> 16;
+    return p;
+  };
+
+  if (warp == kWorkers / 32) {
+    // ======================== issuer warp ========================
+    // per step, six chunks of 128 gate units (W, W_g, U_mix blocks, two
+    // halves each), 8 slabs of [512 h' columns x 16 units] per chunk; chunk q
+    // reads A slot q % 4
+    const bool leader = lane == 0;
+    const uint32_t a_addr = tc::smem_addr(sA), r_addr = tc::smem_addr(ring);
+    uint32_t s_cons = 0, s_fill = 0;
+    bool dead = false;
+    auto die = [&]() {
+      dead = true;
+      timed_out = true;
+      *s_abort = 1;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    };
+    auto fill = [&]() {
+      if (dead) return;
+      const uint32_t s = s_fill, slot = s % kRing;
+      if (s >= (uint32_t)kRing && !tc::mbar_wait(&empty[slot], ((s / kRing) - 1) & 1, wlim)) {
+        die();
+        return;
+      }
+      mbar_expect_tx(&full[slot], kW1tSlab);
+      bulk_g2s(ring + slot * kSlotBytes, w1t + (size_t)(s % kNW1t) * kW1tSlab, kW1tSlab, &full[slot]);
+      ++s_fill;
+    };
+    auto chunk = [&](int q) {
+      for (int kk = 0; kk < 8; ++kk) {
+        if (dead) return;
+        const uint32_t s = s_cons, slot = s % kRing;
+        if (!tc::mbar_wait(&full[slot], (s / kRing) & 1, wlim)) {
+          die();
+          return;
+        }
+        tc::fence_after_sync();
+        const uint32_t sa = r_addr + slot * kSlotBytes;
+        const uint64_t da = tc::make_desc(a_addr + (uint32_t)(q % 4) * 32768u + 256u * kk, 128, 2048);
+        const uint32_t accf = (q == 0 && kk == 0) ? 0u : 1u;
+        tc::mma_bf16(tbase, da, tc::make_desc(sa, 128, 256), kIdesc256, accf);
+        tc::mma_bf16(tbase + 256, da, tc::make_desc(sa + 8192, 128, 256), kIdesc256, accf);
+        tc::mma_commit(&empty[slot]);
+        ++s_cons;
+        while (!dead && s_fill < s_cons + kRing - 1) fill();
+      }
+    };
+    auto go = [&]() {
+      __syncwarp();
+      tc::group_barrier(kBarGo, kThreads);
+      tc::fence_after_sync();
+    };
+    if (leader)
+      for (int q = 0; q < kRing; ++q) fill();
+    __syncwarp();
+    for (int step = 0; step < N; ++step) {
+      go();                            // dh' of the previous step read, chunks 0-3 written
+      if (leader) {
+        chunk(0);
+        chunk(1);
+        tc::mma_commit(done);          // slots 0, 1 free again
+        chunk(2);
+        chunk(3);
+        tc::mma_commit(done);
+        while (!dead && s_fill < s_cons + kRing) fill();
+      }
+      go();                            // chunks 4, 5 written
+      if (leader) {
+        chunk(4);
+        chunk(5);
+        tc::mma_commit(done);          // dh' complete
+        while (!dead && s_fill < s_cons + kRing) fill();
+      }
+      __syncwarp();
+    }
+    if (leader)
+      for (uint32_t s = s_cons; s < s_fill; ++s) tc::mbar_wait(&full[s % kRing], (s / kRing) & 1, kWait2);
+    __syncwarp();
+  } else {
+    // ======================== worker warps ========================
+    const int part = warp >> 2, quarter = warp & 3;
+    const int m = quarter * 32 + lane;                         // sample row = TMEM lane
+    const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16);
+    const int64_t b = (int64_t)blockIdx.x * 128 + m;           // rows past B carry zeros
+    const int h = part >> 1, cb = 64 * (part & 1);             // this slice's chunk half and column base
+    const int64_t nkb = a.Bp * N / 16;
+    uint32_t pd = 0;
+    auto wait_done = [&]() {
+      if (!tc::mbar_wait(done, pd, wlim)) {
+        timed_out = true;
+        *s_abort = 1;
+        flag_status(a.hdr, NQS_ETIMEOUT);
+      }
+      pd ^= 1;
+      tc::fence_after_sync();
+    };
+    auto to_issuer = [&]() {
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::group_arrive(kBarGo, kThreads);
+    };
+    auto slot_row = [&](int slot, int col) { return sA + slot * 32768 + tc::kmajor_offset(m, col, 128); };
+    for (int step = 0; step < N; ++step) {
+      const int t = N - 1 - step;
+      const Pz p = P(t);
+      const int64_t cell = (int64_t)t * a.Bp + b;
+      const bool has_h = t + 1 < N && P(t + 1).r > 0;         // horizontal successor in this lattice row
+      const bool has_v = p.j + 1 < Ly;                        // vertical successor (i, j + 1)
+      const float* ch = a.carry_h + b * WD;
+      const float* cv = a.carry_v + (b * Lx + p.i) * WD;
+      uint32_t dmp[32];                                        // dh_mix chunk, packed BF16
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) {
+        const int u0 = 64 * part + 8 * g8;
+        float dh[8];
+        {
+          const float4 x0 = *reinterpret_cast<const float4*>(a.tape_dh + cell * WD + u0);
+          const float4 x1 = *reinterpret_cast<const float4*>(a.tape_dh + cell * WD + u0 + 4);
+          dh[0] = x0.x; dh[1] = x0.y; dh[2] = x0.z; dh[3] = x0.w;
+          dh[4] = x1.x; dh[5] = x1.y; dh[6] = x1.z; dh[7] = x1.w;
+        }
+        if (has_h) {
+          const float4 x0 = *reinterpret_cast<const float4*>(ch + u0);
+          const float4 x1 = *reinterpret_cast<const float4*>(ch + u0 + 4);
+          dh[0] += x0.x; dh[1] += x0.y; dh[2] += x0.z; dh[3] += x0.w;
+          dh[4] += x1.x; dh[5] += x1.y; dh[6] += x1.z; dh[7] += x1.w;
+        }
+        if (has_v) {
+          const float4 x0 = *reinterpret_cast<const float4*>(cv + u0);
+          const float4 x1 = *reinterpret_cast<const float4*>(cv + u0 + 4);
+          dh[0] += x0.x; dh[1] += x0.y; dh[2] += x0.z; dh[3] += x0.w;
+          dh[4] += x1.x; dh[5] += x1.y; dh[6] += x1.z; dh[7] += x1.w;
+        }
+        const __half* f = a.tape_f + cell * (3 * WD) + u0;
+        const uint4 r1 = *reinterpret_cast<const uint4*>(f);
+        const uint4 r2 = *reinterpret_cast<const uint4*>(f + WD);
+        const uint4 r3 = *reinterpret_cast<const uint4*>(f + 2 * WD);
+        const __half2* f1 = reinterpret_cast<const __half2*>(&r1);
+        const __half2* f2 = reinterpret_cast<const __half2*>(&r2);
+        const __half2* f3 = reinterpret_cast<const __half2*>(&r3);
+        float gw[8], gg[8], gm[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 a1 = __half22float2(f1[q]), a2 = __half22float2(f2[q]), a3 = __half22float2(f3[q]);
+          gw[2 * q] = dh[2 * q] * a1.x;
+          gw[2 * q + 1] = dh[2 * q + 1] * a1.y;
+          gg[2 * q] = dh[2 * q] * a2.x;
+          gg[2 * q + 1] = dh[2 * q + 1] * a2.y;
+          gm[2 * q] = dh[2 * q] * a3.x;
+          gm[2 * q + 1] = dh[2 * q + 1] * a3.y;
+        }
+        const uint4 pw = pack8_bf16(gw), pg = pack8_bf16(gg), pm = pack8_bf16(gm);
+        *reinterpret_cast<uint4*>(slot_row(h, cb + 8 * g8)) = pw;
+        *reinterpret_cast<uint4*>(slot_row(2 + h, cb + 8 * g8)) = pg;
+        dmp[4 * g8] = pm.x;
+        dmp[4 * g8 + 1] = pm.y;
+        dmp[4 * g8 + 2] = pm.z;
+        dmp[4 * g8 + 3] = pm.w;
+        *reinterpret_cast<uint4*>(a.g1 + tape_off(cell, u0, 128, nkb)) = pw;
+        *reinterpret_cast<uint4*>(a.g1 + tape_off(cell, WD + u0, 128, nkb)) = pg;
+        *reinterpret_cast<uint4*>(a.g1 + tape_off(cell, 2 * WD + u0, 128, nkb)) = pm;
+      }
+      to_issuer();
+      wait_done();                                             // chunks 0, 1 done: their slots are free
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8)
+        *reinterpret_cast<uint4*>(slot_row(h, cb + 8 * g8)) =
+            make_uint4(dmp[4 * g8], dmp[4 * g8 + 1], dmp[4 * g8 + 2], dmp[4 * g8 + 3]);
+      to_issuer();
+      wait_done();                                             // chunks 2, 3
+      wait_done();                                             // chunks 4, 5: dh' in TMEM
+      // dh' = [horizontal predecessor's share | vertical predecessor's share]
+#pragma unroll
+      for (int g8 = 0; g8 < 8; ++g8) {
+        const int u0 = 64 * part + 8 * g8;
+        uint32_t rh[8], rv[8];
+        tld8(trow + u0, rh);
+        tld8(trow + 256 + u0, rv);
+        tc::tmem_wait_ld();
+        tie(rh);
+        tie(rv);
+        float* dh_ = a.carry_h + b * WD + u0;
+        float* dv_ = a.carry_v + (b * Lx + p.i) * WD + u0;
+        reinterpret_cast<float4*>(dh_)[0] =
+            make_float4(__uint_as_float(rh[0]), __uint_as_float(rh[1]), __uint_as_float(rh[2]), __uint_as_float(rh[3]));
+        reinterpret_cast<float4*>(dh_)[1] =
+            make_float4(__uint_as_float(rh[4]), __uint_as_float(rh[5]), __uint_as_float(rh[6]), __uint_as_float(rh[7]));
+        reinterpret_cast<float4*>(dv_)[0] =
+            make_float4(__uint_as_float(rv[0]), __uint_as_float(rv[1]), __uint_as_float(rv[2]), __uint_as_float(rv[3]));
+        reinterpret_cast<float4*>(dv_)[1] =
+            make_float4(__uint_as_float(rv[4]), __uint_as_float(rv[5]), __uint_as_float(rv[6]), __uint_as_float(rv[7]));
+      }
+    }
+  }
+  tc::fence_before_sync();
+  if (__syncthreads_or(timed_out) && threadIdx.x == kWorkers) tc::drain_mmas(drain, kWait2);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// Weight-gradient GEMMs.  Output tiles: GEMM1 (G1^T X1) t = 0..11: M-tile
+// t / 2 of the 768 gate rows against h_hor (+ the 16 extra columns) for even
+// t, h_ver for odd t; GEMM2 (G2^T X2) t = 12..15: M-tile t - 12 of the 512
+// GLU rows against h (+ extras).  A work unit is one tile over one of
+// `splits` ranges of 16-cell blocks; its FP32 sums go to out[unit][128][272].
+struct WgArgs {
+  const uint8_t* g1;
+  const uint8_t* x1a;
+  const uint8_t* x1b;
+  const uint8_t* x1c;
+  const uint8_t* g2;
+  const uint8_t* x2a;
+  const uint8_t* x2c;
+  int64_t nkb;
+  int splits;
+  float* out;
+  WsHeader* hdr;
+};
+constexpr int kWgTiles = 16, kWgCols = 272, kWgRing = 8;
+constexpr uint32_t kWgSlot = 4096 + 8192 + 512;   // A block, B block, B extras block
+
+struct SG {
+  static constexpr uint32_t kRingOff = 0;
+  static constexpr uint32_t kBar = kRingOff + kWgRing * kWgSlot;      // full[R], empty[R], done, drain
+  static constexpr uint32_t kMisc = kBar + (2 * kWgRing + 2) * 8;
+  static constexpr uint32_t kBytes = 1024 + kMisc + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+};
+
+__global__ void __launch_bounds__(128, 1) tc2dw_wgrad_kernel(WgArgs a) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;
+  uint8_t* ring = sm + SG::kRingOff;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + SG::kBar);
+  uint64_t* empty = full + kWgRing;
+  uint64_t* done = empty + kWgRing;
+  uint64_t* drain = done + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SG::kMisc);
+  const int unit = blockIdx.x, tile = unit / a.splits, split = unit % a.splits;
+  const bool g1 = tile < 12;
+  const int mt = g1 ? tile / 2 : tile - 12, nt = g1 ? tile % 2 : 0;
+  const uint8_t* A = (g1 ? a.g1 : a.g2) + (size_t)mt * a.nkb * 4096;
+  const uint8_t* Bm = g1 ? (nt == 0 ? a.x1a : a.x1b) : a.x2a;
+  const uint8_t* Bx = g1 ? (nt == 0 ? a.x1c : nullptr) : a.x2c;
+  const int64_t kps = (a.nkb + a.splits - 1) / a.splits, kb0 = (int64_t)split * kps;
+  const int64_t kb1 = kb0 + kps < a.nkb ? kb0 + kps : a.nkb;
+  const int64_t nk = kb1 > kb0 ? kb1 - kb0 : 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kWgRing; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(drain, 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  bool timed_out = false;
+  if (threadIdx.x == 0 && nk > 0) {
+    // both operands MN-major: rows = 16 cells (K), columns = 128 gate / GLU rows (M) or inputs (N)
+    constexpr uint32_t i256 = tc::make_idesc_bf16(128, 256) | (1u << 15) | (1u << 16);
+    constexpr uint32_t i16 = tc::make_idesc_bf16(128, 16) | (1u << 15) | (1u << 16);
+    const uint32_t r_addr = tc::smem_addr(ring);
+    const uint32_t bytes = 4096 + 8192 + (Bx ? 512 : 0);
+    int64_t s_cons = 0, s_fill = 0;
+    bool dead = false;
+    auto fill = [&]() {
+      if (dead || s_fill >= nk) return;
+      const int64_t s = s_fill;
+      const uint32_t slot = (uint32_t)(s % kWgRing);
+      if (s >= kWgRing && !tc::mbar_wait(&empty[slot], (uint32_t)((s / kWgRing) - 1) & 1, wlim)) {
+        dead = true;
+        return;
+      }
+      uint8_t* d = ring + slot * kWgSlot;
+      const int64_t kb = kb0 + s;
+      mbar_expect_tx(&full[slot], bytes);
+      bulk_g2s(d, A + (size_t)kb * 4096, 4096, &full[slot]);
+      bulk_g2s(d + 4096, Bm + (size_t)kb * 8192, 8192, &full[slot]);
+      if (Bx) bulk_g2s(d + 12288, Bx + (size_t)kb * 512, 512, &full[slot]);
+      ++s_fill;
+    };
+    for (int q = 0; q < kWgRing; ++q) fill();
+    while (!dead && s_cons < nk) {
+      const int64_t s = s_cons;
+      const uint32_t slot = (uint32_t)(s % kWgRing);
+      if (!tc::mbar_wait(&full[slot], (uint32_t)(s / kWgRing) & 1, wlim)) {
+        dead = true;
+        break;
+      }
+      tc::fence_after_sync();
+      const uint32_t sa = r_addr + slot * kWgSlot;
+      const uint32_t accf = s > 0 ? 1u : 0u;
+      const uint64_t da = tc::make_desc(sa, 2048, 128);
+      tc::mma_bf16(tbase, da, tc::make_desc(sa + 4096, 4096, 128), i256, accf);
+      if (Bx) tc::mma_bf16(tbase + 256, da, tc::make_desc(sa + 12288, 256, 128), i16, accf);
+      tc::mma_commit(&empty[slot]);
+      ++s_cons;
+      while (!dead && s_fill < nk && s_fill < s_cons + kWgRing - 1) fill();
+    }
+    tc::mma_commit(done);
+    if (dead) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    // no copy may still be landing when the CTA exits
+    for (int64_t s = s_cons; s < s_fill; ++s)
+      tc::mbar_wait(&full[(uint32_t)(s % kWgRing)], (uint32_t)(s / kWgRing) & 1, kWait2);
+  }
+  __syncwarp();
+  if (nk > 0 && !tc::mbar_wait(done, 0, wlim)) {
+    timed_out = true;
+    flag_status(a.hdr, NQS_ETIMEOUT);
+  }
+  tc::fence_after_sync();
+  // the unit's sums: lane m of the TMEM accumulator = output row m
+  const int w = threadIdx.x >> 5, m = threadIdx.x;
+  const uint32_t trow = tbase + ((uint32_t)(w * 32) << 16);
+  float* out = a.out + ((size_t)unit * 128 + m) * kWgCols;
+  const int ncol = Bx ? kWgCols : 256;
+  for (int c = 0; c < ncol; c += 8) {
+    uint32_t r[8];
+    tld8(trow + c, r);
+    tc::tmem_wait_ld();
+    tie(r);
+    float4 v0 = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+    float4 v1 = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+    if (nk == 0 || timed_out) v0 = v1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    reinterpret_cast<float4*>(out + c)[0] = v0;
+    reinterpret_cast<float4*>(out + c)[1] = v1;
+  }
+  tc::fence_before_sync();
+  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(drain, kWait2);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
+}
+
+// dU_out[0] = sum_cells gd y, dU_out[1] = -dU_out[0], dc = (sum gd, -sum gd):
+// per block, a fixed range of cells in order; thread k < 256 sums column k,
+// thread 256 the gd themselves.
+constexpr int kRoBlocks = 304;
+__global__ void __launch_bounds__(288) tc2dw_readout_kernel(const __nv_bfloat16* __restrict__ y,
+                                                          const float* __restrict__ gd, int64_t ncell,
+                                                          float* __restrict__ part) {
+  const int64_t per = (ncell + gridDim.x - 1) / gridDim.x, c0 = blockIdx.x * per;
+  const int64_t c1 = c0 + per < ncell ? c0 + per : ncell;
+  const int k = threadIdx.x;
+  if (k > WD) return;
+  float acc = 0.0f;
+  for (int64_t c = c0; c < c1; ++c) acc = fmaf(gd[c], k < WD ? __bfloat162float(y[c * WD + k]) : 1.0f, acc);
+  part[(size_t)blockIdx.x * (WD + 1) + k] = acc;
+}
+
+// Every flat parameter (App. A layout) from the GEMM units' sums (splits in
+// order) and the readout blocks' sums.
+__global__ void tc2dw_final_kernel(const float* __restrict__ wg, int splits, const float* __restrict__ ro, int nro,
+                                   float* __restrict__ grad) {
+  constexpr int D = WD, W2c = 2 * D + 4;
+  const int oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D, ob1 = oW1 + D * D,
+            oW2 = ob1 + D, ob2 = oW2 + D * D, oUo = ob2 + D, oc = oUo + 2 * D, P = oc + 2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  int tile = -1, row = 0, col = 0;
+  float sign = 1.0f;
+  if (i < ob) {                                  // W, W_g [d, 2d + 4], U_mix [d, 2d]
+    const int g = i < oWg ? 0 : i < oU ? 1 : 2;
+    const int w = g < 2 ? W2c : 2 * D, r = (i - (g == 0 ? 0 : g == 1 ? oWg : oU)) / w,
+              cc = (i - (g == 0 ? 0 : g == 1 ? oWg : oU)) % w;
+    const int gr = g * D + r;                    // gate row of G1
+    tile = 2 * (gr / 128) + (cc >= D && cc < 2 * D ? 1 : 0);
+    row = gr % 128;
+    col = cc < D ? cc : cc < 2 * D ? cc - D : 256 + 1 + (cc - 2 * D);
+  } else if (i < oW1) {                          // b, b_g: the extra column 0
+    const int g = i < obg ? 0 : 1, gr = g * D + (i - (g == 0 ? ob : obg));
+    tile = 2 * (gr / 128);
+    row = gr % 128;
+    col = 256;
+  } else if (i < oUo) {                          // W_1, b_1, W_2, b_2
+    const int g = i < oW2 ? 0 : 1, base = g == 0 ? oW1 : oW2, r0 = i - base;
+    const bool bias = r0 >= D * D;
+    const int v = bias ? r0 - D * D : r0 / D;
+    const int gr = g * D + v;
+    tile = 12 + gr / 128;
+    row = gr % 128;
+    col = bias ? 256 : r0 % D;
+  }
+  float s = 0.0f;
+  if (tile >= 0) {
+    for (int sp = 0; sp < splits; ++sp) s += wg[(((size_t)tile * splits + sp) * 128 + row) * kWgCols + col];
+  } else {                                       // U_out [2, d], c [2]
+    const int k = i < oc ? (i - oUo) % D : D;
+    sign = (i < oc ? (i - oUo) / D : i - oc) == 0 ? 1.0f : -1.0f;
+    for (int q = 0; q < nro; ++q) s += ro[(size_t)q * (WD + 1) + k];
+  }
+  grad[i] = sign * s;
+}
+
 }  // namespace
 
 cudaError_t tc2dw_pack(const float* params, uint8_t* wimg, cudaStream_t st) {
@@ -814,6 +1554,132 @@ cudaError_t tc2dw_chains(const Tc2Chains& c, const uint8_t* wimg, const uint8_t*
   a.counter = c.counter;
   a.hdr = c.hdr;
   return launch_w<2>(a, wimg, sm_count_w(), st);
+}
+
+namespace {
+constexpr int kWgSplits = 9;   // 16 tiles x 9 cell ranges: 144 units, one wave on 152 SMs
+
+struct WideGradLayout {
+  size_t img2, nup, tape_f, tape_dh, g1, x1a, x1b, x1c, g2, x2a, x2c, y, gd, carry_h, carry_v, wg, ro, total;
+};
+
+WideGradLayout wide_grad_layout(int64_t B, int Lx, int N) {
+  const size_t Bp = (size_t)((B + 127) / 128 * 128), cells = Bp * (size_t)N;
+  WideGradLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off += (bytes + 255) / 256 * 256; return at; };
+  L.img2 = take(kBwdImg);
+  L.nup = take((size_t)B * N * 4);
+  L.tape_f = take(cells * 3 * WD * 2);
+  L.tape_dh = take(cells * WD * 4);
+  L.g1 = take(cells * 3 * WD * 2);
+  L.x1a = take(cells * WD * 2);
+  L.x1b = take(cells * WD * 2);
+  L.x1c = take(cells * 16 * 2);
+  L.g2 = take(cells * 2 * WD * 2);
+  L.x2a = take(cells * WD * 2);
+  L.x2c = take(cells * 16 * 2);
+  L.y = take(cells * WD * 2);
+  L.gd = take(cells * 4);
+  L.carry_h = take(Bp * WD * 4);
+  L.carry_v = take(Bp * (size_t)Lx * WD * 4);
+  L.wg = take((size_t)kWgTiles * kWgSplits * 128 * kWgCols * 4);
+  L.ro = take((size_t)kRoBlocks * (WD + 1) * 4);
+  L.total = off;
+  return L;
+}
+}  // namespace
+
+size_t tc2dw_grad_bytes(int64_t B, int Lx, int N) { return wide_grad_layout(B, Lx, N).total; }
+
+cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cudaStream_t st) {
+  const WideGradLayout L = wide_grad_layout(g.B, g.Lx, g.N);
+  uint8_t* w = g.scratch;
+  const int64_t Bp = (g.B + 127) / 128 * 128, cells = Bp * g.N, nkb = cells / 16;
+  uint8_t* img2 = w + L.img2;
+  cudaError_t e;
+  const int nbwd = kNW1t * 512 * 16 + kNGlut * 256 * 16;
+  pack_wide_bwd_kernel<<<(nbwd + 255) / 256, 256, 0, st>>>(g.params, img2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int* nup = reinterpret_cast<int*>(w + L.nup);
+  if (g.B > 0) {
+    nup_prefix_kernel<<<(unsigned)((g.B + 127) / 128), 128, 0, st>>>(g.sigma, g.B, g.Lx, g.N, nup);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // 1. tape pass
+  WArgs a{};
+  a.B = g.B;
+  a.Lx = g.Lx;
+  a.N = g.N;
+  a.sz0 = g.sz0;
+  a.sigma_in = g.sigma;
+  a.hcache = const_cast<float*>(g.hcache);
+  a.nup_tab = nup;
+  a.hdr = g.hdr;
+  a.img2 = img2;
+  a.wts = g.weights;
+  a.Bp = Bp;
+  a.tape_f = reinterpret_cast<__half*>(w + L.tape_f);
+  a.tape_dh = reinterpret_cast<float*>(w + L.tape_dh);
+  a.x1a = w + L.x1a;
+  a.x1b = w + L.x1b;
+  a.x1c = w + L.x1c;
+  a.g2 = w + L.g2;
+  a.x2a = w + L.x2a;
+  a.x2c = w + L.x2c;
+  a.ytape = reinterpret_cast<__nv_bfloat16*>(w + L.y);
+  a.gd = reinterpret_cast<float*>(w + L.gd);
+  const int64_t ntile = (int64_t)g.N * (Bp / 128);
+  if ((e = launch_w<4>(a, wimg, ntile < sm_count_w() ? ntile : sm_count_w(), st)) != cudaSuccess) return e;
+  // 2. sequential sweep
+  SwArgs sw{};
+  sw.B = g.B;
+  sw.Bp = Bp;
+  sw.Lx = g.Lx;
+  sw.N = g.N;
+  sw.tape_f = a.tape_f;
+  sw.tape_dh = a.tape_dh;
+  sw.carry_h = reinterpret_cast<float*>(w + L.carry_h);
+  sw.carry_v = reinterpret_cast<float*>(w + L.carry_v);
+  sw.g1 = w + L.g1;
+  sw.hdr = g.hdr;
+  if ((e = cudaFuncSetAttribute(tc2dw_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SS::kBytes)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  if (Bp > 0) {
+    tc2dw_sweep_kernel<<<(unsigned)(Bp / 128), kThreads, SS::kBytes, st>>>(img2, sw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // 3. weight-gradient GEMMs and the readout gradients
+  WgArgs wg{};
+  wg.g1 = sw.g1;
+  wg.x1a = a.x1a;
+  wg.x1b = a.x1b;
+  wg.x1c = a.x1c;
+  wg.g2 = a.g2;
+  wg.x2a = a.x2a;
+  wg.x2c = a.x2c;
+  wg.nkb = nkb;
+  wg.splits = kWgSplits;
+  wg.out = reinterpret_cast<float*>(w + L.wg);
+  wg.hdr = g.hdr;
+  if ((e = cudaFuncSetAttribute(tc2dw_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SG::kBytes)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  tc2dw_wgrad_kernel<<<kWgTiles * kWgSplits, 128, SG::kBytes, st>>>(wg);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  float* ro = reinterpret_cast<float*>(w + L.ro);
+  tc2dw_readout_kernel<<<kRoBlocks, 288, 0, st>>>(a.ytape, a.gd, cells, ro);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 4. the flat gradient
+  constexpr int D = WD;
+  const int P = 6 * D * D + 10 * D + 2 * D * D + 4 * D + 2;
+  tc2dw_final_kernel<<<(P + 255) / 256, 256, 0, st>>>(wg.out, kWgSplits, ro, kRoBlocks, grad);
+  return cudaGetLastError();
 }
 
 cudaError_t tc2dw_set_wait_polls(uint32_t polls) { return cudaMemcpyToSymbol(tc::g_wait_polls, &polls, sizeof(polls)); }

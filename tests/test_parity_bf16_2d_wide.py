@@ -12,9 +12,10 @@ states, FP32 accumulation and state), so the bounds are the ones derived there
   E_loc         per sample 1e-2 S + 1e-5 N, S the summed exchange magnitude;
   sampling      the oracle's decision along the GPU's path outside a window of
                 8e-4 (j + 1) at row j, at most 1 % of the free draws inside it;
-  gradient      the FP32 reverse sweep on the BF16 forward's cache (the BF16
-                reverse sweep is built for d_h <= 64): cosine >= 0.999 and
-                relative L2 error <= 2e-2 against the oracle's gradient.
+  gradient      the BF16 reverse sweep (gate and GLU gradients and the
+                weight-gradient operands rounded to BF16, factors to FP16,
+                FP32 accumulation): cosine >= 0.999 and relative L2 error
+                <= 2e-2 against the oracle's gradient, as at d_h <= 64.
 Chains: 6 x 6 at B = 768 gives about 23,000 chain jobs, more than the 19,456
 rows of the persistent grid, so rows pull several jobs and restart from the
 cache.  The full-size case runs the 16 x 16, B = 8192 step in the launch
@@ -162,11 +163,30 @@ def test_wide_vmc_gradient(Lx, Ly, B):
     assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
+@pytest.mark.parametrize("Lx,Ly,B,sz0", [(4, 4, 100, True), (3, 5, 77, False), (5, 4, 130, True), (16, 16, 4, True)])
+def test_wide_logpsi_grad(Lx, Ly, B, sz0):
+    desc, d32, mod, pf, p = setup(Lx, Ly, D, sz0, seed=5, noise=0.05 if Lx * Ly <= 64 else 0.0)
+    sig = inputs.random_configs(B, mod.N, seed=6, sz0=sz0)
+    w = inputs.random_weights(B, seed=7).astype(np.float32)
+    sg = dev(sig, torch.uint8)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    g = nqs.logpsi_grad(desc, p, sg, hc, dev(w), ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    g = g.double().cpu().numpy()
+    cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
+
+
 def test_wide_full_size_16x16_b8192():
     """The 16 x 16, d_h = 256 Heisenberg step at B = 8192 in BF16: status clean,
     every draw of 64 samples checked against the oracle, and on 64 samples the
     local energies within the per-sample bound of the FP32 path and their
-    mean per site within 1e-4 of it; the gradient of the full batch finite."""
+    mean per site within 1e-4 of it; the gradient of the full batch finite,
+    and the full-batch reverse sweep against the oracle on 4 samples."""
     Lx = Ly = 16
     B = 8192
     desc, d32, mod, pf, p = setup(Lx, Ly, D, True, seed=3, noise=0.0)   # the workload's weights
@@ -192,6 +212,20 @@ def test_wide_full_size_16x16_b8192():
     e16, e32 = el.double().cpu().numpy()[pick], el32.double().cpu().numpy()
     assert abs(e16.mean() - e32.mean()) / mod.N <= 1e-4
     assert_eloc_per_sample(e16, e32, s[pick], Lx, Ly, 1.0, mod.N)
+    # the reverse sweep at the full batch (the step's launch configuration)
+    # against the oracle's gradient on 4 samples (weights zero elsewhere)
+    gpick = pick[:4]
+    e_all = el.double().cpu().numpy()
+    wv = np.zeros(B, dtype=np.float32)
+    wv[gpick] = (2.0 * (e_all[gpick] - e_all.mean()) / B).astype(np.float32)
+    gp = nqs.logpsi_grad(desc, p, sig, hc, dev(wv), ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    g_ref = ov.logpsi_grad(mod, pf, s[gpick], wv[gpick].astype(np.float64))
+    gp = gp.double().cpu().numpy()
+    cos = gp @ g_ref / (np.linalg.norm(gp) * np.linalg.norm(g_ref))
+    rel = np.linalg.norm(gp - g_ref) / np.linalg.norm(g_ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
 @pytest.mark.parametrize("Lx,Ly", [(17, 16), (16, 17)])
