@@ -60,9 +60,10 @@ nqs_status check_built(const Dims& d) {
 }
 
 bool use_tc(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU1D; }
-// the BF16 reverse sweep is built for d_h <= 64; at d_h = 128 the BF16 model's
-// gradient runs the FP32 reverse sweep on the (FP32) prefix cache
+// the 1D BF16 reverse sweep: weight gradients in TMEM for d_h <= 64 (tc1d.cu),
+// through operand tapes and a separate GEMM at d_h = 128 (tc1d_grad128.cu)
 bool use_tc_grad(const Dims& d) { return use_tc(d) && d.d <= 64; }
+bool use_tc128_grad(const Dims& d) { return use_tc(d) && d.d == 128; }
 // flat offset of the cRNN phase layer [U_phi | c_phi] (after the amplitude parameters)
 size_t phase_offset(const Dims& d) { return 3 * (size_t)d.d * d.d + 12 * (size_t)d.d + 2; }
 bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_GRU2D; }
@@ -120,6 +121,12 @@ Layout layout(const Dims& d, int64_t B, int op) {
       break;
     case NQS_OP_LOGPSI_GRAD:
     case NQS_OP_VMC_GRAD: {
+      if (use_tc128_grad(d)) {
+        L.a = take(d.P * sizeof(float));                       // the flat FP32 gradient
+        L.b = take((size_t)B * sizeof(float));                 // weights
+        L.c = take(tc1d128_grad_bytes(B, d.N));                // tapes of the reverse sweep
+        break;
+      }
       if (use_tc2dw_grad(d)) {
         L.a = take(d.P * sizeof(float));                       // the flat FP32 gradient
         L.b = take((size_t)B * sizeof(float));                 // weights
@@ -234,6 +241,21 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     t.hdr = static_cast<WsHeader*>(ws);
     if (tc1d_bptt(t, img, w3, wt, d.d, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(tc1d_bptt_reduce(t, d.d, grad, st));
+  }
+  if (use_tc128_grad(d)) {
+    uint8_t* wimg = at<uint8_t>(ws, L.w);
+    if (tc1d_pack(params, wimg, d.d, st) != cudaSuccess) return NQS_ECUDA;
+    Tc1WGrad g{};
+    g.B = B;
+    g.N = d.N;
+    g.sigma = sigma;
+    g.hcache = hcache;
+    g.weights = weights;
+    g.params = params;
+    g.scratch = at<uint8_t>(ws, L.c);
+    g.hdr = static_cast<WsHeader*>(ws);
+    if (tc1d128_grad(g, wimg, partial, st) != cudaSuccess) return NQS_ECUDA;
+    return cuda_status(reduce_partials(partial, 1, (int)d.P, grad, st));
   }
   if (use_tc2dw_grad(d)) {
     uint8_t* wimg = at<uint8_t>(ws, L.w);
@@ -729,7 +751,7 @@ nqs_status nqs_vmc_grad_global(const nqs_model_desc* desc, const float* params, 
 
 nqs_status nqs_set_wait_limit(int64_t polls) {
   const uint32_t v = polls < 0 ? tc_default_wait_polls() : (uint32_t)(polls > 0xFFFFFFFFll ? 0xFFFFFFFFll : polls);
-  if (tc1d_set_wait_polls(v) != cudaSuccess || tc2d_set_wait_polls(v) != cudaSuccess || tc2dw_set_wait_polls(v) != cudaSuccess ||
+  if (tc1d_set_wait_polls(v) != cudaSuccess || tc2d_set_wait_polls(v) != cudaSuccess || tc2dw_set_wait_polls(v) != cudaSuccess || tc1d128_set_wait_polls(v) != cudaSuccess ||
       tc2d_grad_set_wait_polls(v) != cudaSuccess)
     return NQS_ECUDA;
   return NQS_OK;

@@ -172,6 +172,21 @@ struct Tc2WGrad {
   WsHeader* hdr;
 };
 size_t tc2dw_grad_bytes(int64_t B, int Lx, int N);
+// d_h = 128 BF16 reverse sweep of the 1D GRU (tc1d_grad128.cu): tape pass,
+// sequential sweep, weight-gradient GEMMs, readout gradients; writes grad [P]
+struct Tc1WGrad {
+  int64_t B;
+  int N;
+  const uint8_t* sigma;
+  const float* hcache;
+  const float* weights;      // [B] w_b of sum_b w_b log psi_b
+  const float* params;
+  uint8_t* scratch;          // tc1d128_grad_bytes(B, N), 256-byte aligned
+  WsHeader* hdr;
+};
+size_t tc1d128_grad_bytes(int64_t B, int N);
+cudaError_t tc1d128_grad(const Tc1WGrad& g, const uint8_t* wimg, float* grad, cudaStream_t st);
+cudaError_t tc1d128_set_wait_polls(uint32_t polls);
 cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cudaStream_t st);
 
 // BF16 tensor-core 2D reverse sweep (tc2d_grad.cu)

@@ -36,12 +36,14 @@
 #include <cuda_fp16.h>
 
 #include "tc2d_common.cuh"
+#include "tc_wgrad.cuh"
 
 namespace nqs {
 
 namespace {
 
 using namespace tc2dh;
+using namespace tcw;
 
 constexpr int WD = 256;                            // d_h
 constexpr int WKA = 2 * WD + 16;                   // A operand columns: [hi(h) | extras | lo(h)]
@@ -139,32 +141,6 @@ __global__ void nup_prefix_kernel(const uint8_t* __restrict__ sigma, int64_t B, 
     const Pz p = zpos(t, Lx);
     n += sigma[b * N + p.j * Lx + p.i] ? 0 : 1;
   }
-}
-
-// Bulk asynchronous copy global -> shared, completing on an mbarrier's
-// transaction count (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" : : "r"(tc::smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-               :
-               : "r"(tc::smem_addr(dst)), "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
-               : "memory");
-}
-
-// Byte offset of element (cell c, column v) in an operand tape of the
-// weight-gradient GEMMs: columns split into tiles of TW, cells into blocks of
-// 16; each (tile, block) is one contiguous MN-major [16 x TW] BF16 operand
-// (rows = cells = K, LBO = (TW / 8) * 128, SBO = 128).  v is a multiple of 8.
-__device__ __forceinline__ size_t tape_off(int64_t c, int v, int TW, int64_t nkb) {
-  const int tile = v / TW, vv = v % TW, r = (int)(c & 15);
-  return ((size_t)tile * nkb + (size_t)(c >> 4)) * (size_t)(16 * TW * 2) + (size_t)((r >> 3) * (TW / 8) * 128) +
-         (size_t)((vv >> 3) * 128) + (size_t)((r & 7) * 16);
-}
-__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
-  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 
 struct SW {
@@ -990,7 +966,7 @@ int sm_count_w() {
 //     successor's carries, G1 = dh [f1 | f2 | f3] (BF16, to the G1 tape and the
 //     A operand, in six chunks of 128 gate units), dh' = G1 [W ; W_g ; U_mix]
 //     (N = 512: the horizontal and the vertical predecessor's carries);
-//  3. weight-gradient GEMMs (tc2dw_wgrad_kernel): dW1 = G1^T [h_hor | h_ver |
+//  3. weight-gradient GEMMs (tcw::wgrad_kernel): dW1 = G1^T [h_hor | h_ver |
 //     1 | one-hots] and dW2 = G2^T [h | 1] summed over every cell, split over
 //     cell ranges, both operands MN-major blocks of 16 cells streamed by bulk
 //     copies; dU_out and dc from gd and y (tc2dw_readout_kernel);
@@ -1286,148 +1262,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
 }
 
-// Weight-gradient GEMMs.  Output tiles: GEMM1 (G1^T X1) t = 0..11: M-tile
-// t / 2 of the 768 gate rows against h_hor (+ the 16 extra columns) for even
-// t, h_ver for odd t; GEMM2 (G2^T X2) t = 12..15: M-tile t - 12 of the 512
-// GLU rows against h (+ extras).  A work unit is one tile over one of
-// `splits` ranges of 16-cell blocks; its FP32 sums go to out[unit][128][272].
-struct WgArgs {
-  const uint8_t* g1;
-  const uint8_t* x1a;
-  const uint8_t* x1b;
-  const uint8_t* x1c;
-  const uint8_t* g2;
-  const uint8_t* x2a;
-  const uint8_t* x2c;
-  int64_t nkb;
-  int splits;
-  float* out;
-  WsHeader* hdr;
-};
-constexpr int kWgTiles = 16, kWgCols = 272, kWgRing = 8;
-constexpr uint32_t kWgSlot = 4096 + 8192 + 512;   // A block, B block, B extras block
-
-struct SG {
-  static constexpr uint32_t kRingOff = 0;
-  static constexpr uint32_t kBar = kRingOff + kWgRing * kWgSlot;      // full[R], empty[R], done, drain
-  static constexpr uint32_t kMisc = kBar + (2 * kWgRing + 2) * 8;
-  static constexpr uint32_t kBytes = 1024 + kMisc + 16;
-  static_assert(kBytes <= 227 * 1024, "shared memory budget");
-};
-
-__global__ void __launch_bounds__(128, 1) tc2dw_wgrad_kernel(WgArgs a) {
-  extern __shared__ uint8_t smraw[];
-  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
-  const uint32_t wlim = tc::g_wait_polls;
-  uint8_t* ring = sm + SG::kRingOff;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + SG::kBar);
-  uint64_t* empty = full + kWgRing;
-  uint64_t* done = empty + kWgRing;
-  uint64_t* drain = done + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SG::kMisc);
-  const int unit = blockIdx.x, tile = unit / a.splits, split = unit % a.splits;
-  const bool g1 = tile < 12;
-  const int mt = g1 ? tile / 2 : tile - 12, nt = g1 ? tile % 2 : 0;
-  const uint8_t* A = (g1 ? a.g1 : a.g2) + (size_t)mt * a.nkb * 4096;
-  const uint8_t* Bm = g1 ? (nt == 0 ? a.x1a : a.x1b) : a.x2a;
-  const uint8_t* Bx = g1 ? (nt == 0 ? a.x1c : nullptr) : a.x2c;
-  const int64_t kps = (a.nkb + a.splits - 1) / a.splits, kb0 = (int64_t)split * kps;
-  const int64_t kb1 = kb0 + kps < a.nkb ? kb0 + kps : a.nkb;
-  const int64_t nk = kb1 > kb0 ? kb1 - kb0 : 0;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < kWgRing; ++q) {
-      tc::mbar_init(&full[q], 1);
-      tc::mbar_init(&empty[q], 1);
-    }
-    tc::mbar_init(done, 1);
-    tc::mbar_init(drain, 1);
-    tc::mbar_fence_init();
-  }
-  if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tbase = *tslot;
-  bool timed_out = false;
-  if (threadIdx.x == 0 && nk > 0) {
-    // both operands MN-major: rows = 16 cells (K), columns = 128 gate / GLU rows (M) or inputs (N)
-    constexpr uint32_t i256 = tc::make_idesc_bf16(128, 256) | (1u << 15) | (1u << 16);
-    constexpr uint32_t i16 = tc::make_idesc_bf16(128, 16) | (1u << 15) | (1u << 16);
-    const uint32_t r_addr = tc::smem_addr(ring);
-    const uint32_t bytes = 4096 + 8192 + (Bx ? 512 : 0);
-    int64_t s_cons = 0, s_fill = 0;
-    bool dead = false;
-    auto fill = [&]() {
-      if (dead || s_fill >= nk) return;
-      const int64_t s = s_fill;
-      const uint32_t slot = (uint32_t)(s % kWgRing);
-      if (s >= kWgRing && !tc::mbar_wait(&empty[slot], (uint32_t)((s / kWgRing) - 1) & 1, wlim)) {
-        dead = true;
-        return;
-      }
-      uint8_t* d = ring + slot * kWgSlot;
-      const int64_t kb = kb0 + s;
-      mbar_expect_tx(&full[slot], bytes);
-      bulk_g2s(d, A + (size_t)kb * 4096, 4096, &full[slot]);
-      bulk_g2s(d + 4096, Bm + (size_t)kb * 8192, 8192, &full[slot]);
-      if (Bx) bulk_g2s(d + 12288, Bx + (size_t)kb * 512, 512, &full[slot]);
-      ++s_fill;
-    };
-    for (int q = 0; q < kWgRing; ++q) fill();
-    while (!dead && s_cons < nk) {
-      const int64_t s = s_cons;
-      const uint32_t slot = (uint32_t)(s % kWgRing);
-      if (!tc::mbar_wait(&full[slot], (uint32_t)(s / kWgRing) & 1, wlim)) {
-        dead = true;
-        break;
-      }
-      tc::fence_after_sync();
-      const uint32_t sa = r_addr + slot * kWgSlot;
-      const uint32_t accf = s > 0 ? 1u : 0u;
-      const uint64_t da = tc::make_desc(sa, 2048, 128);
-      tc::mma_bf16(tbase, da, tc::make_desc(sa + 4096, 4096, 128), i256, accf);
-      if (Bx) tc::mma_bf16(tbase + 256, da, tc::make_desc(sa + 12288, 256, 128), i16, accf);
-      tc::mma_commit(&empty[slot]);
-      ++s_cons;
-      while (!dead && s_fill < nk && s_fill < s_cons + kWgRing - 1) fill();
-    }
-    tc::mma_commit(done);
-    if (dead) {
-      timed_out = true;
-      flag_status(a.hdr, NQS_ETIMEOUT);
-    }
-    // no copy may still be landing when the CTA exits
-    for (int64_t s = s_cons; s < s_fill; ++s)
-      tc::mbar_wait(&full[(uint32_t)(s % kWgRing)], (uint32_t)(s / kWgRing) & 1, kWait2);
-  }
-  __syncwarp();
-  if (nk > 0 && !tc::mbar_wait(done, 0, wlim)) {
-    timed_out = true;
-    flag_status(a.hdr, NQS_ETIMEOUT);
-  }
-  tc::fence_after_sync();
-  // the unit's sums: lane m of the TMEM accumulator = output row m
-  const int w = threadIdx.x >> 5, m = threadIdx.x;
-  const uint32_t trow = tbase + ((uint32_t)(w * 32) << 16);
-  float* out = a.out + ((size_t)unit * 128 + m) * kWgCols;
-  const int ncol = Bx ? kWgCols : 256;
-  for (int c = 0; c < ncol; c += 8) {
-    uint32_t r[8];
-    tld8(trow + c, r);
-    tc::tmem_wait_ld();
-    tie(r);
-    float4 v0 = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
-    float4 v1 = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
-    if (nk == 0 || timed_out) v0 = v1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    reinterpret_cast<float4*>(out + c)[0] = v0;
-    reinterpret_cast<float4*>(out + c)[1] = v1;
-  }
-  tc::fence_before_sync();
-  if (__syncthreads_or(timed_out) && threadIdx.x == 0) tc::drain_mmas(drain, kWait2);
-  __syncthreads();
-  tc::fence_after_sync();
-  if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 512);
-}
+// Weight-gradient GEMMs (tcw::wgrad_kernel<256>).  Output tiles: GEMM1 (G1^T
+// X1) t = 0..11: M-tile t / 2 of the 768 gate rows against h_hor (+ the 16
+// extra columns) for even t, h_ver for odd t; GEMM2 (G2^T X2) t = 12..15:
+// M-tile t - 12 of the 512 GLU rows against h (+ extras).  A work unit is one
+// tile over one of kWgSplits ranges of 16-cell blocks.
+constexpr int kWgTiles = 16, kWgCols = tcw::WgS<256>::kCols;
 
 // dU_out[0] = sum_cells gd y, dU_out[1] = -dU_out[0], dc = (sum gd, -sum gd):
 // per block, a fixed range of cells in order; thread k < 256 sums column k,
@@ -1654,24 +1494,18 @@ cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cuda
   }
   // 3. weight-gradient GEMMs and the readout gradients
   WgArgs wg{};
-  wg.g1 = sw.g1;
-  wg.x1a = a.x1a;
-  wg.x1b = a.x1b;
-  wg.x1c = a.x1c;
-  wg.g2 = a.g2;
-  wg.x2a = a.x2a;
-  wg.x2c = a.x2c;
+  for (int t = 0; t < kWgTiles; ++t) {
+    const bool first = t < 12;
+    const int mt = first ? t / 2 : t - 12, nt = first ? t % 2 : 0;
+    wg.tiles[t].A = (first ? sw.g1 : a.g2) + (size_t)mt * nkb * 4096;
+    wg.tiles[t].Bm = first ? (nt == 0 ? a.x1a : a.x1b) : a.x2a;
+    wg.tiles[t].Bx = first ? (nt == 0 ? a.x1c : nullptr) : a.x2c;
+  }
   wg.nkb = nkb;
   wg.splits = kWgSplits;
   wg.out = reinterpret_cast<float*>(w + L.wg);
   wg.hdr = g.hdr;
-  if ((e = cudaFuncSetAttribute(tc2dw_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SG::kBytes)) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return e;
-  }
-  tc2dw_wgrad_kernel<<<kWgTiles * kWgSplits, 128, SG::kBytes, st>>>(wg);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_wgrad<256>(wg, kWgTiles, st)) != cudaSuccess) return e;
   float* ro = reinterpret_cast<float*>(w + L.ro);
   tc2dw_readout_kernel<<<kRoBlocks, 288, 0, st>>>(a.ytape, a.gd, cells, ro);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

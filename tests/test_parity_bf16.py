@@ -211,7 +211,8 @@ def test_bf16_d128_against_oracle():
     from an FP32 table, 2 or 4 threads per row): log psi and cache, every
     sampling draw (window 2e-3: twice the d_h = 64 window, the gate GEMMs sum
     twice as many BF16 products), per-sample local energies, and the gradient
-    (the FP32 reverse sweep on the cache of the BF16 forward)."""
+    of the BF16 reverse sweep (tape pass, sequential sweep, weight-gradient
+    GEMMs) at the d_h <= 64 bounds."""
     N, d, B = 60, 128, 200
     desc, mod, pf, p = setup(N, d)
     sig = inputs.random_configs(B, N, seed=61)
@@ -239,6 +240,29 @@ def test_bf16_d128_against_oracle():
     g_ref = ov.vmc_gradient(mod, pf, sm.astype(np.int64), e_ref)
     gg = g.double().cpu().numpy()
     assert gg @ g_ref / (np.linalg.norm(gg) * np.linalg.norm(g_ref)) >= 0.999
+    assert np.linalg.norm(gg - g_ref) / np.linalg.norm(g_ref) <= 2e-2
+
+
+@pytest.mark.parametrize("N,B", [(60, 200), (17, 129), (100, 33), (3, 300)])
+def test_bf16_d128_logpsi_grad(N, B):
+    """The d_h = 128 BF16 reverse sweep on random configurations and weights
+    (ragged tiles, short and long chains) against the oracle's reverse sweep:
+    cosine >= 0.999 and relative L2 error <= 2e-2, as at d_h <= 64."""
+    d = 128
+    desc, mod, pf, p = setup(N, d, seed=63)
+    sig = inputs.random_configs(B, N, seed=64)
+    w = inputs.random_weights(B, seed=65).astype(np.float32)
+    sg = torch.tensor(sig, device=DEV)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    g = nqs.logpsi_grad(desc, p, sg, hc, torch.tensor(w, device=DEV), ws=ws)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    gg = g.double().cpu().numpy()
+    cos = gg @ ref / (np.linalg.norm(gg) * np.linalg.norm(ref))
+    rel = np.linalg.norm(gg - ref) / np.linalg.norm(ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
 def test_bf16_d128_variants_agree_bitwise():
