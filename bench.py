@@ -633,7 +633,7 @@ def run_replicas(args, w):
         "vs_baseline": None, "dtype": "bf16" if chosen is r16 else "f32", "data": "synthetic",
         "config": {"workload": w["name"], "global_batch": total_B, "seq_len": N, "replicas": R,
                    "parallelism": "single",
-                   "precision": ("bf16 tensor-core replicas (d_h 16-128; the d_h 128 gradient on the FP32 sweep)"
+                   "precision": ("bf16 tensor-core replicas (d_h 16-128) and reverse sweeps"
                                  if chosen is r16 else "fp32"),
                    "fp32_value": total_B / (r32["step_ms"] * 1e-3), "fp32_ms_per_step": r32["step_ms"],
                    "bf16_check": check,
