@@ -68,7 +68,9 @@ constexpr size_t kBwdImg = kOffGlut + (size_t)kNGlut * kGlutSlab;
 constexpr int kTapeSlabs = kCellSlabs + kNGlut;    // 115 slabs per tape-pass tile
 constexpr int kRing = 5;                           // ring slots
 constexpr uint32_t kSlotBytes = 16384;
-constexpr int kWorkers = 512, kThreads = kWorkers + 32;
+constexpr int kWorkers = 512;
+constexpr int kSync = kWorkers + 32;               // threads at the named barriers: workers + issuer warp
+constexpr int kThreads = kWorkers + 64;            // + the producer warp (copies only)
 constexpr uint32_t kBarAll = 1, kBarGo = 2, kBarW = 3;   // named barriers
 constexpr uint32_t kIdesc256 = tc::make_idesc_bf16(128, 256);
 constexpr uint32_t kIdesc128 = tc::make_idesc_bf16(128, 128);
@@ -156,6 +158,52 @@ struct SW {
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
 };
 
+// The producer warp's loop (lane 0): copy slab s into ring slot s % kRing as
+// soon as the MMAs that read the slot's previous slab have committed to
+// empty[slot], running up to kRing slabs ahead of the issuer, until the
+// issuer raises *stop; then wait for the copies issued beyond the issuer's
+// last consumed slab (*cons), so that none lands after the CTA has exited.
+// src(s, ptr, bytes) names slab s of the kernel's sequence.
+template <typename Src>
+__device__ void produce_slabs(uint8_t* ring, uint64_t* full, uint64_t* empty, volatile int* stop,
+                              volatile uint32_t* cons, volatile int* abort_flag, WsHeader* hdr, uint32_t wlim,
+                              bool& timed_out, Src src) {
+  uint32_t s = 0;
+  for (;; ++s) {
+    const uint32_t slot = s % kRing;
+    if (s >= (uint32_t)kRing) {
+      const uint32_t par = ((s / kRing) - 1) & 1;
+      bool got = false;
+      for (uint32_t it = 0; it < wlim; ++it) {
+        if (tc::mbar_wait(&empty[slot], par, 1)) {
+          got = true;
+          break;
+        }
+        if (*stop) break;
+      }
+      if (!got) {
+        if (!*stop) {
+          timed_out = true;
+          *abort_flag = 1;
+          flag_status(hdr, NQS_ETIMEOUT);
+        }
+        break;
+      }
+    }
+    if (*stop) break;
+    const uint8_t* ptr;
+    uint32_t bytes;
+    src(s, ptr, bytes);
+    mbar_expect_tx(&full[slot], bytes);
+    bulk_g2s(ring + slot * kSlotBytes, ptr, bytes, &full[slot]);
+  }
+  // the issuer publishes its count before it raises *stop (bounded wait:
+  // after a timeout here the issuer still finishes its loop)
+  for (uint32_t it = 0; it < (1u << 22) && !*stop; ++it) __nanosleep(1000);
+  const uint32_t c0 = *cons;
+  for (uint32_t q = c0; q < s; ++q) tc::mbar_wait(&full[q % kRing], (q / kRing) & 1, tc::kDefaultWaitPolls);
+}
+
 struct WArgs {
   int64_t B;
   int Lx, N, nb, sz0;
@@ -212,6 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
   uint64_t* drain = done + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SW::kMisc);
   volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SW::kMisc + 4);
+  volatile int* s_stop = reinterpret_cast<volatile int*>(sm + SW::kMisc + 8);          // issuer done
+  volatile uint32_t* s_consf = reinterpret_cast<volatile uint32_t*>(sm + SW::kMisc + 12);   // its slab count
 
   const float* aux = reinterpret_cast<const float*>(img + kOffAux);
   for (int i = threadIdx.x; i < WD + 1; i += kThreads) sAux[i] = aux[i];
@@ -227,6 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
     tc::mbar_init(done, 1);
     tc::mbar_init(drain, 1);
     *s_abort = 0;
+    *s_stop = 0;
+    *s_consf = 0;
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -237,45 +289,40 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   bool timed_out = false;
 
-  if (warp == kWorkers / 32) {
+  if (warp == kWorkers / 32 + 1) {
+    // ======================== producer warp ========================
+    if (lane == 0)
+      produce_slabs(ring, full, empty, s_stop, s_consf, s_abort, a.hdr, wlim, timed_out,
+                    [&](uint32_t s, const uint8_t*& src, uint32_t& bytes) {
+                      if constexpr (MODE == 3) {
+                        src = img + kOffGlu + (size_t)(s % kNGlu) * kGluSlab;
+                        bytes = kGluSlab;
+                      } else {
+                        if (MODE == 4 && s % kTapeSlabs >= (uint32_t)kCellSlabs) {
+                          src = a.img2 + kOffGlut + (size_t)(s % kTapeSlabs - kCellSlabs) * kGlutSlab;
+                          bytes = kGlutSlab;
+                          return;
+                        }
+                        const uint32_t q = s % (MODE == 4 ? kTapeSlabs : kCellSlabs);
+                        src = q < (uint32_t)kGateSlabs ? img + (size_t)q * kGateSlab
+                                                       : img + kOffGlu + (size_t)(q - kGateSlabs) * kGluSlab;
+                        bytes = q < (uint32_t)kGateSlabs ? kGateSlab : kGluSlab;
+                      }
+                    });
+    __syncwarp();
+  } else if (warp == kWorkers / 32) {
     // ======================== issuer warp ========================
     const bool leader = lane == 0;
     const uint32_t a_addr = tc::smem_addr(sA), r_addr = tc::smem_addr(ring);
-    uint32_t s_cons = 0, s_fill = 0;   // slabs consumed by MMAs / copied (leader)
-    bool dead = false;                 // a wait gave up: no more copies or MMAs
+    uint32_t s_cons = 0;               // slabs consumed by MMAs (leader)
+    bool dead = false;                 // a wait gave up: no more MMAs
     auto die = [&]() {
       dead = true;
       timed_out = true;
       *s_abort = 1;
       flag_status(a.hdr, NQS_ETIMEOUT);
     };
-    auto fill = [&]() {                // copy slab s_fill into its slot
-      if (dead) return;
-      const uint32_t s = s_fill, slot = s % kRing;
-      // the slot's previous slab: its MMAs have committed to empty[slot]
-      if (s >= (uint32_t)kRing && !tc::mbar_wait(&empty[slot], ((s / kRing) - 1) & 1, wlim)) {
-        die();
-        return;
-      }
-      const uint8_t* src;
-      uint32_t bytes;
-      if constexpr (MODE == 3) {
-        src = img + kOffGlu + (size_t)(s % kNGlu) * kGluSlab;
-        bytes = kGluSlab;
-      } else if (MODE == 4 && s % kTapeSlabs >= (uint32_t)kCellSlabs) {
-        src = a.img2 + kOffGlut + (size_t)(s % kTapeSlabs - kCellSlabs) * kGlutSlab;
-        bytes = kGlutSlab;
-      } else {
-        const uint32_t q = s % (MODE == 4 ? kTapeSlabs : kCellSlabs);
-        src = q < (uint32_t)kGateSlabs ? img + (size_t)q * kGateSlab : img + kOffGlu + (size_t)(q - kGateSlabs) * kGluSlab;
-        bytes = q < (uint32_t)kGateSlabs ? kGateSlab : kGluSlab;
-      }
-      mbar_expect_tx(&full[slot], bytes);
-      bulk_g2s(ring + slot * kSlotBytes, src, bytes, &full[slot]);
-      ++s_fill;
-    };
-    // one slab: wait for its copy, issue its MMAs, release the slot, refill
-    // the slots of earlier slabs (their MMAs precede the ones just issued)
+    // one slab: wait for its copy, issue its MMAs, release the slot to the producer
     auto consume = [&](auto&& mmas) {
       if (dead) return;
       const uint32_t s = s_cons, slot = s % kRing;
@@ -287,13 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       mmas(r_addr + slot * kSlotBytes);
       tc::mma_commit(&empty[slot]);
       ++s_cons;
-      while (!dead && s_fill < s_cons + kRing - 1) fill();
     };
-    // end of a phase: completion to the workers, then the last slab's slot
-    auto end_phase = [&]() {
-      tc::mma_commit(done);
-      while (!dead && s_fill < s_cons + kRing) fill();
-    };
+    // end of a phase: its completion to the workers
+    auto end_phase = [&]() { tc::mma_commit(done); };
     auto desc_a = [&](int col) { return tc::make_desc(a_addr + (uint32_t)col * 16, 128, kSboA); };
     // gate slab: rows [0, 256) -> TMEM [0, 256), rows [256, 384) -> [256, 384)
     auto mma_gate = [&](uint32_t sa, int col, bool lo, uint32_t accf) {
@@ -347,14 +390,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
     };
     auto go = [&]() {                  // the workers' inputs / TMEM reads are done
       __syncwarp();
-      tc::group_barrier(kBarGo, kThreads);
+      tc::group_barrier(kBarGo, kSync);
       tc::fence_after_sync();
     };
-    if (leader)
-      for (int q = 0; q < kRing; ++q) fill();
-    __syncwarp();
     for (;;) {
-      const bool any = tc::group_barrier_or(false, kBarAll, kThreads);
+      const bool any = tc::group_barrier_or(false, kBarAll, kSync);
       if (!any) break;
       tc::fence_after_sync();
       if constexpr (MODE == 3) {
@@ -376,9 +416,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       }
       __syncwarp();
     }
-    // no copy may still be landing when the CTA exits
-    if (leader)
-      for (uint32_t s = s_cons; s < s_fill; ++s) tc::mbar_wait(&full[s % kRing], (s / kRing) & 1, kWait2);
+    // the producer waits for its copies past this count, then exits
+    if (leader) {
+      *s_consf = s_cons;
+      __threadfence_block();
+      *s_stop = 1;
+    }
     __syncwarp();
   } else {
     // ======================== worker warps ========================
@@ -478,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       cp_wait_2d();
       tc::fence_async_smem();
       tc::fence_before_sync();
-      tc::group_arrive(kBarGo, kThreads);
+      tc::group_arrive(kBarGo, kSync);
     };
 
     if constexpr (MODE == 4) {
@@ -573,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
-        if (!tc::group_barrier_or(has && !*s_abort, kBarAll, kThreads)) break;
+        if (!tc::group_barrier_or(has && !*s_abort, kBarAll, kSync)) break;
         wait_done();                                    // chunk 0 on h_hor
         stage_x(src_v, a.x1b, cell);
         to_issuer();
@@ -664,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
-        const bool any = tc::group_barrier_or(valid && !*s_abort, kBarAll, kThreads);
+        const bool any = tc::group_barrier_or(valid && !*s_abort, kBarAll, kSync);
         if (!any) break;
         wait_done();
         const float z = glu_readout(nullptr);
@@ -832,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
         cp_wait_2d();
         tc::fence_async_smem();
         tc::fence_before_sync();
-        const bool any = tc::group_barrier_or(active && !*s_abort, kBarAll, kThreads);
+        const bool any = tc::group_barrier_or(active && !*s_abort, kBarAll, kSync);
         if (!any) break;
         float uni = 0.0f;
         if (MODE == 0 && active)
@@ -1032,6 +1075,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
   uint64_t* drain = done + 1;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + SS::kMisc);
   volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SS::kMisc + 4);
+  volatile int* s_stop = reinterpret_cast<volatile int*>(sm + SS::kMisc + 8);
+  volatile uint32_t* s_consf = reinterpret_cast<volatile uint32_t*>(sm + SS::kMisc + 12);
   const int N = a.N, Lx = a.Lx, Ly = a.N / a.Lx;
   for (int t = threadIdx.x; t < N; t += kThreads) {
     const Pz p = zpos(t, Lx);
@@ -1045,6 +1090,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
     tc::mbar_init(done, 1);
     tc::mbar_init(drain, 1);
     *s_abort = 0;
+    *s_stop = 0;
+    *s_consf = 0;
     tc::mbar_fence_init();
   }
   if (threadIdx.x < 32) tc::tmem_alloc(tslot, 512);
@@ -1063,31 +1110,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
     return p;
   };
 
-  if (warp == kWorkers / 32) {
+  if (warp == kWorkers / 32 + 1) {
+    // ======================== producer warp ========================
+    if (lane == 0)
+      produce_slabs(ring, full, empty, s_stop, s_consf, s_abort, a.hdr, wlim, timed_out,
+                    [&](uint32_t s, const uint8_t*& src, uint32_t& bytes) {
+                      src = w1t + (size_t)(s % kNW1t) * kW1tSlab;
+                      bytes = kW1tSlab;
+                    });
+    __syncwarp();
+  } else if (warp == kWorkers / 32) {
     // ======================== issuer warp ========================
     // per step, six chunks of 128 gate units (W, W_g, U_mix blocks, two
     // halves each), 8 slabs of [512 h' columns x 16 units] per chunk; chunk q
     // reads A slot q % 4
     const bool leader = lane == 0;
     const uint32_t a_addr = tc::smem_addr(sA), r_addr = tc::smem_addr(ring);
-    uint32_t s_cons = 0, s_fill = 0;
+    uint32_t s_cons = 0;
     bool dead = false;
     auto die = [&]() {
       dead = true;
       timed_out = true;
       *s_abort = 1;
       flag_status(a.hdr, NQS_ETIMEOUT);
-    };
-    auto fill = [&]() {
-      if (dead) return;
-      const uint32_t s = s_fill, slot = s % kRing;
-      if (s >= (uint32_t)kRing && !tc::mbar_wait(&empty[slot], ((s / kRing) - 1) & 1, wlim)) {
-        die();
-        return;
-      }
-      mbar_expect_tx(&full[slot], kW1tSlab);
-      bulk_g2s(ring + slot * kSlotBytes, w1t + (size_t)(s % kNW1t) * kW1tSlab, kW1tSlab, &full[slot]);
-      ++s_fill;
     };
     auto chunk = [&](int q) {
       for (int kk = 0; kk < 8; ++kk) {
@@ -1105,17 +1150,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
         tc::mma_bf16(tbase + 256, da, tc::make_desc(sa + 8192, 128, 256), kIdesc256, accf);
         tc::mma_commit(&empty[slot]);
         ++s_cons;
-        while (!dead && s_fill < s_cons + kRing - 1) fill();
       }
     };
     auto go = [&]() {
       __syncwarp();
-      tc::group_barrier(kBarGo, kThreads);
+      tc::group_barrier(kBarGo, kSync);
       tc::fence_after_sync();
     };
-    if (leader)
-      for (int q = 0; q < kRing; ++q) fill();
-    __syncwarp();
     for (int step = 0; step < N; ++step) {
       go();                            // dh' of the previous step read, chunks 0-3 written
       if (leader) {
@@ -1125,19 +1166,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
         chunk(2);
         chunk(3);
         tc::mma_commit(done);
-        while (!dead && s_fill < s_cons + kRing) fill();
       }
       go();                            // chunks 4, 5 written
       if (leader) {
         chunk(4);
         chunk(5);
         tc::mma_commit(done);          // dh' complete
-        while (!dead && s_fill < s_cons + kRing) fill();
       }
       __syncwarp();
     }
-    if (leader)
-      for (uint32_t s = s_cons; s < s_fill; ++s) tc::mbar_wait(&full[s % kRing], (s / kRing) & 1, kWait2);
+    if (leader) {
+      *s_consf = s_cons;
+      __threadfence_block();
+      *s_stop = 1;
+    }
     __syncwarp();
   } else {
     // ======================== worker warps ========================
@@ -1160,7 +1202,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
     auto to_issuer = [&]() {
       tc::fence_async_smem();
       tc::fence_before_sync();
-      tc::group_arrive(kBarGo, kThreads);
+      tc::group_arrive(kBarGo, kSync);
     };
     auto slot_row = [&](int slot, int col) { return sA + slot * 32768 + tc::kmajor_offset(m, col, 128); };
     for (int step = 0; step < N; ++step) {
