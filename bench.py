@@ -376,7 +376,7 @@ def run_gpu(args, w):
     r32 = measure(nqs.FP32)
     chosen, r16, check = r32, None, None
     bf16_ok = args.precision != "fp32" and not phase and (w["d"] in (16, 32, 64, 128) if w["cell"] == 1
-                                                          else (w["d"] in (32, 64) and N <= 128)
+                                                          else (w["d"] in (32, 64) and N <= 256)
                                                           or (w["d"] == 256 and N <= 256))
     if bf16_ok:
         r16 = measure(nqs.BF16)

@@ -100,13 +100,11 @@ typedef struct {
   int32_t precision;  /* NQS_FP32 | NQS_BF16: BF16 runs the 1D cell GEMMs of
                          sampling, teacher forcing, the local-energy chains and
                          the reverse sweep on the tensor cores (BF16 operands,
-                         FP32 accumulation and FP32 state; d_h in {16, 32, 64};
-                         at d_h = 128 sampling, teacher forcing and the chains,
-                         with the FP32 reverse sweep on the prefix cache),
-                         and the 2D cell and GLU GEMMs of sampling, teacher
-                         forcing, the Heisenberg chains and the reverse
-                         sweep (d_h in {32, 64}, N <= 128); other shapes
-                         return NQS_EUNSUPPORTED */
+                         FP32 accumulation and FP32 state; d_h in {16, 32, 64,
+                         128}), and the 2D cell and GLU GEMMs of sampling,
+                         teacher forcing, the Heisenberg chains and the
+                         reverse sweep (d_h in {32, 64, 256}, N <= 256); other
+                         shapes return NQS_EUNSUPPORTED */
   int32_t phase;      /* 1: complex RNN (cRNN, Sec. II and Eq. softsign): a phase
                          layer z_phi = U_phi h_n + c_phi after the amplitude head,
                          phi_n = pi Softsign(z_phi) . onehot(sigma_n), log psi =

@@ -46,8 +46,8 @@ nqs_status check_desc(const nqs_model_desc* desc, Dims* out) {
 
 // Paths built so far: FP32 1D GRU (no mask), FP32 2D GRU, the BF16
 // tensor-core 1D GRU for d_h in {16, 32, 64, 128} and the BF16 tensor-core 2D
-// GRU for d_h in {32, 64} with N <= 128 (configurations as 128-bit masks) and
-// for d_h = 256 with N <= 256.
+// GRU for d_h in {32, 64, 256} with N <= 256 (configurations as 128- or
+// 256-bit masks).
 nqs_status check_built(const Dims& d) {
   if (d.cell == NQS_GRU1D && d.sz0) return NQS_EUNSUPPORTED;
   // the cRNN phase head: FP32 1D GRU, d_h >= 16

@@ -1,6 +1,7 @@
 // BF16 tensor-core path of the 2D GRU wave function with its GLU head (App. A):
 // zig-zag sampling / teacher forcing and the prefix-cached Heisenberg chains
-// (Eq. heisenberg, Marshall-rotated, Sec. III B), for d_h in {32, 64}.
+// (Eq. heisenberg, Marshall-rotated, Sec. III B), for d_h in {32, 64} on up to
+// 256 sites (d_h = 256: tc2d_wide.cu).
 //
 // One CTA = one tile of 128 rows (= TMEM lanes), one thread per row.  Per
 // cell (position t = (i, j) of the zig-zag order, Sec. II):
@@ -86,8 +87,6 @@ __global__ void pack2d_tc_kernel(const float* __restrict__ p, uint8_t* __restric
 // Heisenberg chain jobs: the antiparallel (sample, bond) pairs in bond order
 // (bonds sorted by the earlier zig-zag position: longest chains first), with
 // each chain's start values taken from the cached-path tables.
-using Job2 = JobT<2>;
-
 __global__ void heis_count_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds, int64_t B,
                                   int N, int* __restrict__ counts) {
   __shared__ int red[32];
@@ -176,8 +175,8 @@ struct S2 {
   static constexpr int kVS = kHS + 128 * HS * 4;           // [128 x HS] f32: vertical-input copy
   static constexpr int kAux = kVS + 128 * HS * 4;          // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kCol = kAux + (D + 4) * 4;          // 128 ints: column-buffer entry of each row's new state
-  static constexpr int kPos = kCol + 128 * 4;              // 128 ints: (i, j, r) of every zig-zag position
-  static constexpr int kZx = kPos + 128 * 4;               // 512 floats: readout partials of the unit slices
+  static constexpr int kPos = kCol + 128 * 4;              // 256 ints: (i, j, r) of every zig-zag position
+  static constexpr int kZx = kPos + 256 * 4;               // 512 floats: readout partials of the unit slices
   static constexpr int kJob = kZx + 512 * 4;               // 128 long long: chain job of each row (split rows)
   static constexpr int kBar = kJob + 128 * 8;              // 3 mbarriers: MMA1, MMA2, drain
   static constexpr int kSlot = kBar + 24;
@@ -201,7 +200,7 @@ struct Tc2Args {
   float* lp_tab;             // chains: cached-path tables
   int* nup_tab;
   const int4* bonds;
-  const Job2* jobs;
+  const void* jobs;          // chains: JobT<NW> records
   const int* njobs;
   float* delta;
   unsigned long long* counter;
@@ -217,7 +216,7 @@ struct Tc2Args {
 // memory.  The readout partials of the unit slices meet in shared memory; the
 // readout sums 16-unit chunks in order and combines the chunks by a fixed
 // pairwise tree in every variant (and in the cached-path tables).
-template <int D, int MODE, int REP = 1, int SPLIT = 1>
+template <int D, int MODE, int REP = 1, int SPLIT = 1, int NW = 2>
 __global__ void __launch_bounds__(128 * SPLIT, 1)
 tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
                    Tc2Args a) {
@@ -292,7 +291,9 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   int t = 0, pa = -1, rank = 0, n_up = 0, bsa = -1, bsb = -1;   // chains: exchanged lattice sites
   float acc = 0.0f, lp_next = 0.0f;
   bool active = false;
-  uint64_t mask[2] = {0ull, 0ull};
+  uint64_t mask[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) mask[w] = 0ull;
   constexpr int HW = DU / 2;          // 32-bit words of this thread's packed BF16 units
   uint32_t hhi[HW], hlo[HW];         // the state just computed, as BF16 hi / lo pairs
 #pragma unroll
@@ -359,7 +360,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       active = false;
       return;
     }
-    const Job2 jb = a.jobs[j];
+    const JobT<NW> jb = reinterpret_cast<const JobT<NW>*>(a.jobs)[j];
     b = jb.b;
     rank = jb.rank;
     const int4 bd = a.bonds[rank];
@@ -369,8 +370,8 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     t = pa + 1;
     acc = jb.acc0;
     n_up = jb.nup0;
-    mask[0] = jb.mask[0];
-    mask[1] = jb.mask[1];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) mask[w] = jb.mask[w];
     active = true;
     plan_inputs(true);
   };
@@ -722,8 +723,8 @@ struct T2S {
   static constexpr int kW2 = 0;                            // [2D x K2] bf16
   static constexpr int kA = kW2 + 2 * D * K2 * 2;          // [128 x KA2] bf16
   static constexpr int kAux = kA + 128 * KA2 * 2;          // D + 4 floats
-  static constexpr int kPos = kAux + (D + 4) * 4;          // 128 ints: lattice site of every position
-  static constexpr int kBar = kPos + 128 * 4;              // 2 mbarriers: MMA, drain
+  static constexpr int kPos = kAux + (D + 4) * 4;          // 256 ints: lattice site of every position
+  static constexpr int kBar = kPos + 256 * 4;              // 2 mbarriers: MMA, drain
   static constexpr int kSlot = kBar + 16;
   static constexpr int kBytes = 1024 + kSlot + 16;
 };
@@ -874,16 +875,23 @@ int sm_count_2d() {
   return sms;
 }
 
-template <int D, int MODE, int REP = 1, int SPLIT = 1>
-cudaError_t launch2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
+template <int D, int MODE, int REP, int SPLIT, int NW>
+cudaError_t launch2_nw(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
   using S = S2<D>;
-  auto k = tc2d_engine_kernel<D, MODE, REP, SPLIT>;
+  auto k = tc2d_engine_kernel<D, MODE, REP, SPLIT, NW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
   const int64_t grid = MODE == 2 ? sm_count_2d() : (a.B + 128 / REP - 1) / (128 / REP);
   if (grid < 1) return cudaSuccess;
   k<<<(unsigned)grid, 128 * SPLIT, S::kBytes, st>>>(w1, w2, aux, a);
   return cudaGetLastError();
+}
+
+// configurations as 128-bit masks up to 128 sites, 256-bit masks up to 256
+template <int D, int MODE, int REP = 1, int SPLIT = 1>
+cudaError_t launch2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
+  return a.N > 128 ? launch2_nw<D, MODE, REP, SPLIT, 4>(a, w1, w2, aux, st)
+                   : launch2_nw<D, MODE, REP, SPLIT, 2>(a, w1, w2, aux, st);
 }
 
 // Sampling / teacher forcing at d_h = 64: 32-sample CTAs with replicated A
@@ -899,9 +907,8 @@ cudaError_t launch2_fwd64(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2
 }  // namespace
 
 int tc2d_supported(int D, int Lx, int N) {
-  if (D == 256) return N <= 256 && Lx >= 1;   // tc2d_wide.cu
-  if (D != 32 && D != 64) return 0;
-  return N <= 128 && Lx >= 1;
+  if (D != 32 && D != 64 && D != 256) return 0;   // d_h = 256: tc2d_wide.cu
+  return N <= 256 && Lx >= 1;
 }
 
 size_t tc2d_colbuf_floats(int64_t B, int Lx, int D) {
@@ -1014,7 +1021,7 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
   if (D == 256) return tc2dw_chains(c, wimg, jb, njobs, st);
-  Job2* jobs = reinterpret_cast<Job2*>(jb);
+  const void* jobs = jb;
   Tc2Args a{};
   a.B = c.B;
   a.Lx = c.Lx;

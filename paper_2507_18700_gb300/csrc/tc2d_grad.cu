@@ -1,6 +1,6 @@
 // BF16 tensor-core reverse sweep of the 2D GRU wave function with its GLU head
 // (App. A): d/dtheta sum_b w_b log psi_b over the zig-zag order (Sec. II),
-// with the zero-magnetisation mask, for d_h in {32, 64} and N <= 128.
+// with the zero-magnetisation mask, for d_h in {32, 64} and N <= 256.
 //
 // Phase 1a, tc2d_tape_kernel, parallel over (tile of 128 samples, position
 // t): from the cached states, everything that does not depend on the

@@ -11,6 +11,8 @@ checks the kernels at a tolerance that does not depend on that amplification.
 """
 import numpy as np
 
+from oracle import model as om
+
 
 def bf16_round(x):
     """Round float32 values to the nearest BF16 (ties to even), as float64."""
@@ -28,3 +30,12 @@ def bf16_weight_model(mod, flat):
     for k in ("U_mix", "W_1", "W_2"):
         t[k] = bf16_round(t[k])
     return mod.pack(t)
+
+
+def draw_window(mod, pf, s):
+    """Per draw (sampling order): the gap between the exact and the
+    BF16-weight models' p0 along the path, plus 1e-4 for the kernels' own
+    error against the BF16-weight model."""
+    gap = np.abs(om.run(mod, pf, sigma=s)["p0"] - om.run(mod, bf16_weight_model(mod, pf), sigma=s)["p0"])
+    order = np.array([mod.lattice_index(i, j) for (i, j) in mod.order()])
+    return gap[:, order] + 1e-4

@@ -40,6 +40,7 @@ import torch
 
 from oracle import hamiltonian as oh, model as om, philox, vmc as ov
 from paper_2507_18700_gb300 import inputs, nqs
+from _bf16 import bf16_weight_model, draw_window
 from _draws import check_draws
 
 pytestmark = pytest.mark.gpu
@@ -263,7 +264,65 @@ def test_bf16_2d_full_size_8x8_d64_b2048():
     assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
-@pytest.mark.parametrize("Lx,Ly,d", [(4, 4, 128), (16, 16, 64), (4, 4, 16), (12, 12, 32)])
+@pytest.mark.parametrize("d", [32, 64])
+def test_bf16_2d_16x16(d):
+    """256 sites at d_h 32 / 64 (256-bit configuration masks, NW = 4 engine):
+    log psi and cache against the BF16-weight model (2e-6 N, 5e-4 max |h|)
+    and the exact one (6e-4 N, 3e-2); every draw against both models
+    (windows: 1e-4, and the exact / BF16-weight p0 gap + 1e-4); per-sample
+    local energies against the FP32 path and on 2 samples the oracle; the
+    reverse sweep against the oracle's gradient.  Xavier weights without
+    noise: with noise the 16 x 16 map expands and the exact model leaves the
+    BF16 one."""
+    Lx = Ly = 16
+    desc, d32, mod, pf, p = setup(Lx, Ly, d, True, seed=9, noise=0.0)
+    sig = inputs.random_configs(6, mod.N, seed=4, sz0=True)
+    lp, hc = nqs.logpsi(desc, p, dev(sig, torch.uint8))
+    torch.cuda.synchronize()
+    ref_b = om.run(mod, bf16_weight_model(mod, pf), sigma=sig.astype(np.int64))
+    np.testing.assert_allclose(lp.cpu().numpy(), ref_b["logpsi"], atol=2e-6 * mod.N, rtol=0)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref_b["hidden"], atol=5e-4 * np.abs(ref_b["hidden"]).max(), rtol=0)
+    ref = om.run(mod, pf, sigma=sig.astype(np.int64))
+    np.testing.assert_allclose(lp.cpu().numpy(), ref["logpsi"], atol=6e-4 * mod.N, rtol=0)
+    np.testing.assert_allclose(hc.cpu().numpy(), ref["hidden"], atol=3e-2, rtol=0)
+    # sampling
+    B = 24
+    s, _, _ = nqs.sample(desc, p, B, seed=3, step=1)
+    torch.cuda.synchronize()
+    s = s.cpu().numpy().astype(np.int64)
+    assert np.all(s.sum(axis=1) == mod.N // 2)
+    u = philox.sampling_uniforms(3, 1, B, mod.N)
+    frac_b, _ = check_draws(mod, bf16_weight_model(mod, pf), s, u, 1e-4)
+    assert frac_b <= 1e-3, frac_b
+    frac, _ = check_draws(mod, pf, s, u, draw_window(mod, pf, s))
+    assert frac <= 1e-2, frac
+    # local energies
+    sm = om.sample(mod, pf, philox.sampling_uniforms(17, 0, 16, mod.N))["sigma"].astype(np.uint8)
+    sg = dev(sm, torch.uint8)
+    ws = nqs.Workspace(DEV)
+    _, hcs = nqs.logpsi(desc, p, sg, ws=ws)
+    el = nqs.local_energy(desc, p, nqs.heisenberg(), sg, hcs, ws=ws)
+    _, hc32 = nqs.logpsi(d32, p, sg)
+    el32 = nqs.local_energy(d32, p, nqs.heisenberg(), sg, hc32)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    e16, e32 = el.double().cpu().numpy(), el32.double().cpu().numpy()
+    assert abs(e16.mean() - e32.mean()) / mod.N <= 1e-4
+    assert_eloc_per_sample(e16, e32, sm, Lx, Ly, 1.0, mod.N)
+    e_ref = oh.heisenberg_local_energy(Lx, Ly, 1.0, True, sm[:2].astype(np.int64), lambda x: om.logpsi(mod, pf, x))
+    assert_eloc_per_sample(e16[:2], e_ref, sm[:2], Lx, Ly, 1.0, mod.N)
+    # reverse sweep
+    w = inputs.random_weights(6, seed=7).astype(np.float32)
+    g = nqs.logpsi_grad(desc, p, dev(sig, torch.uint8), hc, dev(w))
+    torch.cuda.synchronize()
+    g_ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    g = g.double().cpu().numpy()
+    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
+
+
+@pytest.mark.parametrize("Lx,Ly,d", [(4, 4, 128), (17, 16, 64), (4, 4, 16), (16, 17, 32)])
 def test_bf16_2d_unsupported_shapes(Lx, Ly, d):
     desc = nqs.model_desc(nqs.GRU2D, Lx, Ly, d, sz0=True, precision=nqs.BF16)
     p = torch.zeros(nqs.param_count(desc), device=DEV)

@@ -27,25 +27,13 @@ import torch
 
 from oracle import hamiltonian as oh, model as om, philox, vmc as ov
 from paper_2507_18700_gb300 import inputs, nqs
-from _bf16 import bf16_weight_model
+from _bf16 import bf16_weight_model, draw_window
 from _draws import check_draws
 from test_parity_bf16_2d import assert_eloc_per_sample, dev, sample_window, setup
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 D = 256
-
-
-def draw_window(mod, pf, s):
-    """Per draw (sampling order): the gap between the exact and the
-    BF16-weight models' p0 along the path, plus 1e-4 for the kernels' own
-    error against the BF16-weight model.  The row-growing window of the
-    d_h <= 64 tests (8e-4 (j + 1), measured at 8 x 8 on an expanding model)
-    is 100 times wider than this gap at 16 x 16 with the workload's weights
-    (at most 1.2e-4 there), and would hold 1.3 % of the draws."""
-    gap = np.abs(om.run(mod, pf, sigma=s)["p0"] - om.run(mod, bf16_weight_model(mod, pf), sigma=s)["p0"])
-    order = np.array([mod.lattice_index(i, j) for (i, j) in mod.order()])
-    return gap[:, order] + 1e-4
 
 
 @pytest.mark.parametrize("Lx,Ly,B,sz0,seed,noise", [(4, 4, 40, True, 0, 0.1), (5, 4, 130, True, 0, 0.1),
@@ -93,6 +81,10 @@ def test_wide_sampling(Lx, Ly, B, sz0, seed, noise):
     if sz0:
         assert np.all(s.sum(axis=1) == mod.N // 2)
     u = philox.sampling_uniforms(3, 1, B, mod.N)
+    # 16 x 16: the row-growing window of the d_h <= 64 tests (8e-4 (j + 1),
+    # measured at 8 x 8 on an expanding model) is 100 times wider than the
+    # exact / BF16-weight p0 gap with the workload's weights (at most 1.2e-4)
+    # and would hold 1.3 % of the draws; the window is that gap instead
     frac, _ = check_draws(mod, pf, s, u, draw_window(mod, pf, s) if mod.N > 128 else sample_window(mod))
     assert frac <= 1e-2, frac
     # every draw is the BF16-weight model's decision outside 1e-4 of its threshold
