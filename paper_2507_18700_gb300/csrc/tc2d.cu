@@ -142,12 +142,12 @@ __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restri
       const int idx = base + before + __popc(bal & ((1u << lane) - 1u));
       JobT<NW> jb;
       jb.b = (int)b;
-      jb.rank = rank;
       const int pa = bd.z;
+      jb.rank_pa_a = rank | (pa << 10) | (bd.x << 18);
       const int64_t row = b * N;
       // bond.x sits at position pa and takes the partner's spin sb
       jb.acc0 = 0.5f * (lp_tab[(row + pa) * 2 + sb] - lp_tab[(row + pa) * 2 + sa]);
-      jb.nup0 = nup_tab[row + pa] + (sb == 0 ? 1 : 0);
+      jb.nup_b = (nup_tab[row + pa] + (sb == 0 ? 1 : 0)) | (bd.y << 16);
 #pragma unroll
       for (int w = 0; w < NW; ++w) jb.mask[w] = 0ull;
       for (int k = 0; k < N; ++k) {
@@ -354,22 +354,21 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
   };
   // Chains: take job j (or go idle).
+  const unsigned long long nj = MODE == 2 ? (unsigned long long)*a.njobs : 0ull;
   auto start_job = [&](unsigned long long j) {
-    const unsigned long long nj = (unsigned long long)*a.njobs;
     if (j >= nj) {
       active = false;
       return;
     }
     const JobT<NW> jb = reinterpret_cast<const JobT<NW>*>(a.jobs)[j];
     b = jb.b;
-    rank = jb.rank;
-    const int4 bd = a.bonds[rank];
-    bsa = bd.x;
-    bsb = bd.y;
-    pa = bd.z;
+    rank = job_rank(jb.rank_pa_a);
+    pa = job_pa(jb.rank_pa_a);
+    bsa = job_site_a(jb.rank_pa_a);
+    bsb = job_site_b(jb.nup_b);
     t = pa + 1;
     acc = jb.acc0;
-    n_up = jb.nup0;
+    n_up = job_nup(jb.nup_b);
 #pragma unroll
     for (int w = 0; w < NW; ++w) mask[w] = jb.mask[w];
     active = true;

@@ -87,13 +87,22 @@ __device__ __forceinline__ void mset(uint64_t (&m)[NW], int k, int s) {
 
 // Heisenberg chain job: one antiparallel (sample, bond) pair with the start
 // values of its chain taken from the cached-path tables.
+// The bond travels in the record (no dependent load of the bond table when a
+// chain starts): rank_pa_a = rank | pa << 10 | site a << 18 (pa = the earlier
+// zig-zag position of the bond, at site a; rank < 1024, pa, a < 256 for N <=
+// 256), nup_b = nup0 | site b << 16.
 template <int NW>
 struct JobT {
-  int b, rank;
+  int b, rank_pa_a;
   float acc0;          // 1/2 [log p_pa(s_new) - log p_pa(s_old)]
-  int nup0;            // up spins before pa+1 on the exchanged configuration
+  int nup_b;           // up spins before pa+1 on the exchanged configuration | site b << 16
   uint64_t mask[NW];   // exchanged configuration, bit k = spin of lattice site k
 };
+__host__ __device__ __forceinline__ int job_rank(int rpa) { return rpa & 1023; }
+__host__ __device__ __forceinline__ int job_pa(int rpa) { return (rpa >> 10) & 255; }
+__host__ __device__ __forceinline__ int job_site_a(int rpa) { return (rpa >> 18) & 255; }
+__host__ __device__ __forceinline__ int job_nup(int nb) { return nb & 0xffff; }
+__host__ __device__ __forceinline__ int job_site_b(int nb) { return (nb >> 16) & 255; }
 static_assert(sizeof(JobT<2>) == 32 && sizeof(JobT<4>) == 48, "job records of 32 / 48 bytes");
 
 // Zero-magnetisation mask (forced outcomes have log p = 0 / -inf).

@@ -813,22 +813,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       };
 
       // Chains: take job j (or go idle).
+      const unsigned long long nj = MODE == 2 ? (unsigned long long)*a.njobs : 0ull;
       auto start_job = [&](unsigned long long j) {
-        const unsigned long long nj = (unsigned long long)*a.njobs;
         if (j >= nj) {
           active = false;
           return;
         }
         const JobT<4> jb = a.jobs[j];
         b = jb.b;
-        rank = jb.rank;
-        const int4 bd = a.bonds[rank];
-        bsa = bd.x;
-        bsb = bd.y;
-        pa = bd.z;
+        rank = job_rank(jb.rank_pa_a);
+        pa = job_pa(jb.rank_pa_a);
+        bsa = job_site_a(jb.rank_pa_a);
+        bsb = job_site_b(jb.nup_b);
         t = pa + 1;
         acc = jb.acc0;
-        n_up = jb.nup0;
+        n_up = job_nup(jb.nup_b);
 #pragma unroll
         for (int w = 0; w < 4; ++w) mask[w] = jb.mask[w];
         active = true;
