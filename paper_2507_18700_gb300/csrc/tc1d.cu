@@ -130,6 +130,14 @@ __device__ __forceinline__ float hw_tanh(float x) {
   return y;
 }
 
+// softplus(x) = max(x, 0) + log(1 + e^-|x|) with the hardware exp2 / log2
+// approximations (the argument of the log lies in (1, 2]): absolute error
+// below 1e-6, against logit errors of ~1e-3 from the BF16 operands; used for
+// the chains' log-probability differences, -log p(s | d) = softplus(-+d).
+__device__ __forceinline__ float softplus_hw(float x) {
+  return fmaxf(x, 0.0f) + __logf(1.0f + __expf(-fabsf(x)));
+}
+
 // Shared-memory carve-up (bytes from a 1024-aligned base).
 template <int D, int GROUPS, int SPLIT>
 struct Smem {
@@ -526,7 +534,7 @@ tc1d_engine_kernel(const float* __restrict__ img, const uint8_t* __restrict__ wi
     if (active && !timed_out) {
       const float d = z + dc;
       if constexpr (MODE == 2) {
-        acc += 0.5f * (log_prob(s_t, d) - log_prob(s_t, dl));
+        acc += 0.5f * (softplus_hw(s_t == 0 ? -dl : dl) - softplus_hw(s_t == 0 ? -d : d));   // log p(d) - log p(dl)
         s_in = s_t;
         if (++t == N) {
           if (part == 0) a.delta[b * N + f] = acc;
