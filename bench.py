@@ -719,40 +719,53 @@ def run_eval(args, w):
 
 
 def run_chain_variants(args, w):
-    """Diagnostic: the 1D BF16 chain kernel in each tile variant (one and two
-    threads per row), pinned with the autotuner off, on one sampled batch:
-    prints per-variant CUDA-event times of the local-energy call (median of
-    --steps after --warmup) and the MUFU tanh rate they imply.  Under ncu each
-    variant's chain launch is the only launch of its template instance."""
+    """Diagnostic: the BF16 chain kernel in each tile variant, pinned with the
+    autotuner off, on one sampled batch: prints per-variant CUDA-event times of
+    the local-energy call (median of --steps after --warmup).  1D TFIM: one and
+    two threads per row (with the MUFU tanh rate they imply); 2D Heisenberg:
+    the default two-tile chain kernel, the one-tile engine with one thread per
+    row and with split rows (bitwise the same energies, checked here).  Under
+    ncu each variant's chain launch is the only launch of its template
+    instance."""
     import numpy as np
     import torch
     from paper_2507_18700_gb300 import inputs, nqs
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    B, N, d = args.batch or w["B"], w["Lx"], w["d"]
-    p = torch.tensor(inputs.xavier_params(1, d, seed=w["seed"], noise_std=w["noise"]).astype(np.float32), device=dev)
-    desc = nqs.model_desc(1, N, 1, d, precision=nqs.BF16)
+    B, d = args.batch or w["B"], w["d"]
+    two = w["cell"] == 2
+    N = w["Lx"] * w["Ly"]
+    p = torch.tensor(inputs.xavier_params(w["cell"], d, seed=w["seed"], noise_std=w["noise"]).astype(np.float32),
+                     device=dev)
+    desc = nqs.model_desc(w["cell"], w["Lx"], w["Ly"], d, sz0=w["sz0"], precision=nqs.BF16)
+    ham = nqs.heisenberg(w["J"]) if two else nqs.tfim(w["J"], w["Gamma"])
     nqs.set_autotune(False)
     s, _, hc = nqs.sample(desc, p, B, seed=1, step=0)
     ws = nqs.Workspace(dev)
-    out = {}
-    for v in (0, 1):
+    out, res = {}, []
+    variants = ((None, "two_tiles"), (0, "one_tile"), (1, "one_tile_split_rows")) if two else \
+        ((0, "threads_per_row_1"), (1, "threads_per_row_2"))
+    for v, name in variants:
         nqs.set_tile_variant(v)
         ts = []
         for k in range(args.warmup + args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            nqs.local_energy(desc, p, nqs.tfim(w["J"], w["Gamma"]), s, hc, ws=ws)
+            e = nqs.local_energy(desc, p, ham, s, hc, ws=ws)
             b.record()
             torch.cuda.synchronize()
             if k >= args.warmup:
                 ts.append(a.elapsed_time(b))
+        res.append(e.clone())
         ms = float(np.median(ts))
-        out["threads_per_row_%d" % (v + 1)] = {
-            "ms": ms, "tanh_per_clock_per_sm": 3 * d * B * N * (N - 1) / 2 / (ms * 1e-3 * 2.07e9 * 152)}
+        out[name] = {"ms": ms}
+        if not two:
+            out[name]["tanh_per_clock_per_sm"] = 3 * d * B * N * (N - 1) / 2 / (ms * 1e-3 * 2.07e9 * 152)
     nqs.set_tile_variant(None)
     nqs.set_autotune(True)
-    print(json.dumps({"probe": "chain-variants", "workload": w["name"], "batch": B, "variants": out}))
+    line = {"probe": "chain-variants", "workload": w["name"], "batch": B, "variants": out,
+            "bitwise_equal": all(bool(torch.equal(res[0], r)) for r in res[1:]), "device_status": ws.status()}
+    print(json.dumps(line))
 
 
 def run_ckpt_probe(args, w):

@@ -861,6 +861,383 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
   if (threadIdx.x < 32) tc::tmem_dealloc(tbase, 128);
 }
 
+// ----------------------------------------------------------------------------
+// Heisenberg chains with two 128-row tiles per CTA (the default chain kernel
+// at d_h <= 64).  With one tile per CTA most of a cell step is the serial
+// work of the tile's rows (A rows, epilogues, row logic), during which the
+// tensor pipe idles, and the MMAs wait for that work in turn.  Here warps 0-3
+// run tile 0 and warps 4-7 tile 1, each tile with its own A operand, TMEM
+// columns, mbarriers, named barriers and MMA-issuing thread, over the same
+// shared weights and the same job queue: one tile's MMAs and loads proceed
+// while the other works through its epilogues.  The arithmetic is the
+// engine's, in the same order (bitwise the same energies).  To fit two A
+// operands beside the weights there are no FP32 staging rows: a cached state
+// is copied by cp.async into the hi / lo slots of its own half of the row's A
+// operand and split there in place, and a row's new state goes to its
+// column-buffer entry by direct stores.
+// ----------------------------------------------------------------------------
+template <int D>
+struct S2P {
+  static constexpr int K1 = 2 * D + 16, K2 = D + 16;
+  static constexpr int KA1 = K1 + 2 * D, KA2 = K2 + D;     // A operand columns: [hi | extras | lo]
+  static constexpr int kW1 = 0;                            // [3D x K1] bf16
+  static constexpr int kW2 = kW1 + 3 * D * K1 * 2;         // [2D x K2] bf16
+  static constexpr int kA = kW2 + 2 * D * K2 * 2;          // 2 tiles x A1 [128 x KA1] bf16 (A2 aliases A1)
+  static constexpr int kAux = kA + 2 * 128 * KA1 * 2;      // D + 4 floats: U_0 - U_1, c_0 - c_1
+  static constexpr int kPos = kAux + (D + 4) * 4;          // 256 ints: (i, j, r) of every zig-zag position
+  static constexpr int kBar = kPos + 256 * 4;              // per tile: MMA1, MMA2, drain
+  static constexpr int kSlot = kBar + 6 * 8;
+  static constexpr int kBytes = 1024 + kSlot + 16;
+  static_assert(kBytes <= 227 * 1024, "shared memory budget");
+  static constexpr uint32_t kTileCols = 3 * D <= 128 ? 128 : 256;   // a tile's accumulators [0, 3D)
+  static constexpr uint32_t kTmemCols = 2 * kTileCols;
+};
+
+template <int D, int NW>
+__global__ void __launch_bounds__(256, 1)
+tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
+                   Tc2Args a) {
+  using S = S2P<D>;
+  constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2, HW = D / 2;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
+  const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
+  uint8_t* sW1 = sm + S::kW1;
+  uint8_t* sW2 = sm + S::kW2;
+  float* sAux = reinterpret_cast<float*>(sm + S::kAux);
+  int* sPos = reinterpret_cast<int*>(sm + S::kPos);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += 256)
+    reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 256)
+    reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
+  for (int i = threadIdx.x; i < D + 1; i += 256) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += 256) {
+    const Pz p = zpos(t, a.Lx);
+    sPos[t] = p.i | (p.j << 8) | (p.r << 16);
+  }
+  tc::fence_async_smem();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 6; ++q) tc::mbar_init(&mbar[q], 1);
+    tc::mbar_fence_init();
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(tslot, S::kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const int g = threadIdx.x >> 7, m = threadIdx.x & 127, lane = threadIdx.x & 31;   // tile; row = TMEM lane
+  const bool issuer = m == 0;                              // the tile's MMA-issuing thread
+  uint8_t* sA = sm + S::kA + g * 128 * KA1 * 2;
+  const uint32_t sA_addr = tc::smem_addr(sA);
+  const uint32_t tmem0 = *tslot;
+  const uint32_t tbase = tmem0 + (uint32_t)g * S::kTileCols;
+  const uint32_t trow = tbase + ((uint32_t)(m & ~31) << 16);
+  uint64_t* mb1 = &mbar[3 * g];
+  uint64_t* mb2 = &mbar[3 * g + 1];
+  uint64_t* mdrain = &mbar[3 * g + 2];
+  const uint32_t bar_or = 1 + g, bar_sync = 3 + g;         // the tile's named barriers (128 threads each)
+  const int Lx = a.Lx, N = a.N;
+  const float dc = sAux[D];
+  float* colrow = a.colbuf + (((int64_t)blockIdx.x * 2 + g) * 128 + m) * Lx * D;   // this row's column buffer
+  auto P = [&](int t) -> Pz {        // zig-zag position t (table lookup)
+    const int v = sPos[t];
+    Pz p;
+    p.i = v & 255;
+    p.j = (v >> 8) & 255;
+    p.r = v >> 16;
+    return p;
+  };
+  auto kmo = [&](int k, int K) { return sA + tc::kmajor_offset(m, k, K); };
+
+  // row state
+  int64_t b = 0;
+  int t = 0, pa = -1, rank = 0, n_up = 0, bsa = -1, bsb = -1;   // exchanged lattice sites
+  float acc = 0.0f, lp_next = 0.0f;
+  bool active = false;
+  uint64_t mask[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) mask[w] = 0ull;
+  uint32_t hhi[HW], hlo[HW];         // the state just computed, as BF16 hi / lo pairs
+#pragma unroll
+  for (int q = 0; q < HW; ++q) hhi[q] = hlo[q] = 0u;
+  // next cell's inputs: 0 zero, 1 registers, 2 cached FP32 state in the A slots, 3 packed copy in the A slots
+  int hsrc = 0, vsrc = 0;
+
+  // The cached state of lattice site k of sample b into the hi / lo slots of
+  // half `half` of this row's A1 operand: floats [8c, 8c + 4) to hi chunk c,
+  // [8c + 4, 8c + 8) to lo chunk c, so that splitting chunk c in place reads
+  // exactly the two slots it then writes.
+  auto fetch_orig = [&](int half, int k) {
+    const float* src = a.hcache + (b * N + k) * D;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      cp_async16_cg(kmo(half * D + 8 * c, KA1), src + 8 * c);
+      cp_async16_cg(kmo(K1 + half * D + 8 * c, KA1), src + 8 * c + 4);
+    }
+  };
+  // Inputs of the cell at position t (after the row moved there).
+  auto plan_inputs = [&](bool fresh) {
+    const Pz p = P(t);
+    hsrc = 0;
+    vsrc = 0;
+    bool copies = false;
+    if (p.r > 0) {
+      if (fresh) {              // chain start: the state at position pa is the original
+        fetch_orig(0, p.j * Lx + zhor(p));
+        hsrc = 2;
+        copies = true;
+      } else {
+        hsrc = 1;
+      }
+    }
+    if (p.j > 0) {
+      const int q = zsnake(p.i, p.j - 1, Lx);
+      if (!fresh && q == t - 1) {
+        vsrc = 1;               // the state just computed (first cell of a row)
+      } else if (q <= pa) {
+        fetch_orig(1, (p.j - 1) * Lx + p.i);
+        vsrc = 2;
+        copies = true;
+      } else {
+        // recomputed by this row (at least two cells back): its packed hi / lo
+        // words go straight into the vertical-input columns
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(colrow + p.i * D);
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) {
+          cp_async16_cg(kmo(D + 8 * c, KA1), src + 16 * c);
+          cp_async16_cg(kmo(K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
+        }
+        vsrc = 3;
+        copies = true;
+      }
+    }
+    if (copies) cp_commit_2d();
+    const int k = p.j * Lx + p.i;
+    const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
+    lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
+  };
+  // Take job j (or go idle).
+  const unsigned long long nj = (unsigned long long)*a.njobs;
+  auto start_job = [&](unsigned long long j) {
+    if (j >= nj) {
+      active = false;
+      return;
+    }
+    const JobT<NW> jb = reinterpret_cast<const JobT<NW>*>(a.jobs)[j];
+    b = jb.b;
+    rank = job_rank(jb.rank_pa_a);
+    pa = job_pa(jb.rank_pa_a);
+    bsa = job_site_a(jb.rank_pa_a);
+    bsb = job_site_b(jb.nup_b);
+    t = pa + 1;
+    acc = jb.acc0;
+    n_up = job_nup(jb.nup_b);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) mask[w] = jb.mask[w];
+    active = true;
+    plan_inputs(true);
+  };
+  // warp-aggregated pull of one job for every lane with `need`, in two halves
+  // called by all lanes (the atomic's round trip overlaps the step)
+  unsigned pbal = 0;
+  unsigned long long pbase = 0;
+  auto pull_issue = [&](bool need) {
+    pbal = __ballot_sync(0xffffffffu, need);
+    if (pbal && lane == __ffs(pbal) - 1) pbase = atomicAdd(a.counter, (unsigned long long)__popc(pbal));
+  };
+  auto pull_take = [&]() -> unsigned long long {
+    if (!pbal) return ~0ull;
+    const unsigned long long base = __shfl_sync(0xffffffffu, pbase, __ffs(pbal) - 1);
+    return (pbal >> lane) & 1u ? base + __popc(pbal & ((1u << lane) - 1u)) : ~0ull;
+  };
+  pull_issue(true);
+  start_job(pull_take());
+
+  uint32_t ph0 = 0, ph1 = 0;
+  bool timed_out = false;
+  const uint32_t one = 0x3F80u;
+  for (;;) {
+    // ---- (a) A1 row ----
+    cp_wait_2d();
+    int s_h = -1, s_v = -1;
+    if (active) {
+      const Pz p = P(t);
+      if (p.r > 0) s_h = mbit(mask, p.j * Lx + zhor(p));
+      if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
+    }
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
+      uint8_t* dhi = kmo(half * D, KA1);
+      uint8_t* dlo = kmo(K1 + half * D, KA1);
+      if (src == 2) {
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) {
+          const float4 f0 = *reinterpret_cast<const float4*>(dhi + 128 * c);
+          const float4 f1 = *reinterpret_cast<const float4*>(dlo + 128 * c);
+          const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+          st_split8(dhi + 128 * c, dlo + 128 * c, v);
+        }
+      } else if (src != 3) {
+        const bool rg = src == 1;
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) {
+          *reinterpret_cast<uint4*>(dhi + 128 * c) =
+              rg ? make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(dlo + 128 * c) =
+              rg ? make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+    }
+    {
+      const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
+      const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
+      *reinterpret_cast<uint4*>(kmo(2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
+      *reinterpret_cast<uint4*>(kmo(2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
+    }
+    // a row on its last cell pulls its successor now (the loads land during the step)
+    pull_issue(active && !timed_out && t == N - 1);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    const bool any = tc::group_barrier_or(active && !timed_out, bar_or, 128);
+    if (!any) break;
+    tc::fence_after_sync();
+    // ---- (b) MMA1 ----
+    if (issuer) {
+      // A column chunk c pairs with W1 chunk c (hi and extras) or c - K1/16 (lo)
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, 3 * D);
+#pragma unroll
+      for (int c = 0; c < KA1 / 16; ++c) {
+        const int kb = c < K1 / 16 ? c : c - K1 / 16;
+        const uint64_t da = tc::make_desc(sA_addr + c * 256, 128, (KA1 / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sW1) + kb * 256, 128, (K1 / 8) * 128);
+        tc::mma_bf16(tbase, da, db, idesc, c > 0);
+      }
+      tc::mma_commit(mb1);
+    }
+    if (!tc::mbar_wait(mb1, ph0, wlim)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph0 ^= 1;
+    tc::fence_after_sync();
+    // ---- (c) epilogue 1: the cell ----
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t aw[8], ag[8], au[8];
+      tld8(trow + 8 * c, aw);
+      tld8(trow + D + 8 * c, ag);
+      tld8(trow + 2 * D + 8 * c, au);
+      tc::tmem_wait_ld();
+      tie(aw);
+      tie(ag);
+      tie(au);
+      float h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float cc = hw_tanh2(__uint_as_float(aw[q]));
+        const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q])), 0.5f);
+        const float mix = __uint_as_float(au[q]);
+        h[q] = fmaf(ug, cc - mix, mix);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) split_bf16(h[2 * q], h[2 * q + 1], hhi[4 * c + q], hlo[4 * c + q]);
+    }
+    // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1: MMA1 has completed)
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      *reinterpret_cast<uint4*>(kmo(8 * c, KA2)) = make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
+      *reinterpret_cast<uint4*>(kmo(K2 + 8 * c, KA2)) =
+          make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
+    }
+    *reinterpret_cast<uint4*>(kmo(D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(kmo(D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    tc::group_barrier(bar_sync, 128);
+    tc::fence_after_sync();
+    // ---- (d) MMA2 (the GLU) ----
+    if (issuer) {
+      constexpr uint32_t idesc = tc::make_idesc_bf16(128, 2 * D);
+#pragma unroll
+      for (int c = 0; c < KA2 / 16; ++c) {
+        const int kb = c < K2 / 16 ? c : c - K2 / 16;
+        const uint64_t da = tc::make_desc(sA_addr + c * 256, 128, (KA2 / 8) * 128);
+        const uint64_t db = tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128);
+        tc::mma_bf16(tbase, da, db, idesc, c > 0);
+      }
+      tc::mma_commit(mb2);
+    }
+    // this state, packed [hi words (D / 2) | lo words (D / 2)], to the row's
+    // column-buffer entry of its lattice column (read back, if at all, by this
+    // thread's own copies at a later step)
+    if (active) {
+      float* e = colrow + P(t).i * D;
+#pragma unroll
+      for (int q = 0; q < HW / 4; ++q) {
+        reinterpret_cast<uint4*>(e)[q] = make_uint4(hhi[4 * q], hhi[4 * q + 1], hhi[4 * q + 2], hhi[4 * q + 3]);
+        reinterpret_cast<uint4*>(e + D / 2)[q] = make_uint4(hlo[4 * q], hlo[4 * q + 1], hlo[4 * q + 2], hlo[4 * q + 3]);
+      }
+    }
+    if (!tc::mbar_wait(mb2, ph1, wlim)) {
+      timed_out = true;
+      flag_status(a.hdr, NQS_ETIMEOUT);
+    }
+    ph1 ^= 1;
+    tc::fence_after_sync();
+    // ---- (e) epilogue 2: GLU and the logit difference (16-unit chunks in
+    // order, chunks by a fixed pairwise tree) ----
+    float zc[D / 16];
+#pragma unroll
+    for (int c = 0; c < D / 16; ++c) zc[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D / 8; ++c) {
+      uint32_t a1[8], a2[8];
+      tld8(trow + 8 * c, a1);
+      tld8(trow + D + 8 * c, a2);
+      tc::tmem_wait_ld();
+      tie(a1);
+      tie(a2);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
+        zc[c / 2] = fmaf(sAux[8 * c + q], y, zc[c / 2]);
+      }
+    }
+#pragma unroll
+    for (int w = 1; w < D / 16; w *= 2)
+#pragma unroll
+      for (int c = 0; c + w < D / 16; c += 2 * w) zc[c] += zc[c + w];
+    const float z = zc[0];
+    // ---- (f) row logic ----
+    bool fin = false;
+    if (active && !timed_out) {
+      const float d = z + dc;
+      const Pz p = P(t);
+      const int s = mbit(mask, p.j * Lx + p.i);
+      const float lp = lp_masked(s, d, n_up, t, N, a.sz0 != 0);
+      acc += 0.5f * (lp - lp_next);
+      n_up += (s == 0);
+      if (++t == N) {
+        fin = true;
+        a.delta[(int64_t)b * a.nb + rank] = acc;
+      } else {
+        plan_inputs(false);
+      }
+    }
+    const unsigned long long jn = pull_take();
+    if (fin) start_job(jn);
+  }
+  cp_wait_2d();
+  tc::fence_before_sync();
+  // after a wait that gave up, TMEM is freed only once both tiles' MMAs have drained
+  if (__syncthreads_or(timed_out) && issuer) tc::drain_mmas(mdrain, kWait2);
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem0, S::kTmemCols);
+}
+
 int sm_count_2d() {
   static int sms = 0;
   if (!sms) {
@@ -903,6 +1280,16 @@ cudaError_t launch2_fwd64(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2
   return launch2<64, MODE, 1>(a, w1, w2, aux, st);
 }
 
+// Chains on two 128-row tiles per CTA, one CTA per SM.
+template <int D>
+cudaError_t launch_chain2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
+  auto k = a.N > 128 ? tc2d_chain2_kernel<D, 4> : tc2d_chain2_kernel<D, 2>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S2P<D>::kBytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  k<<<(unsigned)sm_count_2d(), 256, S2P<D>::kBytes, st>>>(w1, w2, aux, a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int tc2d_supported(int D, int Lx, int N) {
@@ -911,7 +1298,7 @@ int tc2d_supported(int D, int Lx, int N) {
 }
 
 size_t tc2d_colbuf_floats(int64_t B, int Lx, int D) {
-  const int64_t rows_fwd = (B + 127) / 128 * 128, rows_chain = (int64_t)sm_count_2d() * 128;
+  const int64_t rows_fwd = (B + 127) / 128 * 128, rows_chain = (int64_t)sm_count_2d() * 256;
   return (size_t)(rows_fwd > rows_chain ? rows_fwd : rows_chain) * Lx * D;
 }
 
@@ -1039,16 +1426,18 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   const uint8_t* w1 = wimg;
   const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
   const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
+  // default: two 128-row tiles per CTA, one thread per row.  Pinned tile
+  // variants select the one-tile engine: 0 with one thread per row, >= 1 with
+  // 16 units per thread (2 threads per row at d_h = 32, 4 at 64).  All three
+  // give bitwise the same energies.
+  const int pin = tc1d_pinned_variant();
   switch (D) {
-    // one thread per row (measured faster at 8 x 8, d_h = 64: 1.19 ms per
-    // launch against 1.33 ms with four threads per row, whose extra barriers
-    // and job publishing outweigh the shorter epilogues); a pinned tile
-    // variant >= 1 selects 16 units per thread (2 threads per row at d_h =
-    // 32, 4 at 64)
     case 32:
-      return tc1d_pinned_variant() >= 1 ? launch2<32, 2, 1, 2>(a, w1, w2, aux, st) : launch2<32, 2>(a, w1, w2, aux, st);
+      if (pin < 0) return launch_chain2<32>(a, w1, w2, aux, st);
+      return pin >= 1 ? launch2<32, 2, 1, 2>(a, w1, w2, aux, st) : launch2<32, 2>(a, w1, w2, aux, st);
     case 64:
-      return tc1d_pinned_variant() >= 1 ? launch2<64, 2, 1, 4>(a, w1, w2, aux, st) : launch2<64, 2>(a, w1, w2, aux, st);
+      if (pin < 0) return launch_chain2<64>(a, w1, w2, aux, st);
+      return pin >= 1 ? launch2<64, 2, 1, 4>(a, w1, w2, aux, st) : launch2<64, 2>(a, w1, w2, aux, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -181,24 +181,29 @@ def test_bf16_2d_forward_tile_rows_agree(Lx, Ly, B):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 90), (8, 8, 64, 70)])
+@pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 90), (8, 8, 64, 70), (8, 8, 64, 1500), (6, 6, 32, 2000),
+                                        (16, 16, 64, 40)])
 def test_bf16_2d_chains_split_rows_agree(Lx, Ly, d, B):
-    """The Heisenberg chains with one thread per row (variant 0) and with the
-    units of a row split over several warps (variant 1; part 0 pulls the jobs
-    and publishes them) give bitwise the same local energies."""
-    desc, _, mod, pf, p = setup(Lx, Ly, d, True, seed=13)
+    """The Heisenberg chains on two 128-row tiles per CTA (the default), on one
+    tile with one thread per row (variant 0) and on one tile with the units of
+    a row split over several warps (variant 1; part 0 pulls the jobs and
+    publishes them) give bitwise the same local energies.  The larger batches
+    hold more chain jobs than the grid has rows, so rows take several jobs from
+    the queue; 16 x 16 runs on 256-bit configuration masks."""
+    desc, _, mod, pf, p = setup(Lx, Ly, d, True, seed=13, noise=0.0 if Lx * Ly > 128 else 0.1)
     sg = dev(inputs.random_configs(B, mod.N, seed=14, sz0=True), torch.uint8)
     ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
     out = []
-    for v in (0, 1):
+    for v in (None, 0, 1):
         nqs.set_tile_variant(v)
-        _, hc = nqs.logpsi(desc, p, sg, ws=ws)
         out.append(nqs.local_energy(desc, p, nqs.heisenberg(), sg, hc, ws=ws).clone())
     nqs.set_tile_variant(None)
     torch.cuda.synchronize()
     assert ws.status() == 0
     assert torch.isfinite(out[0]).all()
     assert torch.equal(out[0], out[1])
+    assert torch.equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 300), (6, 4, 64, 200)])
