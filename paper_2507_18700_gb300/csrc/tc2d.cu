@@ -882,7 +882,10 @@ struct S2P {
   static constexpr int KA1 = K1 + 2 * D, KA2 = K2 + D;     // A operand columns: [hi | extras | lo]
   static constexpr int kW1 = 0;                            // [3D x K1] bf16
   static constexpr int kW2 = kW1 + 3 * D * K1 * 2;         // [2D x K2] bf16
-  static constexpr int kA = kW2 + 2 * D * K2 * 2;          // 2 tiles x A1 [128 x KA1] bf16 (A2 aliases A1)
+  // 2 tiles x A1 [128 x KA1] bf16; A2 [128 x KA2] aliases A1 with A1's row-group
+  // stride, so that every warp's rows lie in one region of their own in both
+  // (a warp reads its rows' A2 slots while other warps already write A1)
+  static constexpr int kA = kW2 + 2 * D * K2 * 2;
   static constexpr int kAux = kA + 2 * 128 * KA1 * 2;      // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kPos = kAux + (D + 4) * 4;          // 256 ints: (i, j, r) of every zig-zag position
   static constexpr int kBar = kPos + 256 * 4;              // per tile: MMA1, MMA2, drain
@@ -949,6 +952,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     return p;
   };
   auto kmo = [&](int k, int K) { return sA + tc::kmajor_offset(m, k, K); };
+  const int mw = m & ~31;            // the warp's first row
 
   // row state
   int64_t b = 0;
@@ -963,30 +967,53 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   for (int q = 0; q < HW; ++q) hhi[q] = hlo[q] = 0u;
   // next cell's inputs: 0 zero, 1 registers, 2 cached FP32 state in the A slots, 3 packed copy in the A slots
   int hsrc = 0, vsrc = 0;
-
-  // The cached state of lattice site k of sample b into the hi / lo slots of
-  // half `half` of this row's A1 operand: floats [8c, 8c + 4) to hi chunk c,
-  // [8c + 4, 8c + 8) to lo chunk c, so that splitting chunk c in place reads
-  // exactly the two slots it then writes.
-  auto fetch_orig = [&](int half, int k) {
-    const float* src = a.hcache + (b * N + k) * D;
+  // The copies a row needs for its next cell, as source address | kind
+  // (sources are 128-byte aligned): ldh the horizontal input (kind 2 only),
+  // ldv the vertical one (kind 2 or 3).  Kind 2: a cached FP32 state (D
+  // floats) into the hi / lo slots of its half of the A1 operand, floats [8c,
+  // 8c + 4) to hi chunk c and [8c + 4, 8c + 8) to lo chunk c, so that
+  // splitting chunk c in place reads exactly the two slots it then writes.
+  // Kind 3: a packed column-buffer entry [hi words | lo words] into the
+  // vertical hi and lo columns.
+  uint64_t ldh = 0, ldv = 0;
+  // The warp issues all its rows' copies together: one instruction covers 8
+  // rows x 4 consecutive 16-byte pieces, so its global side touches 8 lines
+  // (64 contiguous bytes per row) rather than 32, and its shared side the 8
+  // rows' distinct bank groups.
+  auto issue_slot = [&](uint64_t mine, int half) {
+    if (!__any_sync(0xffffffffu, mine != 0)) return;
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      cp_async16_cg(kmo(half * D + 8 * c, KA1), src + 8 * c);
-      cp_async16_cg(kmo(K1 + half * D + 8 * c, KA1), src + 8 * c + 4);
+    for (int q = 0; q < 4; ++q) {
+      const int i = 8 * q + (lane & 7);
+      const uint64_t u = __shfl_sync(0xffffffffu, mine, i);
+      if (u) {
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(u & ~(uint64_t)15);
+        const bool packed = (u & 15) == 3;
+#pragma unroll
+        for (int kk = 0; kk < D / 16; ++kk) {
+          const int pc = 4 * kk + (lane >> 3);      // 16-byte piece of the source
+          const int col = packed ? (pc < D / 8 ? D + 8 * pc : K1 + D + 8 * (pc - D / 8))
+                                 : ((pc & 1) ? K1 : 0) + half * D + 8 * (pc >> 1);
+          cp_async16_cg(sA + tc::kmajor_offset(mw + i, col, KA1), src + 16 * pc);
+        }
+      }
     }
+  };
+  auto issue_copies = [&]() {
+    issue_slot(ldh, 0);
+    issue_slot(ldv, 1);
+    cp_commit_2d();
+    ldh = ldv = 0;
   };
   // Inputs of the cell at position t (after the row moved there).
   auto plan_inputs = [&](bool fresh) {
     const Pz p = P(t);
     hsrc = 0;
     vsrc = 0;
-    bool copies = false;
     if (p.r > 0) {
       if (fresh) {              // chain start: the state at position pa is the original
-        fetch_orig(0, p.j * Lx + zhor(p));
+        ldh = reinterpret_cast<uint64_t>(a.hcache + (b * N + p.j * Lx + zhor(p)) * D) | 2u;
         hsrc = 2;
-        copies = true;
       } else {
         hsrc = 1;
       }
@@ -996,23 +1023,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       if (!fresh && q == t - 1) {
         vsrc = 1;               // the state just computed (first cell of a row)
       } else if (q <= pa) {
-        fetch_orig(1, (p.j - 1) * Lx + p.i);
+        ldv = reinterpret_cast<uint64_t>(a.hcache + (b * N + (p.j - 1) * Lx + p.i) * D) | 2u;
         vsrc = 2;
-        copies = true;
       } else {
         // recomputed by this row (at least two cells back): its packed hi / lo
         // words go straight into the vertical-input columns
-        const uint8_t* src = reinterpret_cast<const uint8_t*>(colrow + p.i * D);
-#pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
-          cp_async16_cg(kmo(D + 8 * c, KA1), src + 16 * c);
-          cp_async16_cg(kmo(K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
-        }
+        ldv = reinterpret_cast<uint64_t>(colrow + p.i * D) | 3u;
         vsrc = 3;
-        copies = true;
       }
     }
-    if (copies) cp_commit_2d();
     const int k = p.j * Lx + p.i;
     const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
     lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
@@ -1053,6 +1072,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   };
   pull_issue(true);
   start_job(pull_take());
+  issue_copies();
 
   uint32_t ph0 = 0, ph1 = 0;
   bool timed_out = false;
@@ -1060,6 +1080,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   for (;;) {
     // ---- (a) A1 row ----
     cp_wait_2d();
+    __syncwarp();   // the copies into this row's slots were issued by other lanes of the warp
     int s_h = -1, s_v = -1;
     if (active) {
       const Pz p = P(t);
@@ -1144,15 +1165,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
       for (int q = 0; q < 4; ++q) split_bf16(h[2 * q], h[2 * q + 1], hhi[4 * c + q], hlo[4 * c + q]);
     }
-    // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1: MMA1 has completed)
+    // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1 with A1's stride: MMA1 has completed)
 #pragma unroll
     for (int c = 0; c < D / 8; ++c) {
-      *reinterpret_cast<uint4*>(kmo(8 * c, KA2)) = make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
-      *reinterpret_cast<uint4*>(kmo(K2 + 8 * c, KA2)) =
+      *reinterpret_cast<uint4*>(kmo(8 * c, KA1)) = make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
+      *reinterpret_cast<uint4*>(kmo(K2 + 8 * c, KA1)) =
           make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
     }
-    *reinterpret_cast<uint4*>(kmo(D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(kmo(D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(kmo(D, KA1)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(kmo(D + 8, KA1)) = make_uint4(0u, 0u, 0u, 0u);
     tc::fence_async_smem();
     tc::fence_before_sync();
     tc::group_barrier(bar_sync, 128);
@@ -1163,22 +1184,33 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
       for (int c = 0; c < KA2 / 16; ++c) {
         const int kb = c < K2 / 16 ? c : c - K2 / 16;
-        const uint64_t da = tc::make_desc(sA_addr + c * 256, 128, (KA2 / 8) * 128);
+        const uint64_t da = tc::make_desc(sA_addr + c * 256, 128, (KA1 / 8) * 128);
         const uint64_t db = tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128);
         tc::mma_bf16(tbase, da, db, idesc, c > 0);
       }
       tc::mma_commit(mb2);
     }
     // this state, packed [hi words (D / 2) | lo words (D / 2)], to the row's
-    // column-buffer entry of its lattice column (read back, if at all, by this
-    // thread's own copies at a later step)
-    if (active) {
-      float* e = colrow + P(t).i * D;
+    // column-buffer entry of its lattice column, by the warp together (8 rows
+    // x 4 pieces per instruction) from the A2 rows, which MMA2 only reads
+    {
+      const int ci_me = active ? P(t).i : -1;
+      float* cbase = a.colbuf + (((int64_t)blockIdx.x * 2 + g) * 128 + mw) * Lx * D;
 #pragma unroll
-      for (int q = 0; q < HW / 4; ++q) {
-        reinterpret_cast<uint4*>(e)[q] = make_uint4(hhi[4 * q], hhi[4 * q + 1], hhi[4 * q + 2], hhi[4 * q + 3]);
-        reinterpret_cast<uint4*>(e + D / 2)[q] = make_uint4(hlo[4 * q], hlo[4 * q + 1], hlo[4 * q + 2], hlo[4 * q + 3]);
+      for (int q = 0; q < 4; ++q) {
+        const int i = 8 * q + (lane & 7);
+        const int ci = __shfl_sync(0xffffffffu, ci_me, i);
+        if (ci >= 0) {
+          uint4* e = reinterpret_cast<uint4*>(cbase + ((int64_t)i * Lx + ci) * D);
+#pragma unroll
+          for (int kk = 0; kk < D / 16; ++kk) {
+            const int pc = 4 * kk + (lane >> 3);
+            const int col = pc < D / 8 ? 8 * pc : K2 + 8 * (pc - D / 8);
+            e[pc] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(mw + i, col, KA1));
+          }
+        }
       }
+      __syncwarp();   // these reads of other rows' A2 slots precede any later write to them
     }
     if (!tc::mbar_wait(mb2, ph1, wlim)) {
       timed_out = true;
@@ -1228,6 +1260,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     const unsigned long long jn = pull_take();
     if (fin) start_job(jn);
+    issue_copies();
   }
   cp_wait_2d();
   tc::fence_before_sync();

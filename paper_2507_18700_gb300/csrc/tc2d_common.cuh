@@ -77,12 +77,21 @@ __device__ __forceinline__ int zhor(const Pz& p) { return (p.j & 1) ? p.i + 1 : 
 __device__ __forceinline__ int zsnake(int i, int j, int Lx) { return j * Lx + ((j & 1) ? Lx - 1 - i : i); }
 
 // A configuration of up to 64 NW spins as a bit mask (bit k = spin of lattice site k).
+// The word is chosen by selects, not by a runtime index, so the mask stays in
+// registers.
 template <int NW>
-__device__ __forceinline__ int mbit(const uint64_t (&m)[NW], int k) { return (int)((m[k >> 6] >> (k & 63)) & 1ull); }
+__device__ __forceinline__ int mbit(const uint64_t (&m)[NW], int k) {
+  uint64_t w = m[0];
+#pragma unroll
+  for (int i = 1; i < NW; ++i) w = (k >> 6) == i ? m[i] : w;
+  return (int)((w >> (k & 63)) & 1ull);
+}
 template <int NW>
 __device__ __forceinline__ void mset(uint64_t (&m)[NW], int k, int s) {
   const uint64_t b = 1ull << (k & 63);
-  m[k >> 6] = s ? (m[k >> 6] | b) : (m[k >> 6] & ~b);
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    if ((k >> 6) == i) m[i] = s ? (m[i] | b) : (m[i] & ~b);
 }
 
 // Heisenberg chain job: one antiparallel (sample, bond) pair with the start
