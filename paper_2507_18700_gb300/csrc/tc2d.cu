@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(256, 1)
 tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
                    Tc2Args a) {
   using S = S2P<D>;
-  constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2, HW = D / 2;
+  constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
@@ -962,10 +962,8 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   uint64_t mask[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) mask[w] = 0ull;
-  uint32_t hhi[HW], hlo[HW];         // the state just computed, as BF16 hi / lo pairs
-#pragma unroll
-  for (int q = 0; q < HW; ++q) hhi[q] = hlo[q] = 0u;
-  // next cell's inputs: 0 zero, 1 registers, 2 cached FP32 state in the A slots, 3 packed copy in the A slots
+  // next cell's inputs: 0 zero, 1 the state just computed (in place in the
+  // horizontal slots), 2 cached FP32 state in the A slots, 3 packed copy in the A slots
   int hsrc = 0, vsrc = 0;
   // The copies a row needs for its next cell, as source address | kind
   // (sources are 128-byte aligned): ldh the horizontal input (kind 2 only),
@@ -1087,6 +1085,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       if (p.r > 0) s_h = mbit(mask, p.j * Lx + zhor(p));
       if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
     }
+    if (active && vsrc == 1) {
+      // the state just computed (hi / lo, left in the horizontal slots by
+      // the A2 row) is this first cell's vertical input
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) {
+        *reinterpret_cast<uint4*>(kmo(D + 8 * c, KA1)) = *reinterpret_cast<const uint4*>(kmo(8 * c, KA1));
+        *reinterpret_cast<uint4*>(kmo(K1 + D + 8 * c, KA1)) = *reinterpret_cast<const uint4*>(kmo(K1 + 8 * c, KA1));
+      }
+    }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
@@ -1100,14 +1107,11 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
           const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
           st_split8(dhi + 128 * c, dlo + 128 * c, v);
         }
-      } else if (src != 3) {
-        const bool rg = src == 1;
+      } else if (src == 0) {
 #pragma unroll
         for (int c = 0; c < D / 8; ++c) {
-          *reinterpret_cast<uint4*>(dhi + 128 * c) =
-              rg ? make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4*>(dlo + 128 * c) =
-              rg ? make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(dhi + 128 * c) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(dlo + 128 * c) = make_uint4(0u, 0u, 0u, 0u);
         }
       }
     }
@@ -1143,34 +1147,37 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     ph0 ^= 1;
     tc::fence_after_sync();
-    // ---- (c) epilogue 1: the cell ----
+    // ---- (c) epilogue 1: the cell, in 16-unit chunks; the A2 row [hi(h) | 1 1
+    // | 0] keeps A1's horizontal hi columns and lo(h) goes to A1's horizontal
+    // lo columns (MMA1 has completed), so that a next cell whose horizontal
+    // input is h finds it in place ----
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t aw[8], ag[8], au[8];
-      tld8(trow + 8 * c, aw);
-      tld8(trow + D + 8 * c, ag);
-      tld8(trow + 2 * D + 8 * c, au);
+    for (int c = 0; c < D / 16; ++c) {
+      uint32_t aw[16], ag[16], au[16];
+      tld16(trow + 16 * c, aw);
+      tld16(trow + D + 16 * c, ag);
+      tld16(trow + 2 * D + 16 * c, au);
       tc::tmem_wait_ld();
       tie(aw);
       tie(ag);
       tie(au);
-      float h[8];
+      float h[16];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < 16; ++q) {
         const float cc = hw_tanh2(__uint_as_float(aw[q]));
         const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q])), 0.5f);
         const float mix = __uint_as_float(au[q]);
         h[q] = fmaf(ug, cc - mix, mix);
       }
+      uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) split_bf16(h[2 * q], h[2 * q + 1], hhi[4 * c + q], hlo[4 * c + q]);
-    }
-    // A2 row [hi(h) | 1 1 | 0 | lo(h)] (aliases A1 with A1's stride: MMA1 has completed)
+      for (int q = 0; q < 8; ++q) split_bf16(h[2 * q], h[2 * q + 1], hi[q], lo[q]);
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      *reinterpret_cast<uint4*>(kmo(8 * c, KA1)) = make_uint4(hhi[4 * c], hhi[4 * c + 1], hhi[4 * c + 2], hhi[4 * c + 3]);
-      *reinterpret_cast<uint4*>(kmo(K2 + 8 * c, KA1)) =
-          make_uint4(hlo[4 * c], hlo[4 * c + 1], hlo[4 * c + 2], hlo[4 * c + 3]);
+      for (int e = 0; e < 2; ++e) {
+        *reinterpret_cast<uint4*>(kmo(16 * c + 8 * e, KA1)) = make_uint4(hi[4 * e], hi[4 * e + 1], hi[4 * e + 2], hi[4 * e + 3]);
+        *reinterpret_cast<uint4*>(kmo(K1 + 16 * c + 8 * e, KA1)) =
+            make_uint4(lo[4 * e], lo[4 * e + 1], lo[4 * e + 2], lo[4 * e + 3]);
+      }
     }
     *reinterpret_cast<uint4*>(kmo(D, KA1)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(kmo(D + 8, KA1)) = make_uint4(0u, 0u, 0u, 0u);
@@ -1183,8 +1190,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       constexpr uint32_t idesc = tc::make_idesc_bf16(128, 2 * D);
 #pragma unroll
       for (int c = 0; c < KA2 / 16; ++c) {
+        // A chunks: hi(h) and the extras, then lo(h) from the horizontal lo columns
         const int kb = c < K2 / 16 ? c : c - K2 / 16;
-        const uint64_t da = tc::make_desc(sA_addr + c * 256, 128, (KA1 / 8) * 128);
+        const int ca = c < K2 / 16 ? c : K1 / 16 + kb;
+        const uint64_t da = tc::make_desc(sA_addr + ca * 256, 128, (KA1 / 8) * 128);
         const uint64_t db = tc::make_desc(tc::smem_addr(sW2) + kb * 256, 128, (K2 / 8) * 128);
         tc::mma_bf16(tbase, da, db, idesc, c > 0);
       }
@@ -1205,7 +1214,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
           for (int kk = 0; kk < D / 16; ++kk) {
             const int pc = 4 * kk + (lane >> 3);
-            const int col = pc < D / 8 ? 8 * pc : K2 + 8 * (pc - D / 8);
+            const int col = pc < D / 8 ? 8 * pc : K1 + 8 * (pc - D / 8);
             e[pc] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(mw + i, col, KA1));
           }
         }
@@ -1222,19 +1231,18 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // order, chunks by a fixed pairwise tree) ----
     float zc[D / 16];
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) zc[c] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      uint32_t a1[8], a2[8];
-      tld8(trow + 8 * c, a1);
-      tld8(trow + D + 8 * c, a2);
+    for (int c = 0; c < D / 16; ++c) {
+      uint32_t a1[16], a2[16];
+      tld16(trow + 16 * c, a1);
+      tld16(trow + D + 16 * c, a2);
       tc::tmem_wait_ld();
       tie(a1);
       tie(a2);
+      zc[c] = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < 16; ++q) {
         const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-        zc[c / 2] = fmaf(sAux[8 * c + q], y, zc[c / 2]);
+        zc[c] = fmaf(sAux[16 * c + q], y, zc[c]);
       }
     }
 #pragma unroll
