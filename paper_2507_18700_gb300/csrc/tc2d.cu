@@ -1003,9 +1003,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     cp_commit_2d();
     ldh = ldv = 0;
   };
-  // Inputs of the cell at position t (after the row moved there).
-  auto plan_inputs = [&](bool fresh) {
-    const Pz p = P(t);
+  // Inputs of the cell at position tn (the row's next cell): sources and the
+  // copies to issue; returns the cached-path log p at tn.
+  auto plan_inputs = [&](int tn, bool fresh) -> float {
+    const Pz p = P(tn);
     hsrc = 0;
     vsrc = 0;
     if (p.r > 0) {
@@ -1018,7 +1019,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     if (p.j > 0) {
       const int q = zsnake(p.i, p.j - 1, Lx);
-      if (!fresh && q == t - 1) {
+      if (!fresh && q == tn - 1) {
         vsrc = 1;               // the state just computed (first cell of a row)
       } else if (q <= pa) {
         ldv = reinterpret_cast<uint64_t>(a.hcache + (b * N + (p.j - 1) * Lx + p.i) * D) | 2u;
@@ -1032,7 +1033,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     const int k = p.j * Lx + p.i;
     const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
-    lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
+    return ldg_f32_v(a.lp_tab + (b * N + tn) * 2 + so);
   };
   // Take job j (or go idle).
   const unsigned long long nj = (unsigned long long)*a.njobs;
@@ -1053,7 +1054,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
     for (int w = 0; w < NW; ++w) mask[w] = jb.mask[w];
     active = true;
-    plan_inputs(true);
+    lp_next = plan_inputs(t, true);
   };
   // warp-aggregated pull of one job for every lane with `need`, in two halves
   // called by all lanes (the atomic's round trip overlaps the step)
@@ -1088,10 +1089,14 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     if (active && vsrc == 1) {
       // the state just computed (hi / lo, left in the horizontal slots by
       // the A2 row) is this first cell's vertical input
+      // (reads before writes throughout: interleaved, they would serialise)
 #pragma unroll
-      for (int c = 0; c < D / 8; ++c) {
-        *reinterpret_cast<uint4*>(kmo(D + 8 * c, KA1)) = *reinterpret_cast<const uint4*>(kmo(8 * c, KA1));
-        *reinterpret_cast<uint4*>(kmo(K1 + D + 8 * c, KA1)) = *reinterpret_cast<const uint4*>(kmo(K1 + 8 * c, KA1));
+      for (int lo = 0; lo < 2; ++lo) {
+        uint4 v[D / 8];
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) v[c] = *reinterpret_cast<const uint4*>(kmo(lo * K1 + 8 * c, KA1));
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) *reinterpret_cast<uint4*>(kmo(lo * K1 + D + 8 * c, KA1)) = v[c];
       }
     }
 #pragma unroll
@@ -1100,11 +1105,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       uint8_t* dhi = kmo(half * D, KA1);
       uint8_t* dlo = kmo(K1 + half * D, KA1);
       if (src == 2) {
+        float4 f0[D / 8], f1[D / 8];
 #pragma unroll
         for (int c = 0; c < D / 8; ++c) {
-          const float4 f0 = *reinterpret_cast<const float4*>(dhi + 128 * c);
-          const float4 f1 = *reinterpret_cast<const float4*>(dlo + 128 * c);
-          const float v[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+          f0[c] = *reinterpret_cast<const float4*>(dhi + 128 * c);
+          f1[c] = *reinterpret_cast<const float4*>(dlo + 128 * c);
+        }
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c) {
+          const float v[8] = {f0[c].x, f0[c].y, f0[c].z, f0[c].w, f1[c].x, f1[c].y, f1[c].z, f1[c].w};
           st_split8(dhi + 128 * c, dlo + 128 * c, v);
         }
       } else if (src == 0) {
@@ -1203,20 +1212,36 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // column-buffer entry of its lattice column, by the warp together (8 rows
     // x 4 pieces per instruction) from the A2 rows, which MMA2 only reads
     {
-      const int ci_me = active ? P(t).i : -1;
+      // all shared reads first, then all global stores (the compiler cannot
+      // tell the two apart, so interleaved they would serialise)
+      // a state is read back from the buffer only as the vertical input of the
+      // cell above it, and not at all when that cell comes right after it
+      // (the last cell of a lattice row) or does not exist (the top row)
+      int ci_me = -1;
+      if (active) {
+        const Pz p = P(t);
+        if (p.r < Lx - 1 && (p.j + 1) * Lx < N) ci_me = p.i;
+      }
       float* cbase = a.colbuf + (((int64_t)blockIdx.x * 2 + g) * 128 + mw) * Lx * D;
+      int ci[4];
+      uint4 v[4][D / 16];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = 8 * q + (lane & 7);
-        const int ci = __shfl_sync(0xffffffffu, ci_me, i);
-        if (ci >= 0) {
-          uint4* e = reinterpret_cast<uint4*>(cbase + ((int64_t)i * Lx + ci) * D);
+        ci[q] = __shfl_sync(0xffffffffu, ci_me, i);
 #pragma unroll
-          for (int kk = 0; kk < D / 16; ++kk) {
-            const int pc = 4 * kk + (lane >> 3);
-            const int col = pc < D / 8 ? 8 * pc : K1 + 8 * (pc - D / 8);
-            e[pc] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(mw + i, col, KA1));
-          }
+        for (int kk = 0; kk < D / 16; ++kk) {
+          const int pc = 4 * kk + (lane >> 3);
+          const int col = pc < D / 8 ? 8 * pc : K1 + 8 * (pc - D / 8);
+          v[q][kk] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(mw + i, col, KA1));
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (ci[q] >= 0) {
+          uint4* e = reinterpret_cast<uint4*>(cbase + ((int64_t)(8 * q + (lane & 7)) * Lx + ci[q]) * D);
+#pragma unroll
+          for (int kk = 0; kk < D / 16; ++kk) e[4 * kk + (lane >> 3)] = v[q][kk];
         }
       }
       __syncwarp();   // these reads of other rows' A2 slots precede any later write to them
@@ -1235,6 +1260,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       uint32_t a1[16], a2[16];
       tld16(trow + 16 * c, a1);
       tld16(trow + D + 16 * c, a2);
+      float u[16];   // U_0 - U_1 of these units, read while the TMEM loads are in flight
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = reinterpret_cast<const float4*>(sAux + 16 * c)[q];
+        u[4 * q] = f.x;
+        u[4 * q + 1] = f.y;
+        u[4 * q + 2] = f.z;
+        u[4 * q + 3] = f.w;
+      }
       tc::tmem_wait_ld();
       tie(a1);
       tie(a2);
@@ -1242,7 +1276,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-        zc[c] = fmaf(sAux[16 * c + q], y, zc[c]);
+        zc[c] = fmaf(u[q], y, zc[c]);
       }
     }
 #pragma unroll
@@ -1263,7 +1297,7 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         fin = true;
         a.delta[(int64_t)b * a.nb + rank] = acc;
       } else {
-        plan_inputs(false);
+        lp_next = plan_inputs(t, false);
       }
     }
     const unsigned long long jn = pull_take();
