@@ -723,8 +723,9 @@ def run_chain_variants(args, w):
     autotuner off, on one sampled batch: prints per-variant CUDA-event times of
     the local-energy call (median of --steps after --warmup).  1D TFIM: one and
     two threads per row (with the MUFU tanh rate they imply); 2D Heisenberg:
-    the default two-tile chain kernel, the one-tile engine with one thread per
-    row and with split rows (bitwise the same energies, checked here).  Under
+    the two-tile chain kernel with two and with one thread per row, the
+    one-tile engine with one thread per row and with split rows (bitwise the
+    same energies, checked here).  Under
     ncu each variant's chain launch is the only launch of its template
     instance."""
     import numpy as np
@@ -743,7 +744,8 @@ def run_chain_variants(args, w):
     s, _, hc = nqs.sample(desc, p, B, seed=1, step=0)
     ws = nqs.Workspace(dev)
     out, res = {}, []
-    variants = ((None, "two_tiles"), (0, "one_tile"), (1, "one_tile_split_rows")) if two else \
+    variants = ((None, "default"), (3, "two_tiles_two_threads_per_row"), (2, "two_tiles_one_thread_per_row"),
+                (0, "one_tile"), (1, "one_tile_split_rows")) if two else \
         ((0, "threads_per_row_1"), (1, "threads_per_row_2"))
     for v, name in variants:
         nqs.set_tile_variant(v)

@@ -888,7 +888,9 @@ struct S2P {
   static constexpr int kA = kW2 + 2 * D * K2 * 2;
   static constexpr int kAux = kA + 2 * 128 * KA1 * 2;      // D + 4 floats: U_0 - U_1, c_0 - c_1
   static constexpr int kPos = kAux + (D + 4) * 4;          // 256 ints: (i, j, r) of every zig-zag position
-  static constexpr int kBar = kPos + 256 * 4;              // per tile: MMA1, MMA2, drain
+  static constexpr int kZx = kPos + 256 * 4;               // split rows: 2 tiles x 2 parts x 128 readout partials
+  static constexpr int kJob = kZx + 2 * 2 * 128 * 4;       // split rows: 2 tiles x 128 published job ids
+  static constexpr int kBar = kJob + 2 * 128 * 8;          // per tile: MMA1, MMA2, drain
   static constexpr int kSlot = kBar + 6 * 8;
   static constexpr int kBytes = 1024 + kSlot + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory budget");
@@ -896,12 +898,15 @@ struct S2P {
   static constexpr uint32_t kTmemCols = 2 * kTileCols;
 };
 
-template <int D, int NW>
-__global__ void __launch_bounds__(256, 1)
+template <int D, int NW, int SP>
+__global__ void __launch_bounds__(256 * SP, 1)
 tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ w2img, const float* __restrict__ aux,
                    Tc2Args a) {
   using S = S2P<D>;
   constexpr int K1 = S::K1, K2 = S::K2, KA1 = S::KA1, KA2 = S::KA2;
+  static_assert(SP == 1 || SP == 2, "one or two threads per row");
+  constexpr int NT = 256 * SP, TT = 128 * SP;   // threads of the CTA, of a tile
+  constexpr int DU = D / SP;                     // hidden units per thread
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = smraw + ((1024 - (tc::smem_addr(smraw) & 1023)) & 1023);
   const uint32_t wlim = tc::g_wait_polls;   // bound of the waits that may give up
@@ -911,12 +916,12 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   int* sPos = reinterpret_cast<int*>(sm + S::kPos);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::kSlot);
-  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += 256)
+  for (int i = threadIdx.x; i < 3 * D * K1 * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sW1)[i] = reinterpret_cast<const uint4*>(w1img)[i];
-  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += 256)
+  for (int i = threadIdx.x; i < 2 * D * K2 * 2 / 16; i += NT)
     reinterpret_cast<uint4*>(sW2)[i] = reinterpret_cast<const uint4*>(w2img)[i];
-  for (int i = threadIdx.x; i < D + 1; i += 256) sAux[i] = aux[i];
-  for (int t = threadIdx.x; t < a.N; t += 256) {
+  for (int i = threadIdx.x; i < D + 1; i += NT) sAux[i] = aux[i];
+  for (int t = threadIdx.x; t < a.N; t += NT) {
     const Pz p = zpos(t, a.Lx);
     sPos[t] = p.i | (p.j << 8) | (p.r << 16);
   }
@@ -929,8 +934,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const int g = threadIdx.x >> 7, m = threadIdx.x & 127, lane = threadIdx.x & 31;   // tile; row = TMEM lane
-  const bool issuer = m == 0;                              // the tile's MMA-issuing thread
+  const int g = threadIdx.x / TT, tt = threadIdx.x % TT;   // tile, thread within the tile
+  const int part = tt >> 7, m = tt & 127, lane = threadIdx.x & 31;   // unit slice; row = TMEM lane
+  const int u0 = part * DU;                                // this thread's first unit
+  const bool issuer = tt == 0;                             // the tile's MMA-issuing thread
   uint8_t* sA = sm + S::kA + g * 128 * KA1 * 2;
   const uint32_t sA_addr = tc::smem_addr(sA);
   const uint32_t tmem0 = *tslot;
@@ -939,7 +946,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   uint64_t* mb1 = &mbar[3 * g];
   uint64_t* mb2 = &mbar[3 * g + 1];
   uint64_t* mdrain = &mbar[3 * g + 2];
-  const uint32_t bar_or = 1 + g, bar_sync = 3 + g;         // the tile's named barriers (128 threads each)
+  // the tile's named barriers (TT threads each)
+  const uint32_t bar_or = 1 + g, bar_sync = 3 + g, bar_z = 5 + g, bar_pub = 7 + g;
+  float* sZx = reinterpret_cast<float*>(sm + S::kZx) + g * 2 * 128;
+  long long* jbuf = reinterpret_cast<long long*>(sm + S::kJob) + g * 128;
   const int Lx = a.Lx, N = a.N;
   const float dc = sAux[D];
   float* colrow = a.colbuf + (((int64_t)blockIdx.x * 2 + g) * 128 + m) * Lx * D;   // this row's column buffer
@@ -988,8 +998,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         const uint8_t* src = reinterpret_cast<const uint8_t*>(u & ~(uint64_t)15);
         const bool packed = (u & 15) == 3;
 #pragma unroll
-        for (int kk = 0; kk < D / 16; ++kk) {
-          const int pc = 4 * kk + (lane >> 3);      // 16-byte piece of the source
+        for (int kk = 0; kk < DU / 16; ++kk) {
+          // 16-byte piece pc of the source, among those of this thread's units
+          const int L = 4 * kk + (lane >> 3);
+          const int pc = packed ? (L < DU / 8 ? u0 / 8 + L : D / 8 + u0 / 8 + (L - DU / 8)) : u0 / 4 + L;
           const int col = packed ? (pc < D / 8 ? D + 8 * pc : K1 + D + 8 * (pc - D / 8))
                                  : ((pc & 1) ? K1 : 0) + half * D + 8 * (pc >> 1);
           cp_async16_cg(sA + tc::kmajor_offset(mw + i, col, KA1), src + 16 * pc);
@@ -1069,8 +1081,17 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     const unsigned long long base = __shfl_sync(0xffffffffu, pbase, __ffs(pbal) - 1);
     return (pbal >> lane) & 1u ? base + __popc(pbal & ((1u << lane) - 1u)) : ~0ull;
   };
-  pull_issue(true);
-  start_job(pull_take());
+  if constexpr (SP == 1) {
+    pull_issue(true);
+    start_job(pull_take());
+  } else {
+    if (part == 0) {
+      pull_issue(true);
+      jbuf[m] = (long long)pull_take();
+    }
+    tc::group_barrier(bar_pub, TT);
+    start_job((unsigned long long)jbuf[m]);
+  }
   issue_copies();
 
   uint32_t ph0 = 0, ph1 = 0;
@@ -1092,49 +1113,49 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       // (reads before writes throughout: interleaved, they would serialise)
 #pragma unroll
       for (int lo = 0; lo < 2; ++lo) {
-        uint4 v[D / 8];
+        uint4 v[DU / 8];
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) v[c] = *reinterpret_cast<const uint4*>(kmo(lo * K1 + 8 * c, KA1));
+        for (int c = 0; c < DU / 8; ++c) v[c] = *reinterpret_cast<const uint4*>(kmo(lo * K1 + u0 + 8 * c, KA1));
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) *reinterpret_cast<uint4*>(kmo(lo * K1 + D + 8 * c, KA1)) = v[c];
+        for (int c = 0; c < DU / 8; ++c) *reinterpret_cast<uint4*>(kmo(lo * K1 + D + u0 + 8 * c, KA1)) = v[c];
       }
     }
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int src = active ? (half == 0 ? hsrc : vsrc) : 0;
-      uint8_t* dhi = kmo(half * D, KA1);
-      uint8_t* dlo = kmo(K1 + half * D, KA1);
+      uint8_t* dhi = kmo(half * D + u0, KA1);
+      uint8_t* dlo = kmo(K1 + half * D + u0, KA1);
       if (src == 2) {
-        float4 f0[D / 8], f1[D / 8];
+        float4 f0[DU / 8], f1[DU / 8];
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
+        for (int c = 0; c < DU / 8; ++c) {
           f0[c] = *reinterpret_cast<const float4*>(dhi + 128 * c);
           f1[c] = *reinterpret_cast<const float4*>(dlo + 128 * c);
         }
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
+        for (int c = 0; c < DU / 8; ++c) {
           const float v[8] = {f0[c].x, f0[c].y, f0[c].z, f0[c].w, f1[c].x, f1[c].y, f1[c].z, f1[c].w};
           st_split8(dhi + 128 * c, dlo + 128 * c, v);
         }
       } else if (src == 0) {
 #pragma unroll
-        for (int c = 0; c < D / 8; ++c) {
+        for (int c = 0; c < DU / 8; ++c) {
           *reinterpret_cast<uint4*>(dhi + 128 * c) = make_uint4(0u, 0u, 0u, 0u);
           *reinterpret_cast<uint4*>(dlo + 128 * c) = make_uint4(0u, 0u, 0u, 0u);
         }
       }
     }
-    {
+    if (part == 0) {
       const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
       const uint32_t ov = s_v < 0 ? 0u : (s_v == 0 ? one : (one << 16));
       *reinterpret_cast<uint4*>(kmo(2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
       *reinterpret_cast<uint4*>(kmo(2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
     }
     // a row on its last cell pulls its successor now (the loads land during the step)
-    pull_issue(active && !timed_out && t == N - 1);
+    if (part == 0) pull_issue(active && !timed_out && t == N - 1);
     tc::fence_async_smem();
     tc::fence_before_sync();
-    const bool any = tc::group_barrier_or(active && !timed_out, bar_or, 128);
+    const bool any = tc::group_barrier_or(active && !timed_out, bar_or, TT);
     if (!any) break;
     tc::fence_after_sync();
     // ---- (b) MMA1 ----
@@ -1161,11 +1182,11 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // lo columns (MMA1 has completed), so that a next cell whose horizontal
     // input is h finds it in place ----
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       uint32_t aw[16], ag[16], au[16];
-      tld16(trow + 16 * c, aw);
-      tld16(trow + D + 16 * c, ag);
-      tld16(trow + 2 * D + 16 * c, au);
+      tld16(trow + u0 + 16 * c, aw);
+      tld16(trow + D + u0 + 16 * c, ag);
+      tld16(trow + 2 * D + u0 + 16 * c, au);
       tc::tmem_wait_ld();
       tie(aw);
       tie(ag);
@@ -1183,16 +1204,19 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       for (int q = 0; q < 8; ++q) split_bf16(h[2 * q], h[2 * q + 1], hi[q], lo[q]);
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        *reinterpret_cast<uint4*>(kmo(16 * c + 8 * e, KA1)) = make_uint4(hi[4 * e], hi[4 * e + 1], hi[4 * e + 2], hi[4 * e + 3]);
-        *reinterpret_cast<uint4*>(kmo(K1 + 16 * c + 8 * e, KA1)) =
+        *reinterpret_cast<uint4*>(kmo(u0 + 16 * c + 8 * e, KA1)) =
+            make_uint4(hi[4 * e], hi[4 * e + 1], hi[4 * e + 2], hi[4 * e + 3]);
+        *reinterpret_cast<uint4*>(kmo(K1 + u0 + 16 * c + 8 * e, KA1)) =
             make_uint4(lo[4 * e], lo[4 * e + 1], lo[4 * e + 2], lo[4 * e + 3]);
       }
     }
-    *reinterpret_cast<uint4*>(kmo(D, KA1)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(kmo(D + 8, KA1)) = make_uint4(0u, 0u, 0u, 0u);
+    if (part == 0) {
+      *reinterpret_cast<uint4*>(kmo(D, KA1)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(kmo(D + 8, KA1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
-    tc::group_barrier(bar_sync, 128);
+    tc::group_barrier(bar_sync, TT);
     tc::fence_after_sync();
     // ---- (d) MMA2 (the GLU) ----
     if (issuer) {
@@ -1224,14 +1248,15 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
       float* cbase = a.colbuf + (((int64_t)blockIdx.x * 2 + g) * 128 + mw) * Lx * D;
       int ci[4];
-      uint4 v[4][D / 16];
+      uint4 v[4][DU / 16];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int i = 8 * q + (lane & 7);
         ci[q] = __shfl_sync(0xffffffffu, ci_me, i);
 #pragma unroll
-        for (int kk = 0; kk < D / 16; ++kk) {
-          const int pc = 4 * kk + (lane >> 3);
+        for (int kk = 0; kk < DU / 16; ++kk) {
+          const int L = 4 * kk + (lane >> 3);   // this thread's units' pieces: hi, then lo
+          const int pc = L < DU / 8 ? u0 / 8 + L : D / 8 + u0 / 8 + (L - DU / 8);
           const int col = pc < D / 8 ? 8 * pc : K1 + 8 * (pc - D / 8);
           v[q][kk] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(mw + i, col, KA1));
         }
@@ -1241,7 +1266,10 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         if (ci[q] >= 0) {
           uint4* e = reinterpret_cast<uint4*>(cbase + ((int64_t)(8 * q + (lane & 7)) * Lx + ci[q]) * D);
 #pragma unroll
-          for (int kk = 0; kk < D / 16; ++kk) e[4 * kk + (lane >> 3)] = v[q][kk];
+          for (int kk = 0; kk < DU / 16; ++kk) {
+            const int L = 4 * kk + (lane >> 3);
+            e[L < DU / 8 ? u0 / 8 + L : D / 8 + u0 / 8 + (L - DU / 8)] = v[q][kk];
+          }
         }
       }
       __syncwarp();   // these reads of other rows' A2 slots precede any later write to them
@@ -1254,16 +1282,16 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     tc::fence_after_sync();
     // ---- (e) epilogue 2: GLU and the logit difference (16-unit chunks in
     // order, chunks by a fixed pairwise tree) ----
-    float zc[D / 16];
+    float zc[DU / 16];
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
+    for (int c = 0; c < DU / 16; ++c) {
       uint32_t a1[16], a2[16];
-      tld16(trow + 16 * c, a1);
-      tld16(trow + D + 16 * c, a2);
+      tld16(trow + u0 + 16 * c, a1);
+      tld16(trow + D + u0 + 16 * c, a2);
       float u[16];   // U_0 - U_1 of these units, read while the TMEM loads are in flight
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float4 f = reinterpret_cast<const float4*>(sAux + 16 * c)[q];
+        const float4 f = reinterpret_cast<const float4*>(sAux + u0 + 16 * c)[q];
         u[4 * q] = f.x;
         u[4 * q + 1] = f.y;
         u[4 * q + 2] = f.z;
@@ -1280,10 +1308,16 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       }
     }
 #pragma unroll
-    for (int w = 1; w < D / 16; w *= 2)
+    for (int w = 1; w < DU / 16; w *= 2)
 #pragma unroll
-      for (int c = 0; c + w < D / 16; c += 2 * w) zc[c] += zc[c + w];
-    const float z = zc[0];
+      for (int c = 0; c + w < DU / 16; c += 2 * w) zc[c] += zc[c + w];
+    float z = zc[0];
+    if constexpr (SP == 2) {
+      // the two halves' sums meet at the top of the same pairwise tree
+      sZx[part * 128 + m] = z;
+      tc::group_barrier(bar_z, TT);
+      z = sZx[m] + sZx[128 + m];
+    }
     // ---- (f) row logic ----
     bool fin = false;
     if (active && !timed_out) {
@@ -1295,13 +1329,20 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       n_up += (s == 0);
       if (++t == N) {
         fin = true;
-        a.delta[(int64_t)b * a.nb + rank] = acc;
+        if (part == 0) a.delta[(int64_t)b * a.nb + rank] = acc;
       } else {
         lp_next = plan_inputs(t, false);
       }
     }
-    const unsigned long long jn = pull_take();
-    if (fin) start_job(jn);
+    if constexpr (SP == 1) {
+      const unsigned long long jn = pull_take();
+      if (fin) start_job(jn);
+    } else {
+      // part 0 pulled the row's job; both parts take it
+      if (part == 0) jbuf[m] = (long long)pull_take();
+      tc::group_barrier(bar_pub, TT);
+      if (fin) start_job((unsigned long long)jbuf[m]);
+    }
     issue_copies();
   }
   cp_wait_2d();
@@ -1355,13 +1396,13 @@ cudaError_t launch2_fwd64(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2
   return launch2<64, MODE, 1>(a, w1, w2, aux, st);
 }
 
-// Chains on two 128-row tiles per CTA, one CTA per SM.
-template <int D>
+// Chains on two 128-row tiles per CTA, one CTA per SM, SP threads per row.
+template <int D, int SP>
 cudaError_t launch_chain2(const Tc2Args& a, const uint8_t* w1, const uint8_t* w2, const float* aux, cudaStream_t st) {
-  auto k = a.N > 128 ? tc2d_chain2_kernel<D, 4> : tc2d_chain2_kernel<D, 2>;
+  auto k = a.N > 128 ? tc2d_chain2_kernel<D, 4, SP> : tc2d_chain2_kernel<D, 2, SP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, S2P<D>::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
-  k<<<(unsigned)sm_count_2d(), 256, S2P<D>::kBytes, st>>>(w1, w2, aux, a);
+  k<<<(unsigned)sm_count_2d(), 256 * SP, S2P<D>::kBytes, st>>>(w1, w2, aux, a);
   return cudaGetLastError();
 }
 
@@ -1501,17 +1542,22 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   const uint8_t* w1 = wimg;
   const uint8_t* w2 = w1 + (size_t)3 * D * (2 * D + 16) * 2;
   const float* aux = reinterpret_cast<const float*>(w2 + (size_t)2 * D * (D + 16) * 2);
-  // default: two 128-row tiles per CTA, one thread per row.  Pinned tile
-  // variants select the one-tile engine: 0 with one thread per row, >= 1 with
-  // 16 units per thread (2 threads per row at d_h = 32, 4 at 64).  All three
-  // give bitwise the same energies.
+  // default: two 128-row tiles per CTA with one thread per row (measured at 8
+  // x 8, d_h = 64, B = 2048: local energy 0.945 ms, against 1.036 ms with two
+  // threads per row, whose extra barriers outweigh the halved epilogues, and
+  // 1.29 ms on one tile).  Pinned tile variants: 0 the one-tile engine with
+  // one thread per row, 1 the one-tile engine with 16 units per thread (2
+  // threads per row at d_h = 32, 4 at 64), 2 two tiles with one thread per
+  // row, 3 two tiles with two.  All give bitwise the same energies.
   const int pin = tc1d_pinned_variant();
   switch (D) {
     case 32:
-      if (pin < 0) return launch_chain2<32>(a, w1, w2, aux, st);
+      if (pin < 0 || pin == 2) return launch_chain2<32, 1>(a, w1, w2, aux, st);
+      if (pin == 3) return launch_chain2<32, 2>(a, w1, w2, aux, st);
       return pin >= 1 ? launch2<32, 2, 1, 2>(a, w1, w2, aux, st) : launch2<32, 2>(a, w1, w2, aux, st);
     case 64:
-      if (pin < 0) return launch_chain2<64>(a, w1, w2, aux, st);
+      if (pin < 0 || pin == 2) return launch_chain2<64, 1>(a, w1, w2, aux, st);
+      if (pin == 3) return launch_chain2<64, 2>(a, w1, w2, aux, st);
       return pin >= 1 ? launch2<64, 2, 1, 4>(a, w1, w2, aux, st) : launch2<64, 2>(a, w1, w2, aux, st);
   }
   return cudaErrorInvalidValue;

@@ -184,10 +184,11 @@ def test_bf16_2d_forward_tile_rows_agree(Lx, Ly, B):
 @pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 90), (8, 8, 64, 70), (8, 8, 64, 1500), (6, 6, 32, 2000),
                                         (16, 16, 64, 40)])
 def test_bf16_2d_chains_split_rows_agree(Lx, Ly, d, B):
-    """The Heisenberg chains on two 128-row tiles per CTA (the default), on one
-    tile with one thread per row (variant 0) and on one tile with the units of
-    a row split over several warps (variant 1; part 0 pulls the jobs and
-    publishes them) give bitwise the same local energies.  The larger batches
+    """The Heisenberg chains on two 128-row tiles per CTA with one thread per
+    row (the default, variant 2) or two (variant 3), on one tile with one
+    thread per row (variant 0) and on one tile with the units of a row split
+    over several warps (variant 1); with split rows part 0 pulls the jobs and
+    publishes them.  All give bitwise the same local energies.  The larger batches
     hold more chain jobs than the grid has rows, so rows take several jobs from
     the queue; 16 x 16 runs on 256-bit configuration masks."""
     desc, _, mod, pf, p = setup(Lx, Ly, d, True, seed=13, noise=0.0 if Lx * Ly > 128 else 0.1)
@@ -195,15 +196,15 @@ def test_bf16_2d_chains_split_rows_agree(Lx, Ly, d, B):
     ws = nqs.Workspace(DEV)
     _, hc = nqs.logpsi(desc, p, sg, ws=ws)
     out = []
-    for v in (None, 0, 1):
+    for v in (None, 0, 1, 2, 3):
         nqs.set_tile_variant(v)
         out.append(nqs.local_energy(desc, p, nqs.heisenberg(), sg, hc, ws=ws).clone())
     nqs.set_tile_variant(None)
     torch.cuda.synchronize()
     assert ws.status() == 0
     assert torch.isfinite(out[0]).all()
-    assert torch.equal(out[0], out[1])
-    assert torch.equal(out[0], out[2])
+    for k in range(1, len(out)):
+        assert torch.equal(out[0], out[k]), k
 
 
 @pytest.mark.parametrize("Lx,Ly,d,B", [(4, 4, 32, 300), (6, 4, 64, 200)])
