@@ -812,6 +812,46 @@ def run_ckpt_probe(args, w):
     print(json.dumps({"probe": "ckpt", "workload": w["name"], "precision": "fp32", "batch": B, "runs": out}))
 
 
+def run_segment_probe(args, w):
+    """Diagnostic: the gradient of sum_b w_b log psi_b of the 2D GRU at d_h =
+    256 in BF16 with its reverse sweep in one pass and in passes of k
+    positions: CUDA-event times (median of --steps after --warmup) and the
+    workspace bytes of the gradient call."""
+    import numpy as np
+    import torch
+    from paper_2507_18700_gb300 import inputs, nqs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    B, d, N = args.batch or w["B"], w["d"], w["Lx"] * w["Ly"]
+    p = torch.tensor(inputs.xavier_params(2, d, seed=w["seed"], noise_std=w["noise"]).astype(np.float32), device=dev)
+    desc = nqs.model_desc(2, w["Lx"], w["Ly"], d, sz0=w["sz0"], precision=nqs.BF16)
+    sig, _, hc = nqs.sample(desc, p, B, seed=1, step=0)
+    wts = torch.tensor(inputs.random_weights(B, seed=2).astype(np.float32), device=dev)
+    out, ref = {}, None
+    for k in (0, 128, 64, 16):
+        nqs.set_sweep_segment(k)
+        ws = nqs.Workspace(dev)
+        ts = []
+        for it in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g = nqs.logpsi_grad(desc, p, sig, hc, wts, ws=ws)
+            b.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        g = g.double()
+        ref = g if ref is None else ref
+        out["one_pass" if k == 0 else "passes_of_%d" % k] = {
+            "ms": float(np.median(ts)), "workspace_bytes": nqs.workspace_bytes(desc, B, nqs.OP_LOGPSI_GRAD),
+            "rel_diff_to_one_pass": float((g - ref).norm() / ref.norm()), "status": ws.status()}
+        del ws
+        torch.cuda.empty_cache()
+    nqs.set_sweep_segment(0)
+    print(json.dumps({"probe": "sweep-segment", "workload": w["name"], "precision": "bf16", "batch": B,
+                      "cache_bytes": B * N * d * 4, "runs": out}))
+
+
 def run_batched_probe(args, w):
     """Diagnostic: the replica family's batched step on the BF16 path, eagerly
     (no graph), for launch lists: prints the median step time."""
@@ -888,7 +928,7 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16"],
                     help="auto: report BF16 when it passes the accuracy check against FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt", "batched", "step"],
+    ap.add_argument("--probe", default=None, choices=["chain-variants", "ckpt", "batched", "step", "sweep-segment"],
                     help="diagnostic run instead of the bench line")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -897,6 +937,9 @@ def main():
         return
     if args.probe == "ckpt":
         run_ckpt_probe(args, w)
+        return
+    if args.probe == "sweep-segment":
+        run_segment_probe(args, w)
         return
     if args.probe == "batched":
         run_batched_probe(args, w)

@@ -431,14 +431,29 @@ void nqs_set_autotune(int on);
  * / teacher-forcing tile writes each A row into all four lane quarters).
  * 2D (d_h 64 where noted): variant 0 selects 128-sample tiles with one
  * thread per row everywhere; any other variant selects 32-sample tiles with
- * replicated A rows for sampling / teacher forcing (d_h 64), 32-sample tiles
- * for the sequential reverse sweep, and 16 units per thread (2 or 4 threads
- * per row) for the chains.  Per-sample results (samples, log psi, cache,
+ * replicated A rows for sampling / teacher forcing (d_h 64) and 32-sample
+ * tiles for the sequential reverse sweep.  The 2D chains (d_h 32 / 64) run
+ * by default on two 128-row tiles per CTA with one thread per row; variant 0
+ * selects one tile with one thread per row, 1 one tile with 16 units per
+ * thread (2 or 4 threads per row), 2 the default, 3 two tiles with two
+ * threads per row.  Per-sample results (samples, log psi, cache,
  * local energies) are bitwise the same in every variant; the gradient, a sum
  * over samples grouped by tile, is bitwise the same for the same rows per tile
  * and equal to rounding otherwise (2D: bitwise the same).  This is for timing
  * and testing them one by one. */
 void nqs_set_tile_variant(int variant);
+
+/* Positions per pass of the reverse sweep of the 2D GRU at d_h = 256 in BF16
+ * (NQS_OP_LOGPSI_GRAD, NQS_OP_VMC_GRAD; App. A).  0 (the default) sweeps all
+ * N positions in one pass; k > 0 sweeps passes of k positions, the last pass
+ * first, with the backward carries running on from pass to pass, so that the
+ * per-cell tapes of the sweep (about 7.2 KB per sample and position) need
+ * workspace for B k cells instead of B N.  The prefix cache is still read at
+ * every position.  The gradient equals the one-pass gradient to rounding (its
+ * weight-gradient sums are grouped by pass).  nqs_workspace_bytes follows the
+ * setting, and the gradient calls check their workspace against it (set it
+ * before sizing the workspace).  Process-wide; other shapes ignore it. */
+void nqs_set_sweep_segment(int32_t positions);
 
 /* Bound, in polls, of every tensor-core wait that may give up (default 2^26
  * polls, about a second); polls < 0 restores the default.  It exists to

@@ -72,6 +72,9 @@ bool use_tc2d(const Dims& d) { return d.precision == NQS_BF16 && d.cell == NQS_G
 bool use_tc2d_grad(const Dims& d) { return use_tc2d(d) && d.d <= 64; }
 bool use_tc2dw_grad(const Dims& d) { return use_tc2d(d) && d.d == 256; }
 
+// Positions per pass of the d_h = 256 2D reverse sweep (0: one pass).
+int g_sweep_seg = 0;
+
 int n_bonds(const Dims& d) { return (d.Lx - 1) * d.Ly + d.Lx * (d.Ly - 1); }
 
 // Workspace layout: [header | packed weights | per-op buffers], 256-aligned.
@@ -130,7 +133,7 @@ Layout layout(const Dims& d, int64_t B, int op) {
       if (use_tc2dw_grad(d)) {
         L.a = take(d.P * sizeof(float));                       // the flat FP32 gradient
         L.b = take((size_t)B * sizeof(float));                 // weights
-        L.c = take(tc2dw_grad_bytes(B, d.Lx, d.N));            // tapes of the reverse sweep
+        L.c = take(tc2dw_grad_bytes(B, d.Lx, d.N, g_sweep_seg));   // tapes of the reverse sweep
         break;
       }
       if (use_tc2d_grad(d)) {
@@ -271,6 +274,7 @@ static nqs_status grad_common(const Dims& d, const Layout& L, const float* param
     g.params = params;
     g.scratch = at<uint8_t>(ws, L.c);
     g.hdr = static_cast<WsHeader*>(ws);
+    g.seg = g_sweep_seg;
     if (tc2dw_grad(g, wimg, partial, st) != cudaSuccess) return NQS_ECUDA;
     return cuda_status(reduce_partials(partial, 1, (int)d.P, grad, st));
   }
@@ -343,6 +347,8 @@ extern "C" {
 
 void nqs_set_autotune(int on) { tc1d_set_autotune(on); }
 void nqs_set_tile_variant(int variant) { tc1d_set_variant(variant); }
+
+void nqs_set_sweep_segment(int32_t positions) { g_sweep_seg = positions > 0 ? positions : 0; }
 
 size_t nqs_param_count(const nqs_model_desc* desc) {
   Dims d;

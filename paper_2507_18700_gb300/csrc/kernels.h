@@ -168,10 +168,11 @@ struct Tc2WGrad {
   const float* hcache;
   const float* weights;      // [B] w_b of sum_b w_b log psi_b
   const float* params;
-  uint8_t* scratch;          // tc2dw_grad_bytes(B, Lx, N), 256-byte aligned
+  uint8_t* scratch;          // tc2dw_grad_bytes(B, Lx, N, seg), 256-byte aligned
   WsHeader* hdr;
+  int seg;                   // positions per pass of the reverse sweep (<= 0 or >= N: one pass)
 };
-size_t tc2dw_grad_bytes(int64_t B, int Lx, int N);
+size_t tc2dw_grad_bytes(int64_t B, int Lx, int N, int seg);
 // d_h = 128 BF16 reverse sweep of the 1D GRU (tc1d_grad128.cu): tape pass,
 // sequential sweep, weight-gradient GEMMs, readout gradients; writes grad [P]
 struct Tc1WGrad {

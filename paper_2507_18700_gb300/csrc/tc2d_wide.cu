@@ -224,7 +224,9 @@ struct WArgs {
   float* delta;
   unsigned long long* counter;
   WsHeader* hdr;
-  // tape pass of the reverse sweep (MODE 4); cells c = t * Bp + b
+  // tape pass of the reverse sweep (MODE 4) over positions [t0, t1); cells
+  // c = (t - t0) * Bp + b
+  int t0, t1;
   const uint8_t* img2;       // backward image (its GLU slabs)
   const float* wts;          // [B] per-sample weights w_b of sum_b w_b log psi_b
   int64_t Bp;                // B rounded up to a whole tile of 128
@@ -526,8 +528,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
 
     if constexpr (MODE == 4) {
       // ---- tape pass of the reverse sweep: tiles of 128 samples at one position ----
-      const int nbt = (int)(a.Bp / 128);
-      const int64_t ntile = (int64_t)N * nbt, nkb = a.Bp * N / 16;
+      const int nbt = (int)(a.Bp / 128), npos = a.t1 - a.t0;
+      const int64_t ntile = (int64_t)npos * nbt, nkb = a.Bp * npos / 16;
       // an FP32 state (null: zeros) into the A operand and, if xt, its BF16
       // rounding into an operand tape of width 256
       auto stage_x = [&](const float* src, uint8_t* xt, int64_t cell) {
@@ -590,10 +592,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_kernel(const uint8_t* __res
       };
       for (int64_t tile = blockIdx.x;; tile += gridDim.x) {
         const bool has = tile < ntile;                  // the same for every row of the CTA
-        const int t = has ? (int)(tile / nbt) : 0;
+        const int t = has ? a.t0 + (int)(tile / nbt) : a.t0;
         const int64_t b = has ? (tile % nbt) * 128 + m : 0;
         const bool valid = has && b < B;                // rows past B: zeros in, zeros out
-        const int64_t cell = (int64_t)t * a.Bp + b;
+        const int64_t cell = (int64_t)(t - a.t0) * a.Bp + b;
         const Pz p = P(t);
         const float* src_h = valid && p.r > 0 ? a.hcache + (b * N + p.j * Lx + zhor(p)) * WD : nullptr;
         const float* src_v = valid && p.j > 0 ? a.hcache + (b * N + (p.j - 1) * Lx + p.i) * WD : nullptr;
@@ -1043,6 +1045,7 @@ __global__ void pack_wide_bwd_kernel(const float* __restrict__ p, uint8_t* __res
 struct SwArgs {
   int64_t B, Bp;
   int Lx, N;
+  int t0, t1;                // positions of this launch, swept t1 - 1 down to t0; cells (t - t0) * Bp + b
   const __half* tape_f;      // [cells, 3, D]
   const float* tape_dh;      // [cells, D]
   float* carry_h;            // [Bp, D] the horizontal successor's dh' share
@@ -1156,7 +1159,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
       tc::group_barrier(kBarGo, kSync);
       tc::fence_after_sync();
     };
-    for (int step = 0; step < N; ++step) {
+    for (int step = 0; step < a.t1 - a.t0; ++step) {
       go();                            // dh' of the previous step read, chunks 0-3 written
       if (leader) {
         chunk(0);
@@ -1187,7 +1190,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
     const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16);
     const int64_t b = (int64_t)blockIdx.x * 128 + m;           // rows past B carry zeros
     const int h = part >> 1, cb = 64 * (part & 1);             // this slice's chunk half and column base
-    const int64_t nkb = a.Bp * N / 16;
+    const int64_t nkb = a.Bp * (a.t1 - a.t0) / 16;
     uint32_t pd = 0;
     auto wait_done = [&]() {
       if (!tc::mbar_wait(done, pd, wlim)) {
@@ -1204,10 +1207,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc2dw_sweep_kernel(const uint8_t*
       tc::group_arrive(kBarGo, kSync);
     };
     auto slot_row = [&](int slot, int col) { return sA + slot * 32768 + tc::kmajor_offset(m, col, 128); };
-    for (int step = 0; step < N; ++step) {
-      const int t = N - 1 - step;
+    for (int step = 0; step < a.t1 - a.t0; ++step) {
+      const int t = a.t1 - 1 - step;
       const Pz p = P(t);
-      const int64_t cell = (int64_t)t * a.Bp + b;
+      const int64_t cell = (int64_t)(t - a.t0) * a.Bp + b;
       const bool has_h = t + 1 < N && P(t + 1).r > 0;         // horizontal successor in this lattice row
       const bool has_v = p.j + 1 < Ly;                        // vertical successor (i, j + 1)
       const float* ch = a.carry_h + b * WD;
@@ -1326,10 +1329,11 @@ __global__ void __launch_bounds__(288) tc2dw_readout_kernel(const __nv_bfloat16*
   part[(size_t)blockIdx.x * (WD + 1) + k] = acc;
 }
 
-// Every flat parameter (App. A layout) from the GEMM units' sums (splits in
-// order) and the readout blocks' sums.
-__global__ void tc2dw_final_kernel(const float* __restrict__ wg, int splits, const float* __restrict__ ro, int nro,
-                                   float* __restrict__ grad) {
+// Every flat parameter (App. A layout) from the GEMM units' sums (segments of
+// positions in order, splits in order within each) and the readout blocks'
+// sums.
+__global__ void tc2dw_final_kernel(const float* __restrict__ wg, int splits, int nseg, const float* __restrict__ ro,
+                                   int nro, float* __restrict__ grad) {
   constexpr int D = WD, W2c = 2 * D + 4;
   const int oWg = D * W2c, oU = 2 * D * W2c, ob = oU + 2 * D * D, obg = ob + D, oW1 = obg + D, ob1 = oW1 + D * D,
             oW2 = ob1 + D, ob2 = oW2 + D * D, oUo = ob2 + D, oc = oUo + 2 * D, P = oc + 2;
@@ -1361,7 +1365,10 @@ __global__ void tc2dw_final_kernel(const float* __restrict__ wg, int splits, con
   }
   float s = 0.0f;
   if (tile >= 0) {
-    for (int sp = 0; sp < splits; ++sp) s += wg[(((size_t)tile * splits + sp) * 128 + row) * kWgCols + col];
+    const size_t seg_stride = (size_t)kWgTiles * splits * 128 * kWgCols;
+    for (int sg = 0; sg < nseg; ++sg)
+      for (int sp = 0; sp < splits; ++sp)
+        s += wg[sg * seg_stride + (((size_t)tile * splits + sp) * 128 + row) * kWgCols + col];
   } else {                                       // U_out [2, d], c [2]
     const int k = i < oc ? (i - oUo) % D : D;
     sign = (i < oc ? (i - oUo) / D : i - oc) == 0 ? 1.0f : -1.0f;
@@ -1444,8 +1451,14 @@ struct WideGradLayout {
   size_t img2, nup, tape_f, tape_dh, g1, x1a, x1b, x1c, g2, x2a, x2c, y, gd, carry_h, carry_v, wg, ro, total;
 };
 
-WideGradLayout wide_grad_layout(int64_t B, int Lx, int N) {
-  const size_t Bp = (size_t)((B + 127) / 128 * 128), cells = Bp * (size_t)N;
+// Positions per pass of the reverse sweep: all N, or seg (> 0) at a time.
+int wide_seg_positions(int N, int seg) { return seg > 0 && seg < N ? seg : N; }
+
+// The tapes hold one pass's cells; the weight-gradient and readout partial
+// sums are kept per pass.
+WideGradLayout wide_grad_layout(int64_t B, int Lx, int N, int seg) {
+  const int S = wide_seg_positions(N, seg), nseg = (N + S - 1) / S;
+  const size_t Bp = (size_t)((B + 127) / 128 * 128), cells = Bp * (size_t)S;
   WideGradLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t at = off; off += (bytes + 255) / 256 * 256; return at; };
@@ -1464,19 +1477,20 @@ WideGradLayout wide_grad_layout(int64_t B, int Lx, int N) {
   L.gd = take(cells * 4);
   L.carry_h = take(Bp * WD * 4);
   L.carry_v = take(Bp * (size_t)Lx * WD * 4);
-  L.wg = take((size_t)kWgTiles * kWgSplits * 128 * kWgCols * 4);
-  L.ro = take((size_t)kRoBlocks * (WD + 1) * 4);
+  L.wg = take((size_t)nseg * kWgTiles * kWgSplits * 128 * kWgCols * 4);
+  L.ro = take((size_t)nseg * kRoBlocks * (WD + 1) * 4);
   L.total = off;
   return L;
 }
 }  // namespace
 
-size_t tc2dw_grad_bytes(int64_t B, int Lx, int N) { return wide_grad_layout(B, Lx, N).total; }
+size_t tc2dw_grad_bytes(int64_t B, int Lx, int N, int seg) { return wide_grad_layout(B, Lx, N, seg).total; }
 
 cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cudaStream_t st) {
-  const WideGradLayout L = wide_grad_layout(g.B, g.Lx, g.N);
+  const WideGradLayout L = wide_grad_layout(g.B, g.Lx, g.N, g.seg);
   uint8_t* w = g.scratch;
-  const int64_t Bp = (g.B + 127) / 128 * 128, cells = Bp * g.N, nkb = cells / 16;
+  const int S = wide_seg_positions(g.N, g.seg), nseg = (g.N + S - 1) / S;
+  const int64_t Bp = (g.B + 127) / 128 * 128;
   uint8_t* img2 = w + L.img2;
   cudaError_t e;
   const int nbwd = kNW1t * 512 * 16 + kNGlut * 256 * 16;
@@ -1487,7 +1501,6 @@ cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cuda
     nup_prefix_kernel<<<(unsigned)((g.B + 127) / 128), 128, 0, st>>>(g.sigma, g.B, g.Lx, g.N, nup);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // 1. tape pass
   WArgs a{};
   a.B = g.B;
   a.Lx = g.Lx;
@@ -1510,9 +1523,6 @@ cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cuda
   a.x2c = w + L.x2c;
   a.ytape = reinterpret_cast<__nv_bfloat16*>(w + L.y);
   a.gd = reinterpret_cast<float*>(w + L.gd);
-  const int64_t ntile = (int64_t)g.N * (Bp / 128);
-  if ((e = launch_w<4>(a, wimg, ntile < sm_count_w() ? ntile : sm_count_w(), st)) != cudaSuccess) return e;
-  // 2. sequential sweep
   SwArgs sw{};
   sw.B = g.B;
   sw.Bp = Bp;
@@ -1529,31 +1539,46 @@ cudaError_t tc2dw_grad(const Tc2WGrad& g, const uint8_t* wimg, float* grad, cuda
     cudaGetLastError();
     return e;
   }
-  if (Bp > 0) {
-    tc2dw_sweep_kernel<<<(unsigned)(Bp / 128), kThreads, SS::kBytes, st>>>(img2, sw);
+  float* wgbuf = reinterpret_cast<float*>(w + L.wg);
+  float* ro = reinterpret_cast<float*>(w + L.ro);
+  // passes over positions [t0, t1), last first: the sweep's carries (in
+  // global memory) run on from one pass into the next
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int t0 = sg * S, t1 = t0 + S < g.N ? t0 + S : g.N;
+    const int64_t cells = Bp * (t1 - t0), nkb = cells / 16;
+    // 1. tape pass
+    a.t0 = t0;
+    a.t1 = t1;
+    const int64_t ntile = (int64_t)(t1 - t0) * (Bp / 128);
+    if ((e = launch_w<4>(a, wimg, ntile < sm_count_w() ? ntile : sm_count_w(), st)) != cudaSuccess) return e;
+    // 2. sequential sweep
+    sw.t0 = t0;
+    sw.t1 = t1;
+    if (Bp > 0) {
+      tc2dw_sweep_kernel<<<(unsigned)(Bp / 128), kThreads, SS::kBytes, st>>>(img2, sw);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // 3. weight-gradient GEMMs and the readout gradients of this pass's cells
+    WgArgs wg{};
+    for (int t = 0; t < kWgTiles; ++t) {
+      const bool first = t < 12;
+      const int mt = first ? t / 2 : t - 12, nt = first ? t % 2 : 0;
+      wg.tiles[t].A = (first ? sw.g1 : a.g2) + (size_t)mt * nkb * 4096;
+      wg.tiles[t].Bm = first ? (nt == 0 ? a.x1a : a.x1b) : a.x2a;
+      wg.tiles[t].Bx = first ? (nt == 0 ? a.x1c : nullptr) : a.x2c;
+    }
+    wg.nkb = nkb;
+    wg.splits = kWgSplits;
+    wg.out = wgbuf + (size_t)sg * kWgTiles * kWgSplits * 128 * kWgCols;
+    wg.hdr = g.hdr;
+    if ((e = launch_wgrad<256>(wg, kWgTiles, st)) != cudaSuccess) return e;
+    tc2dw_readout_kernel<<<kRoBlocks, 288, 0, st>>>(a.ytape, a.gd, cells, ro + (size_t)sg * kRoBlocks * (WD + 1));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // 3. weight-gradient GEMMs and the readout gradients
-  WgArgs wg{};
-  for (int t = 0; t < kWgTiles; ++t) {
-    const bool first = t < 12;
-    const int mt = first ? t / 2 : t - 12, nt = first ? t % 2 : 0;
-    wg.tiles[t].A = (first ? sw.g1 : a.g2) + (size_t)mt * nkb * 4096;
-    wg.tiles[t].Bm = first ? (nt == 0 ? a.x1a : a.x1b) : a.x2a;
-    wg.tiles[t].Bx = first ? (nt == 0 ? a.x1c : nullptr) : a.x2c;
-  }
-  wg.nkb = nkb;
-  wg.splits = kWgSplits;
-  wg.out = reinterpret_cast<float*>(w + L.wg);
-  wg.hdr = g.hdr;
-  if ((e = launch_wgrad<256>(wg, kWgTiles, st)) != cudaSuccess) return e;
-  float* ro = reinterpret_cast<float*>(w + L.ro);
-  tc2dw_readout_kernel<<<kRoBlocks, 288, 0, st>>>(a.ytape, a.gd, cells, ro);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // 4. the flat gradient
   constexpr int D = WD;
   const int P = 6 * D * D + 10 * D + 2 * D * D + 4 * D + 2;
-  tc2dw_final_kernel<<<(P + 255) / 256, 256, 0, st>>>(wg.out, kWgSplits, ro, kRoBlocks, grad);
+  tc2dw_final_kernel<<<(P + 255) / 256, 256, 0, st>>>(wgbuf, kWgSplits, nseg, ro, nseg * kRoBlocks, grad);
   return cudaGetLastError();
 }
 

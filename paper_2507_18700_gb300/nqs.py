@@ -25,7 +25,7 @@ STATUS = {0: "NQS_OK", 1: "NQS_EINVAL", 2: "NQS_ESHAPE", 3: "NQS_EWORKSPACE", 4:
 EXPORTS = ["nqs_param_count", "nqs_workspace_bytes", "nqs_grow_hidden", "nqs_sample", "nqs_logpsi",
            "nqs_local_energy", "nqs_local_energy_static", "nqs_logpsi_grad", "nqs_vmc_grad", "nqs_workspace_status",
            "nqs_status_string", "nqs_vmc_step_batched_workspace_bytes", "nqs_vmc_step_batched",
-           "nqs_set_autotune", "nqs_set_tile_variant", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit", "nqs_adam_step",
+           "nqs_set_autotune", "nqs_set_tile_variant", "nqs_set_sweep_segment", "nqs_energy_sums", "nqs_vmc_grad_global", "nqs_set_wait_limit", "nqs_adam_step",
            "nqs_record_stats", "nqs_evaluate_workspace_bytes", "nqs_evaluate", "nqs_ckpt_floats",
            "nqs_ckpt_workspace_bytes", "nqs_logpsi_ckpt", "nqs_logpsi_grad_ckpt"]
 
@@ -172,6 +172,8 @@ def lib():
     L.nqs_set_autotune.argtypes = [ctypes.c_int]
     L.nqs_set_tile_variant.restype = None
     L.nqs_set_tile_variant.argtypes = [ctypes.c_int]
+    L.nqs_set_sweep_segment.restype = None
+    L.nqs_set_sweep_segment.argtypes = [ctypes.c_int32]
     L.nqs_status_string.restype = ctypes.c_char_p
     L.nqs_status_string.argtypes = [ctypes.c_int]
     _lib = L
@@ -214,6 +216,12 @@ def set_wait_limit(polls):
     """Bound of the tensor-core waits that may give up (None: the default);
     0 makes every such wait give up at once (testing NQS_ETIMEOUT)."""
     _check(lib().nqs_set_wait_limit(-1 if polls is None else int(polls)), "nqs_set_wait_limit")
+
+
+def set_sweep_segment(positions):
+    """Positions per pass of the d_h = 256 2D BF16 reverse sweep (None or 0:
+    one pass); workspace sizes follow the setting."""
+    lib().nqs_set_sweep_segment(0 if positions is None else int(positions))
 
 
 def set_tile_variant(variant):

@@ -164,3 +164,24 @@ def test_static_scratch_call_rejects_bad_descriptors_like_the_workspace_call(L):
     assert f(ctypes.byref(nqs.model_desc(1, 12, 1, 8, precision=nqs.BF16)), fake, ctypes.byref(ham), fake, fake,
              4, fake, None) == 7
     assert f(ctypes.byref(nqs.model_desc(2, 4, 4, 8)), fake, ctypes.byref(ham), fake, fake, 4, fake, None) == 7
+
+
+def test_sweep_segment_bounds_the_wide_gradient_workspace(L):
+    """Passes of k positions in the d_h = 256 2D BF16 reverse sweep keep tapes
+    for B k cells instead of B N: the gradient workspace at 16 x 16, B = 8192
+    shrinks with k, and 0 restores the one-pass size."""
+    desc = nqs.model_desc(nqs.GRU2D, 16, 16, 256, sz0=True, precision=nqs.BF16)
+    size = lambda: L.nqs_workspace_bytes(ctypes.byref(desc), None, 8192, nqs.OP_LOGPSI_GRAD)
+    try:
+        one = size()
+        L.nqs_set_sweep_segment(16)
+        k16 = size()
+        L.nqs_set_sweep_segment(64)
+        k64 = size()
+    finally:
+        L.nqs_set_sweep_segment(0)
+    assert size() == one
+    # tapes ~7.2 KB per (sample, position): B N of them in one pass
+    assert one > 8192 * 256 * 7000
+    assert k16 < k64 < one
+    assert k16 < one / 10

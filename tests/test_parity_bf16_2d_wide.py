@@ -173,6 +173,35 @@ def test_wide_logpsi_grad(Lx, Ly, B, sz0):
     assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
 
 
+@pytest.mark.parametrize("Lx,Ly,B,seg", [(4, 4, 100, 5), (5, 4, 130, 7), (16, 16, 4, 16), (16, 16, 4, 100)])
+def test_wide_logpsi_grad_segmented(Lx, Ly, B, seg):
+    """The reverse sweep in passes of `seg` positions (the last pass first,
+    the carries running on between passes; ragged last pass where seg does not
+    divide N) gives the one-pass gradient to rounding, and the oracle's within
+    the BF16 tolerance."""
+    desc, d32, mod, pf, p = setup(Lx, Ly, D, True, seed=5, noise=0.05 if Lx * Ly <= 64 else 0.0)
+    sig = inputs.random_configs(B, mod.N, seed=6, sz0=True)
+    w = inputs.random_weights(B, seed=7).astype(np.float32)
+    sg = dev(sig, torch.uint8)
+    ws = nqs.Workspace(DEV)
+    _, hc = nqs.logpsi(desc, p, sg, ws=ws)
+    one = nqs.logpsi_grad(desc, p, sg, hc, dev(w), ws=ws).clone()
+    try:
+        nqs.set_sweep_segment(seg)
+        g = nqs.logpsi_grad(desc, p, sg, hc, dev(w), ws=ws).clone()
+    finally:
+        nqs.set_sweep_segment(0)
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    one, g = one.double().cpu().numpy(), g.double().cpu().numpy()
+    assert np.isfinite(g).all()
+    assert np.linalg.norm(g - one) <= 1e-5 * np.linalg.norm(one), np.linalg.norm(g - one) / np.linalg.norm(one)
+    ref = ov.logpsi_grad(mod, pf, sig.astype(np.int64), w.astype(np.float64))
+    cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert cos >= 0.999 and rel <= 2e-2, (cos, rel)
+
+
 def test_wide_full_size_16x16_b8192():
     """The 16 x 16, d_h = 256 Heisenberg step at B = 8192 in BF16: status clean,
     every draw of 64 samples checked against the oracle, and on 64 samples the
