@@ -307,9 +307,9 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
   };
   // Chains: the original state of lattice site k of sample b.
   auto fetch_orig = [&](float* dst, int k) { fetch(dst, a.hcache + (b * N + k) * D); };
-  // Inputs of the cell at position t (after the row moved there): sources and copies.
-  auto plan_inputs = [&](bool fresh) {
-    const Pz p = P(t);
+  // Inputs of the cell at position tn (the row's next cell): sources and copies.
+  auto plan_inputs = [&](int tn, bool fresh) {
+    const Pz p = P(tn);
     hsrc = 0;
     vsrc = 0;
     bool copies = false;
@@ -324,7 +324,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     if (p.j > 0) {
       const int q = zsnake(p.i, p.j - 1, Lx);
-      if (!fresh && q == t - 1) {
+      if (!fresh && q == tn - 1) {
         vsrc = 1;               // the state just computed (first cell of a row)
       } else if (MODE == 2 && q <= pa) {
         fetch_orig(vs, (p.j - 1) * Lx + p.i);
@@ -333,15 +333,14 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       } else {
         // recomputed by this row (at least two cells back): its packed hi / lo
         // words go straight into the A operand's vertical-input columns
+        // (replicated rows: into the first copy only; step (a) replicates it)
         const uint8_t* src = reinterpret_cast<const uint8_t*>(colrow + p.i * D);
+        const int row = REP == 4 ? r : m;
 #pragma unroll
-        for (int c = u0 / 8; c < u0 / 8 + DU / 8; ++c)
-#pragma unroll
-          for (int c4 = 0; c4 < REP; ++c4) {
-            const int row = REP == 4 ? r + 32 * c4 : m;
-            cp_async16_2d(sA + tc::kmajor_offset(row, D + 8 * c, KA1), src + 16 * c);
-            cp_async16_2d(sA + tc::kmajor_offset(row, K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
-          }
+        for (int c = u0 / 8; c < u0 / 8 + DU / 8; ++c) {
+          cp_async16_2d(sA + tc::kmajor_offset(row, D + 8 * c, KA1), src + 16 * c);
+          cp_async16_2d(sA + tc::kmajor_offset(row, K1 + D + 8 * c, KA1), src + 2 * D + 16 * c);
+        }
         vsrc = 3;
         copies = true;
       }
@@ -350,7 +349,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     if constexpr (MODE == 2) {
       const int k = p.j * Lx + p.i;
       const int so = mbit(mask, k) ^ ((k == bsa || k == bsb) ? 1 : 0);   // original spin at k
-      lp_next = ldg_f32_v(a.lp_tab + (b * N + t) * 2 + so);
+      lp_next = ldg_f32_v(a.lp_tab + (b * N + tn) * 2 + so);
     }
   };
   // Chains: take job j (or go idle).
@@ -372,7 +371,7 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
 #pragma unroll
     for (int w = 0; w < NW; ++w) mask[w] = jb.mask[w];
     active = true;
-    plan_inputs(true);
+    plan_inputs(t, true);
   };
   // warp-aggregated pull of one job for every lane with `need`, in two halves
   // called by all lanes: the atomic is issued first and its result is read
@@ -422,6 +421,23 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       const Pz p = P(t);
       if (p.r > 0) s_h = mbit(mask, p.j * Lx + zhor(p));
       if (p.j > 0) s_v = mbit(mask, (p.j - 1) * Lx + p.i);
+    }
+    if (REP == 4 && active && vsrc == 3) {
+      // the vertical input copied into the first copy of the row: to the others
+      // (reads first: interleaved with the writes they would serialise)
+      uint4 vh[DU / 8], vl[DU / 8];
+#pragma unroll
+      for (int c = 0; c < DU / 8; ++c) {
+        vh[c] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(r, D + u0 + 8 * c, KA1));
+        vl[c] = *reinterpret_cast<const uint4*>(sA + tc::kmajor_offset(r, K1 + D + u0 + 8 * c, KA1));
+      }
+#pragma unroll
+      for (int c4 = 1; c4 < REP; ++c4)
+#pragma unroll
+        for (int c = 0; c < DU / 8; ++c) {
+          *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r + 32 * c4, D + u0 + 8 * c, KA1)) = vh[c];
+          *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(r + 32 * c4, K1 + D + u0 + 8 * c, KA1)) = vl[c];
+        }
     }
 #pragma unroll
     for (int c4 = 0; c4 < REP; ++c4) {
@@ -565,19 +581,30 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
       const int kc = MODE != 2 ? P(step).j * Lx + P(step).i : 0;
       const float* pbase = MODE == 2 ? sHS : sVS;
       if constexpr (NSL == 1) {
-        constexpr int L = D / 4, RPI = 32 / L;
+        // groups of G rows: all shared reads of a group, then its global
+        // stores (interleaved, the stores would serialise behind the reads)
+        constexpr int L = D / 4, RPI = 32 / L, G = 4;
         const int lr = lane / L, lq = lane % L;
-#pragma unroll 4
-        for (int i = 0; i < 32; i += RPI) {
-          const int mr = warp * 32 + i + lr;
-          const int ci = sCol[mr];
-          if (ci >= 0) {
-            const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
-            reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D)[lq] =
-                reinterpret_cast<const float4*>(pbase + mr * S::HS)[lq];
-            if (MODE != 2 && a.hcache)
-              reinterpret_cast<float4*>(a.hcache + (((int64_t)blockIdx.x * 128 + mr) * N + kc) * D)[lq] =
-                  reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
+#pragma unroll
+        for (int i0 = 0; i0 < 32; i0 += RPI * G) {
+          int ci[G];
+          float4 vp[G], vf[G];
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int mr = warp * 32 + i0 + RPI * g + lr;
+            ci[g] = sCol[mr];
+            vp[g] = reinterpret_cast<const float4*>(pbase + mr * S::HS)[lq];
+            if (MODE != 2) vf[g] = reinterpret_cast<const float4*>(sHS + mr * S::HS)[lq];
+          }
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int mr = warp * 32 + i0 + RPI * g + lr;
+            if (ci[g] >= 0) {
+              const int64_t slot = (int64_t)blockIdx.x * 128 + mr;
+              reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci[g]) * D)[lq] = vp[g];
+              if (MODE != 2 && a.hcache)
+                reinterpret_cast<float4*>(a.hcache + (slot * N + kc) * D)[lq] = vf[g];
+            }
           }
         }
       } else {
@@ -585,21 +612,35 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
         // DU / 8 packed hi, DU / 8 packed lo and (forward modes) DU / 4 FP32
         // pieces of 16 bytes per row
         constexpr int PH = DU / 8, PF = MODE != 2 ? DU / 4 : 0, PPR = 2 * PH + PF;
+        constexpr int NIT = PPR, G = NIT < 4 ? NIT : 4;   // 32 * PPR pieces, 32 per pass
+        static_assert(NIT % G == 0, "store groups");
         const int m0 = REP == 4 ? 0 : (warp % 4) * 32;
-#pragma unroll 4
-        for (int idx = lane; idx < 32 * PPR; idx += 32) {
-          const int mr = m0 + idx / PPR, pc = idx % PPR;
-          const int ci = sCol[mr];
-          if (ci >= 0) {
-            const int64_t slot = (int64_t)blockIdx.x * RT + mr;
-            if (pc < 2 * PH) {
-              const int off = (pc < PH ? u0 / 2 : D / 2 + u0 / 2) + 4 * (pc % PH);
-              *reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci) * D + off) =
-                  *reinterpret_cast<const float4*>(pbase + mr * S::HS + off);
-            } else if (MODE != 2 && a.hcache) {
-              const int off = u0 + 4 * (pc - 2 * PH);
-              *reinterpret_cast<float4*>(a.hcache + (slot * N + kc) * D + off) =
-                  *reinterpret_cast<const float4*>(sHS + mr * S::HS + off);
+        // groups of G pieces per lane: all shared reads, then the global stores
+#pragma unroll
+        for (int it0 = 0; it0 < NIT; it0 += G) {
+          int ci[G];
+          float4 v[G];
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int idx = lane + 32 * (it0 + g);
+            const int mr = m0 + idx / PPR, pc = idx % PPR;
+            ci[g] = sCol[mr];
+            const int off = pc < 2 * PH ? (pc < PH ? u0 / 2 : D / 2 + u0 / 2) + 4 * (pc % PH) : u0 + 4 * (pc - 2 * PH);
+            v[g] = *reinterpret_cast<const float4*>((pc < 2 * PH ? pbase : sHS) + mr * S::HS + off);
+          }
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int idx = lane + 32 * (it0 + g);
+            const int mr = m0 + idx / PPR, pc = idx % PPR;
+            if (ci[g] >= 0) {
+              const int64_t slot = (int64_t)blockIdx.x * RT + mr;
+              if (pc < 2 * PH) {
+                const int off = (pc < PH ? u0 / 2 : D / 2 + u0 / 2) + 4 * (pc % PH);
+                *reinterpret_cast<float4*>(a.colbuf + (slot * Lx + ci[g]) * D + off) = v[g];
+              } else if (MODE != 2 && a.hcache) {
+                const int off = u0 + 4 * (pc - 2 * PH);
+                *reinterpret_cast<float4*>(a.hcache + (slot * N + kc) * D + off) = v[g];
+              }
             }
           }
         }
@@ -612,6 +653,12 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     }
     ph1 ^= 1;
     tc::fence_after_sync();
+    // sampling / teacher forcing: the next position does not depend on this
+    // cell's outcome, so its input copies go out now (the A operand is free)
+    // and land during epilogue 2 and the row logic
+    if constexpr (MODE != 2) {
+      if (active && !timed_out && t + 1 < N) plan_inputs(t + 1, false);
+    }
     // ---- (e) epilogue 2: GLU and the logit difference (16-unit chunks in
     // order, chunks by a fixed pairwise tree) ----
     float zc[DU / 16];
@@ -685,8 +732,8 @@ tc2d_engine_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
           if (!isfinite(lpsi)) flag_status(a.hdr, NQS_ENONFINITE);
           active = false;
         }
-      } else {
-        plan_inputs(false);
+      } else if constexpr (MODE == 2) {
+        plan_inputs(t, false);
       }
     }
     if constexpr (MODE == 2) {
