@@ -77,28 +77,45 @@ __global__ void vmc_weights_kernel(const float* __restrict__ eloc, const double*
     w[i] = (float)(2.0 * ((double)eloc[i] - mean) / M);
 }
 
-// grad[p] = sum_r partial[r][p], accumulated in FP64 in a fixed order and
-// written as T (float, or double for gradients that are summed over ranks).
-// A block sums 32 columns: 8 row groups (r = g mod 8) per column, each with
-// 4 independent FP64 accumulators, then the 8 group sums in a fixed tree.
+// grad[p] = sum_r partial[r][p] in a fixed order, written as T (float, or
+// double for gradients that are summed over ranks).  The accumulators are
+// unevaluated pairs hi + lo of FP32 words updated with Knuth's two-sum (s =
+// hi + x exactly equals s_rounded + e), so that each keeps about 48
+// significant bits, like an FP64 sum of FP32 terms, while running on the FP32
+// pipe (GB300's FP64 rate is a small fraction of it: with FP64 adds and
+// conversions this reduction took ~44 us for 304 rows x 34 k columns).
+// A block sums 32 columns: 8 row groups (r = g mod 8) per column, each with 4
+// independent accumulators, then the 8 group sums in a fixed tree in FP64.
+struct Fsum {
+  float hi, lo;
+};
+__device__ __forceinline__ void fsum_add(Fsum& a, float x) {
+  const float s = a.hi + x;
+  const float bp = s - a.hi;
+  const float e = (a.hi - (s - bp)) + (x - bp);   // two-sum: a.hi + x = s + e exactly
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ double fsum_value(const Fsum& a) { return (double)a.hi + (double)a.lo; }
+
 template <typename T>
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float* __restrict__ partial, int rows, int P,
                                                               int64_t ld, T* __restrict__ grad) {
   __shared__ double red[8][33];
   const int col = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + col;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  Fsum a0{0.0f, 0.0f}, a1{0.0f, 0.0f}, a2{0.0f, 0.0f}, a3{0.0f, 0.0f};
   if (p < P) {
     int r = g;
     for (; r + 24 < rows; r += 32) {
-      a0 += (double)partial[(size_t)r * ld + p];
-      a1 += (double)partial[(size_t)(r + 8) * ld + p];
-      a2 += (double)partial[(size_t)(r + 16) * ld + p];
-      a3 += (double)partial[(size_t)(r + 24) * ld + p];
+      fsum_add(a0, partial[(size_t)r * ld + p]);
+      fsum_add(a1, partial[(size_t)(r + 8) * ld + p]);
+      fsum_add(a2, partial[(size_t)(r + 16) * ld + p]);
+      fsum_add(a3, partial[(size_t)(r + 24) * ld + p]);
     }
-    for (; r < rows; r += 8) a0 += (double)partial[(size_t)r * ld + p];
+    for (; r < rows; r += 8) fsum_add(a0, partial[(size_t)r * ld + p]);
   }
-  red[g][col] = (a0 + a1) + (a2 + a3);
+  red[g][col] = (fsum_value(a0) + fsum_value(a1)) + (fsum_value(a2) + fsum_value(a3));
   __syncthreads();
   if (g == 0 && p < P) {
     const double s = ((red[0][col] + red[1][col]) + (red[2][col] + red[3][col])) +

@@ -103,11 +103,26 @@ __global__ void heis_count_kernel(const uint8_t* __restrict__ sigma, const int4*
   }
 }
 
+// Configuration of every sample as a bit mask (bit k = spin of site k).
+template <int NW>
+__global__ void heis_masks_kernel(const uint8_t* __restrict__ sigma, int64_t B, int N, uint64_t* __restrict__ masks) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  uint64_t m[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) m[w] = 0ull;
+  for (int k = 0; k < N; ++k)
+    if (sigma[b * N + k]) m[k >> 6] |= 1ull << (k & 63);
+#pragma unroll
+  for (int w = 0; w < NW; ++w) masks[b * NW + w] = m[w];
+}
+
 template <int NW>
 __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restrict__ sigma, const int4* __restrict__ bonds,
                                                         const float* __restrict__ lp_tab, const int* __restrict__ nup_tab,
-                                                        const int* __restrict__ counts, int64_t B, int N, int nb,
-                                                        JobT<NW>* __restrict__ jobs, int* __restrict__ njobs) {
+                                                        const int* __restrict__ counts, const uint64_t* __restrict__ masks,
+                                                        int64_t B, int N, int nb, JobT<NW>* __restrict__ jobs,
+                                                        int* __restrict__ njobs) {
   __shared__ int wsum[32];
   __shared__ int base_s;
   const int rank = blockIdx.x;
@@ -148,11 +163,13 @@ __global__ void __launch_bounds__(1024) heis_jobs_kernel(const uint8_t* __restri
       // bond.x sits at position pa and takes the partner's spin sb
       jb.acc0 = 0.5f * (lp_tab[(row + pa) * 2 + sb] - lp_tab[(row + pa) * 2 + sa]);
       jb.nup_b = (nup_tab[row + pa] + (sb == 0 ? 1 : 0)) | (bd.y << 16);
+      // the exchanged configuration: the two antiparallel spins swap, i.e. both flip
 #pragma unroll
-      for (int w = 0; w < NW; ++w) jb.mask[w] = 0ull;
-      for (int k = 0; k < N; ++k) {
-        const int kk = k == bd.x ? bd.y : k == bd.y ? bd.x : k;
-        if (sigma[row + kk]) jb.mask[k >> 6] |= 1ull << (k & 63);
+      for (int w = 0; w < NW; ++w) {
+        uint64_t mw = masks[b * NW + w];
+        if ((bd.x >> 6) == w) mw ^= 1ull << (bd.x & 63);
+        if ((bd.y >> 6) == w) mw ^= 1ull << (bd.y & 63);
+        jb.mask[w] = mw;
       }
       jobs[idx] = jb;
     }
@@ -1473,9 +1490,14 @@ size_t tc2d_wimg_bytes(int D) {
 // engine is the d_h <= 64 one, 256-bit masks otherwise
 static bool wide_jobs(int N, int D) { return N > 128 || D == 256; }
 
-size_t tc2d_jobs_bytes(int64_t B, int nb, int N, int D) {
+// [job records | counts (nb) and the job count | sample masks (16-byte aligned)]
+static size_t jobs_masks_offset(int64_t B, int nb, int N, int D) {
   const size_t rec = wide_jobs(N, D) ? sizeof(JobT<4>) : sizeof(JobT<2>);
-  return (size_t)B * nb * rec + (size_t)(nb + 4) * sizeof(int);
+  return ((size_t)B * nb * rec + (size_t)(nb + 4) * sizeof(int) + 15) / 16 * 16;
+}
+
+size_t tc2d_jobs_bytes(int64_t B, int nb, int N, int D) {
+  return jobs_masks_offset(B, nb, N, D) + (size_t)B * (wide_jobs(N, D) ? 4 : 2) * sizeof(uint64_t);
 }
 
 cudaError_t tc2d_pack(const float* params, uint8_t* wimg, int D, cudaStream_t st) {
@@ -1558,15 +1580,20 @@ cudaError_t tc2d_heis_chains(const Tc2Chains& c, const uint8_t* wimg, int D, cud
   const size_t rec = wide ? sizeof(JobT<4>) : sizeof(JobT<2>);
   int* counts = reinterpret_cast<int*>(jb + (size_t)c.B * c.nb * rec);
   int* njobs = counts + c.nb;
+  uint64_t* masks = reinterpret_cast<uint64_t*>(jb + jobs_masks_offset(c.B, c.nb, c.N, D));
   heis_count_kernel<<<c.nb, 256, 0, st>>>(c.sigma, c.bonds, c.B, c.N, counts);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (!wide)
-    heis_jobs_kernel<2><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb,
+  const unsigned mblocks = (unsigned)((c.B + 255) / 256);
+  if (!wide) {
+    if (mblocks) heis_masks_kernel<2><<<mblocks, 256, 0, st>>>(c.sigma, c.B, c.N, masks);
+    heis_jobs_kernel<2><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, masks, c.B, c.N, c.nb,
                                                 reinterpret_cast<JobT<2>*>(jb), njobs);
-  else
-    heis_jobs_kernel<4><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, c.B, c.N, c.nb,
+  } else {
+    if (mblocks) heis_masks_kernel<4><<<mblocks, 256, 0, st>>>(c.sigma, c.B, c.N, masks);
+    heis_jobs_kernel<4><<<c.nb, 1024, 0, st>>>(c.sigma, c.bonds, c.lp_tab, c.nup_tab, counts, masks, c.B, c.N, c.nb,
                                                 reinterpret_cast<JobT<4>*>(jb), njobs);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c.counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
   if (D == 256) return tc2dw_chains(c, wimg, jb, njobs, st);
