@@ -113,10 +113,14 @@ __device__ __forceinline__ float masked_lp(int s, float d, int n_up, int n_done,
 // (lattice a, lattice b, zig-zag position of a, of b), pa < pb, sorted by pa
 // (longest chains first).  One block.
 // ----------------------------------------------------------------------------
+template <bool SH>
 __global__ void bonds2d_kernel(int Lx, int Ly, int4* __restrict__ out) {
+  // bond k: sites (a, b), zig-zag positions (pa, pb) with pa < pb; ranked by
+  // (pa, k) against every bond's pa, kept in shared memory (SH) or recomputed
+  // (lattices whose keys do not fit)
+  extern __shared__ int key[];
   const int nh = (Lx - 1) * Ly, nb = nh + Lx * (Ly - 1);
-  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    int a, b;
+  auto bond = [&](int k, int& a, int& b, int& pa, int& pb) {
     if (k < nh) {
       const int j = k / (Lx - 1), i = k % (Lx - 1);
       a = j * Lx + i;
@@ -126,25 +130,33 @@ __global__ void bonds2d_kernel(int Lx, int Ly, int4* __restrict__ out) {
       a = j * Lx + i;
       b = a + Lx;
     }
-    int pa = snake_pos(a % Lx, a / Lx, Lx), pb = snake_pos(b % Lx, b / Lx, Lx);
+    pa = snake_pos(a % Lx, a / Lx, Lx);
+    pb = snake_pos(b % Lx, b / Lx, Lx);
     if (pa > pb) {
       int t = pa; pa = pb; pb = t;
       t = a; a = b; b = t;
     }
-    // rank by (pa, k)
+  };
+  if constexpr (SH) {
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      int a, b, pa, pb;
+      bond(k, a, b, pa, pb);
+      key[k] = pa;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    int a, b, pa, pb;
+    bond(k, a, b, pa, pb);
     int rank = 0;
     for (int q = 0; q < nb; ++q) {
-      int qa, qb;
-      if (q < nh) {
-        const int j = q / (Lx - 1), i = q % (Lx - 1);
-        qa = j * Lx + i; qb = qa + 1;
+      int qa = 0, qb = 0, qpa = 0, qpb = 0;
+      if constexpr (SH) {
+        qpa = key[q];
       } else {
-        const int w = q - nh, j = w / Lx, i = w % Lx;
-        qa = j * Lx + i; qb = qa + Lx;
+        bond(q, qa, qb, qpa, qpb);
       }
-      const int p1 = snake_pos(qa % Lx, qa / Lx, Lx), p2 = snake_pos(qb % Lx, qb / Lx, Lx);
-      const int qp = p1 < p2 ? p1 : p2;
-      rank += (qp < pa) || (qp == pa && q < k);
+      rank += (qpa < pa) || (qpa == pa && q < k);
     }
     out[rank] = make_int4(a, b, pa, pb);
   }
@@ -897,7 +909,12 @@ cudaError_t gru2d_forward(const Eng2Args& a, const float* img, int D, bool sampl
 }
 
 cudaError_t gru2d_bonds(int Lx, int Ly, int4* bonds, cudaStream_t st) {
-  bonds2d_kernel<<<1, 256, 0, st>>>(Lx, Ly, bonds);
+  const int nb = (Lx - 1) * Ly + Lx * (Ly - 1);
+  if (nb <= 0) return cudaSuccess;
+  if ((size_t)nb * sizeof(int) <= 48 * 1024)
+    bonds2d_kernel<true><<<1, 256, (size_t)nb * sizeof(int), st>>>(Lx, Ly, bonds);
+  else
+    bonds2d_kernel<false><<<1, 256, 0, st>>>(Lx, Ly, bonds);
   return cudaGetLastError();
 }
 

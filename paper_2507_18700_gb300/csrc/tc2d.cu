@@ -803,7 +803,7 @@ struct Tab2Args {
 };
 
 template <int D>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 3)
 tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ aux, Tab2Args a) {
   using S = T2S<D>;
   constexpr int K2 = S::K2, KA2 = S::KA2;
@@ -1545,8 +1545,10 @@ cudaError_t launch_tables(const Tab2Args& a, const uint8_t* w2, const float* aux
   auto k = tc2d_tables_kernel<D>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, T2S<D>::kBytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  // three CTAs per SM (60 KB of shared memory, 128 TMEM columns each at d_h
+  // 64), so that one tile's loads and MMA overlap the others' epilogues
   const int64_t ntile = (a.B * a.N + 127) / 128;
-  const int64_t grid = ntile < sm_count_2d() ? ntile : sm_count_2d();
+  const int64_t grid = ntile < 3 * sm_count_2d() ? ntile : 3 * sm_count_2d();
   if (grid < 1) return cudaSuccess;
   k<<<(unsigned)grid, 128, T2S<D>::kBytes, st>>>(w2, aux, a);
   return cudaGetLastError();
