@@ -226,15 +226,15 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
         const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
         const float* src =
             hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+        // all loads of the state first (interleaved with the shared stores
+        // they would serialise), then its hi / lo rows
+        float v[D];
 #pragma unroll
-        for (int c = 0; c < D / 16; ++c) {
-          float v[16];
-          ld16(src + 16 * c, ok, v);
-          st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c, KA1),
-                    sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c, KA1), v);
-          st_split8(sA1 + tc::kmajor_offset(m, half * D + 16 * c + 8, KA1),
-                    sA1 + tc::kmajor_offset(m, K1 + half * D + 16 * c + 8, KA1), v + 8);
-        }
+        for (int c = 0; c < D / 16; ++c) ld16(src + 16 * c, ok, *reinterpret_cast<float(*)[16]>(v + 16 * c));
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c)
+          st_split8(sA1 + tc::kmajor_offset(m, half * D + 8 * c, KA1), sA1 + tc::kmajor_offset(m, K1 + half * D + 8 * c, KA1),
+                    v + 8 * c);
       }
       {
         const uint32_t oh = s_h < 0 ? 0u : (s_h == 0 ? one : (one << 16));
@@ -242,12 +242,13 @@ tc2d_tape_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict__ 
         *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D, KA1)) = make_uint4(one | (one << 16), oh, ov, oh);
         *reinterpret_cast<uint4*>(sA1 + tc::kmajor_offset(m, 2 * D + 8, KA1)) = make_uint4(ov, 0u, 0u, 0u);
       }
+      {
+        float v[D];
 #pragma unroll
-      for (int c = 0; c < D / 16; ++c) {
-        float v[16];
-        ld16(hc + (int64_t)k * D + 16 * c, valid, v);
-        st_split8(sA2 + tc::kmajor_offset(m, 16 * c, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c, KA2), v);
-        st_split8(sA2 + tc::kmajor_offset(m, 16 * c + 8, KA2), sA2 + tc::kmajor_offset(m, K2 + 16 * c + 8, KA2), v + 8);
+        for (int c = 0; c < D / 16; ++c) ld16(hc + (int64_t)k * D + 16 * c, valid, *reinterpret_cast<float(*)[16]>(v + 16 * c));
+#pragma unroll
+        for (int c = 0; c < D / 8; ++c)
+          st_split8(sA2 + tc::kmajor_offset(m, 8 * c, KA2), sA2 + tc::kmajor_offset(m, K2 + 8 * c, KA2), v + 8 * c);
       }
       *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
       *reinterpret_cast<uint4*>(sA2 + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
@@ -779,23 +780,25 @@ __global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
     const Pz p = zpos(t, Lx);
     const uint8_t* sg = a.sigma + (valid ? b : 0) * N;
     const float* hc = a.hcache + (valid ? b : 0) * (int64_t)N * D;
-    // G images (this thread copies a 1/128 share of each)
+    // G images (this thread copies a 1/128 share of each), asynchronously:
+    // they land while the X operands are built
     const uint4* g1 = reinterpret_cast<const uint4*>(a.g1img + (size_t)im * 128 * GW1 * 2);
     const uint4* g2 = reinterpret_cast<const uint4*>(a.g2img + (size_t)im * 128 * GW2 * 2);
-    for (int q = m; q < 128 * GW1 * 2 / 16; q += 128) reinterpret_cast<uint4*>(sG1)[q] = g1[q];
-    for (int q = m; q < 128 * GW2 * 2 / 16; q += 128) reinterpret_cast<uint4*>(sG2)[q] = g2[q];
+    for (int q = m; q < 128 * GW1 * 2 / 16; q += 128) cp_async16_cg(reinterpret_cast<uint4*>(sG1) + q, g1 + q);
+    for (int q = m; q < 128 * GW2 * 2 / 16; q += 128) cp_async16_cg(reinterpret_cast<uint4*>(sG2) + q, g2 + q);
+    cp_commit_2d();
     // X1 = [h_hor | h_ver | 1 1 | onehot(s_hor) onehot(s_ver) x2 | 0], X2 = [h | 1 1 | 0]
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const bool ok = valid && (half == 0 ? p.r > 0 : p.j > 0);
       const float* src = hc + (int64_t)(half == 0 ? p.j * Lx + (p.r > 0 ? zhor(p) : 0) : (p.j > 0 ? (p.j - 1) * Lx + p.i : 0)) * D;
+      // all loads of the state first (interleaved with the shared stores
+      // they would serialise), then the BF16 rows
+      float v[D];
 #pragma unroll
-      for (int c = 0; c < D / 16; ++c) {
-        float v[16];
-        ld16(src + 16 * c, ok, v);
-        st_bf16_8(sX1 + tc::kmajor_offset(m, half * D + 16 * c, K1), v);
-        st_bf16_8(sX1 + tc::kmajor_offset(m, half * D + 16 * c + 8, K1), v + 8);
-      }
+      for (int c = 0; c < D / 16; ++c) ld16(src + 16 * c, ok, *reinterpret_cast<float(*)[16]>(v + 16 * c));
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) st_bf16_8(sX1 + tc::kmajor_offset(m, half * D + 8 * c, K1), v + 8 * c);
     }
     {
       const int s_h = p.r > 0 ? (valid ? (sg[p.j * Lx + zhor(p)] ? 1 : 0) : 0) : -1;
@@ -805,15 +808,17 @@ __global__ void __launch_bounds__(128, 1) tc2d_wgrad_kernel(Wgrad2Args a) {
       *reinterpret_cast<uint4*>(sX1 + tc::kmajor_offset(m, 2 * D, K1)) = make_uint4(one | (one << 16), oh, ov, oh);
       *reinterpret_cast<uint4*>(sX1 + tc::kmajor_offset(m, 2 * D + 8, K1)) = make_uint4(ov, 0u, 0u, 0u);
     }
+    {
+      float v[D];
 #pragma unroll
-    for (int c = 0; c < D / 16; ++c) {
-      float v[16];
-      ld16(hc + (int64_t)(p.j * Lx + p.i) * D + 16 * c, valid, v);
-      st_bf16_8(sX2 + tc::kmajor_offset(m, 16 * c, K2), v);
-      st_bf16_8(sX2 + tc::kmajor_offset(m, 16 * c + 8, K2), v + 8);
+      for (int c = 0; c < D / 16; ++c)
+        ld16(hc + (int64_t)(p.j * Lx + p.i) * D + 16 * c, valid, *reinterpret_cast<float(*)[16]>(v + 16 * c));
+#pragma unroll
+      for (int c = 0; c < D / 8; ++c) st_bf16_8(sX2 + tc::kmajor_offset(m, 8 * c, K2), v + 8 * c);
     }
     *reinterpret_cast<uint4*>(sX2 + tc::kmajor_offset(m, D, K2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(sX2 + tc::kmajor_offset(m, D + 8, K2)) = make_uint4(0u, 0u, 0u, 0u);
+    cp_wait_2d();
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
