@@ -848,12 +848,21 @@ tc2d_tables_kernel(const uint8_t* __restrict__ w2img, const float* __restrict__ 
     const int64_t b = valid ? cell / N : 0;
     const int t = valid ? (int)(cell % N) : 0;
     const float* hc = a.hcache + (b * N + sSite[t]) * D;
+    {
+      // all loads of the state first (interleaved with the shared stores they
+      // would serialise), then its hi / lo rows
+      float v[D];
 #pragma unroll
-    for (int c = 0; c < D / 8; ++c) {
-      float v[8];
+      for (int q = 0; q < D / 4; ++q) {
+        const float4 x = valid ? reinterpret_cast<const float4*>(hc)[q] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+      }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = valid ? hc[8 * c + q] : 0.0f;
-      st_split8(sA + tc::kmajor_offset(m, 8 * c, KA2), sA + tc::kmajor_offset(m, K2 + 8 * c, KA2), v);
+      for (int c = 0; c < D / 8; ++c)
+        st_split8(sA + tc::kmajor_offset(m, 8 * c, KA2), sA + tc::kmajor_offset(m, K2 + 8 * c, KA2), v + 8 * c);
     }
     *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D, KA2)) = make_uint4(one | (one << 16), 0u, 0u, 0u);
     *reinterpret_cast<uint4*>(sA + tc::kmajor_offset(m, D + 8, KA2)) = make_uint4(0u, 0u, 0u, 0u);
