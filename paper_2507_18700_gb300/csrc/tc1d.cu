@@ -36,7 +36,10 @@ namespace nqs {
 namespace {
 
 constexpr uint32_t kWaitLimit = tc::kDefaultWaitPolls;   // the drain's bound
-constexpr int kPPEarly = 0;   // ping-pong: sub-chunks of the epilogue left when the token is passed (0 = after the last)
+// ping-pong: sub-chunks of the epilogue left when the token is passed (0 =
+// after the last); measured on the TFIM N = 100, d_h = 64, B = 4096 step:
+// 1.782 ms with 0, 1.764 ms with 1, 1.798 ms with 2
+constexpr int kPPEarly = 1;
 
 // Gate weights with the biases and one-hot input columns folded in, as a
 // K-major BF16 operand of 4D rows x (D + 16) columns (see tc.cuh).  Biases and
