@@ -1254,22 +1254,30 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // | 0] keeps A1's horizontal hi columns and lo(h) goes to A1's horizontal
     // lo columns (MMA1 has completed), so that a next cell whose horizontal
     // input is h finds it in place ----
+    // (TMEM loads double-buffered: chunk c + 1's are in flight while chunk c
+    // is computed)
+    constexpr int NC = DU / 16;
+    uint32_t ra[2][3][16];
+    auto load1 = [&](int c, uint32_t (&r)[3][16]) {
+      tld16(trow + u0 + 16 * c, r[0]);
+      tld16(trow + D + u0 + 16 * c, r[1]);
+      tld16(trow + 2 * D + u0 + 16 * c, r[2]);
+    };
+    load1(0, ra[0]);
+    tc::tmem_wait_ld();
+    tie(ra[0][0]);
+    tie(ra[0][1]);
+    tie(ra[0][2]);
 #pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      uint32_t aw[16], ag[16], au[16];
-      tld16(trow + u0 + 16 * c, aw);
-      tld16(trow + D + u0 + 16 * c, ag);
-      tld16(trow + 2 * D + u0 + 16 * c, au);
-      tc::tmem_wait_ld();
-      tie(aw);
-      tie(ag);
-      tie(au);
+    for (int c = 0; c < NC; ++c) {
+      uint32_t (&cur)[3][16] = ra[c & 1];
+      if (c + 1 < NC) load1(c + 1, ra[(c + 1) & 1]);
       float h[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float cc = hw_tanh2(__uint_as_float(aw[q]));
-        const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(ag[q])), 0.5f);
-        const float mix = __uint_as_float(au[q]);
+        const float cc = hw_tanh2(__uint_as_float(cur[0][q]));
+        const float ug = fmaf(0.5f, hw_tanh2(__uint_as_float(cur[1][q])), 0.5f);
+        const float mix = __uint_as_float(cur[2][q]);
         h[q] = fmaf(ug, cc - mix, mix);
       }
       uint32_t hi[8], lo[8];
@@ -1281,6 +1289,12 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
             make_uint4(hi[4 * e], hi[4 * e + 1], hi[4 * e + 2], hi[4 * e + 3]);
         *reinterpret_cast<uint4*>(kmo(K1 + u0 + 16 * c + 8 * e, KA1)) =
             make_uint4(lo[4 * e], lo[4 * e + 1], lo[4 * e + 2], lo[4 * e + 3]);
+      }
+      if (c + 1 < NC) {
+        tc::tmem_wait_ld();
+        tie(ra[(c + 1) & 1][0]);
+        tie(ra[(c + 1) & 1][1]);
+        tie(ra[(c + 1) & 1][2]);
       }
     }
     if (part == 0) {
@@ -1356,28 +1370,42 @@ tc2d_chain2_kernel(const uint8_t* __restrict__ w1img, const uint8_t* __restrict_
     // ---- (e) epilogue 2: GLU and the logit difference (16-unit chunks in
     // order, chunks by a fixed pairwise tree) ----
     float zc[DU / 16];
-#pragma unroll
-    for (int c = 0; c < DU / 16; ++c) {
-      uint32_t a1[16], a2[16];
-      tld16(trow + u0 + 16 * c, a1);
-      tld16(trow + D + u0 + 16 * c, a2);
-      float u[16];   // U_0 - U_1 of these units, read while the TMEM loads are in flight
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float4 f = reinterpret_cast<const float4*>(sAux + u0 + 16 * c)[q];
-        u[4 * q] = f.x;
-        u[4 * q + 1] = f.y;
-        u[4 * q + 2] = f.z;
-        u[4 * q + 3] = f.w;
-      }
+    {
+      // TMEM loads double-buffered as in epilogue 1
+      constexpr int NC = DU / 16;
+      uint32_t rb[2][2][16];
+      auto load2 = [&](int c, uint32_t (&r)[2][16]) {
+        tld16(trow + u0 + 16 * c, r[0]);
+        tld16(trow + D + u0 + 16 * c, r[1]);
+      };
+      load2(0, rb[0]);
       tc::tmem_wait_ld();
-      tie(a1);
-      tie(a2);
-      zc[c] = 0.0f;
+      tie(rb[0][0]);
+      tie(rb[0][1]);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float y = __uint_as_float(a1[q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(a2[q])), 0.5f);
-        zc[c] = fmaf(u[q], y, zc[c]);
+      for (int c = 0; c < NC; ++c) {
+        uint32_t (&cur)[2][16] = rb[c & 1];
+        if (c + 1 < NC) load2(c + 1, rb[(c + 1) & 1]);
+        float u[16];   // U_0 - U_1 of these units
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 f = reinterpret_cast<const float4*>(sAux + u0 + 16 * c)[q];
+          u[4 * q] = f.x;
+          u[4 * q + 1] = f.y;
+          u[4 * q + 2] = f.z;
+          u[4 * q + 3] = f.w;
+        }
+        zc[c] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float y = __uint_as_float(cur[0][q]) * fmaf(0.5f, hw_tanh2(__uint_as_float(cur[1][q])), 0.5f);
+          zc[c] = fmaf(u[q], y, zc[c]);
+        }
+        if (c + 1 < NC) {
+          tc::tmem_wait_ld();
+          tie(rb[(c + 1) & 1][0]);
+          tie(rb[(c + 1) & 1][1]);
+        }
       }
     }
 #pragma unroll
