@@ -393,9 +393,10 @@ def run_gpu(args, w):
         mufu = sum(chosen["cells"]) * 3 * d / (sum(chosen["le_ms"]) * 1e-3) / 1e12
         mufu_peak = 152 * 16 * sm_mhz * 1e6 / 1e12
         # DRAM bytes of one chain launch, from an ncu capture of the 1D chain
-        # kernel at B = 1024 (dram__bytes_read.sum 26,543,616, write 0: the
-        # prefix cache read once), scaled by B (traffic grows with B)
-        traffic = (26543616 * B / 1024.0) if (w["cell"] == 1 and w["d"] == 64 and N == 100) else None
+        # kernel as it stands at B = 1024 (dram__bytes_read.sum 26,536,448,
+        # write 0: the prefix cache read once), scaled by B (traffic grows
+        # with B)
+        traffic = (26536448 * B / 1024.0) if (w["cell"] == 1 and w["d"] == 64 and N == 100) else None
         roof = {"bound": "tensor",
                 "kernel": "nqs_local_energy (prefix-cached %s chains, tcgen05 BF16)"
                           % ("TFIM" if w["cell"] == 1 else "Heisenberg"),
